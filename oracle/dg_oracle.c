@@ -1,0 +1,750 @@
+/*
+ * dg_oracle.c -- plain, slow, FP64 CPU reference of the modal Discontinuous
+ * Galerkin method of Cernetic, Springel, Guillet & Pakmor (2024), specialised
+ * to isothermal Euler (p = cs^2 rho) as used for driven supersonic turbulence.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark.  It shares no code, table or header with
+ * the CUDA library and must stay that way.
+ *
+ * Everything here follows the paper's definitions one step at a time:
+ *   - basis expansion and orthonormality ............ Sec. 2.1, eq. (state_vector_expansion)
+ *   - weak form / weight evolution ................. Sec. 2.2, eqs. (weakform), (weight_evolution)
+ *   - Gauss quadrature with (k+1) points per axis ... Sec. 2.2 and Sec. 7 (v_k, s_k)
+ *   - von Neumann-Richtmyer viscous pressure ........ Sec. 3.1 (quadratic + linear term, Pi_max)
+ *   - positivity check and rescaling ............... Sec. 3.1, last paragraph before 3.1.1
+ *   - primitive-variable projection ................ Sec. 3.2, eq. (weights_equation)
+ *   - Ornstein-Uhlenbeck driving ................... Sec. 4.2, eqs. (ornstein_uhlenbeck...), (eddy_turnover_time)
+ *   - SSP Runge-Kutta stages and dt ~ h/(k+1) ....... Sec. 7
+ * Basis values and derivatives are evaluated directly (product of 1D
+ * Legendre values) at every point; no sum factorisation, no modal
+ * differentiation, no batching.  Readings where the paper is silent are the
+ * ones documented with the library (isothermal EOS, Rusanov flux, quotient-rule
+ * divergence, CFL formula, OU normalisation, SplitMix64 + Box-Muller).
+ */
+#include "dg_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* 1D building blocks                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Legendre P_m(x) by Bonnet's recurrence (m+1)P_{m+1} = (2m+1) x P_m - m P_{m-1}. */
+double orc_legendre(int m, double x)
+{
+    if (m == 0) return 1.0;
+    double p0 = 1.0, p1 = x;
+    for (int j = 1; j < m; ++j) {
+        double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+/* P'_m(x) from P'_{j+1} = P'_{j-1} + (2j+1) P_j (valid on the closed interval). */
+double orc_legendre_deriv(int m, double x)
+{
+    if (m == 0) return 0.0;
+    if (m == 1) return 1.0;
+    double dm1 = 0.0, d0 = 1.0; /* P'_0, P'_1 */
+    for (int j = 1; j < m; ++j) {
+        double d = dm1 + (2.0 * j + 1.0) * orc_legendre(j, x);
+        dm1 = d0;
+        d0 = d;
+    }
+    return d0;
+}
+
+/* normalised Legendre sqrt(2m+1) P_m: (1/2) int_{-1}^{1} Pn_a Pn_b = delta_ab */
+static double pn(int m, double x) { return sqrt(2.0 * m + 1.0) * orc_legendre(m, x); }
+static double dpn(int m, double x) { return sqrt(2.0 * m + 1.0) * orc_legendre_deriv(m, x); }
+
+/* Gauss-Legendre nodes (ascending) and weights: Newton iteration on P_n. */
+void orc_gauss(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(ORC_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double dz = orc_legendre(n, z) / orc_legendre_deriv(n, z);
+            z -= dz;
+            if (fabs(dz) < 1e-17) break;
+        }
+        double dp = orc_legendre_deriv(n, z);
+        x[n - 1 - i] = z;
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+int orc_nmodes(int k) { return (k + 1) * (k + 2) * (k + 3) / 6; }
+
+/* complete P_k set: total degree ascending, then i descending, then j descending */
+void orc_mode_list(int k, int32_t* ijl)
+{
+    int c = 0;
+    for (int d = 0; d <= k; ++d)
+        for (int i = d; i >= 0; --i)
+            for (int j = d - i; j >= 0; --j) {
+                ijl[3 * c + 0] = i;
+                ijl[3 * c + 1] = j;
+                ijl[3 * c + 2] = d - i - j;
+                ++c;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* per-call tables of basis values at the quadrature points                  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int k, b, n, nq, ns;
+    int32_t ijl[3 * 84];
+    double xg[16], wg[16];
+    double* phi;  /* [nq][b]             phi_l(xi_q)                          */
+    double* dphi; /* [3][nq][b]          d phi_l / d xi_d at xi_q              */
+    double* wq;   /* [nq]                w_a w_b w_c                           */
+    double* phif; /* [3][2][ns][b]       phi_l on face (dir d, side 0:-1, 1:+1) */
+    double* ws;   /* [ns]                face weights                          */
+} tabs;
+
+static double basis(const tabs* T, int l, const double xi[3])
+{
+    return pn(T->ijl[3 * l], xi[0]) * pn(T->ijl[3 * l + 1], xi[1]) * pn(T->ijl[3 * l + 2], xi[2]);
+}
+
+static double basis_grad(const tabs* T, int l, int d, const double xi[3])
+{
+    double f[3];
+    for (int e = 0; e < 3; ++e) f[e] = (e == d) ? dpn(T->ijl[3 * l + e], xi[e]) : pn(T->ijl[3 * l + e], xi[e]);
+    return f[0] * f[1] * f[2];
+}
+
+/* volume point q = a + n (b + n c) sits at (xg[a], xg[b], xg[c]) */
+static void vol_point(const tabs* T, int q, double xi[3])
+{
+    int n = T->n;
+    xi[0] = T->xg[q % n];
+    xi[1] = T->xg[(q / n) % n];
+    xi[2] = T->xg[q / (n * n)];
+}
+
+/* face point s = a + n b on the face normal to d: tangential axes in increasing order */
+static void face_point(const tabs* T, int d, int side, int s, double xi[3])
+{
+    int n = T->n, t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+    xi[d] = side ? 1.0 : -1.0;
+    xi[t1] = T->xg[s % n];
+    xi[t2] = T->xg[s / n];
+}
+
+static void tabs_init(tabs* T, int k, int nquad)
+{
+    T->k = k;
+    T->b = orc_nmodes(k);
+    T->n = nquad;
+    T->nq = nquad * nquad * nquad;
+    T->ns = nquad * nquad;
+    orc_mode_list(k, T->ijl);
+    orc_gauss(nquad, T->xg, T->wg);
+    int b = T->b, nq = T->nq, ns = T->ns;
+    T->phi = (double*)malloc(sizeof(double) * nq * b);
+    T->dphi = (double*)malloc(sizeof(double) * 3 * nq * b);
+    T->wq = (double*)malloc(sizeof(double) * nq);
+    T->phif = (double*)malloc(sizeof(double) * 6 * ns * b);
+    T->ws = (double*)malloc(sizeof(double) * ns);
+    for (int q = 0; q < nq; ++q) {
+        double xi[3];
+        vol_point(T, q, xi);
+        int n = T->n;
+        T->wq[q] = T->wg[q % n] * T->wg[(q / n) % n] * T->wg[q / (n * n)];
+        for (int l = 0; l < b; ++l) {
+            T->phi[q * b + l] = basis(T, l, xi);
+            for (int d = 0; d < 3; ++d) T->dphi[(d * nq + q) * b + l] = basis_grad(T, l, d, xi);
+        }
+    }
+    for (int s = 0; s < ns; ++s) T->ws[s] = T->wg[s % T->n] * T->wg[s / T->n];
+    for (int d = 0; d < 3; ++d)
+        for (int side = 0; side < 2; ++side)
+            for (int s = 0; s < ns; ++s) {
+                double xi[3];
+                face_point(T, d, side, s, xi);
+                for (int l = 0; l < b; ++l) T->phif[((d * 2 + side) * ns + s) * b + l] = basis(T, l, xi);
+            }
+}
+
+static void tabs_free(tabs* T)
+{
+    free(T->phi);
+    free(T->dphi);
+    free(T->wq);
+    free(T->phif);
+    free(T->ws);
+}
+
+static double eval(const tabs* T, const double* coef, const double* row)
+{
+    double s = 0.0;
+    for (int l = 0; l < T->b; ++l) s += coef[l] * row[l];
+    return s;
+}
+
+static int cell_index(int N, int ix, int iy, int iz)
+{
+    ix = (ix % N + N) % N;
+    iy = (iy % N + N) % N;
+    iz = (iz % N + N) % N;
+    return (iz * N + iy) * N + ix;
+}
+
+/* ------------------------------------------------------------------------ */
+/* pointwise physics                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* von Neumann-Richtmyer viscous pressure (Sec. 3.1): for div v < 0,
+ *   Pi = alpha rho (h/p)^2 |div v|^2 + beta rho cs (h/p) |div v|,
+ * limited by Pi_max = (1/2) rho (h/p)^2 |div v| / dt with dt fixed at the start
+ * of the step; zero for div v >= 0.  p = k+1.  dt <= 0 disables the limit. */
+double orc_vnr(const orc_cfg* cfg, double rho, double divv, double dt)
+{
+    if (cfg->av_mode != 1 || !(divv < 0.0)) return 0.0;
+    double hp = (1.0 / cfg->N) / (cfg->k + 1);
+    double a = -divv;
+    double Pi = cfg->alpha * rho * hp * hp * a * a + cfg->beta * rho * cfg->cs * hp * a;
+    if (dt > 0.0) {
+        double Pmax = 0.5 * rho * hp * hp * a / dt;
+        if (Pi > Pmax) Pi = Pmax;
+    }
+    return Pi;
+}
+
+/* Rusanov (local Lax-Friedrichs) flux along +e_d between a left state and a
+ * right state given in primitive form W = (rho, vx, vy, vz):
+ *   F* = (F_d(U_L) + F_d(U_R))/2 - lambda (U_R - U_L)/2,
+ *   lambda = max(|v_d^L|, |v_d^R|) + cs,
+ *   F_d(U) = (rho v_d, rho v_i v_d + cs^2 rho delta_id),  U = (rho, rho v). */
+void orc_rusanov(double cs, int d, const double WL[4], const double WR[4], double F[4])
+{
+    double UL[4], UR[4], FL[4], FR[4];
+    UL[0] = WL[0];
+    UR[0] = WR[0];
+    for (int i = 0; i < 3; ++i) {
+        UL[1 + i] = WL[0] * WL[1 + i];
+        UR[1 + i] = WR[0] * WR[1 + i];
+    }
+    FL[0] = UL[1 + d];
+    FR[0] = UR[1 + d];
+    for (int i = 0; i < 3; ++i) {
+        FL[1 + i] = UL[1 + i] * WL[1 + d] + (i == d ? cs * cs * WL[0] : 0.0);
+        FR[1 + i] = UR[1 + i] * WR[1 + d] + (i == d ? cs * cs * WR[0] : 0.0);
+    }
+    double lam = fmax(fabs(WL[1 + d]), fabs(WR[1 + d])) + cs;
+    for (int v = 0; v < 4; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* CFL time step (Sec. 7: dt proportional to h/(k+1))                        */
+/*   dt = cfl h / ((k+1) max_{cells, volume points} sum_d (|v_d| + cs))     */
+/* ------------------------------------------------------------------------ */
+double orc_dt(const orc_cfg* cfg, const double* u)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nc = N * N * N;
+    double smax = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        const double* uc = u + (size_t)c * 4 * b;
+        for (int q = 0; q < T.nq; ++q) {
+            double rho = eval(&T, uc, T.phi + q * b), s = 0.0;
+            for (int d = 0; d < 3; ++d) s += fabs(eval(&T, uc + (1 + d) * b, T.phi + q * b) / rho) + cfg->cs;
+            if (s > smax) smax = s;
+        }
+    }
+    tabs_free(&T);
+    return cfg->cfl * (1.0 / N) / ((cfg->k + 1) * smax);
+}
+
+/* ------------------------------------------------------------------------ */
+/* primitive projection (Sec. 3.2, eq. weights_equation):                    */
+/*   vhat_l = (1/|K|) int_K (m/rho) phi_l dV  by (k+1)^3-point Gauss         */
+/* ------------------------------------------------------------------------ */
+void orc_project_velocity(const orc_cfg* cfg, const double* u, double* vhat)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nc = N * N * N;
+    for (int c = 0; c < nc; ++c) {
+        const double* uc = u + (size_t)c * 4 * b;
+        double* vc = vhat + (size_t)c * 3 * b;
+        memset(vc, 0, sizeof(double) * 3 * b);
+        for (int q = 0; q < T.nq; ++q) {
+            const double* ph = T.phi + q * b;
+            double rho = eval(&T, uc, ph);
+            for (int i = 0; i < 3; ++i) {
+                double vq = eval(&T, uc + (1 + i) * b, ph) / rho;
+                for (int l = 0; l < b; ++l) vc[i * b + l] += 0.125 * T.wq[q] * ph[l] * vq;
+            }
+        }
+    }
+    tabs_free(&T);
+}
+
+/* mean acceleration abar = <rho a_h> / <rho>, removed so that the forcing adds
+ * no net momentum (both averages are volume integrals by quadrature). */
+void orc_forcing_mean(const orc_cfg* cfg, const double* u, const double* ahat, double abar[3])
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nc = N * N * N;
+    double num[3] = {0, 0, 0}, den = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        const double* uc = u + (size_t)c * 4 * b;
+        const double* ac = ahat + (size_t)c * 3 * b;
+        for (int q = 0; q < T.nq; ++q) {
+            const double* ph = T.phi + q * b;
+            double rho = eval(&T, uc, ph);
+            den += 0.125 * T.wq[q] * rho;
+            for (int i = 0; i < 3; ++i) num[i] += 0.125 * T.wq[q] * rho * eval(&T, ac + i * b, ph);
+        }
+    }
+    for (int i = 0; i < 3; ++i) abar[i] = num[i] / den;
+    tabs_free(&T);
+}
+
+/* ------------------------------------------------------------------------ */
+/* right-hand side (Sec. 2.2, eq. weight_evolution, |K| = h^3):              */
+/*   dw_l/dt = 1/(4h) [ sum_q w_q sum_d dphi_l/dxi_d F_d(U_q)                 */
+/*                      - sum_faces sum_s w_s phi_l(xi_s) F*.n_out ]          */
+/*             + (1/8) sum_q w_q phi_l rho_q (a_h(xi_q) - abar)   (momentum)  */
+/* Volume: conserved values at the internal points, Pi added to the pressure */
+/* (Sec. 3.1).  Faces: rho from its own expansion, v from the projected      */
+/* velocity, no viscous pressure (Sec. 3.1, 3.2).                            */
+/* ------------------------------------------------------------------------ */
+int orc_rhs(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, double* dudt)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nq = T.nq, ns = T.ns;
+    size_t nc = (size_t)N * N * N;
+    double h = 1.0 / N, cs2 = cfg->cs * cfg->cs;
+    double* vhat = (double*)malloc(sizeof(double) * nc * 3 * b);
+    orc_project_velocity(cfg, u, vhat);
+    double abar[3] = {0, 0, 0};
+    if (ahat) orc_forcing_mean(cfg, u, ahat, abar);
+    memset(dudt, 0, sizeof(double) * nc * 4 * b);
+
+    /* volume integral and forcing source, cell by cell */
+    for (size_t c = 0; c < nc; ++c) {
+        const double* uc = u + c * 4 * b;
+        double* rc = dudt + c * 4 * b;
+        for (int q = 0; q < nq; ++q) {
+            const double* ph = T.phi + q * b;
+            double rho = eval(&T, uc, ph), m[3], v[3], drho[3], dmd[3];
+            for (int i = 0; i < 3; ++i) {
+                m[i] = eval(&T, uc + (1 + i) * b, ph);
+                v[i] = m[i] / rho;
+            }
+            for (int d = 0; d < 3; ++d) {
+                const double* dph = T.dphi + ((size_t)d * nq + q) * b;
+                drho[d] = (2.0 / h) * eval(&T, uc, dph);
+                dmd[d] = (2.0 / h) * eval(&T, uc + (1 + d) * b, dph);
+            }
+            /* div v = (div m - v . grad rho) / rho */
+            double divv = (dmd[0] + dmd[1] + dmd[2] - (v[0] * drho[0] + v[1] * drho[1] + v[2] * drho[2])) / rho;
+            double P = cs2 * rho + orc_vnr(cfg, rho, divv, dt_pimax);
+            double F[4][3]; /* F[var][d] */
+            for (int d = 0; d < 3; ++d) {
+                F[0][d] = m[d];
+                for (int i = 0; i < 3; ++i) F[1 + i][d] = m[i] * v[d] + (i == d ? P : 0.0);
+            }
+            for (int l = 0; l < b; ++l) {
+                double g[3];
+                for (int d = 0; d < 3; ++d) g[d] = T.dphi[((size_t)d * nq + q) * b + l];
+                for (int var = 0; var < 4; ++var)
+                    rc[var * b + l] += T.wq[q] * (g[0] * F[var][0] + g[1] * F[var][1] + g[2] * F[var][2]) / (4.0 * h);
+            }
+            if (ahat) {
+                const double* ac = ahat + c * 3 * b;
+                for (int i = 0; i < 3; ++i) {
+                    double src = rho * (eval(&T, ac + i * b, ph) - abar[i]);
+                    for (int l = 0; l < b; ++l) rc[(1 + i) * b + l] += 0.125 * T.wq[q] * ph[l] * src;
+                }
+            }
+        }
+    }
+
+    /* surface integral: one pass over interfaces, each flux added to both cells */
+    for (int iz = 0; iz < N; ++iz)
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                int cL = cell_index(N, ix, iy, iz);
+                for (int d = 0; d < 3; ++d) {
+                    int cR = cell_index(N, ix + (d == 0), iy + (d == 1), iz + (d == 2));
+                    const double* phL = T.phif + ((size_t)(d * 2 + 1) * ns) * b; /* xi_d = +1 in L */
+                    const double* phR = T.phif + ((size_t)(d * 2 + 0) * ns) * b; /* xi_d = -1 in R */
+                    for (int s = 0; s < ns; ++s) {
+                        double WL[4], WR[4], Fs[4];
+                        WL[0] = eval(&T, u + (size_t)cL * 4 * b, phL + s * b);
+                        WR[0] = eval(&T, u + (size_t)cR * 4 * b, phR + s * b);
+                        for (int i = 0; i < 3; ++i) {
+                            WL[1 + i] = eval(&T, vhat + ((size_t)cL * 3 + i) * b, phL + s * b);
+                            WR[1 + i] = eval(&T, vhat + ((size_t)cR * 3 + i) * b, phR + s * b);
+                        }
+                        orc_rusanov(cfg->cs, d, WL, WR, Fs);
+                        for (int var = 0; var < 4; ++var)
+                            for (int l = 0; l < b; ++l) {
+                                dudt[((size_t)cL * 4 + var) * b + l] -= T.ws[s] * phL[s * b + l] * Fs[var] / (4.0 * h);
+                                dudt[((size_t)cR * 4 + var) * b + l] += T.ws[s] * phR[s * b + l] * Fs[var] / (4.0 * h);
+                            }
+                    }
+                }
+            }
+    free(vhat);
+    tabs_free(&T);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* positivity (Sec. 3.1): density checked at every volume and face Gauss      */
+/* point; if the minimum is below the floor and the mean is above it, all   */
+/* higher-order weights of all variables are scaled by                       */
+/*   theta = (rho_mean - eps) / (rho_mean - rho_min);                         */
+/* a mean at or below the floor is a failure (the step is retried with a     */
+/* smaller dt by the driver).                                                 */
+/* ------------------------------------------------------------------------ */
+int orc_limit(const orc_cfg* cfg, double* u)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b;
+    size_t nc = (size_t)N * N * N;
+    double eps = cfg->rho_floor;
+    int status = 0;
+    for (size_t c = 0; c < nc; ++c) {
+        double* uc = u + c * 4 * b;
+        double rmin = INFINITY;
+        for (int q = 0; q < T.nq; ++q) rmin = fmin(rmin, eval(&T, uc, T.phi + q * b));
+        for (int f = 0; f < 6; ++f)
+            for (int s = 0; s < T.ns; ++s) rmin = fmin(rmin, eval(&T, uc, T.phif + ((size_t)f * T.ns + s) * b));
+        if (rmin < eps) {
+            double rbar = uc[0];
+            if (rbar > eps) {
+                double theta = (rbar - eps) / (rbar - rmin);
+                for (int var = 0; var < 4; ++var)
+                    for (int l = 1; l < b; ++l) uc[var * b + l] *= theta;
+                status |= ORC_LIMITED;
+            } else {
+                status |= ORC_FAIL;
+            }
+        }
+    }
+    tabs_free(&T);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* one SSP Runge-Kutta step (Sec. 7) with the limiter after every stage      */
+/*   RK2: u1 = un + dt L(un);  un+1 = un/2 + (u1 + dt L(u1))/2               */
+/*   RK3: u1 = un + dt L(un);  u2 = 3un/4 + (u1 + dt L(u1))/4;               */
+/*        un+1 = un/3 + 2(u2 + dt L(u2))/3                                    */
+/* dt also fixes Pi_max for every stage.                                      */
+/* ------------------------------------------------------------------------ */
+int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt)
+{
+    int b = orc_nmodes(cfg->k);
+    size_t n = (size_t)cfg->N * cfg->N * cfg->N * 4 * b;
+    double* un = (double*)malloc(sizeof(double) * n);
+    double* us = (double*)malloc(sizeof(double) * n);
+    double* L = (double*)malloc(sizeof(double) * n);
+    memcpy(un, u, sizeof(double) * n);
+    memcpy(us, u, sizeof(double) * n);
+    int status = 0;
+    static const double a2[2] = {0.0, 0.5}, b2[2] = {1.0, 0.5};
+    static const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double* A = (cfg->rk_stages == 2) ? a2 : a3;
+    const double* B = (cfg->rk_stages == 2) ? b2 : b3;
+    for (int s = 0; s < cfg->rk_stages; ++s) {
+        orc_rhs(cfg, us, ahat, dt, L);
+        for (size_t i = 0; i < n; ++i) us[i] = A[s] * un[i] + B[s] * (us[i] + dt * L[i]);
+        status |= orc_limit(cfg, us);
+    }
+    memcpy(u, us, sizeof(double) * n);
+    free(un);
+    free(us);
+    free(L);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ornstein-Uhlenbeck driving (Sec. 4.2)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea & Flood 2014), as published. */
+uint64_t orc_splitmix64(uint64_t* state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+static double uniform53(uint64_t* st) { return (double)(orc_splitmix64(st) >> 11) * (1.0 / 9007199254740992.0); }
+
+/* standard normal by Box-Muller; the cosine branch first, then the sine branch */
+static double gauss(orc_ou* ou)
+{
+    if (ou->have_spare) {
+        ou->have_spare = 0;
+        return ou->spare;
+    }
+    double u1 = 1.0 - uniform53(&ou->rng); /* (0, 1] */
+    double u2 = uniform53(&ou->rng);
+    double r = sqrt(-2.0 * log(u1));
+    ou->spare = r * sin(2.0 * ORC_PI * u2);
+    ou->have_spare = 1;
+    return r * cos(2.0 * ORC_PI * u2);
+}
+
+/* Modes: integer k with kmin2 <= |k|^2 <= kmax2, one representative of each
+ * +-k pair (first non-zero component positive), lexicographic order.
+ * t_c = T = L/(2 cs M) (eq. eddy_turnover_time), update interval t_c/100,
+ * f = exp(-dt_drive/t_c).  sigma = 2 M^2 cs^2 / L is the rms acceleration:
+ * each real component of x has stationary variance
+ * s^2 = sigma^2 / (4 nmodes (2 zeta^2 + (1-zeta)^2)), so that <|a|^2> = sigma^2
+ * after the Helmholtz projection with solenoidal weight zeta. */
+void orc_ou_init(orc_ou* ou, int kmin2, int kmax2, double zeta, double mach, double cs, double L, uint64_t seed,
+                 double t_off)
+{
+    memset(ou, 0, sizeof(*ou));
+    int K = (int)floor(sqrt((double)kmax2) + 1e-9);
+    int nm = 0;
+    for (int kx = -K; kx <= K; ++kx)
+        for (int ky = -K; ky <= K; ++ky)
+            for (int kz = -K; kz <= K; ++kz) {
+                int r2 = kx * kx + ky * ky + kz * kz;
+                if (r2 < kmin2 || r2 > kmax2) continue;
+                int first = kx != 0 ? kx : (ky != 0 ? ky : kz);
+                if (first <= 0) continue;
+                if (nm < ORC_MAX_MODES) {
+                    ou->kvec[nm][0] = kx;
+                    ou->kvec[nm][1] = ky;
+                    ou->kvec[nm][2] = kz;
+                }
+                ++nm;
+            }
+    ou->nmodes = nm;
+    ou->zeta = zeta;
+    ou->tc = L / (2.0 * cs * mach);
+    ou->dt_drive = ou->tc / 100.0;
+    ou->f = exp(-ou->dt_drive / ou->tc);
+    ou->sigma = 2.0 * mach * mach * cs * cs / L;
+    ou->s = ou->sigma / sqrt(4.0 * nm * (2.0 * zeta * zeta + (1.0 - zeta) * (1.0 - zeta)));
+    ou->rng = seed;
+    for (int m = 0; m < nm; ++m)
+        for (int i = 0; i < 3; ++i)
+            for (int r = 0; r < 2; ++r) ou->x[m][i][r] = ou->s * gauss(ou);
+    ou->t_next = ou->dt_drive;
+    ou->t_off = t_off;
+    ou->on = 1;
+    ou->dirty = 1;
+}
+
+/* x <- f x + s sqrt(1 - f^2) z  (eq. ornstein_uhlenbeck_process_time_evolution) */
+void orc_ou_advance(orc_ou* ou)
+{
+    double c = ou->s * sqrt(1.0 - ou->f * ou->f);
+    for (int m = 0; m < ou->nmodes; ++m)
+        for (int i = 0; i < 3; ++i)
+            for (int r = 0; r < 2; ++r) ou->x[m][i][r] = ou->f * ou->x[m][i][r] + c * gauss(ou);
+}
+
+/* ahat_k = P_zeta(k) x_k,  P_zeta = zeta (I - k k^T/|k|^2) + (1 - zeta) k k^T/|k|^2 */
+void orc_ou_amplitudes(const orc_ou* ou, double* amp)
+{
+    for (int m = 0; m < ou->nmodes; ++m) {
+        double kk[3], k2 = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            kk[i] = ou->kvec[m][i];
+            k2 += kk[i] * kk[i];
+        }
+        for (int r = 0; r < 2; ++r)
+            for (int i = 0; i < 3; ++i) {
+                double s = 0.0;
+                for (int j = 0; j < 3; ++j) {
+                    double kkij = kk[i] * kk[j] / k2;
+                    double P = ou->zeta * ((i == j ? 1.0 : 0.0) - kkij) + (1.0 - ou->zeta) * kkij;
+                    s += P * ou->x[m][j][r];
+                }
+                amp[(m * 3 + i) * 2 + r] = s;
+            }
+    }
+}
+
+/* a(x) = sum_k 2 Re(ahat_k exp(2 pi i k.x)), projected per cell onto the basis:
+ * ahat_l = (1/8) sum_q w_q phi_l(xi_q) a(x_q),  x_q = x_c + (h/2) xi_q. */
+void orc_forcing_project(const orc_cfg* cfg, int nmodes, const int32_t* kvec, const double* amp, double* ahat)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b;
+    double h = 1.0 / N;
+    for (int iz = 0; iz < N; ++iz)
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                double* ac = ahat + (size_t)cell_index(N, ix, iy, iz) * 3 * b;
+                memset(ac, 0, sizeof(double) * 3 * b);
+                for (int q = 0; q < T.nq; ++q) {
+                    double xi[3];
+                    vol_point(&T, q, xi);
+                    double x = (ix + 0.5 + 0.5 * xi[0]) * h, y = (iy + 0.5 + 0.5 * xi[1]) * h,
+                           z = (iz + 0.5 + 0.5 * xi[2]) * h;
+                    double a[3] = {0, 0, 0};
+                    for (int m = 0; m < nmodes; ++m) {
+                        double th = 2.0 * ORC_PI * (kvec[3 * m] * x + kvec[3 * m + 1] * y + kvec[3 * m + 2] * z);
+                        double c = cos(th), s = sin(th);
+                        for (int i = 0; i < 3; ++i)
+                            a[i] += 2.0 * (amp[(m * 3 + i) * 2] * c - amp[(m * 3 + i) * 2 + 1] * s);
+                    }
+                    for (int i = 0; i < 3; ++i)
+                        for (int l = 0; l < b; ++l) ac[i * b + l] += 0.125 * T.wq[q] * T.phi[q * b + l] * a[i];
+                }
+            }
+    tabs_free(&T);
+}
+
+/* ------------------------------------------------------------------------ */
+/* time-stepping driver with the driving schedule and the dt retry           */
+/* At the start of a step: while t >= t_next advance the OU process and      */
+/* t_next += dt_drive; re-project the forcing when it changed.  After t_off  */
+/* (if > 0) the forcing is switched off.  A step whose stages report a       */
+/* failure is redone from the same state with dt/2, at most 3 times.         */
+/* Returns 0, or -1 when the retries are exhausted (state left at u^n).     */
+/* ------------------------------------------------------------------------ */
+int orc_run(const orc_cfg* cfg, double* u, orc_ou* ou, int use_forcing, double* ahat, int nsteps, double* t,
+            double* dt_last)
+{
+    int b = orc_nmodes(cfg->k);
+    size_t n = (size_t)cfg->N * cfg->N * cfg->N * 4 * b;
+    double* bak = (double*)malloc(sizeof(double) * n);
+    double* amp = (double*)malloc(sizeof(double) * ORC_MAX_MODES * 6);
+    int rc = 0;
+    for (int st = 0; st < nsteps; ++st) {
+        const double* force = NULL;
+        if (use_forcing && ou->on && ou->t_off > 0.0 && *t > ou->t_off) ou->on = 0;
+        if (use_forcing && ou->on) {
+            while (*t >= ou->t_next) {
+                orc_ou_advance(ou);
+                ou->t_next += ou->dt_drive;
+                ou->dirty = 1;
+            }
+            if (ou->dirty) {
+                orc_ou_amplitudes(ou, amp);
+                orc_forcing_project(cfg, ou->nmodes, &ou->kvec[0][0], amp, ahat);
+                ou->dirty = 0;
+            }
+            force = ahat;
+        }
+        double dt = orc_dt(cfg, u);
+        int status = ORC_FAIL;
+        double dtt = dt;
+        memcpy(bak, u, sizeof(double) * n);
+        for (int r = 0; r <= 3; ++r) {
+            dtt = dt / (double)(1 << r);
+            status = orc_step(cfg, u, force, dtt);
+            if (!(status & ORC_FAIL)) break;
+            memcpy(u, bak, sizeof(double) * n);
+        }
+        if (status & ORC_FAIL) {
+            rc = -1;
+            break;
+        }
+        *t += dtt;
+        if (dt_last) *dt_last = dtt;
+    }
+    free(bak);
+    free(amp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* diagnostics (Sec. 4.1 and the energy bookkeeping of Sec. 4.2)             */
+/*  0 mass, 1-3 momentum, 4 kinetic energy, 5 M = <v^2>^(1/2)/cs,            */
+/*  6 M_rho = (2 E_kin / M_tot)^(1/2)/cs, 7 min rho, 8 max rho (volume       */
+/*  points), 9 volume fraction with Pi > 0.01 cs^2 rho, 10 injected power    */
+/*  int m.(a_h - abar) dV, 11 max sum_d(|v_d| + cs), 12 int Pi div v dV.      */
+/* ------------------------------------------------------------------------ */
+void orc_diagnostics(const orc_cfg* cfg, const double* u, const double* ahat, double dt, double* out)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nq = T.nq;
+    size_t nc = (size_t)N * N * N;
+    double h = 1.0 / N, V = h * h * h, cs = cfg->cs;
+    double abar[3] = {0, 0, 0};
+    if (ahat) orc_forcing_mean(cfg, u, ahat, abar);
+    for (int i = 0; i < ORC_NDIAG; ++i) out[i] = 0.0;
+    out[7] = INFINITY;
+    out[8] = -INFINITY;
+    for (size_t c = 0; c < nc; ++c) {
+        const double* uc = u + c * 4 * b;
+        out[0] += uc[0] * V;
+        for (int i = 0; i < 3; ++i) out[1 + i] += uc[(1 + i) * b] * V;
+        for (int q = 0; q < nq; ++q) {
+            const double* ph = T.phi + q * b;
+            double wv = 0.125 * T.wq[q] * V;
+            double rho = eval(&T, uc, ph), m[3], v2 = 0.0, s = 0.0, drho[3], dmd[3], vd = 0.0, dm = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                m[i] = eval(&T, uc + (1 + i) * b, ph);
+                v2 += (m[i] / rho) * (m[i] / rho);
+                s += fabs(m[i] / rho) + cs;
+            }
+            for (int d = 0; d < 3; ++d) {
+                const double* dph = T.dphi + ((size_t)d * nq + q) * b;
+                drho[d] = (2.0 / h) * eval(&T, uc, dph);
+                dmd[d] = (2.0 / h) * eval(&T, uc + (1 + d) * b, dph);
+                vd += (m[d] / rho) * drho[d];
+                dm += dmd[d];
+            }
+            double divv = (dm - vd) / rho;
+            double Pi = orc_vnr(cfg, rho, divv, dt);
+            out[4] += wv * 0.5 * rho * v2;
+            out[5] += wv * v2;
+            out[7] = fmin(out[7], rho);
+            out[8] = fmax(out[8], rho);
+            if (Pi > 0.01 * cs * cs * rho) out[9] += wv;
+            if (ahat) {
+                const double* ac = ahat + c * 3 * b;
+                for (int i = 0; i < 3; ++i) out[10] += wv * m[i] * (eval(&T, ac + i * b, ph) - abar[i]);
+            }
+            if (s > out[11]) out[11] = s;
+            out[12] += wv * Pi * divv;
+        }
+    }
+    double vol = 1.0;
+    out[5] = sqrt(out[5] / vol) / cs;
+    out[6] = sqrt(2.0 * out[4] / out[0]) / cs;
+    out[9] /= vol;
+    tabs_free(&T);
+}
+
+/* L1 density difference (eq. l1_norm) between two states, by (k+3)-point
+ * Gauss quadrature per axis in every cell, divided by the box volume. */
+double orc_l1_density(const orc_cfg* cfg, const double* uA, const double* uB)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 3);
+    int N = cfg->N, b = T.b;
+    size_t nc = (size_t)N * N * N;
+    double h = 1.0 / N, sum = 0.0;
+    for (size_t c = 0; c < nc; ++c)
+        for (int q = 0; q < T.nq; ++q) {
+            double d = eval(&T, uA + c * 4 * b, T.phi + q * b) - eval(&T, uB + c * 4 * b, T.phi + q * b);
+            sum += 0.125 * T.wq[q] * fabs(d) * h * h * h;
+        }
+    tabs_free(&T);
+    return sum;
+}

@@ -1,0 +1,90 @@
+/*
+ * dg_oracle.h -- plain FP64 CPU reference ("oracle") of the modal DG method
+ * for 3D isothermal Euler on a periodic Cartesian mesh.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The product path
+ * (the CUDA library and its binding) never calls, links or includes anything
+ * here, and this file includes nothing from the product.
+ *
+ * Conventions (shared with the product only by specification, not by code):
+ *   - N cells per axis, unit box L = 1, cell size h = 1/N.
+ *   - cell index c = (iz*N + iy)*N + ix, cell centre x_c = (i + 1/2) h.
+ *   - degree k, b = (k+1)(k+2)(k+3)/6 modes per field, n = k+1 Gauss points
+ *     per axis.
+ *   - basis phi_{ijl}(xi) = Pn_i(xi_x) Pn_j(xi_y) Pn_l(xi_z), i+j+l <= k,
+ *     Pn_m = sqrt(2m+1) P_m (orthonormal: (1/8) int phi_a phi_b = delta_ab).
+ *     Mode order: total degree ascending; within a degree i descending, then
+ *     j descending.
+ *   - state u[c][var][mode], var = (rho, m_x, m_y, m_z).
+ *   - forcing / velocity coefficient arrays: [c][3][mode].
+ */
+#ifndef DG_ORACLE_H
+#define DG_ORACLE_H
+#include <stdint.h>
+
+typedef struct {
+    int32_t N;          /* cells per axis                                   */
+    int32_t k;          /* polynomial degree (1..3 used, up to 6 accepted)  */
+    double cs;          /* isothermal sound speed                           */
+    int32_t av_mode;    /* 0 = no artificial viscosity, 1 = von Neumann-
+                           Richtmyer viscous pressure                       */
+    double alpha;       /* quadratic vNR coefficient                        */
+    double beta;        /* linear (bulk) vNR coefficient                    */
+    double rho_floor;   /* positivity floor epsilon                         */
+    double cfl;         /* Courant number                                   */
+    int32_t rk_stages;  /* 2 (SSP-RK2) or 3 (SSP-RK3)                        */
+} orc_cfg;
+
+/* status bits of a stage / step */
+#define ORC_LIMITED 1   /* at least one cell was rescaled by the limiter    */
+#define ORC_FAIL    2   /* a cell mean fell to or below the floor           */
+
+/* OU driving state (host side, Sec. 4.2) */
+#define ORC_MAX_MODES 512
+typedef struct {
+    int32_t nmodes;
+    int32_t kvec[ORC_MAX_MODES][3];
+    double x[ORC_MAX_MODES][3][2];     /* OU variables, real/imag           */
+    double zeta, sigma, tc, dt_drive, s, f;
+    double t_next, t_off;
+    uint64_t rng;                      /* SplitMix64 state                  */
+    int32_t have_spare; double spare;  /* Box-Muller second branch          */
+    int32_t on;                        /* 0 once switched off at t_off      */
+    int32_t dirty;                     /* forcing needs re-projection       */
+} orc_ou;
+
+int  orc_nmodes(int k);
+void orc_mode_list(int k, int32_t* ijl);
+void orc_gauss(int n, double* x, double* w);
+double orc_legendre(int m, double x);
+double orc_legendre_deriv(int m, double x);
+
+double orc_dt(const orc_cfg* cfg, const double* u);
+void orc_project_velocity(const orc_cfg* cfg, const double* u, double* vhat);
+void orc_forcing_mean(const orc_cfg* cfg, const double* u, const double* ahat,
+                      double abar[3]);
+double orc_vnr(const orc_cfg* cfg, double rho, double divv, double dt);
+void orc_rusanov(double cs, int d, const double WL[4], const double WR[4],
+                 double F[4]);
+int orc_rhs(const orc_cfg* cfg, const double* u, const double* ahat,
+            double dt_pimax, double* dudt);
+int orc_limit(const orc_cfg* cfg, double* u);
+int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt);
+
+void orc_ou_init(orc_ou* ou, int kmin2, int kmax2, double zeta, double mach,
+                 double cs, double L, uint64_t seed, double t_off);
+void orc_ou_advance(orc_ou* ou);
+void orc_ou_amplitudes(const orc_ou* ou, double* ahat_modes /* [nm][3][2] */);
+void orc_forcing_project(const orc_cfg* cfg, int nmodes, const int32_t* kvec,
+                         const double* amp, double* ahat);
+int orc_run(const orc_cfg* cfg, double* u, orc_ou* ou, int use_forcing,
+            double* ahat, int nsteps, double* t, double* dt_last);
+
+void orc_diagnostics(const orc_cfg* cfg, const double* u, const double* ahat,
+                     double dt, double* out /* ORC_NDIAG */);
+#define ORC_NDIAG 13
+double orc_l1_density(const orc_cfg* cfg, const double* uA, const double* uB);
+
+uint64_t orc_splitmix64(uint64_t* state);
+#endif

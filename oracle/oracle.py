@@ -1,0 +1,235 @@
+"""ctypes wrapper of the FP64 CPU oracle (``dg_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The CUDA library and its Python
+binding never import this module.
+
+Every array is a C-contiguous float64 numpy array in the cell-major layout
+``u[cell][var][mode]`` with cell = (iz*N + iy)*N + ix.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+ORC_LIMITED = 1
+ORC_FAIL = 2
+NDIAG = 13
+DIAG_NAMES = ("mass", "mom_x", "mom_y", "mom_z", "ekin", "mach", "mach_rho", "rho_min", "rho_max",
+              "av_frac", "inj_power", "max_speed", "av_work")
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with the host C compiler (plain C11, -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "dg_oracle.h"))):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cfg(C.Structure):
+    _fields_ = [("N", C.c_int32), ("k", C.c_int32), ("cs", C.c_double), ("av_mode", C.c_int32),
+                ("alpha", C.c_double), ("beta", C.c_double), ("rho_floor", C.c_double), ("cfl", C.c_double),
+                ("rk_stages", C.c_int32)]
+
+
+MAX_MODES = 512
+
+
+class OU(C.Structure):
+    _fields_ = [("nmodes", C.c_int32), ("kvec", C.c_int32 * 3 * MAX_MODES),
+                ("x", C.c_double * 2 * 3 * MAX_MODES),
+                ("zeta", C.c_double), ("sigma", C.c_double), ("tc", C.c_double), ("dt_drive", C.c_double),
+                ("s", C.c_double), ("f", C.c_double), ("t_next", C.c_double), ("t_off", C.c_double),
+                ("rng", C.c_uint64), ("have_spare", C.c_int32), ("spare", C.c_double), ("on", C.c_int32),
+                ("dirty", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        d = C.POINTER(C.c_double)
+        _lib.orc_dt.restype = C.c_double
+        _lib.orc_vnr.restype = C.c_double
+        _lib.orc_legendre.restype = C.c_double
+        _lib.orc_legendre_deriv.restype = C.c_double
+        _lib.orc_l1_density.restype = C.c_double
+        _lib.orc_splitmix64.restype = C.c_uint64
+        _lib.orc_legendre.argtypes = [C.c_int, C.c_double]
+        _lib.orc_legendre_deriv.argtypes = [C.c_int, C.c_double]
+        _lib.orc_vnr.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double]
+        _lib.orc_rusanov.argtypes = [C.c_double, C.c_int, d, d, d]
+        _lib.orc_ou_init.argtypes = [C.POINTER(OU), C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, C.c_uint64, C.c_double]
+        _lib.orc_rhs.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d]
+        _lib.orc_step.argtypes = [C.POINTER(Cfg), d, d, C.c_double]
+        _lib.orc_run.argtypes = [C.POINTER(Cfg), d, C.POINTER(OU), C.c_int, d, C.c_int, d, d]
+        _lib.orc_diagnostics.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d]
+        _lib.orc_forcing_project.argtypes = [C.POINTER(Cfg), C.c_int, C.POINTER(C.c_int32), d, d]
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def nmodes(k: int) -> int:
+    return (k + 1) * (k + 2) * (k + 3) // 6
+
+
+def mode_list(k: int) -> np.ndarray:
+    b = nmodes(k)
+    out = np.zeros((b, 3), dtype=np.int32)
+    lib().orc_mode_list(C.c_int(k), out.ctypes.data_as(C.POINTER(C.c_int32)))
+    return out
+
+
+def gauss(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().orc_gauss(C.c_int(n), _p(x), _p(w))
+    return x, w
+
+
+def legendre(m: int, x: float) -> float:
+    return lib().orc_legendre(m, x)
+
+
+def legendre_deriv(m: int, x: float) -> float:
+    return lib().orc_legendre_deriv(m, x)
+
+
+def make_cfg(N, k, cs=1.0, av_mode=1, alpha=2.0, beta=0.2, rho_floor=1e-3, cfl=0.3, rk_stages=None) -> Cfg:
+    if rk_stages is None:
+        rk_stages = 2 if k == 1 else 3
+    return Cfg(N, k, cs, av_mode, alpha, beta, rho_floor, cfl, rk_stages)
+
+
+def _shape(cfg, nvar=4):
+    return (cfg.N ** 3, nvar, nmodes(cfg.k))
+
+
+def dt(cfg: Cfg, u: np.ndarray) -> float:
+    return lib().orc_dt(C.byref(cfg), _p(u))
+
+
+def project_velocity(cfg: Cfg, u: np.ndarray) -> np.ndarray:
+    out = np.zeros(_shape(cfg, 3))
+    lib().orc_project_velocity(C.byref(cfg), _p(u), _p(out))
+    return out
+
+
+def forcing_mean(cfg: Cfg, u: np.ndarray, ahat: np.ndarray) -> np.ndarray:
+    out = np.zeros(3)
+    lib().orc_forcing_mean(C.byref(cfg), _p(u), _p(ahat), _p(out))
+    return out
+
+
+def vnr(cfg: Cfg, rho: float, divv: float, dt_: float) -> float:
+    return lib().orc_vnr(C.byref(cfg), rho, divv, dt_)
+
+
+def rusanov(cs: float, d: int, WL, WR) -> np.ndarray:
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.zeros(4)
+    lib().orc_rusanov(cs, d, _p(WL), _p(WR), _p(F))
+    return F
+
+
+def rhs(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None = None, dt_pimax: float = 0.0) -> np.ndarray:
+    out = np.zeros(_shape(cfg))
+    lib().orc_rhs(C.byref(cfg), _p(u), _p(ahat), dt_pimax, _p(out))
+    return out
+
+
+def limit(cfg: Cfg, u: np.ndarray) -> int:
+    return lib().orc_limit(C.byref(cfg), _p(u))
+
+
+def step(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None, dt_: float) -> int:
+    """One SSP-RK step in place; returns the OR of the stage limiter statuses."""
+    return lib().orc_step(C.byref(cfg), _p(u), _p(ahat), dt_)
+
+
+class Forcing:
+    """Host OU driving state of the oracle (Sec. 4.2)."""
+
+    def __init__(self, mach: float, zeta: float, seed: int, cs: float = 1.0, kmin2: int = 1, kmax2: int = 9,
+                 t_off: float = 0.0):
+        self.ou = OU()
+        lib().orc_ou_init(C.byref(self.ou), kmin2, kmax2, zeta, mach, cs, 1.0, seed, t_off)
+
+    @property
+    def nmodes(self) -> int:
+        return self.ou.nmodes
+
+    def kvec(self) -> np.ndarray:
+        return np.ctypeslib.as_array(self.ou.kvec)[: self.nmodes].copy()
+
+    def x(self) -> np.ndarray:
+        return np.ctypeslib.as_array(self.ou.x)[: self.nmodes].copy()
+
+    def advance(self):
+        lib().orc_ou_advance(C.byref(self.ou))
+
+    def amplitudes(self) -> np.ndarray:
+        amp = np.zeros((MAX_MODES, 3, 2))
+        lib().orc_ou_amplitudes(C.byref(self.ou), _p(amp))
+        return amp[: self.nmodes].copy()
+
+
+def forcing_project(cfg: Cfg, kvec: np.ndarray, amp: np.ndarray) -> np.ndarray:
+    kv = np.ascontiguousarray(kvec, dtype=np.int32)
+    amp = np.ascontiguousarray(amp, dtype=np.float64)
+    out = np.zeros(_shape(cfg, 3))
+    lib().orc_forcing_project(C.byref(cfg), C.c_int(len(kv)), kv.ctypes.data_as(C.POINTER(C.c_int32)),
+                              _p(amp), _p(out))
+    return out
+
+
+def run(cfg: Cfg, u: np.ndarray, nsteps: int, forcing: Forcing | None = None, t: float = 0.0,
+        ahat: np.ndarray | None = None):
+    """Advance ``u`` in place by ``nsteps`` steps (driving schedule + dt retry).
+
+    Returns (rc, t, dt_last, ahat); ``ahat`` carries the current projected
+    forcing between calls (pass it back in to continue a run)."""
+    if ahat is None:
+        ahat = np.zeros(_shape(cfg, 3))
+    tt = C.c_double(t)
+    dl = C.c_double(0.0)
+    ou = forcing.ou if forcing is not None else OU()
+    rc = lib().orc_run(C.byref(cfg), _p(u), C.byref(ou), 1 if forcing is not None else 0, _p(ahat), nsteps,
+                       C.byref(tt), C.byref(dl))
+    return rc, tt.value, dl.value, ahat
+
+
+def diagnostics(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None = None, dt_: float = 0.0) -> dict:
+    out = np.zeros(NDIAG)
+    lib().orc_diagnostics(C.byref(cfg), _p(u), _p(ahat), dt_, _p(out))
+    return dict(zip(DIAG_NAMES, out.tolist()))
+
+
+def l1_density(cfg: Cfg, uA: np.ndarray, uB: np.ndarray) -> float:
+    return lib().orc_l1_density(C.byref(cfg), _p(uA), _p(uB))
+
+
+def splitmix64(state: int, n: int) -> list[int]:
+    s = C.c_uint64(state)
+    return [lib().orc_splitmix64(C.byref(s)) for _ in range(n)]
