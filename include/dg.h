@@ -1,0 +1,224 @@
+/*
+ * dg.h -- C ABI of libdg, a GB300 (sm_103a) implementation of the right-hand
+ * side and time step of the modal Discontinuous Galerkin method for 3D
+ * isothermal Euler on a periodic Cartesian mesh, driven by Ornstein-Uhlenbeck
+ * forcing (Cernetic, Springel, Guillet & Pakmor 2024).
+ *
+ * ------------------------------------------------------------------------
+ * Data layout (all device buffers are owned by the caller, e.g. torch
+ * tensors; the library never allocates or frees device memory):
+ *   N cells per axis, unit box, h = 1/N; cell c = (iz*N + iy)*N + ix.
+ *   degree k in {1,2,3}; b = (k+1)(k+2)(k+3)/6 modes; n = k+1 Gauss points
+ *   per axis.  Basis phi_{ijl}(xi) = Pn_i(xi_x) Pn_j(xi_y) Pn_l(xi_z),
+ *   Pn_m = sqrt(2m+1) P_m, i+j+l <= k, ordered by total degree, then i
+ *   descending, then j descending (mode 0 is the cell mean).
+ *   state   u[c][4][b]      var = rho, m_x, m_y, m_z   ("state layout")
+ *   vhat    [c][3][b]       projected velocity (Sec. 3.2)
+ *   ahat    [c][3][b]       projected driving acceleration (Sec. 4.2)
+ *   Element type: double for DG_PREC_F64, float for DG_PREC_F32 / DG_PREC_X3.
+ *
+ * Conventions:
+ *   - every function returns DG_OK (0) or a DG_E* code; nothing throws and
+ *     nothing exits; the text of the last error is dg_last_error(ctx).
+ *   - kernels run on the caller's stream (dg_opts.stream, a cudaStream_t);
+ *     calls that return host values synchronise that stream.
+ *   - a context is not thread-safe: one host thread per context.
+ * ------------------------------------------------------------------------
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define DG_OK 0
+#define DG_EINVAL 1        /* bad argument (null pointer, size, mode)           */
+#define DG_ECUDA 2         /* a CUDA runtime call failed                         */
+#define DG_ENOMEM 3        /* caller's scratch buffer too small                  */
+#define DG_EPOSITIVITY 4   /* positivity retries exhausted (state left at u^n)  */
+#define DG_ENONFINITE 5    /* a NaN/Inf coefficient was produced                 */
+#define DG_ESTATE 6        /* called before dg_set_state                         */
+
+/* ---- precision modes ----------------------------------------------------- */
+#define DG_PREC_F64 0      /* everything in FP64 (parity mode)                   */
+#define DG_PREC_F32 1      /* FP32 state and arithmetic; FP64 global sums        */
+#define DG_PREC_X3 2       /* FP32 state; basis<->quadrature transforms on the
+                              tensor cores as split-BF16 x3 products with FP32
+                              accumulation; FP64 global sums                      */
+
+/* ---- artificial viscosity modes ------------------------------------------ */
+#define DG_AV_OFF 0
+#define DG_AV_VNR 1        /* von Neumann-Richtmyer viscous pressure (Sec. 3.1)  */
+#define DG_AV_LEARNED 2    /* per-cell coefficient predicted by the MLP           */
+
+/* status bits reported by dg_step / dg_diagnostics */
+#define DG_ST_LIMITED 1u   /* positivity rescaling happened in some cell         */
+#define DG_ST_FAIL 2u      /* a cell mean reached the density floor              */
+#define DG_ST_NONFINITE 4u /* a NaN/Inf was produced                              */
+
+typedef struct {
+    int32_t n[3];          /* cells per axis; this build requires n[0]=n[1]=n[2] */
+    double L[3];           /* box size; this build requires L = 1                */
+} dg_mesh;
+
+/* Viscous pressure Pi = alpha rho (h/p)^2 |div v|^2 + beta rho cs (h/p) |div v|
+ * for div v < 0, capped at Pi_max = rho (h/p)^2 |div v| / (2 dt)  (Sec. 3.1,
+ * p = k+1).  rho_floor is the positivity floor (Sec. 3.1, Sec. 5 uses 1e-3).
+ * nu_gate: in DG_AV_LEARNED mode cells whose predicted coefficient
+ * nu/(cs h/p) is below nu_gate skip the divergence evaluation. */
+typedef struct {
+    int32_t mode;          /* DG_AV_OFF, DG_AV_VNR, DG_AV_LEARNED                 */
+    double alpha;          /* default 2.0                                          */
+    double beta;           /* default 0.2                                          */
+    double rho_floor;      /* default 1e-3                                         */
+    double nu_gate;        /* default 0 (no gating)                                */
+} dg_nu_params;
+
+typedef struct {
+    int32_t precision;     /* DG_PREC_*                                           */
+    int32_t rk_stages;     /* 2 (SSP-RK2) or 3 (SSP-RK3), Sec. 7                   */
+    double cfl;            /* dt = cfl h / ((k+1) max sum_d(|v_d| + cs))           */
+    void* stream;          /* cudaStream_t; must not be NULL                       */
+    void* u[3];            /* three state registers, each N^3*4*b elements; the
+                              current state rotates among them (dg_get_state
+                              returns it; u[0] receives dg_set_state)            */
+    void* vhat;            /* N^3*3*b elements                                     */
+    void* ahat;            /* N^3*3*b elements                                     */
+    void* scratch;         /* >= dg_scratch_bytes(), 256-byte aligned              */
+    size_t scratch_bytes;
+} dg_opts;
+
+/* Driving (Sec. 4.2, eq. ornstein_uhlenbeck_process_time_evolution).  Modes:
+ * integer k with kmin2 <= |k|^2 <= kmax2, one of each +-k pair.  Correlation
+ * time tc = L/(2 cs mach) (eq. eddy_turnover_time), update interval
+ * tc/100, rms acceleration sigma = 2 mach^2 cs^2 / L split evenly over the
+ * modes and the solenoidal/compressive parts with weight zeta.  The OU
+ * variables are drawn from SplitMix64(seed) + Box-Muller on the host.
+ * t_off > 0 switches the driving off once t > t_off. */
+typedef struct {
+    int32_t on;
+    int32_t kmin2, kmax2;
+    double zeta;
+    double mach;
+    uint64_t seed;
+    double t_off;
+} dg_forcing;
+
+typedef struct {
+    double mass, mom[3], ekin, mach, mach_rho, rho_min, rho_max;
+    double av_frac;        /* volume fraction with Pi > 0.01 cs^2 rho              */
+    double inj_power;      /* int m.(a_h - abar) dV                                */
+    double max_speed;      /* max sum_d(|v_d| + cs) over volume points             */
+    double av_work;        /* int Pi div v dV                                      */
+    uint32_t status;       /* sticky DG_ST_* bits since the last dg_set_state       */
+    double t;              /* simulation time                                      */
+    int64_t steps;         /* steps taken                                          */
+} dg_diag;
+
+/* checkpoint metadata: everything besides the coefficients that a resumed
+ * run needs to continue bit-identically */
+typedef struct {
+    double t;
+    int64_t steps;
+    double dt_last;
+    int32_t forcing_on;
+    int32_t forcing_dirty;
+    double t_next;
+    uint64_t rng;
+    int32_t have_spare;
+    double spare;
+    int32_t nmodes;
+    double x[512][3][2];   /* OU variables                                        */
+} dg_meta;
+
+typedef struct dg_ctx dg_ctx;
+
+/* Bytes of device scratch a context with these parameters needs. */
+int dg_scratch_bytes(const dg_mesh* mesh, int order, const dg_nu_params* nu, size_t* bytes);
+
+/* Create a context.  Builds the basis/quadrature tables (Sec. 2.1-2.2),
+ * records the caller's buffers and stream.  No kernel runs before
+ * dg_set_state.  On error *ctx is NULL. */
+int dg_init(dg_ctx** ctx, const dg_mesh* mesh, int order, double cs, const dg_nu_params* nu,
+            const dg_opts* opts);
+void dg_free(dg_ctx* ctx);
+const char* dg_last_error(const dg_ctx* ctx);
+
+/* Copy a state (state layout, element type of the precision mode) into the
+ * context; src on the host (pinned or pageable) or on the device. */
+int dg_set_state(dg_ctx* ctx, const void* src, int src_on_host);
+int dg_get_state(dg_ctx* ctx, void* dst, int dst_on_host);
+
+/* Single evaluation of the semi-discrete right-hand side (Sec. 2.2, eq.
+ * weight_evolution):
+ *   dw_l/dt = 1/(4h) [ sum_q w_q sum_d dphi_l/dxi_d F_d(U_q)
+ *                      - sum_faces sum_s w_s phi_l(xi_s) F*.n ]
+ *             + (1/8) sum_q w_q phi_l rho_q (a_h(xi_q) - abar)  (momentum)
+ * with the viscous pressure at volume points only (Sec. 3.1), face states
+ * from rho and the projected velocity (Sec. 3.2), Rusanov fluxes, and
+ * dt_for_pimax fixing Pi_max (<= 0: no cap).  u_in and dudt are device
+ * buffers in state layout; ahat (device, [c][3][b]) may be NULL (no forcing).
+ * vhat of the context is overwritten. */
+int dg_rhs(dg_ctx* ctx, const void* u_in, const void* ahat, void* dudt, double dt_for_pimax);
+
+/* Projection of the primitive velocity onto the basis (Sec. 3.2, eq.
+ * weights_equation) by (k+1)^3-point Gauss quadrature: u_in -> vhat_out. */
+int dg_project_velocity(dg_ctx* ctx, const void* u_in, void* vhat_out);
+
+/* Advance nsteps SSP-RK steps (Sec. 7).  Per step: driving update when due,
+ * dt from the CFL condition on u^n, S stages of (projection, RHS, stage
+ * combine, positivity rescaling).  A step in which a cell mean reaches the
+ * floor is redone from u^n with dt/2, at most 3 times; then DG_EPOSITIVITY
+ * with the state left at u^n.  Synchronises the stream once per step.
+ * fixed_dt > 0 replaces the CFL dt (used to replay a recorded sequence). */
+int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_last);
+
+/* Configure the driving; draws the initial OU state from its stationary law
+ * and projects the acceleration onto the basis before the next step. */
+int dg_set_forcing(dg_ctx* ctx, const dg_forcing* f);
+
+/* Use an explicit projected acceleration (device or host, [c][3][b]) and
+ * disable the OU schedule. */
+int dg_set_forcing_coeffs(dg_ctx* ctx, const void* ahat_src, int src_on_host);
+
+/* Project the acceleration of explicit Fourier modes onto the basis:
+ * a(x) = sum_m 2 Re(amp_m exp(2 pi i kvec_m . x)); kvec [nm][3] int32 and
+ * amp [nm][3][2] double on the host; result into ctx's ahat. */
+int dg_forcing_from_modes(dg_ctx* ctx, int nmodes, const int32_t* kvec, const double* amp);
+
+/* Diagnostics of the current state (Sec. 4.1); FP64 accumulation on the GPU.
+ * dt_for_pimax as in dg_rhs.  Synchronises the stream. */
+int dg_diagnostics(dg_ctx* ctx, double dt_for_pimax, dg_diag* out);
+
+/* L1 density difference (eq. l1_norm) between two device states, by
+ * (k+3)-point Gauss quadrature per axis per cell.  Synchronises. */
+int dg_l1_density(dg_ctx* ctx, const void* uA, const void* uB, double* out);
+
+/* Kernel timing: with profiling on, every launch of the library is bracketed
+ * by CUDA events on the context's stream and its duration accumulated per
+ * kernel family (read back after the stream is synchronised).  Launch counts
+ * are kept whether or not profiling is on. */
+typedef struct {
+    int64_t launches;      /* kernels launched since the last reset               */
+    int64_t n_project, n_rhs, n_force, n_other;
+    double ms_project;     /* projection kernel (K_A)                             */
+    double ms_rhs;         /* RHS + stage update kernel (K_B)                     */
+    double ms_force;       /* forcing projection                                  */
+    double ms_other;       /* diagnostics, L1                                     */
+} dg_prof;
+int dg_profile(dg_ctx* ctx, int enable);          /* enable/disable; resets counts */
+int dg_profile_read(dg_ctx* ctx, dg_prof* out);   /* synchronises the stream       */
+
+/* Checkpoint metadata (coefficients via dg_get_state / dg_set_state). */
+int dg_get_meta(dg_ctx* ctx, dg_meta* out);
+int dg_set_meta(dg_ctx* ctx, const dg_meta* in);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,108 @@
+"""ctypes binding of libdg (include/dg.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; torch supplies device
+memory and the stream.  Importing this module fails loudly when libdg.so has
+not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdg.so")
+
+DG_OK, DG_EINVAL, DG_ECUDA, DG_ENOMEM, DG_EPOSITIVITY, DG_ENONFINITE, DG_ESTATE = range(7)
+PREC_F64, PREC_F32, PREC_X3 = 0, 1, 2
+AV_OFF, AV_VNR, AV_LEARNED = 0, 1, 2
+ST_LIMITED, ST_FAIL, ST_NONFINITE = 1, 2, 4
+ERROR_NAMES = {DG_EINVAL: "DG_EINVAL", DG_ECUDA: "DG_ECUDA", DG_ENOMEM: "DG_ENOMEM",
+               DG_EPOSITIVITY: "DG_EPOSITIVITY", DG_ENONFINITE: "DG_ENONFINITE", DG_ESTATE: "DG_ESTATE"}
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("L", C.c_double * 3)]
+
+
+class NuParams(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double), ("rho_floor", C.c_double),
+                ("nu_gate", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("rk_stages", C.c_int32), ("cfl", C.c_double), ("stream", C.c_void_p),
+                ("u", C.c_void_p * 3), ("vhat", C.c_void_p), ("ahat", C.c_void_p), ("scratch", C.c_void_p),
+                ("scratch_bytes", C.c_size_t)]
+
+
+class Forcing(C.Structure):
+    _fields_ = [("on", C.c_int32), ("kmin2", C.c_int32), ("kmax2", C.c_int32), ("zeta", C.c_double),
+                ("mach", C.c_double), ("seed", C.c_uint64), ("t_off", C.c_double)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("mass", C.c_double), ("mom", C.c_double * 3), ("ekin", C.c_double), ("mach", C.c_double),
+                ("mach_rho", C.c_double), ("rho_min", C.c_double), ("rho_max", C.c_double),
+                ("av_frac", C.c_double), ("inj_power", C.c_double), ("max_speed", C.c_double),
+                ("av_work", C.c_double), ("status", C.c_uint32), ("t", C.c_double), ("steps", C.c_int64)]
+
+
+class Meta(C.Structure):
+    _fields_ = [("t", C.c_double), ("steps", C.c_int64), ("dt_last", C.c_double), ("forcing_on", C.c_int32),
+                ("forcing_dirty", C.c_int32), ("t_next", C.c_double), ("rng", C.c_uint64),
+                ("have_spare", C.c_int32), ("spare", C.c_double), ("nmodes", C.c_int32),
+                ("x", C.c_double * 2 * 3 * 512)]
+
+
+class Prof(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("n_project", C.c_int64), ("n_rhs", C.c_int64), ("n_force", C.c_int64),
+                ("n_other", C.c_int64), ("ms_project", C.c_double), ("ms_rhs", C.c_double),
+                ("ms_force", C.c_double), ("ms_other", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libdg.so (built in-tree by paper_2401_06841_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libdg.so is not built: run paper_2401_06841_gb300.build.build() "
+                              "(nvcc, sm_103a); there is no fallback implementation")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.dg_scratch_bytes.argtypes = [C.POINTER(Mesh), i, C.POINTER(NuParams), C.POINTER(C.c_size_t)]
+        L.dg_init.argtypes = [C.POINTER(vp), C.POINTER(Mesh), i, d, C.POINTER(NuParams), C.POINTER(Opts)]
+        L.dg_free.argtypes = [vp]
+        L.dg_free.restype = None
+        L.dg_last_error.argtypes = [vp]
+        L.dg_last_error.restype = C.c_char_p
+        L.dg_set_state.argtypes = [vp, vp, i]
+        L.dg_get_state.argtypes = [vp, vp, i]
+        L.dg_rhs.argtypes = [vp, vp, vp, vp, d]
+        L.dg_project_velocity.argtypes = [vp, vp, vp]
+        L.dg_step.argtypes = [vp, i, d, C.POINTER(d), C.POINTER(d)]
+        L.dg_set_forcing.argtypes = [vp, C.POINTER(Forcing)]
+        L.dg_set_forcing_coeffs.argtypes = [vp, vp, i]
+        L.dg_forcing_from_modes.argtypes = [vp, i, vp, vp]
+        L.dg_diagnostics.argtypes = [vp, d, C.POINTER(Diag)]
+        L.dg_l1_density.argtypes = [vp, vp, vp, C.POINTER(d)]
+        L.dg_get_meta.argtypes = [vp, C.POINTER(Meta)]
+        L.dg_set_meta.argtypes = [vp, C.POINTER(Meta)]
+        L.dg_profile.argtypes = [vp, i]
+        L.dg_profile_read.argtypes = [vp, C.POINTER(Prof)]
+        _lib = L
+    return _lib
+
+
+# every symbol include/dg.h declares
+EXPORTS = ("dg_scratch_bytes", "dg_init", "dg_free", "dg_last_error", "dg_set_state", "dg_get_state", "dg_rhs",
+           "dg_project_velocity", "dg_step", "dg_set_forcing", "dg_set_forcing_coeffs", "dg_forcing_from_modes",
+           "dg_diagnostics", "dg_l1_density", "dg_get_meta", "dg_set_meta", "dg_profile", "dg_profile_read")
+
+
+class DGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (ERROR_NAMES.get(code, str(code)), msg))
+        self.code = code

@@ -1,0 +1,876 @@
+// dg_api.cu -- host side of libdg: the C ABI of include/dg.h, basis and
+// quadrature tables, the Ornstein-Uhlenbeck driving process, and the
+// orchestration of the kernels on the caller's stream.
+//
+// The tables are computed here from first principles and share no code with
+// any other implementation: Gauss-Legendre nodes and weights come from the
+// eigen-decomposition of the Jacobi matrix of the Legendre recurrence
+// (Golub & Welsch 1969) by cyclic Jacobi rotations in long double.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_launch.cuh"
+
+using namespace dg;
+
+// ---------------------------------------------------------------------------
+// basis and quadrature tables
+// ---------------------------------------------------------------------------
+namespace {
+
+// Golub-Welsch: nodes = eigenvalues of the symmetric tridiagonal Jacobi matrix
+// with off-diagonal j/sqrt(4j^2-1); weights = 2 * (first eigenvector entry)^2.
+void gauss_rule(int n, long double* x, long double* w)
+{
+    std::vector<long double> A(n * n, 0.0L), V(n * n, 0.0L);
+    for (int j = 1; j < n; ++j) {
+        long double bj = j / sqrtl(4.0L * j * j - 1.0L);
+        A[(j - 1) * n + j] = A[j * n + j - 1] = bj;
+    }
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0L;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        long double off = 0.0L;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+        if (off < 1e-40L) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                long double apq = A[p * n + q];
+                if (fabsl(apq) < 1e-300L) continue;
+                long double theta = (A[q * n + q] - A[p * n + p]) / (2.0L * apq);
+                long double t = (theta >= 0 ? 1.0L : -1.0L) / (fabsl(theta) + sqrtl(theta * theta + 1.0L));
+                long double c = 1.0L / sqrtl(t * t + 1.0L), s = t * c;
+                for (int k = 0; k < n; ++k) {  // A <- A J
+                    long double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // A <- J^T A
+                    long double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {  // V <- V J
+                    long double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    for (int i = 0; i < n; ++i)  // sort ascending
+        for (int j = i + 1; j < n; ++j)
+            if (A[idx[j] * n + idx[j]] < A[idx[i] * n + idx[i]]) std::swap(idx[i], idx[j]);
+    for (int i = 0; i < n; ++i) {
+        long double xi = A[idx[i] * n + idx[i]];
+        x[i] = fabsl(xi) < 1e-30L ? 0.0L : xi;
+        w[i] = 2.0L * V[0 * n + idx[i]] * V[0 * n + idx[i]];
+    }
+    for (int i = 0; i < n / 2; ++i) {  // enforce the exact symmetry of the rule
+        long double xs = 0.5L * (x[n - 1 - i] - x[i]), ws = 0.5L * (w[i] + w[n - 1 - i]);
+        x[i] = -xs;
+        x[n - 1 - i] = xs;
+        w[i] = w[n - 1 - i] = ws;
+    }
+}
+
+// normalised Legendre sqrt(2m+1) P_m(x), three-term recurrence
+long double pnorm(int m, long double x)
+{
+    long double p0 = 1.0L, p1 = x;
+    if (m == 0) return 1.0L;
+    for (int j = 2; j <= m; ++j) {
+        long double p2 = ((2.0L * j - 1.0L) * x * p1 - (j - 1.0L) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+    }
+    return sqrtl(2.0L * m + 1.0L) * p1;
+}
+
+template <int K>
+std::vector<double> build_tables()
+{
+    using Dm = Dims<K>;
+    using L = TabLayout<K>;
+    constexpr int b = Dm::b, n = Dm::n, nq = Dm::nq, ns = Dm::ns, nf = Dm::nf, nl = Dm::nl, nql = Dm::nql;
+    constexpr Modes<K> M{};
+    std::vector<double> t(L::total, 0.0);
+    long double xg[16], wg[16], xl[16], wl[16];
+    gauss_rule(n, xg, wg);
+    gauss_rule(nl, xl, wl);
+    auto phi = [&](int l, long double a, long double bb, long double c) {
+        return pnorm(M.i[l], a) * pnorm(M.j[l], bb) * pnorm(M.l[l], c);
+    };
+    for (int q = 0; q < nq; ++q) {
+        const int ia = q % n, ib = (q / n) % n, ic = q / (n * n);
+        const long double wq = wg[ia] * wg[ib] * wg[ic] / 8.0L;
+        t[L::wq + q] = (double)wq;
+        t[L::xq + 3 * q + 0] = (double)xg[ia];
+        t[L::xq + 3 * q + 1] = (double)xg[ib];
+        t[L::xq + 3 * q + 2] = (double)xg[ic];
+        for (int l = 0; l < b; ++l) {
+            const long double p = phi(l, xg[ia], xg[ib], xg[ic]);
+            t[L::phiT + l * nq + q] = (double)p;
+            t[L::wphi + q * b + l] = (double)(wq * p);
+        }
+    }
+    // face f = 2d + side (side 1: xi_d = +1); point s = a + n*c over the two
+    // tangential axes in increasing order
+    for (int f = 0; f < 6; ++f) {
+        const int d = f >> 1;
+        const long double sd = (f & 1) ? 1.0L : -1.0L;
+        const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        for (int s = 0; s < ns; ++s) {
+            long double xi[3];
+            xi[d] = sd;
+            xi[t1] = xg[s % n];
+            xi[t2] = xg[s / n];
+            const long double ws = wg[s % n] * wg[s / n];
+            for (int l = 0; l < b; ++l) {
+                const long double p = phi(l, xi[0], xi[1], xi[2]);
+                t[L::phifT + l * nf + f * ns + s] = (double)p;
+                t[L::lift + (f * ns + s) * b + l] = (double)(-sd * ws * p);
+            }
+        }
+    }
+    for (int q = 0; q < nql; ++q) {
+        const int ia = q % nl, ib = (q / nl) % nl, ic = q / (nl * nl);
+        t[L::wL + q] = (double)(wl[ia] * wl[ib] * wl[ic] / 8.0L);
+        for (int l = 0; l < b; ++l) t[L::phiL + l * nql + q] = (double)phi(l, xl[ia], xl[ib], xl[ic]);
+    }
+    return t;
+}
+
+std::vector<double> tables_for(int K)
+{
+    if (K == 1) return build_tables<1>();
+    if (K == 2) return build_tables<2>();
+    return build_tables<3>();
+}
+
+int tab_total(int K)
+{
+    if (K == 1) return TabLayout<1>::total;
+    if (K == 2) return TabLayout<2>::total;
+    return TabLayout<3>::total;
+}
+
+// ---------------------------------------------------------------------------
+// Ornstein-Uhlenbeck driving (Sec. 4.2)
+// ---------------------------------------------------------------------------
+constexpr int kMaxModes = 512;
+
+struct Driver {
+    bool on = false, dirty = false;
+    int nm = 0, kmaxc = 0;
+    int kv[kMaxModes][3];
+    double x[kMaxModes][3][2];
+    double zeta = 0, tc = 0, dtd = 0, f = 0, s = 0, t_next = 0, t_off = 0;
+    uint64_t rng = 0;
+    bool have_spare = false;
+    double spare = 0;
+
+    // SplitMix64 (Steele, Lea & Flood 2014)
+    uint64_t next()
+    {
+        rng += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = rng;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    }
+    double uni() { return (double)(next() >> 11) * 0x1.0p-53; }
+    // Box-Muller, cosine branch first, sine branch on the following call
+    double normal()
+    {
+        if (have_spare) {
+            have_spare = false;
+            return spare;
+        }
+        const double u1 = 1.0 - uni(), u2 = uni();
+        const double r = std::sqrt(-2.0 * std::log(u1));
+        const double ang = 2.0 * 3.14159265358979323846 * u2;
+        spare = r * std::sin(ang);
+        have_spare = true;
+        return r * std::cos(ang);
+    }
+    void init(const dg_forcing& F, double cs)
+    {
+        const int K = (int)std::floor(std::sqrt((double)F.kmax2) + 1e-9);
+        nm = 0;
+        kmaxc = 0;
+        for (int a = -K; a <= K; ++a)
+            for (int b = -K; b <= K; ++b)
+                for (int c = -K; c <= K; ++c) {
+                    const int r2 = a * a + b * b + c * c;
+                    if (r2 < F.kmin2 || r2 > F.kmax2) continue;
+                    const int lead = a ? a : (b ? b : c);
+                    if (lead <= 0 || nm >= kMaxModes) continue;
+                    kv[nm][0] = a;
+                    kv[nm][1] = b;
+                    kv[nm][2] = c;
+                    ++nm;
+                }
+        kmaxc = K;
+        zeta = F.zeta;
+        tc = 1.0 / (2.0 * cs * F.mach);   // L = 1
+        dtd = tc / 100.0;
+        f = std::exp(-dtd / tc);
+        const double sigma = 2.0 * F.mach * F.mach * cs * cs;
+        s = sigma / std::sqrt(4.0 * nm * (2.0 * zeta * zeta + (1.0 - zeta) * (1.0 - zeta)));
+        rng = F.seed;
+        have_spare = false;
+        for (int m = 0; m < nm; ++m)
+            for (int i = 0; i < 3; ++i)
+                for (int r = 0; r < 2; ++r) x[m][i][r] = s * normal();
+        t_next = dtd;
+        t_off = F.t_off;
+        on = F.on != 0;
+        dirty = true;
+    }
+    void advance()
+    {
+        const double c = s * std::sqrt(1.0 - f * f);
+        for (int m = 0; m < nm; ++m)
+            for (int i = 0; i < 3; ++i)
+                for (int r = 0; r < 2; ++r) x[m][i][r] = f * x[m][i][r] + c * normal();
+    }
+    // amplitudes A_k = P_zeta(k) x_k, P_zeta = zeta (I - kk^T/k^2) + (1-zeta) kk^T/k^2
+    void amplitudes(std::vector<double>& amp, std::vector<int>& kvec) const
+    {
+        amp.assign(nm * 6, 0.0);
+        kvec.assign(nm * 3, 0);
+        for (int m = 0; m < nm; ++m) {
+            double k2 = 0;
+            for (int i = 0; i < 3; ++i) {
+                kvec[m * 3 + i] = kv[m][i];
+                k2 += (double)kv[m][i] * kv[m][i];
+            }
+            for (int r = 0; r < 2; ++r)
+                for (int i = 0; i < 3; ++i) {
+                    double acc = 0;
+                    for (int j = 0; j < 3; ++j) {
+                        const double kk = (double)kv[m][i] * kv[m][j] / k2;
+                        acc += (zeta * ((i == j ? 1.0 : 0.0) - kk) + (1.0 - zeta) * kk) * x[m][j][r];
+                    }
+                    amp[(m * 3 + i) * 2 + r] = acc;
+                }
+        }
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct dg_ctx {
+    int N = 0, K = 0, prec = 0, rk = 3, b = 0;
+    long ncell = 0;
+    double cs = 1, cfl = 0.3, h = 1;
+    dg_nu_params nu{};
+    cudaStream_t st = nullptr;
+    void* reg[3] = {nullptr, nullptr, nullptr};
+    int cur = 0;
+    void* vhat = nullptr;
+    void* ahat = nullptr;
+    char* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    Ctl* ctl = nullptr;
+    double* partials = nullptr;
+    void* tab = nullptr;
+    int* d_kvec = nullptr;
+    double* d_amp = nullptr;
+    int nsm = 0;
+    bool state_set = false;
+    bool forcing_active = false;  // ahat holds a forcing to apply
+    Driver drv;
+    double t = 0.0, dt_last = 0.0;
+    int64_t steps = 0;
+    unsigned int status = 0;
+    std::string err;
+    // profiling: events recorded around launches, resolved in dg_profile_read
+    bool prof = false;
+    dg_prof counts{};
+    struct Pending {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    ~dg_ctx()
+    {
+        for (auto& p : pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+struct ScratchLayout {
+    size_t ctl, partials, tab, kvec, amp, total;
+};
+
+ScratchLayout scratch_layout(int K)
+{
+    ScratchLayout s{};
+    size_t off = 0;
+    s.ctl = off;
+    off = align256(off + sizeof(Ctl));
+    s.partials = off;
+    off = align256(off + sizeof(double) * 16 * kMaxGrid);
+    s.tab = off;
+    off = align256(off + sizeof(double) * tab_total(K));
+    s.kvec = off;
+    off = align256(off + sizeof(int) * 3 * kMaxModes);
+    s.amp = off;
+    off = align256(off + sizeof(double) * 6 * kMaxModes);
+    s.total = off;
+    return s;
+}
+
+int fail(dg_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, DG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+Launch make_launch(const dg_ctx* c)
+{
+    Launch L{};
+    L.st = c->st;
+    L.K = c->K;
+    L.N = c->N;
+    L.ncell = c->ncell;
+    L.ph.cs = c->cs;
+    L.ph.cs2 = c->cs * c->cs;
+    L.ph.h = c->h;
+    L.ph.hp = c->h / (c->K + 1);
+    L.ph.alpha = c->nu.alpha;
+    L.ph.beta = c->nu.beta;
+    L.ph.floor_ = c->nu.rho_floor;
+    L.ph.av_mode = c->nu.mode;
+    L.tab = c->tab;
+    L.ctl = c->ctl;
+    L.partials = c->partials;
+    L.nsm = c->nsm;
+    return L;
+}
+
+size_t elem(const dg_ctx* c) { return c->prec == DG_PREC_F64 ? sizeof(double) : sizeof(float); }
+size_t state_bytes(const dg_ctx* c) { return elem(c) * (size_t)c->ncell * 4 * c->b; }
+size_t vec_bytes(const dg_ctx* c) { return elem(c) * (size_t)c->ncell * 3 * c->b; }
+
+enum { KIND_PROJECT = 0, KIND_RHS = 1, KIND_FORCE = 2, KIND_OTHER = 3 };
+
+cudaEvent_t take_event(dg_ctx* c)
+{
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// bracket one launch: begin() before, end() after
+struct Timed {
+    dg_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Timed(dg_ctx* c_, int k) : c(c_), kind(k)
+    {
+        c->counts.launches += 1;
+        if (kind == KIND_PROJECT) c->counts.n_project += 1;
+        if (kind == KIND_RHS) c->counts.n_rhs += 1;
+        if (kind == KIND_FORCE) c->counts.n_force += 1;
+        if (kind == KIND_OTHER) c->counts.n_other += 1;
+        if (c->prof) {
+            a = take_event(c);
+            cudaEventRecord(a, c->st);
+        }
+    }
+    ~Timed()
+    {
+        if (c->prof && a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c->st);
+            c->pending.push_back({a, b, kind});
+        }
+    }
+};
+
+cudaError_t project(dg_ctx* c, const void* u, void* vhat, bool with_force, bool dt_flag)
+{
+    Timed tm(c, KIND_PROJECT);
+    Launch L = make_launch(c);
+    int flags = (with_force ? F_FORCE : 0) | (dt_flag ? F_DT : 0);
+    if (c->prec == DG_PREC_F64)
+        return launch_project<double>(L, (const double*)u, (double*)vhat, (const double*)c->ahat, flags);
+    return launch_project<float>(L, (const float*)u, (float*)vhat, (const float*)c->ahat, flags);
+}
+
+cudaError_t rhs_stage(dg_ctx* c, const void* u_in, const void* u_n, void* out, const void* ahat, double ra, double rb,
+                      bool update, double dt_pimax, bool with_force)
+{
+    Timed tm(c, KIND_RHS);
+    Launch L = make_launch(c);
+    int flags = with_force ? F_FORCE : 0;
+    if (c->prec == DG_PREC_F64)
+        return launch_rhs<double>(L, (const double*)u_in, (const double*)u_n, (double*)out, (double*)c->vhat,
+                                  (const double*)ahat, ra, rb, update, dt_pimax, flags);
+    return launch_rhs<float>(L, (const float*)u_in, (const float*)u_n, (float*)out, (float*)c->vhat,
+                             (const float*)ahat, (float)ra, (float)rb, update, dt_pimax, flags);
+}
+
+int upload_forcing(dg_ctx* ctx)
+{
+    std::vector<double> amp;
+    std::vector<int> kv;
+    ctx->drv.amplitudes(amp, kv);
+    if (ctx->drv.nm == 0) return DG_OK;
+    CK(cudaMemcpyAsync(ctx->d_kvec, kv.data(), sizeof(int) * kv.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_amp, amp.data(), sizeof(double) * amp.size(), cudaMemcpyHostToDevice, ctx->st));
+    Launch L = make_launch(ctx);
+    cudaError_t e;
+    {
+        Timed tm(ctx, KIND_FORCE);
+        e = (ctx->prec == DG_PREC_F64)
+                ? launch_force<double>(L, ctx->drv.nm, ctx->d_kvec, ctx->d_amp, ctx->drv.kmaxc, (double*)ctx->ahat)
+                : launch_force<float>(L, ctx->drv.nm, ctx->d_kvec, ctx->d_amp, ctx->drv.kmaxc, (float*)ctx->ahat);
+    }
+    CK(e);
+    // the host buffers must stay valid until the copies ran
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->forcing_active = true;
+    return DG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int dg_scratch_bytes(const dg_mesh* mesh, int order, const dg_nu_params* nu, size_t* bytes)
+{
+    (void)mesh;
+    (void)nu;
+    if (!bytes || order < 1 || order > 3) return DG_EINVAL;
+    *bytes = scratch_layout(order).total;
+    return DG_OK;
+}
+
+int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu_params* nu, const dg_opts* opts)
+{
+    if (!out) return DG_EINVAL;
+    *out = nullptr;
+    if (!mesh || !nu || !opts) return DG_EINVAL;
+    if (order < 1 || order > 3) return DG_EINVAL;
+    if (mesh->n[0] < 1 || mesh->n[0] != mesh->n[1] || mesh->n[0] != mesh->n[2]) return DG_EINVAL;
+    if (mesh->n[0] > 2048) return DG_EINVAL;
+    for (int d = 0; d < 3; ++d)
+        if (mesh->L[d] != 1.0) return DG_EINVAL;
+    if (!(cs > 0.0)) return DG_EINVAL;
+    if (nu->mode < 0 || nu->mode > 2 || !(nu->rho_floor >= 0.0)) return DG_EINVAL;
+    if (opts->precision < 0 || opts->precision > 1) return DG_EINVAL;  // X3 transforms: see dg_x3.cu
+    if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
+    if (!(opts->cfl > 0.0)) return DG_EINVAL;
+    if (!opts->stream) return DG_EINVAL;
+    for (int i = 0; i < 3; ++i)
+        if (!opts->u[i]) return DG_EINVAL;
+    if (!opts->vhat || !opts->ahat || !opts->scratch) return DG_EINVAL;
+    if (((uintptr_t)opts->scratch) & 255u) return DG_EINVAL;
+    ScratchLayout sl = scratch_layout(order);
+    if (opts->scratch_bytes < sl.total) return DG_ENOMEM;
+
+    dg_ctx* ctx = new (std::nothrow) dg_ctx();
+    if (!ctx) return DG_ENOMEM;
+    ctx->N = mesh->n[0];
+    ctx->K = order;
+    ctx->b = (order + 1) * (order + 2) * (order + 3) / 6;
+    ctx->ncell = (long)ctx->N * ctx->N * ctx->N;
+    ctx->h = 1.0 / ctx->N;
+    ctx->cs = cs;
+    ctx->cfl = opts->cfl;
+    ctx->rk = opts->rk_stages;
+    ctx->prec = opts->precision;
+    ctx->nu = *nu;
+    ctx->st = (cudaStream_t)opts->stream;
+    for (int i = 0; i < 3; ++i) ctx->reg[i] = opts->u[i];
+    ctx->vhat = opts->vhat;
+    ctx->ahat = opts->ahat;
+    ctx->scratch = (char*)opts->scratch;
+    ctx->scratch_bytes = opts->scratch_bytes;
+    ctx->ctl = (Ctl*)(ctx->scratch + sl.ctl);
+    ctx->partials = (double*)(ctx->scratch + sl.partials);
+    ctx->tab = ctx->scratch + sl.tab;
+    ctx->d_kvec = (int*)(ctx->scratch + sl.kvec);
+    ctx->d_amp = (double*)(ctx->scratch + sl.amp);
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = (ctx->prec == DG_PREC_F64) ? setup_kernels<double>(order) : setup_kernels<float>(order);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "dg_init: %s\n", cudaGetErrorString(e));
+        delete ctx;
+        return DG_ECUDA;
+    }
+    // tables in the element type of the precision mode
+    std::vector<double> t = tables_for(order);
+    Ctl c0{};
+    c0.dt_scale = 1.0;
+    c0.dt_num = ctx->cfl * ctx->h / (order + 1);
+    e = cudaMemcpyAsync(ctx->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess) {
+        if (ctx->prec == DG_PREC_F64) {
+            e = cudaMemcpyAsync(ctx->tab, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, ctx->st);
+        } else {
+            std::vector<float> tf(t.begin(), t.end());
+            e = cudaMemcpyAsync(ctx->tab, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice, ctx->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ahat, 0, vec_bytes(ctx), ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "dg_init: %s\n", cudaGetErrorString(e));
+        delete ctx;
+        return DG_ECUDA;
+    }
+    *out = ctx;
+    return DG_OK;
+}
+
+void dg_free(dg_ctx* ctx) { delete ctx; }
+
+const char* dg_last_error(const dg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int dg_set_state(dg_ctx* ctx, const void* src, int src_on_host)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!src) return fail(ctx, DG_EINVAL, "dg_set_state: null source");
+    ctx->cur = 0;
+    CK(cudaMemcpyAsync(ctx->reg[0], src, state_bytes(ctx), src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       ctx->st));
+    unsigned int zero = 0u;
+    CK(cudaMemcpyAsync(&ctx->ctl->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->status = 0u;
+    ctx->state_set = true;
+    return DG_OK;
+}
+
+int dg_get_state(dg_ctx* ctx, void* dst, int dst_on_host)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!dst) return fail(ctx, DG_EINVAL, "dg_get_state: null destination");
+    if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_get_state: no state set");
+    CK(cudaMemcpyAsync(dst, ctx->reg[ctx->cur], state_bytes(ctx),
+                       dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_project_velocity(dg_ctx* ctx, const void* u_in, void* vhat_out)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!u_in || !vhat_out) return fail(ctx, DG_EINVAL, "dg_project_velocity: null buffer");
+    CK(project(ctx, u_in, vhat_out, false, false));
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_rhs(dg_ctx* ctx, const void* u_in, const void* ahat, void* dudt, double dt_for_pimax)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!u_in || !dudt) return fail(ctx, DG_EINVAL, "dg_rhs: null buffer");
+    const void* saved = ctx->ahat;
+    ctx->ahat = const_cast<void*>(ahat);
+    cudaError_t e = project(ctx, u_in, ctx->vhat, ahat != nullptr, false);
+    ctx->ahat = const_cast<void*>(saved);
+    CK(e);
+    CK(rhs_stage(ctx, u_in, nullptr, dudt, ahat, 0.0, 1.0, false, dt_for_pimax, ahat != nullptr));
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_set_forcing(dg_ctx* ctx, const dg_forcing* f)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!f) return fail(ctx, DG_EINVAL, "dg_set_forcing: null");
+    if (f->on && (!(f->mach > 0.0) || f->kmin2 < 1 || f->kmax2 < f->kmin2 || f->kmax2 > 64 || f->zeta < 0.0 ||
+                  f->zeta > 1.0))
+        return fail(ctx, DG_EINVAL, "dg_set_forcing: bad parameters");
+    if (!f->on) {
+        ctx->drv.on = false;
+        ctx->forcing_active = false;
+        CK(cudaMemsetAsync(ctx->ahat, 0, vec_bytes(ctx), ctx->st));
+        return DG_OK;
+    }
+    ctx->drv.init(*f, ctx->cs);
+    if (ctx->drv.nm > kMaxModes) return fail(ctx, DG_EINVAL, "dg_set_forcing: too many modes");
+    ctx->forcing_active = false;
+    return DG_OK;
+}
+
+int dg_set_forcing_coeffs(dg_ctx* ctx, const void* src, int src_on_host)
+{
+    if (!ctx) return DG_EINVAL;
+    ctx->drv.on = false;
+    if (!src) {
+        ctx->forcing_active = false;
+        CK(cudaMemsetAsync(ctx->ahat, 0, vec_bytes(ctx), ctx->st));
+        return DG_OK;
+    }
+    CK(cudaMemcpyAsync(ctx->ahat, src, vec_bytes(ctx), src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->forcing_active = true;
+    return DG_OK;
+}
+
+int dg_forcing_from_modes(dg_ctx* ctx, int nmodes, const int32_t* kvec, const double* amp)
+{
+    if (!ctx) return DG_EINVAL;
+    if (nmodes < 1 || nmodes > kMaxModes || !kvec || !amp) return fail(ctx, DG_EINVAL, "dg_forcing_from_modes: bad args");
+    int kmaxc = 0;
+    for (int i = 0; i < 3 * nmodes; ++i) kmaxc = std::max(kmaxc, std::abs((int)kvec[i]));
+    if (kmaxc > 8) return fail(ctx, DG_EINVAL, "dg_forcing_from_modes: |k_d| > 8");
+    CK(cudaMemcpyAsync(ctx->d_kvec, kvec, sizeof(int) * 3 * nmodes, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_amp, amp, sizeof(double) * 6 * nmodes, cudaMemcpyHostToDevice, ctx->st));
+    Launch L = make_launch(ctx);
+    cudaError_t e;
+    {
+        Timed tm(ctx, KIND_FORCE);
+        e = (ctx->prec == DG_PREC_F64)
+                ? launch_force<double>(L, nmodes, ctx->d_kvec, ctx->d_amp, kmaxc, (double*)ctx->ahat)
+                : launch_force<float>(L, nmodes, ctx->d_kvec, ctx->d_amp, kmaxc, (float*)ctx->ahat);
+    }
+    CK(e);
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->drv.on = false;
+    ctx->forcing_active = true;
+    return DG_OK;
+}
+
+int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_last)
+{
+    if (!ctx) return DG_EINVAL;
+    if (nsteps < 0) return fail(ctx, DG_EINVAL, "dg_step: nsteps < 0");
+    if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_step: no state set");
+    static const double A2[2] = {0.0, 0.5}, B2[2] = {1.0, 0.5};
+    static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double* RA = ctx->rk == 2 ? A2 : A3;
+    const double* RB = ctx->rk == 2 ? B2 : B3;
+    for (int st = 0; st < nsteps; ++st) {
+        // driving schedule (Sec. 4.2): OU update at the first step with t >= t_next
+        if (ctx->drv.on && ctx->drv.t_off > 0.0 && ctx->t > ctx->drv.t_off) {
+            ctx->drv.on = false;
+            ctx->forcing_active = false;
+            CK(cudaMemsetAsync(ctx->ahat, 0, vec_bytes(ctx), ctx->st));
+        }
+        if (ctx->drv.on) {
+            while (ctx->t >= ctx->drv.t_next) {
+                ctx->drv.advance();
+                ctx->drv.t_next += ctx->drv.dtd;
+                ctx->drv.dirty = true;
+            }
+            if (ctx->drv.dirty) {
+                int rc = upload_forcing(ctx);
+                if (rc) return rc;
+                ctx->drv.dirty = false;
+            }
+        }
+        const bool force = ctx->forcing_active;
+        const int A = ctx->cur, B = (ctx->cur + 1) % 3, C = (ctx->cur + 2) % 3;
+        // register use: RK3  A->B, (B,A)->C, (C,A)->B ; RK2  A->B, (B,A)->C
+        const int in3[3] = {A, B, C}, out3[3] = {B, C, B};
+        const int in2[2] = {A, B}, out2[2] = {B, C};
+        const int* in = ctx->rk == 2 ? in2 : in3;
+        const int* out = ctx->rk == 2 ? out2 : out3;
+        bool ok = false;
+        double dt = 0.0;
+        unsigned int status = 0u;
+        for (int retry = 0; retry <= 3 && !ok; ++retry) {
+            struct {
+                double dt_scale, fixed_dt;
+            } hs = {1.0 / (double)(1 << retry), fixed_dt};
+            CK(cudaMemcpyAsync(&ctx->ctl->dt_scale, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->st));
+            unsigned int zero = 0u;
+            CK(cudaMemcpyAsync(&ctx->ctl->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->st));
+            for (int s = 0; s < ctx->rk; ++s) {
+                CK(project(ctx, ctx->reg[in[s]], ctx->vhat, force, s == 0));
+                CK(rhs_stage(ctx, ctx->reg[in[s]], ctx->reg[A], ctx->reg[out[s]], ctx->ahat, RA[s], RB[s], true, 0.0,
+                             force));
+            }
+            struct {
+                unsigned int status;
+                double dt;
+            } back{};
+            CK(cudaMemcpyAsync(&back.status, &ctx->ctl->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaMemcpyAsync(&back.dt, &ctx->ctl->dt, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            status = back.status;
+            dt = back.dt;
+            ok = !(status & DG_ST_FAIL);
+        }
+        if (!ok) {
+            ctx->status |= status;
+            return fail(ctx, DG_EPOSITIVITY, "dg_step: positivity retries exhausted");
+        }
+        ctx->status |= status;
+        ctx->cur = out[ctx->rk - 1];
+        ctx->t += dt;
+        ctx->dt_last = dt;
+        ctx->steps += 1;
+        if (status & DG_ST_NONFINITE) return fail(ctx, DG_ENONFINITE, "dg_step: non-finite coefficient");
+    }
+    if (t_out) *t_out = ctx->t;
+    if (dt_last) *dt_last = ctx->dt_last;
+    return DG_OK;
+}
+
+int dg_diagnostics(dg_ctx* ctx, double dt_for_pimax, dg_diag* out)
+{
+    if (!ctx || !out) return DG_EINVAL;
+    if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_diagnostics: no state set");
+    const void* u = ctx->reg[ctx->cur];
+    const bool force = ctx->forcing_active;
+    // abar of the current state first (into the control block), then the reductions
+    CK(project(ctx, u, ctx->vhat, force, false));
+    Launch L = make_launch(ctx);
+    int flags = force ? F_FORCE : 0;
+    Timed tm(ctx, KIND_OTHER);
+    cudaError_t e = (ctx->prec == DG_PREC_F64)
+                        ? launch_diag<double>(L, (const double*)u, (const double*)ctx->ahat, dt_for_pimax, flags)
+                        : launch_diag<float>(L, (const float*)u, (const float*)ctx->ahat, dt_for_pimax, flags);
+    CK(e);
+    double d[16];
+    CK(cudaMemcpyAsync(d, ctx->ctl->diag, sizeof(d), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    out->mass = d[0];
+    for (int i = 0; i < 3; ++i) out->mom[i] = d[1 + i];
+    out->ekin = d[4];
+    out->mach = std::sqrt(d[5]) / ctx->cs;
+    out->mach_rho = std::sqrt(2.0 * d[4] / d[0]) / ctx->cs;
+    out->rho_min = d[7];
+    out->rho_max = d[8];
+    out->av_frac = d[9];
+    out->inj_power = d[10];
+    out->max_speed = d[11];
+    out->av_work = d[12];
+    out->status = ctx->status;
+    out->t = ctx->t;
+    out->steps = ctx->steps;
+    return DG_OK;
+}
+
+int dg_l1_density(dg_ctx* ctx, const void* uA, const void* uB, double* out)
+{
+    if (!ctx || !uA || !uB || !out) return DG_EINVAL;
+    Launch L = make_launch(ctx);
+    Timed tm(ctx, KIND_OTHER);
+    cudaError_t e = (ctx->prec == DG_PREC_F64) ? launch_l1<double>(L, (const double*)uA, (const double*)uB)
+                                               : launch_l1<float>(L, (const float*)uA, (const float*)uB);
+    CK(e);
+    CK(cudaMemcpyAsync(out, &ctx->ctl->l1, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_profile(dg_ctx* ctx, int enable)
+{
+    if (!ctx) return DG_EINVAL;
+    CK(cudaStreamSynchronize(ctx->st));
+    for (auto& p : ctx->pending) {
+        ctx->pool.push_back(p.a);
+        ctx->pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    ctx->counts = dg_prof{};
+    ctx->prof = enable != 0;
+    return DG_OK;
+}
+
+int dg_profile_read(dg_ctx* ctx, dg_prof* out)
+{
+    if (!ctx || !out) return DG_EINVAL;
+    CK(cudaStreamSynchronize(ctx->st));
+    for (auto& p : ctx->pending) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, p.a, p.b));
+        if (p.kind == KIND_PROJECT) ctx->counts.ms_project += ms;
+        if (p.kind == KIND_RHS) ctx->counts.ms_rhs += ms;
+        if (p.kind == KIND_FORCE) ctx->counts.ms_force += ms;
+        if (p.kind == KIND_OTHER) ctx->counts.ms_other += ms;
+        ctx->pool.push_back(p.a);
+        ctx->pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    *out = ctx->counts;
+    return DG_OK;
+}
+
+int dg_get_meta(dg_ctx* ctx, dg_meta* m)
+{
+    if (!ctx || !m) return DG_EINVAL;
+    std::memset(m, 0, sizeof(*m));
+    m->t = ctx->t;
+    m->steps = ctx->steps;
+    m->dt_last = ctx->dt_last;
+    m->forcing_on = ctx->drv.on ? 1 : 0;
+    m->forcing_dirty = ctx->drv.dirty ? 1 : 0;
+    m->t_next = ctx->drv.t_next;
+    m->rng = ctx->drv.rng;
+    m->have_spare = ctx->drv.have_spare ? 1 : 0;
+    m->spare = ctx->drv.spare;
+    m->nmodes = ctx->drv.nm;
+    std::memcpy(m->x, ctx->drv.x, sizeof(double) * 6 * ctx->drv.nm);
+    return DG_OK;
+}
+
+int dg_set_meta(dg_ctx* ctx, const dg_meta* m)
+{
+    if (!ctx || !m) return DG_EINVAL;
+    if (m->nmodes != ctx->drv.nm) return fail(ctx, DG_EINVAL, "dg_set_meta: call dg_set_forcing with the same modes first");
+    ctx->t = m->t;
+    ctx->steps = m->steps;
+    ctx->dt_last = m->dt_last;
+    ctx->drv.on = m->forcing_on != 0;
+    ctx->drv.t_next = m->t_next;
+    ctx->drv.rng = m->rng;
+    ctx->drv.have_spare = m->have_spare != 0;
+    ctx->drv.spare = m->spare;
+    std::memcpy(ctx->drv.x, m->x, sizeof(double) * 6 * m->nmodes);
+    // re-project the current OU amplitudes before the next step
+    ctx->drv.dirty = ctx->drv.on;
+    if (!ctx->drv.on) ctx->forcing_active = false;
+    return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+// dg_common.cuh -- compile-time basis description and pointwise physics shared
+// by the kernels of libdg (sm_103a).
+//
+// Basis (Sec. 2.1): phi_{ijl}(xi) = Pn_i(xi_x) Pn_j(xi_y) Pn_l(xi_z),
+// Pn_m = sqrt(2m+1) P_m, complete degree-k set, ordered by total degree, then i
+// descending, then j descending.  (1/8) int phi_a phi_b = delta_ab.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace dg {
+
+template <int K>
+struct Dims {
+    static constexpr int n = K + 1;                          // Gauss points per axis
+    static constexpr int b = (K + 1) * (K + 2) * (K + 3) / 6;  // modes per field
+    static constexpr int nq = n * n * n;                     // volume points
+    static constexpr int ns = n * n;                         // points per face
+    static constexpr int nf = 6 * ns;                        // face points per cell
+    static constexpr int nl = K + 3;                         // L1-norm points per axis
+    static constexpr int nql = nl * nl * nl;
+};
+
+template <int K>
+struct Modes {
+    int i[Dims<K>::b], j[Dims<K>::b], l[Dims<K>::b];
+    constexpr Modes() : i{}, j{}, l{}
+    {
+        int c = 0;
+        for (int d = 0; d <= K; ++d)
+            for (int a = d; a >= 0; --a)
+                for (int e = d - a; e >= 0; --e) {
+                    i[c] = a;
+                    j[c] = e;
+                    l[c] = d - a - e;
+                    ++c;
+                }
+    }
+};
+
+constexpr double csqrt(double x)
+{
+    if (x <= 0.0) return 0.0;
+    double r = x > 1.0 ? x : 1.0;
+    for (int it = 0; it < 200; ++it) r = 0.5 * (r + x / r);
+    return r;
+}
+
+// (1/2) int_{-1}^{1} Pn_a(t) Pn_b'(t) dt: Pn_b' = sum_{a<b, a+b odd} sqrt((2a+1)(2b+1)) Pn_a
+constexpr double dcoef(int a, int b) { return (a < b && ((a + b) & 1)) ? csqrt((2.0 * a + 1.0) * (2.0 * b + 1.0)) : 0.0; }
+
+// Modal differentiation matrix D_d[m][l] = (1/8) int phi_m dphi_l/dxi_d.  The
+// derivative of a degree-k polynomial stays in the span, so
+//   d/dxi_d (sum_l c_l phi_l) = sum_m (sum_l D_d[m][l] c_l) phi_m   exactly.
+template <int K>
+constexpr double Dmat(int d, int m, int l)
+{
+    constexpr Modes<K> M{};
+    int am[3] = {M.i[m], M.j[m], M.l[m]};
+    int al[3] = {M.i[l], M.j[l], M.l[l]};
+    for (int e = 0; e < 3; ++e)
+        if (e != d && am[e] != al[e]) return 0.0;
+    return dcoef(am[d], al[d]);
+}
+
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+// g = scale * D_d c   (gradient coefficients of one field)
+template <typename T, int K, int D>
+__device__ __forceinline__ void modal_grad(const T* c, T* g, T scale)
+{
+    constexpr int b = Dims<K>::b;
+    static_for<0, b>([&](auto m) {
+        T acc = T(0);
+        static_for<0, b>([&](auto l) {
+            constexpr double v = Dmat<K>(D, decltype(m)::value, decltype(l)::value);
+            if constexpr (v != 0.0) acc += T(v) * c[decltype(l)::value];
+        });
+        g[decltype(m)::value] = acc * scale;
+    });
+}
+
+// r += scale * D_d^T f   (weak-form volume term from projected flux coefficients)
+template <typename T, int K, int D>
+__device__ __forceinline__ void modal_grad_T_acc(const T* f, T* r, T scale)
+{
+    constexpr int b = Dims<K>::b;
+    static_for<0, b>([&](auto l) {
+        T acc = T(0);
+        static_for<0, b>([&](auto m) {
+            constexpr double v = Dmat<K>(D, decltype(m)::value, decltype(l)::value);
+            if constexpr (v != 0.0) acc += T(v) * f[decltype(m)::value];
+        });
+        r[decltype(l)::value] += acc * scale;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// control block in the caller's scratch (FP64 global quantities)
+// ---------------------------------------------------------------------------
+struct Ctl {
+    unsigned int status;     // sticky DG_ST_* bits
+    unsigned int cnt_proj;   // last-block counter of the projection kernel
+    unsigned int cnt_diag;   // last-block counter of diagnostics / L1
+    unsigned int pad0;
+    unsigned long long smax; // bits of max sum_d(|v_d|+cs) (positive double)
+    double dt;               // dt of the current step (fixes Pi_max)
+    double dt_scale;         // 1, 1/2, 1/4, 1/8 on retries
+    double fixed_dt;         // > 0 replaces the CFL dt
+    double abar[3];          // <rho a_h>/<rho>
+    double rho_sum;          // <rho>
+    double dt_num;           // cfl h / (k+1)
+    double diag[16];         // diagnostics result
+    double l1;               // L1 result
+    double pad[4];
+};
+
+// kernel flags
+enum { F_DT = 1, F_FORCE = 2 };
+
+#define DG_ST_LIMITED_ 1u
+#define DG_ST_FAIL_ 2u
+#define DG_ST_NONFINITE_ 4u
+#define DG_NDIAG 13
+
+// ---------------------------------------------------------------------------
+// pointwise physics
+// ---------------------------------------------------------------------------
+struct Phys {
+    double cs, cs2, h, hp;       // sound speed, cs^2, cell size, h/(k+1)
+    double alpha, beta, floor_;  // vNR coefficients, density floor
+    int av_mode;                 // 0 off, 1 vNR, 2 learned
+};
+
+// von Neumann-Richtmyer viscous pressure at a volume point (Sec. 3.1):
+// Pi = alpha rho (h/p)^2 D^2 + beta rho cs (h/p) |D| for D = div v < 0,
+// limited by rho (h/p)^2 |D| / (2 dt); zero otherwise.  dt <= 0: no limit.
+template <typename T>
+__device__ __forceinline__ T vnr_pressure(const Phys& P, T rho, T divv, T dt)
+{
+    if (!(divv < T(0))) return T(0);
+    T a = -divv, hp = T(P.hp);
+    T Pi = T(P.alpha) * rho * hp * hp * a * a + T(P.beta) * rho * T(P.cs) * hp * a;
+    if (dt > T(0)) {
+        T Pmax = T(0.5) * rho * hp * hp * a / dt;
+        Pi = Pi < Pmax ? Pi : Pmax;
+    }
+    return Pi;
+}
+
+// Rusanov flux along +e_d, left/right primitive states (rho, v):
+//   F* = (F(U_L) + F(U_R))/2 - lambda (U_R - U_L)/2,
+//   lambda = max(|v_d^L|, |v_d^R|) + cs, F(U) = (rho v_d, rho v_i v_d + cs^2 rho delta_id)
+template <typename T, int D>
+__device__ __forceinline__ void rusanov(T cs, T cs2, const T WL[4], const T WR[4], T F[4])
+{
+    T UL[4], UR[4];
+    UL[0] = WL[0];
+    UR[0] = WR[0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        UL[1 + i] = WL[0] * WL[1 + i];
+        UR[1 + i] = WR[0] * WR[1 + i];
+    }
+    T vl = WL[1 + D], vr = WR[1 + D];
+    T lam = fmax(fabs(vl), fabs(vr)) + cs;
+    T FL[4], FR[4];
+    FL[0] = UL[1 + D];
+    FR[0] = UR[1 + D];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        FL[1 + i] = UL[1 + i] * vl + (i == D ? cs2 * WL[0] : T(0));
+        FR[1 + i] = UR[1 + i] * vr + (i == D ? cs2 * WR[0] : T(0));
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v] = T(0.5) * (FL[v] + FR[v]) - T(0.5) * lam * (UR[v] - UL[v]);
+}
+
+template <typename T>
+__device__ __forceinline__ void rusanov_dir(int d, T cs, T cs2, const T WL[4], const T WR[4], T F[4])
+{
+    if (d == 0)
+        rusanov<T, 0>(cs, cs2, WL, WR, F);
+    else if (d == 1)
+        rusanov<T, 1>(cs, cs2, WL, WR, F);
+    else
+        rusanov<T, 2>(cs, cs2, WL, WR, F);
+}
+
+// ordered integer keys so that atomicMin/Max work on floating-point values
+__device__ __forceinline__ int float_key(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float key_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+__device__ __forceinline__ long long double_key(double f)
+{
+    long long i = __double_as_longlong(f);
+    return i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ double key_double(long long i)
+{
+    return __longlong_as_double(i >= 0 ? i : i ^ 0x7fffffffffffffffLL);
+}
+
+// ---------------------------------------------------------------------------
+// table layout (element type T) in the caller's scratch, per degree
+// ---------------------------------------------------------------------------
+template <int K>
+struct TabLayout {
+    using D = Dims<K>;
+    static constexpr int phiT = 0;                              // [b][nq]   phi_l(xi_q)
+    static constexpr int wphi = phiT + D::b * D::nq;            // [nq][b]   w_q/8 phi_l(xi_q)
+    static constexpr int phifT = wphi + D::nq * D::b;           // [b][nf]   phi_l on face points
+    static constexpr int lift = phifT + D::b * D::nf;           // [nf][b]   -sign_f w_s phi_l
+    static constexpr int wq = lift + D::nf * D::b;              // [nq]      w_q/8
+    static constexpr int phiL = wq + D::nq;                     // [b][nql]  phi_l at L1 points
+    static constexpr int wL = phiL + D::b * D::nql;             // [nql]     w/8 at L1 points
+    static constexpr int xq = wL + D::nql;                      // [nq][3]   reference coords
+    static constexpr int total = xq + 3 * D::nq;
+};
+
+}  // namespace dg

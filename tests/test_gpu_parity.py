@@ -1,0 +1,230 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Element-by-element comparison on the same seeded inputs.  Bounds (relative
+L2 per field): FP64 <= 1e-12, FP32 <= 1e-5 for a single evaluation (FP32
+unit round-off 6e-8 times the cancellation in the flux divergence of random
+discontinuous states, about 10-100).  Mesh sizes span several tiles and end
+with a ragged tile for every degree (tile = 32/8/4 cells for k = 1/2/3).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = pytest.mark.skip(reason="no CUDA device")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2401_06841_gb300 import Solver  # noqa: E402
+from paper_2401_06841_gb300 import inputs as I  # noqa: E402
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def rel_l2_fields(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    out = []
+    for v in range(ref.shape[1]):
+        den = np.linalg.norm(ref[:, v])
+        out.append(np.linalg.norm(got[:, v] - ref[:, v]) / (den if den > 0 else 1.0))
+    return np.array(out)
+
+
+def ahat_for(N, k, seed=3, mach=2.0):
+    fo = O.Forcing(mach=mach, zeta=0.5, seed=seed)
+    return O.forcing_project(O.make_cfg(N, k), fo.kvec(), fo.amplitudes())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_projection_parity(k, prec):
+    N = 5
+    u = I.random_state(N, k, seed=20 + k)
+    s = Solver(N, k, precision=prec)
+    got = s.project_velocity(u).cpu().numpy()
+    ref = O.project_velocity(O.make_cfg(N, k), u)
+    assert rel_l2_fields(got, ref).max() < TOL[prec]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("forced", [False, True])
+def test_rhs_parity(k, prec, forced):
+    N = 5
+    u = I.random_state(N, k, seed=30 + k)
+    cfg = O.make_cfg(N, k)
+    a = ahat_for(N, k) if forced else None
+    # a dt that caps the viscous pressure at part of the points
+    dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
+    ref = O.rhs(cfg, u, a, dt)
+    s = Solver(N, k, precision=prec)
+    got = s.rhs(u, a, dt).cpu().numpy()
+    err = rel_l2_fields(got, ref)
+    assert err.max() < TOL[prec], err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_rhs_parity_av_off_and_uncapped(k):
+    N = 4
+    u = I.random_state(N, k, seed=40 + k)
+    for av, dt in (("off", 0.0), ("vnr", 0.0)):
+        cfg = O.make_cfg(N, k, av_mode=0 if av == "off" else 1)
+        ref = O.rhs(cfg, u, None, dt)
+        s = Solver(N, k, precision="f64", av=av)
+        got = s.rhs(u, None, dt).cpu().numpy()
+        assert rel_l2_fields(got, ref).max() < 1e-12
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_forcing_projection_parity(k):
+    N = 6
+    fo = O.Forcing(mach=3.0, zeta=0.5, seed=5)
+    ref = O.forcing_project(O.make_cfg(N, k), fo.kvec(), fo.amplitudes())
+    s = Solver(N, k, precision="f64")
+    got = s.forcing_from_modes(fo.kvec(), fo.amplitudes()).cpu().numpy()
+    assert rel_l2_fields(got, ref).max() < 1e-12
+    s32 = Solver(N, k, precision="f32")
+    got32 = s32.forcing_from_modes(fo.kvec(), fo.amplitudes()).cpu().numpy()
+    assert rel_l2_fields(got32, ref).max() < 1e-5
+
+
+@pytest.mark.gpu
+def test_config1_twenty_driven_steps_fp64():
+    # 16^3 cells, k=1, SSP-RK2, rho=1, v=0, OU |k| in [1,3], zeta=0.5, seed 0,
+    # Mach 2, 20 steps at CFL 0.3
+    N, k = 16, 1
+    u = I.uniform_state(N, k)
+    s = Solver(N, k, precision="f64", rk_stages=2, cfl=0.3)
+    s.set_state(u)
+    s.set_forcing(mach=2.0, zeta=0.5, seed=0)
+    t, dt = s.step(20)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, t_ref, dt_ref, _ = O.run(O.make_cfg(N, k, rk_stages=2, cfl=0.3), ref, 20,
+                                 forcing=O.Forcing(mach=2.0, zeta=0.5, seed=0))
+    assert rc == 0
+    assert abs(t - t_ref) <= 1e-13 * t_ref
+    err = rel_l2_fields(got, ref)
+    assert err.max() < 1e-12, err
+    d = s.diagnostics()
+    assert d["mach"] > 0.0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("k", [2, 3])
+def test_driven_steps_parity(k, prec):
+    N = 5
+    u = I.random_state(N, k, seed=50 + k, v_rms=0.8)
+    s = Solver(N, k, precision=prec)
+    s.set_state(u)
+    s.set_forcing(mach=3.0, zeta=1.0, seed=1)
+    s.step(3)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, _, _, _ = O.run(O.make_cfg(N, k), ref, 3, forcing=O.Forcing(mach=3.0, zeta=1.0, seed=1))
+    assert rc == 0
+    err = rel_l2_fields(got, ref)
+    assert err.max() < (1e-12 if prec == "f64" else 3e-5), err
+
+
+@pytest.mark.gpu
+def test_limiter_parity():
+    # states whose density dips below the floor: both sides rescale the same cells
+    N, k = 4, 2
+    u = I.random_state(N, k, seed=61, rho_wiggle=0.995, rho_mean=0.05, rho_spread=1.5, v_rms=2.0)
+    s = Solver(N, k, precision="f64")
+    s.set_state(u)
+    s.step(1)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    cfg = O.make_cfg(N, k)
+    dt = O.dt(cfg, ref)
+    st = O.step(cfg, ref, None, dt)
+    assert st & O.ORC_LIMITED
+    assert s.diagnostics()["status"] & 1
+    assert rel_l2_fields(got, ref).max() < 1e-12
+
+
+@pytest.mark.gpu
+def test_positivity_failure_is_retried_then_reported():
+    from paper_2401_06841_gb300 import _lib as B
+    N, k = 4, 1
+    u = I.uniform_state(N, k)
+    u[5, 0, 0] = -1.0
+    s = Solver(N, k, precision="f64")
+    s.set_state(u)
+    with pytest.raises(B.DGError) as ei:
+        s.step(1)
+    assert ei.value.code == B.DG_EPOSITIVITY
+    assert np.array_equal(s.get_state().cpu().numpy(), u)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_diagnostics_parity(prec):
+    N, k = 6, 2
+    u = I.random_state(N, k, seed=70)
+    a = ahat_for(N, k)
+    s = Solver(N, k, precision=prec)
+    s.set_state(u)
+    s.set_forcing_coeffs(a)
+    dt = 1e-3
+    got = s.diagnostics(dt)
+    ref = O.diagnostics(O.make_cfg(N, k), u, a, dt)
+    tol = 1e-12 if prec == "f64" else 2e-5
+    for key in ("mass", "mom_x", "mom_y", "mom_z", "ekin", "mach", "mach_rho", "rho_min", "rho_max", "max_speed",
+                "inj_power", "av_work"):
+        assert got[key] == pytest.approx(ref[key], rel=tol, abs=tol * 10), key
+    assert got["av_frac"] == pytest.approx(ref["av_frac"], abs=0.02 if prec == "f32" else 1e-12)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [1, 3])
+def test_l1_density_parity(k):
+    N = 5
+    a = I.random_state(N, k, seed=80)
+    b = I.random_state(N, k, seed=81)
+    s = Solver(N, k, precision="f64")
+    assert s.l1_density(a, b) == pytest.approx(O.l1_density(O.make_cfg(N, k), a, b), rel=1e-12)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_checkpoint_resume_is_bit_identical(prec):
+    N, k = 6, 2
+    u = I.random_state(N, k, seed=90, v_rms=0.6)
+    a = Solver(N, k, precision=prec)
+    a.set_state(u)
+    a.set_forcing(mach=2.0, zeta=0.5, seed=3)
+    a.step(4)
+    snap = a.get_state().clone()
+    meta = a.get_meta()
+    a.step(4)
+    full = a.get_state().cpu().numpy()
+    b = Solver(N, k, precision=prec)
+    b.set_forcing(mach=2.0, zeta=0.5, seed=3)
+    b.set_state(snap)
+    b.set_meta(meta)
+    b.step(4)
+    assert np.array_equal(b.get_state().cpu().numpy(), full)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_conservation_on_gpu(prec):
+    N, k = 8, 3
+    u = I.random_state(N, k, seed=95)
+    s = Solver(N, k, precision=prec)
+    s.set_state(u)
+    s.set_forcing(mach=3.0, zeta=0.5, seed=2)
+    d0 = s.diagnostics()
+    s.step(3)
+    d1 = s.diagnostics()
+    tol = 1e-13 if prec == "f64" else 1e-6
+    assert abs(d1["mass"] - d0["mass"]) < tol * d0["mass"]
+    for c in ("mom_x", "mom_y", "mom_z"):
+        assert abs(d1[c] - d0[c]) < tol * 10 * d0["mass"]
