@@ -135,7 +135,10 @@ def test_driven_steps_parity(k, prec):
 def test_limiter_parity():
     # states whose density dips below the floor: both sides rescale the same cells
     N, k = 4, 2
-    u = I.random_state(N, k, seed=61, rho_wiggle=0.995, rho_mean=0.05, rho_spread=1.5, v_rms=2.0)
+    u = I.random_state(N, k, seed=61, rho_wiggle=0.5)
+    # cells 0 and 9: a steep x-slope makes the density negative near xi_x = -1
+    u[0, 0, 1] = 0.9 * u[0, 0, 0]
+    u[9, 0, 1] = -0.8 * u[9, 0, 0]
     s = Solver(N, k, precision="f64")
     s.set_state(u)
     s.step(1)
