@@ -87,7 +87,11 @@ typedef struct {
     void* u[3];            /* three state registers, each N^3*4*b elements; the
                               current state rotates among them (dg_get_state
                               returns it; u[0] receives dg_set_state)            */
-    void* vhat;            /* N^3*3*b elements                                     */
+    void* vhat;            /* dg_vhat_bytes() bytes, 256-byte aligned: two
+                              projected-velocity buffers of N^3*3*b elements (a
+                              stage reads one while its epilogue writes the next
+                              stage's into the other); the second starts at the
+                              first multiple of 256 bytes past the first          */
     void* ahat;            /* N^3*3*b elements                                     */
     void* scratch;         /* >= dg_scratch_bytes(), 256-byte aligned              */
     size_t scratch_bytes;
@@ -140,6 +144,8 @@ typedef struct dg_ctx dg_ctx;
 
 /* Bytes of device scratch a context with these parameters needs. */
 int dg_scratch_bytes(const dg_mesh* mesh, int order, const dg_nu_params* nu, size_t* bytes);
+/* Bytes of the projected-velocity buffer dg_opts.vhat must provide. */
+int dg_vhat_bytes(const dg_mesh* mesh, int order, int precision, size_t* bytes);
 
 /* Create a context.  Builds the basis/quadrature tables (Sec. 2.1-2.2),
  * records the caller's buffers and stream.  No kernel runs before

@@ -73,6 +73,7 @@ def lib() -> C.CDLL:
         L = C.CDLL(LIB_PATH)
         vp, i, d = C.c_void_p, C.c_int, C.c_double
         L.dg_scratch_bytes.argtypes = [C.POINTER(Mesh), i, C.POINTER(NuParams), C.POINTER(C.c_size_t)]
+        L.dg_vhat_bytes.argtypes = [C.POINTER(Mesh), i, i, C.POINTER(C.c_size_t)]
         L.dg_init.argtypes = [C.POINTER(vp), C.POINTER(Mesh), i, d, C.POINTER(NuParams), C.POINTER(Opts)]
         L.dg_free.argtypes = [vp]
         L.dg_free.restype = None
@@ -97,7 +98,7 @@ def lib() -> C.CDLL:
 
 
 # every symbol include/dg.h declares
-EXPORTS = ("dg_scratch_bytes", "dg_init", "dg_free", "dg_last_error", "dg_set_state", "dg_get_state", "dg_rhs",
+EXPORTS = ("dg_scratch_bytes", "dg_vhat_bytes", "dg_init", "dg_free", "dg_last_error", "dg_set_state", "dg_get_state", "dg_rhs",
            "dg_project_velocity", "dg_step", "dg_set_forcing", "dg_set_forcing_coeffs", "dg_forcing_from_modes",
            "dg_diagnostics", "dg_l1_density", "dg_get_meta", "dg_set_meta", "dg_profile", "dg_profile_read")
 

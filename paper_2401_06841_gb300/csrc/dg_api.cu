@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -17,6 +18,7 @@
 
 #include "../../include/dg.h"
 #include "dg_launch.cuh"
+#include "dg_tile.cuh"
 
 using namespace dg;
 
@@ -156,6 +158,160 @@ std::vector<double> tables_for(int K)
     return build_tables<3>();
 }
 
+// split of x into bfloat16 hi + lo, each rounded to nearest even
+uint16_t bf16_rne(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+float bf16_to_float(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+
+// dense B[K][N] (row-major, zero padded) -> mma.sync m16n8k16 B fragments:
+// words [K/16][N/8][lane][hi(k=2t,2t+1) hi(k=2t+8,2t+9) lo(...) lo(...)], n = g
+void to_fragments(const std::vector<double>& B, int Kd, int Nd, uint32_t* out)
+{
+    for (int kt = 0; kt < Kd / 16; ++kt)
+        for (int nt = 0; nt < Nd / 8; ++nt)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3, n = nt * 8 + g;
+                uint32_t w[4];
+                for (int half = 0; half < 2; ++half) {
+                    const int k0 = kt * 16 + 2 * t + 8 * half;
+                    uint16_t hi[2], lo[2];
+                    for (int j = 0; j < 2; ++j) {
+                        const float x = (float)B[(size_t)(k0 + j) * Nd + n];
+                        hi[j] = bf16_rne(x);
+                        lo[j] = bf16_rne(x - bf16_to_float(hi[j]));
+                    }
+                    w[half] = (uint32_t)hi[0] | ((uint32_t)hi[1] << 16);
+                    w[2 + half] = (uint32_t)lo[0] | ((uint32_t)lo[1] << 16);
+                }
+                for (int j = 0; j < 4; ++j) out[(((size_t)kt * (Nd / 8) + nt) * 32 + lane) * 4 + j] = w[j];
+            }
+}
+
+// tables of the tile kernels (TileTab<K, BK>): the basis at the volume points
+// (zero padded), its weighted transpose, the 2D face basis and its weighted
+// transpose -- dense for the CUDA-core products, fragment-ordered split-BF16
+// for the tensor-core products -- then the dense basis at the volume and
+// face points for the exact positivity check.  Returned as raw 32/64-bit
+// words of the element type (float bits for BK_X3 fragments).
+template <int K, int BK>
+std::vector<double> build_tile_tables_dense(std::vector<double>& phi_d, std::vector<double>& wphi_d,
+                                            std::vector<double>& psi_d, std::vector<double>& psil_d)
+{
+    using Cf = TileCfg<K, BK>;
+    using TT = TileTab<K, BK>;
+    constexpr int b = Cf::b, n = Cf::n, nq = Cf::nq, ns = Cf::ns, nf = Cf::nf;
+    constexpr int KP = Cf::KP, NQP = Cf::NQP, NP = Cf::NP, B2 = Cf::B2, B2K = Cf::B2K, NSP = Cf::NSP, B2N = Cf::B2N;
+    constexpr Modes<K> M{};
+    constexpr Modes2<K> M2{};
+    std::vector<double> t(TT::total, 0.0);
+    phi_d.assign((size_t)KP * NQP, 0.0);
+    wphi_d.assign((size_t)NQP * NP, 0.0);
+    psi_d.assign((size_t)B2K * NSP, 0.0);
+    psil_d.assign((size_t)NSP * B2N, 0.0);
+    long double xg[16], wg[16];
+    gauss_rule(n, xg, wg);
+    auto phi = [&](int l, long double a, long double bb, long double c) {
+        return pnorm(M.i[l], a) * pnorm(M.j[l], bb) * pnorm(M.l[l], c);
+    };
+    for (int q = 0; q < nq; ++q) {
+        const int ia = q % n, ib = (q / n) % n, ic = q / (n * n);
+        const long double wq = wg[ia] * wg[ib] * wg[ic] / 8.0L;
+        for (int l = 0; l < b; ++l) {
+            const long double p = phi(l, xg[ia], xg[ib], xg[ic]);
+            phi_d[(size_t)l * NQP + q] = (double)p;
+            wphi_d[(size_t)q * NP + l] = (double)(wq * p);
+            t[TT::phiv + l * nq + q] = (double)p;
+        }
+    }
+    for (int s = 0; s < ns; ++s) {
+        const int a = s % n, c = s / n;
+        const long double ws = wg[a] * wg[c];
+        for (int p2 = 0; p2 < B2; ++p2) {
+            const long double ps = pnorm(M2.p[p2], xg[a]) * pnorm(M2.q[p2], xg[c]);
+            psi_d[(size_t)p2 * NSP + s] = (double)ps;
+            psil_d[(size_t)s * B2N + p2] = (double)(ws * ps);
+        }
+    }
+    for (int f = 0; f < 6; ++f) {
+        const int d = f >> 1;
+        const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        for (int s = 0; s < ns; ++s) {
+            long double xi[3];
+            xi[d] = (f & 1) ? 1.0L : -1.0L;
+            xi[t1] = xg[s % n];
+            xi[t2] = xg[s / n];
+            for (int l = 0; l < b; ++l) t[TT::phif + l * nf + f * ns + s] = (double)phi(l, xi[0], xi[1], xi[2]);
+        }
+    }
+    if (BK == BK_FMA) {
+        std::copy(phi_d.begin(), phi_d.end(), t.begin() + Cf::oPhi);
+        std::copy(wphi_d.begin(), wphi_d.end(), t.begin() + Cf::oWPhi);
+        std::copy(psi_d.begin(), psi_d.end(), t.begin() + Cf::oPsi);
+        std::copy(psil_d.begin(), psil_d.end(), t.begin() + Cf::oPsiL);
+    }
+    return t;
+}
+
+// tile tables in the element type: FP64, FP32, or FP32 with X3 fragments
+template <int K>
+std::vector<char> tile_tables_bytes(int prec)
+{
+    std::vector<double> ph, wp, ps, pl;
+    if (prec == DG_PREC_F64) {
+        std::vector<double> t = build_tile_tables_dense<K, BK_FMA>(ph, wp, ps, pl);
+        std::vector<char> out(t.size() * sizeof(double));
+        std::memcpy(out.data(), t.data(), out.size());
+        return out;
+    }
+    if (prec == DG_PREC_F32) {
+        std::vector<double> t = build_tile_tables_dense<K, BK_FMA>(ph, wp, ps, pl);
+        std::vector<float> f(t.begin(), t.end());
+        std::vector<char> out(f.size() * sizeof(float));
+        std::memcpy(out.data(), f.data(), out.size());
+        return out;
+    }
+    using Cf = TileCfg<K, BK_X3>;
+    std::vector<double> t = build_tile_tables_dense<K, BK_X3>(ph, wp, ps, pl);
+    std::vector<float> f(t.begin(), t.end());
+    std::vector<uint32_t> w(f.size());
+    std::memcpy(w.data(), f.data(), f.size() * sizeof(float));
+    to_fragments(ph, Cf::KP, Cf::NQP, w.data() + Cf::oPhi);
+    to_fragments(wp, Cf::NQP, Cf::NP, w.data() + Cf::oWPhi);
+    to_fragments(ps, Cf::B2K, Cf::NSP, w.data() + Cf::oPsi);
+    to_fragments(pl, Cf::NSP, Cf::B2N, w.data() + Cf::oPsiL);
+    std::vector<char> out(w.size() * sizeof(uint32_t));
+    std::memcpy(out.data(), w.data(), out.size());
+    return out;
+}
+
+std::vector<char> tile_tables_for(int K, int prec)
+{
+    if (K == 1) return tile_tables_bytes<1>(prec);
+    if (K == 2) return tile_tables_bytes<2>(prec);
+    return tile_tables_bytes<3>(prec);
+}
+
+int ttab_total(int K)
+{
+    // words of the larger of the two backends' layouts
+    auto mx = [](int a, int b) { return a > b ? a : b; };
+    if (K == 1) return mx(TileTab<1, BK_FMA>::total, TileTab<1, BK_X3>::total);
+    if (K == 2) return mx(TileTab<2, BK_FMA>::total, TileTab<2, BK_X3>::total);
+    return mx(TileTab<3, BK_FMA>::total, TileTab<3, BK_X3>::total);
+}
+
 int tab_total(int K)
 {
     if (K == 1) return TabLayout<1>::total;
@@ -289,6 +445,7 @@ struct dg_ctx {
     Ctl* ctl = nullptr;
     double* partials = nullptr;
     void* tab = nullptr;
+    void* ttab = nullptr;
     int* d_kvec = nullptr;
     double* d_amp = nullptr;
     int nsm = 0;
@@ -321,7 +478,7 @@ struct dg_ctx {
 namespace {
 
 struct ScratchLayout {
-    size_t ctl, partials, tab, kvec, amp, total;
+    size_t ctl, partials, tab, ttab, kvec, amp, total;
 };
 
 ScratchLayout scratch_layout(int K)
@@ -334,6 +491,8 @@ ScratchLayout scratch_layout(int K)
     off = align256(off + sizeof(double) * 16 * kMaxGrid);
     s.tab = off;
     off = align256(off + sizeof(double) * tab_total(K));
+    s.ttab = off;
+    off = align256(off + sizeof(double) * ttab_total(K));
     s.kvec = off;
     off = align256(off + sizeof(int) * 3 * kMaxModes);
     s.amp = off;
@@ -371,15 +530,19 @@ Launch make_launch(const dg_ctx* c)
     L.ph.floor_ = c->nu.rho_floor;
     L.ph.av_mode = c->nu.mode;
     L.tab = c->tab;
+    L.ttab = c->ttab;
     L.ctl = c->ctl;
     L.partials = c->partials;
     L.nsm = c->nsm;
+    L.bk = (c->prec == DG_PREC_X3) ? 1 : 0;
     return L;
 }
 
 size_t elem(const dg_ctx* c) { return c->prec == DG_PREC_F64 ? sizeof(double) : sizeof(float); }
 size_t state_bytes(const dg_ctx* c) { return elem(c) * (size_t)c->ncell * 4 * c->b; }
 size_t vec_bytes(const dg_ctx* c) { return elem(c) * (size_t)c->ncell * 3 * c->b; }
+// the second projected-velocity buffer starts 256-byte aligned
+void* vh_buf(const dg_ctx* c, int i) { return (char*)c->vhat + (size_t)i * align256(vec_bytes(c)); }
 
 enum { KIND_PROJECT = 0, KIND_RHS = 1, KIND_FORCE = 2, KIND_OTHER = 3 };
 
@@ -422,27 +585,24 @@ struct Timed {
     }
 };
 
-cudaError_t project(dg_ctx* c, const void* u, void* vhat, bool with_force, bool dt_flag)
+cudaError_t tile(dg_ctx* c, const TileLaunch& t)
 {
-    Timed tm(c, KIND_PROJECT);
+    Timed tm(c, t.mode == 0 ? KIND_PROJECT : KIND_RHS);
     Launch L = make_launch(c);
-    int flags = (with_force ? F_FORCE : 0) | (dt_flag ? F_DT : 0);
-    if (c->prec == DG_PREC_F64)
-        return launch_project<double>(L, (const double*)u, (double*)vhat, (const double*)c->ahat, flags);
-    return launch_project<float>(L, (const float*)u, (float*)vhat, (const float*)c->ahat, flags);
+    return (c->prec == DG_PREC_F64) ? launch_tile<double>(L, t) : launch_tile<float>(L, t);
 }
 
-cudaError_t rhs_stage(dg_ctx* c, const void* u_in, const void* u_n, void* out, const void* ahat, double ra, double rb,
-                      bool update, double dt_pimax, bool with_force)
+// projection of u into vhat (+ forcing sums into abar slot, + CFL dt)
+cudaError_t project(dg_ctx* c, const void* u, void* vhat, const void* ahat, bool dt_flag, int abar_out)
 {
-    Timed tm(c, KIND_RHS);
-    Launch L = make_launch(c);
-    int flags = with_force ? F_FORCE : 0;
-    if (c->prec == DG_PREC_F64)
-        return launch_rhs<double>(L, (const double*)u_in, (const double*)u_n, (double*)out, (double*)c->vhat,
-                                  (const double*)ahat, ra, rb, update, dt_pimax, flags);
-    return launch_rhs<float>(L, (const float*)u_in, (const float*)u_n, (float*)out, (float*)c->vhat,
-                             (const float*)ahat, (float)ra, (float)rb, update, dt_pimax, flags);
+    TileLaunch t{};
+    t.mode = 0;
+    t.u_in = u;
+    t.vh_out = vhat;
+    t.ahat = ahat;
+    t.flags = (ahat ? F_FORCE : 0) | (dt_flag ? F_DT : 0);
+    t.abar_out = abar_out;
+    return tile(c, t);
 }
 
 int upload_forcing(dg_ctx* ctx)
@@ -484,6 +644,16 @@ int dg_scratch_bytes(const dg_mesh* mesh, int order, const dg_nu_params* nu, siz
     return DG_OK;
 }
 
+int dg_vhat_bytes(const dg_mesh* mesh, int order, int precision, size_t* bytes)
+{
+    if (!mesh || !bytes || order < 1 || order > 3 || precision < 0 || precision > 2) return DG_EINVAL;
+    const size_t n = (size_t)mesh->n[0] * mesh->n[1] * mesh->n[2];
+    const size_t b = (size_t)(order + 1) * (order + 2) * (order + 3) / 6;
+    const size_t v = n * 3 * b * (precision == DG_PREC_F64 ? sizeof(double) : sizeof(float));
+    *bytes = align256(v) + v;
+    return DG_OK;
+}
+
 int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu_params* nu, const dg_opts* opts)
 {
     if (!out) return DG_EINVAL;
@@ -496,7 +666,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
         if (mesh->L[d] != 1.0) return DG_EINVAL;
     if (!(cs > 0.0)) return DG_EINVAL;
     if (nu->mode < 0 || nu->mode > 2 || !(nu->rho_floor >= 0.0)) return DG_EINVAL;
-    if (opts->precision < 0 || opts->precision > 1) return DG_EINVAL;  // X3 transforms: see dg_x3.cu
+    if (opts->precision < 0 || opts->precision > 2) return DG_EINVAL;
     if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
     if (!(opts->cfl > 0.0)) return DG_EINVAL;
     if (!opts->stream) return DG_EINVAL;
@@ -528,6 +698,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->ctl = (Ctl*)(ctx->scratch + sl.ctl);
     ctx->partials = (double*)(ctx->scratch + sl.partials);
     ctx->tab = ctx->scratch + sl.tab;
+    ctx->ttab = ctx->scratch + sl.ttab;
     ctx->d_kvec = (int*)(ctx->scratch + sl.kvec);
     ctx->d_amp = (double*)(ctx->scratch + sl.amp);
 
@@ -542,6 +713,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     }
     // tables in the element type of the precision mode
     std::vector<double> t = tables_for(order);
+    std::vector<char> tt = tile_tables_for(order, ctx->prec);
     Ctl c0{};
     c0.dt_scale = 1.0;
     c0.dt_num = ctx->cfl * ctx->h / (order + 1);
@@ -552,8 +724,9 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
         } else {
             std::vector<float> tf(t.begin(), t.end());
             e = cudaMemcpyAsync(ctx->tab, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice, ctx->st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
         }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ttab, tt.data(), tt.size(), cudaMemcpyHostToDevice, ctx->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ahat, 0, vec_bytes(ctx), ctx->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
@@ -600,7 +773,7 @@ int dg_project_velocity(dg_ctx* ctx, const void* u_in, void* vhat_out)
 {
     if (!ctx) return DG_EINVAL;
     if (!u_in || !vhat_out) return fail(ctx, DG_EINVAL, "dg_project_velocity: null buffer");
-    CK(project(ctx, u_in, vhat_out, false, false));
+    CK(project(ctx, u_in, vhat_out, nullptr, false, 0));
     CK(cudaStreamSynchronize(ctx->st));
     return DG_OK;
 }
@@ -609,12 +782,17 @@ int dg_rhs(dg_ctx* ctx, const void* u_in, const void* ahat, void* dudt, double d
 {
     if (!ctx) return DG_EINVAL;
     if (!u_in || !dudt) return fail(ctx, DG_EINVAL, "dg_rhs: null buffer");
-    const void* saved = ctx->ahat;
-    ctx->ahat = const_cast<void*>(ahat);
-    cudaError_t e = project(ctx, u_in, ctx->vhat, ahat != nullptr, false);
-    ctx->ahat = const_cast<void*>(saved);
-    CK(e);
-    CK(rhs_stage(ctx, u_in, nullptr, dudt, ahat, 0.0, 1.0, false, dt_for_pimax, ahat != nullptr));
+    CK(project(ctx, u_in, vh_buf(ctx, 0), ahat, false, 0));
+    TileLaunch t{};
+    t.mode = 1;
+    t.u_in = u_in;
+    t.out = dudt;
+    t.vh_in = vh_buf(ctx, 0);
+    t.ahat = ahat;
+    t.dt_pimax = dt_for_pimax;
+    t.flags = ahat ? F_FORCE : 0;
+    t.abar_in = 0;
+    CK(tile(ctx, t));
     CK(cudaStreamSynchronize(ctx->st));
     return DG_OK;
 }
@@ -723,10 +901,24 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
             CK(cudaMemcpyAsync(&ctx->ctl->dt_scale, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->st));
             unsigned int zero = 0u;
             CK(cudaMemcpyAsync(&ctx->ctl->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->st));
+            // stage 1 projection (+ CFL dt); later stages get theirs from the
+            // previous stage's epilogue (double-buffered vhat / abar slots)
+            CK(project(ctx, ctx->reg[A], vh_buf(ctx, 0), force ? ctx->ahat : nullptr, true, 0));
             for (int s = 0; s < ctx->rk; ++s) {
-                CK(project(ctx, ctx->reg[in[s]], ctx->vhat, force, s == 0));
-                CK(rhs_stage(ctx, ctx->reg[in[s]], ctx->reg[A], ctx->reg[out[s]], ctx->ahat, RA[s], RB[s], true, 0.0,
-                             force));
+                TileLaunch t{};
+                t.mode = 2;
+                t.u_in = ctx->reg[in[s]];
+                t.u_n = ctx->reg[A];
+                t.out = ctx->reg[out[s]];
+                t.vh_in = vh_buf(ctx, s & 1);
+                t.vh_out = vh_buf(ctx, (s + 1) & 1);
+                t.ahat = force ? ctx->ahat : nullptr;
+                t.rk_a = RA[s];
+                t.rk_b = RB[s];
+                t.flags = (force ? F_FORCE : 0) | (s + 1 < ctx->rk ? F_NEXTPROJ : 0);
+                t.abar_in = s & 1;
+                t.abar_out = (s + 1) & 1;
+                CK(tile(ctx, t));
             }
             struct {
                 unsigned int status;
@@ -762,7 +954,7 @@ int dg_diagnostics(dg_ctx* ctx, double dt_for_pimax, dg_diag* out)
     const void* u = ctx->reg[ctx->cur];
     const bool force = ctx->forcing_active;
     // abar of the current state first (into the control block), then the reductions
-    CK(project(ctx, u, ctx->vhat, force, false));
+    CK(project(ctx, u, vh_buf(ctx, 0), force ? ctx->ahat : nullptr, false, 0));
     Launch L = make_launch(ctx);
     int flags = force ? F_FORCE : 0;
     Timed tm(ctx, KIND_OTHER);

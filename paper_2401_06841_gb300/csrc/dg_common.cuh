@@ -117,8 +117,7 @@ struct Ctl {
     double dt;               // dt of the current step (fixes Pi_max)
     double dt_scale;         // 1, 1/2, 1/4, 1/8 on retries
     double fixed_dt;         // > 0 replaces the CFL dt
-    double abar[3];          // <rho a_h>/<rho>
-    double rho_sum;          // <rho>
+    double abar2[2][3];      // <rho a_h>/<rho>, one slot per projected-velocity buffer
     double dt_num;           // cfl h / (k+1)
     double diag[16];         // diagnostics result
     double l1;               // L1 result

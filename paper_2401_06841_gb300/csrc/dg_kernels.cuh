@@ -1,5 +1,6 @@
-// dg_kernels.cuh -- CUDA-core kernels of libdg (FP64 and FP32), templated on
-// the element type T and the degree K.
+// dg_kernels.cuh -- auxiliary CUDA-core kernels of libdg (FP64 and FP32):
+// forcing projection, diagnostics, L1 norm; templated on the element type T
+// and the degree K.  The hot-path kernels are in dg_tile.cuh.
 //
 // All kernels walk tiles of TC consecutive cells with a grid sized to the
 // resident capacity of the GPU (grid-stride over tiles), stage the tile's
@@ -88,458 +89,6 @@ __device__ bool last_block_reduce(double* partials, const double* mine, int nv, 
     }
     if (threadIdx.x == 0) *counter = 0u;
     return true;
-}
-
-// ---------------------------------------------------------------------------
-// K_A: primitive projection (Sec. 3.2, eq. weights_equation), the FP64 sums
-// <rho a_h>, <rho> of the momentum-neutral forcing, and at the first stage of
-// a step the CFL maximum and dt (Sec. 7: dt ~ h/(k+1)).
-// ---------------------------------------------------------------------------
-template <typename T, int K>
-__global__ void __launch_bounds__(Tile<K>::NT) k_project(KArgs<T> a)
-{
-    using D = Dims<K>;
-    using L = TabLayout<K>;
-    constexpr int b = D::b, nq = D::nq, TC = Tile<K>::TC, NT = Tile<K>::NT;
-    __shared__ T s_u[TC][4][b];
-    __shared__ T s_v[TC][nq][3];
-    __shared__ double s_buf[NT];
-    __shared__ double s_tot[8];
-    __shared__ unsigned long long s_smax;
-    const int tid = threadIdx.x;
-    const long ntile = (a.ncell + TC - 1) / TC;
-    const T* phiT = a.tab + L::phiT;
-    const T* wphi = a.tab + L::wphi;
-    double sums[4] = {0.0, 0.0, 0.0, 0.0};  // sum rho_l a_il (3), sum rho_0
-    if (tid == 0) s_smax = 0ull;
-    __syncthreads();
-    double smax = 0.0;
-    for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const long c0 = tile * TC;
-        for (int e = tid; e < TC * 4 * b; e += NT) {
-            long c = c0 + e / (4 * b);
-            (&s_u[0][0][0])[e] = (c < a.ncell) ? a.u_in[c0 * 4 * b + e] : ((e % (4 * b)) == 0 ? T(1) : T(0));
-        }
-        __syncthreads();
-        {
-            const int lc = tid / nq, q = tid % nq;
-            T r = 0, m0 = 0, m1 = 0, m2 = 0;
-#pragma unroll
-            for (int l = 0; l < b; ++l) {
-                T p = __ldg(phiT + l * nq + q);
-                r += s_u[lc][0][l] * p;
-                m0 += s_u[lc][1][l] * p;
-                m1 += s_u[lc][2][l] * p;
-                m2 += s_u[lc][3][l] * p;
-            }
-            T ir = T(1) / r;
-            T v0 = m0 * ir, v1 = m1 * ir, v2 = m2 * ir;
-            s_v[lc][q][0] = v0;
-            s_v[lc][q][1] = v1;
-            s_v[lc][q][2] = v2;
-            if ((a.flags & F_DT) && c0 + lc < a.ncell) {
-                double s = fabs((double)v0) + fabs((double)v1) + fabs((double)v2) + 3.0 * a.ph.cs;
-                smax = s > smax ? s : smax;
-            }
-        }
-        __syncthreads();
-        for (int e = tid; e < TC * b; e += NT) {
-            const int lc = e / b, l = e % b;
-            T v0 = 0, v1 = 0, v2 = 0;
-#pragma unroll 8
-            for (int q = 0; q < nq; ++q) {
-                T w = __ldg(wphi + q * b + l);
-                v0 += w * s_v[lc][q][0];
-                v1 += w * s_v[lc][q][1];
-                v2 += w * s_v[lc][q][2];
-            }
-            const long c = c0 + lc;
-            if (c < a.ncell) {
-                a.vhat[c * 3 * b + l] = v0;
-                a.vhat[c * 3 * b + b + l] = v1;
-                a.vhat[c * 3 * b + 2 * b + l] = v2;
-            }
-        }
-        if ((a.flags & F_FORCE) && tid < TC && c0 + tid < a.ncell) {
-            const long c = c0 + tid;
-            const T* ac = a.ahat + c * 3 * b;
-            for (int i = 0; i < 3; ++i) {
-                double s = 0.0;
-                for (int l = 0; l < b; ++l) s += (double)s_u[tid][0][l] * (double)ac[i * b + l];
-                sums[i] += s;
-            }
-            sums[3] += (double)s_u[tid][0][0];
-        }
-        __syncthreads();
-    }
-    // block reductions: max speed (atomic on the bit pattern; positive doubles
-    // order like unsigned integers) and the forcing sums (fixed order)
-    if (a.flags & F_DT) {
-        atomicMax(&s_smax, (unsigned long long)__double_as_longlong(smax));
-        __syncthreads();
-        if (tid == 0) atomicMax(&a.ctl->smax, s_smax);
-    }
-    double mine[4];
-    for (int i = 0; i < 4; ++i) {
-        s_buf[tid] = sums[i];
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int j = 0; j < NT; ++j) t += s_buf[j];
-            mine[i] = t;
-        }
-        __syncthreads();
-    }
-    if (last_block_reduce<NT>(a.partials, mine, 4, &a.ctl->cnt_proj, s_tot, s_buf)) {
-        if (tid == 0) {
-            if (a.flags & F_FORCE) {
-                for (int i = 0; i < 3; ++i) a.ctl->abar[i] = s_tot[i] / s_tot[3];
-                a.ctl->rho_sum = s_tot[3];
-            } else {
-                a.ctl->abar[0] = a.ctl->abar[1] = a.ctl->abar[2] = 0.0;
-            }
-            if (a.flags & F_DT) {
-                unsigned long long bits = atomicAdd(&a.ctl->smax, 0ull);
-                double sm = __longlong_as_double((long long)bits);
-                double dt = a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / sm;
-                a.ctl->dt = dt * a.ctl->dt_scale;
-                a.ctl->smax = 0ull;
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K_B: right-hand side (Sec. 2.2, eq. weight_evolution) with vNR viscous
-// pressure at the volume points (Sec. 3.1), projected-velocity face states
-// (Sec. 3.2), Rusanov fluxes, forcing source; with UPDATE the SSP-RK stage
-// combine (Sec. 7) and the positivity rescaling (Sec. 3.1) are fused in.
-// ---------------------------------------------------------------------------
-template <typename T, int K>
-struct RhsSmem {
-    using D = Dims<K>;
-    static constexpr int TC = Tile<K>::TC, b = D::b, EC = 12;
-    static constexpr int PT = (D::nq * EC > D::nf * 4) ? D::nq * EC : D::nf * 4;
-    static constexpr int u = 0;                      // [TC][4][b]
-    static constexpr int ec = u + TC * 4 * b;        // [TC][b][EC]
-    static constexpr int vh = ec + TC * b * EC;      // [TC][3][b]
-    static constexpr int nb = vh + TC * 3 * b;       // [TC][6][4][b]
-    static constexpr int pt = nb + TC * 24 * b;      // [TC][PT]
-    static constexpr int P = pt + TC * PT;           // [TC][9][b]
-    static constexpr int R = P + TC * 9 * b;         // [TC][4][b]
-    static constexpr int nw = R + TC * 4 * b;        // [TC][4][b]
-    static constexpr int total = nw + TC * 4 * b;
-    static constexpr size_t bytes = sizeof(T) * total;
-};
-
-template <typename T>
-__device__ __forceinline__ void atomic_min_key(void* p, T v);
-template <>
-__device__ __forceinline__ void atomic_min_key<float>(void* p, float v)
-{
-    atomicMin((int*)p, float_key(v));
-}
-template <>
-__device__ __forceinline__ void atomic_min_key<double>(void* p, double v)
-{
-    atomicMin((long long*)p, double_key(v));
-}
-
-template <typename T, int K, bool UPDATE>
-__global__ void __launch_bounds__(Tile<K>::NT) k_rhs(KArgs<T> a)
-{
-    using D = Dims<K>;
-    using L = TabLayout<K>;
-    using S = RhsSmem<T, K>;
-    constexpr int b = D::b, nq = D::nq, ns = D::ns, nf = D::nf, TC = Tile<K>::TC, NT = Tile<K>::NT;
-    constexpr int EC = S::EC;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
-    T* s_u = sm + S::u;
-    T* s_ec = sm + S::ec;
-    T* s_vh = sm + S::vh;
-    T* s_nb = sm + S::nb;
-    T* s_pt = sm + S::pt;
-    T* s_P = sm + S::P;
-    T* s_R = sm + S::R;
-    T* s_nw = sm + S::nw;
-    __shared__ int s_minf[TC];
-    __shared__ long long s_mind[TC];
-    __shared__ unsigned int s_status;
-
-    const int tid = threadIdx.x;
-    const long ntile = (a.ncell + TC - 1) / TC;
-    const T* phiT = a.tab + L::phiT;
-    const T* wphi = a.tab + L::wphi;
-    const T* phifT = a.tab + L::phifT;
-    const T* lift = a.tab + L::lift;
-    const bool force = (a.flags & F_FORCE) != 0;
-    const T two_h = T(2.0 / a.ph.h);
-    const T inv4h = T(0.25 / a.ph.h);
-    const double dtd = UPDATE ? a.ctl->dt : a.dt_pimax;
-    const T dt = T(dtd);
-    const T abar0 = force ? T(a.ctl->abar[0]) : T(0);
-    const T abar1 = force ? T(a.ctl->abar[1]) : T(0);
-    const T abar2 = force ? T(a.ctl->abar[2]) : T(0);
-    const T cs = T(a.ph.cs), cs2 = T(a.ph.cs2);
-    if (tid == 0) s_status = 0u;
-
-    for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const long c0 = tile * TC;
-        // ---- 1. stage the tile, its forcing and its face neighbours ----
-        for (int e = tid; e < TC * 4 * b; e += NT) {
-            long c = c0 + e / (4 * b);
-            s_u[e] = (c < a.ncell) ? a.u_in[c0 * 4 * b + e] : ((e % (4 * b)) == 0 ? T(1) : T(0));
-        }
-        for (int e = tid; e < TC * 3 * b; e += NT) {
-            const int lc = e / (3 * b), i = (e / b) % 3, l = e % b;
-            const long c = c0 + lc;
-            s_vh[e] = (c < a.ncell) ? a.vhat[c0 * 3 * b + e] : T(0);
-            s_ec[(lc * b + l) * EC + 8 + i] = (force && c < a.ncell) ? a.ahat[c0 * 3 * b + e] : T(0);
-        }
-        for (int e = tid; e < TC * 24 * b; e += NT) {
-            const int lc = e / (24 * b), f = (e / (4 * b)) % 6, v = (e / b) % 4, l = e % b;
-            const long c = c0 + lc;
-            T val = (v == 0 && l == 0) ? T(1) : T(0);
-            if (c < a.ncell) {
-                const long nc = neighbour(c, f, a.N);
-                val = (v == 0) ? a.u_in[nc * 4 * b + l] : a.vhat[nc * 3 * b + (v - 1) * b + l];
-            }
-            s_nb[e] = val;
-        }
-        __syncthreads();
-        // ---- 2. modal gradients: rho_x, rho_y, rho_z, div m ----
-        for (int e = tid; e < TC * 5; e += NT) {
-            const int lc = e / 5, g = e % 5;
-            const T* u = s_u + lc * 4 * b;
-            T out[b];
-            if (g == 0) {
-#pragma unroll
-                for (int l = 0; l < b; ++l)
-                    for (int v = 0; v < 4; ++v) s_ec[(lc * b + l) * EC + v] = u[v * b + l];
-                continue;
-            }
-            if (g == 1) modal_grad<T, K, 0>(u, out, two_h);
-            if (g == 2) modal_grad<T, K, 1>(u, out, two_h);
-            if (g == 3) modal_grad<T, K, 2>(u, out, two_h);
-            if (g == 4) {
-                T t[b];
-                modal_grad<T, K, 0>(u + b, out, two_h);
-                modal_grad<T, K, 1>(u + 2 * b, t, two_h);
-#pragma unroll
-                for (int l = 0; l < b; ++l) out[l] += t[l];
-                modal_grad<T, K, 2>(u + 3 * b, t, two_h);
-#pragma unroll
-                for (int l = 0; l < b; ++l) out[l] += t[l];
-            }
-#pragma unroll
-            for (int l = 0; l < b; ++l) s_ec[(lc * b + l) * EC + 3 + g] = out[l];
-        }
-        __syncthreads();
-        // ---- 3. pointwise volume physics, one thread per (cell, point) ----
-        {
-            const int lc = tid / nq, q = tid % nq;
-            T f[11];
-#pragma unroll
-            for (int i = 0; i < 11; ++i) f[i] = T(0);
-            const T* ec = s_ec + lc * b * EC;
-#pragma unroll
-            for (int l = 0; l < b; ++l) {
-                const T p = __ldg(phiT + l * nq + q);
-#pragma unroll
-                for (int i = 0; i < 11; ++i) f[i] += ec[l * EC + i] * p;
-            }
-            const T rho = f[0], ir = T(1) / rho;
-            const T vx = f[1] * ir, vy = f[2] * ir, vz = f[3] * ir;
-            // div v = (div m - v . grad rho) / rho   (quotient rule)
-            const T divv = (f[7] - (vx * f[4] + vy * f[5] + vz * f[6])) * ir;
-            T Pi = T(0);
-            if (a.ph.av_mode == 1) Pi = vnr_pressure<T>(a.ph, rho, divv, dt);
-            const T P = cs2 * rho + Pi;
-            T* o = s_pt + lc * S::PT + q * EC;
-            o[0] = f[1] * vx + P;
-            o[1] = f[2] * vy + P;
-            o[2] = f[3] * vz + P;
-            o[3] = f[1] * vy;
-            o[4] = f[1] * vz;
-            o[5] = f[2] * vz;
-            o[6] = rho * (f[8] - abar0);
-            o[7] = rho * (f[9] - abar1);
-            o[8] = rho * (f[10] - abar2);
-        }
-        __syncthreads();
-        // ---- 4. projection of the 6 flux-tensor components and the forcing ----
-        for (int e = tid; e < TC * b * 3; e += NT) {
-            const int lc = e / (3 * b), l = (e / 3) % b, g = e % 3;
-            const T* pt = s_pt + lc * S::PT + 3 * g;
-            T p0 = 0, p1 = 0, p2 = 0;
-#pragma unroll 4
-            for (int q = 0; q < nq; ++q) {
-                const T w = __ldg(wphi + q * b + l);
-                p0 += w * pt[q * EC + 0];
-                p1 += w * pt[q * EC + 1];
-                p2 += w * pt[q * EC + 2];
-            }
-            T* P = s_P + lc * 9 * b;
-            P[(3 * g + 0) * b + l] = p0;
-            P[(3 * g + 1) * b + l] = p1;
-            P[(3 * g + 2) * b + l] = p2;
-        }
-        __syncthreads();
-        // ---- 5. face traces and Rusanov fluxes (s_pt reused as [TC][nf][4]) ----
-        for (int e = tid; e < TC * nf; e += NT) {
-            const int lc = e / nf, fs = e % nf, f = fs / ns, s = fs % ns, d = f >> 1;
-            const int fo = (f ^ 1) * ns + s;  // same point on the neighbour's opposite face
-            const T* u = s_u + lc * 4 * b;
-            const T* vh = s_vh + lc * 3 * b;
-            const T* nb = s_nb + (lc * 6 + f) * 4 * b;
-            T Ws[4] = {0, 0, 0, 0}, Wn[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (int l = 0; l < b; ++l) {
-                const T ps = __ldg(phifT + l * nf + fs), pn = __ldg(phifT + l * nf + fo);
-                Ws[0] += u[l] * ps;
-                Wn[0] += nb[l] * pn;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    Ws[1 + i] += vh[i * b + l] * ps;
-                    Wn[1 + i] += nb[(1 + i) * b + l] * pn;
-                }
-            }
-            T F[4];
-            if (f & 1)
-                rusanov_dir<T>(d, cs, cs2, Ws, Wn, F);  // + face: this cell is the left state
-            else
-                rusanov_dir<T>(d, cs, cs2, Wn, Ws, F);  // - face: the neighbour is the left state
-            T* o = s_pt + lc * S::PT + fs * 4;
-            o[0] = F[0];
-            o[1] = F[1];
-            o[2] = F[2];
-            o[3] = F[3];
-        }
-        __syncthreads();
-        // ---- 6. assemble: volume term in modal space, forcing, surface lift ----
-        for (int e = tid; e < TC * 4; e += NT) {
-            const int lc = e / 4, v = e % 4;
-            T r[b];
-#pragma unroll
-            for (int l = 0; l < b; ++l) r[l] = T(0);
-            const T* P = s_P + lc * 9 * b;
-            if (v == 0) {
-                const T* u = s_u + lc * 4 * b;
-                modal_grad_T_acc<T, K, 0>(u + b, r, two_h);
-                modal_grad_T_acc<T, K, 1>(u + 2 * b, r, two_h);
-                modal_grad_T_acc<T, K, 2>(u + 3 * b, r, two_h);
-            } else {
-                const int i = v - 1;
-                // F_d(m_i): diagonal i==d -> comp i; off-diagonal pairs (x,y)=3 (x,z)=4 (y,z)=5
-                const int cx = (i == 0) ? 0 : (i == 1 ? 3 : 4);
-                const int cy = (i == 0) ? 3 : (i == 1 ? 1 : 5);
-                const int cz = (i == 0) ? 4 : (i == 1 ? 5 : 2);
-                modal_grad_T_acc<T, K, 0>(P + cx * b, r, two_h);
-                modal_grad_T_acc<T, K, 1>(P + cy * b, r, two_h);
-                modal_grad_T_acc<T, K, 2>(P + cz * b, r, two_h);
-#pragma unroll
-                for (int l = 0; l < b; ++l) r[l] += P[(6 + i) * b + l];
-            }
-#pragma unroll
-            for (int l = 0; l < b; ++l) s_R[(lc * 4 + v) * b + l] = r[l];
-        }
-        __syncthreads();
-        for (int e = tid; e < TC * b; e += NT) {
-            const int lc = e / b, l = e % b;
-            const T* F = s_pt + lc * S::PT;
-            T r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-#pragma unroll 4
-            for (int fs = 0; fs < nf; ++fs) {
-                const T w = __ldg(lift + fs * b + l);
-                r0 += w * F[fs * 4 + 0];
-                r1 += w * F[fs * 4 + 1];
-                r2 += w * F[fs * 4 + 2];
-                r3 += w * F[fs * 4 + 3];
-            }
-            T* R = s_R + lc * 4 * b;
-            R[0 * b + l] += inv4h * r0;
-            R[1 * b + l] += inv4h * r1;
-            R[2 * b + l] += inv4h * r2;
-            R[3 * b + l] += inv4h * r3;
-        }
-        __syncthreads();
-        // ---- 7. epilogue ----
-        if constexpr (!UPDATE) {
-            for (int e = tid; e < TC * 4 * b; e += NT) {
-                const long c = c0 + e / (4 * b);
-                if (c < a.ncell) a.out[c0 * 4 * b + e] = s_R[e];
-            }
-            __syncthreads();
-        } else {
-            for (int e = tid; e < TC * 4 * b; e += NT) {
-                const long c = c0 + e / (4 * b);
-                T w = T(0);
-                if (c < a.ncell) {
-                    // the first stage has rk_a = 0: u^n is not read
-                    const T un = (a.rk_a != T(0)) ? a.u_n[c0 * 4 * b + e] : T(0);
-                    w = a.rk_a * un + a.rk_b * (s_u[e] + dt * s_R[e]);
-                } else {
-                    w = ((e % (4 * b)) == 0) ? T(1) : T(0);
-                }
-                s_nw[e] = w;
-            }
-            if (tid < TC) {
-                s_minf[tid] = 0x7fffffff;
-                s_mind[tid] = 0x7fffffffffffffffLL;
-            }
-            __syncthreads();
-            // density at every volume and face Gauss point of the new state
-            for (int e = tid; e < TC * (nq + nf); e += NT) {
-                const int lc = e / (nq + nf), p = e % (nq + nf);
-                const T* r = s_nw + lc * 4 * b;
-                T rho = 0;
-                if (p < nq) {
-#pragma unroll
-                    for (int l = 0; l < b; ++l) rho += r[l] * __ldg(phiT + l * nq + p);
-                } else {
-#pragma unroll
-                    for (int l = 0; l < b; ++l) rho += r[l] * __ldg(phifT + l * nf + (p - nq));
-                }
-                if constexpr (sizeof(T) == 4)
-                    atomicMin(&s_minf[lc], float_key((float)rho));
-                else
-                    atomicMin(&s_mind[lc], double_key((double)rho));
-            }
-            __syncthreads();
-            unsigned int st = 0u;
-            for (int e = tid; e < TC * 4 * b; e += NT) {
-                const int lc = e / (4 * b), l = e % b;
-                const long c = c0 + lc;
-                if (c >= a.ncell) continue;
-                T rmin;
-                if constexpr (sizeof(T) == 4)
-                    rmin = (T)key_float(s_minf[lc]);
-                else
-                    rmin = (T)key_double(s_mind[lc]);
-                const T rbar = s_nw[lc * 4 * b];
-                const T eps = T(a.ph.floor_);
-                T w = s_nw[e];
-                if (rmin < eps) {
-                    if (rbar > eps) {
-                        const T theta = (rbar - eps) / (rbar - rmin);
-                        if (l > 0) w *= theta;
-                        st |= DG_ST_LIMITED_;
-                    } else {
-                        st |= DG_ST_FAIL_;
-                    }
-                }
-                if (!isfinite((double)w)) st |= DG_ST_NONFINITE_;
-                a.out[c0 * 4 * b + e] = w;
-            }
-            if (st) atomicOr(&s_status, st);
-            __syncthreads();
-        }
-    }
-    if constexpr (UPDATE) {
-        __syncthreads();
-        if (tid == 0 && s_status) atomicOr(&a.ctl->status, s_status);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -717,8 +266,8 @@ __global__ void __launch_bounds__(Tile<K>::NT) k_diag(KArgs<T> a)
                 acc[5] += w * v2;
                 if (Pi > 0.01 * a.ph.cs2 * rho) acc[9] += w;
                 if (force)
-                    acc[10] += w * (mxv * ((double)f[8] - a.ctl->abar[0]) + myv * ((double)f[9] - a.ctl->abar[1]) +
-                                    mzv * ((double)f[10] - a.ctl->abar[2]));
+                    acc[10] += w * (mxv * ((double)f[8] - a.ctl->abar2[0][0]) + myv * ((double)f[9] - a.ctl->abar2[0][1]) +
+                                    mzv * ((double)f[10] - a.ctl->abar2[0][2]));
                 acc[12] += w * Pi * divv;
                 mn = rho < mn ? rho : mn;
                 mx = rho > mx ? rho : mx;

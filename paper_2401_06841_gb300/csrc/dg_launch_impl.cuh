@@ -3,41 +3,50 @@
 #pragma once
 
 #include "dg_kernels.cuh"
+#include "dg_tile.cuh"
 #include "dg_launch.cuh"
 
 namespace dg {
 
 template <typename T, int K>
 struct Occ {
-    static int project, rhs_u, rhs_r, force, diag;
+    static int tile[2][3], force, diag;
 };
 template <typename T, int K>
-int Occ<T, K>::project = 0;
-template <typename T, int K>
-int Occ<T, K>::rhs_u = 0;
-template <typename T, int K>
-int Occ<T, K>::rhs_r = 0;
+int Occ<T, K>::tile[2][3] = {{0, 0, 0}, {0, 0, 0}};
 template <typename T, int K>
 int Occ<T, K>::force = 0;
 template <typename T, int K>
 int Occ<T, K>::diag = 0;
 
+template <typename T, int K, int MODE, int BK>
+static cudaError_t setup_tile()
+{
+    const size_t sm = sizeof(T) * TileCfg<K, BK>::total;
+    cudaError_t e = cudaFuncSetAttribute(k_tile<T, K, MODE, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::tile[BK][MODE], k_tile<T, K, MODE, BK>,
+                                                         TileCfg<K, BK>::NT, sm);
+}
+
+template <typename T, int K, int BK>
+static cudaError_t setup_modes()
+{
+    cudaError_t e;
+    if ((e = setup_tile<T, K, TM_PROJECT, BK>()) != cudaSuccess) return e;
+    if ((e = setup_tile<T, K, TM_RHS, BK>()) != cudaSuccess) return e;
+    return setup_tile<T, K, TM_STAGE, BK>();
+}
+
 template <typename T, int K>
 static cudaError_t setup_k()
 {
-    using S = RhsSmem<T, K>;
     constexpr int NT = Tile<K>::NT;
     cudaError_t e;
-    e = cudaFuncSetAttribute(k_rhs<T, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_rhs<T, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::rhs_u, k_rhs<T, K, true>, NT, S::bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::rhs_r, k_rhs<T, K, false>, NT, S::bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::project, k_project<T, K>, NT, 0);
-    if (e != cudaSuccess) return e;
+    if ((e = setup_modes<T, K, BK_FMA>()) != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4) {
+        if ((e = setup_modes<T, K, BK_X3>()) != cudaSuccess) return e;
+    }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::force, k_force<T, K>, NT, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::diag, k_diag<T, K>, NT, 0);
@@ -75,40 +84,49 @@ static KArgs<T> make_args(const Launch& L)
     return a;
 }
 
-template <typename T, int K>
-static cudaError_t project_k(const Launch& L, const T* u, T* vhat, const T* ahat, int flags)
+template <typename T, int K, int BK>
+static cudaError_t tile_kb(const Launch& L, const TileLaunch& t)
 {
-    KArgs<T> a = make_args<T, K>(L);
-    a.u_in = u;
-    a.vhat = vhat;
-    a.ahat = ahat;
-    a.flags = flags;
-    const long ntile = (L.ncell + Tile<K>::TC - 1) / Tile<K>::TC;
-    k_project<T, K><<<grid_for(ntile, Occ<T, K>::project, L.nsm), Tile<K>::NT, 0, L.st>>>(a);
+    TArgs<T> a{};
+    a.u_in = static_cast<const T*>(t.u_in);
+    a.u_n = static_cast<const T*>(t.u_n);
+    a.out = static_cast<T*>(t.out);
+    a.vh_in = static_cast<const T*>(t.vh_in);
+    a.vh_out = static_cast<T*>(t.vh_out);
+    a.ahat = static_cast<const T*>(t.ahat);
+    a.tab = static_cast<const T*>(L.ttab);
+    a.ctl = L.ctl;
+    a.partials = L.partials;
+    a.ncell = L.ncell;
+    a.N = L.N;
+    a.ph = L.ph;
+    a.rk_a = T(t.rk_a);
+    a.rk_b = T(t.rk_b);
+    a.dt_pimax = t.dt_pimax;
+    a.flags = t.flags;
+    a.abar_in = t.abar_in;
+    a.abar_out = t.abar_out;
+    using Cf = TileCfg<K, BK>;
+    const long ntile = (L.ncell + Cf::TC - 1) / Cf::TC;
+    const size_t sm = sizeof(T) * Cf::total;
+    const int g = grid_for(ntile, Occ<T, K>::tile[BK][t.mode], L.nsm);
+    if (t.mode == TM_PROJECT)
+        k_tile<T, K, TM_PROJECT, BK><<<g, Cf::NT, sm, L.st>>>(a);
+    else if (t.mode == TM_RHS)
+        k_tile<T, K, TM_RHS, BK><<<g, Cf::NT, sm, L.st>>>(a);
+    else
+        k_tile<T, K, TM_STAGE, BK><<<g, Cf::NT, sm, L.st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T, int K>
-static cudaError_t rhs_k(const Launch& L, const T* u_in, const T* u_n, T* out, T* vhat, const T* ahat, T rk_a, T rk_b,
-                         bool update, double dt_pimax, int flags)
+static cudaError_t tile_k(const Launch& L, const TileLaunch& t)
 {
-    KArgs<T> a = make_args<T, K>(L);
-    a.u_in = u_in;
-    a.u_n = u_n;
-    a.out = out;
-    a.vhat = vhat;
-    a.ahat = ahat;
-    a.rk_a = rk_a;
-    a.rk_b = rk_b;
-    a.dt_pimax = dt_pimax;
-    a.flags = flags;
-    const long ntile = (L.ncell + Tile<K>::TC - 1) / Tile<K>::TC;
-    const size_t sm = RhsSmem<T, K>::bytes;
-    if (update)
-        k_rhs<T, K, true><<<grid_for(ntile, Occ<T, K>::rhs_u, L.nsm), Tile<K>::NT, sm, L.st>>>(a);
-    else
-        k_rhs<T, K, false><<<grid_for(ntile, Occ<T, K>::rhs_r, L.nsm), Tile<K>::NT, sm, L.st>>>(a);
-    return cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+        if (L.bk == BK_X3) return tile_kb<T, K, BK_X3>(L, t);
+    }
+    if (L.bk != BK_FMA) return cudaErrorInvalidValue;
+    return tile_kb<T, K, BK_FMA>(L, t);
 }
 
 template <typename T, int K>
@@ -153,15 +171,9 @@ static cudaError_t l1_k(const Launch& L, const T* uA, const T* uB)
     } while (0)
 
 template <typename T>
-cudaError_t launch_project(const Launch& L, const T* u, T* vhat, const T* ahat, int flags)
+cudaError_t launch_tile(const Launch& L, const TileLaunch& t)
 {
-    DG_DISPATCH(project_k, u, vhat, ahat, flags);
-}
-template <typename T>
-cudaError_t launch_rhs(const Launch& L, const T* u_in, const T* u_n, T* out, T* vhat, const T* ahat, T rk_a, T rk_b,
-                       bool update, double dt_pimax, int flags)
-{
-    DG_DISPATCH(rhs_k, u_in, u_n, out, vhat, ahat, rk_a, rk_b, update, dt_pimax, flags);
+    DG_DISPATCH(tile_k, t);
 }
 template <typename T>
 cudaError_t launch_force(const Launch& L, int nm, const int* kvec, const double* amp, int kmaxc, T* ahat)
@@ -181,9 +193,7 @@ cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB)
 
 #define DG_INSTANTIATE(T)                                                                                         \
     template cudaError_t setup_kernels<T>(int);                                                                  \
-    template cudaError_t launch_project<T>(const Launch&, const T*, T*, const T*, int);                          \
-    template cudaError_t launch_rhs<T>(const Launch&, const T*, const T*, T*, T*, const T*, T, T, bool, double,   \
-                                       int);                                                                     \
+    template cudaError_t launch_tile<T>(const Launch&, const TileLaunch&);                                       \
     template cudaError_t launch_force<T>(const Launch&, int, const int*, const double*, int, T*);               \
     template cudaError_t launch_diag<T>(const Launch&, const T*, const T*, double, int);                        \
     template cudaError_t launch_l1<T>(const Launch&, const T*, const T*);

@@ -1,0 +1,904 @@
+// dg_tile.cuh -- tile kernels of libdg: every basis <-> point transform of a
+// tile of TC cells is a block-level matrix product staged in shared memory,
+// with rows = (cell, field) so that one basis table serves the whole tile.
+//
+//   evaluation   V[(c,f)][q]  = sum_l A[(c,f)][l] Phi[l][q]          (Sec. 2.1)
+//   projection   P[(c,g)][l]  = sum_q F[(c,g)][q] WPhi[q][l]         (Sec. 3.2, eq. weights_equation)
+//   face traces  Tr[r][s]     = sum_p C2[r][p] Psi[p][s]             (2D basis on a face)
+//   face lift    L2[r][p]     = sum_s Fs[r][s] PsiL[s][p]
+// with WPhi = (w_q/8) Phi^T and PsiL = w_s Psi^T.  Derivatives are taken in
+// modal space (exact in P_k): grad coefficients (2/h) D_d c and the weak-form
+// volume term (2/h) sum_d D_d^T Fhat_d (Sec. 2.2, eq. weight_evolution).
+// Traces on a face first collapse the normal direction with the known values
+// Pn_m(+-1) = (+-1)^m sqrt(2m+1) and then evaluate a 2D expansion.
+//
+// The matrix products run on the CUDA cores as register-tiled FMA loops
+// (FP64 and FP32 modes).  Shared-memory operands use padded leading
+// dimensions (multiples of 4 elements) and 16-byte vector loads.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "dg_kernels.cuh"
+
+namespace dg {
+
+constexpr int r4(int x) { return (x + 3) / 4 * 4; }
+constexpr int r8(int x) { return (x + 7) / 8 * 8; }
+
+template <int K>
+struct Modes2 {
+    static constexpr int B2 = (K + 1) * (K + 2) / 2;
+    int p[B2], q[B2];
+    constexpr Modes2() : p{}, q{}
+    {
+        int c = 0;
+        for (int d = 0; d <= K; ++d)
+            for (int a = d; a >= 0; --a) {
+                p[c] = a;
+                q[c] = d - a;
+                ++c;
+            }
+    }
+};
+
+template <int K>
+constexpr int idx2(int p, int q)
+{
+    constexpr Modes2<K> M{};
+    for (int i = 0; i < Modes2<K>::B2; ++i)
+        if (M.p[i] == p && M.q[i] == q) return i;
+    return -1;
+}
+// degree along the face normal d, and the 2D mode of the tangential degrees
+// (tangential axes in increasing order)
+template <int K>
+constexpr int normal_deg(int d, int m)
+{
+    constexpr Modes<K> M{};
+    return d == 0 ? M.i[m] : (d == 1 ? M.j[m] : M.l[m]);
+}
+template <int K>
+constexpr int tang_mode(int d, int m)
+{
+    constexpr Modes<K> M{};
+    const int a = (d == 0) ? M.j[m] : M.i[m];
+    const int c = (d == 2) ? M.j[m] : M.l[m];
+    return idx2<K>(a, c);
+}
+// sup of |phi_m| over the reference cell
+template <int K>
+constexpr double sup_phi(int m)
+{
+    constexpr Modes<K> M{};
+    return csqrt((2.0 * M.i[m] + 1.0) * (2.0 * M.j[m] + 1.0) * (2.0 * M.l[m] + 1.0));
+}
+
+constexpr int r16(int x) { return (x + 15) / 16 * 16; }
+
+enum { BK_FMA = 0, BK_X3 = 1 };
+
+// BK_FMA: FP32/FP64 register-tiled FMA products; BK_X3: split-BF16 x3 tensor-
+// core products (mma.sync m16n8k16, FP32 accumulate) -- K dims padded to 16,
+// N dims to 8, row strides chosen for conflict-free fragment loads.
+template <int K, int BK = BK_FMA>
+struct TileCfg {
+    using D = Dims<K>;
+    static constexpr bool X = (BK == BK_X3);
+    static constexpr int b = D::b, n = D::n, nq = D::nq, ns = D::ns, nf = D::nf;
+    static constexpr int TC = (K == 1) ? 32 : 16;  // cells per tile
+    static constexpr int NT = 256;                 // threads per block
+    static constexpr int FE = 12;                  // evaluated fields (11 used)
+    static constexpr int FP = 9;                   // projected components
+    static constexpr int B2 = (K + 1) * (K + 2) / 2;
+    static constexpr int KP = X ? r16(b) : r4(b);     // evaluation: K (modes)
+    static constexpr int NQP = X ? r16(nq) : r8(nq);  // evaluation: N; projection: K (points)
+    static constexpr int NP = X ? r8(b) : r4(b);      // projection: N (modes)
+    static constexpr int B2K = X ? r16(B2) : r4(B2);  // face trace: K (2D modes)
+    static constexpr int NSP = X ? r16(ns) : r4(ns);  // face trace: N; lift: K (face points)
+    static constexpr int B2N = X ? r8(B2) : r4(B2);   // lift: N (2D modes)
+    static constexpr int PADA = X ? 4 : 0, PADV = 4;
+    static constexpr int LDA = KP + PADA;     // evaluation coefficients rows
+    static constexpr int LDV = NQP + PADV;    // point values / point fluxes rows
+    static constexpr int LDP = NP;            // projections rows
+    static constexpr int LDC2 = B2K + PADA;   // collapsed face coefficients rows
+    static constexpr int LDT = NSP + PADV;    // face traces / face fluxes rows
+    static constexpr int LDL = B2N;           // lifted face fluxes rows
+    static constexpr int RE = TC * FE;   // eval rows
+    static constexpr int RP = TC * FP;   // projection rows
+    static constexpr int RC = TC * 16;   // face rows per direction: cell x side x (self,nbr) x (rho,v)
+    static constexpr int RL = TC * 8;    // face flux rows per direction: cell x side x var
+    // B operands in shared memory: FMA -> dense T arrays [K][N]; X3 ->
+    // fragments, K*N uint32 words [K/16][N/8][32 lanes][hi0 hi1 lo0 lo1]
+    static constexpr int szPhi = KP * NQP;
+    static constexpr int szWPhi = NQP * NP;
+    static constexpr int szPsi = B2K * NSP;
+    static constexpr int szPsiL = NSP * B2N;
+    // shared-memory layout in elements of T (X3 tables count as 4-byte words
+    // inside a float region), every offset a multiple of 4
+    static constexpr int oPhi = 0;
+    static constexpr int oWPhi = oPhi + szPhi;
+    static constexpr int oPsi = oWPhi + szWPhi;
+    static constexpr int oPsiL = oPsi + szPsi;
+    static constexpr int smem_tabs = oPsiL + szPsiL;
+    static constexpr int oU = r4(smem_tabs);              // [TC][4][b] state of the tile
+    static constexpr int oVH = oU + r4(TC * 4 * b);       // [TC][3][b] own projected velocity
+    static constexpr int oR = oVH + r4(TC * 3 * b);       // [TC][4][b] right-hand side
+    // evaluation coefficients [RE][LDA]; the projections [RP][LDP] reuse the
+    // region once the evaluation product has consumed the coefficients
+    static constexpr int oA = oR + r4(TC * 4 * b);
+    static constexpr int oP = oA;
+    static constexpr int SZA = (RE * LDA > RP * LDP) ? RE * LDA : RP * LDP;
+    // big region: point values | point fluxes | faces.  Faces: region 1 holds
+    // the collapsed coefficients, later the face fluxes; region 2 the traces,
+    // later the lifted fluxes (each pair has disjoint lifetimes)
+    static constexpr int FA = (RC * LDC2 > RL * LDT) ? RC * LDC2 : RL * LDT;
+    static constexpr int FB = (RC * LDT > RL * LDL) ? RC * LDT : RL * LDL;
+    static constexpr int BIGV = RE * LDV;
+    static constexpr int oBig = oA + SZA;
+    static constexpr int BIG = BIGV > FA + FB ? BIGV : FA + FB;
+    static constexpr int total = oBig + BIG;
+    static constexpr int oC2 = 0, oFs = 0, oTr = FA, oL2 = FA;
+};
+
+// tables in the caller's scratch for the tile kernels: the shared-memory
+// block (same layout as in shared memory) followed by the dense FP values of
+// phi at volume and face points used by the exact positivity check
+template <int K, int BK = BK_FMA>
+struct TileTab {
+    using C = TileCfg<K, BK>;
+    static constexpr int smem_tabs = C::smem_tabs;
+    static constexpr int phiv = r4(smem_tabs);                    // [b][nq]
+    static constexpr int phif = phiv + r4(C::b * C::nq);          // [b][nf]
+    static constexpr int total = phif + C::b * C::nf;
+};
+
+// --------------------------------------------------------------------------
+// vector helpers
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T* o);
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float* o)
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double* p, double* o)
+{
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    const double2 w = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = w.x;
+    o[3] = w.y;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T* o);
+template <>
+__device__ __forceinline__ void st4<float>(float* p, const float* o)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+template <>
+__device__ __forceinline__ void st4<double>(double* p, const double* o)
+{
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+}
+
+// four elements p[e..e+3] of an array with `valid` readable elements: one
+// 16-byte load when the chunk lies inside, element-wise (zero past the end)
+// otherwise
+template <typename T>
+__device__ __forceinline__ void ld4_guard(const T* p, int e, int valid, T* o)
+{
+    if (e + 3 < valid) {
+        ld4<T>(p + e, o);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = (e + j < valid) ? p[e + j] : T(0);
+    }
+}
+
+// --------------------------------------------------------------------------
+// block GEMM on the CUDA cores: C[M][N] = A[M][K] B[K][N] (row-major, shared)
+// thread micro-tile TM x TN with interleaved rows (row = mt + i*M/TM)
+// --------------------------------------------------------------------------
+constexpr int pick_tn(int N) { return (N % 8 == 0 && N >= 32) ? 8 : 4; }
+constexpr int pick_tm(int M, int N, int NT)
+{
+    const int ncol = N / pick_tn(N);
+    for (int tm = 1; tm <= 8; ++tm)
+        if (M % tm == 0 && (M / tm) * ncol <= NT) return tm;
+    for (int tm = 8; tm >= 1; --tm)
+        if (M % tm == 0) return tm;
+    return 1;
+}
+
+template <typename T, int M, int N, int KK, int LDA, int LDB, int LDC, int NT>
+__device__ __forceinline__ void gemm_fma(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Cm)
+{
+    constexpr int TN = pick_tn(N), TM = pick_tm(M, N, NT);
+    constexpr int MT = M / TM, NCOL = N / TN;
+    static_assert(M % TM == 0 && N % TN == 0 && KK % 4 == 0, "gemm shape");
+    static_assert(LDA % 4 == 0 && LDB % 4 == 0 && LDC % 4 == 0, "gemm strides");
+    for (int t = threadIdx.x; t < MT * NCOL; t += NT) {
+        const int mt = t / NCOL, nt = t % NCOL;
+        T acc[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+#pragma unroll
+        for (int k = 0; k < KK; k += 4) {
+            T a[TM][4], bb[4][TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) ld4<T>(A + (mt + i * MT) * LDA + k, a[i]);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                for (int j = 0; j < TN; j += 4) ld4<T>(B + (k + kk) * LDB + nt * TN + j, &bb[kk][j]);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[i][j] += a[i][kk] * bb[kk][j];
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; j += 4) st4<T>(Cm + (mt + i * MT) * LDC + nt * TN + j, &acc[i][j]);
+    }
+}
+
+// --------------------------------------------------------------------------
+// block GEMM on the tensor cores, split-BF16 x3 with FP32 accumulation:
+//   a = a_hi + a_lo, b = b_hi + b_lo (bf16, round to nearest),
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi   (relative error ~ 2^-16)
+// A is FP32 in shared memory, split while forming the fragments; B is stored
+// pre-split in fragment order (uint4 per lane and 16x8 tile).
+// mma.sync.m16n8k16 fragments (lane = 4 g + t): A regs (g,2t) (g+8,2t)
+// (g,2t+8) (g+8,2t+8); B regs (k=2t, n=g) (k=2t+8, n=g); C (g,2t) (g+8,2t).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int M, int N, int KK, int LDA, int LDC, int NT>
+__device__ __forceinline__ void gemm_x3(const float* __restrict__ A, const uint4* __restrict__ Bf,
+                                        float* __restrict__ Cm)
+{
+    constexpr int MT = M / 16, NTL = N / 8, KT = KK / 16, NW = NT / 32;
+    static_assert(M % 16 == 0 && N % 8 == 0 && KK % 16 == 0 && LDA % 2 == 0 && LDC % 2 == 0, "x3 shape");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    for (int mt = warp; mt < MT; mt += NW) {
+        float acc[NTL][4];
+#pragma unroll
+        for (int j = 0; j < NTL; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) {
+            const float* ap = A + (mt * 16 + g) * LDA + kt * 16 + 2 * t;
+            const float2 x0 = *reinterpret_cast<const float2*>(ap);
+            const float2 x1 = *reinterpret_cast<const float2*>(ap + 8 * LDA);
+            const float2 x2 = *reinterpret_cast<const float2*>(ap + 8);
+            const float2 x3 = *reinterpret_cast<const float2*>(ap + 8 * LDA + 8);
+            uint32_t ah[4], al[4];
+            split_bf16x2(x0.x, x0.y, ah[0], al[0]);
+            split_bf16x2(x1.x, x1.y, ah[1], al[1]);
+            split_bf16x2(x2.x, x2.y, ah[2], al[2]);
+            split_bf16x2(x3.x, x3.y, ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < NTL; ++nt) {
+                const uint4 bf = Bf[(kt * NTL + nt) * 32 + lane];
+                mma_bf16(acc[nt], al, bf.x, bf.y);
+                mma_bf16(acc[nt], ah, bf.z, bf.w);
+                mma_bf16(acc[nt], ah, bf.x, bf.y);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < NTL; ++nt) {
+            *reinterpret_cast<float2*>(Cm + (mt * 16 + g) * LDC + nt * 8 + 2 * t) = make_float2(acc[nt][0], acc[nt][1]);
+            *reinterpret_cast<float2*>(Cm + (mt * 16 + g + 8) * LDC + nt * 8 + 2 * t) =
+                make_float2(acc[nt][2], acc[nt][3]);
+        }
+    }
+}
+
+// C[M][N] = A[M][KK] B[KK][N] with the backend of the tile configuration;
+// B is the table at shared-memory offset OFF
+template <typename T, int BK, int M, int N, int KK, int LDA, int LDC, int NT>
+__device__ __forceinline__ void mm(const T* A, const T* tabs, int off, T* Cm)
+{
+    if constexpr (BK == BK_X3) {
+        gemm_x3<M, N, KK, LDA, LDC, NT>(reinterpret_cast<const float*>(A),
+                                        reinterpret_cast<const uint4*>(tabs + off), reinterpret_cast<float*>(Cm));
+    } else {
+        gemm_fma<T, M, N, KK, LDA, N, LDC, NT>(A, tabs + off, Cm);
+    }
+}
+
+// --------------------------------------------------------------------------
+// collapse of a 3D expansion onto the face (d, side): coefficients of the 2D
+// expansion in the tangential coordinates
+// --------------------------------------------------------------------------
+template <typename T, int K, int Dd, int NOUT>
+__device__ __forceinline__ void collapse(const T* c, int side, T* c2)
+{
+    constexpr int b = Dims<K>::b;
+#pragma unroll
+    for (int p = 0; p < NOUT; ++p) c2[p] = T(0);
+    static_for<0, b>([&](auto m) {
+        constexpr int nd = normal_deg<K>(Dd, decltype(m)::value);
+        constexpr int tm = tang_mode<K>(Dd, decltype(m)::value);
+        constexpr double f = csqrt(2.0 * nd + 1.0);
+        const T s = (side || !(nd & 1)) ? T(f) : T(-f);
+        c2[tm] += s * c[decltype(m)::value];
+    });
+}
+
+// R[m] += scale * Pn_{normal}(sigma) * L2[tang(m)],  sigma = side ? +1 : -1
+template <typename T, int K, int Dd>
+__device__ __forceinline__ void expand_acc(const T* L2, int side, T scale, T* R)
+{
+    constexpr int b = Dims<K>::b;
+    static_for<0, b>([&](auto m) {
+        constexpr int nd = normal_deg<K>(Dd, decltype(m)::value);
+        constexpr int tm = tang_mode<K>(Dd, decltype(m)::value);
+        constexpr double f = csqrt(2.0 * nd + 1.0);
+        const T s = (side || !(nd & 1)) ? T(f) : T(-f);
+        R[decltype(m)::value] += scale * s * L2[tm];
+    });
+}
+
+enum { TM_PROJECT = 0, TM_RHS = 1, TM_STAGE = 2 };
+enum { F_NEXTPROJ = 4 };
+
+template <typename T>
+struct TArgs {
+    const T* u_in;     // u^(s)
+    const T* u_n;      // u^n
+    T* out;            // u^(s+1) or dudt
+    const T* vh_in;    // projected velocity of u_in [c][3][b]
+    T* vh_out;         // projected velocity of the output (fused projection / K_A)
+    const T* ahat;     // forcing coefficients or nullptr
+    const T* tab;      // TileTab tables
+    Ctl* ctl;
+    double* partials;
+    long ncell;
+    int N;
+    Phys ph;
+    T rk_a, rk_b;
+    double dt_pimax;
+    int flags;         // F_DT | F_FORCE | F_NEXTPROJ
+    int abar_in;       // slot of ctl->abar2 read by this stage
+    int abar_out;      // slot written by the projection
+};
+
+// --------------------------------------------------------------------------
+// projection of the primitive velocity of the TC states in sU (Sec. 3.2),
+// the per-cell forcing sums <rho a_h> = sum_l rho_l a_l and the CFL maximum
+// --------------------------------------------------------------------------
+template <typename T, int K, int BK>
+__device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, bool dt_flag, T& smax, double* sums)
+{
+    using C = TileCfg<K, BK>;
+    constexpr int b = C::b, nq = C::nq, TC = C::TC, NT = C::NT, KP = C::KP, NQP = C::NQP, NP = C::NP;
+    constexpr int LDA = C::LDA, LDV = C::LDV, LDP = C::LDP;
+    T* sU = sm + C::oU;
+    T* sA = sm + C::oA;
+    T* sV = sm + C::oBig;
+    T* sP = sm + C::oP;
+    // rows (cell, field) for rho, m_x, m_y, m_z
+    for (int e = threadIdx.x; e < TC * 4 * KP; e += NT) {
+        const int r = e / KP, l = e % KP;
+        sA[r * LDA + l] = (l < b) ? sU[r * b + l] : T(0);
+    }
+    __syncthreads();
+    mm<T, BK, TC * 4, NQP, KP, LDA, LDV, NT>(sA, sm, C::oPhi, sV);
+    __syncthreads();
+    // v = m / rho at the volume points; rows (cell, i) of the projection input
+    constexpr int PER = (TC * NQP + NT - 1) / NT;
+    T vv[PER][3];
+#pragma unroll
+    for (int it = 0; it < PER; ++it) {
+        const int e = threadIdx.x + it * NT;
+        vv[it][0] = vv[it][1] = vv[it][2] = T(0);
+        if (e < TC * NQP) {
+            const int c = e / NQP, q = e % NQP;
+            if (q < nq) {
+                const T* v = sV + (c * 4) * LDV + q;
+                const T ir = T(1) / v[0];
+                vv[it][0] = v[LDV] * ir;
+                vv[it][1] = v[2 * LDV] * ir;
+                vv[it][2] = v[3 * LDV] * ir;
+                if (dt_flag && c0 + c < a.ncell) {
+                    const T sp = fabs(vv[it][0]) + fabs(vv[it][1]) + fabs(vv[it][2]);
+                    smax = sp > smax ? sp : smax;
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PER; ++it) {
+        const int e = threadIdx.x + it * NT;
+        if (e < TC * NQP) {
+            const int c = e / NQP, q = e % NQP;
+            T* f = sV + (c * 3) * LDV + q;
+            f[0] = vv[it][0];
+            f[LDV] = vv[it][1];
+            f[2 * LDV] = vv[it][2];
+        }
+    }
+    __syncthreads();
+    mm<T, BK, TC * 3, NP, NQP, LDV, LDP, NT>(sV, sm, C::oWPhi, sP);
+    __syncthreads();
+    for (int e = threadIdx.x; e < TC * 3 * b; e += NT) {
+        const int r = e / b, l = e % b;
+        const long c = c0 + r / 3;
+        if (c < a.ncell) a.vh_out[c0 * 3 * b + e] = sP[r * LDP + l];
+    }
+    if (a.flags & F_FORCE) {
+        // the tile's a_h staged in the (free) own-velocity buffer
+        T* sAh = sm + C::oVH;
+        const long nvalid = (a.ncell - c0) < TC ? (a.ncell - c0) : TC;
+        for (int e = 4 * threadIdx.x; e < TC * 3 * b; e += 4 * NT) {
+            T v[4];
+            ld4_guard<T>(a.ahat + c0 * 3 * b, e, (int)nvalid * 3 * b, v);
+            st4<T>(sAh + e, v);
+        }
+        __syncthreads();
+        if (threadIdx.x < TC * 3) {
+            const int c = threadIdx.x / 3, i = threadIdx.x % 3;
+            if (c < nvalid) {
+                const T* u = sU + c * 4 * b;
+                const T* ah = sAh + (c * 3 + i) * b;
+                T s = T(0);
+#pragma unroll
+                for (int l = 0; l < b; ++l) s += u[l] * ah[l];
+                sums[i] += (double)s;
+                if (i == 0) sums[3] += (double)u[0];
+            }
+        }
+    }
+}
+
+template <typename T, int K, int MODE, int BK>
+__global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
+{
+    using C = TileCfg<K, BK>;
+    using TT = TileTab<K, BK>;
+    using Dm = Dims<K>;
+    constexpr int b = C::b, nq = C::nq, ns = C::ns, nf = C::nf, TC = C::TC, NT = C::NT;
+    constexpr int FE = C::FE, KP = C::KP, NQP = C::NQP, NP = C::NP, B2K = C::B2K, NSP = C::NSP, B2N = C::B2N;
+    constexpr int LDA = C::LDA, LDV = C::LDV, LDP = C::LDP, LDC2 = C::LDC2, LDT = C::LDT, LDL = C::LDL;
+    constexpr int RE = C::RE, RP = C::RP, RC = C::RC, RL = C::RL;
+    static_assert(BK == BK_FMA || sizeof(T) == 4, "the tensor-core path is FP32");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    T* sU = sm + C::oU;
+    T* sVH = sm + C::oVH;
+    T* sR = sm + C::oR;
+    T* sA = sm + C::oA;
+    T* sP = sm + C::oP;
+    T* sBig = sm + C::oBig;
+    __shared__ int s_flag[TC];
+    __shared__ float s_minf[TC];
+    __shared__ double s_mind[TC];
+    __shared__ unsigned int s_status;
+    __shared__ double s_buf[NT];
+    __shared__ double s_tot[8];
+    __shared__ unsigned long long s_smax;
+
+    const int tid = threadIdx.x;
+    // tables -> shared (once per block)
+    for (int e = tid; e < C::smem_tabs; e += NT) sm[e] = a.tab[e];
+    if (tid == 0) {
+        s_status = 0u;
+        s_smax = 0ull;
+    }
+    const long ntile = (a.ncell + TC - 1) / TC;
+    const bool force = (a.flags & F_FORCE) != 0;
+    const T two_h = T(2.0 / a.ph.h);
+    const T inv4h = T(0.25 / a.ph.h);
+    const T cs = T(a.ph.cs), cs2 = T(a.ph.cs2);
+    T smax = T(0);
+    double sums[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool do_proj = (MODE == TM_PROJECT) || (MODE == TM_STAGE && (a.flags & F_NEXTPROJ));
+    T dt = T(0), ab0 = T(0), ab1 = T(0), ab2 = T(0);
+    if constexpr (MODE != TM_PROJECT) {
+        dt = T(MODE == TM_STAGE ? a.ctl->dt : a.dt_pimax);
+        if (force) {
+            ab0 = T(a.ctl->abar2[a.abar_in][0]);
+            ab1 = T(a.ctl->abar2[a.abar_in][1]);
+            ab2 = T(a.ctl->abar2[a.abar_in][2]);
+        }
+    }
+    __syncthreads();
+
+    for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const long c0 = tile * TC;
+        const long nvalid = (a.ncell - c0) < TC ? (a.ncell - c0) : TC;
+        // ---- stage the tile (cells past the end: rho = 1, everything else 0) ----
+        for (int e = 4 * tid; e < TC * 4 * b; e += 4 * NT) {
+            T v[4];
+            ld4_guard<T>(a.u_in + c0 * 4 * b, e, (int)nvalid * 4 * b, v);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((e + j) / (4 * b) >= nvalid) v[j] = ((e + j) % (4 * b)) == 0 ? T(1) : T(0);
+            st4<T>(sU + e, v);
+        }
+        if constexpr (MODE == TM_PROJECT) {
+            __syncthreads();
+            tile_project<T, K, BK>(sm, a, c0, (a.flags & F_DT) != 0, smax, sums);
+            __syncthreads();
+            continue;
+        } else {
+            for (int e = 4 * tid; e < TC * 3 * b; e += 4 * NT) {
+                T v[4];
+                ld4_guard<T>(a.vh_in + c0 * 3 * b, e, (int)nvalid * 3 * b, v);
+                st4<T>(sVH + e, v);
+            }
+            for (int e = tid; e < TC * 3 * b; e += NT) {
+                const int c = e / (3 * b), i = (e / b) % 3, l = e % b;
+                sA[(c * FE + 8 + i) * LDA + l] = (force && c < nvalid) ? a.ahat[c0 * 3 * b + e] : T(0);
+            }
+            __syncthreads();
+            // ---- evaluation coefficients: rho, m, grad rho, div m, (a_h staged above) ----
+            for (int e = tid; e < RE; e += NT) {
+                const int c = e / FE, f = e % FE;
+                const T* u = sU + c * 4 * b;
+                T* row = sA + e * LDA;
+                if (f >= 8 && f < 11) {
+#pragma unroll
+                    for (int l = b; l < KP; ++l) row[l] = T(0);
+                    continue;
+                }
+                T out[b];
+                if (f < 4) {
+#pragma unroll
+                    for (int l = 0; l < b; ++l) out[l] = u[f * b + l];
+                } else if (f == 4) {
+                    modal_grad<T, K, 0>(u, out, two_h);
+                } else if (f == 5) {
+                    modal_grad<T, K, 1>(u, out, two_h);
+                } else if (f == 6) {
+                    modal_grad<T, K, 2>(u, out, two_h);
+                } else if (f == 7) {
+                    T t2[b];
+                    modal_grad<T, K, 0>(u + b, out, two_h);
+                    modal_grad<T, K, 1>(u + 2 * b, t2, two_h);
+#pragma unroll
+                    for (int l = 0; l < b; ++l) out[l] += t2[l];
+                    modal_grad<T, K, 2>(u + 3 * b, t2, two_h);
+#pragma unroll
+                    for (int l = 0; l < b; ++l) out[l] += t2[l];
+                } else {
+#pragma unroll
+                    for (int l = 0; l < b; ++l) out[l] = T(0);
+                }
+#pragma unroll
+                for (int l = 0; l < KP; ++l) row[l] = (l < b) ? out[l] : T(0);
+            }
+            __syncthreads();
+            // ---- evaluation at the volume points ----
+            mm<T, BK, RE, NQP, KP, LDA, LDV, NT>(sA, sm, C::oPhi, sBig);
+            __syncthreads();
+            // ---- pointwise volume physics (Sec. 3.1: Pi at internal points only) ----
+            constexpr int PER = (TC * NQP + NT - 1) / NT;
+            T fl[PER][9];
+#pragma unroll
+            for (int it = 0; it < PER; ++it) {
+                const int e = tid + it * NT;
+#pragma unroll
+                for (int g = 0; g < 9; ++g) fl[it][g] = T(0);
+                if (e < TC * NQP) {
+                    const int c = e / NQP, q = e % NQP;
+                    if (q < nq) {
+                        const T* v = sBig + (c * FE) * LDV + q;
+                        const T rho = v[0], ir = T(1) / rho;
+                        const T mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV];
+                        const T vx = mx * ir, vy = my * ir, vz = mz * ir;
+                        const T divv = (v[7 * LDV] - (vx * v[4 * LDV] + vy * v[5 * LDV] + vz * v[6 * LDV])) * ir;
+                        T Pi = T(0);
+                        if (a.ph.av_mode == 1) Pi = vnr_pressure<T>(a.ph, rho, divv, dt);
+                        const T P = cs2 * rho + Pi;
+                        fl[it][0] = mx * vx + P;
+                        fl[it][1] = my * vy + P;
+                        fl[it][2] = mz * vz + P;
+                        fl[it][3] = mx * vy;
+                        fl[it][4] = mx * vz;
+                        fl[it][5] = my * vz;
+                        fl[it][6] = rho * (v[8 * LDV] - ab0);
+                        fl[it][7] = rho * (v[9 * LDV] - ab1);
+                        fl[it][8] = rho * (v[10 * LDV] - ab2);
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int it = 0; it < PER; ++it) {
+                const int e = tid + it * NT;
+                if (e < TC * NQP) {
+                    const int c = e / NQP, q = e % NQP;
+                    T* f = sBig + (c * 9) * LDV + q;
+#pragma unroll
+                    for (int g = 0; g < 9; ++g) f[g * LDV] = fl[it][g];
+                }
+            }
+            __syncthreads();
+            // ---- projection of the flux tensor and the forcing density ----
+            mm<T, BK, RP, NP, NQP, LDV, LDP, NT>(sBig, sm, C::oWPhi, sP);
+            __syncthreads();
+            // ---- volume term in modal space + forcing source ----
+            for (int e = tid; e < TC * 4; e += NT) {
+                const int c = e / 4, v = e % 4;
+                T r[b];
+#pragma unroll
+                for (int l = 0; l < b; ++l) r[l] = T(0);
+                const T* P = sP + c * 9 * LDP;
+                if (v == 0) {
+                    const T* u = sU + c * 4 * b;
+                    modal_grad_T_acc<T, K, 0>(u + b, r, two_h);
+                    modal_grad_T_acc<T, K, 1>(u + 2 * b, r, two_h);
+                    modal_grad_T_acc<T, K, 2>(u + 3 * b, r, two_h);
+                } else {
+                    const int i = v - 1;
+                    const int cx = (i == 0) ? 0 : (i == 1 ? 3 : 4);
+                    const int cy = (i == 0) ? 3 : (i == 1 ? 1 : 5);
+                    const int cz = (i == 0) ? 4 : (i == 1 ? 5 : 2);
+                    modal_grad_T_acc<T, K, 0>(P + cx * LDP, r, two_h);
+                    modal_grad_T_acc<T, K, 1>(P + cy * LDP, r, two_h);
+                    modal_grad_T_acc<T, K, 2>(P + cz * LDP, r, two_h);
+#pragma unroll
+                    for (int l = 0; l < b; ++l) r[l] += P[(6 + i) * LDP + l];
+                }
+#pragma unroll
+                for (int l = 0; l < b; ++l) sR[(c * 4 + v) * b + l] = r[l];
+            }
+            __syncthreads();
+            // ---- faces, one direction at a time (Sec. 3.2 face states, Rusanov) ----
+            T* sC2 = sBig + C::oC2;
+            T* sTr = sBig + C::oTr;
+            T* sFs = sBig + C::oFs;
+            T* sL2 = sBig + C::oL2;
+            static_for<0, 3>([&](auto dd) {
+                constexpr int Dd = decltype(dd)::value;
+                // collapse rows r = ((c*2 + side)*2 + who)*4 + field
+                for (int r = tid; r < RC; r += NT) {
+                    const int field = r & 3, who = (r >> 2) & 1, side = (r >> 3) & 1, c = r >> 4;
+                    T cf[b];
+                    int fside = side;
+                    if (who == 0) {
+                        const T* src = (field == 0) ? sU + c * 4 * b : sVH + (c * 3 + field - 1) * b;
+#pragma unroll
+                        for (int l = 0; l < b; ++l) cf[l] = src[l];
+                    } else {
+                        fside = 1 - side;
+                        const long cc = c0 + c;
+                        if (cc < a.ncell) {
+                            const long nc = neighbour(cc, 2 * Dd + side, a.N);
+                            const T* src = (field == 0) ? a.u_in + nc * 4 * b : a.vh_in + (nc * 3 + field - 1) * b;
+                            if constexpr (b % 4 == 0) {
+#pragma unroll
+                                for (int l = 0; l < b; l += 4) ld4<T>(src + l, cf + l);
+                            } else {
+#pragma unroll
+                                for (int l = 0; l < b; ++l) cf[l] = __ldg(src + l);
+                            }
+                        } else {
+#pragma unroll
+                            for (int l = 0; l < b; ++l) cf[l] = (field == 0 && l == 0) ? T(1) : T(0);
+                        }
+                    }
+                    T c2[B2K];
+                    collapse<T, K, Dd, B2K>(cf, fside, c2);
+#pragma unroll
+                    for (int p = 0; p < B2K; ++p) sC2[r * LDC2 + p] = c2[p];
+                }
+                __syncthreads();
+                mm<T, BK, RC, NSP, B2K, LDC2, LDT, NT>(sC2, sm, C::oPsi, sTr);
+                __syncthreads();
+                // Rusanov at every face point; F* along +e_d with L = lower cell
+                for (int e = tid; e < TC * 2 * NSP; e += NT) {
+                    const int s = e % NSP, side = (e / NSP) & 1, c = e / (2 * NSP);
+                    T F[4] = {T(0), T(0), T(0), T(0)};
+                    if (s < ns) {
+                        const int rs = ((c * 2 + side) * 2 + 0) * 4, rn = ((c * 2 + side) * 2 + 1) * 4;
+                        T Ws[4], Wn[4];
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) {
+                            Ws[f] = sTr[(rs + f) * LDT + s];
+                            Wn[f] = sTr[(rn + f) * LDT + s];
+                        }
+                        if (side)
+                            rusanov<T, Dd>(cs, cs2, Ws, Wn, F);
+                        else
+                            rusanov<T, Dd>(cs, cs2, Wn, Ws, F);
+                    }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) sFs[((c * 2 + side) * 4 + v) * LDT + s] = F[v];
+                }
+                __syncthreads();
+                mm<T, BK, RL, B2N, NSP, LDT, LDL, NT>(sFs, sm, C::oPsiL, sL2);
+                __syncthreads();
+                for (int e = tid; e < TC * 4; e += NT) {
+                    const int c = e / 4, v = e % 4;
+                    T* R = sR + (c * 4 + v) * b;
+                    // + face (side 1): -1/(4h); - face (side 0): +1/(4h)
+                    expand_acc<T, K, Dd>(sL2 + ((c * 2 + 1) * 4 + v) * LDL, 1, -inv4h, R);
+                    expand_acc<T, K, Dd>(sL2 + ((c * 2 + 0) * 4 + v) * LDL, 0, inv4h, R);
+                }
+                __syncthreads();
+            });
+            // ---- epilogue ----
+            if constexpr (MODE == TM_RHS) {
+                for (int e = tid; e < TC * 4 * b; e += NT) {
+                    if (e / (4 * b) < nvalid) a.out[c0 * 4 * b + e] = sR[e];
+                }
+                __syncthreads();
+            } else {
+                // SSP-RK stage combine (Sec. 7), new state kept in sU
+                for (int e = tid; e < TC * 4 * b; e += NT) {
+                    T w;
+                    if (e / (4 * b) < nvalid) {
+                        const T un = (a.rk_a != T(0)) ? a.u_n[c0 * 4 * b + e] : T(0);
+                        w = a.rk_a * un + a.rk_b * (sU[e] + dt * sR[e]);
+                    } else {
+                        w = ((e % (4 * b)) == 0) ? T(1) : T(0);
+                    }
+                    sU[e] = w;
+                }
+                __syncthreads();
+                // positivity (Sec. 3.1): a cell passes when rho_0 - sum_l |rho_l| sup|phi_l| >= eps;
+                // otherwise rho is evaluated at every volume and face Gauss point
+                const T eps = T(a.ph.floor_);
+                if (tid < TC) {
+                    const T* r = sU + tid * 4 * b;
+                    T bound = T(0);
+                    static_for<1, b>([&](auto m) {
+                        constexpr double sp = sup_phi<K>(decltype(m)::value);
+                        bound += fabs(r[decltype(m)::value]) * T(sp);
+                    });
+                    s_flag[tid] = (r[0] - bound < eps) ? 1 : 0;
+                    s_minf[tid] = 3.0e38f;
+                    s_mind[tid] = 1.0e300;
+                }
+                __syncthreads();
+                {
+                    constexpr int G = NT / TC;
+                    const int c = tid / G, g = tid % G;
+                    if (c < TC && s_flag[c]) {
+                        const T* r = sU + c * 4 * b;
+                        const T* phiv = a.tab + TT::phiv;
+                        const T* phif = a.tab + TT::phif;
+                        T mn = T(1e30);
+                        for (int p = g; p < nq + nf; p += G) {
+                            T rho = T(0);
+                            if (p < nq) {
+#pragma unroll
+                                for (int l = 0; l < b; ++l) rho += r[l] * __ldg(phiv + l * nq + p);
+                            } else {
+#pragma unroll
+                                for (int l = 0; l < b; ++l) rho += r[l] * __ldg(phif + l * nf + (p - nq));
+                            }
+                            mn = rho < mn ? rho : mn;
+                        }
+                        if constexpr (sizeof(T) == 4)
+                            atomicMin(reinterpret_cast<int*>(&s_minf[c]), float_key((float)mn));
+                        else
+                            atomicMin(reinterpret_cast<long long*>(&s_mind[c]), double_key((double)mn));
+                    }
+                }
+                __syncthreads();
+                unsigned int st = 0u;
+                for (int e = tid; e < TC * 4 * b; e += NT) {
+                    const int c = e / (4 * b), l = e % b;
+                    T w = sU[e];
+                    if (s_flag[c]) {
+                        T rmin;
+                        if constexpr (sizeof(T) == 4)
+                            rmin = (T)key_float(*reinterpret_cast<int*>(&s_minf[c]));
+                        else
+                            rmin = (T)key_double(*reinterpret_cast<long long*>(&s_mind[c]));
+                        const T rbar = sU[c * 4 * b];
+                        if (rmin < eps) {
+                            if (rbar > eps) {
+                                if (l > 0) w *= (rbar - eps) / (rbar - rmin);
+                                st |= DG_ST_LIMITED_;
+                            } else {
+                                st |= DG_ST_FAIL_;
+                            }
+                        }
+                    }
+                    if (c < nvalid) {
+                        if (!isfinite(w)) st |= DG_ST_NONFINITE_;
+                        a.out[c0 * 4 * b + e] = w;
+                    }
+                }
+                __syncthreads();
+                // the limited state is the input of the fused projection
+                for (int e = tid; e < TC * 4 * b; e += NT) {
+                    const int c = e / (4 * b), l = e % b;
+                    if (s_flag[c] && l > 0) {
+                        const T rbar = sU[c * 4 * b];
+                        T rmin;
+                        if constexpr (sizeof(T) == 4)
+                            rmin = (T)key_float(*reinterpret_cast<int*>(&s_minf[c]));
+                        else
+                            rmin = (T)key_double(*reinterpret_cast<long long*>(&s_mind[c]));
+                        if (rmin < eps && rbar > eps) sU[e] *= (rbar - eps) / (rbar - rmin);
+                    }
+                }
+                if (st) atomicOr(&s_status, st);
+                __syncthreads();
+                if (do_proj) {
+                    tile_project<T, K, BK>(sm, a, c0, false, smax, sums);
+                    __syncthreads();
+                }
+            }
+        }
+    }
+    // ---- block-level reductions ----
+    if constexpr (MODE == TM_STAGE) {
+        if (tid == 0 && s_status) atomicOr(&a.ctl->status, s_status);
+    }
+    if (do_proj) {
+        if (a.flags & F_DT) {
+            const double sp = (double)smax + 3.0 * a.ph.cs;
+            atomicMax(&s_smax, (unsigned long long)__double_as_longlong(sp));
+            __syncthreads();
+            if (tid == 0) atomicMax(&a.ctl->smax, s_smax);
+        }
+        double mine[4];
+        for (int i = 0; i < 4; ++i) {
+            s_buf[tid] = sums[i];
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int j = 0; j < NT; ++j) t += s_buf[j];
+                mine[i] = t;
+            }
+            __syncthreads();
+        }
+        if (last_block_reduce<NT>(a.partials, mine, 4, &a.ctl->cnt_proj, s_tot, s_buf)) {
+            if (tid == 0) {
+                const int o = a.abar_out;
+                if (a.flags & F_FORCE) {
+                    for (int i = 0; i < 3; ++i) a.ctl->abar2[o][i] = s_tot[i] / s_tot[3];
+                } else {
+                    a.ctl->abar2[o][0] = a.ctl->abar2[o][1] = a.ctl->abar2[o][2] = 0.0;
+                }
+                if (a.flags & F_DT) {
+                    const unsigned long long bits = atomicAdd(&a.ctl->smax, 0ull);
+                    const double sm_ = __longlong_as_double((long long)bits);
+                    const double dtv = a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / sm_;
+                    a.ctl->dt = dtv * a.ctl->dt_scale;
+                    a.ctl->smax = 0ull;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace dg

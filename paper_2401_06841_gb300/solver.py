@@ -44,7 +44,9 @@ class Solver:
         self._check(self.L.dg_scratch_bytes(C.byref(self.mesh), k, C.byref(self.nu), C.byref(nb)), None)
         with torch.cuda.device(self.device):
             self.regs = [torch.zeros(self.ncell, 4, self.b, dtype=self.dtype, device=self.device) for _ in range(3)]
-            self.vhat = torch.zeros(self.ncell, 3, self.b, dtype=self.dtype, device=self.device)
+            vb = C.c_size_t(0)
+            self._check(self.L.dg_vhat_bytes(C.byref(self.mesh), k, self.prec, C.byref(vb)), None)
+            self.vhat = torch.zeros(int(vb.value), dtype=torch.uint8, device=self.device)
             self.ahat = torch.zeros(self.ncell, 3, self.b, dtype=self.dtype, device=self.device)
             self.scratch = torch.zeros(int(nb.value) + 256, dtype=torch.uint8, device=self.device)
         base = self.scratch.data_ptr()

@@ -231,3 +231,84 @@ def test_conservation_on_gpu(prec):
     assert abs(d1["mass"] - d0["mass"]) < tol * d0["mass"]
     for c in ("mom_x", "mom_y", "mom_z"):
         assert abs(d1[c] - d0[c]) < tol * 10 * d0["mass"]
+
+
+# --------------------------------------------------------------------------
+# split-BF16 x3 tensor-core transforms (FP32 state, FP32 accumulation)
+# Every product a*b is formed as a_hi b_hi + a_hi b_lo + a_lo b_hi with bf16
+# halves, so each product carries a relative error of order 2^-16 = 1.5e-5;
+# sums over 20-64 terms and the cancellation in the flux divergence of random
+# discontinuous states give the bound below for one RHS evaluation.
+# --------------------------------------------------------------------------
+TOL_X3 = 5e-5
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_projection_parity_x3(k):
+    N = 5
+    u = I.random_state(N, k, seed=20 + k)
+    s = Solver(N, k, precision="x3")
+    got = s.project_velocity(u).cpu().numpy()
+    ref = O.project_velocity(O.make_cfg(N, k), u)
+    err = rel_l2_fields(got, ref)
+    print("x3 projection k=%d rel-L2 per component %s" % (k, err))
+    assert err.max() < TOL_X3
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("forced", [False, True])
+def test_rhs_parity_x3(k, forced):
+    N = 5
+    u = I.random_state(N, k, seed=30 + k)
+    cfg = O.make_cfg(N, k)
+    a = ahat_for(N, k) if forced else None
+    dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
+    ref = O.rhs(cfg, u, a, dt)
+    s = Solver(N, k, precision="x3")
+    got = s.rhs(u, a, dt).cpu().numpy()
+    err = rel_l2_fields(got, ref)
+    print("x3 rhs k=%d forced=%s rel-L2 per field %s" % (k, forced, err))
+    assert err.max() < TOL_X3, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [2, 3])
+def test_driven_steps_parity_x3(k):
+    N = 5
+    u = I.random_state(N, k, seed=50 + k, v_rms=0.8)
+    s = Solver(N, k, precision="x3")
+    s.set_state(u)
+    s.set_forcing(mach=3.0, zeta=1.0, seed=1)
+    s.step(3)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, _, _, _ = O.run(O.make_cfg(N, k), ref, 3, forcing=O.Forcing(mach=3.0, zeta=1.0, seed=1))
+    assert rc == 0
+    err = rel_l2_fields(got, ref)
+    print("x3 3 driven steps k=%d rel-L2 per field %s" % (k, err))
+    assert err.max() < 1e-4, err
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("x3", 2e-4)])
+def test_full_size_rhs_64_k3(prec, tol):
+    # the benchmark's configuration (64^3 cells, k=3) and launch shapes:
+    # one forced RHS of a smooth turbulent state against the oracle.  The
+    # RHS of a smooth state is a small difference of large volume and face
+    # terms: FP32 shows a relative error of ~60 unit round-offs (3.5e-6), so
+    # the x3 bound is that cancellation factor times the 2^-16 product error
+    # with a safety factor of 2.
+    N, k = 64, 3
+    u = I.turbulent_state(N, k, seed=102, mach=3.0)
+    u[:, 0, :] = I.random_state(N, k, seed=7, rho_wiggle=0.3, v_rms=0.0)[:, 0, :]
+    a = ahat_for(N, k, seed=0, mach=3.0)
+    dt = 2e-4
+    ref = O.rhs(O.make_cfg(N, k), u, a, dt)
+    s = Solver(N, k, precision=prec)
+    got = s.rhs(u, a, dt).cpu().numpy()
+    err = rel_l2_fields(got, ref)
+    print("full-size 64^3 k=3 %s rel-L2 per field %s" % (prec, err))
+    assert err.max() < tol, err
