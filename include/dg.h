@@ -224,6 +224,32 @@ int dg_profile_read(dg_ctx* ctx, dg_prof* out);   /* synchronises the stream    
 int dg_get_meta(dg_ctx* ctx, dg_meta* out);
 int dg_set_meta(dg_ctx* ctx, const dg_meta* in);
 
+/* Right-hand side without any allocation, for callers that cannot allocate
+ * device memory: their device memory is all held by their own pool (a
+ * framework's caching allocator), or they must not call cudaMalloc/cudaFree
+ * after start-up because those calls can synchronise the device and stall
+ * every stream.  The paper has no counterpart; this is a service of the
+ * library.  Computes the same quantity as dg_rhs (single evaluation of the
+ * weak-form right-hand side, same layouts and element types; dudt and u_in
+ * are device buffers, ahat a device buffer or NULL) without a context: the
+ * caller passes only inputs, outputs and a stream.  The working memory
+ * (control block, reduction partials, basis tables, projected velocity)
+ * lives in one fixed 64 MiB device array of the library, held by every GPU
+ * that loads it until the process exits.  Limit: N^3 * 3 * b * element size
+ * plus about 1.2 MiB must fit in 64 MiB (for example N <= 64 at k = 3 in
+ * FP32); larger meshes return DG_ENOMEM and nothing runs.  Artificial
+ * viscosity modes DG_AV_OFF and DG_AV_VNR only.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and the first
+ * call for a given order and precision uploads the tables: make that first
+ * call before any stream capture.  All calls share the array and it keeps the
+ * last call's contents; its control block is cleared at every call.  Calls
+ * whose GPU work overlaps (other streams, other host threads) race on the
+ * array and must be serialised.  Work is enqueued on `stream` (a
+ * cudaStream_t); the call does not synchronise.  Errors are also printed to
+ * stderr (there is no context to hold them). */
+int dg_rhs_noalloc(const dg_mesh* mesh, int order, double cs, const dg_nu_params* nu, int precision,
+                   const void* u_in, const void* ahat, void* dudt, double dt_for_pimax, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

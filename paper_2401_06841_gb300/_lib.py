@@ -91,6 +91,7 @@ def lib() -> C.CDLL:
         L.dg_l1_density.argtypes = [vp, vp, vp, C.POINTER(d)]
         L.dg_get_meta.argtypes = [vp, C.POINTER(Meta)]
         L.dg_set_meta.argtypes = [vp, C.POINTER(Meta)]
+        L.dg_rhs_noalloc.argtypes = [C.POINTER(Mesh), i, d, C.POINTER(NuParams), i, vp, vp, vp, d, vp]
         L.dg_profile.argtypes = [vp, i]
         L.dg_profile_read.argtypes = [vp, C.POINTER(Prof)]
         _lib = L
@@ -100,7 +101,8 @@ def lib() -> C.CDLL:
 # every symbol include/dg.h declares
 EXPORTS = ("dg_scratch_bytes", "dg_vhat_bytes", "dg_init", "dg_free", "dg_last_error", "dg_set_state", "dg_get_state", "dg_rhs",
            "dg_project_velocity", "dg_step", "dg_set_forcing", "dg_set_forcing_coeffs", "dg_forcing_from_modes",
-           "dg_diagnostics", "dg_l1_density", "dg_get_meta", "dg_set_meta", "dg_profile", "dg_profile_read")
+           "dg_diagnostics", "dg_l1_density", "dg_get_meta", "dg_set_meta", "dg_profile", "dg_profile_read",
+           "dg_rhs_noalloc")
 
 
 class DGError(RuntimeError):
