@@ -324,7 +324,37 @@ void orc_forcing_mean(const orc_cfg* cfg, const double* u, const double* ahat, d
 /* (Sec. 3.1).  Faces: rho from its own expansion, v from the projected      */
 /* velocity, no viscous pressure (Sec. 3.1, 3.2).                            */
 /* ------------------------------------------------------------------------ */
+static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, const double* nu_cell,
+                    double* dudt);
+
 int orc_rhs(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, double* dudt)
+{
+    return rhs_impl(cfg, u, ahat, dt_pimax, NULL, dudt);
+}
+
+/* Viscous pressure with a per-cell coefficient nu (av_mode 2, the learned
+ * sensor): Pi = rho nu |div v| for div v < 0, with the same cap
+ * Pi_max = (1/2) rho (h/p)^2 |div v| / dt as the vNR form (Sec. 3.1). */
+double orc_pi_nu(const orc_cfg* cfg, double rho, double divv, double nu, double dt)
+{
+    if (!(divv < 0.0)) return 0.0;
+    double hp = (1.0 / cfg->N) / (cfg->k + 1);
+    double Pi = rho * nu * (-divv);
+    if (dt > 0.0) {
+        double Pmax = 0.5 * rho * hp * hp * (-divv) / dt;
+        if (Pi > Pmax) Pi = Pmax;
+    }
+    return Pi;
+}
+
+int orc_rhs_nu(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, const double* nu_cell,
+               double* dudt)
+{
+    return rhs_impl(cfg, u, ahat, dt_pimax, nu_cell, dudt);
+}
+
+static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, const double* nu_cell,
+                    double* dudt)
 {
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
@@ -355,7 +385,8 @@ int orc_rhs(const orc_cfg* cfg, const double* u, const double* ahat, double dt_p
             }
             /* div v = (div m - v . grad rho) / rho */
             double divv = (dmd[0] + dmd[1] + dmd[2] - (v[0] * drho[0] + v[1] * drho[1] + v[2] * drho[2])) / rho;
-            double P = cs2 * rho + orc_vnr(cfg, rho, divv, dt_pimax);
+            double P = cs2 * rho +
+                       (nu_cell ? orc_pi_nu(cfg, rho, divv, nu_cell[c], dt_pimax) : orc_vnr(cfg, rho, divv, dt_pimax));
             double F[4][3]; /* F[var][d] */
             for (int d = 0; d < 3; ++d) {
                 F[0][d] = m[d];
@@ -747,4 +778,52 @@ double orc_l1_density(const orc_cfg* cfg, const double* uA, const double* uB)
         }
     tabs_free(&T);
     return sum;
+}
+
+/* ------------------------------------------------------------------------ */
+/* learned-sensor features and labels (per cell)                             */
+/*  x[c][0..b)   = rho_l / rho_0                                              */
+/*  x[c][b..2b)  = |v|hat_l / cs, |v|hat the Gauss projection of |m/rho|    */
+/*  y[c]         = log(max(nu_cell, nu_f) / (cs h/p)),                       */
+/*  nu_cell = max over volume points with div v < 0 of Pi/(rho |div v|) for  */
+/*  the vNR pressure of Sec. 3.1 (cap with dt), nu_f = 1e-6 cs h/p.          */
+/* ------------------------------------------------------------------------ */
+void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, double* y)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nq = T.nq;
+    size_t nc = (size_t)N * N * N;
+    double h = 1.0 / N, hp = h / (cfg->k + 1), ref = cfg->cs * hp;
+    for (size_t c = 0; c < nc; ++c) {
+        const double* uc = u + c * 4 * b;
+        double* xc = x + c * 2 * b;
+        for (int l = 0; l < b; ++l) {
+            xc[l] = uc[l] / uc[0];
+            xc[b + l] = 0.0;
+        }
+        double nu = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            const double* ph = T.phi + q * b;
+            double rho = eval(&T, uc, ph), m[3], v[3], drho[3], dmd[3];
+            for (int i = 0; i < 3; ++i) {
+                m[i] = eval(&T, uc + (1 + i) * b, ph);
+                v[i] = m[i] / rho;
+            }
+            for (int d = 0; d < 3; ++d) {
+                const double* dph = T.dphi + ((size_t)d * nq + q) * b;
+                drho[d] = (2.0 / h) * eval(&T, uc, dph);
+                dmd[d] = (2.0 / h) * eval(&T, uc + (1 + d) * b, dph);
+            }
+            double divv = (dmd[0] + dmd[1] + dmd[2] - (v[0] * drho[0] + v[1] * drho[1] + v[2] * drho[2])) / rho;
+            double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            for (int l = 0; l < b; ++l) xc[b + l] += 0.125 * T.wq[q] * ph[l] * speed / cfg->cs;
+            if (divv < 0.0) {
+                double nq_ = orc_vnr(cfg, rho, divv, dt) / (rho * (-divv));
+                if (nq_ > nu) nu = nq_;
+            }
+        }
+        y[c] = log((nu > 1e-6 * ref ? nu : 1e-6 * ref) / ref);
+    }
+    tabs_free(&T);
 }

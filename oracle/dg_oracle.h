@@ -70,6 +70,10 @@ void orc_rusanov(double cs, int d, const double WL[4], const double WR[4],
 int orc_rhs(const orc_cfg* cfg, const double* u, const double* ahat,
             double dt_pimax, double* dudt);
 int orc_limit(const orc_cfg* cfg, double* u);
+double orc_pi_nu(const orc_cfg* cfg, double rho, double divv, double nu, double dt);
+int orc_rhs_nu(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, const double* nu_cell,
+               double* dudt);
+void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, double* y);
 int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt);
 
 void orc_ou_init(orc_ou* ou, int kmin2, int kmax2, double zeta, double mach,

@@ -79,6 +79,10 @@ def lib():
         _lib.orc_run.argtypes = [C.POINTER(Cfg), d, C.POINTER(OU), C.c_int, d, C.c_int, d, d]
         _lib.orc_diagnostics.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d]
         _lib.orc_forcing_project.argtypes = [C.POINTER(Cfg), C.c_int, C.POINTER(C.c_int32), d, d]
+        _lib.orc_rhs_nu.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d, d]
+        _lib.orc_av_features.argtypes = [C.POINTER(Cfg), d, C.c_double, d, d]
+        _lib.orc_pi_nu.restype = C.c_double
+        _lib.orc_pi_nu.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double, C.c_double]
     return _lib
 
 
@@ -157,6 +161,28 @@ def rhs(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None = None, dt_pimax: float
     out = np.zeros(_shape(cfg))
     lib().orc_rhs(C.byref(cfg), _p(u), _p(ahat), dt_pimax, _p(out))
     return out
+
+
+def rhs_nu(cfg: Cfg, u: np.ndarray, nu_cell: np.ndarray, ahat: np.ndarray | None = None,
+           dt_pimax: float = 0.0) -> np.ndarray:
+    """RHS with the per-cell viscous coefficient nu (learned-sensor mode)."""
+    out = np.zeros(_shape(cfg))
+    nu = np.ascontiguousarray(nu_cell, dtype=np.float64)
+    lib().orc_rhs_nu(C.byref(cfg), _p(u), _p(ahat), dt_pimax, _p(nu), _p(out))
+    return out
+
+
+def pi_nu(cfg: Cfg, rho: float, divv: float, nu: float, dt_: float) -> float:
+    return lib().orc_pi_nu(C.byref(cfg), rho, divv, nu, dt_)
+
+
+def av_features(cfg: Cfg, u: np.ndarray, dt_: float):
+    """(x [cells][2b], y [cells]) inputs and targets of the learned sensor."""
+    b = nmodes(cfg.k)
+    x = np.zeros((cfg.N ** 3, 2 * b))
+    y = np.zeros(cfg.N ** 3)
+    lib().orc_av_features(C.byref(cfg), _p(u), dt_, _p(x), _p(y))
+    return x, y
 
 
 def limit(cfg: Cfg, u: np.ndarray) -> int:
