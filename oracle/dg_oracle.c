@@ -786,7 +786,10 @@ double orc_l1_density(const orc_cfg* cfg, const double* uA, const double* uB)
 /*  x[c][b..2b)  = |v|hat_l / cs, |v|hat the Gauss projection of |m/rho|    */
 /*  y[c]         = log(max(nu_cell, nu_f) / (cs h/p)),                       */
 /*  nu_cell = max over volume points with div v < 0 of Pi/(rho |div v|) for  */
-/*  the vNR pressure of Sec. 3.1 (cap with dt), nu_f = 1e-6 cs h/p.          */
+/*  the vNR pressure of Sec. 3.1 (cap with dt); nu_f = max(beta, 0.05) cs h/p */
+/*  is the coefficient every compressive point receives from the linear term */
+/*  (Pi only acts where div v < 0, so cells without compression carry the    */
+/*  floor).                                                                   */
 /* ------------------------------------------------------------------------ */
 void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, double* y)
 {
@@ -823,7 +826,8 @@ void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, 
                 if (nq_ > nu) nu = nq_;
             }
         }
-        y[c] = log((nu > 1e-6 * ref ? nu : 1e-6 * ref) / ref);
+        const double floor_ = (cfg->beta > 0.05 ? cfg->beta : 0.05) * ref;
+        y[c] = log((nu > floor_ ? nu : floor_) / ref);
     }
     tabs_free(&T);
 }

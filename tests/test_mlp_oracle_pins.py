@@ -86,10 +86,12 @@ def test_sensor_labels_closed_form():
     assert np.allclose(x[:, 0], 1.0) and np.allclose(x[:, 1:b], 0.0)
     # |v| = c h/2 |xi|; 3-point Gauss projection of |xi| onto Pn_0: (w_a |xi_a|)/2 = (5/9) sqrt(3/5)
     assert np.allclose(x[:, b], c * h / 2 * (5.0 / 9.0) * math.sqrt(0.6), atol=1e-14)
-    # expansion: no compressive point, label at the floor
+    # expansion: no compressive point, label at the floor max(beta, 0.05)
     u[:, 1, ml.index((1, 0, 0))] *= -1
     _, y2 = O.av_features(cfg, u, 0.0)
-    assert np.allclose(y2, math.log(1e-6))
+    assert np.allclose(y2, math.log(0.2))
+    _, y3 = O.av_features(O.make_cfg(N, k, beta=0.0), u, 0.0)
+    assert np.allclose(y3, math.log(0.05))
 
 
 def test_rhs_with_cell_coefficient_equals_vnr_when_nu_matches():
