@@ -205,6 +205,49 @@ int dg_diagnostics(dg_ctx* ctx, double dt_for_pimax, dg_diag* out);
  * (k+3)-point Gauss quadrature per axis per cell.  Synchronises. */
 int dg_l1_density(dg_ctx* ctx, const void* uA, const void* uB, double* out);
 
+/* ---- learned viscosity sensor (not in the paper: a small network stands in
+ * for the shock sensor and is judged against it) ------------------------------
+ * Network y = W3 . gelu(W2 gelu(W1 x + b1) + b2) + b3, gelu(z) = z/2 (1 +
+ * erf(z/sqrt 2)), 64 hidden units, D = 2b inputs per cell
+ *   x = (rho_l / rho_0, |v|hat_l / cs),  |v|hat the Gauss projection of |v|,
+ * output y = log(nu / (cs h/p)).  In DG_AV_LEARNED mode the viscous pressure
+ * at a volume point is Pi = rho nu |div v| for div v < 0, capped at
+ * rho (h/p)^2 |div v| / (2 dt) as in Sec. 3.1; nu is evaluated once per step
+ * (BF16 tensor-core inference, FP32 accumulation) and kept for its stages.
+ * Parameters: FP32 array of dg_av_param_count() floats in the order
+ * W1 [64][D] row-major, b1 [64], W2 [64][64], b2 [64], W3 [64], b3. */
+typedef struct {
+    double lr, beta1, beta2, eps;  /* Adam (Kingma & Ba); 1e-3, 0.9, 0.999, 1e-8 */
+    int32_t batch;                 /* <= 4096 */
+    int32_t epochs;
+} dg_train_opts;
+
+int dg_av_param_count(dg_ctx* ctx, int64_t* n);
+/* Set / get the FP32 parameters (host arrays of dg_av_param_count floats);
+ * setting them resets the Adam moments. */
+int dg_set_av_weights(dg_ctx* ctx, const float* w, size_t n);
+int dg_get_av_weights(dg_ctx* ctx, float* w, size_t n);
+/* Inputs and plain-sensor targets of every cell of the current state (device
+ * buffers x [N^3][2b], y [N^3] FP32): y = log(max(nu_cell, nu_f) / (cs h/p)),
+ * nu_cell the largest Pi/(rho |div v|) of the vNR pressure over the cell's
+ * compressive volume points (dt_for_pimax fixes the cap), nu_f = max(beta,
+ * 0.05) cs h/p the coefficient of the linear term.  Needs a
+ * context created in DG_AV_LEARNED mode (it holds the |v| projection). */
+int dg_generate_pairs(dg_ctx* ctx, double dt_for_pimax, float* x, float* y, int64_t cap, int64_t* n_out);
+/* Minibatch Adam on the mean squared error of y over (x [n][2b], y [n]),
+ * device buffers, batches in the given row order; *loss_out = mean batch
+ * loss of the last epoch.  FP32 forward/backward kernels; gradient sums in a
+ * fixed order (run to run identical). */
+int dg_mlp_train(dg_ctx* ctx, const float* x, const float* y, int64_t n, const dg_train_opts* opts, double* loss_out);
+/* Loss and gradient of one batch (n <= 4096) at the current parameters;
+ * grad is a device array of dg_av_param_count floats. */
+int dg_mlp_grad(dg_ctx* ctx, const float* x, const float* y, int64_t n, float* grad, double* loss);
+/* Network output y for explicit inputs (device x [n][2b] -> y [n]), using the
+ * BF16 inference kernel of the learned mode. */
+int dg_mlp_forward(dg_ctx* ctx, const float* x, int64_t n, float* y);
+/* Per-cell coefficient nu of the current state (device float [N^3]). */
+int dg_av_nu(dg_ctx* ctx, float* nu_out);
+
 /* Kernel timing: with profiling on, every launch of the library is bracketed
  * by CUDA events on the context's stream and its duration accumulated per
  * kernel family (read back after the stream is synchronised).  Launch counts

@@ -54,6 +54,11 @@ class Meta(C.Structure):
                 ("x", C.c_double * 2 * 3 * 512)]
 
 
+class TrainOpts(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("batch", C.c_int32), ("epochs", C.c_int32)]
+
+
 class Prof(C.Structure):
     _fields_ = [("launches", C.c_int64), ("n_project", C.c_int64), ("n_rhs", C.c_int64), ("n_force", C.c_int64),
                 ("n_other", C.c_int64), ("ms_project", C.c_double), ("ms_rhs", C.c_double),
@@ -91,6 +96,14 @@ def lib() -> C.CDLL:
         L.dg_l1_density.argtypes = [vp, vp, vp, C.POINTER(d)]
         L.dg_get_meta.argtypes = [vp, C.POINTER(Meta)]
         L.dg_set_meta.argtypes = [vp, C.POINTER(Meta)]
+        L.dg_av_param_count.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.dg_set_av_weights.argtypes = [vp, vp, C.c_size_t]
+        L.dg_get_av_weights.argtypes = [vp, vp, C.c_size_t]
+        L.dg_generate_pairs.argtypes = [vp, d, vp, vp, C.c_int64, C.POINTER(C.c_int64)]
+        L.dg_mlp_train.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(TrainOpts), C.POINTER(d)]
+        L.dg_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, C.POINTER(d)]
+        L.dg_mlp_forward.argtypes = [vp, vp, C.c_int64, vp]
+        L.dg_av_nu.argtypes = [vp, vp]
         L.dg_rhs_noalloc.argtypes = [C.POINTER(Mesh), i, d, C.POINTER(NuParams), i, vp, vp, vp, d, vp]
         L.dg_profile.argtypes = [vp, i]
         L.dg_profile_read.argtypes = [vp, C.POINTER(Prof)]
@@ -102,7 +115,8 @@ def lib() -> C.CDLL:
 EXPORTS = ("dg_scratch_bytes", "dg_vhat_bytes", "dg_init", "dg_free", "dg_last_error", "dg_set_state", "dg_get_state", "dg_rhs",
            "dg_project_velocity", "dg_step", "dg_set_forcing", "dg_set_forcing_coeffs", "dg_forcing_from_modes",
            "dg_diagnostics", "dg_l1_density", "dg_get_meta", "dg_set_meta", "dg_profile", "dg_profile_read",
-           "dg_rhs_noalloc")
+           "dg_rhs_noalloc", "dg_av_param_count", "dg_set_av_weights", "dg_get_av_weights", "dg_generate_pairs",
+           "dg_mlp_train", "dg_mlp_grad", "dg_mlp_forward", "dg_av_nu")
 
 
 class DGError(RuntimeError):

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
@@ -18,6 +19,7 @@
 
 #include "../../include/dg.h"
 #include "dg_launch.cuh"
+#include "dg_mlp.cuh"
 #include "dg_tile.cuh"
 
 using namespace dg;
@@ -456,6 +458,19 @@ struct dg_ctx {
     int64_t steps = 0;
     unsigned int status = 0;
     std::string err;
+    // learned viscosity sensor
+    float* mw = nullptr;       // FP32 master weights
+    float* mm = nullptr;       // Adam first moments
+    float* mv = nullptr;       // Adam second moments
+    float* mg = nullptr;       // gradient
+    uint32_t* mpack = nullptr; // packed BF16 inference weights
+    double* mloss = nullptr;
+    float* mwork = nullptr;
+    float* nu_cell = nullptr;  // per-cell coefficient (learned mode)
+    void* vabs = nullptr;      // per-cell |v| projection (learned mode)
+    int mlp_D = 0, mlp_P = 0;
+    long adam_t = 0;
+    bool weights_set = false;
     // profiling: events recorded around launches, resolved in dg_profile_read
     bool prof = false;
     dg_prof counts{};
@@ -478,10 +493,16 @@ struct dg_ctx {
 namespace {
 
 struct ScratchLayout {
-    size_t ctl, partials, tab, ttab, kvec, amp, total;
+    size_t ctl, partials, tab, ttab, kvec, amp;
+    size_t mw, mm, mv, mg, mpack, mloss, mwork;  // learned sensor: weights, Adam moments, grad, packed, loss, work
+    size_t nu, vabs;                             // per-cell coefficient and |v| projection (learned mode)
+    size_t total;
 };
 
-ScratchLayout scratch_layout(int K)
+constexpr int kMlpMaxParams = 64 * 40 + 64 + 64 * 64 + 64 + 64 + 1;
+constexpr int kMlpPackWords = 8192;
+
+ScratchLayout scratch_layout(int K, long ncell = 0, bool learned = false)
 {
     ScratchLayout s{};
     size_t off = 0;
@@ -497,6 +518,25 @@ ScratchLayout scratch_layout(int K)
     off = align256(off + sizeof(int) * 3 * kMaxModes);
     s.amp = off;
     off = align256(off + sizeof(double) * 6 * kMaxModes);
+    s.mw = off;
+    off = align256(off + sizeof(float) * kMlpMaxParams);
+    s.mm = off;
+    off = align256(off + sizeof(float) * kMlpMaxParams);
+    s.mv = off;
+    off = align256(off + sizeof(float) * kMlpMaxParams);
+    s.mg = off;
+    off = align256(off + sizeof(float) * kMlpMaxParams);
+    s.mpack = off;
+    off = align256(off + sizeof(uint32_t) * kMlpPackWords);
+    s.mloss = off;
+    off = align256(off + sizeof(double) * 16);
+    s.mwork = off;
+    off = align256(off + sizeof(float) * mlp_work_floats_host());
+    s.nu = off;
+    if (learned) off = align256(off + sizeof(float) * (size_t)ncell);
+    s.vabs = off;
+    const size_t b = (size_t)(K + 1) * (K + 2) * (K + 3) / 6;
+    if (learned) off = align256(off + sizeof(double) * (size_t)ncell * b);
     s.total = off;
     return s;
 }
@@ -605,6 +645,71 @@ cudaError_t project(dg_ctx* c, const void* u, void* vhat, const void* ahat, bool
     return tile(c, t);
 }
 
+// pack FP32 weights into the BF16 fragments of the fused inference kernel
+template <int D>
+void pack_mlp(const float* w, uint32_t* out)
+{
+    using PK = MlpPack<D>;
+    const MlpLayout L = MlpLayout::make(D);
+    auto bf = [](float x) { return (uint32_t)bf16_rne(x); };
+    auto frag = [&](auto Bat, int Kd, int Nd, uint32_t* dst) {
+        for (int kt = 0; kt < Kd / 16; ++kt)
+            for (int nt = 0; nt < Nd / 8; ++nt)
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int g = lane >> 2, t = lane & 3, n = nt * 8 + g, k0 = kt * 16 + 2 * t;
+                    uint32_t* o = dst + (((size_t)kt * (Nd / 8) + nt) * 32 + lane) * 2;
+                    o[0] = bf(Bat(k0, n)) | (bf(Bat(k0 + 1, n)) << 16);
+                    o[1] = bf(Bat(k0 + 8, n)) | (bf(Bat(k0 + 9, n)) << 16);
+                }
+    };
+    frag([&](int k, int n) { return k < D ? w[L.oW1 + n * D + k] : 0.0f; }, PK::KD, 64, out + PK::w1);
+    frag([&](int k, int n) { return w[L.oW2 + n * 64 + k]; }, 64, 64, out + PK::w2);
+    frag([&](int k, int n) { return n == 0 ? w[L.oW3 + k] : 0.0f; }, 64, 8, out + PK::w3);
+    float* bias = reinterpret_cast<float*>(out + PK::bias);
+    for (int j = 0; j < 64; ++j) {
+        bias[j] = w[L.ob1 + j];
+        bias[64 + j] = w[L.ob2 + j];
+    }
+    bias[128] = w[L.ob3];
+}
+
+int upload_weights(dg_ctx* ctx, const float* w_host)
+{
+    static_assert(MlpPack<40>::words <= kMlpPackWords, "pack size");
+    std::vector<uint32_t> pk(kMlpPackWords, 0u);
+    if (ctx->mlp_D == 8) pack_mlp<8>(w_host, pk.data());
+    if (ctx->mlp_D == 20) pack_mlp<20>(w_host, pk.data());
+    if (ctx->mlp_D == 40) pack_mlp<40>(w_host, pk.data());
+    CK(cudaMemcpyAsync(ctx->mw, w_host, sizeof(float) * ctx->mlp_P, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->mpack, pk.data(), sizeof(uint32_t) * kMlpPackWords, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->weights_set = true;
+    return DG_OK;
+}
+
+// learned mode: projection of |v| of u, then the per-cell coefficient nu = cs h/p exp(net(x))
+cudaError_t learned_nu(dg_ctx* c, const void* u)
+{
+    {
+        TileLaunch t{};
+        t.mode = 0;
+        t.u_in = u;
+        t.vh_out = vh_buf(c, 1);
+        t.vabs_out = c->vabs;
+        t.flags = F_VABS;
+        t.abar_out = 1;
+        cudaError_t e = tile(c, t);
+        if (e != cudaSuccess) return e;
+    }
+    Timed tm(c, KIND_OTHER);
+    Launch L = make_launch(c);
+    return (c->prec == DG_PREC_F64)
+               ? mlp_infer<double>(L, (const double*)u, (const double*)c->vabs, nullptr, c->ncell, c->mpack, c->nu_cell,
+                                   nullptr)
+               : mlp_infer<float>(L, (const float*)u, (const float*)c->vabs, nullptr, c->ncell, c->mpack, c->nu_cell,
+                                  nullptr);
+}
+
 int upload_forcing(dg_ctx* ctx)
 {
     std::vector<double> amp;
@@ -637,10 +742,9 @@ extern "C" {
 
 int dg_scratch_bytes(const dg_mesh* mesh, int order, const dg_nu_params* nu, size_t* bytes)
 {
-    (void)mesh;
-    (void)nu;
-    if (!bytes || order < 1 || order > 3) return DG_EINVAL;
-    *bytes = scratch_layout(order).total;
+    if (!bytes || !mesh || !nu || order < 1 || order > 3) return DG_EINVAL;
+    const long ncell = (long)mesh->n[0] * mesh->n[1] * mesh->n[2];
+    *bytes = scratch_layout(order, ncell, nu->mode == DG_AV_LEARNED).total;
     return DG_OK;
 }
 
@@ -674,7 +778,8 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
         if (!opts->u[i]) return DG_EINVAL;
     if (!opts->vhat || !opts->ahat || !opts->scratch) return DG_EINVAL;
     if (((uintptr_t)opts->scratch) & 255u) return DG_EINVAL;
-    ScratchLayout sl = scratch_layout(order);
+    const long ncell0 = (long)mesh->n[0] * mesh->n[0] * mesh->n[0];
+    ScratchLayout sl = scratch_layout(order, ncell0, nu->mode == DG_AV_LEARNED);
     if (opts->scratch_bytes < sl.total) return DG_ENOMEM;
 
     dg_ctx* ctx = new (std::nothrow) dg_ctx();
@@ -701,6 +806,17 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->ttab = ctx->scratch + sl.ttab;
     ctx->d_kvec = (int*)(ctx->scratch + sl.kvec);
     ctx->d_amp = (double*)(ctx->scratch + sl.amp);
+    ctx->mw = (float*)(ctx->scratch + sl.mw);
+    ctx->mm = (float*)(ctx->scratch + sl.mm);
+    ctx->mv = (float*)(ctx->scratch + sl.mv);
+    ctx->mg = (float*)(ctx->scratch + sl.mg);
+    ctx->mpack = (uint32_t*)(ctx->scratch + sl.mpack);
+    ctx->mloss = (double*)(ctx->scratch + sl.mloss);
+    ctx->mwork = (float*)(ctx->scratch + sl.mwork);
+    ctx->nu_cell = (float*)(ctx->scratch + sl.nu);
+    ctx->vabs = ctx->scratch + sl.vabs;
+    ctx->mlp_D = 2 * ctx->b;
+    ctx->mlp_P = mlp_params(ctx->mlp_D);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -782,8 +898,12 @@ int dg_rhs(dg_ctx* ctx, const void* u_in, const void* ahat, void* dudt, double d
 {
     if (!ctx) return DG_EINVAL;
     if (!u_in || !dudt) return fail(ctx, DG_EINVAL, "dg_rhs: null buffer");
+    const bool learned = ctx->nu.mode == DG_AV_LEARNED;
+    if (learned && !ctx->weights_set) return fail(ctx, DG_ESTATE, "dg_rhs: learned mode needs dg_set_av_weights");
+    if (learned) CK(learned_nu(ctx, u_in));
     CK(project(ctx, u_in, vh_buf(ctx, 0), ahat, false, 0));
     TileLaunch t{};
+    t.nu = learned ? ctx->nu_cell : nullptr;
     t.mode = 1;
     t.u_in = u_in;
     t.out = dudt;
@@ -865,6 +985,8 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
     static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
     const double* RA = ctx->rk == 2 ? A2 : A3;
     const double* RB = ctx->rk == 2 ? B2 : B3;
+    if (ctx->nu.mode == DG_AV_LEARNED && !ctx->weights_set)
+        return fail(ctx, DG_ESTATE, "dg_step: learned mode needs dg_set_av_weights");
     for (int st = 0; st < nsteps; ++st) {
         // driving schedule (Sec. 4.2): OU update at the first step with t >= t_next
         if (ctx->drv.on && ctx->drv.t_off > 0.0 && ctx->t > ctx->drv.t_off) {
@@ -903,9 +1025,12 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
             CK(cudaMemcpyAsync(&ctx->ctl->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->st));
             // stage 1 projection (+ CFL dt); later stages get theirs from the
             // previous stage's epilogue (double-buffered vhat / abar slots)
+            const bool learned = ctx->nu.mode == DG_AV_LEARNED;
+            if (learned) CK(learned_nu(ctx, ctx->reg[A]));  // once per step, cached for all stages
             CK(project(ctx, ctx->reg[A], vh_buf(ctx, 0), force ? ctx->ahat : nullptr, true, 0));
             for (int s = 0; s < ctx->rk; ++s) {
                 TileLaunch t{};
+                t.nu = learned ? ctx->nu_cell : nullptr;
                 t.mode = 2;
                 t.u_in = ctx->reg[in[s]];
                 t.u_n = ctx->reg[A];
@@ -991,6 +1116,155 @@ int dg_l1_density(dg_ctx* ctx, const void* uA, const void* uB, double* out)
                                                : launch_l1<float>(L, (const float*)uA, (const float*)uB);
     CK(e);
     CK(cudaMemcpyAsync(out, &ctx->ctl->l1, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_set_av_weights(dg_ctx* ctx, const float* w, size_t n)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!w || n != (size_t)ctx->mlp_P) return fail(ctx, DG_EINVAL, "dg_set_av_weights: need dg_av_param_count floats");
+    const int rc = upload_weights(ctx, w);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(ctx->mm, 0, sizeof(float) * ctx->mlp_P, ctx->st));
+    CK(cudaMemsetAsync(ctx->mv, 0, sizeof(float) * ctx->mlp_P, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->adam_t = 0;
+    return DG_OK;
+}
+
+int dg_get_av_weights(dg_ctx* ctx, float* w, size_t n)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!w || n != (size_t)ctx->mlp_P) return fail(ctx, DG_EINVAL, "dg_get_av_weights: bad size");
+    CK(cudaMemcpyAsync(w, ctx->mw, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_av_param_count(dg_ctx* ctx, int64_t* n)
+{
+    if (!ctx || !n) return DG_EINVAL;
+    *n = ctx->mlp_P;
+    return DG_OK;
+}
+
+int dg_mlp_forward(dg_ctx* ctx, const float* x, int64_t n, float* y)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!x || !y || n < 1) return fail(ctx, DG_EINVAL, "dg_mlp_forward: bad arguments");
+    if (!ctx->weights_set) return fail(ctx, DG_ESTATE, "dg_mlp_forward: no weights");
+    Launch L = make_launch(ctx);
+    {
+        Timed tm(ctx, KIND_OTHER);
+        CK(mlp_infer<float>(L, nullptr, nullptr, x, (long)n, ctx->mpack, nullptr, y));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_mlp_grad(dg_ctx* ctx, const float* x, const float* y, int64_t n, float* grad, double* loss)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!x || !y || !grad || !loss || n < 1 || n > kMlpBatchMax) return fail(ctx, DG_EINVAL, "dg_mlp_grad: bad arguments");
+    if (!ctx->weights_set) return fail(ctx, DG_ESTATE, "dg_mlp_grad: no weights");
+    {
+        Timed tm(ctx, KIND_OTHER);
+        CK(mlp_train_pass(ctx->st, ctx->mlp_D, ctx->mw, x, y, (int)n, ctx->mwork, ctx->mg, ctx->mloss));
+    }
+    CK(cudaMemcpyAsync(grad, ctx->mg, sizeof(float) * ctx->mlp_P, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(loss, ctx->mloss, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_mlp_train(dg_ctx* ctx, const float* x, const float* y, int64_t n, const dg_train_opts* o, double* loss_out)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!x || !y || !o || n < 1 || o->batch < 1 || o->batch > kMlpBatchMax || o->epochs < 1)
+        return fail(ctx, DG_EINVAL, "dg_mlp_train: bad arguments");
+    if (!ctx->weights_set) return fail(ctx, DG_ESTATE, "dg_mlp_train: initialise the weights first");
+    const int D = ctx->mlp_D;
+    double last = 0.0;
+    std::vector<double> losses;
+    for (int ep = 0; ep < o->epochs; ++ep) {
+        losses.clear();
+        for (int64_t s0 = 0; s0 < n; s0 += o->batch) {
+            const int nb = (int)std::min<int64_t>(o->batch, n - s0);
+            CK(mlp_train_pass(ctx->st, D, ctx->mw, x + s0 * D, y + s0, nb, ctx->mwork, ctx->mg, ctx->mloss));
+            ctx->adam_t += 1;
+            const float c1 = (float)(1.0 / (1.0 - std::pow(o->beta1, (double)ctx->adam_t)));
+            const float c2 = (float)(1.0 / (1.0 - std::pow(o->beta2, (double)ctx->adam_t)));
+            CK(mlp_adam(ctx->st, ctx->mlp_P, ctx->mw, ctx->mg, ctx->mm, ctx->mv, (float)o->lr, (float)o->beta1,
+                        (float)o->beta2, (float)o->eps, c1, c2));
+            double l = 0.0;
+            CK(cudaMemcpyAsync(&l, ctx->mloss, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            losses.push_back(l);
+        }
+        double sum = 0.0;
+        for (double l : losses) sum += l;
+        last = sum / losses.size();
+    }
+    // refresh the packed inference weights from the trained master copy
+    std::vector<float> w(ctx->mlp_P);
+    CK(cudaMemcpyAsync(w.data(), ctx->mw, sizeof(float) * ctx->mlp_P, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const int rc = upload_weights(ctx, w.data());
+    if (rc) return rc;
+    if (loss_out) *loss_out = last;
+    return DG_OK;
+}
+
+int dg_generate_pairs(dg_ctx* ctx, double dt_for_pimax, float* x, float* y, int64_t cap, int64_t* n_out)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!x || !y || !n_out) return fail(ctx, DG_EINVAL, "dg_generate_pairs: null buffer");
+    if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_generate_pairs: no state set");
+    if (cap < ctx->ncell) return fail(ctx, DG_ENOMEM, "dg_generate_pairs: cap < number of cells");
+    if (ctx->nu.mode != DG_AV_LEARNED)
+        return fail(ctx, DG_EINVAL, "dg_generate_pairs: needs a context created in DG_AV_LEARNED mode");
+    const void* u = ctx->reg[ctx->cur];
+    TileLaunch t{};
+    t.mode = 0;
+    t.u_in = u;
+    t.vh_out = vh_buf(ctx, 1);
+    t.vabs_out = ctx->vabs;
+    t.flags = F_VABS;
+    t.abar_out = 1;
+    CK(tile(ctx, t));
+    Launch L = make_launch(ctx);
+    {
+        Timed tm(ctx, KIND_OTHER);
+        const char* tt = (const char*)ctx->ttab;
+        if (ctx->prec == DG_PREC_F64) {
+            const double* phiv = (const double*)tt + (ctx->K == 1   ? TileTab<1, BK_FMA>::phiv
+                                                      : ctx->K == 2 ? TileTab<2, BK_FMA>::phiv
+                                                                    : TileTab<3, BK_FMA>::phiv);
+            CK(launch_features<double>(L, (const double*)u, (const double*)ctx->vabs, phiv, dt_for_pimax, x, y));
+        } else {
+            const bool x3 = ctx->prec == DG_PREC_X3;
+            const int off = ctx->K == 1 ? (x3 ? TileTab<1, BK_X3>::phiv : TileTab<1, BK_FMA>::phiv)
+                            : ctx->K == 2 ? (x3 ? TileTab<2, BK_X3>::phiv : TileTab<2, BK_FMA>::phiv)
+                                          : (x3 ? TileTab<3, BK_X3>::phiv : TileTab<3, BK_FMA>::phiv);
+            const float* phiv = (const float*)tt + off;
+            CK(launch_features<float>(L, (const float*)u, (const float*)ctx->vabs, phiv, dt_for_pimax, x, y));
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    *n_out = ctx->ncell;
+    return DG_OK;
+}
+
+int dg_av_nu(dg_ctx* ctx, float* nu_out)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!nu_out) return fail(ctx, DG_EINVAL, "dg_av_nu: null buffer");
+    if (ctx->nu.mode != DG_AV_LEARNED || !ctx->weights_set)
+        return fail(ctx, DG_ESTATE, "dg_av_nu: needs learned mode with weights");
+    if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_av_nu: no state set");
+    CK(learned_nu(ctx, ctx->reg[ctx->cur]));
+    CK(cudaMemcpyAsync(nu_out, ctx->nu_cell, sizeof(float) * ctx->ncell, cudaMemcpyDeviceToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return DG_OK;
 }

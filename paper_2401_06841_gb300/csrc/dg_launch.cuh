@@ -41,6 +41,8 @@ struct TileLaunch {
     double dt_pimax;
     int flags;
     int abar_in, abar_out;
+    const float* nu;     // learned sensor: per-cell coefficient
+    void* vabs_out;      // learned sensor: projection of |v|
 };
 template <typename T>
 cudaError_t launch_tile(const Launch& L, const TileLaunch& t);
@@ -50,5 +52,20 @@ template <typename T>
 cudaError_t launch_diag(const Launch& L, const T* u, const T* ahat, double dt_pimax, int flags);
 template <typename T>
 cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB);
+
+// learned viscosity sensor
+constexpr int kMlpHidden = 64;
+constexpr int kMlpBatchMax = 4096;
+inline int mlp_params(int D) { return kMlpHidden * D + kMlpHidden + kMlpHidden * kMlpHidden + 2 * kMlpHidden + 1; }
+inline size_t mlp_work_floats_host() { return (size_t)6 * kMlpHidden * kMlpBatchMax + kMlpBatchMax; }
+cudaError_t mlp_train_pass(cudaStream_t st, int D, const float* W, const float* X, const float* Y, int n, float* work,
+                           float* G, double* loss);
+cudaError_t mlp_adam(cudaStream_t st, int P, float* W, const float* G, float* m, float* v, float lr, float b1, float b2,
+                     float eps, float c1, float c2);
+template <typename T>
+cudaError_t mlp_infer(const Launch& L, const T* u, const T* vabs, const float* X, long n, const uint32_t* packed,
+                      float* nu, float* y);
+template <typename T>
+cudaError_t launch_features(const Launch& L, const T* u, const T* vabs, const T* phiv, double dt, float* X, float* Y);
 
 }  // namespace dg

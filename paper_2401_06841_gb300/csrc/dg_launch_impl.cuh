@@ -106,6 +106,8 @@ static cudaError_t tile_kb(const Launch& L, const TileLaunch& t)
     a.flags = t.flags;
     a.abar_in = t.abar_in;
     a.abar_out = t.abar_out;
+    a.nu = t.nu;
+    a.vabs_out = static_cast<T*>(t.vabs_out);
     using Cf = TileCfg<K, BK>;
     const long ntile = (L.ncell + Cf::TC - 1) / Cf::TC;
     const size_t sm = sizeof(T) * Cf::total;

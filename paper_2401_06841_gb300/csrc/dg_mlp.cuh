@@ -1,0 +1,397 @@
+// dg_mlp.cuh -- learned viscosity sensor: a per-cell network
+//   y = W3 . gelu(W2 gelu(W1 x + b1) + b2) + b3,   gelu(z) = z/2 (1 + erf(z/sqrt 2))
+// predicting y = log(nu / (cs h/p)) from x = (rho_l/rho_0, |v|hat_l/cs), the
+// normalised modal coefficients of the cell (D = 2b inputs, 64 hidden units).
+// Training runs in FP32 on the CUDA cores (forward with stored activations,
+// backward, per-parameter gradient sums in a fixed order, Adam); inference is
+// one fused kernel with BF16 tensor-core products and FP32 accumulation, the
+// accumulator fragments of a layer feeding the next layer's operand fragments
+// directly in registers.
+//
+// Parameter layout (FP32): W1 [64][D], b1 [64], W2 [64][64], b2 [64], W3 [64], b3.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "dg_tile.cuh"
+
+namespace dg {
+
+constexpr int MLP_H = 64;
+constexpr int MLP_BMAX = 4096;  // largest training batch
+
+struct MlpLayout {
+    int D, P, oW1, ob1, oW2, ob2, oW3, ob3;
+    __host__ __device__ static MlpLayout make(int D)
+    {
+        MlpLayout L{};
+        L.D = D;
+        L.oW1 = 0;
+        L.ob1 = MLP_H * D;
+        L.oW2 = L.ob1 + MLP_H;
+        L.ob2 = L.oW2 + MLP_H * MLP_H;
+        L.oW3 = L.ob2 + MLP_H;
+        L.ob3 = L.oW3 + MLP_H;
+        L.P = L.ob3 + 1;
+        return L;
+    }
+};
+
+// training work arrays, each [64][MLP_BMAX] (sample index fastest) plus r [MLP_BMAX]
+enum { MW_Z1 = 0, MW_A1 = 1, MW_Z2 = 2, MW_A2 = 3, MW_DZ1 = 4, MW_DZ2 = 5, MW_R = 6 };
+constexpr size_t mlp_work_floats() { return (size_t)6 * MLP_H * MLP_BMAX + MLP_BMAX; }
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_prime_f(float z)
+{
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// forward pass of a batch, one thread per sample; stores z1, a1, z2, a2, r = y^ - y
+template <int D>
+__global__ void __launch_bounds__(128) k_mlp_fwd(const float* __restrict__ W, const float* __restrict__ X,
+                                                 const float* __restrict__ Y, int n, float* __restrict__ work)
+{
+    const MlpLayout L = MlpLayout::make(D);
+    extern __shared__ float sW[];
+    for (int e = threadIdx.x; e < L.P; e += blockDim.x) sW[e] = W[e];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) x[d] = X[(size_t)i * D + d];
+    float a1[MLP_H];
+#pragma unroll 4
+    for (int j = 0; j < MLP_H; ++j) {
+        float z = sW[L.ob1 + j];
+#pragma unroll
+        for (int d = 0; d < D; ++d) z += sW[L.oW1 + j * D + d] * x[d];
+        a1[j] = gelu_f(z);
+        work[(size_t)MW_Z1 * MLP_H * MLP_BMAX + (size_t)j * MLP_BMAX + i] = z;
+        work[(size_t)MW_A1 * MLP_H * MLP_BMAX + (size_t)j * MLP_BMAX + i] = a1[j];
+    }
+    float y = sW[L.ob3];
+#pragma unroll 4
+    for (int j = 0; j < MLP_H; ++j) {
+        float z = sW[L.ob2 + j];
+#pragma unroll
+        for (int k = 0; k < MLP_H; ++k) z += sW[L.oW2 + j * MLP_H + k] * a1[k];
+        const float a = gelu_f(z);
+        work[(size_t)MW_Z2 * MLP_H * MLP_BMAX + (size_t)j * MLP_BMAX + i] = z;
+        work[(size_t)MW_A2 * MLP_H * MLP_BMAX + (size_t)j * MLP_BMAX + i] = a;
+        y += sW[L.oW3 + j] * a;
+    }
+    work[(size_t)6 * MLP_H * MLP_BMAX + i] = y - Y[i];
+}
+
+// backward pass, one thread per sample: dz2 = (2 r / n) W3 gelu'(z2),
+// dz1 = (W2^T dz2) gelu'(z1)
+template <int D>
+__global__ void __launch_bounds__(128) k_mlp_bwd(const float* __restrict__ W, int n, float* __restrict__ work)
+{
+    const MlpLayout L = MlpLayout::make(D);
+    extern __shared__ float sW[];
+    for (int e = threadIdx.x; e < L.P; e += blockDim.x) sW[e] = W[e];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float d3 = 2.0f * work[(size_t)6 * MLP_H * MLP_BMAX + i] / (float)n;
+    float dz2[MLP_H];
+#pragma unroll
+    for (int j = 0; j < MLP_H; ++j) {
+        const float z = work[(size_t)MW_Z2 * MLP_H * MLP_BMAX + (size_t)j * MLP_BMAX + i];
+        dz2[j] = d3 * sW[L.oW3 + j] * gelu_prime_f(z);
+        work[(size_t)MW_DZ2 * MLP_H * MLP_BMAX + (size_t)j * MLP_BMAX + i] = dz2[j];
+    }
+#pragma unroll 4
+    for (int k = 0; k < MLP_H; ++k) {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < MLP_H; ++j) s += sW[L.oW2 + j * MLP_H + k] * dz2[j];
+        const float z = work[(size_t)MW_Z1 * MLP_H * MLP_BMAX + (size_t)k * MLP_BMAX + i];
+        work[(size_t)MW_DZ1 * MLP_H * MLP_BMAX + (size_t)k * MLP_BMAX + i] = s * gelu_prime_f(z);
+    }
+}
+
+// gradient of the batch loss, one thread per parameter (fixed summation
+// order over the samples, FP64 accumulation); the extra thread P writes the
+// mean squared error
+template <int D>
+__global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ X, int n, const float* __restrict__ work,
+                                                  float* __restrict__ G, double* __restrict__ loss)
+{
+    const MlpLayout L = MlpLayout::make(D);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > L.P) return;
+    const float* R = work + (size_t)6 * MLP_H * MLP_BMAX;
+    double acc = 0.0;
+    if (p == L.P) {
+        for (int i = 0; i < n; ++i) acc += (double)R[i] * (double)R[i];
+        *loss = acc / n;
+        return;
+    }
+    auto row = [&](int which, int j) { return work + ((size_t)which * MLP_H + j) * MLP_BMAX; };
+    if (p < L.ob1) {
+        const int j = p / D, d = p % D;
+        const float* dz = row(MW_DZ1, j);
+        for (int i = 0; i < n; ++i) acc += (double)dz[i] * (double)X[(size_t)i * D + d];
+    } else if (p < L.oW2) {
+        const float* dz = row(MW_DZ1, p - L.ob1);
+        for (int i = 0; i < n; ++i) acc += (double)dz[i];
+    } else if (p < L.ob2) {
+        const int j = (p - L.oW2) / MLP_H, k = (p - L.oW2) % MLP_H;
+        const float* dz = row(MW_DZ2, j);
+        const float* a = row(MW_A1, k);
+        for (int i = 0; i < n; ++i) acc += (double)dz[i] * (double)a[i];
+    } else if (p < L.oW3) {
+        const float* dz = row(MW_DZ2, p - L.ob2);
+        for (int i = 0; i < n; ++i) acc += (double)dz[i];
+    } else if (p < L.ob3) {
+        const float* a = row(MW_A2, p - L.oW3);
+        for (int i = 0; i < n; ++i) acc += 2.0 * (double)R[i] / n * (double)a[i];
+    } else {
+        for (int i = 0; i < n; ++i) acc += 2.0 * (double)R[i] / n;
+    }
+    G[p] = (float)acc;
+}
+
+// Adam (Kingma & Ba 2015) with bias corrections c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+static __global__ void k_mlp_adam(float* __restrict__ W, const float* __restrict__ G, float* __restrict__ m,
+                           float* __restrict__ v, int P, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const float g = G[p];
+    const float mm = b1 * m[p] + (1.0f - b1) * g;
+    const float vv = b2 * v[p] + (1.0f - b2) * g * g;
+    m[p] = mm;
+    v[p] = vv;
+    W[p] -= lr * (mm * c1) / (sqrtf(vv * c2) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// fused inference: one warp per 16 samples, three BF16 mma.sync layers
+// packed weights: B1 = W1^T [KD][64], B2 = W2^T [64][64], B3 = W3 as [64][8]
+// (column 0), each as fragments [K/16][N/8][32 lanes][2 words], then b1, b2, b3
+// ---------------------------------------------------------------------------
+template <int D>
+struct MlpPack {
+    static constexpr int KD = r16(D);
+    static constexpr int w1 = 0;                              // words
+    static constexpr int w2 = w1 + (KD / 16) * 8 * 64;
+    static constexpr int w3 = w2 + 4 * 8 * 64;
+    static constexpr int bias = w3 + 4 * 1 * 64;              // floats b1[64], b2[64], b3
+    static constexpr int words = bias + 2 * MLP_H + 1;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// x(r, k): FROMSTATE reads the cell's state (rho_l/rho_0) and |v|hat/cs,
+// otherwise an explicit feature matrix X [n][D]
+template <typename T, int K, bool FROMSTATE>
+__global__ void __launch_bounds__(256) k_mlp_infer(const T* __restrict__ u, const T* __restrict__ vabs,
+                                                   const float* __restrict__ X, long n,
+                                                   const uint32_t* __restrict__ packed, float cs, float ref,
+                                                   float* __restrict__ nu_out, float* __restrict__ y_out)
+{
+    constexpr int b = Dims<K>::b, D = 2 * b;
+    using PK = MlpPack<D>;
+    constexpr int KT1 = PK::KD / 16;
+    __shared__ uint32_t sP[PK::words];
+    for (int e = threadIdx.x; e < PK::words; e += blockDim.x) sP[e] = packed[e];
+    __syncthreads();
+    const uint2* B1 = reinterpret_cast<const uint2*>(sP + PK::w1);
+    const uint2* B2 = reinterpret_cast<const uint2*>(sP + PK::w2);
+    const uint2* B3 = reinterpret_cast<const uint2*>(sP + PK::w3);
+    const float* bias = reinterpret_cast<const float*>(sP + PK::bias);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float inv_cs = 1.0f / cs;
+    auto feat = [&](long r, int k) -> float {
+        if (r >= n || k >= D) return 0.0f;
+        if constexpr (FROMSTATE) {
+            if (k < b) return (float)(u[r * 4 * b + k] / u[r * 4 * b]);
+            return (float)vabs[r * b + (k - b)] * inv_cs;
+        } else {
+            return X[r * D + k];
+        }
+    };
+    const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long base = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * 16; base < n; base += nwarps * 16) {
+        const long r0 = base + g, r1 = base + g + 8;
+        float acc1[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc1[j][0] = acc1[j][1] = acc1[j][2] = acc1[j][3] = 0.f;
+#pragma unroll
+        for (int kt = 0; kt < KT1; ++kt) {
+            const int k0 = kt * 16 + 2 * t;
+            uint32_t A[4];
+            A[0] = pack_bf16x2(feat(r0, k0), feat(r0, k0 + 1));
+            A[1] = pack_bf16x2(feat(r1, k0), feat(r1, k0 + 1));
+            A[2] = pack_bf16x2(feat(r0, k0 + 8), feat(r0, k0 + 9));
+            A[3] = pack_bf16x2(feat(r1, k0 + 8), feat(r1, k0 + 9));
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const uint2 bw = B1[(kt * 8 + nt) * 32 + lane];
+                mma_bf16(acc1[nt], A, bw.x, bw.y);
+            }
+        }
+        // bias + GELU; the m16n8 accumulator tiles 2j, 2j+1 form the A operand of k-chunk j
+        uint32_t A2[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float h[2][4];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int nt = 2 * j + s, c = nt * 8 + 2 * t;
+                h[s][0] = gelu_f(acc1[nt][0] + bias[c]);
+                h[s][1] = gelu_f(acc1[nt][1] + bias[c + 1]);
+                h[s][2] = gelu_f(acc1[nt][2] + bias[c]);
+                h[s][3] = gelu_f(acc1[nt][3] + bias[c + 1]);
+            }
+            A2[j][0] = pack_bf16x2(h[0][0], h[0][1]);
+            A2[j][1] = pack_bf16x2(h[0][2], h[0][3]);
+            A2[j][2] = pack_bf16x2(h[1][0], h[1][1]);
+            A2[j][3] = pack_bf16x2(h[1][2], h[1][3]);
+        }
+        float acc2[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const uint2 bw = B2[(kt * 8 + nt) * 32 + lane];
+                mma_bf16(acc2[nt], A2[kt], bw.x, bw.y);
+            }
+        uint32_t A3[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float h[2][4];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int nt = 2 * j + s, c = MLP_H + nt * 8 + 2 * t;
+                h[s][0] = gelu_f(acc2[nt][0] + bias[c]);
+                h[s][1] = gelu_f(acc2[nt][1] + bias[c + 1]);
+                h[s][2] = gelu_f(acc2[nt][2] + bias[c]);
+                h[s][3] = gelu_f(acc2[nt][3] + bias[c + 1]);
+            }
+            A3[j][0] = pack_bf16x2(h[0][0], h[0][1]);
+            A3[j][1] = pack_bf16x2(h[0][2], h[0][3]);
+            A3[j][2] = pack_bf16x2(h[1][0], h[1][1]);
+            A3[j][3] = pack_bf16x2(h[1][2], h[1][3]);
+        }
+        float acc3[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const uint2 bw = B3[kt * 32 + lane];
+            mma_bf16(acc3, A3[kt], bw.x, bw.y);
+        }
+        if (t == 0) {
+            const float b3 = bias[2 * MLP_H];
+            const float y0 = acc3[0] + b3, y1 = acc3[2] + b3;
+            if (r0 < n) {
+                if (nu_out) nu_out[r0] = ref * expf(y0);
+                if (y_out) y_out[r0] = y0;
+            }
+            if (r1 < n) {
+                if (nu_out) nu_out[r1] = ref * expf(y1);
+                if (y_out) y_out[r1] = y1;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// features and labels of the learned sensor for every cell (thread per
+// (cell, point)): x = (rho_l/rho_0, |v|hat_l/cs), y = log(max(nu_cell,
+// nu_f)/ref), nu_cell = max over compressive points of Pi_vNR/(rho |div v|),
+// nu_f = max(beta, 0.05) ref the coefficient of the linear term
+// ---------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(Tile<K>::NT) k_features(const T* __restrict__ u, const T* __restrict__ vabs,
+                                                          const T* __restrict__ phiv, long ncell, Phys ph, double dt,
+                                                          float* __restrict__ X, float* __restrict__ Y)
+{
+    using Dm = Dims<K>;
+    constexpr int b = Dm::b, nq = Dm::nq, TC = Tile<K>::TC, NT = Tile<K>::NT, EC = 12;
+    __shared__ T s_u[TC][4][b];
+    __shared__ T s_ec[TC][b][EC];
+    __shared__ T s_phi[b * nq];  // basis at the volume points [b][nq]
+    __shared__ int s_max[TC];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < b * nq; e += NT) s_phi[e] = phiv[e];
+    const T two_h = T(2.0 / ph.h);
+    const float ref = (float)(ph.cs * ph.hp);
+    const long ntile = (ncell + TC - 1) / TC;
+    for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const long c0 = tile * TC;
+        for (int e = tid; e < TC * 4 * b; e += NT) {
+            const long c = c0 + e / (4 * b);
+            (&s_u[0][0][0])[e] = (c < ncell) ? u[c0 * 4 * b + e] : ((e % (4 * b)) == 0 ? T(1) : T(0));
+        }
+        if (tid < TC) s_max[tid] = 0;
+        __syncthreads();
+        for (int e = tid; e < TC * 5; e += NT) {
+            const int lc = e / 5, g = e % 5;
+            const T* uu = &s_u[lc][0][0];
+            T out[b];
+            if (g == 0) {
+                for (int l = 0; l < b; ++l)
+                    for (int v = 0; v < 4; ++v) s_ec[lc][l][v] = uu[v * b + l];
+                continue;
+            }
+            if (g == 1) modal_grad<T, K, 0>(uu, out, two_h);
+            if (g == 2) modal_grad<T, K, 1>(uu, out, two_h);
+            if (g == 3) modal_grad<T, K, 2>(uu, out, two_h);
+            if (g == 4) {
+                T t2[b];
+                modal_grad<T, K, 0>(uu + b, out, two_h);
+                modal_grad<T, K, 1>(uu + 2 * b, t2, two_h);
+                for (int l = 0; l < b; ++l) out[l] += t2[l];
+                modal_grad<T, K, 2>(uu + 3 * b, t2, two_h);
+                for (int l = 0; l < b; ++l) out[l] += t2[l];
+            }
+            for (int l = 0; l < b; ++l) s_ec[lc][l][3 + g] = out[l];
+        }
+        __syncthreads();
+        {
+            const int lc = tid / nq, q = tid % nq;
+            T f[8];
+            for (int i = 0; i < 8; ++i) f[i] = T(0);
+            for (int l = 0; l < b; ++l) {
+                const T p = s_phi[l * nq + q];
+                for (int i = 0; i < 8; ++i) f[i] += s_ec[lc][l][i] * p;
+            }
+            const T rho = f[0], vx = f[1] / rho, vy = f[2] / rho, vz = f[3] / rho;
+            const T divv = (f[7] - (vx * f[4] + vy * f[5] + vz * f[6])) / rho;
+            if (divv < T(0)) {
+                const T Pi = vnr_pressure<T>(ph, rho, divv, T(dt));
+                const float nuq = (float)(Pi / (rho * (-divv)));
+                atomicMax(&s_max[lc], __float_as_int(nuq));  // positive floats order like ints
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < TC * 2 * b; e += NT) {
+            const int lc = e / (2 * b), k = e % (2 * b);
+            const long c = c0 + lc;
+            if (c >= ncell) continue;
+            X[c * 2 * b + k] = (k < b) ? (float)(s_u[lc][0][k] / s_u[lc][0][0])
+                                       : (float)(vabs[c * b + (k - b)] / T(ph.cs));
+        }
+        for (int lc = tid; lc < TC; lc += NT) {
+            const long c = c0 + lc;
+            if (c >= ncell) continue;
+            const float nu = __int_as_float(s_max[lc]);
+            const float fl = fmaxf((float)ph.beta, 0.05f) * ref;
+            Y[c] = logf(fmaxf(nu, fl) / ref);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace dg

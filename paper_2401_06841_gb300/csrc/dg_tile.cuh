@@ -371,7 +371,7 @@ __device__ __forceinline__ void expand_acc(const T* L2, int side, T scale, T* R)
 }
 
 enum { TM_PROJECT = 0, TM_RHS = 1, TM_STAGE = 2 };
-enum { F_NEXTPROJ = 4 };
+enum { F_NEXTPROJ = 4, F_VABS = 8 };
 
 template <typename T>
 struct TArgs {
@@ -392,15 +392,33 @@ struct TArgs {
     int flags;         // F_DT | F_FORCE | F_NEXTPROJ
     int abar_in;       // slot of ctl->abar2 read by this stage
     int abar_out;      // slot written by the projection
+    const float* nu;   // per-cell viscous coefficient (learned sensor) or nullptr
+    T* vabs_out;       // projection of |v| (F_VABS) [c][b]
 };
+
+// viscous pressure with a per-cell coefficient (learned sensor):
+// Pi = rho nu |div v| for div v < 0, capped like the vNR form (Sec. 3.1)
+template <typename T>
+__device__ __forceinline__ T nu_pressure(const Phys& P, T rho, T divv, T nu, T dt)
+{
+    if (!(divv < T(0))) return T(0);
+    const T a = -divv, hp = T(P.hp);
+    T Pi = rho * nu * a;
+    if (dt > T(0)) {
+        const T Pmax = T(0.5) * rho * hp * hp * a / dt;
+        Pi = Pi < Pmax ? Pi : Pmax;
+    }
+    return Pi;
+}
 
 // --------------------------------------------------------------------------
 // projection of the primitive velocity of the TC states in sU (Sec. 3.2),
 // the per-cell forcing sums <rho a_h> = sum_l rho_l a_l and the CFL maximum
 // --------------------------------------------------------------------------
-template <typename T, int K, int BK>
+template <typename T, int K, int BK, bool VABS = false>
 __device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, bool dt_flag, T& smax, double* sums)
 {
+    constexpr int NPR = VABS ? 4 : 3;  // projected rows per cell: v (and |v|)
     using C = TileCfg<K, BK>;
     constexpr int b = C::b, nq = C::nq, TC = C::TC, NT = C::NT, KP = C::KP, NQP = C::NQP, NP = C::NP;
     constexpr int LDA = C::LDA, LDV = C::LDV, LDP = C::LDP;
@@ -418,11 +436,12 @@ __device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, 
     __syncthreads();
     // v = m / rho at the volume points; rows (cell, i) of the projection input
     constexpr int PER = (TC * NQP + NT - 1) / NT;
-    T vv[PER][3];
+    T vv[PER][NPR];
 #pragma unroll
     for (int it = 0; it < PER; ++it) {
         const int e = threadIdx.x + it * NT;
-        vv[it][0] = vv[it][1] = vv[it][2] = T(0);
+#pragma unroll
+        for (int i = 0; i < NPR; ++i) vv[it][i] = T(0);
         if (e < TC * NQP) {
             const int c = e / NQP, q = e % NQP;
             if (q < nq) {
@@ -431,6 +450,8 @@ __device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, 
                 vv[it][0] = v[LDV] * ir;
                 vv[it][1] = v[2 * LDV] * ir;
                 vv[it][2] = v[3 * LDV] * ir;
+                if constexpr (VABS)
+                    vv[it][NPR - 1] = sqrt(vv[it][0] * vv[it][0] + vv[it][1] * vv[it][1] + vv[it][2] * vv[it][2]);
                 if (dt_flag && c0 + c < a.ncell) {
                     const T sp = fabs(vv[it][0]) + fabs(vv[it][1]) + fabs(vv[it][2]);
                     smax = sp > smax ? sp : smax;
@@ -444,19 +465,23 @@ __device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, 
         const int e = threadIdx.x + it * NT;
         if (e < TC * NQP) {
             const int c = e / NQP, q = e % NQP;
-            T* f = sV + (c * 3) * LDV + q;
-            f[0] = vv[it][0];
-            f[LDV] = vv[it][1];
-            f[2 * LDV] = vv[it][2];
+            T* f = sV + (c * NPR) * LDV + q;
+#pragma unroll
+            for (int i = 0; i < NPR; ++i) f[i * LDV] = vv[it][i];
         }
     }
     __syncthreads();
-    mm<T, BK, TC * 3, NP, NQP, LDV, LDP, NT>(sV, sm, C::oWPhi, sP);
+    mm<T, BK, TC * NPR, NP, NQP, LDV, LDP, NT>(sV, sm, C::oWPhi, sP);
     __syncthreads();
     for (int e = threadIdx.x; e < TC * 3 * b; e += NT) {
-        const int r = e / b, l = e % b;
-        const long c = c0 + r / 3;
-        if (c < a.ncell) a.vh_out[c0 * 3 * b + e] = sP[r * LDP + l];
+        const int r = e / b, l = e % b, c = r / 3, i = r % 3;
+        if (c0 + c < a.ncell) a.vh_out[c0 * 3 * b + e] = sP[(c * NPR + i) * LDP + l];
+    }
+    if constexpr (VABS) {
+        for (int e = threadIdx.x; e < TC * b; e += NT) {
+            const int c = e / b, l = e % b;
+            if (c0 + c < a.ncell) a.vabs_out[c0 * b + e] = sP[(c * NPR + 3) * LDP + l];
+        }
     }
     if (a.flags & F_FORCE) {
         // the tile's a_h staged in the (free) own-velocity buffer
@@ -502,6 +527,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     T* sA = sm + C::oA;
     T* sP = sm + C::oP;
     T* sBig = sm + C::oBig;
+    __shared__ T s_nu[TC];
     __shared__ int s_flag[TC];
     __shared__ float s_minf[TC];
     __shared__ double s_mind[TC];
@@ -550,10 +576,14 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
         }
         if constexpr (MODE == TM_PROJECT) {
             __syncthreads();
-            tile_project<T, K, BK>(sm, a, c0, (a.flags & F_DT) != 0, smax, sums);
+            if (a.flags & F_VABS)
+                tile_project<T, K, BK, true>(sm, a, c0, (a.flags & F_DT) != 0, smax, sums);
+            else
+                tile_project<T, K, BK, false>(sm, a, c0, (a.flags & F_DT) != 0, smax, sums);
             __syncthreads();
             continue;
         } else {
+            if (tid < TC) s_nu[tid] = (a.ph.av_mode == 2 && tid < nvalid) ? T(a.nu[c0 + tid]) : T(0);
             for (int e = 4 * tid; e < TC * 3 * b; e += 4 * NT) {
                 T v[4];
                 ld4_guard<T>(a.vh_in + c0 * 3 * b, e, (int)nvalid * 3 * b, v);
@@ -621,7 +651,10 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                         const T vx = mx * ir, vy = my * ir, vz = mz * ir;
                         const T divv = (v[7 * LDV] - (vx * v[4 * LDV] + vy * v[5 * LDV] + vz * v[6 * LDV])) * ir;
                         T Pi = T(0);
-                        if (a.ph.av_mode == 1) Pi = vnr_pressure<T>(a.ph, rho, divv, dt);
+                        if (a.ph.av_mode == 1)
+                            Pi = vnr_pressure<T>(a.ph, rho, divv, dt);
+                        else if (a.ph.av_mode == 2)
+                            Pi = nu_pressure<T>(a.ph, rho, divv, s_nu[c], dt);
                         const T P = cs2 * rho + Pi;
                         fl[it][0] = mx * vx + P;
                         fl[it][1] = my * vy + P;

@@ -177,3 +177,59 @@ class Solver:
         p = B.Prof()
         self._check(self.L.dg_profile_read(self.h, C.byref(p)), self.h)
         return {f: getattr(p, f) for f, _ in B.Prof._fields_}
+
+    # ---- learned viscosity sensor ------------------------------------------
+    def av_param_count(self) -> int:
+        n = C.c_int64(0)
+        self._check(self.L.dg_av_param_count(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def set_av_weights(self, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+        self._check(self.L.dg_set_av_weights(self.h, w.ctypes.data, w.size), self.h)
+
+    def get_av_weights(self) -> np.ndarray:
+        w = np.zeros(self.av_param_count(), dtype=np.float32)
+        self._check(self.L.dg_get_av_weights(self.h, w.ctypes.data, w.size), self.h)
+        return w
+
+    def generate_pairs(self, dt_pimax: float = 0.0):
+        D = 2 * self.b
+        x = torch.empty(self.ncell, D, dtype=torch.float32, device=self.device)
+        y = torch.empty(self.ncell, dtype=torch.float32, device=self.device)
+        n = C.c_int64(0)
+        torch.cuda.current_stream(self.device).synchronize()
+        self._check(self.L.dg_generate_pairs(self.h, dt_pimax, x.data_ptr(), y.data_ptr(), self.ncell, C.byref(n)),
+                    self.h)
+        return x, y
+
+    def mlp_train(self, x, y, epochs: int = 10, batch: int = 4096, lr: float = 1e-3) -> float:
+        x = torch.as_tensor(x, dtype=torch.float32, device=self.device).contiguous()
+        y = torch.as_tensor(y, dtype=torch.float32, device=self.device).contiguous()
+        o = B.TrainOpts(lr, 0.9, 0.999, 1e-8, batch, epochs)
+        loss = C.c_double(0)
+        torch.cuda.current_stream(self.device).synchronize()
+        self._check(self.L.dg_mlp_train(self.h, x.data_ptr(), y.data_ptr(), len(y), C.byref(o), C.byref(loss)), self.h)
+        return loss.value
+
+    def mlp_grad(self, x, y):
+        x = torch.as_tensor(x, dtype=torch.float32, device=self.device).contiguous()
+        y = torch.as_tensor(y, dtype=torch.float32, device=self.device).contiguous()
+        g = torch.empty(self.av_param_count(), dtype=torch.float32, device=self.device)
+        loss = C.c_double(0)
+        torch.cuda.current_stream(self.device).synchronize()
+        self._check(self.L.dg_mlp_grad(self.h, x.data_ptr(), y.data_ptr(), len(y), g.data_ptr(), C.byref(loss)),
+                    self.h)
+        return loss.value, g
+
+    def mlp_forward(self, x):
+        x = torch.as_tensor(x, dtype=torch.float32, device=self.device).contiguous()
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=self.device)
+        torch.cuda.current_stream(self.device).synchronize()
+        self._check(self.L.dg_mlp_forward(self.h, x.data_ptr(), x.shape[0], y.data_ptr()), self.h)
+        return y
+
+    def av_nu(self):
+        nu = torch.empty(self.ncell, dtype=torch.float32, device=self.device)
+        self._check(self.L.dg_av_nu(self.h, nu.data_ptr()), self.h)
+        return nu
