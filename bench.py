@@ -1,16 +1,26 @@
-"""Throughput benchmark: DOF-updates per second per SSP-RK stage.
+"""Throughput benchmark: DOF-updates per second per SSP-RK stage, mixed /
+learned variants vs plain FP32 at fixed L1 error.
 
-Workload (default): 64^3 cells, degree k=3 (20 modes x 4 fields), SSP-RK3,
-isothermal cs=1, vNR artificial viscosity (alpha=2, beta=0.2), OU driving at
-Mach 3 (zeta=0.5, seed 0).  The timed state is synthetic driven turbulence:
-a Gaussian random velocity field with E(k) ~ k^-2 at Mach 3 (seed 102, exact
-Legendre coefficients), rho = 1, relaxed by the method itself for a few
-untimed steps so that shocks and density contrasts form.
+Workload: 64^3 cells, degree k=3 (20 modes x 4 fields = 20,971,520 DOF),
+SSP-RK3, isothermal cs=1, CFL 0.3, vNR artificial viscosity (alpha=2,
+beta=0.2), Rusanov faces, OU driving at Mach 3 (|k| in [1,3], zeta=0.5,
+seed 0).  The timed state is synthetic driven turbulence: a Gaussian random
+velocity field with E(k) ~ k^-2 at rms Mach 3 (seed 102, exact Legendre
+coefficients), rho = 1, relaxed by the method itself (plain FP32) for 30
+driven steps so that shocks and density contrasts form.
 
 One step = the whole hot path: driving update when due, CFL dt, and per
-stage the velocity projection, the RHS with AV, Riemann fluxes, forcing, the
-stage combine and the positivity rescaling.  L2 is flushed (a 256 MB write)
-before every timed step, outside the timed interval.
+stage the velocity projection, the RHS with viscous pressure, Riemann fluxes
+and forcing, the stage combine and the positivity rescaling.  L2 is flushed
+(a 256 MB write) before every timed step, outside the timed interval.
+
+Variants: plain FP32, split-BF16 x3 tensor-core transforms ("x3"), and the
+learned viscosity sensor (network trained here, untimed, on plain-sensor
+pairs of the relaxed state).  Fixed L1: from the relaxed state each variant
+runs 20 undriven steps at a fixed dt; the reference is the plain FP32 scheme
+on the 2N^3 mesh from the exactly prolonged state (40 steps at dt/2),
+restricted back by L2 projection; a variant counts when its density L1 error
+is within 1.1x of plain FP32's.  `value` is the fastest counting variant.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (a 16^3 sub-box at the same degree and scheme).
@@ -22,7 +32,6 @@ import json
 import os
 import subprocess
 import sys
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -33,10 +42,12 @@ UNIT = "DOF-updates/s"
 
 
 def workload(args):
-    return {"workload": "driven isothermal turbulence, 64^3 cells, DG k=3 (P3), SSP-RK3, Mach 3",
-            "N": args.N, "k": args.k, "rk_stages": 3, "mach": args.mach, "cs": 1.0, "cfl": 0.3,
-            "av": "vNR alpha=2 beta=0.2", "riemann": "Rusanov", "forcing": "OU |k|<=3 zeta=0.5 seed 0",
-            "state": "synthetic k^-2 velocity (seed 102) relaxed %d steps" % args.relax,
+    return {"workload": "driven isothermal turbulence, %d^3 cells, DG k=%d (P%d), SSP-RK3, Mach %g"
+                        % (args.N, args.k, args.k, args.mach),
+            "N": args.N, "k": args.k, "dof": 4 * ((args.k + 1) * (args.k + 2) * (args.k + 3) // 6) * args.N ** 3,
+            "rk_stages": 3, "mach": args.mach, "cs": 1.0, "cfl": 0.3, "av": "vNR alpha=2 beta=0.2",
+            "riemann": "Rusanov", "forcing": "OU |k|<=3 zeta=0.5 seed 0",
+            "state": "synthetic k^-2 velocity (seed 102) relaxed %d driven steps" % args.relax,
             "l2": "flushed (256 MB write) before every timed step"}
 
 
@@ -97,7 +108,6 @@ def peaks():
 
 def oracle_arm(args, steps, warmup):
     """FP64 CPU oracle on a bounded sample: a 16^3 box at the workload's degree."""
-    import numpy as np
     from oracle import oracle as O
     from paper_2401_06841_gb300 import inputs as I
     n = args.sample_N
@@ -140,20 +150,21 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f32", "x3", "f64"])
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--mach", type=float, default=3.0)
     ap.add_argument("--relax", type=int, default=30)
     ap.add_argument("--sample-N", dest="sample_N", type=int, default=16)
     ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=4)
+    ap.add_argument("--l1-steps", dest="l1_steps", type=int, default=20)
+    ap.add_argument("--variants", default="f32,x3,learned-f32,learned-x3")
     ap.add_argument("--no-cpu", dest="no_cpu", action="store_true")
+    ap.add_argument("--no-l1", dest="no_l1", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -163,89 +174,167 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
     from paper_2401_06841_gb300 import Solver
     from paper_2401_06841_gb300 import inputs as I
+    from paper_2401_06841_gb300 import transfer as Tr
 
     N, k = args.N, args.k
     b = (k + 1) * (k + 2) * (k + 3) // 6
     S = 3
-    # independent replica per rank (the path shards into independent problems)
-    u0 = I.turbulent_state(N, k, seed=102 + rank, mach=args.mach)
-    s = Solver(N, k, precision=args.precision, rk_stages=S, cfl=0.3, device="cuda:%d" % local)
-    s.set_state(u0)
-    s.set_forcing(mach=args.mach, zeta=0.5, seed=rank)
-    s.step(args.relax)
-    stream = s.stream
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=s.device)
-
-    def flush_l2():
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-
-    for _ in range(args.warmup):
-        flush_l2()
-        s.step(1)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = Clocks(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    s.profile(True)
-    for i in range(args.steps):
-        flush_l2()
-        starts[i].record(stream)
-        s.step(1)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    prof = s.profile_read()
-    s.profile(False)
-    clk = clocks.stop()
-    if world > 1:
-        dist.barrier()
-    ms = sum(a.elapsed_time(e) for a, e in zip(starts, ends)) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=s.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     dof = 4 * b * N ** 3
-    value = dof * S * world / (ms * 1e-3)
+    # the relaxed driven state (independent replica per rank)
+    base = Solver(N, k, precision="f32", rk_stages=S, device=dev)
+    base.set_state(I.turbulent_state(N, k, seed=102 + rank, mach=args.mach))
+    base.set_forcing(mach=args.mach, zeta=0.5, seed=rank)
+    snaps = []
+    for i in range(args.relax):
+        _, dtl = base.step(1)
+        if i % 10 == 9:
+            snaps.append((base.get_state().clone(), dtl))
+    S0 = base.get_state().clone()
+    meta0 = base.get_meta()
 
-    # dominant kernel: RHS + stage update (K_B); algorithmic bytes per DOF per
-    # stage averaged over SSP-RK3: u^(s) 1 word + u^n 2/3 word + out 1 word + a_h 3/4 word
-    esz = 8 if args.precision == "f64" else 4
-    rhs_ms = prof["ms_rhs"] / max(prof["n_rhs"], 1)
+    variants = [v for v in args.variants.split(",") if v]
+    weights = None
+    if any(v.startswith("learned") for v in variants):
+        # plain-sensor pairs of the relaxed snapshots -> trained weights (untimed)
+        trainer = Solver(N, k, precision="f32", av="learned", device=dev)
+        trainer.set_av_weights(I.mlp_init(2 * b, seed=1))
+        xs, ys = [], []
+        for u, dtl in snaps:
+            trainer.set_state(u)
+            x, y = trainer.generate_pairs(dtl)
+            xs.append(x)
+            ys.append(y)
+        X, Y = torch.cat(xs), torch.cat(ys)
+        perm = torch.randperm(len(Y), device=X.device, generator=torch.Generator(device=X.device).manual_seed(0))
+        trainer.mlp_train(X[perm], Y[perm], epochs=5, batch=4096, lr=2e-3)
+        weights = trainer.get_av_weights()
+        trainer.close()
+        del X, Y, xs, ys
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def make(v):
+        prec = v.split("-")[-1]
+        s = Solver(N, k, precision=prec, rk_stages=S, av="learned" if v.startswith("learned") else "vnr", device=dev)
+        if weights is not None and v.startswith("learned"):
+            s.set_av_weights(weights)
+        return s
+
+    clocks = Clocks(local)
+    res = {}
+    clocks.start()
+    time.sleep(0.2)
+    for v in variants:
+        s = make(v)
+        s.set_forcing(mach=args.mach, zeta=0.5, seed=rank)
+        s.set_state(S0)
+        s.set_meta(meta0)
+        stream = s.stream
+
+        def flush_l2():
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+
+        for _ in range(args.warmup):
+            flush_l2()
+            s.step(1)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        s.profile(True)
+        for i in range(args.steps):
+            flush_l2()
+            starts[i].record(stream)
+            s.step(1)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        s.profile(False)
+        ms = sum(a.elapsed_time(e) for a, e in zip(starts, ends)) / args.steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        res[v] = {"value": dof * S * world / (ms * 1e-3), "ms_per_step": ms, "prof": prof, "solver": s}
+    clk = clocks.stop()
+
+    # ---- fixed L1: undriven decay from the relaxed state, fixed dt ----
+    if not args.no_l1:
+        dt0 = 0.3 * (1.0 / N) / ((k + 1) * base.diagnostics()["max_speed"])
+        dt = 0.8 * dt0
+        fine = Solver(2 * N, k, precision="f32", rk_stages=S, device=dev)
+        fine.set_state(Tr.prolong(S0, N, k))
+        fine.step(2 * args.l1_steps, fixed_dt=dt / 2)
+        ref = Tr.restrict(fine.get_state(), N, k).contiguous()
+        fine.close()
+        del fine
+        for v in variants:
+            s = res[v]["solver"]
+            s.set_forcing(mach=args.mach, on=False)
+            s.set_state(S0)
+            s.step(args.l1_steps, fixed_dt=dt)
+            res[v]["l1"] = s.l1_density(s.get_state(), ref)
+        l1_f32 = res["f32"]["l1"] if "f32" in res else None
+        for v in variants:
+            res[v]["at_fixed_l1"] = (l1_f32 is not None and res[v]["l1"] <= 1.1 * l1_f32)
+    else:
+        for v in variants:
+            res[v]["l1"] = None
+            res[v]["at_fixed_l1"] = v == "f32"
+
+    counting = [v for v in variants if res[v]["at_fixed_l1"]]
+    head = max(counting, key=lambda v: res[v]["value"]) if counting else variants[0]
+    hs = res[head]["solver"]
+    prof = res[head]["prof"]
+    # dominant kernel: RHS + stage update; algorithmic bytes per DOF per stage
+    # (SSP-RK3 average): u^(s) 1 word + u^n 2/3 word + u^(s+1) 1 word + a_h 3/4 word
+    esz = 4
+    n_stage = prof["n_rhs"]
+    rhs_ms = prof["ms_rhs"] / max(n_stage, 1)
     bytes_per_launch = dof * esz * (1 + 2.0 / 3.0 + 1 + 0.75)
     hbm, bf16, src = peaks()
     achieved = bytes_per_launch / (rhs_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "k_rhs (RHS + SSP-RK stage + positivity)", "peak_source": src,
-            "kernel_ms": rhs_ms, "project_ms": prof["ms_project"] / max(prof["n_project"], 1)}
+            "traffic": None, "kernel": "k_tile stage (RHS + SSP-RK stage + positivity + next projection), %s" % head,
+            "peak_source": src, "launches_timed": int(n_stage),
+            "kernel_ms": rhs_ms, "bytes_per_launch": bytes_per_launch}
 
-    # end to end through the public API with host buffers: H2D state, one step, D2H state
-    host_in = torch.from_numpy(s.get_state().cpu().numpy()).pin_memory()
+    # end to end through the C ABI with pinned host buffers: H2D state, one step, D2H state
+    hs.set_forcing(mach=args.mach, zeta=0.5, seed=rank)
+    hs.set_state(S0)
+    host_in = S0.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     e2e_ms = []
-    for i in range(max(3, args.steps // 4)):
+    for _ in range(max(3, args.steps // 4)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.L.dg_set_state(s.h, host_in.data_ptr(), 1)
-        s.step(1)
-        s.L.dg_get_state(s.h, host_out.data_ptr(), 1)
+        hs.L.dg_set_state(hs.h, host_in.data_ptr(), 1)
+        hs.step(1)
+        hs.L.dg_get_state(hs.h, host_out.data_ptr(), 1)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_ms.sort()
     e2e_v = dof * S * world / (e2e_ms[len(e2e_ms) // 2] * 1e-3)
     nbytes = host_in.numel() * host_in.element_size()
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"f32": "f32", "x3": "bf16x3+f32", "f64": "f64"}[args.precision],
-            "data": "synthetic", "config": workload(args), "roofline": roof, "clocks": clk,
+    line = {"metric": METRIC, "value": res[head]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res[head]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "x3": "bf16x3+f32"}[head.split("-")[-1]], "data": "synthetic",
+            "config": dict(workload(args), variant=head), "roofline": roof, "clocks": clk,
             "gpu_launches": int(prof["launches"]),
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "diag": {k_: v for k_, v in s.diagnostics().items() if k_ in ("mach", "rho_min", "rho_max", "av_frac")}}
+            "variants": {v: {"value": res[v]["value"], "ms_per_step": res[v]["ms_per_step"], "l1_rho": res[v]["l1"],
+                             "at_fixed_l1": res[v]["at_fixed_l1"],
+                             "stage_kernel_ms": res[v]["prof"]["ms_rhs"] / max(res[v]["prof"]["n_rhs"], 1),
+                             "project_kernel_ms": res[v]["prof"]["ms_project"] / max(res[v]["prof"]["n_project"], 1),
+                             "other_ms_per_step": res[v]["prof"]["ms_other"] / args.steps}
+                         for v in variants},
+            "diag": {k_: v for k_, v in hs.diagnostics().items() if k_ in ("mach", "rho_min", "rho_max", "av_frac")}}
     if rank == 0 and not args.no_cpu:
         v, wall, cb = oracle_arm(args, args.cpu_steps, 1)
         cb["value"] = v

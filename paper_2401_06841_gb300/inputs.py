@@ -177,3 +177,14 @@ def uniform_state(N: int, k: int, rho: float = 1.0, v=(0.0, 0.0, 0.0)) -> np.nda
     for i in range(3):
         u[:, 1 + i, 0] = rho * v[i]
     return u
+
+
+def mlp_init(D: int, seed: int, H: int = 64) -> np.ndarray:
+    """Seeded Kaiming-uniform parameters of the learned sensor's network in the
+    library's flat layout (W1 [H][D], b1 [H], W2 [H][H], b2 [H], W3 [H], b3):
+    weights U(-sqrt(6/fan_in), +sqrt(6/fan_in)), biases zero.  FP32."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.uniform(-1, 1, (H, D)) * np.sqrt(6.0 / D)
+    W2 = rng.uniform(-1, 1, (H, H)) * np.sqrt(6.0 / H)
+    W3 = rng.uniform(-1, 1, H) * np.sqrt(6.0 / H)
+    return np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3, np.zeros(1)]).astype(np.float32)
