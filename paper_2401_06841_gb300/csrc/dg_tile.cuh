@@ -88,7 +88,9 @@ struct TileCfg {
     static constexpr int b = D::b, n = D::n, nq = D::nq, ns = D::ns, nf = D::nf;
     static constexpr int TC = (K == 1) ? 32 : 16;  // cells per tile
     static constexpr int NT = 256;                 // threads per block
-    static constexpr int FE = 12;                  // evaluated fields (11 used)
+    // evaluated fields: rho, m, grad rho, div m, a_h (11; the CUDA-core product keeps
+    // a twelfth zero row for a 6x8 register tile, the tensor-core product needs 16-row tiles)
+    static constexpr int FE = X ? 11 : 12;
     static constexpr int FP = 9;                   // projected components
     static constexpr int B2 = (K + 1) * (K + 2) / 2;
     static constexpr int KP = X ? r16(b) : r4(b);     // evaluation: K (modes)
@@ -120,13 +122,16 @@ struct TileCfg {
     static constexpr int oWPhi = oPhi + szPhi;
     static constexpr int oPsi = oWPhi + szWPhi;
     static constexpr int oPsiL = oPsi + szPsi;
-    static constexpr int smem_tabs = oPsiL + szPsiL;
+    static constexpr int tabsz = oPsiL + szPsiL;          // table block (global layout)
+    static constexpr int smem_tabs = tabsz;               // tables copied to shared memory
     static constexpr int oU = r4(smem_tabs);              // [TC][4][b] state of the tile
     static constexpr int oVH = oU + r4(TC * 4 * b);       // [TC][3][b] own projected velocity
     static constexpr int oR = oVH + r4(TC * 3 * b);       // [TC][4][b] right-hand side
+    static constexpr int oUn = oR + r4(TC * 4 * b);       // [TC][4][b] u^n, prefetched (stage mode)
+    static constexpr int oAh = oUn + r4(TC * 4 * b);      // [TC][3][b] forcing coefficients of the tile
     // evaluation coefficients [RE][LDA]; the projections [RP][LDP] reuse the
     // region once the evaluation product has consumed the coefficients
-    static constexpr int oA = oR + r4(TC * 4 * b);
+    static constexpr int oA = oAh + r4(TC * 3 * b);
     static constexpr int oP = oA;
     static constexpr int SZA = (RE * LDA > RP * LDP) ? RE * LDA : RP * LDP;
     // big region: point values | point fluxes | faces.  Faces: region 1 holds
@@ -147,8 +152,8 @@ struct TileCfg {
 template <int K, int BK = BK_FMA>
 struct TileTab {
     using C = TileCfg<K, BK>;
-    static constexpr int smem_tabs = C::smem_tabs;
-    static constexpr int phiv = r4(smem_tabs);                    // [b][nq]
+    static constexpr int tabsz = C::tabsz;
+    static constexpr int phiv = r4(tabsz);                        // [b][nq]
     static constexpr int phif = phiv + r4(C::b * C::nq);          // [b][nf]
     static constexpr int total = phif + C::b * C::nf;
 };
@@ -203,6 +208,45 @@ __device__ __forceinline__ void ld4_guard(const T* p, int e, int valid, T* o)
 #pragma unroll
         for (int j = 0; j < 4; ++j) o[j] = (e + j < valid) ? p[e + j] : T(0);
     }
+}
+
+// 16-byte asynchronous global -> shared copies (cp.async, cache-global)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// all but the most recent commit group complete
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// stage `count` elements of a tile into shared memory: 16-byte async copies for
+// the chunks that lie inside the `valid` readable elements, plain loads (zero
+// past the end) for a straddling chunk.  count and the base pointers are
+// multiples of 16 bytes.
+template <typename T, int NT>
+__device__ __forceinline__ void stage_async(T* dst, const T* src, int count, int valid)
+{
+    constexpr int V = 16 / sizeof(T);
+    for (int e = V * threadIdx.x; e < count; e += V * NT) {
+        if (e + V <= valid) {
+            cp_async16(dst + e, src + e);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) dst[e + j] = (e + j < valid) ? src[e + j] : T(0);
+        }
+    }
+}
+
+// reciprocal: correctly rounded in FP32 without the division subroutine
+template <typename T>
+__device__ __forceinline__ T rcp(T x)
+{
+    if constexpr (sizeof(T) == 4)
+        return __frcp_rn(x);
+    else
+        return T(1) / x;
 }
 
 // --------------------------------------------------------------------------
@@ -416,7 +460,8 @@ __device__ __forceinline__ T nu_pressure(const Phys& P, T rho, T divv, T nu, T d
 // the per-cell forcing sums <rho a_h> = sum_l rho_l a_l and the CFL maximum
 // --------------------------------------------------------------------------
 template <typename T, int K, int BK, bool VABS = false>
-__device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, bool dt_flag, T& smax, double* sums)
+__device__ __forceinline__ void tile_project(T* sm, const T* tabs, const TArgs<T>& a, long c0, bool dt_flag, T& smax,
+                                             double* sums)
 {
     constexpr int NPR = VABS ? 4 : 3;  // projected rows per cell: v (and |v|)
     using C = TileCfg<K, BK>;
@@ -432,7 +477,7 @@ __device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, 
         sA[r * LDA + l] = (l < b) ? sU[r * b + l] : T(0);
     }
     __syncthreads();
-    mm<T, BK, TC * 4, NQP, KP, LDA, LDV, NT>(sA, sm, C::oPhi, sV);
+    mm<T, BK, TC * 4, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sV);
     __syncthreads();
     // v = m / rho at the volume points; rows (cell, i) of the projection input
     constexpr int PER = (TC * NQP + NT - 1) / NT;
@@ -446,7 +491,7 @@ __device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, 
             const int c = e / NQP, q = e % NQP;
             if (q < nq) {
                 const T* v = sV + (c * 4) * LDV + q;
-                const T ir = T(1) / v[0];
+                const T ir = rcp<T>(v[0]);
                 vv[it][0] = v[LDV] * ir;
                 vv[it][1] = v[2 * LDV] * ir;
                 vv[it][2] = v[3 * LDV] * ir;
@@ -471,7 +516,7 @@ __device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, 
         }
     }
     __syncthreads();
-    mm<T, BK, TC * NPR, NP, NQP, LDV, LDP, NT>(sV, sm, C::oWPhi, sP);
+    mm<T, BK, TC * NPR, NP, NQP, LDV, LDP, NT>(sV, tabs, C::oWPhi, sP);
     __syncthreads();
     for (int e = threadIdx.x; e < TC * 3 * b; e += NT) {
         const int r = e / b, l = e % b, c = r / 3, i = r % 3;
@@ -484,15 +529,9 @@ __device__ __forceinline__ void tile_project(T* sm, const TArgs<T>& a, long c0, 
         }
     }
     if (a.flags & F_FORCE) {
-        // the tile's a_h staged in the (free) own-velocity buffer
-        T* sAh = sm + C::oVH;
+        // <rho a_h> per cell from the tile's staged forcing coefficients
+        const T* sAh = sm + C::oAh;
         const long nvalid = (a.ncell - c0) < TC ? (a.ncell - c0) : TC;
-        for (int e = 4 * threadIdx.x; e < TC * 3 * b; e += 4 * NT) {
-            T v[4];
-            ld4_guard<T>(a.ahat + c0 * 3 * b, e, (int)nvalid * 3 * b, v);
-            st4<T>(sAh + e, v);
-        }
-        __syncthreads();
         if (threadIdx.x < TC * 3) {
             const int c = threadIdx.x / 3, i = threadIdx.x % 3;
             if (c < nvalid) {
@@ -532,13 +571,18 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     __shared__ float s_minf[TC];
     __shared__ double s_mind[TC];
     __shared__ unsigned int s_status;
-    __shared__ double s_buf[NT];
     __shared__ double s_tot[8];
+    // block reductions after the tile loop use the (then free) big region
+    double* s_buf = reinterpret_cast<double*>(sm + C::oBig);
+    static_assert(C::BIG * sizeof(T) >= NT * sizeof(double), "reduction buffer");
     __shared__ unsigned long long s_smax;
 
     const int tid = threadIdx.x;
     // tables -> shared (once per block)
     for (int e = tid; e < C::smem_tabs; e += NT) sm[e] = a.tab[e];
+    const T* tabs = sm;
+    T* sUn = sm + C::oUn;
+    T* sAh = sm + C::oAh;
     if (tid == 0) {
         s_status = 0u;
         s_smax = 0ull;
@@ -574,12 +618,20 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 if ((e + j) / (4 * b) >= nvalid) v[j] = ((e + j) % (4 * b)) == 0 ? T(1) : T(0);
             st4<T>(sU + e, v);
         }
+        // two commit groups: the tile's a_h (needed first), then u^n (needed by the epilogue)
+        if (force) stage_async<T, NT>(sAh, a.ahat + c0 * 3 * b, TC * 3 * b, (int)nvalid * 3 * b);
+        cp_async_commit();
+        if constexpr (MODE == TM_STAGE) {
+            if (a.rk_a != T(0)) stage_async<T, NT>(sUn, a.u_n + c0 * 4 * b, TC * 4 * b, (int)nvalid * 4 * b);
+        }
+        cp_async_commit();
         if constexpr (MODE == TM_PROJECT) {
+            cp_async_wait_all();
             __syncthreads();
             if (a.flags & F_VABS)
-                tile_project<T, K, BK, true>(sm, a, c0, (a.flags & F_DT) != 0, smax, sums);
+                tile_project<T, K, BK, true>(sm, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums);
             else
-                tile_project<T, K, BK, false>(sm, a, c0, (a.flags & F_DT) != 0, smax, sums);
+                tile_project<T, K, BK, false>(sm, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums);
             __syncthreads();
             continue;
         } else {
@@ -589,11 +641,12 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 ld4_guard<T>(a.vh_in + c0 * 3 * b, e, (int)nvalid * 3 * b, v);
                 st4<T>(sVH + e, v);
             }
+            cp_async_wait_prior();
+            __syncthreads();
             for (int e = tid; e < TC * 3 * b; e += NT) {
                 const int c = e / (3 * b), i = (e / b) % 3, l = e % b;
-                sA[(c * FE + 8 + i) * LDA + l] = (force && c < nvalid) ? a.ahat[c0 * 3 * b + e] : T(0);
+                sA[(c * FE + 8 + i) * LDA + l] = (force && c < nvalid) ? sAh[e] : T(0);
             }
-            __syncthreads();
             // ---- evaluation coefficients: rho, m, grad rho, div m, (a_h staged above) ----
             for (int e = tid; e < RE; e += NT) {
                 const int c = e / FE, f = e % FE;
@@ -632,7 +685,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             }
             __syncthreads();
             // ---- evaluation at the volume points ----
-            mm<T, BK, RE, NQP, KP, LDA, LDV, NT>(sA, sm, C::oPhi, sBig);
+            mm<T, BK, RE, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sBig);
             __syncthreads();
             // ---- pointwise volume physics (Sec. 3.1: Pi at internal points only) ----
             constexpr int PER = (TC * NQP + NT - 1) / NT;
@@ -646,7 +699,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     const int c = e / NQP, q = e % NQP;
                     if (q < nq) {
                         const T* v = sBig + (c * FE) * LDV + q;
-                        const T rho = v[0], ir = T(1) / rho;
+                        const T rho = v[0], ir = rcp<T>(rho);
                         const T mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV];
                         const T vx = mx * ir, vy = my * ir, vz = mz * ir;
                         const T divv = (v[7 * LDV] - (vx * v[4 * LDV] + vy * v[5 * LDV] + vz * v[6 * LDV])) * ir;
@@ -681,7 +734,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             }
             __syncthreads();
             // ---- projection of the flux tensor and the forcing density ----
-            mm<T, BK, RP, NP, NQP, LDV, LDP, NT>(sBig, sm, C::oWPhi, sP);
+            mm<T, BK, RP, NP, NQP, LDV, LDP, NT>(sBig, tabs, C::oWPhi, sP);
             __syncthreads();
             // ---- volume term in modal space + forcing source ----
             for (int e = tid; e < TC * 4; e += NT) {
@@ -750,7 +803,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     for (int p = 0; p < B2K; ++p) sC2[r * LDC2 + p] = c2[p];
                 }
                 __syncthreads();
-                mm<T, BK, RC, NSP, B2K, LDC2, LDT, NT>(sC2, sm, C::oPsi, sTr);
+                mm<T, BK, RC, NSP, B2K, LDC2, LDT, NT>(sC2, tabs, C::oPsi, sTr);
                 __syncthreads();
                 // Rusanov at every face point; F* along +e_d with L = lower cell
                 for (int e = tid; e < TC * 2 * NSP; e += NT) {
@@ -773,7 +826,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     for (int v = 0; v < 4; ++v) sFs[((c * 2 + side) * 4 + v) * LDT + s] = F[v];
                 }
                 __syncthreads();
-                mm<T, BK, RL, B2N, NSP, LDT, LDL, NT>(sFs, sm, C::oPsiL, sL2);
+                mm<T, BK, RL, B2N, NSP, LDT, LDL, NT>(sFs, tabs, C::oPsiL, sL2);
                 __syncthreads();
                 for (int e = tid; e < TC * 4; e += NT) {
                     const int c = e / 4, v = e % 4;
@@ -791,11 +844,13 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 }
                 __syncthreads();
             } else {
-                // SSP-RK stage combine (Sec. 7), new state kept in sU
+                // SSP-RK stage combine (Sec. 7), new state kept in sU; u^n was prefetched
+                cp_async_wait_all();
+                __syncthreads();
                 for (int e = tid; e < TC * 4 * b; e += NT) {
                     T w;
                     if (e / (4 * b) < nvalid) {
-                        const T un = (a.rk_a != T(0)) ? a.u_n[c0 * 4 * b + e] : T(0);
+                        const T un = (a.rk_a != T(0)) ? sUn[e] : T(0);
                         w = a.rk_a * un + a.rk_b * (sU[e] + dt * sR[e]);
                     } else {
                         w = ((e % (4 * b)) == 0) ? T(1) : T(0);
@@ -886,7 +941,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 if (st) atomicOr(&s_status, st);
                 __syncthreads();
                 if (do_proj) {
-                    tile_project<T, K, BK>(sm, a, c0, false, smax, sums);
+                    tile_project<T, K, BK>(sm, tabs, a, c0, false, smax, sums);
                     __syncthreads();
                 }
             }
