@@ -736,6 +736,36 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             // ---- projection of the flux tensor and the forcing density ----
             mm<T, BK, RP, NP, NQP, LDV, LDP, NT>(sBig, tabs, C::oWPhi, sP);
             __syncthreads();
+            // ---- neighbour coefficients of the face rows, fetched one face
+            // direction ahead so that their latency overlaps the work of the
+            // previous phase (rows r = tid + j NT; only "neighbour" rows load) ----
+            constexpr int NR = RC / NT;
+            static_assert(RC % NT == 0, "face rows per thread");
+            T nbr[NR][b];
+            auto load_nbr = [&](auto dd) {
+                constexpr int Dd = decltype(dd)::value;
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    const int r = tid + j * NT;
+                    const int field = r & 3, who = (r >> 2) & 1, side = (r >> 3) & 1, c = r >> 4;
+                    const long cc = c0 + c;
+                    if (who == 1 && cc < a.ncell) {
+                        const long nc = neighbour(cc, 2 * Dd + side, a.N);
+                        const T* src = (field == 0) ? a.u_in + nc * 4 * b : a.vh_in + (nc * 3 + field - 1) * b;
+                        if constexpr (b % 4 == 0) {
+#pragma unroll
+                            for (int l = 0; l < b; l += 4) ld4<T>(src + l, nbr[j] + l);
+                        } else {
+#pragma unroll
+                            for (int l = 0; l < b; ++l) nbr[j][l] = __ldg(src + l);
+                        }
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < b; ++l) nbr[j][l] = (field == 0 && l == 0) ? T(1) : T(0);
+                    }
+                }
+            };
+            load_nbr(std::integral_constant<int, 0>{});
             // ---- volume term in modal space + forcing source ----
             for (int e = tid; e < TC * 4; e += NT) {
                 const int c = e / 4, v = e % 4;
@@ -762,7 +792,8 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
 #pragma unroll
                 for (int l = 0; l < b; ++l) sR[(c * 4 + v) * b + l] = r[l];
             }
-            __syncthreads();
+            // (no barrier: the face collapse below touches other buffers; the
+            // barrier after it orders these writes before the face lift)
             // ---- faces, one direction at a time (Sec. 3.2 face states, Rusanov) ----
             T* sC2 = sBig + C::oC2;
             T* sTr = sBig + C::oTr;
@@ -770,8 +801,17 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             T* sL2 = sBig + C::oL2;
             static_for<0, 3>([&](auto dd) {
                 constexpr int Dd = decltype(dd)::value;
+                // this direction's neighbour rows; start the next direction's loads
+                T cur[NR][b];
+#pragma unroll
+                for (int j = 0; j < NR; ++j)
+#pragma unroll
+                    for (int l = 0; l < b; ++l) cur[j][l] = nbr[j][l];
+                if constexpr (Dd < 2) load_nbr(std::integral_constant<int, Dd + 1>{});
                 // collapse rows r = ((c*2 + side)*2 + who)*4 + field
-                for (int r = tid; r < RC; r += NT) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    const int r = tid + j * NT;
                     const int field = r & 3, who = (r >> 2) & 1, side = (r >> 3) & 1, c = r >> 4;
                     T cf[b];
                     int fside = side;
@@ -781,21 +821,8 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                         for (int l = 0; l < b; ++l) cf[l] = src[l];
                     } else {
                         fside = 1 - side;
-                        const long cc = c0 + c;
-                        if (cc < a.ncell) {
-                            const long nc = neighbour(cc, 2 * Dd + side, a.N);
-                            const T* src = (field == 0) ? a.u_in + nc * 4 * b : a.vh_in + (nc * 3 + field - 1) * b;
-                            if constexpr (b % 4 == 0) {
 #pragma unroll
-                                for (int l = 0; l < b; l += 4) ld4<T>(src + l, cf + l);
-                            } else {
-#pragma unroll
-                                for (int l = 0; l < b; ++l) cf[l] = __ldg(src + l);
-                            }
-                        } else {
-#pragma unroll
-                            for (int l = 0; l < b; ++l) cf[l] = (field == 0 && l == 0) ? T(1) : T(0);
-                        }
+                        for (int l = 0; l < b; ++l) cf[l] = cur[j][l];
                     }
                     T c2[B2K];
                     collapse<T, K, Dd, B2K>(cf, fside, c2);
@@ -835,10 +862,14 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     expand_acc<T, K, Dd>(sL2 + ((c * 2 + 1) * 4 + v) * LDL, 1, -inv4h, R);
                     expand_acc<T, K, Dd>(sL2 + ((c * 2 + 0) * 4 + v) * LDL, 0, inv4h, R);
                 }
-                __syncthreads();
+                // no barrier: the next direction's collapse writes the other face
+                // region, and the barrier after it orders this lift before the
+                // next trace product overwrites the lifted fluxes; both epilogues
+                // start with a barrier
             });
             // ---- epilogue ----
             if constexpr (MODE == TM_RHS) {
+                __syncthreads();
                 for (int e = tid; e < TC * 4 * b; e += NT) {
                     if (e / (4 * b) < nvalid) a.out[c0 * 4 * b + e] = sR[e];
                 }
