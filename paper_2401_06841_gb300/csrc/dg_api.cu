@@ -440,6 +440,11 @@ struct dg_ctx {
     cudaStream_t st = nullptr;
     void* reg[3] = {nullptr, nullptr, nullptr};
     int cur = 0;
+    // projection carried over from the last stage of the previous step:
+    // vhat buffer / abar slot pb and ctl->sn already hold the projection,
+    // the forcing sums and the wave-speed bound of reg[cur]
+    bool carry = false;
+    int pb = 0;
     void* vhat = nullptr;
     void* ahat = nullptr;
     char* scratch = nullptr;
@@ -450,6 +455,8 @@ struct dg_ctx {
     void* ttab = nullptr;
     int* d_kvec = nullptr;
     double* d_amp = nullptr;
+    void* gtab = nullptr;  // forcing: 1D factors
+    Rule1 r1{};            // 1D Gauss rule
     int nsm = 0;
     bool state_set = false;
     bool forcing_active = false;  // ahat holds a forcing to apply
@@ -493,7 +500,7 @@ struct dg_ctx {
 namespace {
 
 struct ScratchLayout {
-    size_t ctl, partials, tab, ttab, kvec, amp;
+    size_t ctl, partials, tab, ttab, kvec, amp, gtab;
     size_t mw, mm, mv, mg, mpack, mloss, mwork;  // learned sensor: weights, Adam moments, grad, packed, loss, work
     size_t nu, vabs;                             // per-cell coefficient and |v| projection (learned mode)
     size_t total;
@@ -502,9 +509,10 @@ struct ScratchLayout {
 constexpr int kMlpMaxParams = 64 * 40 + 64 + 64 * 64 + 64 + 64 + 1;
 constexpr int kMlpPackWords = 8192;
 
-ScratchLayout scratch_layout(int K, long ncell = 0, bool learned = false)
+ScratchLayout scratch_layout(int K, int N, bool learned = false)
 {
     ScratchLayout s{};
+    const long ncell = (long)N * N * N;
     size_t off = 0;
     s.ctl = off;
     off = align256(off + sizeof(Ctl));
@@ -518,6 +526,8 @@ ScratchLayout scratch_layout(int K, long ncell = 0, bool learned = false)
     off = align256(off + sizeof(int) * 3 * kMaxModes);
     s.amp = off;
     off = align256(off + sizeof(double) * 6 * kMaxModes);
+    s.gtab = off;
+    off = align256(off + sizeof(double) * 2 * (size_t)N * kForceNK * (K + 1));
     s.mw = off;
     off = align256(off + sizeof(float) * kMlpMaxParams);
     s.mm = off;
@@ -575,6 +585,8 @@ Launch make_launch(const dg_ctx* c)
     L.partials = c->partials;
     L.nsm = c->nsm;
     L.bk = (c->prec == DG_PREC_X3) ? 1 : 0;
+    L.r1 = c->r1;
+    L.gtab = c->gtab;
     return L;
 }
 
@@ -624,6 +636,13 @@ struct Timed {
         }
     }
 };
+
+// any call other than dg_step may overwrite the projected-velocity buffers,
+// the forcing or the state: the next step projects afresh
+void drop_carry(dg_ctx* c)
+{
+    if (c) c->carry = false;
+}
 
 cudaError_t tile(dg_ctx* c, const TileLaunch& t)
 {
@@ -743,8 +762,9 @@ extern "C" {
 int dg_scratch_bytes(const dg_mesh* mesh, int order, const dg_nu_params* nu, size_t* bytes)
 {
     if (!bytes || !mesh || !nu || order < 1 || order > 3) return DG_EINVAL;
-    const long ncell = (long)mesh->n[0] * mesh->n[1] * mesh->n[2];
-    *bytes = scratch_layout(order, ncell, nu->mode == DG_AV_LEARNED).total;
+    const int N = std::max(mesh->n[0], std::max(mesh->n[1], mesh->n[2]));
+    if (N < 1) return DG_EINVAL;
+    *bytes = scratch_layout(order, N, nu->mode == DG_AV_LEARNED).total;
     return DG_OK;
 }
 
@@ -778,8 +798,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
         if (!opts->u[i]) return DG_EINVAL;
     if (!opts->vhat || !opts->ahat || !opts->scratch) return DG_EINVAL;
     if (((uintptr_t)opts->scratch) & 255u) return DG_EINVAL;
-    const long ncell0 = (long)mesh->n[0] * mesh->n[0] * mesh->n[0];
-    ScratchLayout sl = scratch_layout(order, ncell0, nu->mode == DG_AV_LEARNED);
+    ScratchLayout sl = scratch_layout(order, mesh->n[0], nu->mode == DG_AV_LEARNED);
     if (opts->scratch_bytes < sl.total) return DG_ENOMEM;
 
     dg_ctx* ctx = new (std::nothrow) dg_ctx();
@@ -806,6 +825,15 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->ttab = ctx->scratch + sl.ttab;
     ctx->d_kvec = (int*)(ctx->scratch + sl.kvec);
     ctx->d_amp = (double*)(ctx->scratch + sl.amp);
+    ctx->gtab = ctx->scratch + sl.gtab;
+    {
+        long double xg[4], wg[4];
+        gauss_rule(order + 1, xg, wg);
+        for (int a = 0; a <= order; ++a) {
+            ctx->r1.x[a] = (double)xg[a];
+            ctx->r1.w[a] = (double)wg[a];
+        }
+    }
     ctx->mw = (float*)(ctx->scratch + sl.mw);
     ctx->mm = (float*)(ctx->scratch + sl.mm);
     ctx->mv = (float*)(ctx->scratch + sl.mv);
@@ -861,6 +889,7 @@ const char* dg_last_error(const dg_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 int dg_set_state(dg_ctx* ctx, const void* src, int src_on_host)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!src) return fail(ctx, DG_EINVAL, "dg_set_state: null source");
     ctx->cur = 0;
@@ -887,6 +916,7 @@ int dg_get_state(dg_ctx* ctx, void* dst, int dst_on_host)
 
 int dg_project_velocity(dg_ctx* ctx, const void* u_in, void* vhat_out)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!u_in || !vhat_out) return fail(ctx, DG_EINVAL, "dg_project_velocity: null buffer");
     CK(project(ctx, u_in, vhat_out, nullptr, false, 0));
@@ -896,6 +926,7 @@ int dg_project_velocity(dg_ctx* ctx, const void* u_in, void* vhat_out)
 
 int dg_rhs(dg_ctx* ctx, const void* u_in, const void* ahat, void* dudt, double dt_for_pimax)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!u_in || !dudt) return fail(ctx, DG_EINVAL, "dg_rhs: null buffer");
     const bool learned = ctx->nu.mode == DG_AV_LEARNED;
@@ -919,6 +950,7 @@ int dg_rhs(dg_ctx* ctx, const void* u_in, const void* ahat, void* dudt, double d
 
 int dg_set_forcing(dg_ctx* ctx, const dg_forcing* f)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!f) return fail(ctx, DG_EINVAL, "dg_set_forcing: null");
     if (f->on && (!(f->mach > 0.0) || f->kmin2 < 1 || f->kmax2 < f->kmin2 || f->kmax2 > 64 || f->zeta < 0.0 ||
@@ -938,6 +970,7 @@ int dg_set_forcing(dg_ctx* ctx, const dg_forcing* f)
 
 int dg_set_forcing_coeffs(dg_ctx* ctx, const void* src, int src_on_host)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     ctx->drv.on = false;
     if (!src) {
@@ -954,6 +987,7 @@ int dg_set_forcing_coeffs(dg_ctx* ctx, const void* src, int src_on_host)
 
 int dg_forcing_from_modes(dg_ctx* ctx, int nmodes, const int32_t* kvec, const double* amp)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (nmodes < 1 || nmodes > kMaxModes || !kvec || !amp) return fail(ctx, DG_EINVAL, "dg_forcing_from_modes: bad args");
     int kmaxc = 0;
@@ -990,6 +1024,7 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
     for (int st = 0; st < nsteps; ++st) {
         // driving schedule (Sec. 4.2): OU update at the first step with t >= t_next
         if (ctx->drv.on && ctx->drv.t_off > 0.0 && ctx->t > ctx->drv.t_off) {
+            ctx->carry = false;
             ctx->drv.on = false;
             ctx->forcing_active = false;
             CK(cudaMemsetAsync(ctx->ahat, 0, vec_bytes(ctx), ctx->st));
@@ -1001,6 +1036,7 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
                 ctx->drv.dirty = true;
             }
             if (ctx->drv.dirty) {
+                ctx->carry = false;  // new a_h: the forcing sums change
                 int rc = upload_forcing(ctx);
                 if (rc) return rc;
                 ctx->drv.dirty = false;
@@ -1016,6 +1052,8 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
         bool ok = false;
         double dt = 0.0;
         unsigned int status = 0u;
+        const bool learned = ctx->nu.mode == DG_AV_LEARNED;
+        const int pb = ctx->pb;
         for (int retry = 0; retry <= 3 && !ok; ++retry) {
             struct {
                 double dt_scale, fixed_dt;
@@ -1023,11 +1061,14 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
             CK(cudaMemcpyAsync(&ctx->ctl->dt_scale, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->st));
             unsigned int zero = 0u;
             CK(cudaMemcpyAsync(&ctx->ctl->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->st));
-            // stage 1 projection (+ CFL dt); later stages get theirs from the
-            // previous stage's epilogue (double-buffered vhat / abar slots)
-            const bool learned = ctx->nu.mode == DG_AV_LEARNED;
+            // stage 1 needs the projection of u^n (+ its wave-speed bound): carried
+            // over from the last stage of the previous step, else a projection
+            // launch; later stages get theirs from the previous stage's epilogue
+            // (double-buffered vhat / abar slots, alternating from slot pb)
+            const bool use_carry = retry == 0 && ctx->carry;
+            ctx->carry = false;
             if (learned) CK(learned_nu(ctx, ctx->reg[A]));  // once per step, cached for all stages
-            CK(project(ctx, ctx->reg[A], vh_buf(ctx, 0), force ? ctx->ahat : nullptr, true, 0));
+            if (!use_carry) CK(project(ctx, ctx->reg[A], vh_buf(ctx, pb), force ? ctx->ahat : nullptr, true, pb));
             for (int s = 0; s < ctx->rk; ++s) {
                 TileLaunch t{};
                 t.nu = learned ? ctx->nu_cell : nullptr;
@@ -1035,14 +1076,17 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
                 t.u_in = ctx->reg[in[s]];
                 t.u_n = ctx->reg[A];
                 t.out = ctx->reg[out[s]];
-                t.vh_in = vh_buf(ctx, s & 1);
-                t.vh_out = vh_buf(ctx, (s + 1) & 1);
+                t.vh_in = vh_buf(ctx, (pb + s) & 1);
+                t.vh_out = vh_buf(ctx, (pb + s + 1) & 1);
                 t.ahat = force ? ctx->ahat : nullptr;
                 t.rk_a = RA[s];
                 t.rk_b = RB[s];
-                t.flags = (force ? F_FORCE : 0) | (s + 1 < ctx->rk ? F_NEXTPROJ : 0);
-                t.abar_in = s & 1;
-                t.abar_out = (s + 1) & 1;
+                // the last stage projects u^(n+1) for the next step (learned mode
+                // re-projects anyway for its features)
+                const bool next = s + 1 < ctx->rk || !learned;
+                t.flags = (force ? F_FORCE : 0) | (next ? F_NEXTPROJ : 0) | (next && s + 1 == ctx->rk ? F_DT : 0);
+                t.abar_in = (pb + s) & 1;
+                t.abar_out = (pb + s + 1) & 1;
                 CK(tile(ctx, t));
             }
             struct {
@@ -1062,6 +1106,8 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
         }
         ctx->status |= status;
         ctx->cur = out[ctx->rk - 1];
+        ctx->pb = (pb + ctx->rk) & 1;
+        ctx->carry = !learned && !(status & DG_ST_NONFINITE);
         ctx->t += dt;
         ctx->dt_last = dt;
         ctx->steps += 1;
@@ -1074,6 +1120,7 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
 
 int dg_diagnostics(dg_ctx* ctx, double dt_for_pimax, dg_diag* out)
 {
+    drop_carry(ctx);
     if (!ctx || !out) return DG_EINVAL;
     if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_diagnostics: no state set");
     const void* u = ctx->reg[ctx->cur];
@@ -1122,6 +1169,7 @@ int dg_l1_density(dg_ctx* ctx, const void* uA, const void* uB, double* out)
 
 int dg_set_av_weights(dg_ctx* ctx, const float* w, size_t n)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!w || n != (size_t)ctx->mlp_P) return fail(ctx, DG_EINVAL, "dg_set_av_weights: need dg_av_param_count floats");
     const int rc = upload_weights(ctx, w);
@@ -1151,6 +1199,7 @@ int dg_av_param_count(dg_ctx* ctx, int64_t* n)
 
 int dg_mlp_forward(dg_ctx* ctx, const float* x, int64_t n, float* y)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!x || !y || n < 1) return fail(ctx, DG_EINVAL, "dg_mlp_forward: bad arguments");
     if (!ctx->weights_set) return fail(ctx, DG_ESTATE, "dg_mlp_forward: no weights");
@@ -1165,6 +1214,7 @@ int dg_mlp_forward(dg_ctx* ctx, const float* x, int64_t n, float* y)
 
 int dg_mlp_grad(dg_ctx* ctx, const float* x, const float* y, int64_t n, float* grad, double* loss)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!x || !y || !grad || !loss || n < 1 || n > kMlpBatchMax) return fail(ctx, DG_EINVAL, "dg_mlp_grad: bad arguments");
     if (!ctx->weights_set) return fail(ctx, DG_ESTATE, "dg_mlp_grad: no weights");
@@ -1180,6 +1230,7 @@ int dg_mlp_grad(dg_ctx* ctx, const float* x, const float* y, int64_t n, float* g
 
 int dg_mlp_train(dg_ctx* ctx, const float* x, const float* y, int64_t n, const dg_train_opts* o, double* loss_out)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!x || !y || !o || n < 1 || o->batch < 1 || o->batch > kMlpBatchMax || o->epochs < 1)
         return fail(ctx, DG_EINVAL, "dg_mlp_train: bad arguments");
@@ -1218,6 +1269,7 @@ int dg_mlp_train(dg_ctx* ctx, const float* x, const float* y, int64_t n, const d
 
 int dg_generate_pairs(dg_ctx* ctx, double dt_for_pimax, float* x, float* y, int64_t cap, int64_t* n_out)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!x || !y || !n_out) return fail(ctx, DG_EINVAL, "dg_generate_pairs: null buffer");
     if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_generate_pairs: no state set");
@@ -1258,6 +1310,7 @@ int dg_generate_pairs(dg_ctx* ctx, double dt_for_pimax, float* x, float* y, int6
 
 int dg_av_nu(dg_ctx* ctx, float* nu_out)
 {
+    drop_carry(ctx);
     if (!ctx) return DG_EINVAL;
     if (!nu_out) return fail(ctx, DG_EINVAL, "dg_av_nu: null buffer");
     if (ctx->nu.mode != DG_AV_LEARNED || !ctx->weights_set)
@@ -1322,6 +1375,7 @@ int dg_get_meta(dg_ctx* ctx, dg_meta* m)
 
 int dg_set_meta(dg_ctx* ctx, const dg_meta* m)
 {
+    drop_carry(ctx);
     if (!ctx || !m) return DG_EINVAL;
     if (m->nmodes != ctx->drv.nm) return fail(ctx, DG_EINVAL, "dg_set_meta: call dg_set_forcing with the same modes first");
     ctx->t = m->t;

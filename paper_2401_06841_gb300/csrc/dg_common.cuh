@@ -108,20 +108,26 @@ __device__ __forceinline__ void modal_grad_T_acc(const T* f, T* r, T scale)
 // ---------------------------------------------------------------------------
 // control block in the caller's scratch (FP64 global quantities)
 // ---------------------------------------------------------------------------
+// 1D Gauss rule on [-1, 1] (n = k+1 <= 4 points)
+struct Rule1 {
+    double x[4], w[4];
+};
+
 struct Ctl {
     unsigned int status;     // sticky DG_ST_* bits
     unsigned int cnt_proj;   // last-block counter of the projection kernel
     unsigned int cnt_diag;   // last-block counter of diagnostics / L1
     unsigned int pad0;
     unsigned long long smax; // bits of max sum_d(|v_d|+cs) (positive double)
-    double dt;               // dt of the current step (fixes Pi_max)
+    double dt;               // dt of the current step (fixes Pi_max), written for the host
     double dt_scale;         // 1, 1/2, 1/4, 1/8 on retries
     double fixed_dt;         // > 0 replaces the CFL dt
     double abar2[2][3];      // <rho a_h>/<rho>, one slot per projected-velocity buffer
     double dt_num;           // cfl h / (k+1)
     double diag[16];         // diagnostics result
     double l1;               // L1 result
-    double pad[4];
+    double sn;               // max sum_d(|v_d|+cs) of the state the next step starts from
+    double pad[3];
 };
 
 // kernel flags

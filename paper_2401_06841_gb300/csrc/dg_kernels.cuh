@@ -95,91 +95,113 @@ __device__ bool last_block_reduce(double* partials, const double* mine, int nv, 
 // K_force: projection of the driving acceleration of explicit Fourier modes
 //   a(x) = sum_m 2 Re(A_m exp(2 pi i k_m . x))   (Sec. 4.2)
 //   ahat_l = sum_q (w_q/8) phi_l(xi_q) a(x_q),  x_q = x_c + (h/2) xi_q
-// Phases are built per axis from exp(2 pi i x_d) in FP64.
+// The tensor Gauss rule, the product basis and the plane waves all factor
+// over the axes, so with the 1D factors
+//   G[i_c][kap][m] = sum_a (w_a/2) Pn_m(xi_a) exp(2 pi i kap (i_c + 1/2 + xi_a/2) h)
+// each mode's projection is G[ix][kx][i_l] G[iy][ky][j_l] G[iz][kz][l_l]:
+// the same sum, regrouped.  k_force_axis builds G in FP64 (stored in T);
+// k_force forms the products per cell.
 // ---------------------------------------------------------------------------
+constexpr int kForceKM = 8;  // |k_d| <= 8 supported
+constexpr int kForceNK = 2 * kForceKM + 1;
+
+// sqrt(2m+1) P_m(x) by the three-term recurrence
+__device__ __forceinline__ double legendre_pn(int m, double x)
+{
+    double p0 = 1.0, p1 = x;
+    if (m == 0) return 1.0;
+    for (int j = 2; j <= m; ++j) {
+        const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+    }
+    return sqrt(2.0 * m + 1.0) * p1;
+}
+
 template <typename T, int K>
-__global__ void __launch_bounds__(Tile<K>::NT)
-    k_force(const T* tab, int N, long ncell, int nm, const int* kvec, const double* amp, int kmaxc, T* ahat)
+__global__ void __launch_bounds__(256) k_force_axis(Rule1 r, int N, int kmaxc, T* G)
+{
+    constexpr int n = K + 1;
+    const int total = N * kForceNK * n;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int m = e % n, kap = (e / n) % kForceNK - kForceKM, ic = e / (n * kForceNK);
+        double re = 0.0, im = 0.0;
+        if (kap >= -kmaxc && kap <= kmaxc) {
+            const double h = 1.0 / N;
+            for (int a = 0; a < n; ++a) {
+                const double wp = 0.5 * r.w[a] * legendre_pn(m, r.x[a]);
+                double sn, cn;
+                sincospi(2.0 * kap * ((ic + 0.5 + 0.5 * r.x[a]) * h), &sn, &cn);
+                re += wp * cn;
+                im += wp * sn;
+            }
+        }
+        G[2 * e] = T(re);
+        G[2 * e + 1] = T(im);
+    }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_force(const T* G, int N, long ncell, int nm, const int* kvec, const double* amp,
+                                               T* ahat)
 {
     using D = Dims<K>;
-    using L = TabLayout<K>;
-    constexpr int b = D::b, nq = D::nq, TC = Tile<K>::TC, NT = Tile<K>::NT;
-    constexpr int KM = 8;  // |k_d| <= 8 supported
-    __shared__ T s_a[TC][nq][3];
+    constexpr int b = D::b, n = K + 1;
+    constexpr Modes<K> M{};
     __shared__ int s_k[512][3];
     __shared__ T s_amp[512][3][2];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < nm; e += NT) {
+    for (int e = threadIdx.x; e < nm; e += blockDim.x) {
         for (int i = 0; i < 3; ++i) {
-            s_k[e][i] = kvec[e * 3 + i];
-            s_amp[e][i][0] = T(amp[(e * 3 + i) * 2]);
-            s_amp[e][i][1] = T(amp[(e * 3 + i) * 2 + 1]);
+            s_k[e][i] = kvec[e * 3 + i] + kForceKM;
+            s_amp[e][i][0] = T(2.0 * amp[(e * 3 + i) * 2]);
+            s_amp[e][i][1] = T(2.0 * amp[(e * 3 + i) * 2 + 1]);
         }
     }
     __syncthreads();
-    const double h = 1.0 / N;
-    const long ntile = (ncell + TC - 1) / TC;
-    const T* xq = tab + L::xq;
-    const T* wphi = tab + L::wphi;
-    for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const long c0 = tile * TC;
-        {
-            const int lc = tid / nq, q = tid % nq;
-            const long c = c0 + lc;
-            T acc[3] = {0, 0, 0};
-            if (c < ncell) {
-                const int ix = (int)(c % N), iy = (int)((c / N) % N), iz = (int)(c / ((long)N * N));
-                const int ic[3] = {ix, iy, iz};
-                T Er[3][2 * KM + 1], Ei[3][2 * KM + 1];
-                for (int d = 0; d < 3; ++d) {
-                    const double x = (ic[d] + 0.5 + 0.5 * (double)xq[q * 3 + d]) * h;
-                    double s1, c1;
-                    sincospi(2.0 * x, &s1, &c1);
-                    double pr = 1.0, pi = 0.0;
-                    Er[d][KM] = T(1);
-                    Ei[d][KM] = T(0);
-                    for (int m = 1; m <= kmaxc; ++m) {
-                        const double nr = pr * c1 - pi * s1, ni = pr * s1 + pi * c1;
-                        pr = nr;
-                        pi = ni;
-                        Er[d][KM + m] = T(pr);
-                        Ei[d][KM + m] = T(pi);
-                        Er[d][KM - m] = T(pr);
-                        Ei[d][KM - m] = T(-pi);
-                    }
-                }
-                for (int m = 0; m < nm; ++m) {
-                    const int kx = s_k[m][0] + KM, ky = s_k[m][1] + KM, kz = s_k[m][2] + KM;
-                    const T xr = Er[0][kx] * Er[1][ky] - Ei[0][kx] * Ei[1][ky];
-                    const T xi = Er[0][kx] * Ei[1][ky] + Ei[0][kx] * Er[1][ky];
-                    const T er = xr * Er[2][kz] - xi * Ei[2][kz];
-                    const T ei = xr * Ei[2][kz] + xi * Er[2][kz];
+    const long rowlen = (long)kForceNK * n * 2;  // T words per cell index of G
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell; c += (long)gridDim.x * blockDim.x) {
+        const int ix = (int)(c % N), iy = (int)((c / N) % N), iz = (int)(c / ((long)N * N));
+        const T* gx = G + ix * rowlen;
+        const T* gy = G + iy * rowlen;
+        const T* gz = G + iz * rowlen;
+        T acc[3][b];
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) acc[i] += T(2) * (s_amp[m][i][0] * er - s_amp[m][i][1] * ei);
-                }
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int l = 0; l < b; ++l) acc[v][l] = T(0);
+        for (int m = 0; m < nm; ++m) {
+            T x[n][2], y[n][2], z[n][2];
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+                x[i][0] = __ldg(gx + (s_k[m][0] * n + i) * 2);
+                x[i][1] = __ldg(gx + (s_k[m][0] * n + i) * 2 + 1);
+                y[i][0] = __ldg(gy + (s_k[m][1] * n + i) * 2);
+                y[i][1] = __ldg(gy + (s_k[m][1] * n + i) * 2 + 1);
+                z[i][0] = __ldg(gz + (s_k[m][2] * n + i) * 2);
+                z[i][1] = __ldg(gz + (s_k[m][2] * n + i) * 2 + 1);
             }
-            s_a[lc][q][0] = acc[0];
-            s_a[lc][q][1] = acc[1];
-            s_a[lc][q][2] = acc[2];
+            T A[3][2];
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                A[v][0] = s_amp[m][v][0];
+                A[v][1] = s_amp[m][v][1];
+            }
+            static_for<0, b>([&](auto L) {
+                constexpr int l = decltype(L)::value;
+                constexpr int i = M.i[l], j = M.j[l], k3 = M.l[l];
+                const T pr = x[i][0] * y[j][0] - x[i][1] * y[j][1];
+                const T pi = x[i][0] * y[j][1] + x[i][1] * y[j][0];
+                const T er = pr * z[k3][0] - pi * z[k3][1];
+                const T ei = pr * z[k3][1] + pi * z[k3][0];
+#pragma unroll
+                for (int v = 0; v < 3; ++v) acc[v][l] += A[v][0] * er - A[v][1] * ei;
+            });
         }
-        __syncthreads();
-        for (int e = tid; e < TC * b; e += NT) {
-            const int lc = e / b, l = e % b;
-            const long c = c0 + lc;
-            T r0 = 0, r1 = 0, r2 = 0;
-            for (int q = 0; q < nq; ++q) {
-                const T w = __ldg(wphi + q * b + l);
-                r0 += w * s_a[lc][q][0];
-                r1 += w * s_a[lc][q][1];
-                r2 += w * s_a[lc][q][2];
-            }
-            if (c < ncell) {
-                ahat[c * 3 * b + l] = r0;
-                ahat[c * 3 * b + b + l] = r1;
-                ahat[c * 3 * b + 2 * b + l] = r2;
-            }
-        }
-        __syncthreads();
+        T* out = ahat + c * 3 * b;
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int l = 0; l < b; ++l) out[v * b + l] = acc[v][l];
     }
 }
 

@@ -20,6 +20,8 @@ struct Launch {
     double* partials;    // [kMaxGrid][16]
     int nsm;             // multiprocessors on the device
     int bk;              // 0: CUDA-core products, 1: split-BF16 x3 tensor-core products
+    Rule1 r1;            // the 1D Gauss rule
+    void* gtab;          // forcing: 1D factors [N][17][k+1][2] of the element type
 };
 
 constexpr int kMaxGrid = 8192;

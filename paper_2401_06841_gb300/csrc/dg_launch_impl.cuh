@@ -47,7 +47,7 @@ static cudaError_t setup_k()
     if constexpr (sizeof(T) == 4) {
         if ((e = setup_modes<T, K, BK_X3>()) != cudaSuccess) return e;
     }
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::force, k_force<T, K>, NT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::force, k_force<T, K>, 256, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::diag, k_diag<T, K>, NT, 0);
     return e;
@@ -134,9 +134,12 @@ static cudaError_t tile_k(const Launch& L, const TileLaunch& t)
 template <typename T, int K>
 static cudaError_t force_k(const Launch& L, int nm, const int* kvec, const double* amp, int kmaxc, T* ahat)
 {
-    const long ntile = (L.ncell + Tile<K>::TC - 1) / Tile<K>::TC;
-    k_force<T, K><<<grid_for(ntile, Occ<T, K>::force, L.nsm), Tile<K>::NT, 0, L.st>>>(
-        static_cast<const T*>(L.tab), L.N, L.ncell, nm, kvec, amp, kmaxc, ahat);
+    if (nm > 512 || kmaxc > kForceKM) return cudaErrorInvalidValue;
+    T* G = static_cast<T*>(L.gtab);
+    const int ng = L.N * kForceNK * (K + 1);
+    k_force_axis<T, K><<<(ng + 255) / 256, 256, 0, L.st>>>(L.r1, L.N, kmaxc, G);
+    const long nb = (L.ncell + 255) / 256;
+    k_force<T, K><<<grid_for(nb, Occ<T, K>::force, L.nsm), 256, 0, L.st>>>(G, L.N, L.ncell, nm, kvec, amp, ahat);
     return cudaGetLastError();
 }
 

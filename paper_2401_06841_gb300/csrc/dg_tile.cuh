@@ -433,7 +433,7 @@ struct TArgs {
     Phys ph;
     T rk_a, rk_b;
     double dt_pimax;
-    int flags;         // F_DT | F_FORCE | F_NEXTPROJ
+    int flags;         // F_DT | F_FORCE | F_NEXTPROJ | F_VABS
     int abar_in;       // slot of ctl->abar2 read by this stage
     int abar_out;      // slot written by the projection
     const float* nu;   // per-cell viscous coefficient (learned sensor) or nullptr
@@ -597,7 +597,16 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     const bool do_proj = (MODE == TM_PROJECT) || (MODE == TM_STAGE && (a.flags & F_NEXTPROJ));
     T dt = T(0), ab0 = T(0), ab1 = T(0), ab2 = T(0);
     if constexpr (MODE != TM_PROJECT) {
-        dt = T(MODE == TM_STAGE ? a.ctl->dt : a.dt_pimax);
+        if constexpr (MODE == TM_STAGE) {
+            // the step's dt (Sec. 7 CFL condition), fixed for all its stages: from the
+            // wave-speed bound of u^n, a prescribed dt, and the retry factor
+            const double sn = a.ctl->sn;
+            const double dtd = (a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / sn) * a.ctl->dt_scale;
+            dt = T(dtd);
+            if (blockIdx.x == 0 && tid == 0) a.ctl->dt = dtd;
+        } else {
+            dt = T(a.dt_pimax);
+        }
         if (force) {
             ab0 = T(a.ctl->abar2[a.abar_in][0]);
             ab1 = T(a.ctl->abar2[a.abar_in][1]);
@@ -972,7 +981,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 if (st) atomicOr(&s_status, st);
                 __syncthreads();
                 if (do_proj) {
-                    tile_project<T, K, BK>(sm, tabs, a, c0, false, smax, sums);
+                    tile_project<T, K, BK>(sm, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums);
                     __syncthreads();
                 }
             }
@@ -1009,10 +1018,9 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     a.ctl->abar2[o][0] = a.ctl->abar2[o][1] = a.ctl->abar2[o][2] = 0.0;
                 }
                 if (a.flags & F_DT) {
+                    // every block of this launch has read ctl->sn before it arrived here
                     const unsigned long long bits = atomicAdd(&a.ctl->smax, 0ull);
-                    const double sm_ = __longlong_as_double((long long)bits);
-                    const double dtv = a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / sm_;
-                    a.ctl->dt = dtv * a.ctl->dt_scale;
+                    a.ctl->sn = __longlong_as_double((long long)bits);
                     a.ctl->smax = 0ull;
                 }
             }

@@ -132,6 +132,36 @@ def test_driven_steps_parity(k, prec):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("rk", [2, 3])
+def test_carried_projection_matches_fresh(rk):
+    # Steps that start from the projection carried over from the previous
+    # step's last stage (one call of 6 steps) against steps that project afresh
+    # (a diagnostics call between steps drops the carried projection); both
+    # against the oracle.  OU updates fall inside the run.
+    N, k = 5, 2
+    u = I.random_state(N, k, seed=71, v_rms=0.8)
+    fo = dict(mach=0.3, zeta=0.5, seed=2)   # t_c/100 spans a few steps
+    a = Solver(N, k, precision="f64", rk_stages=rk)
+    a.set_state(u)
+    a.set_forcing(**fo)
+    a.step(6)
+    b = Solver(N, k, precision="f64", rk_stages=rk)
+    b.set_state(u)
+    b.set_forcing(**fo)
+    for i in range(6):
+        b.step(1)
+        if i % 2 == 0:
+            b.diagnostics()
+    ua = a.get_state().cpu().numpy()
+    ub = b.get_state().cpu().numpy()
+    assert rel_l2_fields(ua, ub).max() < 1e-13
+    ref = u.copy()
+    rc, _, _, _ = O.run(O.make_cfg(N, k, rk_stages=rk), ref, 6, forcing=O.Forcing(**fo))
+    assert rc == 0
+    assert rel_l2_fields(ua, ref).max() < 1e-12
+
+
+@pytest.mark.gpu
 def test_limiter_parity():
     # states whose density dips below the floor: both sides rescale the same cells
     N, k = 4, 2
