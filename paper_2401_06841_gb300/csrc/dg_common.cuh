@@ -163,6 +163,37 @@ __device__ __forceinline__ T vnr_pressure(const Phys& P, T rho, T divv, T dt)
     return Pi;
 }
 
+// the same viscous pressure with the coefficients folded once per launch:
+//   Pi = rho a (a2 a + b1),  a = -div v > 0,  a2 = alpha (h/p)^2, b1 = beta cs (h/p),
+//   Pi <- min(Pi, rho a cap) with cap = (h/p)^2 / (2 dt) (cap < 0: no cap)
+template <typename T>
+struct AvCoef {
+    T a2, b1, cap;
+};
+template <typename T>
+__host__ __device__ inline AvCoef<T> av_coef(const Phys& P, double dt)
+{
+    AvCoef<T> c;
+    c.a2 = T(P.alpha * P.hp * P.hp);
+    c.b1 = T(P.beta * P.cs * P.hp);
+    c.cap = dt > 0.0 ? T(0.5 * P.hp * P.hp / dt) : T(-1);
+    return c;
+}
+template <typename T>
+__device__ __forceinline__ T vnr_pressure(const AvCoef<T>& c, T rho, T divv)
+{
+    if (!(divv < T(0))) return T(0);
+    const T ra = rho * (-divv);
+    T Pi = ra * (c.a2 * (-divv) + c.b1);
+    if (c.cap >= T(0)) {
+        // the cap compares the pressures themselves (rho may be negative at a
+        // point of a state the limiter has not seen yet)
+        const T Pm = ra * c.cap;
+        Pi = Pi < Pm ? Pi : Pm;
+    }
+    return Pi;
+}
+
 // Rusanov flux along +e_d, left/right primitive states (rho, v):
 //   F* = (F(U_L) + F(U_R))/2 - lambda (U_R - U_L)/2,
 //   lambda = max(|v_d^L|, |v_d^R|) + cs, F(U) = (rho v_d, rho v_i v_d + cs^2 rho delta_id)

@@ -239,6 +239,24 @@ __device__ __forceinline__ void stage_async(T* dst, const T* src, int count, int
     }
 }
 
+// as stage_async for a state tile [cells][4][b] (B4 = 4b elements per cell):
+// the cells past the end get rho_0 = 1 and zeros elsewhere, so that the
+// padded cells stay finite.  Each 16-byte chunk is written by one thread.
+template <typename T, int NT, int B4>
+__device__ __forceinline__ void stage_async_state(T* dst, const T* src, int count, int valid)
+{
+    constexpr int V = 16 / sizeof(T);
+    for (int e = V * threadIdx.x; e < count; e += V * NT) {
+        if (e + V <= valid) {
+            cp_async16(dst + e, src + e);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                dst[e + j] = (e + j < valid) ? src[e + j] : (((e + j) % B4) == 0 ? T(1) : T(0));
+        }
+    }
+}
+
 // reciprocal: correctly rounded in FP32 without the division subroutine
 template <typename T>
 __device__ __forceinline__ T rcp(T x)
@@ -443,14 +461,14 @@ struct TArgs {
 // viscous pressure with a per-cell coefficient (learned sensor):
 // Pi = rho nu |div v| for div v < 0, capped like the vNR form (Sec. 3.1)
 template <typename T>
-__device__ __forceinline__ T nu_pressure(const Phys& P, T rho, T divv, T nu, T dt)
+__device__ __forceinline__ T nu_pressure(const AvCoef<T>& cf, T rho, T divv, T nu)
 {
     if (!(divv < T(0))) return T(0);
-    const T a = -divv, hp = T(P.hp);
-    T Pi = rho * nu * a;
-    if (dt > T(0)) {
-        const T Pmax = T(0.5) * rho * hp * hp * a / dt;
-        Pi = Pi < Pmax ? Pi : Pmax;
+    const T ra = rho * (-divv);
+    T Pi = ra * nu;
+    if (cf.cap >= T(0)) {
+        const T Pm = ra * cf.cap;
+        Pi = Pi < Pm ? Pi : Pm;
     }
     return Pi;
 }
@@ -459,15 +477,36 @@ __device__ __forceinline__ T nu_pressure(const Phys& P, T rho, T divv, T nu, T d
 // projection of the primitive velocity of the TC states in sU (Sec. 3.2),
 // the per-cell forcing sums <rho a_h> = sum_l rho_l a_l and the CFL maximum
 // --------------------------------------------------------------------------
+// per-cell forcing sums <rho a_h> = sum_l rho_l a_l (orthonormal basis) and <rho>
+template <typename T, int K, int BK>
+__device__ __forceinline__ void forcing_sums(const T* sm, const T* sU, const TArgs<T>& a, long c0, double* sums)
+{
+    using C = TileCfg<K, BK>;
+    constexpr int b = C::b, TC = C::TC;
+    const T* sAh = sm + C::oAh;
+    const long nvalid = (a.ncell - c0) < TC ? (a.ncell - c0) : TC;
+    if (threadIdx.x < TC * 3) {
+        const int c = threadIdx.x / 3, i = threadIdx.x % 3;
+        if (c < nvalid) {
+            const T* u = sU + c * 4 * b;
+            const T* ah = sAh + (c * 3 + i) * b;
+            T s = T(0);
+#pragma unroll
+            for (int l = 0; l < b; ++l) s += u[l] * ah[l];
+            sums[i] += (double)s;
+            if (i == 0) sums[3] += (double)u[0];
+        }
+    }
+}
+
 template <typename T, int K, int BK, bool VABS = false>
-__device__ __forceinline__ void tile_project(T* sm, const T* tabs, const TArgs<T>& a, long c0, bool dt_flag, T& smax,
-                                             double* sums)
+__device__ __forceinline__ void tile_project(T* sm, const T* sU, const T* tabs, const TArgs<T>& a, long c0, bool dt_flag,
+                                             T& smax, double* sums, bool with_sums)
 {
     constexpr int NPR = VABS ? 4 : 3;  // projected rows per cell: v (and |v|)
     using C = TileCfg<K, BK>;
     constexpr int b = C::b, nq = C::nq, TC = C::TC, NT = C::NT, KP = C::KP, NQP = C::NQP, NP = C::NP;
     constexpr int LDA = C::LDA, LDV = C::LDV, LDP = C::LDP;
-    T* sU = sm + C::oU;
     T* sA = sm + C::oA;
     T* sV = sm + C::oBig;
     T* sP = sm + C::oP;
@@ -528,23 +567,7 @@ __device__ __forceinline__ void tile_project(T* sm, const T* tabs, const TArgs<T
             if (c0 + c < a.ncell) a.vabs_out[c0 * b + e] = sP[(c * NPR + 3) * LDP + l];
         }
     }
-    if (a.flags & F_FORCE) {
-        // <rho a_h> per cell from the tile's staged forcing coefficients
-        const T* sAh = sm + C::oAh;
-        const long nvalid = (a.ncell - c0) < TC ? (a.ncell - c0) : TC;
-        if (threadIdx.x < TC * 3) {
-            const int c = threadIdx.x / 3, i = threadIdx.x % 3;
-            if (c < nvalid) {
-                const T* u = sU + c * 4 * b;
-                const T* ah = sAh + (c * 3 + i) * b;
-                T s = T(0);
-#pragma unroll
-                for (int l = 0; l < b; ++l) s += u[l] * ah[l];
-                sums[i] += (double)s;
-                if (i == 0) sums[3] += (double)u[0];
-            }
-        }
-    }
+    if (with_sums && (a.flags & F_FORCE)) forcing_sums<T, K, BK>(sm, sU, a, c0, sums);
 }
 
 template <typename T, int K, int MODE, int BK>
@@ -596,6 +619,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     double sums[4] = {0.0, 0.0, 0.0, 0.0};
     const bool do_proj = (MODE == TM_PROJECT) || (MODE == TM_STAGE && (a.flags & F_NEXTPROJ));
     T dt = T(0), ab0 = T(0), ab1 = T(0), ab2 = T(0);
+    AvCoef<T> avc{};
     if constexpr (MODE != TM_PROJECT) {
         if constexpr (MODE == TM_STAGE) {
             // the step's dt (Sec. 7 CFL condition), fixed for all its stages: from the
@@ -603,9 +627,11 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             const double sn = a.ctl->sn;
             const double dtd = (a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / sn) * a.ctl->dt_scale;
             dt = T(dtd);
+            avc = av_coef<T>(a.ph, dtd);
             if (blockIdx.x == 0 && tid == 0) a.ctl->dt = dtd;
         } else {
             dt = T(a.dt_pimax);
+            avc = av_coef<T>(a.ph, a.dt_pimax);
         }
         if (force) {
             ab0 = T(a.ctl->abar2[a.abar_in][0]);
@@ -613,45 +639,73 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             ab2 = T(a.ctl->abar2[a.abar_in][2]);
         }
     }
+    // stage mode: the inputs of a tile (u^(s), its projected velocity, a_h, u^n)
+    // are fetched asynchronously while the previous tile finishes (its
+    // projection for the next stage); u lands in the right-hand-side buffer,
+    // free by then, and is moved to the state buffer when the tile starts
+    auto issue = [&](long t, T* dU) {
+        const long cb = t * TC;
+        const int nv = (int)((a.ncell - cb) < TC ? (a.ncell - cb) : TC);
+        stage_async_state<T, NT, 4 * b>(dU, a.u_in + cb * 4 * b, TC * 4 * b, nv * 4 * b);
+        stage_async<T, NT>(sVH, a.vh_in + cb * 3 * b, TC * 3 * b, nv * 3 * b);
+        if (force) stage_async<T, NT>(sAh, a.ahat + cb * 3 * b, TC * 3 * b, nv * 3 * b);
+        if (a.rk_a != T(0)) stage_async<T, NT>(sUn, a.u_n + cb * 4 * b, TC * 4 * b, nv * 4 * b);
+        cp_async_commit();
+    };
+    if constexpr (MODE == TM_STAGE) {
+        if (blockIdx.x < ntile) issue(blockIdx.x, sU);
+    }
     __syncthreads();
 
     for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const long c0 = tile * TC;
         const long nvalid = (a.ncell - c0) < TC ? (a.ncell - c0) : TC;
-        // ---- stage the tile (cells past the end: rho = 1, everything else 0) ----
-        for (int e = 4 * tid; e < TC * 4 * b; e += 4 * NT) {
-            T v[4];
-            ld4_guard<T>(a.u_in + c0 * 4 * b, e, (int)nvalid * 4 * b, v);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if ((e + j) / (4 * b) >= nvalid) v[j] = ((e + j) % (4 * b)) == 0 ? T(1) : T(0);
-            st4<T>(sU + e, v);
-        }
-        // two commit groups: the tile's a_h (needed first), then u^n (needed by the epilogue)
-        if (force) stage_async<T, NT>(sAh, a.ahat + c0 * 3 * b, TC * 3 * b, (int)nvalid * 3 * b);
-        cp_async_commit();
         if constexpr (MODE == TM_STAGE) {
-            if (a.rk_a != T(0)) stage_async<T, NT>(sUn, a.u_n + c0 * 4 * b, TC * 4 * b, (int)nvalid * 4 * b);
-        }
-        cp_async_commit();
-        if constexpr (MODE == TM_PROJECT) {
+            if (tid < TC) s_nu[tid] = (a.ph.av_mode == 2 && tid < nvalid) ? T(a.nu[c0 + tid]) : T(0);
             cp_async_wait_all();
             __syncthreads();
-            if (a.flags & F_VABS)
-                tile_project<T, K, BK, true>(sm, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums);
-            else
-                tile_project<T, K, BK, false>(sm, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums);
-            __syncthreads();
-            continue;
+            if (tile != blockIdx.x) {
+                // prefetched into the right-hand-side buffer (free at the time):
+                // move to the state buffer (fixed buffers keep the addressing static)
+                for (int e = 4 * tid; e < TC * 4 * b; e += 4 * NT) {
+                    T v[4];
+                    ld4<T>(sR + e, v);
+                    st4<T>(sU + e, v);
+                }
+                __syncthreads();
+            }
         } else {
+            // ---- stage the tile (cells past the end: rho = 1, everything else 0) ----
+            for (int e = 4 * tid; e < TC * 4 * b; e += 4 * NT) {
+                T v[4];
+                ld4_guard<T>(a.u_in + c0 * 4 * b, e, (int)nvalid * 4 * b, v);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if ((e + j) / (4 * b) >= nvalid) v[j] = ((e + j) % (4 * b)) == 0 ? T(1) : T(0);
+                st4<T>(sU + e, v);
+            }
+            if (force) stage_async<T, NT>(sAh, a.ahat + c0 * 3 * b, TC * 3 * b, (int)nvalid * 3 * b);
+            cp_async_commit();
+            if constexpr (MODE == TM_PROJECT) {
+                cp_async_wait_all();
+                __syncthreads();
+                if (a.flags & F_VABS)
+                    tile_project<T, K, BK, true>(sm, sU, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums, true);
+                else
+                    tile_project<T, K, BK, false>(sm, sU, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums, true);
+                __syncthreads();
+                continue;
+            }
             if (tid < TC) s_nu[tid] = (a.ph.av_mode == 2 && tid < nvalid) ? T(a.nu[c0 + tid]) : T(0);
             for (int e = 4 * tid; e < TC * 3 * b; e += 4 * NT) {
                 T v[4];
                 ld4_guard<T>(a.vh_in + c0 * 3 * b, e, (int)nvalid * 3 * b, v);
                 st4<T>(sVH + e, v);
             }
-            cp_async_wait_prior();
+            cp_async_wait_all();
             __syncthreads();
+        }
+        if constexpr (MODE != TM_PROJECT) {
             for (int e = tid; e < TC * 3 * b; e += NT) {
                 const int c = e / (3 * b), i = (e / b) % 3, l = e % b;
                 sA[(c * FE + 8 + i) * LDA + l] = (force && c < nvalid) ? sAh[e] : T(0);
@@ -714,9 +768,9 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                         const T divv = (v[7 * LDV] - (vx * v[4 * LDV] + vy * v[5 * LDV] + vz * v[6 * LDV])) * ir;
                         T Pi = T(0);
                         if (a.ph.av_mode == 1)
-                            Pi = vnr_pressure<T>(a.ph, rho, divv, dt);
+                            Pi = vnr_pressure<T>(avc, rho, divv);
                         else if (a.ph.av_mode == 2)
-                            Pi = nu_pressure<T>(a.ph, rho, divv, s_nu[c], dt);
+                            Pi = nu_pressure<T>(avc, rho, divv, s_nu[c]);
                         const T P = cs2 * rho + Pi;
                         fl[it][0] = mx * vx + P;
                         fl[it][1] = my * vy + P;
@@ -885,7 +939,6 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 __syncthreads();
             } else {
                 // SSP-RK stage combine (Sec. 7), new state kept in sU; u^n was prefetched
-                cp_async_wait_all();
                 __syncthreads();
                 for (int e = tid; e < TC * 4 * b; e += NT) {
                     T w;
@@ -980,8 +1033,14 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 }
                 if (st) atomicOr(&s_status, st);
                 __syncthreads();
+                if (do_proj && force) {
+                    forcing_sums<T, K, BK>(sm, sU, a, c0, sums);
+                    __syncthreads();
+                }
+                // the staging buffers of this tile are free: fetch the next tile
+                if (tile + gridDim.x < ntile) issue(tile + gridDim.x, sR);
                 if (do_proj) {
-                    tile_project<T, K, BK>(sm, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums);
+                    tile_project<T, K, BK>(sm, sU, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums, false);
                     __syncthreads();
                 }
             }
