@@ -106,6 +106,27 @@ def peaks():
     return 6800.0, 1900.0, "fallback"
 
 
+def profiled_traffic(args, variant):
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary
+    of this workload, or None when there is none or the kernel sources changed
+    since the capture (their SHA-1 is recorded next to the figure)."""
+    import hashlib
+    import re
+    f = os.path.join(ROOT, "profiles", "k_tile_%s_stage_%dc_k%d.md" % (variant, args.N, args.k))
+    if not os.path.exists(f):
+        return None
+    txt = open(f).read()
+    m_t = re.search(r"traffic_per_launch_bytes:\s*(\d+)", txt)
+    m_h = re.search(r"kernel_sources_sha1:\s*([0-9a-f]{40})", txt)
+    if not (m_t and m_h):
+        return None
+    h = hashlib.sha1()
+    for name in ("dg_tile.cuh", "dg_common.cuh", "dg_launch_impl.cuh"):
+        with open(os.path.join(ROOT, "paper_2401_06841_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return int(m_t.group(1)) if h.hexdigest() == m_h.group(1) else None
+
+
 def oracle_arm(args, steps, warmup):
     """FP64 CPU oracle on a bounded sample: a 16^3 box at the workload's degree."""
     from oracle import oracle as O
@@ -300,7 +321,8 @@ def main():
     hbm, bf16, src = peaks()
     achieved = bytes_per_launch / (rhs_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "k_tile stage (RHS + SSP-RK stage + positivity + next projection), %s" % head,
+            "traffic": profiled_traffic(args, head),
+            "kernel": "k_tile stage (RHS + SSP-RK stage + positivity + next projection), %s" % head,
             "peak_source": src, "launches_timed": int(n_stage),
             "kernel_ms": rhs_ms, "bytes_per_launch": bytes_per_launch}
 
