@@ -46,7 +46,8 @@ def workload(args):
                         % (args.N, args.k, args.k, args.mach),
             "N": args.N, "k": args.k, "dof": 4 * ((args.k + 1) * (args.k + 2) * (args.k + 3) // 6) * args.N ** 3,
             "rk_stages": 3, "mach": args.mach, "cs": 1.0, "cfl": 0.3, "av": "vNR alpha=2 beta=0.2",
-            "riemann": "Rusanov", "forcing": "OU |k|<=3 zeta=0.5 seed 0",
+            "riemann": {"rusanov": "Rusanov", "hll": "HLL", "hllc": "HLLC"}[args.riemann],
+            "forcing": "OU |k|<=3 zeta=0.5 seed 0",
             "state": "synthetic k^-2 velocity (seed 102) relaxed %d driven steps" % args.relax,
             "l2": "flushed (256 MB write) before every timed step"}
 
@@ -132,7 +133,7 @@ def oracle_arm(args, steps, warmup):
     from oracle import oracle as O
     from paper_2401_06841_gb300 import inputs as I
     n = args.sample_N
-    cfg = O.make_cfg(n, args.k, rk_stages=3)
+    cfg = O.make_cfg(n, args.k, rk_stages=3, riemann=args.riemann)
     u = I.turbulent_state(n, args.k, seed=102, mach=args.mach)
     fo = O.Forcing(mach=args.mach, zeta=0.5, seed=0)
     t, ahat = 0.0, None
@@ -181,6 +182,7 @@ def main():
     ap.add_argument("--variants", default="f32,x3,learned-f32,learned-x3")
     ap.add_argument("--no-cpu", dest="no_cpu", action="store_true")
     ap.add_argument("--no-l1", dest="no_l1", action="store_true")
+    ap.add_argument("--riemann", default="rusanov", choices=["rusanov", "hll", "hllc"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -205,7 +207,7 @@ def main():
     S = 3
     dof = 4 * b * N ** 3
     # the relaxed driven state (independent replica per rank)
-    base = Solver(N, k, precision="f32", rk_stages=S, device=dev)
+    base = Solver(N, k, precision="f32", rk_stages=S, device=dev, riemann=args.riemann)
     base.set_state(I.turbulent_state(N, k, seed=102 + rank, mach=args.mach))
     base.set_forcing(mach=args.mach, zeta=0.5, seed=rank)
     snaps = []
@@ -220,7 +222,7 @@ def main():
     weights = None
     if any(v.startswith("learned") for v in variants):
         # plain-sensor pairs of the relaxed snapshots -> trained weights (untimed)
-        trainer = Solver(N, k, precision="f32", av="learned", device=dev)
+        trainer = Solver(N, k, precision="f32", av="learned", device=dev, riemann=args.riemann)
         trainer.set_av_weights(I.mlp_init(2 * b, seed=1))
         xs, ys = [], []
         for u, dtl in snaps:
@@ -239,7 +241,8 @@ def main():
 
     def make(v):
         prec = v.split("-")[-1]
-        s = Solver(N, k, precision=prec, rk_stages=S, av="learned" if v.startswith("learned") else "vnr", device=dev)
+        s = Solver(N, k, precision=prec, rk_stages=S, av="learned" if v.startswith("learned") else "vnr", device=dev,
+                   riemann=args.riemann)
         if weights is not None and v.startswith("learned"):
             s.set_av_weights(weights)
         return s
@@ -288,7 +291,7 @@ def main():
     if not args.no_l1:
         dt0 = 0.3 * (1.0 / N) / ((k + 1) * base.diagnostics()["max_speed"])
         dt = 0.8 * dt0
-        fine = Solver(2 * N, k, precision="f32", rk_stages=S, device=dev)
+        fine = Solver(2 * N, k, precision="f32", rk_stages=S, device=dev, riemann=args.riemann)
         fine.set_state(Tr.prolong(S0, N, k))
         fine.step(2 * args.l1_steps, fixed_dt=dt / 2)
         ref = Tr.restrict(fine.get_state(), N, k).contiguous()

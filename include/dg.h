@@ -56,6 +56,14 @@ extern "C" {
 #define DG_AV_VNR 1        /* von Neumann-Richtmyer viscous pressure (Sec. 3.1)  */
 #define DG_AV_LEARNED 2    /* per-cell coefficient predicted by the MLP           */
 
+/* ---- face flux (Sec. 2: approximate Riemann solver on cell faces) --------- */
+#define DG_RIEMANN_RUSANOV 0  /* local Lax-Friedrichs: F* = {F} - max(|v_n|+cs) [U]/2 */
+#define DG_RIEMANN_HLL 1      /* HLL with the Davis speed bounds
+                                 S_L = min(v_n^L, v_n^R) - cs, S_R = max(v_n^L, v_n^R) + cs */
+#define DG_RIEMANN_HLLC 2     /* HLLC (Toro) for p = cs^2 rho, the paper's face solver:
+                                 HLL mass and normal momentum; the tangential momenta
+                                 cross with the side of the contact wave S_M = m*_n/rho* */
+
 /* status bits reported by dg_step / dg_diagnostics */
 #define DG_ST_LIMITED 1u   /* positivity rescaling happened in some cell         */
 #define DG_ST_FAIL 2u      /* a cell mean reached the density floor              */
@@ -95,6 +103,7 @@ typedef struct {
     void* ahat;            /* N^3*3*b elements                                     */
     void* scratch;         /* >= dg_scratch_bytes(), 256-byte aligned              */
     size_t scratch_bytes;
+    int32_t riemann;       /* DG_RIEMANN_*; 0 (Rusanov) when zero-initialised     */
 } dg_opts;
 
 /* Driving (Sec. 4.2, eq. ornstein_uhlenbeck_process_time_evolution).  Modes:

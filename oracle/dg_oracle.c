@@ -246,6 +246,87 @@ void orc_rusanov(double cs, int d, const double WL[4], const double WR[4], doubl
     for (int v = 0; v < 4; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
 }
 
+/* Conserved state and flux along e_d of a primitive state W = (rho, v). */
+static void cons_flux(double cs, int d, const double W[4], double U[4], double F[4])
+{
+    U[0] = W[0];
+    for (int i = 0; i < 3; ++i) U[1 + i] = W[0] * W[1 + i];
+    F[0] = U[1 + d];
+    for (int i = 0; i < 3; ++i) F[1 + i] = U[1 + i] * W[1 + d] + (i == d ? cs * cs * W[0] : 0.0);
+}
+
+/* HLL flux along +e_d (Harten, Lax & van Leer; Toro, Riemann Solvers, ch. 10).
+ * The isothermal signal speeds are bounded by the Davis estimates
+ *   S_L = min(v_d^L, v_d^R) - cs,   S_R = max(v_d^L, v_d^R) + cs,
+ * and the flux is F_L for S_L >= 0, F_R for S_R <= 0, otherwise the flux of
+ * the single averaged state between the two waves,
+ *   F* = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L). */
+void orc_hll(double cs, int d, const double WL[4], const double WR[4], double F[4])
+{
+    double UL[4], UR[4], FL[4], FR[4];
+    cons_flux(cs, d, WL, UL, FL);
+    cons_flux(cs, d, WR, UR, FR);
+    const double SL = fmin(WL[1 + d], WR[1 + d]) - cs;
+    const double SR = fmax(WL[1 + d], WR[1 + d]) + cs;
+    for (int v = 0; v < 4; ++v) {
+        if (SL >= 0.0)
+            F[v] = FL[v];
+        else if (SR <= 0.0)
+            F[v] = FR[v];
+        else
+            F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
+    }
+}
+
+/* HLLC flux along +e_d for the isothermal system (Toro's HLLC with p = cs^2 rho,
+ * the scheme the paper uses on faces, Sec. 2).  With the HLL speeds S_L, S_R,
+ * the star region holds two states separated by the contact wave
+ * S_M = m_d* / rho*.  Pressure continuity across the contact makes the density
+ * the same on both sides, so rho* and m_d* are the HLL averages
+ *   U_hll = (S_R U_R - S_L U_L - (F_R - F_L)) / (S_R - S_L),
+ * and each star state carries the tangential velocity of its own side:
+ *   U*_K = (rho*, m_d*, rho* v_t^K).
+ * The flux is F_L (S_L >= 0), F*_L = F_L + S_L (U*_L - U_L) (S_L < 0 <= S_M),
+ * F*_R = F_R + S_R (U*_R - U_R) (S_M < 0 < S_R), F_R (S_R <= 0). */
+void orc_hllc(double cs, int d, const double WL[4], const double WR[4], double F[4])
+{
+    double UL[4], UR[4], FL[4], FR[4];
+    cons_flux(cs, d, WL, UL, FL);
+    cons_flux(cs, d, WR, UR, FR);
+    const double SL = fmin(WL[1 + d], WR[1 + d]) - cs;
+    const double SR = fmax(WL[1 + d], WR[1 + d]) + cs;
+    if (SL >= 0.0) {
+        for (int v = 0; v < 4; ++v) F[v] = FL[v];
+        return;
+    }
+    if (SR <= 0.0) {
+        for (int v = 0; v < 4; ++v) F[v] = FR[v];
+        return;
+    }
+    const double rs = (SR * UR[0] - SL * UL[0] - (FR[0] - FL[0])) / (SR - SL);
+    const double ms = (SR * UR[1 + d] - SL * UL[1 + d] - (FR[1 + d] - FL[1 + d])) / (SR - SL);
+    const double SM = ms / rs;
+    const int left = SM >= 0.0;
+    const double* W = left ? WL : WR;
+    const double* U = left ? UL : UR;
+    const double* FK = left ? FL : FR;
+    const double SK = left ? SL : SR;
+    double Us[4];
+    Us[0] = rs;
+    for (int i = 0; i < 3; ++i) Us[1 + i] = (i == d) ? ms : rs * W[1 + i];
+    for (int v = 0; v < 4; ++v) F[v] = FK[v] + SK * (Us[v] - U[v]);
+}
+
+void orc_riemann(int solver, double cs, int d, const double WL[4], const double WR[4], double F[4])
+{
+    if (solver == ORC_HLL)
+        orc_hll(cs, d, WL, WR, F);
+    else if (solver == ORC_HLLC)
+        orc_hllc(cs, d, WL, WR, F);
+    else
+        orc_rusanov(cs, d, WL, WR, F);
+}
+
 /* ------------------------------------------------------------------------ */
 /* CFL time step (Sec. 7: dt proportional to h/(k+1))                        */
 /*   dt = cfl h / ((k+1) max_{cells, volume points} sum_d (|v_d| + cs))     */
@@ -425,7 +506,7 @@ static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, dou
                             WL[1 + i] = eval(&T, vhat + ((size_t)cL * 3 + i) * b, phL + s * b);
                             WR[1 + i] = eval(&T, vhat + ((size_t)cR * 3 + i) * b, phR + s * b);
                         }
-                        orc_rusanov(cfg->cs, d, WL, WR, Fs);
+                        orc_riemann(cfg->riemann, cfg->cs, d, WL, WR, Fs);
                         for (int var = 0; var < 4; ++var)
                             for (int l = 0; l < b; ++l) {
                                 dudt[((size_t)cL * 4 + var) * b + l] -= T.ws[s] * phL[s * b + l] * Fs[var] / (4.0 * h);

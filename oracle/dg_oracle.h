@@ -34,7 +34,12 @@ typedef struct {
     double rho_floor;   /* positivity floor epsilon                         */
     double cfl;         /* Courant number                                   */
     int32_t rk_stages;  /* 2 (SSP-RK2) or 3 (SSP-RK3)                        */
+    int32_t riemann;    /* face flux: 0 Rusanov, 1 HLL, 2 HLLC               */
 } orc_cfg;
+
+#define ORC_RUSANOV 0
+#define ORC_HLL 1
+#define ORC_HLLC 2
 
 /* status bits of a stage / step */
 #define ORC_LIMITED 1   /* at least one cell was rescaled by the limiter    */
@@ -66,6 +71,10 @@ void orc_forcing_mean(const orc_cfg* cfg, const double* u, const double* ahat,
                       double abar[3]);
 double orc_vnr(const orc_cfg* cfg, double rho, double divv, double dt);
 void orc_rusanov(double cs, int d, const double WL[4], const double WR[4],
+                 double F[4]);
+void orc_hll(double cs, int d, const double WL[4], const double WR[4], double F[4]);
+void orc_hllc(double cs, int d, const double WL[4], const double WR[4], double F[4]);
+void orc_riemann(int solver, double cs, int d, const double WL[4], const double WR[4],
                  double F[4]);
 int orc_rhs(const orc_cfg* cfg, const double* u, const double* ahat,
             double dt_pimax, double* dudt);

@@ -39,7 +39,10 @@ def build(force: bool = False) -> str:
 class Cfg(C.Structure):
     _fields_ = [("N", C.c_int32), ("k", C.c_int32), ("cs", C.c_double), ("av_mode", C.c_int32),
                 ("alpha", C.c_double), ("beta", C.c_double), ("rho_floor", C.c_double), ("cfl", C.c_double),
-                ("rk_stages", C.c_int32)]
+                ("rk_stages", C.c_int32), ("riemann", C.c_int32)]
+
+
+RIEMANN = {"rusanov": 0, "hll": 1, "hllc": 2}
 
 
 MAX_MODES = 512
@@ -72,6 +75,7 @@ def lib():
         _lib.orc_legendre_deriv.argtypes = [C.c_int, C.c_double]
         _lib.orc_vnr.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double]
         _lib.orc_rusanov.argtypes = [C.c_double, C.c_int, d, d, d]
+        _lib.orc_riemann.argtypes = [C.c_int, C.c_double, C.c_int, d, d, d]
         _lib.orc_ou_init.argtypes = [C.POINTER(OU), C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                      C.c_double, C.c_uint64, C.c_double]
         _lib.orc_rhs.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d]
@@ -119,10 +123,11 @@ def legendre_deriv(m: int, x: float) -> float:
     return lib().orc_legendre_deriv(m, x)
 
 
-def make_cfg(N, k, cs=1.0, av_mode=1, alpha=2.0, beta=0.2, rho_floor=1e-3, cfl=0.3, rk_stages=None) -> Cfg:
+def make_cfg(N, k, cs=1.0, av_mode=1, alpha=2.0, beta=0.2, rho_floor=1e-3, cfl=0.3, rk_stages=None,
+             riemann="rusanov") -> Cfg:
     if rk_stages is None:
         rk_stages = 2 if k == 1 else 3
-    return Cfg(N, k, cs, av_mode, alpha, beta, rho_floor, cfl, rk_stages)
+    return Cfg(N, k, cs, av_mode, alpha, beta, rho_floor, cfl, rk_stages, RIEMANN[riemann])
 
 
 def _shape(cfg, nvar=4):
@@ -154,6 +159,15 @@ def rusanov(cs: float, d: int, WL, WR) -> np.ndarray:
     WR = np.ascontiguousarray(WR, dtype=np.float64)
     F = np.zeros(4)
     lib().orc_rusanov(cs, d, _p(WL), _p(WR), _p(F))
+    return F
+
+
+def riemann(solver: str, cs: float, d: int, WL, WR) -> np.ndarray:
+    """Face flux along +e_d of the named solver ("rusanov", "hll", "hllc")."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.zeros(4)
+    lib().orc_riemann(RIEMANN[solver], cs, d, _p(WL), _p(WR), _p(F))
     return F
 
 

@@ -440,6 +440,7 @@ struct dg_ctx {
     cudaStream_t st = nullptr;
     void* reg[3] = {nullptr, nullptr, nullptr};
     int cur = 0;
+    int riemann = 0;  // DG_RIEMANN_*
     // projection carried over from the last stage of the previous step:
     // vhat buffer / abar slot pb and ctl->sn already hold the projection,
     // the forcing sums and the wave-speed bound of reg[cur]
@@ -579,6 +580,7 @@ Launch make_launch(const dg_ctx* c)
     L.ph.beta = c->nu.beta;
     L.ph.floor_ = c->nu.rho_floor;
     L.ph.av_mode = c->nu.mode;
+    L.ph.riemann = c->riemann;
     L.tab = c->tab;
     L.ttab = c->ttab;
     L.ctl = c->ctl;
@@ -793,6 +795,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     if (opts->precision < 0 || opts->precision > 2) return DG_EINVAL;
     if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
     if (!(opts->cfl > 0.0)) return DG_EINVAL;
+    if (opts->riemann < DG_RIEMANN_RUSANOV || opts->riemann > DG_RIEMANN_HLLC) return DG_EINVAL;
     if (!opts->stream) return DG_EINVAL;
     for (int i = 0; i < 3; ++i)
         if (!opts->u[i]) return DG_EINVAL;
@@ -811,6 +814,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->cs = cs;
     ctx->cfl = opts->cfl;
     ctx->rk = opts->rk_stages;
+    ctx->riemann = opts->riemann;
     ctx->prec = opts->precision;
     ctx->nu = *nu;
     ctx->st = (cudaStream_t)opts->stream;

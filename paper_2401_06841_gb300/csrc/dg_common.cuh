@@ -145,6 +145,7 @@ struct Phys {
     double cs, cs2, h, hp;       // sound speed, cs^2, cell size, h/(k+1)
     double alpha, beta, floor_;  // vNR coefficients, density floor
     int av_mode;                 // 0 off, 1 vNR, 2 learned
+    int riemann;                 // face flux: 0 Rusanov, 1 HLL, 2 HLLC
 };
 
 // von Neumann-Richtmyer viscous pressure at a volume point (Sec. 3.1):
@@ -222,15 +223,66 @@ __device__ __forceinline__ void rusanov(T cs, T cs2, const T WL[4], const T WR[4
     for (int v = 0; v < 4; ++v) F[v] = T(0.5) * (FL[v] + FR[v]) - T(0.5) * lam * (UR[v] - UL[v]);
 }
 
-template <typename T>
-__device__ __forceinline__ void rusanov_dir(int d, T cs, T cs2, const T WL[4], const T WR[4], T F[4])
+// HLL flux along +e_d with the Davis bounds S_L = min(v_d^L, v_d^R) - cs,
+// S_R = max(v_d^L, v_d^R) + cs: the upwind flux when both bounds have one sign,
+// else (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).  With CONTACT
+// (HLLC for p = cs^2 rho, the paper's solver) the mass and normal-momentum
+// fluxes stay HLL's and the tangential momenta cross the face with the mass
+// flux at the tangential velocity of the side the contact wave
+// S_M = m_d*/rho* (HLL averages) leaves behind.
+template <typename T, int D, bool CONTACT>
+__device__ __forceinline__ void hll(T cs, T cs2, const T WL[4], const T WR[4], T F[4])
 {
-    if (d == 0)
-        rusanov<T, 0>(cs, cs2, WL, WR, F);
-    else if (d == 1)
-        rusanov<T, 1>(cs, cs2, WL, WR, F);
+    const T vl = WL[1 + D], vr = WR[1 + D];
+    const T SL = fmin(vl, vr) - cs, SR = fmax(vl, vr) + cs;
+    T UL[4], UR[4], FL[4], FR[4];
+    UL[0] = WL[0];
+    UR[0] = WR[0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        UL[1 + i] = WL[0] * WL[1 + i];
+        UR[1 + i] = WR[0] * WR[1 + i];
+    }
+    FL[0] = UL[1 + D];
+    FR[0] = UR[1 + D];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        FL[1 + i] = UL[1 + i] * vl + (i == D ? cs2 * WL[0] : T(0));
+        FR[1 + i] = UR[1 + i] * vr + (i == D ? cs2 * WR[0] : T(0));
+    }
+    if (SL >= T(0)) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) F[v] = FL[v];
+        return;
+    }
+    if (SR <= T(0)) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) F[v] = FR[v];
+        return;
+    }
+    const T inv = T(1) / (SR - SL);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) * inv;
+    if constexpr (CONTACT) {
+        const T rs = (SR * UR[0] - SL * UL[0] - (FR[0] - FL[0])) * inv;
+        const T ms = (SR * UR[1 + D] - SL * UL[1 + D] - (FR[1 + D] - FL[1 + D])) * inv;
+        const T* Wup = (ms / rs >= T(0)) ? WL : WR;
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (t != D) F[1 + t] = F[0] * Wup[1 + t];
+    }
+}
+
+// the face flux selected by Phys::riemann (uniform over a launch)
+template <typename T, int D>
+__device__ __forceinline__ void riemann_flux(int solver, T cs, T cs2, const T WL[4], const T WR[4], T F[4])
+{
+    if (solver == 2)
+        hll<T, D, true>(cs, cs2, WL, WR, F);
+    else if (solver == 1)
+        hll<T, D, false>(cs, cs2, WL, WR, F);
     else
-        rusanov<T, 2>(cs, cs2, WL, WR, F);
+        rusanov<T, D>(cs, cs2, WL, WR, F);
 }
 
 // ordered integer keys so that atomicMin/Max work on floating-point values

@@ -257,14 +257,19 @@ __device__ __forceinline__ void stage_async_state(T* dst, const T* src, int coun
     }
 }
 
-// reciprocal: correctly rounded in FP32 without the division subroutine
+// reciprocal: in FP32 the hardware approximation (PTX rcp.approx) refined by
+// one Newton-Raphson step r <- r + r (1 - x r), within about one ulp of 1/x
 template <typename T>
 __device__ __forceinline__ T rcp(T x)
 {
-    if constexpr (sizeof(T) == 4)
-        return __frcp_rn(x);
-    else
+    if constexpr (sizeof(T) == 4) {
+        float r0;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x));
+        const float e = fmaf(-x, r0, 1.0f);
+        return fmaf(r0, e, r0);
+    } else {
         return T(1) / x;
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -908,9 +913,9 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                             Wn[f] = sTr[(rn + f) * LDT + s];
                         }
                         if (side)
-                            rusanov<T, Dd>(cs, cs2, Ws, Wn, F);
+                            riemann_flux<T, Dd>(a.ph.riemann, cs, cs2, Ws, Wn, F);
                         else
-                            rusanov<T, Dd>(cs, cs2, Wn, Ws, F);
+                            riemann_flux<T, Dd>(a.ph.riemann, cs, cs2, Wn, Ws, F);
                     }
 #pragma unroll
                     for (int v = 0; v < 4; ++v) sFs[((c * 2 + side) * 4 + v) * LDT + s] = F[v];

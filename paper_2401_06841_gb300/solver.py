@@ -19,11 +19,12 @@ class Solver:
     """DG solver context on one GPU.
 
     N cells per axis, degree k (1..3), sound speed cs; precision 'f64', 'f32'
-    or 'x3'; av 'off' | 'vnr' | 'learned'."""
+    or 'x3'; av 'off' | 'vnr' | 'learned'; face flux riemann 'rusanov' | 'hll' | 'hllc'."""
 
     def __init__(self, N: int, k: int, cs: float = 1.0, precision: str = "f32", rk_stages: int | None = None,
                  cfl: float = 0.3, av: str = "vnr", alpha: float = 2.0, beta: float = 0.2, rho_floor: float = 1e-3,
-                 nu_gate: float = 0.0, device: str | int = "cuda", stream: torch.cuda.Stream | None = None):
+                 nu_gate: float = 0.0, device: str | int = "cuda", stream: torch.cuda.Stream | None = None,
+                 riemann: str = "rusanov"):
         self.L = B.lib()
         self.N, self.k, self.cs = N, k, cs
         self.b = nmodes(k)
@@ -53,7 +54,7 @@ class Solver:
         off = (-base) % 256
         opts = B.Opts(self.prec, rk_stages, cfl, C.c_void_p(self.stream.cuda_stream),
                       (C.c_void_p * 3)(*[r.data_ptr() for r in self.regs]), self.vhat.data_ptr(),
-                      self.ahat.data_ptr(), base + off, int(nb.value))
+                      self.ahat.data_ptr(), base + off, int(nb.value), B.RIEMANN[riemann])
         torch.cuda.synchronize(self.device)
         h = C.c_void_p(0)
         rc = self.L.dg_init(C.byref(h), C.byref(self.mesh), k, cs, C.byref(self.nu), C.byref(opts))

@@ -65,6 +65,60 @@ def test_rhs_parity(k, prec, forced):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("riemann", ["hll", "hllc"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "x3"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_rhs_parity_hll_hllc(k, prec, riemann):
+    # the HLL / HLLC face fluxes (Sec. 2) against the oracle's star-state form;
+    # forced, viscous pressure capped at part of the points
+    N = 5
+    u = I.random_state(N, k, seed=90 + k, v_rms=0.8)
+    cfg = O.make_cfg(N, k, riemann=riemann)
+    a = ahat_for(N, k)
+    dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
+    ref = O.rhs(cfg, u, a, dt)
+    s = Solver(N, k, precision=prec, riemann=riemann)
+    got = s.rhs(u, a, dt).cpu().numpy()
+    err = rel_l2_fields(got, ref)
+    assert err.max() < {"f64": 1e-12, "f32": 1e-5, "x3": 5e-5}[prec], err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_driven_steps_parity_hllc(prec):
+    N, k = 5, 3
+    u = I.random_state(N, k, seed=95, v_rms=0.8)
+    s = Solver(N, k, precision=prec, riemann="hllc")
+    s.set_state(u)
+    s.set_forcing(mach=3.0, zeta=0.5, seed=4)
+    s.step(3)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, _, _, _ = O.run(O.make_cfg(N, k, riemann="hllc"), ref, 3, forcing=O.Forcing(mach=3.0, zeta=0.5, seed=4))
+    assert rc == 0
+    assert rel_l2_fields(got, ref).max() < (1e-12 if prec == "f64" else 3e-5)
+
+
+@pytest.mark.gpu
+def test_hllc_keeps_a_steady_shear_layer():
+    # a piecewise-constant shear layer is a steady state of the HLLC scheme
+    N, k = 8, 2
+    b = I.nmodes(k)
+    u = np.zeros((N ** 3, 4, b))
+    ix = np.arange(N ** 3) % N
+    u[:, 0, 0] = 1.4
+    u[:, 2, 0] = np.where(ix < N // 2, 1.4 * 0.8, -1.4 * 0.5)
+    u[:, 3, 0] = np.where(ix < N // 2, -1.4 * 0.3, 1.4 * 0.6)
+    # FP32: the cancelling volume and face terms are of size cs^2 rho (2/h) ~ 22,
+    # so their round-off leaves ~22 x 6e-8 x (a few terms per mode)
+    for prec in ("f64", "f32"):
+        r = Solver(N, k, precision=prec, riemann="hllc").rhs(u, None, 0.0).cpu().numpy()
+        assert np.abs(r).max() < (1e-12 if prec == "f64" else 1e-4)
+        r2 = Solver(N, k, precision=prec, riemann="hll").rhs(u, None, 0.0).cpu().numpy()
+        assert np.abs(r2).max() > 1e-2
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_rhs_parity_av_off_and_uncapped(k):
     N = 4
