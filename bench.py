@@ -15,8 +15,8 @@ and forcing, the stage combine and the positivity rescaling.  L2 is flushed
 (a 256 MB write) before every timed step, outside the timed interval.
 
 Variants: plain FP32, split-BF16 x3 tensor-core transforms ("x3"), and the
-learned viscosity sensor (network trained here, untimed, on plain-sensor
-pairs of the relaxed state).  Fixed L1: from the relaxed state each variant
+learned viscosity sensor (network trained here, untimed: 20 epochs of Adam
+over the plain-sensor pairs of three relaxation snapshots).  Fixed L1: from the relaxed state each variant
 runs 20 undriven steps at a fixed dt; the reference is the plain FP32 scheme
 on the 2N^3 mesh from the exactly prolonged state (40 steps at dt/2),
 restricted back by L2 projection; a variant counts when its density L1 error
@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--no-cpu", dest="no_cpu", action="store_true")
     ap.add_argument("--no-l1", dest="no_l1", action="store_true")
     ap.add_argument("--riemann", default="rusanov", choices=["rusanov", "hll", "hllc"])
+    ap.add_argument("--train-epochs", dest="train_epochs", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -220,6 +221,7 @@ def main():
 
     variants = [v for v in args.variants.split(",") if v]
     weights = None
+    training = None
     if any(v.startswith("learned") for v in variants):
         # plain-sensor pairs of the relaxed snapshots -> trained weights (untimed)
         trainer = Solver(N, k, precision="f32", av="learned", device=dev, riemann=args.riemann)
@@ -232,7 +234,11 @@ def main():
             ys.append(y)
         X, Y = torch.cat(xs), torch.cat(ys)
         perm = torch.randperm(len(Y), device=X.device, generator=torch.Generator(device=X.device).manual_seed(0))
-        trainer.mlp_train(X[perm], Y[perm], epochs=5, batch=4096, lr=2e-3)
+        t_train = time.perf_counter()
+        train_loss = trainer.mlp_train(X[perm], Y[perm], epochs=args.train_epochs, batch=4096, lr=2e-3)
+        t_train = time.perf_counter() - t_train
+        training = {"pairs": int(len(Y)), "epochs": args.train_epochs, "batch": 4096,
+                    "final_loss": train_loss, "seconds": t_train}
         weights = trainer.get_av_weights()
         trainer.close()
         del X, Y, xs, ys
@@ -360,6 +366,8 @@ def main():
                              "other_ms_per_step": res[v]["prof"]["ms_other"] / args.steps}
                          for v in variants},
             "diag": {k_: v for k_, v in hs.diagnostics().items() if k_ in ("mach", "rho_min", "rho_max", "av_frac")}}
+    if training is not None:
+        line["learned_training"] = training
     if rank == 0 and not args.no_cpu:
         v, wall, cb = oracle_arm(args, args.cpu_steps, 1)
         cb["value"] = v

@@ -866,8 +866,10 @@ double orc_l1_density(const orc_cfg* cfg, const double* uA, const double* uB)
 /*  x[c][0..b)   = rho_l / rho_0                                              */
 /*  x[c][b..2b)  = |v|hat_l / cs, |v|hat the Gauss projection of |m/rho|    */
 /*  y[c]         = log(max(nu_cell, nu_f) / (cs h/p)),                       */
-/*  nu_cell = max over volume points with div v < 0 of Pi/(rho |div v|) for  */
-/*  the vNR pressure of Sec. 3.1 (cap with dt); nu_f = max(beta, 0.05) cs h/p */
+/*  nu_cell = Gauss-weighted mean, over the volume points with div v < 0, of */
+/*  the pointwise coefficient Pi/(rho |div v|) of the vNR pressure of        */
+/*  Sec. 3.1 (cap with dt), the coefficient the learned pressure             */
+/*  rho nu |div v| applies at those same points; nu_f = max(beta, 0.05) cs h/p*/
 /*  is the coefficient every compressive point receives from the linear term */
 /*  (Pi only acts where div v < 0, so cells without compression carry the    */
 /*  floor).                                                                   */
@@ -886,7 +888,7 @@ void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, 
             xc[l] = uc[l] / uc[0];
             xc[b + l] = 0.0;
         }
-        double nu = 0.0;
+        double nsum = 0.0, wsum = 0.0;
         for (int q = 0; q < nq; ++q) {
             const double* ph = T.phi + q * b;
             double rho = eval(&T, uc, ph), m[3], v[3], drho[3], dmd[3];
@@ -903,10 +905,11 @@ void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, 
             double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
             for (int l = 0; l < b; ++l) xc[b + l] += 0.125 * T.wq[q] * ph[l] * speed / cfg->cs;
             if (divv < 0.0) {
-                double nq_ = orc_vnr(cfg, rho, divv, dt) / (rho * (-divv));
-                if (nq_ > nu) nu = nq_;
+                nsum += T.wq[q] * orc_vnr(cfg, rho, divv, dt) / (rho * (-divv));
+                wsum += T.wq[q];
             }
         }
+        const double nu = wsum > 0.0 ? nsum / wsum : 0.0;
         const double floor_ = (cfg->beta > 0.05 ? cfg->beta : 0.05) * ref;
         y[c] = log((nu > floor_ ? nu : floor_) / ref);
     }

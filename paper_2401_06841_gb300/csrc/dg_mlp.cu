@@ -64,7 +64,8 @@ static cudaError_t features_k(const Launch& L, const T* u, const T* vabs, const 
 {
     const long ntile = (L.ncell + Tile<K>::TC - 1) / Tile<K>::TC;
     long g = ntile < 4L * L.nsm ? ntile : 4L * L.nsm;
-    k_features<T, K><<<(int)g, Tile<K>::NT, 0, L.st>>>(u, vabs, phiv, L.ncell, L.ph, dt, X, Y);
+    const T* wq = static_cast<const T*>(L.tab) + TabLayout<K>::wq;
+    k_features<T, K><<<(int)g, Tile<K>::NT, 0, L.st>>>(u, vabs, phiv, wq, L.ncell, L.ph, dt, X, Y);
     return cudaGetLastError();
 }
 

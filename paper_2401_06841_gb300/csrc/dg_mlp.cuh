@@ -309,20 +309,22 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const T* __restrict__ u, cons
 // ---------------------------------------------------------------------------
 // features and labels of the learned sensor for every cell (thread per
 // (cell, point)): x = (rho_l/rho_0, |v|hat_l/cs), y = log(max(nu_cell,
-// nu_f)/ref), nu_cell = max over compressive points of Pi_vNR/(rho |div v|),
-// nu_f = max(beta, 0.05) ref the coefficient of the linear term
+// nu_f)/ref), nu_cell = the Gauss-weighted mean of Pi_vNR/(rho |div v|) over
+// the compressive points (summed in a fixed order), nu_f = max(beta, 0.05) ref
+// the coefficient of the linear term
 // ---------------------------------------------------------------------------
 template <typename T, int K>
 __global__ void __launch_bounds__(Tile<K>::NT) k_features(const T* __restrict__ u, const T* __restrict__ vabs,
-                                                          const T* __restrict__ phiv, long ncell, Phys ph, double dt,
-                                                          float* __restrict__ X, float* __restrict__ Y)
+                                                          const T* __restrict__ phiv, const T* __restrict__ wq,
+                                                          long ncell, Phys ph, double dt, float* __restrict__ X,
+                                                          float* __restrict__ Y)
 {
     using Dm = Dims<K>;
     constexpr int b = Dm::b, nq = Dm::nq, TC = Tile<K>::TC, NT = Tile<K>::NT, EC = 12;
     __shared__ T s_u[TC][4][b];
     __shared__ T s_ec[TC][b][EC];
     __shared__ T s_phi[b * nq];  // basis at the volume points [b][nq]
-    __shared__ int s_max[TC];
+    __shared__ T s_nw[TC][nq], s_w[TC][nq];  // w_q nu_q and w_q at compressive points, else 0
     const int tid = threadIdx.x;
     for (int e = tid; e < b * nq; e += NT) s_phi[e] = phiv[e];
     const T two_h = T(2.0 / ph.h);
@@ -334,7 +336,6 @@ __global__ void __launch_bounds__(Tile<K>::NT) k_features(const T* __restrict__ 
             const long c = c0 + e / (4 * b);
             (&s_u[0][0][0])[e] = (c < ncell) ? u[c0 * 4 * b + e] : ((e % (4 * b)) == 0 ? T(1) : T(0));
         }
-        if (tid < TC) s_max[tid] = 0;
         __syncthreads();
         for (int e = tid; e < TC * 5; e += NT) {
             const int lc = e / 5, g = e % 5;
@@ -359,7 +360,8 @@ __global__ void __launch_bounds__(Tile<K>::NT) k_features(const T* __restrict__ 
             for (int l = 0; l < b; ++l) s_ec[lc][l][3 + g] = out[l];
         }
         __syncthreads();
-        {
+        static_assert(TC * nq <= NT, "one thread per (cell, point)");
+        if (tid < TC * nq) {
             const int lc = tid / nq, q = tid % nq;
             T f[8];
             for (int i = 0; i < 8; ++i) f[i] = T(0);
@@ -369,11 +371,14 @@ __global__ void __launch_bounds__(Tile<K>::NT) k_features(const T* __restrict__ 
             }
             const T rho = f[0], vx = f[1] / rho, vy = f[2] / rho, vz = f[3] / rho;
             const T divv = (f[7] - (vx * f[4] + vy * f[5] + vz * f[6])) / rho;
+            T nw = T(0), w = T(0);
             if (divv < T(0)) {
                 const T Pi = vnr_pressure<T>(ph, rho, divv, T(dt));
-                const float nuq = (float)(Pi / (rho * (-divv)));
-                atomicMax(&s_max[lc], __float_as_int(nuq));  // positive floats order like ints
+                w = wq[q];
+                nw = w * (Pi / (rho * (-divv)));
             }
+            s_nw[lc][q] = nw;
+            s_w[lc][q] = w;
         }
         __syncthreads();
         for (int e = tid; e < TC * 2 * b; e += NT) {
@@ -386,7 +391,12 @@ __global__ void __launch_bounds__(Tile<K>::NT) k_features(const T* __restrict__ 
         for (int lc = tid; lc < TC; lc += NT) {
             const long c = c0 + lc;
             if (c >= ncell) continue;
-            const float nu = __int_as_float(s_max[lc]);
+            T sn = T(0), sw = T(0);
+            for (int q = 0; q < nq; ++q) {
+                sn += s_nw[lc][q];
+                sw += s_w[lc][q];
+            }
+            const float nu = sw > T(0) ? (float)(sn / sw) : 0.f;
             const float fl = fmaxf((float)ph.beta, 0.05f) * ref;
             Y[c] = logf(fmaxf(nu, fl) / ref);
         }

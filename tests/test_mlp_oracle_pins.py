@@ -9,6 +9,7 @@ import math
 
 import numpy as np
 import pytest
+from numpy.polynomial import legendre as npleg
 
 from oracle import mlp_oracle as M
 from oracle import oracle as O
@@ -92,6 +93,46 @@ def test_sensor_labels_closed_form():
     assert np.allclose(y2, math.log(0.2))
     _, y3 = O.av_features(O.make_cfg(N, k, beta=0.0), u, 0.0)
     assert np.allclose(y3, math.log(0.05))
+
+
+def pnorm(m, x):
+    c = np.zeros(m + 1)
+    c[m] = 1.0
+    return math.sqrt(2 * m + 1) * npleg.legval(x, c)
+
+
+@pytest.mark.parametrize("e", [4.0, 9.0])
+def test_sensor_label_is_the_weighted_mean_over_compressive_points(e):
+    # rho = 1, v_x(xi) with dv/dx = -c + e xi^2 (xi the cell's reference x):
+    # div v varies over the Gauss points (and changes sign for e > c); the
+    # label averages Pi/(rho |div v|) with the Gauss weights over the
+    # compressive points only (the y, z weights cancel in the ratio)
+    N, k, c = 4, 3, 6.0
+    cfg = O.make_cfg(N, k, alpha=2.0, beta=0.2)
+    b = O.nmodes(k)
+    ml = [tuple(r) for r in O.mode_list(k)]
+    h = 1.0 / N
+    hp = h / (k + 1)
+    # v(xi) = (h/2) (-c xi + e xi^3 / 3), projected on Pn_m by a 10-point Gauss rule
+    t, w = npleg.leggauss(10)
+    v = (h / 2) * (-c * t + e * t ** 3 / 3)
+    u = np.zeros((N ** 3, 4, b))
+    u[:, 0, 0] = 1.0
+    for m in range(k + 1):
+        u[:, 1, ml.index((m, 0, 0))] = 0.5 * np.sum(w * v * pnorm(m, t))
+    _, y = O.av_features(cfg, u, 0.0)
+    xa, wa = npleg.leggauss(k + 1)
+    D = -c + e * xa ** 2
+    comp = D < 0
+    nu_a = 2.0 * hp * hp * np.abs(D) + 0.2 * hp
+    nu = np.sum(wa[comp] * nu_a[comp]) / np.sum(wa[comp])
+    assert comp.any() and (e < c) == comp.all()
+    assert np.allclose(y, math.log(max(nu, 0.2 * hp) / hp), rtol=0, atol=1e-12)
+    if comp.all():
+        # neither the maximum nor the unweighted mean (for e > c the two
+        # compressive points share one value)
+        assert abs(math.log(nu_a[comp].max() / hp) - y[0]) > 1e-3
+        assert abs(math.log(nu_a[comp].mean() / hp) - y[0]) > 1e-4
 
 
 def test_rhs_with_cell_coefficient_equals_vnr_when_nu_matches():
