@@ -77,8 +77,11 @@ typedef struct {
 /* Viscous pressure Pi = alpha rho (h/p)^2 |div v|^2 + beta rho cs (h/p) |div v|
  * for div v < 0, capped at Pi_max = rho (h/p)^2 |div v| / (2 dt)  (Sec. 3.1,
  * p = k+1).  rho_floor is the positivity floor (Sec. 3.1, Sec. 5 uses 1e-3).
- * nu_gate: in DG_AV_LEARNED mode cells whose predicted coefficient
- * nu/(cs h/p) is below nu_gate skip the divergence evaluation. */
+ * nu_gate (>= 0): in DG_AV_LEARNED mode a cell whose predicted coefficient
+ * nu/(cs h/p) is below nu_gate gets nu = 0, i.e. no viscous pressure at any of
+ * its points (the sensor's "no shock here" decision); 0 disables the gate.
+ * The tile kernels evaluate div v for every cell of a tile either way, so the
+ * gate changes the result, not the work. */
 typedef struct {
     int32_t mode;          /* DG_AV_OFF, DG_AV_VNR, DG_AV_LEARNED                 */
     double alpha;          /* default 2.0                                          */

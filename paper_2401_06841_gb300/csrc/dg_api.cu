@@ -581,6 +581,7 @@ Launch make_launch(const dg_ctx* c)
     L.ph.floor_ = c->nu.rho_floor;
     L.ph.av_mode = c->nu.mode;
     L.ph.riemann = c->riemann;
+    L.ph.nu_gate = c->nu.nu_gate;
     L.tab = c->tab;
     L.ttab = c->ttab;
     L.ctl = c->ctl;
@@ -708,20 +709,10 @@ int upload_weights(dg_ctx* ctx, const float* w_host)
     return DG_OK;
 }
 
-// learned mode: projection of |v| of u, then the per-cell coefficient nu = cs h/p exp(net(x))
-cudaError_t learned_nu(dg_ctx* c, const void* u)
+// learned mode: the per-cell coefficient nu = cs h/p exp(net(x)) from u and
+// the projection of |v| already in c->vabs
+cudaError_t learned_infer(dg_ctx* c, const void* u)
 {
-    {
-        TileLaunch t{};
-        t.mode = 0;
-        t.u_in = u;
-        t.vh_out = vh_buf(c, 1);
-        t.vabs_out = c->vabs;
-        t.flags = F_VABS;
-        t.abar_out = 1;
-        cudaError_t e = tile(c, t);
-        if (e != cudaSuccess) return e;
-    }
     Timed tm(c, KIND_OTHER);
     Launch L = make_launch(c);
     return (c->prec == DG_PREC_F64)
@@ -729,6 +720,21 @@ cudaError_t learned_nu(dg_ctx* c, const void* u)
                                    nullptr)
                : mlp_infer<float>(L, (const float*)u, (const float*)c->vabs, nullptr, c->ncell, c->mpack, c->nu_cell,
                                   nullptr);
+}
+
+// learned mode: projection of |v| of u (v-hat into the scratch slot 1), then the coefficient
+cudaError_t learned_nu(dg_ctx* c, const void* u)
+{
+    TileLaunch t{};
+    t.mode = 0;
+    t.u_in = u;
+    t.vh_out = vh_buf(c, 1);
+    t.vabs_out = c->vabs;
+    t.flags = F_VABS;
+    t.abar_out = 1;
+    cudaError_t e = tile(c, t);
+    if (e != cudaSuccess) return e;
+    return learned_infer(c, u);
 }
 
 int upload_forcing(dg_ctx* ctx)
@@ -791,7 +797,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     for (int d = 0; d < 3; ++d)
         if (mesh->L[d] != 1.0) return DG_EINVAL;
     if (!(cs > 0.0)) return DG_EINVAL;
-    if (nu->mode < 0 || nu->mode > 2 || !(nu->rho_floor >= 0.0)) return DG_EINVAL;
+    if (nu->mode < 0 || nu->mode > 2 || !(nu->rho_floor >= 0.0) || !(nu->nu_gate >= 0.0)) return DG_EINVAL;
     if (opts->precision < 0 || opts->precision > 2) return DG_EINVAL;
     if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
     if (!(opts->cfl > 0.0)) return DG_EINVAL;
@@ -1071,12 +1077,16 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
             // (double-buffered vhat / abar slots, alternating from slot pb)
             const bool use_carry = retry == 0 && ctx->carry;
             ctx->carry = false;
-            if (learned) CK(learned_nu(ctx, ctx->reg[A]));  // once per step, cached for all stages
+            // learned mode: the coefficient once per step, cached for all stages (the
+            // carried projection includes |v|)
+            if (learned) CK(use_carry ? learned_infer(ctx, ctx->reg[A]) : learned_nu(ctx, ctx->reg[A]));
             if (!use_carry) CK(project(ctx, ctx->reg[A], vh_buf(ctx, pb), force ? ctx->ahat : nullptr, true, pb));
             for (int s = 0; s < ctx->rk; ++s) {
+                const bool last = s + 1 == ctx->rk;
                 TileLaunch t{};
                 t.nu = learned ? ctx->nu_cell : nullptr;
-                t.mode = 2;
+                t.mode = (learned && last) ? 3 : 2;
+                t.vabs_out = (learned && last) ? ctx->vabs : nullptr;
                 t.u_in = ctx->reg[in[s]];
                 t.u_n = ctx->reg[A];
                 t.out = ctx->reg[out[s]];
@@ -1085,10 +1095,9 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
                 t.ahat = force ? ctx->ahat : nullptr;
                 t.rk_a = RA[s];
                 t.rk_b = RB[s];
-                // the last stage projects u^(n+1) for the next step (learned mode
-                // re-projects anyway for its features)
-                const bool next = s + 1 < ctx->rk || !learned;
-                t.flags = (force ? F_FORCE : 0) | (next ? F_NEXTPROJ : 0) | (next && s + 1 == ctx->rk ? F_DT : 0);
+                // every stage projects its output; the last one for the next step,
+                // with the CFL bound (and |v| in learned mode)
+                t.flags = (force ? F_FORCE : 0) | F_NEXTPROJ | (last ? F_DT : 0);
                 t.abar_in = (pb + s) & 1;
                 t.abar_out = (pb + s + 1) & 1;
                 CK(tile(ctx, t));
@@ -1111,7 +1120,7 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
         ctx->status |= status;
         ctx->cur = out[ctx->rk - 1];
         ctx->pb = (pb + ctx->rk) & 1;
-        ctx->carry = !learned && !(status & DG_ST_NONFINITE);
+        ctx->carry = !(status & DG_ST_NONFINITE);
         ctx->t += dt;
         ctx->dt_last = dt;
         ctx->steps += 1;

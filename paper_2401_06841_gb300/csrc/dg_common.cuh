@@ -146,6 +146,7 @@ struct Phys {
     double alpha, beta, floor_;  // vNR coefficients, density floor
     int av_mode;                 // 0 off, 1 vNR, 2 learned
     int riemann;                 // face flux: 0 Rusanov, 1 HLL, 2 HLLC
+    double nu_gate;              // learned sensor: nu/(cs h/p) below this -> no viscous pressure
 };
 
 // von Neumann-Richtmyer viscous pressure at a volume point (Sec. 3.1):

@@ -30,7 +30,8 @@ template <typename T>
 cudaError_t setup_kernels(int K);
 // tile kernel modes: 0 projection only (velocity projection, forcing sums,
 // CFL dt with F_DT), 1 right-hand side only, 2 right-hand side + SSP-RK stage
-// (+ the next stage's projection with F_NEXTPROJ)
+// (+ the next stage's projection with F_NEXTPROJ), 3 as 2 with the projection
+// of |v| (vabs_out) for the learned sensor
 struct TileLaunch {
     int mode;
     const void* u_in;

@@ -10,10 +10,10 @@ namespace dg {
 
 template <typename T, int K>
 struct Occ {
-    static int tile[2][3], force, diag;
+    static int tile[2][4], force, diag;
 };
 template <typename T, int K>
-int Occ<T, K>::tile[2][3] = {{0, 0, 0}, {0, 0, 0}};
+int Occ<T, K>::tile[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
 template <typename T, int K>
 int Occ<T, K>::force = 0;
 template <typename T, int K>
@@ -35,7 +35,8 @@ static cudaError_t setup_modes()
     cudaError_t e;
     if ((e = setup_tile<T, K, TM_PROJECT, BK>()) != cudaSuccess) return e;
     if ((e = setup_tile<T, K, TM_RHS, BK>()) != cudaSuccess) return e;
-    return setup_tile<T, K, TM_STAGE, BK>();
+    if ((e = setup_tile<T, K, TM_STAGE, BK>()) != cudaSuccess) return e;
+    return setup_tile<T, K, TM_STAGE_VABS, BK>();
 }
 
 template <typename T, int K>
@@ -116,8 +117,10 @@ static cudaError_t tile_kb(const Launch& L, const TileLaunch& t)
         k_tile<T, K, TM_PROJECT, BK><<<g, Cf::NT, sm, L.st>>>(a);
     else if (t.mode == TM_RHS)
         k_tile<T, K, TM_RHS, BK><<<g, Cf::NT, sm, L.st>>>(a);
-    else
+    else if (t.mode == TM_STAGE)
         k_tile<T, K, TM_STAGE, BK><<<g, Cf::NT, sm, L.st>>>(a);
+    else
+        k_tile<T, K, TM_STAGE_VABS, BK><<<g, Cf::NT, sm, L.st>>>(a);
     return cudaGetLastError();
 }
 

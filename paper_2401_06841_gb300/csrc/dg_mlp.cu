@@ -44,11 +44,13 @@ static cudaError_t infer_k(const Launch& L, const T* u, const T* vabs, const flo
     long g = (n + 127) / 128;
     if (g > 8L * L.nsm) g = 8L * L.nsm;
     if (g < 1) g = 1;
+    const float gate = (float)L.ph.nu_gate;
     if (u)
-        k_mlp_infer<T, K, true><<<(int)g, 256, 0, L.st>>>(u, vabs, nullptr, n, packed, (float)L.ph.cs, ref, nu, y);
+        k_mlp_infer<T, K, true><<<(int)g, 256, 0, L.st>>>(u, vabs, nullptr, n, packed, (float)L.ph.cs, ref, gate, nu,
+                                                          y);
     else
-        k_mlp_infer<T, K, false><<<(int)g, 256, 0, L.st>>>(nullptr, nullptr, X, n, packed, (float)L.ph.cs, ref, nu,
-                                                           y);
+        k_mlp_infer<T, K, false><<<(int)g, 256, 0, L.st>>>(nullptr, nullptr, X, n, packed, (float)L.ph.cs, ref, gate,
+                                                           nu, y);
     return cudaGetLastError();
 }
 

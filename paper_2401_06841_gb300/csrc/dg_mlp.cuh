@@ -197,7 +197,7 @@ template <typename T, int K, bool FROMSTATE>
 __global__ void __launch_bounds__(256) k_mlp_infer(const T* __restrict__ u, const T* __restrict__ vabs,
                                                    const float* __restrict__ X, long n,
                                                    const uint32_t* __restrict__ packed, float cs, float ref,
-                                                   float* __restrict__ nu_out, float* __restrict__ y_out)
+                                                   float gate, float* __restrict__ nu_out, float* __restrict__ y_out)
 {
     constexpr int b = Dims<K>::b, D = 2 * b;
     using PK = MlpPack<D>;
@@ -295,11 +295,11 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const T* __restrict__ u, cons
             const float b3 = bias[2 * MLP_H];
             const float y0 = acc3[0] + b3, y1 = acc3[2] + b3;
             if (r0 < n) {
-                if (nu_out) nu_out[r0] = ref * expf(y0);
+                if (nu_out) nu_out[r0] = expf(y0) < gate ? 0.f : ref * expf(y0);
                 if (y_out) y_out[r0] = y0;
             }
             if (r1 < n) {
-                if (nu_out) nu_out[r1] = ref * expf(y1);
+                if (nu_out) nu_out[r1] = expf(y1) < gate ? 0.f : ref * expf(y1);
                 if (y_out) y_out[r1] = y1;
             }
         }

@@ -437,7 +437,10 @@ __device__ __forceinline__ void expand_acc(const T* L2, int side, T scale, T* R)
     });
 }
 
-enum { TM_PROJECT = 0, TM_RHS = 1, TM_STAGE = 2 };
+// kernel modes: projection only; RHS only; RHS + stage combine (+ the next
+// stage's projection with F_NEXTPROJ); the same with the projection of |v|
+// for the learned sensor's features (the last stage of a learned-mode step)
+enum { TM_PROJECT = 0, TM_RHS = 1, TM_STAGE = 2, TM_STAGE_VABS = 3 };
 enum { F_NEXTPROJ = 4, F_VABS = 8 };
 
 template <typename T>
@@ -622,11 +625,12 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     const T cs = T(a.ph.cs), cs2 = T(a.ph.cs2);
     T smax = T(0);
     double sums[4] = {0.0, 0.0, 0.0, 0.0};
-    const bool do_proj = (MODE == TM_PROJECT) || (MODE == TM_STAGE && (a.flags & F_NEXTPROJ));
+    constexpr bool STAGE = (MODE == TM_STAGE || MODE == TM_STAGE_VABS);
+    const bool do_proj = (MODE == TM_PROJECT) || (STAGE && (a.flags & F_NEXTPROJ));
     T dt = T(0), ab0 = T(0), ab1 = T(0), ab2 = T(0);
     AvCoef<T> avc{};
     if constexpr (MODE != TM_PROJECT) {
-        if constexpr (MODE == TM_STAGE) {
+        if constexpr (STAGE) {
             // the step's dt (Sec. 7 CFL condition), fixed for all its stages: from the
             // wave-speed bound of u^n, a prescribed dt, and the retry factor
             const double sn = a.ctl->sn;
@@ -657,7 +661,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
         if (a.rk_a != T(0)) stage_async<T, NT>(sUn, a.u_n + cb * 4 * b, TC * 4 * b, nv * 4 * b);
         cp_async_commit();
     };
-    if constexpr (MODE == TM_STAGE) {
+    if constexpr (STAGE) {
         if (blockIdx.x < ntile) issue(blockIdx.x, sU);
     }
     __syncthreads();
@@ -665,7 +669,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const long c0 = tile * TC;
         const long nvalid = (a.ncell - c0) < TC ? (a.ncell - c0) : TC;
-        if constexpr (MODE == TM_STAGE) {
+        if constexpr (STAGE) {
             if (tid < TC) s_nu[tid] = (a.ph.av_mode == 2 && tid < nvalid) ? T(a.nu[c0 + tid]) : T(0);
             cp_async_wait_all();
             __syncthreads();
@@ -1045,14 +1049,15 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 // the staging buffers of this tile are free: fetch the next tile
                 if (tile + gridDim.x < ntile) issue(tile + gridDim.x, sR);
                 if (do_proj) {
-                    tile_project<T, K, BK>(sm, sU, tabs, a, c0, (a.flags & F_DT) != 0, smax, sums, false);
+                    tile_project<T, K, BK, MODE == TM_STAGE_VABS>(sm, sU, tabs, a, c0, (a.flags & F_DT) != 0, smax,
+                                                                 sums, false);
                     __syncthreads();
                 }
             }
         }
     }
     // ---- block-level reductions ----
-    if constexpr (MODE == TM_STAGE) {
+    if constexpr (STAGE) {
         if (tid == 0 && s_status) atomicOr(&a.ctl->status, s_status);
     }
     if (do_proj) {

@@ -104,6 +104,31 @@ def test_learned_rhs_parity(k):
 
 
 @pytest.mark.gpu
+def test_learned_gate_zeroes_the_coefficient_of_quiet_cells():
+    # nu_gate: cells whose predicted nu/(cs h/p) falls below the gate get nu = 0
+    # (no viscous pressure); the right-hand side equals the oracle's with the
+    # gated coefficients
+    N, k = 5, 2
+    u = I.random_state(N, k, seed=64)
+    s0, th = learned_solver(N, k, "f64", seed=2)
+    s0.set_state(u)
+    nu0 = s0.av_nu().cpu().numpy().astype(np.float64)
+    ref_scale = 1.0 * (1.0 / N) / (k + 1)
+    gate = float(np.median(nu0 / ref_scale))
+    s = Solver(N, k, precision="f64", av="learned", nu_gate=gate)
+    s.set_av_weights(th.astype(np.float32))
+    s.set_state(u)
+    nu = s.av_nu().cpu().numpy().astype(np.float64)
+    quiet = nu0 / ref_scale < gate
+    assert 0 < quiet.sum() < len(nu)
+    assert (nu[quiet] == 0).all() and np.array_equal(nu[~quiet], nu0[~quiet])
+    dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
+    got = s.rhs(u, None, dt).cpu().numpy()
+    ref = O.rhs_nu(O.make_cfg(N, k), u, nu, None, dt)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+
+
+@pytest.mark.gpu
 def test_gpu_training_follows_fp64_adam():
     k = 2
     D = 2 * I.nmodes(k)
