@@ -915,3 +915,121 @@ void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, 
     }
     tabs_free(&T);
 }
+
+
+/* ------------------------------------------------------------------------ */
+/* turbulence statistics                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Volume-weighted PDF of s = log10(rho / rho_mean) (Sec. 4.3 bins the log of
+ * the density; here the whole volume, sampled at every cell's Gauss points
+ * with their weights, so each sample carries its share of the volume):
+ * hist[i] = volume fraction with s in [lo + i ds, lo + (i+1) ds),
+ * ds = (hi - lo) / nbins; samples outside [lo, hi) are not counted. */
+void orc_density_pdf(const orc_cfg* cfg, const double* u, double lo, double hi, int nbins, double* hist)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    const int N = cfg->N, b = T.b;
+    const size_t nc = (size_t)N * N * N;
+    double mass = 0.0;
+    for (size_t c = 0; c < nc; ++c) mass += u[c * 4 * b] / (double)nc;  /* cell means, unit box */
+    for (int i = 0; i < nbins; ++i) hist[i] = 0.0;
+    const double ds = (hi - lo) / nbins;
+    for (size_t c = 0; c < nc; ++c)
+        for (int q = 0; q < T.nq; ++q) {
+            const double rho = eval(&T, u + c * 4 * b, T.phi + q * b);
+            if (!(rho > 0.0)) continue;
+            const double sv = log10(rho / mass);
+            const int i = (int)floor((sv - lo) / ds);
+            if (i >= 0 && i < nbins) hist[i] += T.wq[q] / 8.0 / (double)nc;
+        }
+    tabs_free(&T);
+}
+
+/* velocity v = m / rho at a point x of the periodic unit box, evaluated from
+ * the expansions of the cell that contains it; returns rho */
+double orc_velocity_at(const orc_cfg* cfg, const double* u, const double x[3], double v[3])
+{
+    const int N = cfg->N, k = cfg->k, b = orc_nmodes(k);
+    int32_t ijl[3 * 84];
+    orc_mode_list(k, ijl);
+    int ic[3];
+    double xi[3];
+    for (int d = 0; d < 3; ++d) {
+        double y = x[d] - floor(x[d]); /* wrap into [0, 1) */
+        double s = y * N;
+        int i = (int)floor(s);
+        if (i >= N) i = N - 1;
+        ic[d] = i;
+        xi[d] = 2.0 * (s - i) - 1.0;
+    }
+    const double* uc = u + (size_t)cell_index(N, ic[0], ic[1], ic[2]) * 4 * b;
+    double f[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = 0; l < b; ++l) {
+        const double ph = orc_legendre(ijl[3 * l], xi[0]) * sqrt(2.0 * ijl[3 * l] + 1.0) *
+                          orc_legendre(ijl[3 * l + 1], xi[1]) * sqrt(2.0 * ijl[3 * l + 1] + 1.0) *
+                          orc_legendre(ijl[3 * l + 2], xi[2]) * sqrt(2.0 * ijl[3 * l + 2] + 1.0);
+        for (int var = 0; var < 4; ++var) f[var] += uc[var * b + l] * ph;
+    }
+    for (int d = 0; d < 3; ++d) v[d] = f[1 + d] / f[0];
+    return f[0];
+}
+
+/* the n-th number of the SplitMix64 sequence started from seed, as a
+ * uniform double in [0, 1) (53 bits) */
+static double splitmix_at(uint64_t seed, uint64_t n)
+{
+    uint64_t st = seed + n * 0x9E3779B97F4A7C15ULL;
+    return (double)(orc_splitmix64(&st) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* Second-order velocity structure function (Sec. 4.1 definition, Sec. 4.3
+ * sampling): nbins logarithmic bins between l_min = 1/((k+1) N) and
+ * l_max = 1/2; in bin j the separation is the bin's logarithmic centre
+ * l_j = l_min (l_max/l_min)^((j + 1/2)/nbins).  Pair p of bin j draws five
+ * uniforms u_r = SplitMix64 number n = (j npairs + p) 5 + r of `seed`:
+ * x = (u_0, u_1, u_2), cos(theta) = 2 u_3 - 1, phi = 2 pi u_4; the partner
+ * is x + l_j (sin theta cos phi, sin theta sin phi, cos theta), wrapped.
+ * v_out[j] = (1/2 <|v(x) - v(x + l)|^2>)^(1/2), l_out[j] = l_j. */
+void orc_structure_function(const orc_cfg* cfg, const double* u, int nbins, int64_t npairs, uint64_t seed,
+                            double* l_out, double* v_out)
+{
+    const double lmin = 1.0 / ((cfg->k + 1) * (double)cfg->N), lmax = 0.5;
+    for (int j = 0; j < nbins; ++j) {
+        const double l = lmin * pow(lmax / lmin, (j + 0.5) / nbins);
+        double acc = 0.0;
+        for (int64_t p = 0; p < npairs; ++p) {
+            const uint64_t n0 = ((uint64_t)j * (uint64_t)npairs + (uint64_t)p) * 5u;
+            double x[3], y[3], va[3], vb[3];
+            for (int d = 0; d < 3; ++d) x[d] = splitmix_at(seed, n0 + d);
+            const double ct = 2.0 * splitmix_at(seed, n0 + 3) - 1.0, phi = 2.0 * ORC_PI * splitmix_at(seed, n0 + 4);
+            const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+            const double dir[3] = {st * cos(phi), st * sin(phi), ct};
+            for (int d = 0; d < 3; ++d) y[d] = x[d] + l * dir[d];
+            orc_velocity_at(cfg, u, x, va);
+            orc_velocity_at(cfg, u, y, vb);
+            for (int d = 0; d < 3; ++d) acc += (va[d] - vb[d]) * (va[d] - vb[d]);
+        }
+        l_out[j] = l;
+        v_out[j] = sqrt(0.5 * acc / (double)npairs);
+    }
+}
+
+/* Velocity on the regular Fourier grid of Sec. 4.3: N_g = (k+1) N points per
+ * axis at x_g = (g + 1/2) / N_g (k+1 points inside every cell, none on a face).
+ * v_out[d][gz][gy][gx], d = 0..2. */
+void orc_sample_velocity(const orc_cfg* cfg, const double* u, double* v_out)
+{
+    const int Ng = (cfg->k + 1) * cfg->N;
+    const size_t n3 = (size_t)Ng * Ng * Ng;
+    for (int gz = 0; gz < Ng; ++gz)
+        for (int gy = 0; gy < Ng; ++gy)
+            for (int gx = 0; gx < Ng; ++gx) {
+                const double x[3] = {(gx + 0.5) / Ng, (gy + 0.5) / Ng, (gz + 0.5) / Ng};
+                double v[3];
+                orc_velocity_at(cfg, u, x, v);
+                const size_t g = ((size_t)gz * Ng + gy) * Ng + gx;
+                for (int d = 0; d < 3; ++d) v_out[d * n3 + g] = v[d];
+            }
+}

@@ -85,6 +85,14 @@ int orc_rhs_nu(const orc_cfg* cfg, const double* u, const double* ahat, double d
 void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, double* y);
 int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt);
 
+/* turbulence statistics (Sec. 4.1 structure function and power spectrum,
+ * Sec. 4.3 density PDF) */
+void orc_density_pdf(const orc_cfg* cfg, const double* u, double lo, double hi, int nbins, double* hist);
+void orc_structure_function(const orc_cfg* cfg, const double* u, int nbins, int64_t npairs, uint64_t seed,
+                            double* l_out, double* v_out);
+void orc_sample_velocity(const orc_cfg* cfg, const double* u, double* v_out);
+double orc_velocity_at(const orc_cfg* cfg, const double* u, const double x[3], double v[3]);
+
 void orc_ou_init(orc_ou* ou, int kmin2, int kmax2, double zeta, double mach,
                  double cs, double L, uint64_t seed, double t_off);
 void orc_ou_advance(orc_ou* ou);

@@ -10,6 +10,7 @@ Every array is a C-contiguous float64 numpy array in the cell-major layout
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -76,6 +77,9 @@ def lib():
         _lib.orc_vnr.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double]
         _lib.orc_rusanov.argtypes = [C.c_double, C.c_int, d, d, d]
         _lib.orc_riemann.argtypes = [C.c_int, C.c_double, C.c_int, d, d, d]
+        _lib.orc_density_pdf.argtypes = [C.POINTER(Cfg), d, C.c_double, C.c_double, C.c_int, d]
+        _lib.orc_structure_function.argtypes = [C.POINTER(Cfg), d, C.c_int, C.c_int64, C.c_uint64, d, d]
+        _lib.orc_sample_velocity.argtypes = [C.POINTER(Cfg), d, d]
         _lib.orc_ou_init.argtypes = [C.POINTER(OU), C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                      C.c_double, C.c_uint64, C.c_double]
         _lib.orc_rhs.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d]
@@ -268,6 +272,54 @@ def diagnostics(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None = None, dt_: fl
 
 def l1_density(cfg: Cfg, uA: np.ndarray, uB: np.ndarray) -> float:
     return lib().orc_l1_density(C.byref(cfg), _p(uA), _p(uB))
+
+
+def density_pdf(cfg: Cfg, u: np.ndarray, lo: float, hi: float, nbins: int) -> np.ndarray:
+    """Volume fractions of log10(rho/rho_mean) in nbins equal bins on [lo, hi)."""
+    h = np.zeros(nbins)
+    lib().orc_density_pdf(C.byref(cfg), _p(u), C.c_double(lo), C.c_double(hi), nbins, _p(h))
+    return h
+
+
+def structure_function(cfg: Cfg, u: np.ndarray, nbins: int, npairs: int, seed: int):
+    """(l, v(l)) on nbins logarithmic bins (second-order velocity structure function)."""
+    l = np.zeros(nbins)
+    v = np.zeros(nbins)
+    lib().orc_structure_function(C.byref(cfg), _p(u), nbins, C.c_int64(npairs), C.c_uint64(seed), _p(l), _p(v))
+    return l, v
+
+
+def sample_velocity(cfg: Cfg, u: np.ndarray) -> np.ndarray:
+    """v on the (k+1)N regular grid at cell-interior points, shape [3][Ng][Ng][Ng] (z, y, x)."""
+    Ng = (cfg.k + 1) * cfg.N
+    out = np.zeros((3, Ng, Ng, Ng))
+    lib().orc_sample_velocity(C.byref(cfg), _p(u), _p(out))
+    return out
+
+
+def power_spectrum(cfg: Cfg, u: np.ndarray, nbins: int):
+    """Shell sums of the velocity power on the (k+1)N grid (Sec. 4.3):
+    v_hat = FFT(v) / Ng^3 over integer wave vectors kappa; bins logarithmic in
+    |kappa| with edges (sqrt(3) Ng/2)^(i/nbins), i = 0..nbins (the last edge
+    included); kappa = 0 left out.  Returns (mean |kappa|, summed power
+    sum_d |v_hat_d|^2, mode count) per bin; E(k) ~ power / bin width."""
+    v = sample_velocity(cfg, u)
+    Ng = v.shape[1]
+    P = np.zeros((Ng, Ng, Ng))
+    for d in range(3):
+        P += np.abs(np.fft.fftn(v[d]) / Ng ** 3) ** 2
+    f = np.fft.fftfreq(Ng, d=1.0 / Ng)
+    KZ, KY, KX = np.meshgrid(f, f, f, indexing="ij")
+    K = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
+    kmax = math.sqrt(3.0) * Ng / 2
+    sel = K > 0
+    idx = np.floor(np.log(K[sel]) / math.log(kmax) * nbins).astype(np.int64)
+    idx = np.minimum(idx, nbins - 1)
+    power = np.bincount(idx, weights=P[sel], minlength=nbins)
+    count = np.bincount(idx, minlength=nbins)
+    ksum = np.bincount(idx, weights=K[sel], minlength=nbins)
+    kmean = np.where(count > 0, ksum / np.maximum(count, 1), 0.0)
+    return kmean, power, count
 
 
 def splitmix64(state: int, n: int) -> list[int]:
