@@ -305,6 +305,48 @@ int dg_set_meta(dg_ctx* ctx, const dg_meta* in);
 int dg_rhs_noalloc(const dg_mesh* mesh, int order, double cs, const dg_nu_params* nu, int precision,
                    const void* u_in, const void* ahat, void* dudt, double dt_for_pimax, void* stream);
 
+/* ---- turbulence statistics (Sec. 4.1 definitions, Sec. 4.3 measurement) ----
+ * Of the current state.  Evaluated in FP64 from the state's coefficients and
+ * accumulated in FP64 with atomics: the summation order, and with it the last
+ * bits, may vary between calls.  nbins in [1, DG_MAX_BINS].  Each call
+ * synchronises the context's stream.  Errors: DG_EINVAL (arguments),
+ * DG_ESTATE (no state), DG_ECUDA. */
+#define DG_MAX_BINS 2000
+
+/* Volume-weighted PDF of s = log10(rho / rho_mean): hist[i] (host, nbins) is
+ * the volume fraction with s in [lo + i ds, lo + (i+1) ds), ds = (hi-lo)/nbins,
+ * sampled at the Gauss points of every cell with their weights (the paper bins
+ * log density over slices; this uses the whole volume). */
+int dg_density_pdf(dg_ctx* ctx, double lo, double hi, int nbins, double* hist);
+
+/* Second-order velocity structure function v(l) = (1/2 <|v(x) - v(x+l)|^2>)^(1/2)
+ * (Sec. 4.1) on nbins logarithmic bins between 1/((k+1)N) and 1/2: bin j uses
+ * l_j = l_min (l_max/l_min)^((j+1/2)/nbins) and npairs random pairs.  Pair p of
+ * bin j takes the SplitMix64 numbers n = (j npairs + p) 5 + r, r = 0..4, of
+ * `seed` (n-th output of the generator started at state `seed`, top 53 bits as
+ * u in [0,1)): x = (u0, u1, u2), cos(theta) = 2 u3 - 1, phi = 2 pi u4, partner
+ * x + l_j (sin theta cos phi, sin theta sin phi, cos theta) wrapped into the box;
+ * v = m/rho from the expansions of the cells the points fall in.  l, v: host
+ * arrays of nbins. */
+int dg_structure_function(dg_ctx* ctx, int nbins, int64_t npairs, uint64_t seed, double* l, double* v);
+
+/* Bytes of the device work buffer dg_power_spectrum needs: the velocity on the
+ * Ng = (k+1)N grid (Ng^3 doubles) and its real-to-complex transform
+ * (Ng^2 (Ng/2+1) complex doubles). */
+int dg_analysis_bytes(const dg_mesh* mesh, int order, size_t* bytes);
+
+/* Velocity power spectrum (Sec. 4.1, Sec. 4.3): v sampled at x_g = (g+1/2)/Ng
+ * (k+1 points inside every cell per axis), v_hat = FFT(v)/Ng^3 per component
+ * (cuFFT, loaded at run time; its plan holds its own work area), summed over
+ * integer wave vectors kappa != 0 in logarithmic shells
+ * i = floor(log|kappa| / log(sqrt(3) Ng/2) nbins) (capped at nbins-1).
+ * kmean[i] = mean |kappa|, power[i] = sum of |v_hat_x|^2+|v_hat_y|^2+|v_hat_z|^2,
+ * count[i] = number of kappa (host arrays of nbins).  E(k) is power / bin
+ * width; the powers add up to the variance of the sampled velocity.
+ * work: device buffer of dg_analysis_bytes(), 256-byte aligned. */
+int dg_power_spectrum(dg_ctx* ctx, void* work, size_t work_bytes, int nbins, double* kmean, double* power,
+                      int64_t* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,10 @@ def lib() -> C.CDLL:
         L.dg_rhs_noalloc.argtypes = [C.POINTER(Mesh), i, d, C.POINTER(NuParams), i, vp, vp, vp, d, vp]
         L.dg_profile.argtypes = [vp, i]
         L.dg_profile_read.argtypes = [vp, C.POINTER(Prof)]
+        L.dg_density_pdf.argtypes = [vp, d, d, i, vp]
+        L.dg_structure_function.argtypes = [vp, i, C.c_int64, C.c_uint64, vp, vp]
+        L.dg_analysis_bytes.argtypes = [C.POINTER(Mesh), i, C.POINTER(C.c_size_t)]
+        L.dg_power_spectrum.argtypes = [vp, vp, C.c_size_t, i, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -117,7 +121,10 @@ EXPORTS = ("dg_scratch_bytes", "dg_vhat_bytes", "dg_init", "dg_free", "dg_last_e
            "dg_project_velocity", "dg_step", "dg_set_forcing", "dg_set_forcing_coeffs", "dg_forcing_from_modes",
            "dg_diagnostics", "dg_l1_density", "dg_get_meta", "dg_set_meta", "dg_profile", "dg_profile_read",
            "dg_rhs_noalloc", "dg_av_param_count", "dg_set_av_weights", "dg_get_av_weights", "dg_generate_pairs",
-           "dg_mlp_train", "dg_mlp_grad", "dg_mlp_forward", "dg_av_nu")
+           "dg_mlp_train", "dg_mlp_grad", "dg_mlp_forward", "dg_av_nu", "dg_density_pdf", "dg_structure_function",
+           "dg_analysis_bytes", "dg_power_spectrum")
+
+MAX_BINS = 2000
 
 
 class DGError(RuntimeError):

@@ -18,6 +18,9 @@
 #include <vector>
 
 #include "../../include/dg.h"
+
+#include <cufft.h>
+#include <dlfcn.h>
 #include "dg_launch.cuh"
 #include "dg_mlp.cuh"
 #include "dg_tile.cuh"
@@ -432,6 +435,34 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
+// cuFFT, loaded at run time: the power spectrum is its only user, and a
+// missing library then fails that call alone
+struct CufftApi {
+    bool ok = false;
+    decltype(&cufftPlan3d) plan3d = nullptr;
+    decltype(&cufftExecD2Z) exec_d2z = nullptr;
+    decltype(&cufftSetStream) set_stream = nullptr;
+    decltype(&cufftDestroy) destroy = nullptr;
+};
+static const CufftApi& cufft_api()
+{
+    static const CufftApi api = [] {
+        CufftApi a;
+        const char* names[] = {"libcufft.so.12", "libcufft.so.11", "libcufft.so"};
+        void* h = nullptr;
+        for (const char* n : names)
+            if ((h = dlopen(n, RTLD_NOW | RTLD_LOCAL)) != nullptr) break;
+        if (!h) return a;
+        a.plan3d = reinterpret_cast<decltype(a.plan3d)>(dlsym(h, "cufftPlan3d"));
+        a.exec_d2z = reinterpret_cast<decltype(a.exec_d2z)>(dlsym(h, "cufftExecD2Z"));
+        a.set_stream = reinterpret_cast<decltype(a.set_stream)>(dlsym(h, "cufftSetStream"));
+        a.destroy = reinterpret_cast<decltype(a.destroy)>(dlsym(h, "cufftDestroy"));
+        a.ok = a.plan3d && a.exec_d2z && a.set_stream && a.destroy;
+        return a;
+    }();
+    return api;
+}
+
 struct dg_ctx {
     int N = 0, K = 0, prec = 0, rk = 3, b = 0;
     long ncell = 0;
@@ -457,6 +488,9 @@ struct dg_ctx {
     int* d_kvec = nullptr;
     double* d_amp = nullptr;
     void* gtab = nullptr;  // forcing: 1D factors
+    double* ana = nullptr; // turbulence statistics accumulators
+    cufftHandle fft = 0;   // power-spectrum plan (created on first use)
+    int fft_ng = 0;
     Rule1 r1{};            // 1D Gauss rule
     int nsm = 0;
     bool state_set = false;
@@ -495,6 +529,7 @@ struct dg_ctx {
             cudaEventDestroy(p.b);
         }
         for (auto e : pool) cudaEventDestroy(e);
+        if (fft_ng > 0 && cufft_api().ok) cufft_api().destroy(fft);
     }
 };
 
@@ -504,6 +539,7 @@ struct ScratchLayout {
     size_t ctl, partials, tab, ttab, kvec, amp, gtab;
     size_t mw, mm, mv, mg, mpack, mloss, mwork;  // learned sensor: weights, Adam moments, grad, packed, loss, work
     size_t nu, vabs;                             // per-cell coefficient and |v| projection (learned mode)
+    size_t ana;                                  // turbulence statistics: 4 x DG_MAX_BINS doubles + 1
     size_t total;
 };
 
@@ -543,6 +579,8 @@ ScratchLayout scratch_layout(int K, int N, bool learned = false)
     off = align256(off + sizeof(double) * 16);
     s.mwork = off;
     off = align256(off + sizeof(float) * mlp_work_floats_host());
+    s.ana = off;
+    off = align256(off + sizeof(double) * (4 * DG_MAX_BINS + 1));
     s.nu = off;
     if (learned) off = align256(off + sizeof(float) * (size_t)ncell);
     s.vabs = off;
@@ -836,6 +874,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->d_kvec = (int*)(ctx->scratch + sl.kvec);
     ctx->d_amp = (double*)(ctx->scratch + sl.amp);
     ctx->gtab = ctx->scratch + sl.gtab;
+    ctx->ana = (double*)(ctx->scratch + sl.ana);
     {
         long double xg[4], wg[4];
         gauss_rule(order + 1, xg, wg);
@@ -1403,6 +1442,125 @@ int dg_set_meta(dg_ctx* ctx, const dg_meta* m)
     // re-project the current OU amplitudes before the next step
     ctx->drv.dirty = ctx->drv.on;
     if (!ctx->drv.on) ctx->forcing_active = false;
+    return DG_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// turbulence statistics
+// ---------------------------------------------------------------------------
+int dg_density_pdf(dg_ctx* ctx, double lo, double hi, int nbins, double* hist)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!hist || nbins < 1 || nbins > DG_MAX_BINS || !(hi > lo))
+        return fail(ctx, DG_EINVAL, "dg_density_pdf: bad bins or null buffer");
+    if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_density_pdf: no state set");
+    double* acc = ctx->ana;
+    double* mean = ctx->ana + 4 * DG_MAX_BINS;
+    CK(cudaMemsetAsync(ctx->ana, 0, sizeof(double) * (4 * DG_MAX_BINS + 1), ctx->st));
+    Launch L = make_launch(ctx);
+    {
+        Timed tm(ctx, KIND_OTHER);
+        const void* u = ctx->reg[ctx->cur];
+        CK(ctx->prec == DG_PREC_F64 ? launch_density_pdf<double>(L, (const double*)u, lo, hi, nbins, mean, acc)
+                                    : launch_density_pdf<float>(L, (const float*)u, lo, hi, nbins, mean, acc));
+    }
+    CK(cudaMemcpyAsync(hist, acc, sizeof(double) * nbins, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_structure_function(dg_ctx* ctx, int nbins, int64_t npairs, uint64_t seed, double* l, double* v)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!l || !v || nbins < 1 || nbins > DG_MAX_BINS || npairs < 1 || npairs > (int64_t(1) << 40) / nbins)
+        return fail(ctx, DG_EINVAL, "dg_structure_function: bad bins, pair count or null buffer");
+    if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_structure_function: no state set");
+    double* acc = ctx->ana;
+    CK(cudaMemsetAsync(acc, 0, sizeof(double) * nbins, ctx->st));
+    Launch L = make_launch(ctx);
+    {
+        Timed tm(ctx, KIND_OTHER);
+        const void* u = ctx->reg[ctx->cur];
+        CK(ctx->prec == DG_PREC_F64
+               ? launch_structure<double>(L, (const double*)u, nbins, (long)npairs, (unsigned long long)seed, acc)
+               : launch_structure<float>(L, (const float*)u, nbins, (long)npairs, (unsigned long long)seed, acc));
+    }
+    std::vector<double> a(nbins);
+    CK(cudaMemcpyAsync(a.data(), acc, sizeof(double) * nbins, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const double lmin = 1.0 / ((ctx->K + 1) * (double)ctx->N), lmax = 0.5;
+    for (int j = 0; j < nbins; ++j) {
+        l[j] = lmin * std::pow(lmax / lmin, (j + 0.5) / nbins);
+        v[j] = std::sqrt(0.5 * a[j] / (double)npairs);
+    }
+    return DG_OK;
+}
+
+static size_t analysis_bytes(int Ng)
+{
+    const size_t n3 = (size_t)Ng * Ng * Ng, nc = (size_t)Ng * Ng * (Ng / 2 + 1);
+    return align256(sizeof(double) * n3) + 2 * sizeof(double) * nc;
+}
+
+int dg_analysis_bytes(const dg_mesh* mesh, int order, size_t* bytes)
+{
+    if (!mesh || !bytes || order < 1 || order > 3 || mesh->n[0] < 1) return DG_EINVAL;
+    *bytes = analysis_bytes((order + 1) * mesh->n[0]);
+    return DG_OK;
+}
+
+int dg_power_spectrum(dg_ctx* ctx, void* work, size_t work_bytes, int nbins, double* kmean, double* power,
+                      int64_t* count)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!kmean || !power || !count || !work || nbins < 1 || nbins > DG_MAX_BINS)
+        return fail(ctx, DG_EINVAL, "dg_power_spectrum: bad bins or null buffer");
+    if (((uintptr_t)work) & 255u) return fail(ctx, DG_EINVAL, "dg_power_spectrum: work not 256-byte aligned");
+    const int Ng = (ctx->K + 1) * ctx->N;
+    if (work_bytes < analysis_bytes(Ng)) return fail(ctx, DG_ENOMEM, "dg_power_spectrum: work buffer too small");
+    if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_power_spectrum: no state set");
+    const CufftApi& fft = cufft_api();
+    if (!fft.ok) return fail(ctx, DG_ECUDA, "dg_power_spectrum: cuFFT library not found");
+    if (ctx->fft_ng != Ng) {
+        if (ctx->fft_ng > 0) fft.destroy(ctx->fft);
+        ctx->fft_ng = 0;
+        if (fft.plan3d(&ctx->fft, Ng, Ng, Ng, CUFFT_D2Z) != CUFFT_SUCCESS)
+            return fail(ctx, DG_ECUDA, "dg_power_spectrum: cuFFT plan failed");
+        ctx->fft_ng = Ng;
+    }
+    if (fft.set_stream(ctx->fft, ctx->st) != CUFFT_SUCCESS) return fail(ctx, DG_ECUDA, "dg_power_spectrum: cuFFT stream");
+    double* grid = static_cast<double*>(work);
+    void* F = static_cast<char*>(work) + align256(sizeof(double) * (size_t)Ng * Ng * Ng);
+    double* pw = ctx->ana;
+    double* ks = ctx->ana + DG_MAX_BINS;
+    unsigned long long* cn = reinterpret_cast<unsigned long long*>(ctx->ana + 2 * DG_MAX_BINS);
+    CK(cudaMemsetAsync(ctx->ana, 0, sizeof(double) * 3 * DG_MAX_BINS, ctx->st));
+    Launch L = make_launch(ctx);
+    const double n3 = (double)Ng * Ng * Ng;
+    const void* u = ctx->reg[ctx->cur];
+    for (int d = 0; d < 3; ++d) {
+        {
+            Timed tm(ctx, KIND_OTHER);
+            CK(ctx->prec == DG_PREC_F64 ? launch_sample<double>(L, (const double*)u, d, grid)
+                                        : launch_sample<float>(L, (const float*)u, d, grid));
+        }
+        if (fft.exec_d2z(ctx->fft, grid, static_cast<cufftDoubleComplex*>(F)) != CUFFT_SUCCESS)
+            return fail(ctx, DG_ECUDA, "dg_power_spectrum: cuFFT execution failed");
+        Timed tm(ctx, KIND_OTHER);
+        CK(launch_shell(L, F, Ng, nbins, 1.0 / (n3 * n3), d == 0, pw, ks, cn));
+    }
+    std::vector<double> hp(nbins), hk(nbins);
+    std::vector<unsigned long long> hc(nbins);
+    CK(cudaMemcpyAsync(hp.data(), pw, sizeof(double) * nbins, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hk.data(), ks, sizeof(double) * nbins, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hc.data(), cn, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int i = 0; i < nbins; ++i) {
+        power[i] = hp[i];
+        count[i] = (int64_t)hc[i];
+        kmean[i] = hc[i] ? hk[i] / (double)hc[i] : 0.0;
+    }
     return DG_OK;
 }
 

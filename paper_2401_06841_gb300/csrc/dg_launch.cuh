@@ -56,6 +56,17 @@ cudaError_t launch_diag(const Launch& L, const T* u, const T* ahat, double dt_pi
 template <typename T>
 cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB);
 
+// turbulence statistics (dg_analysis.cu)
+template <typename T>
+cudaError_t launch_density_pdf(const Launch& L, const T* u, double lo, double hi, int nbins, double* mean,
+                               double* hist);
+template <typename T>
+cudaError_t launch_structure(const Launch& L, const T* u, int nbins, long npairs, unsigned long long seed, double* acc);
+template <typename T>
+cudaError_t launch_sample(const Launch& L, const T* u, int d, double* out);
+cudaError_t launch_shell(const Launch& L, const void* F, int Ng, int nbins, double scale2, int first, double* power,
+                         double* ksum, unsigned long long* count);
+
 // learned viscosity sensor
 constexpr int kMlpHidden = 64;
 constexpr int kMlpBatchMax = 4096;

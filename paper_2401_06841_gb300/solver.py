@@ -204,6 +204,38 @@ class Solver:
                     self.h)
         return x, y
 
+    # ------------------------------------------------------------------
+    # turbulence statistics of the current state
+    def density_pdf(self, lo: float = -2.0, hi: float = 2.0, nbins: int = 200) -> np.ndarray:
+        """Volume fractions of log10(rho/rho_mean) in nbins equal bins on [lo, hi)."""
+        h = np.zeros(nbins)
+        self._check(self.L.dg_density_pdf(self.h, lo, hi, nbins, h.ctypes.data), self.h)
+        return h
+
+    def structure_function(self, nbins: int = 100, npairs: int = 100000, seed: int = 0):
+        """(l, v(l)): second-order velocity structure function on logarithmic bins."""
+        l = np.zeros(nbins)
+        v = np.zeros(nbins)
+        self._check(self.L.dg_structure_function(self.h, nbins, npairs, seed, l.ctypes.data, v.ctypes.data), self.h)
+        return l, v
+
+    def power_spectrum(self, nbins: int = 2000):
+        """(mean |kappa|, summed power, mode count) per logarithmic |kappa| shell of
+        the velocity on the (k+1)N grid."""
+        nb = C.c_size_t(0)
+        self._check(self.L.dg_analysis_bytes(C.byref(self.mesh), self.k, C.byref(nb)), None)
+        work = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device=self.device)
+        base = work.data_ptr()
+        off = (-base) % 256
+        km = np.zeros(nbins)
+        pw = np.zeros(nbins)
+        cnt = np.zeros(nbins, dtype=np.int64)
+        torch.cuda.synchronize(self.device)
+        self._check(self.L.dg_power_spectrum(self.h, base + off, int(nb.value), nbins, km.ctypes.data,
+                                             pw.ctypes.data, cnt.ctypes.data), self.h)
+        del work
+        return km, pw, cnt
+
     def mlp_train(self, x, y, epochs: int = 10, batch: int = 4096, lr: float = 1e-3) -> float:
         x = torch.as_tensor(x, dtype=torch.float32, device=self.device).contiguous()
         y = torch.as_tensor(y, dtype=torch.float32, device=self.device).contiguous()
