@@ -368,6 +368,21 @@ def main():
             "diag": {k_: v for k_, v in hs.diagnostics().items() if k_ in ("mach", "rho_min", "rho_max", "av_frac")}}
     if training is not None:
         line["learned_training"] = training
+    # turbulence statistics of the final state (paper's measurement settings):
+    # density PDF (200 bins), structure function (100 bins x 1e5 pairs),
+    # velocity power spectrum on the (k+1)N grid (2000 shells); wall ms per call
+    ana = {}
+    for name, fn in (("density_pdf_ms", lambda: hs.density_pdf(-2.0, 2.0, 200)),
+                     ("structure_function_ms", lambda: hs.structure_function(100, 100000, 0)),
+                     ("power_spectrum_ms", lambda: hs.power_spectrum(2000))):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        ana[name] = 1e3 * (time.perf_counter() - t0)
+        if name == "power_spectrum_ms":
+            ana["spectrum_total_power"] = float(out[1].sum())
+    line["analysis"] = ana
     if rank == 0 and not args.no_cpu:
         v, wall, cb = oracle_arm(args, args.cpu_steps, 1)
         cb["value"] = v
