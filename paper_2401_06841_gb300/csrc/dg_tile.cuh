@@ -720,19 +720,28 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 sA[(c * FE + 8 + i) * LDA + l] = (force && c < nvalid) ? sAh[e] : T(0);
             }
             // ---- evaluation coefficients: rho, m, grad rho, div m, (a_h staged above) ----
+            // threads run field-major (a warp covers one or two fields, so the
+            // per-field branches below do not diverge within it)
             for (int e = tid; e < RE; e += NT) {
-                const int c = e / FE, f = e % FE;
+                const int f = e / TC, c = e % TC;
                 const T* u = sU + c * 4 * b;
-                T* row = sA + e * LDA;
+                T* row = sA + (c * FE + f) * LDA;
                 if (f >= 8 && f < 11) {
 #pragma unroll
                     for (int l = b; l < KP; ++l) row[l] = T(0);
                     continue;
                 }
-                T out[b];
-                if (f < 4) {
+                T out[KP];
 #pragma unroll
-                    for (int l = 0; l < b; ++l) out[l] = u[f * b + l];
+                for (int l = b; l < KP; ++l) out[l] = T(0);
+                if (f < 4) {
+                    if constexpr (b % 4 == 0) {
+#pragma unroll
+                        for (int l = 0; l < b; l += 4) ld4<T>(u + f * b + l, out + l);
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < b; ++l) out[l] = u[f * b + l];
+                    }
                 } else if (f == 4) {
                     modal_grad<T, K, 0>(u, out, two_h);
                 } else if (f == 5) {
@@ -752,8 +761,9 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
 #pragma unroll
                     for (int l = 0; l < b; ++l) out[l] = T(0);
                 }
+                static_assert(KP % 4 == 0 && LDA % 4 == 0, "row vectors");
 #pragma unroll
-                for (int l = 0; l < KP; ++l) row[l] = (l < b) ? out[l] : T(0);
+                for (int l = 0; l < KP; l += 4) st4<T>(row + l, out + l);
             }
             __syncthreads();
             // ---- evaluation at the volume points ----
@@ -839,8 +849,9 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             };
             load_nbr(std::integral_constant<int, 0>{});
             // ---- volume term in modal space + forcing source ----
+            // (variable-major threads: the v == 0 and v > 0 branches split by warp)
             for (int e = tid; e < TC * 4; e += NT) {
-                const int c = e / 4, v = e % 4;
+                const int v = e / TC, c = e % TC;
                 T r[b];
 #pragma unroll
                 for (int l = 0; l < b; ++l) r[l] = T(0);
@@ -858,11 +869,24 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     modal_grad_T_acc<T, K, 0>(P + cx * LDP, r, two_h);
                     modal_grad_T_acc<T, K, 1>(P + cy * LDP, r, two_h);
                     modal_grad_T_acc<T, K, 2>(P + cz * LDP, r, two_h);
+                    if constexpr (b % 4 == 0) {
+                        T fa[b];
 #pragma unroll
-                    for (int l = 0; l < b; ++l) r[l] += P[(6 + i) * LDP + l];
+                        for (int l = 0; l < b; l += 4) ld4<T>(P + (6 + i) * LDP + l, fa + l);
+#pragma unroll
+                        for (int l = 0; l < b; ++l) r[l] += fa[l];
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < b; ++l) r[l] += P[(6 + i) * LDP + l];
+                    }
                 }
+                if constexpr (b % 4 == 0) {
 #pragma unroll
-                for (int l = 0; l < b; ++l) sR[(c * 4 + v) * b + l] = r[l];
+                    for (int l = 0; l < b; l += 4) st4<T>(sR + (c * 4 + v) * b + l, r + l);
+                } else {
+#pragma unroll
+                    for (int l = 0; l < b; ++l) sR[(c * 4 + v) * b + l] = r[l];
+                }
             }
             // (no barrier: the face collapse below touches other buffers; the
             // barrier after it orders these writes before the face lift)
@@ -889,8 +913,13 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     int fside = side;
                     if (who == 0) {
                         const T* src = (field == 0) ? sU + c * 4 * b : sVH + (c * 3 + field - 1) * b;
+                        if constexpr (b % 4 == 0) {
 #pragma unroll
-                        for (int l = 0; l < b; ++l) cf[l] = src[l];
+                            for (int l = 0; l < b; l += 4) ld4<T>(src + l, cf + l);
+                        } else {
+#pragma unroll
+                            for (int l = 0; l < b; ++l) cf[l] = src[l];
+                        }
                     } else {
                         fside = 1 - side;
 #pragma unroll
@@ -898,8 +927,9 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     }
                     T c2[B2K];
                     collapse<T, K, Dd, B2K>(cf, fside, c2);
+                    static_assert(B2K % 4 == 0 && LDC2 % 4 == 0, "row vectors");
 #pragma unroll
-                    for (int p = 0; p < B2K; ++p) sC2[r * LDC2 + p] = c2[p];
+                    for (int p = 0; p < B2K; p += 4) st4<T>(sC2 + r * LDC2 + p, c2 + p);
                 }
                 __syncthreads();
                 mm<T, BK, RC, NSP, B2K, LDC2, LDT, NT>(sC2, tabs, C::oPsi, sTr);
@@ -930,9 +960,26 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 for (int e = tid; e < TC * 4; e += NT) {
                     const int c = e / 4, v = e % 4;
                     T* R = sR + (c * 4 + v) * b;
+                    static_assert(LDL % 4 == 0 && B2N % 4 == 0, "row vectors");
+                    T l1[B2N], l0[B2N];
+#pragma unroll
+                    for (int p = 0; p < B2N; p += 4) {
+                        ld4<T>(sL2 + ((c * 2 + 1) * 4 + v) * LDL + p, l1 + p);
+                        ld4<T>(sL2 + ((c * 2 + 0) * 4 + v) * LDL + p, l0 + p);
+                    }
                     // + face (side 1): -1/(4h); - face (side 0): +1/(4h)
-                    expand_acc<T, K, Dd>(sL2 + ((c * 2 + 1) * 4 + v) * LDL, 1, -inv4h, R);
-                    expand_acc<T, K, Dd>(sL2 + ((c * 2 + 0) * 4 + v) * LDL, 0, inv4h, R);
+                    if constexpr (b % 4 == 0) {
+                        T rr[b];
+#pragma unroll
+                        for (int l = 0; l < b; l += 4) ld4<T>(R + l, rr + l);
+                        expand_acc<T, K, Dd>(l1, 1, -inv4h, rr);
+                        expand_acc<T, K, Dd>(l0, 0, inv4h, rr);
+#pragma unroll
+                        for (int l = 0; l < b; l += 4) st4<T>(R + l, rr + l);
+                    } else {
+                        expand_acc<T, K, Dd>(l1, 1, -inv4h, R);
+                        expand_acc<T, K, Dd>(l0, 0, inv4h, R);
+                    }
                 }
                 // no barrier: the next direction's collapse writes the other face
                 // region, and the barrier after it orders this lift before the
