@@ -346,7 +346,13 @@ double orc_dt(const orc_cfg* cfg, const double* u)
         }
     }
     tabs_free(&T);
-    return cfg->cfl * (1.0 / N) / ((cfg->k + 1) * smax);
+    double dt = cfg->cfl * (1.0 / N) / ((cfg->k + 1) * smax);
+    if (cfg->eps_diff > 0.0) {
+        /* explicit diffusion: dt <= cfl (h/(k+1))^2 / (2 eps) */
+        const double hp = (1.0 / N) / (cfg->k + 1), dd = cfg->cfl * hp * hp / (2.0 * cfg->eps_diff);
+        if (dd < dt) dt = dd;
+    }
+    return dt;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -517,6 +523,7 @@ static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, dou
             }
     free(vhat);
     tabs_free(&T);
+    orc_diffusion_rhs(cfg, u, dudt); /* + div(eps grad u) when eps > 0 */
     return 0;
 }
 
@@ -1032,4 +1039,168 @@ void orc_sample_velocity(const orc_cfg* cfg, const double* u, double* v_out)
                 const size_t g = ((size_t)gz * Ng + gy) * Ng + gx;
                 for (int d = 0; d < 3; ++d) v_out[d * n3 + g] = v[d];
             }
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* diffusion operator div(eps grad u) (Sec. 2, diffusion across cell         */
+/* boundaries).  The second derivative at an interface comes from a          */
+/* "virtual" cell that covers both neighbours: on their union the solution   */
+/* is replaced by the one polynomial whose projections onto each cell's      */
+/* basis are that cell's coefficients (recovery); its normal derivative at   */
+/* the face is the interface gradient.  Weak form on a cell K:               */
+/*   (1/|K|) [ -int_K eps grad phi_l . grad u dV                             */
+/*             + int_dK eps phi_l (grad u_rec . n) dS ]                      */
+/* ------------------------------------------------------------------------ */
+
+/* Gaussian elimination with partial pivoting, A [n][n] row-major, b [n] */
+static void solve_dense(int n, double* A, double* b)
+{
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[r * n + c]) > fabs(A[p * n + c])) p = r;
+        if (p != c) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[c * n + j];
+                A[c * n + j] = A[p * n + j];
+                A[p * n + j] = t;
+            }
+            double t = b[c];
+            b[c] = b[p];
+            b[p] = t;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            const double f = A[r * n + c] / A[c * n + c];
+            for (int j = c; j < n; ++j) A[r * n + j] -= f * A[c * n + j];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int j = r + 1; j < n; ++j) s -= A[r * n + j] * b[j];
+        b[r] = s / A[r * n + r];
+    }
+}
+
+/* 1D recovery across a face.  Coordinate s in half-cell units on the union
+ * of the two cells: L = [-2, 0] (s = xi - 1), R = [0, 2] (s = xi + 1).  With
+ * the K+1 normalised-Legendre coefficients of each side, find the polynomial
+ * r of degree 2K+1 with (1/2) int_{-1}^{1} Pn_a(xi) r(xi -+ 1) dxi = c_a for
+ * a = 0..K on both sides; return dr/ds at the face s = 0.  r is expanded in
+ * monomials of s and the moments are taken with a 10-point Gauss rule (exact
+ * for the degree 3K+1 <= 10 integrands). */
+double orc_recover_dn(int K, const double* cL, const double* cR)
+{
+    const int n = 2 * K + 2;
+    double A[64], rhs[8], xg[10], wg[10];
+    orc_gauss(10, xg, wg);
+    for (int a = 0; a <= K; ++a)
+        for (int j = 0; j < n; ++j) {
+            double mL = 0.0, mR = 0.0;
+            for (int g = 0; g < 10; ++g) {
+                const double pa = sqrt(2.0 * a + 1.0) * orc_legendre(a, xg[g]);
+                mL += 0.5 * wg[g] * pa * pow(xg[g] - 1.0, j);
+                mR += 0.5 * wg[g] * pa * pow(xg[g] + 1.0, j);
+            }
+            A[a * n + j] = mL;
+            A[(K + 1 + a) * n + j] = mR;
+        }
+    for (int a = 0; a <= K; ++a) {
+        rhs[a] = cL[a];
+        rhs[K + 1 + a] = cR[a];
+    }
+    solve_dense(n, A, rhs);
+    return rhs[1]; /* d/ds of sum_j r_j s^j at s = 0 */
+}
+
+void orc_diffusion_rhs(const orc_cfg* cfg, const double* u, double* dudt)
+{
+    const double eps = cfg->eps_diff;
+    if (!(eps > 0.0)) return;
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    const int N = cfg->N, b = T.b, k = cfg->k, nq = T.nq, ns = T.ns;
+    const size_t nc = (size_t)N * N * N;
+    const double h = 1.0 / N;
+    /* the recovered face derivative is linear in the two coefficient columns:
+     * its weights, per number of normal modes K+1, from unit columns */
+    double wL[4][4], wR[4][4];
+    for (int K = 0; K <= k; ++K)
+        for (int a = 0; a <= K; ++a) {
+            double e[4] = {0, 0, 0, 0}, z[4] = {0, 0, 0, 0};
+            e[a] = 1.0;
+            wL[K][a] = orc_recover_dn(K, e, z);
+            wR[K][a] = orc_recover_dn(K, z, e);
+        }
+    /* mode index of the degree triple */
+    int midx[4][4][4];
+    for (int l = 0; l < b; ++l) midx[T.ijl[3 * l]][T.ijl[3 * l + 1]][T.ijl[3 * l + 2]] = l;
+    /* volume: -(eps/|K|) int grad phi_l . grad u = -eps (4/h^2) (1/8) sum_q w_q grad_xi phi_l . grad_xi u */
+    for (size_t c = 0; c < nc; ++c)
+        for (int var = 0; var < 4; ++var) {
+            const double* uc = u + (c * 4 + var) * b;
+            for (int q = 0; q < nq; ++q) {
+                double g[3];
+                for (int d = 0; d < 3; ++d) g[d] = eval(&T, uc, T.dphi + ((size_t)d * nq + q) * b);
+                for (int l = 0; l < b; ++l) {
+                    double s = 0.0;
+                    for (int d = 0; d < 3; ++d) s += T.dphi[((size_t)d * nq + q) * b + l] * g[d];
+                    dudt[(c * 4 + var) * b + l] -= eps * (4.0 / (h * h)) * 0.125 * T.wq[q] * s;
+                }
+            }
+        }
+    /* faces: for each cell's + face along d, L = the cell, R = its neighbour */
+    for (int d = 0; d < 3; ++d) {
+        const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        for (int iz = 0; iz < N; ++iz)
+            for (int iy = 0; iy < N; ++iy)
+                for (int ix = 0; ix < N; ++ix) {
+                    const int ic[3] = {ix, iy, iz};
+                    int jc[3] = {ix, iy, iz};
+                    jc[d] += 1;
+                    const size_t cL = (size_t)cell_index(N, ic[0], ic[1], ic[2]);
+                    const size_t cR = (size_t)cell_index(N, jc[0], jc[1], jc[2]);
+                    for (int var = 0; var < 4; ++var) {
+                        const double* uL = u + (cL * 4 + var) * b;
+                        const double* uR = u + (cR * 4 + var) * b;
+                        /* normal derivative (physical) at the face points */
+                        double gs[64];
+                        for (int s = 0; s < ns; ++s) gs[s] = 0.0;
+                        /* one 1D recovery per tangential degree pair (p1, p2), p1 + p2 <= k */
+                        for (int p1 = 0; p1 <= k; ++p1)
+                            for (int p2 = 0; p1 + p2 <= k; ++p2) {
+                                const int K = k - p1 - p2;
+                                double dn = 0.0;
+                                for (int a = 0; a <= K; ++a) {
+                                    int deg[3];
+                                    deg[d] = a;
+                                    deg[t1] = p1;
+                                    deg[t2] = p2;
+                                    const int m = midx[deg[0]][deg[1]][deg[2]];
+                                    dn += wL[K][a] * uL[m] + wR[K][a] * uR[m];
+                                }
+                                dn *= 2.0 / h;
+                                for (int s = 0; s < ns; ++s) {
+                                    const double x1 = T.xg[s % T.n], x2 = T.xg[s / T.n];
+                                    gs[s] += dn * sqrt(2.0 * p1 + 1.0) * orc_legendre(p1, x1) * sqrt(2.0 * p2 + 1.0) *
+                                             orc_legendre(p2, x2);
+                                }
+                            }
+                        /* (eps/|K|) int_face phi_l (grad u . n) dS = eps/h^3 (h/2)^2 sum_s w_s phi_l(s) g_s */
+                        const double* phL = T.phif + ((size_t)(d * 2 + 1) * ns) * b;
+                        const double* phR = T.phif + ((size_t)(d * 2 + 0) * ns) * b;
+                        for (int l = 0; l < b; ++l) {
+                            double sL = 0.0, sR = 0.0;
+                            for (int s = 0; s < ns; ++s) {
+                                sL += T.ws[s] * phL[s * b + l] * gs[s];
+                                sR += T.ws[s] * phR[s * b + l] * gs[s];
+                            }
+                            dudt[(cL * 4 + var) * b + l] += eps / (4.0 * h) * sL;
+                            dudt[(cR * 4 + var) * b + l] -= eps / (4.0 * h) * sR;
+                        }
+                    }
+                }
+    }
+    tabs_free(&T);
 }

@@ -35,6 +35,7 @@ typedef struct {
     double cfl;         /* Courant number                                   */
     int32_t rk_stages;  /* 2 (SSP-RK2) or 3 (SSP-RK3)                        */
     int32_t riemann;    /* face flux: 0 Rusanov, 1 HLL, 2 HLLC               */
+    double eps_diff;    /* diffusion coefficient of div(eps grad u), 0: off  */
 } orc_cfg;
 
 #define ORC_RUSANOV 0
@@ -66,6 +67,8 @@ double orc_legendre(int m, double x);
 double orc_legendre_deriv(int m, double x);
 
 double orc_dt(const orc_cfg* cfg, const double* u);
+double orc_recover_dn(int K, const double* cL, const double* cR);
+void orc_diffusion_rhs(const orc_cfg* cfg, const double* u, double* dudt);
 void orc_project_velocity(const orc_cfg* cfg, const double* u, double* vhat);
 void orc_forcing_mean(const orc_cfg* cfg, const double* u, const double* ahat,
                       double abar[3]);

@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
 class Cfg(C.Structure):
     _fields_ = [("N", C.c_int32), ("k", C.c_int32), ("cs", C.c_double), ("av_mode", C.c_int32),
                 ("alpha", C.c_double), ("beta", C.c_double), ("rho_floor", C.c_double), ("cfl", C.c_double),
-                ("rk_stages", C.c_int32), ("riemann", C.c_int32)]
+                ("rk_stages", C.c_int32), ("riemann", C.c_int32), ("eps_diff", C.c_double)]
 
 
 RIEMANN = {"rusanov": 0, "hll": 1, "hllc": 2}
@@ -77,6 +77,9 @@ def lib():
         _lib.orc_vnr.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double]
         _lib.orc_rusanov.argtypes = [C.c_double, C.c_int, d, d, d]
         _lib.orc_riemann.argtypes = [C.c_int, C.c_double, C.c_int, d, d, d]
+        _lib.orc_recover_dn.restype = C.c_double
+        _lib.orc_recover_dn.argtypes = [C.c_int, d, d]
+        _lib.orc_diffusion_rhs.argtypes = [C.POINTER(Cfg), d, d]
         _lib.orc_density_pdf.argtypes = [C.POINTER(Cfg), d, C.c_double, C.c_double, C.c_int, d]
         _lib.orc_structure_function.argtypes = [C.POINTER(Cfg), d, C.c_int, C.c_int64, C.c_uint64, d, d]
         _lib.orc_sample_velocity.argtypes = [C.POINTER(Cfg), d, d]
@@ -128,10 +131,10 @@ def legendre_deriv(m: int, x: float) -> float:
 
 
 def make_cfg(N, k, cs=1.0, av_mode=1, alpha=2.0, beta=0.2, rho_floor=1e-3, cfl=0.3, rk_stages=None,
-             riemann="rusanov") -> Cfg:
+             riemann="rusanov", eps_diff=0.0) -> Cfg:
     if rk_stages is None:
         rk_stages = 2 if k == 1 else 3
-    return Cfg(N, k, cs, av_mode, alpha, beta, rho_floor, cfl, rk_stages, RIEMANN[riemann])
+    return Cfg(N, k, cs, av_mode, alpha, beta, rho_floor, cfl, rk_stages, RIEMANN[riemann], eps_diff)
 
 
 def _shape(cfg, nvar=4):
@@ -173,6 +176,20 @@ def riemann(solver: str, cs: float, d: int, WL, WR) -> np.ndarray:
     F = np.zeros(4)
     lib().orc_riemann(RIEMANN[solver], cs, d, _p(WL), _p(WR), _p(F))
     return F
+
+
+def recover_dn(K: int, cL, cR) -> float:
+    """d/ds at the face of the degree-2K+1 recovery of two cells' K+1 coefficients (s in half cells)."""
+    cL = np.ascontiguousarray(cL, dtype=np.float64)
+    cR = np.ascontiguousarray(cR, dtype=np.float64)
+    return lib().orc_recover_dn(K, _p(cL), _p(cR))
+
+
+def diffusion_rhs(cfg: Cfg, u: np.ndarray) -> np.ndarray:
+    """The diffusion operator div(eps grad u) alone, in modal coefficients."""
+    out = np.zeros(_shape(cfg))
+    lib().orc_diffusion_rhs(C.byref(cfg), _p(u), _p(out))
+    return out
 
 
 def rhs(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None = None, dt_pimax: float = 0.0) -> np.ndarray:
