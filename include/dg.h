@@ -81,13 +81,21 @@ typedef struct {
  * nu/(cs h/p) is below nu_gate gets nu = 0, i.e. no viscous pressure at any of
  * its points (the sensor's "no shock here" decision); 0 disables the gate.
  * The tile kernels evaluate div v for every cell of a tile either way, so the
- * gate changes the result, not the work. */
+ * gate changes the result, not the work.
+ * diffusion (>= 0): eps of div(eps grad u).  The interface gradient is the
+ * normal derivative at the face of the polynomial recovered over the face's
+ * two cells (degree 2K+1 in the normal direction from the K+1 normal
+ * coefficients of each cell, per tangential mode): the paper's "virtual cell"
+ * over both neighbours.  The time step is also limited by
+ * dt <= cfl (h/(k+1))^2 / (2 eps). */
 typedef struct {
     int32_t mode;          /* DG_AV_OFF, DG_AV_VNR, DG_AV_LEARNED                 */
     double alpha;          /* default 2.0                                          */
     double beta;           /* default 0.2                                          */
     double rho_floor;      /* default 1e-3                                         */
     double nu_gate;        /* default 0 (no gating)                                */
+    double diffusion;      /* eps of an added div(eps grad u) on all four variables
+                              (Sec. 2, diffusion across cell boundaries); 0: off   */
 } dg_nu_params;
 
 typedef struct {
@@ -293,7 +301,8 @@ int dg_set_meta(dg_ctx* ctx, const dg_meta* in);
  * that loads it until the process exits.  Limit: N^3 * 3 * b * element size
  * plus about 1.2 MiB must fit in 64 MiB (for example N <= 64 at k = 3 in
  * FP32); larger meshes return DG_ENOMEM and nothing runs.  Artificial
- * viscosity modes DG_AV_OFF and DG_AV_VNR only.  The first call on a device
+ * viscosity modes DG_AV_OFF and DG_AV_VNR only, no diffusion operator (nu->diffusion
+ * must be 0).  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) and the first
  * call for a given order and precision uploads the tables: make that first
  * call before any stream capture.  All calls share the array and it keeps the

@@ -27,7 +27,7 @@ class Mesh(C.Structure):
 
 class NuParams(C.Structure):
     _fields_ = [("mode", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double), ("rho_floor", C.c_double),
-                ("nu_gate", C.c_double)]
+                ("nu_gate", C.c_double), ("diffusion", C.c_double)]
 
 
 class Opts(C.Structure):

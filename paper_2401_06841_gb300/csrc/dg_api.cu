@@ -90,6 +90,70 @@ void gauss_rule(int n, long double* x, long double* w)
 }
 
 // normalised Legendre sqrt(2m+1) P_m(x), three-term recurrence
+// Recovery weights of the face gradient: on the union of two cells, s in
+// half-cell units (left cell s = xi - 1, right cell s = xi + 1), the polynomial
+// r(s) = sum_{j <= 2K+1} d_j P_j(s/2) whose normalised-Legendre moments on each
+// cell are that cell's K+1 normal coefficients; dr/ds at s = 0 is linear in
+// the 2K+2 coefficients: wL[a] (left), wR[a] (right).
+long double leg(int j, long double x)  // P_j(x)
+{
+    long double p0 = 1.0L, p1 = x;
+    if (j == 0) return p0;
+    for (int i = 1; i < j; ++i) {
+        const long double p2 = ((2.0L * i + 1.0L) * x * p1 - i * p0) / (i + 1.0L);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+void recovery_weights(int K, double* wL, double* wR)
+{
+    const int n = 2 * K + 2;
+    long double xg[12], wg[12];
+    gauss_rule(12, xg, wg);
+    long double A[8][16] = {};
+    for (int a = 0; a <= K; ++a)
+        for (int j = 0; j < n; ++j) {
+            long double mL = 0.0L, mR = 0.0L;
+            for (int g = 0; g < 12; ++g) {
+                const long double pa = sqrtl(2.0L * a + 1.0L) * leg(a, xg[g]);
+                mL += 0.5L * wg[g] * pa * leg(j, (xg[g] - 1.0L) / 2.0L);
+                mR += 0.5L * wg[g] * pa * leg(j, (xg[g] + 1.0L) / 2.0L);
+            }
+            A[a][j] = mL;
+            A[K + 1 + a][j] = mR;
+        }
+    // inverse by Gauss-Jordan with partial pivoting ([A | I] in 8 x 16)
+    for (int i = 0; i < n; ++i) A[i][n + i] = 1.0L;
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabsl(A[r][c]) > fabsl(A[p][c])) p = r;
+        for (int j = 0; j < 2 * n; ++j) std::swap(A[c][j], A[p][j]);
+        const long double inv = 1.0L / A[c][c];
+        for (int j = 0; j < 2 * n; ++j) A[c][j] *= inv;
+        for (int r = 0; r < n; ++r)
+            if (r != c) {
+                const long double f = A[r][c];
+                for (int j = 0; j < 2 * n; ++j) A[r][j] -= f * A[c][j];
+            }
+    }
+    // dr/ds(0) = sum_j d_j P_j'(0) / 2, P'_{j+1}(0) = P'_{j-1}(0) + (2j+1) P_j(0)
+    long double dp[8] = {};
+    dp[0] = 0.0L;
+    dp[1] = 1.0L;
+    for (int j = 1; j + 1 < n; ++j) dp[j + 1] = dp[j - 1] + (2.0L * j + 1.0L) * leg(j, 0.0L);
+    for (int a = 0; a < n; ++a) {
+        long double w = 0.0L;
+        for (int j = 0; j < n; ++j) w += 0.5L * dp[j] * A[j][n + a];
+        if (a <= K)
+            wL[a] = (double)w;
+        else
+            wR[a - K - 1] = (double)w;
+    }
+}
+
 long double pnorm(int m, long double x)
 {
     long double p0 = 1.0L, p1 = x;
@@ -492,6 +556,7 @@ struct dg_ctx {
     cufftHandle fft = 0;   // power-spectrum plan (created on first use)
     int fft_ng = 0;
     Rule1 r1{};            // 1D Gauss rule
+    double recL[4][4] = {}, recR[4][4] = {};  // recovery weights of the face gradient
     int nsm = 0;
     bool state_set = false;
     bool forcing_active = false;  // ahat holds a forcing to apply
@@ -620,6 +685,9 @@ Launch make_launch(const dg_ctx* c)
     L.ph.av_mode = c->nu.mode;
     L.ph.riemann = c->riemann;
     L.ph.nu_gate = c->nu.nu_gate;
+    L.ph.eps = c->nu.diffusion;
+    std::memcpy(L.ph.recL, c->recL, sizeof(c->recL));
+    std::memcpy(L.ph.recR, c->recR, sizeof(c->recR));
     L.tab = c->tab;
     L.ttab = c->ttab;
     L.ctl = c->ctl;
@@ -835,7 +903,8 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     for (int d = 0; d < 3; ++d)
         if (mesh->L[d] != 1.0) return DG_EINVAL;
     if (!(cs > 0.0)) return DG_EINVAL;
-    if (nu->mode < 0 || nu->mode > 2 || !(nu->rho_floor >= 0.0) || !(nu->nu_gate >= 0.0)) return DG_EINVAL;
+    if (nu->mode < 0 || nu->mode > 2 || !(nu->rho_floor >= 0.0) || !(nu->nu_gate >= 0.0) || !(nu->diffusion >= 0.0))
+        return DG_EINVAL;
     if (opts->precision < 0 || opts->precision > 2) return DG_EINVAL;
     if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
     if (!(opts->cfl > 0.0)) return DG_EINVAL;
@@ -874,6 +943,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->d_kvec = (int*)(ctx->scratch + sl.kvec);
     ctx->d_amp = (double*)(ctx->scratch + sl.amp);
     ctx->gtab = ctx->scratch + sl.gtab;
+    for (int K = 0; K <= order; ++K) recovery_weights(K, ctx->recL[K], ctx->recR[K]);
     ctx->ana = (double*)(ctx->scratch + sl.ana);
     {
         long double xg[4], wg[4];
@@ -910,6 +980,10 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     Ctl c0{};
     c0.dt_scale = 1.0;
     c0.dt_num = ctx->cfl * ctx->h / (order + 1);
+    {
+        const double hp = ctx->h / (order + 1);
+        c0.dt_diff = nu->diffusion > 0.0 ? ctx->cfl * hp * hp / (2.0 * nu->diffusion) : 0.0;
+    }
     e = cudaMemcpyAsync(ctx->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st);
     if (e == cudaSuccess) {
         if (ctx->prec == DG_PREC_F64) {

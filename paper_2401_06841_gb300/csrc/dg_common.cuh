@@ -127,7 +127,8 @@ struct Ctl {
     double diag[16];         // diagnostics result
     double l1;               // L1 result
     double sn;               // max sum_d(|v_d|+cs) of the state the next step starts from
-    double pad[3];
+    double dt_diff;          // explicit diffusion limit cfl (h/(k+1))^2 / (2 eps), 0: none
+    double pad[2];
 };
 
 // kernel flags
@@ -147,6 +148,10 @@ struct Phys {
     int av_mode;                 // 0 off, 1 vNR, 2 learned
     int riemann;                 // face flux: 0 Rusanov, 1 HLL, 2 HLLC
     double nu_gate;              // learned sensor: nu/(cs h/p) below this -> no viscous pressure
+    double eps;                  // diffusion coefficient of div(eps grad u), 0: off
+    // recovered face derivative d r/ds at the face (s in half cells) from the
+    // K+1 normal coefficients of the left and right cell: sum_a recL[K][a] cL_a + recR[K][a] cR_a
+    double recL[4][4], recR[4][4];
 };
 
 // von Neumann-Richtmyer viscous pressure at a volume point (Sec. 3.1):

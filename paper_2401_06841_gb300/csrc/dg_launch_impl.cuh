@@ -10,23 +10,24 @@ namespace dg {
 
 template <typename T, int K>
 struct Occ {
-    static int tile[2][4], force, diag;
+    static int tile[2][2][4], force, diag;  // [diffusion][back end][mode]
 };
 template <typename T, int K>
-int Occ<T, K>::tile[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+int Occ<T, K>::tile[2][2][4] = {};
 template <typename T, int K>
 int Occ<T, K>::force = 0;
 template <typename T, int K>
 int Occ<T, K>::diag = 0;
 
-template <typename T, int K, int MODE, int BK>
+template <typename T, int K, int MODE, int BK, bool DIFF = false>
 static cudaError_t setup_tile()
 {
     const size_t sm = sizeof(T) * TileCfg<K, BK>::total;
-    cudaError_t e = cudaFuncSetAttribute(k_tile<T, K, MODE, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tile<T, K, MODE, BK, DIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::tile[BK][MODE], k_tile<T, K, MODE, BK>,
-                                                         TileCfg<K, BK>::NT, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::tile[DIFF][BK][MODE],
+                                                         k_tile<T, K, MODE, BK, DIFF>, TileCfg<K, BK>::NT, sm);
 }
 
 template <typename T, int K, int BK>
@@ -36,7 +37,23 @@ static cudaError_t setup_modes()
     if ((e = setup_tile<T, K, TM_PROJECT, BK>()) != cudaSuccess) return e;
     if ((e = setup_tile<T, K, TM_RHS, BK>()) != cudaSuccess) return e;
     if ((e = setup_tile<T, K, TM_STAGE, BK>()) != cudaSuccess) return e;
-    return setup_tile<T, K, TM_STAGE_VABS, BK>();
+    if ((e = setup_tile<T, K, TM_STAGE_VABS, BK>()) != cudaSuccess) return e;
+    if ((e = setup_tile<T, K, TM_RHS, BK, true>()) != cudaSuccess) return e;
+    if ((e = setup_tile<T, K, TM_STAGE, BK, true>()) != cudaSuccess) return e;
+    return setup_tile<T, K, TM_STAGE_VABS, BK, true>();
+}
+
+// tile-kernel set-up and launch of one degree; explicitly instantiated per
+// translation unit (DG_TILES_*) so that the heaviest degree compiles apart
+template <typename T, int K>
+cudaError_t setup_tiles()
+{
+    cudaError_t e;
+    if ((e = setup_modes<T, K, BK_FMA>()) != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4) {
+        if ((e = setup_modes<T, K, BK_X3>()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T, int K>
@@ -44,10 +61,7 @@ static cudaError_t setup_k()
 {
     constexpr int NT = Tile<K>::NT;
     cudaError_t e;
-    if ((e = setup_modes<T, K, BK_FMA>()) != cudaSuccess) return e;
-    if constexpr (sizeof(T) == 4) {
-        if ((e = setup_modes<T, K, BK_X3>()) != cudaSuccess) return e;
-    }
+    if ((e = setup_tiles<T, K>()) != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::force, k_force<T, K>, 256, 0);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&Occ<T, K>::diag, k_diag<T, K>, NT, 0);
@@ -112,20 +126,24 @@ static cudaError_t tile_kb(const Launch& L, const TileLaunch& t)
     using Cf = TileCfg<K, BK>;
     const long ntile = (L.ncell + Cf::TC - 1) / Cf::TC;
     const size_t sm = sizeof(T) * Cf::total;
-    const int g = grid_for(ntile, Occ<T, K>::tile[BK][t.mode], L.nsm);
+    const bool dif = L.ph.eps > 0.0 && t.mode != TM_PROJECT;
+    const int g = grid_for(ntile, Occ<T, K>::tile[dif][BK][t.mode], L.nsm);
     if (t.mode == TM_PROJECT)
         k_tile<T, K, TM_PROJECT, BK><<<g, Cf::NT, sm, L.st>>>(a);
     else if (t.mode == TM_RHS)
-        k_tile<T, K, TM_RHS, BK><<<g, Cf::NT, sm, L.st>>>(a);
+        dif ? k_tile<T, K, TM_RHS, BK, true><<<g, Cf::NT, sm, L.st>>>(a)
+            : k_tile<T, K, TM_RHS, BK><<<g, Cf::NT, sm, L.st>>>(a);
     else if (t.mode == TM_STAGE)
-        k_tile<T, K, TM_STAGE, BK><<<g, Cf::NT, sm, L.st>>>(a);
+        dif ? k_tile<T, K, TM_STAGE, BK, true><<<g, Cf::NT, sm, L.st>>>(a)
+            : k_tile<T, K, TM_STAGE, BK><<<g, Cf::NT, sm, L.st>>>(a);
     else
-        k_tile<T, K, TM_STAGE_VABS, BK><<<g, Cf::NT, sm, L.st>>>(a);
+        dif ? k_tile<T, K, TM_STAGE_VABS, BK, true><<<g, Cf::NT, sm, L.st>>>(a)
+            : k_tile<T, K, TM_STAGE_VABS, BK><<<g, Cf::NT, sm, L.st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T, int K>
-static cudaError_t tile_k(const Launch& L, const TileLaunch& t)
+cudaError_t tile_k(const Launch& L, const TileLaunch& t)
 {
     if constexpr (sizeof(T) == 4) {
         if (L.bk == BK_X3) return tile_kb<T, K, BK_X3>(L, t);
@@ -198,6 +216,13 @@ cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB)
 {
     DG_DISPATCH(l1_k, uA, uB);
 }
+
+#define DG_TILES_EXTERN(T, K)                                                   \
+    extern template cudaError_t tile_k<T, K>(const Launch&, const TileLaunch&); \
+    extern template cudaError_t setup_tiles<T, K>();
+#define DG_TILES_INSTANTIATE(T, K)                                       \
+    template cudaError_t tile_k<T, K>(const Launch&, const TileLaunch&); \
+    template cudaError_t setup_tiles<T, K>();
 
 #define DG_INSTANTIATE(T)                                                                                         \
     template cudaError_t setup_kernels<T>(int);                                                                  \

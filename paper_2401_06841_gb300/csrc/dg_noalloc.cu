@@ -229,6 +229,7 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double cs, const d
     if (mesh->n[0] < 1 || mesh->n[0] != mesh->n[1] || mesh->n[0] != mesh->n[2]) return report(DG_EINVAL, "mesh");
     for (int d = 0; d < 3; ++d)
         if (mesh->L[d] != 1.0) return report(DG_EINVAL, "box size must be 1");
+    if (nu->diffusion != 0.0) return report(DG_EINVAL, "the diffusion operator needs a context (dg_init)");
     if (!(cs > 0.0) || nu->mode < 0 || nu->mode > 1 || !(nu->rho_floor >= 0.0))
         return report(DG_EINVAL, "cs or artificial-viscosity parameters");
     const long N = mesh->n[0];

@@ -440,6 +440,39 @@ __device__ __forceinline__ void expand_acc(const T* L2, int side, T scale, T* R)
 // kernel modes: projection only; RHS only; RHS + stage combine (+ the next
 // stage's projection with F_NEXTPROJ); the same with the projection of |v|
 // for the learned sensor's features (the last stage of a learned-mode step)
+// Diffusion across the faces along Dd (div(eps grad u), Sec. 2): the interface
+// gradient is the normal derivative of the polynomial recovered over the two
+// cells of a face, per tangential mode tau a combination of the two cells'
+// normal coefficient columns, g_tau = sum_a recL[K_tau][a] cL + recR[K_tau][a] cR
+// (K_tau + 1 normal modes).  Its lift is exact in modal space:
+//   + face of the cell: R_m += (2 eps / h^2) Pn_a(+1) g_tau,
+//   - face of the cell: R_m -= (2 eps / h^2) Pn_a(-1) g_tau.
+template <typename T, int K, int Dd>
+__device__ __forceinline__ void diffusion_faces(const Phys& ph, const T* self, const T* minus, const T* plus, T* R)
+{
+    constexpr int b = Dims<K>::b, B2 = (K + 1) * (K + 2) / 2;
+    constexpr Modes<K> M{};
+    T gp[B2], gm[B2];
+#pragma unroll
+    for (int p = 0; p < B2; ++p) gp[p] = gm[p] = T(0);
+    static_for<0, b>([&](auto mm) {
+        constexpr int m = decltype(mm)::value;
+        constexpr int nd = normal_deg<K>(Dd, m), tm = tang_mode<K>(Dd, m);
+        constexpr int Kt = K - (M.i[m] + M.j[m] + M.l[m] - nd);
+        // + face: left = this cell, right = the + neighbour; - face: left = the - neighbour
+        gp[tm] += T(ph.recL[Kt][nd]) * self[m] + T(ph.recR[Kt][nd]) * plus[m];
+        gm[tm] += T(ph.recL[Kt][nd]) * minus[m] + T(ph.recR[Kt][nd]) * self[m];
+    });
+    const T scale = T(2.0 * ph.eps / (ph.h * ph.h));
+    static_for<0, b>([&](auto mm) {
+        constexpr int m = decltype(mm)::value;
+        constexpr int nd = normal_deg<K>(Dd, m), tm = tang_mode<K>(Dd, m);
+        constexpr double f = csqrt(2.0 * nd + 1.0);
+        constexpr double fm = (nd & 1) ? -f : f;
+        R[m] += scale * (T(f) * gp[tm] - T(fm) * gm[tm]);
+    });
+}
+
 enum { TM_PROJECT = 0, TM_RHS = 1, TM_STAGE = 2, TM_STAGE_VABS = 3 };
 enum { F_NEXTPROJ = 4, F_VABS = 8 };
 
@@ -578,7 +611,9 @@ __device__ __forceinline__ void tile_project(T* sm, const T* sU, const T* tabs, 
     if (with_sums && (a.flags & F_FORCE)) forcing_sums<T, K, BK>(sm, sU, a, c0, sums);
 }
 
-template <typename T, int K, int MODE, int BK>
+// DIFF: the diffusion operator div(eps grad u) is compiled in (a separate
+// instantiation, so that the plain scheme carries none of its code)
+template <typename T, int K, int MODE, int BK, bool DIFF = false>
 __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
 {
     using C = TileCfg<K, BK>;
@@ -629,12 +664,15 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     const bool do_proj = (MODE == TM_PROJECT) || (STAGE && (a.flags & F_NEXTPROJ));
     T dt = T(0), ab0 = T(0), ab1 = T(0), ab2 = T(0);
     AvCoef<T> avc{};
+    const T diff_vol = T(-4.0 * a.ph.eps / (a.ph.h * a.ph.h));
     if constexpr (MODE != TM_PROJECT) {
         if constexpr (STAGE) {
             // the step's dt (Sec. 7 CFL condition), fixed for all its stages: from the
             // wave-speed bound of u^n, a prescribed dt, and the retry factor
             const double sn = a.ctl->sn;
-            const double dtd = (a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / sn) * a.ctl->dt_scale;
+            double dtc = a.ctl->dt_num / sn;
+            if (a.ctl->dt_diff > 0.0 && a.ctl->dt_diff < dtc) dtc = a.ctl->dt_diff;
+            const double dtd = (a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : dtc) * a.ctl->dt_scale;
             dt = T(dtd);
             avc = av_coef<T>(a.ph, dtd);
             if (blockIdx.x == 0 && tid == 0) a.ctl->dt = dtd;
@@ -880,6 +918,17 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                         for (int l = 0; l < b; ++l) r[l] += P[(6 + i) * LDP + l];
                     }
                 }
+                if constexpr (DIFF) {
+                    // -(eps/|K|) int grad phi_l . grad u = -eps (4/h^2) sum_d (D_d^T D_d u)_l
+                    const T* uv = sU + c * 4 * b + v * b;
+                    T t[b];
+                    modal_grad<T, K, 0>(uv, t, T(1));
+                    modal_grad_T_acc<T, K, 0>(t, r, diff_vol);
+                    modal_grad<T, K, 1>(uv, t, T(1));
+                    modal_grad_T_acc<T, K, 1>(t, r, diff_vol);
+                    modal_grad<T, K, 2>(uv, t, T(1));
+                    modal_grad_T_acc<T, K, 2>(t, r, diff_vol);
+                }
                 if constexpr (b % 4 == 0) {
 #pragma unroll
                     for (int l = 0; l < b; l += 4) st4<T>(sR + (c * 4 + v) * b + l, r + l);
@@ -968,17 +1017,44 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                         ld4<T>(sL2 + ((c * 2 + 0) * 4 + v) * LDL + p, l0 + p);
                     }
                     // + face (side 1): -1/(4h); - face (side 0): +1/(4h)
+                    T rr[b];
                     if constexpr (b % 4 == 0) {
-                        T rr[b];
 #pragma unroll
                         for (int l = 0; l < b; l += 4) ld4<T>(R + l, rr + l);
-                        expand_acc<T, K, Dd>(l1, 1, -inv4h, rr);
-                        expand_acc<T, K, Dd>(l0, 0, inv4h, rr);
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < b; ++l) rr[l] = R[l];
+                    }
+                    expand_acc<T, K, Dd>(l1, 1, -inv4h, rr);
+                    expand_acc<T, K, Dd>(l0, 0, inv4h, rr);
+                    if constexpr (DIFF) {
+                        if (c0 + c < a.ncell) {
+                        // the variable's coefficient rows of both face neighbours
+                        T um[b], up[b];
+                        const T* srcm = a.u_in + (neighbour(c0 + c, 2 * Dd, a.N) * 4 + v) * b;
+                        const T* srcp = a.u_in + (neighbour(c0 + c, 2 * Dd + 1, a.N) * 4 + v) * b;
+                        if constexpr (b % 4 == 0) {
+#pragma unroll
+                            for (int l = 0; l < b; l += 4) {
+                                ld4<T>(srcm + l, um + l);
+                                ld4<T>(srcp + l, up + l);
+                            }
+                        } else {
+#pragma unroll
+                            for (int l = 0; l < b; ++l) {
+                                um[l] = __ldg(srcm + l);
+                                up[l] = __ldg(srcp + l);
+                            }
+                        }
+                        diffusion_faces<T, K, Dd>(a.ph, sU + c * 4 * b + v * b, um, up, rr);
+                        }
+                    }
+                    if constexpr (b % 4 == 0) {
 #pragma unroll
                         for (int l = 0; l < b; l += 4) st4<T>(R + l, rr + l);
                     } else {
-                        expand_acc<T, K, Dd>(l1, 1, -inv4h, R);
-                        expand_acc<T, K, Dd>(l0, 0, inv4h, R);
+#pragma unroll
+                        for (int l = 0; l < b; ++l) R[l] = rr[l];
                     }
                 }
                 // no barrier: the next direction's collapse writes the other face

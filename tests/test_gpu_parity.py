@@ -119,8 +119,65 @@ def test_hllc_keeps_a_steady_shear_layer():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32", "x3"])
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_rhs_parity_av_off_and_uncapped(k):
+def test_rhs_parity_diffusion(k, prec):
+    # div(eps grad u) with the recovered interface gradient (Sec. 2), on top of
+    # the forced RHS with capped viscous pressure
+    N = 5
+    u = I.random_state(N, k, seed=100 + k, v_rms=0.8)
+    cfg = O.make_cfg(N, k, eps_diff=0.02)
+    a = ahat_for(N, k)
+    dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
+    ref = O.rhs(cfg, u, a, dt)
+    s = Solver(N, k, precision=prec, diffusion=0.02)
+    got = s.rhs(u, a, dt).cpu().numpy()
+    err = rel_l2_fields(got, ref)
+    assert err.max() < {"f64": 1e-12, "f32": 1e-5, "x3": 5e-5}[prec], err
+    # the diffusion part alone, FP64
+    if prec == "f64":
+        plain = Solver(N, k, precision="f64").rhs(u, a, dt).cpu().numpy()
+        dref = O.diffusion_rhs(cfg, u)
+        assert rel_l2_fields(got - plain, dref).max() < 1e-11
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_driven_steps_parity_diffusion(prec):
+    # the diffusive time-step limit binds (eps = 0.3 at N = 5, k = 2)
+    N, k = 5, 2
+    u = I.random_state(N, k, seed=105, v_rms=0.8)
+    s = Solver(N, k, precision=prec, diffusion=0.3, riemann="hllc")
+    s.set_state(u)
+    s.set_forcing(mach=3.0, zeta=0.5, seed=6)
+    t, _ = s.step(4)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    cfg = O.make_cfg(N, k, eps_diff=0.3, riemann="hllc")
+    rc, t_ref, _, _ = O.run(cfg, ref, 4, forcing=O.Forcing(mach=3.0, zeta=0.5, seed=6))
+    assert rc == 0
+    # (FP32: the wave-speed bound comes from FP32 point values when it binds)
+    assert abs(t - t_ref) <= (1e-13 if prec == "f64" else 1e-6) * t_ref
+    assert rel_l2_fields(got, ref).max() < (1e-12 if prec == "f64" else 3e-5)
+
+
+@pytest.mark.gpu
+def test_shear_wave_viscous_decay_on_the_gpu():
+    # rho = 1, v_y = A sin(2 pi x): decays as exp(-eps (2 pi)^2 t) under
+    # div(eps grad u); 16^3 cells, k = 3, FP32
+    import math
+    N, k, A, eps = 16, 3, 0.05, 0.05
+    b = I.nmodes(k)
+    sn = I.fourier_coeffs(N, k, (1, 0, 0)).imag
+    u = np.zeros((N ** 3, 4, b))
+    u[:, 0, 0] = 1.0
+    u[:, 2, :] = A * sn
+    s = Solver(N, k, precision="f32", av="off", riemann="hllc", diffusion=eps)
+    s.set_state(u)
+    t, _ = s.step(80)
+    got = s.get_state().cpu().numpy().astype(np.float64)
+    amp = np.sum(got[:, 2, :] * sn) / np.sum(sn * sn)
+    assert abs(amp / (A * math.exp(-eps * (2 * np.pi) ** 2 * t)) - 1) < 1e-4, (amp, t)
     N = 4
     u = I.random_state(N, k, seed=40 + k)
     for av, dt in (("off", 0.0), ("vnr", 0.0)):
