@@ -47,7 +47,7 @@ def workload(args):
             "N": args.N, "k": args.k, "dof": 4 * ((args.k + 1) * (args.k + 2) * (args.k + 3) // 6) * args.N ** 3,
             "rk_stages": 3, "mach": args.mach, "cs": 1.0, "cfl": 0.3, "av": "vNR alpha=2 beta=0.2",
             "riemann": {"rusanov": "Rusanov", "hll": "HLL", "hllc": "HLLC"}[args.riemann],
-            "forcing": "OU |k|<=3 zeta=0.5 seed 0",
+            "forcing": "OU |k|<=3 zeta=0.5 seed 0", "diffusion": args.diffusion,
             "state": "synthetic k^-2 velocity (seed 102) relaxed %d driven steps" % args.relax,
             "l2": "flushed (256 MB write) before every timed step"}
 
@@ -133,7 +133,7 @@ def oracle_arm(args, steps, warmup):
     from oracle import oracle as O
     from paper_2401_06841_gb300 import inputs as I
     n = args.sample_N
-    cfg = O.make_cfg(n, args.k, rk_stages=3, riemann=args.riemann)
+    cfg = O.make_cfg(n, args.k, rk_stages=3, riemann=args.riemann, eps_diff=args.diffusion)
     u = I.turbulent_state(n, args.k, seed=102, mach=args.mach)
     fo = O.Forcing(mach=args.mach, zeta=0.5, seed=0)
     t, ahat = 0.0, None
@@ -149,6 +149,35 @@ def oracle_arm(args, steps, warmup):
     return value, wall, {"kind": "oracle", "cores": 1,
                          "sample": "%d^3 cells at k=%d, SSP-RK3, driven, %d steps (single-threaded FP64 C)"
                                    % (n, args.k, steps)}
+
+
+# ---- one process per GPU (torchrun): independent replicas, no data-path collective ----
+def rank_info():
+    """(world size, rank, local rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time per step (the job's time): all-reduce MAX."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(dof, stages, world, ms):
+    """Whole-job DOF-updates/s per stage: every rank advances its own replica
+    of dof unknowns by `stages` stages per step in ms milliseconds."""
+    return dof * stages * world / (ms * 1e-3)
+
+
+def replica_seeds(rank):
+    """(initial-state seed, forcing seed) of a rank's replica."""
+    return 102 + rank, rank
 
 
 def run_reference(args):
@@ -184,6 +213,7 @@ def main():
     ap.add_argument("--no-l1", dest="no_l1", action="store_true")
     ap.add_argument("--riemann", default="rusanov", choices=["rusanov", "hll", "hllc"])
     ap.add_argument("--train-epochs", dest="train_epochs", type=int, default=20)
+    ap.add_argument("--diffusion", type=float, default=0.0, help="eps of an added div(eps grad u)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -192,9 +222,8 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_info()
+    state_seed, force_seed = replica_seeds(rank)
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -208,9 +237,9 @@ def main():
     S = 3
     dof = 4 * b * N ** 3
     # the relaxed driven state (independent replica per rank)
-    base = Solver(N, k, precision="f32", rk_stages=S, device=dev, riemann=args.riemann)
-    base.set_state(I.turbulent_state(N, k, seed=102 + rank, mach=args.mach))
-    base.set_forcing(mach=args.mach, zeta=0.5, seed=rank)
+    base = Solver(N, k, precision="f32", rk_stages=S, device=dev, riemann=args.riemann, diffusion=args.diffusion)
+    base.set_state(I.turbulent_state(N, k, seed=state_seed, mach=args.mach))
+    base.set_forcing(mach=args.mach, zeta=0.5, seed=force_seed)
     snaps = []
     for i in range(args.relax):
         _, dtl = base.step(1)
@@ -224,7 +253,8 @@ def main():
     training = None
     if any(v.startswith("learned") for v in variants):
         # plain-sensor pairs of the relaxed snapshots -> trained weights (untimed)
-        trainer = Solver(N, k, precision="f32", av="learned", device=dev, riemann=args.riemann)
+        trainer = Solver(N, k, precision="f32", av="learned", device=dev, riemann=args.riemann,
+                         diffusion=args.diffusion)
         trainer.set_av_weights(I.mlp_init(2 * b, seed=1))
         xs, ys = [], []
         for u, dtl in snaps:
@@ -248,7 +278,7 @@ def main():
     def make(v):
         prec = v.split("-")[-1]
         s = Solver(N, k, precision=prec, rk_stages=S, av="learned" if v.startswith("learned") else "vnr", device=dev,
-                   riemann=args.riemann)
+                   riemann=args.riemann, diffusion=args.diffusion)
         if weights is not None and v.startswith("learned"):
             s.set_av_weights(weights)
         return s
@@ -259,7 +289,7 @@ def main():
     time.sleep(0.2)
     for v in variants:
         s = make(v)
-        s.set_forcing(mach=args.mach, zeta=0.5, seed=rank)
+        s.set_forcing(mach=args.mach, zeta=0.5, seed=force_seed)
         s.set_state(S0)
         s.set_meta(meta0)
         stream = s.stream
@@ -286,18 +316,16 @@ def main():
         prof = s.profile_read()
         s.profile(False)
         ms = sum(a.elapsed_time(e) for a, e in zip(starts, ends)) / args.steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        res[v] = {"value": dof * S * world / (ms * 1e-3), "ms_per_step": ms, "prof": prof, "solver": s}
+        ms = max_over_ranks(ms, world, dev)
+        res[v] = {"value": job_value(dof, S, world, ms), "ms_per_step": ms, "prof": prof, "solver": s}
     clk = clocks.stop()
 
     # ---- fixed L1: undriven decay from the relaxed state, fixed dt ----
     if not args.no_l1:
         dt0 = 0.3 * (1.0 / N) / ((k + 1) * base.diagnostics()["max_speed"])
         dt = 0.8 * dt0
-        fine = Solver(2 * N, k, precision="f32", rk_stages=S, device=dev, riemann=args.riemann)
+        fine = Solver(2 * N, k, precision="f32", rk_stages=S, device=dev, riemann=args.riemann,
+                      diffusion=args.diffusion)
         fine.set_state(Tr.prolong(S0, N, k))
         fine.step(2 * args.l1_steps, fixed_dt=dt / 2)
         ref = Tr.restrict(fine.get_state(), N, k).contiguous()
@@ -336,7 +364,7 @@ def main():
             "kernel_ms": rhs_ms, "bytes_per_launch": bytes_per_launch}
 
     # end to end through the C ABI with pinned host buffers: H2D state, one step, D2H state
-    hs.set_forcing(mach=args.mach, zeta=0.5, seed=rank)
+    hs.set_forcing(mach=args.mach, zeta=0.5, seed=force_seed)
     hs.set_state(S0)
     host_in = S0.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -349,7 +377,7 @@ def main():
         hs.L.dg_get_state(hs.h, host_out.data_ptr(), 1)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_ms.sort()
-    e2e_v = dof * S * world / (e2e_ms[len(e2e_ms) // 2] * 1e-3)
+    e2e_v = job_value(dof, S, world, max_over_ranks(e2e_ms[len(e2e_ms) // 2], world, dev))
     nbytes = host_in.numel() * host_in.element_size()
 
     line = {"metric": METRIC, "value": res[head]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
