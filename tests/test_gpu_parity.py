@@ -273,6 +273,45 @@ def test_carried_projection_matches_fresh(rk):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 3])
+def test_tiny_periodic_meshes(N, k, prec):
+    # N = 1: every face neighbour is the cell itself; N = 2: both neighbours
+    # along an axis are the same cell; tiles hold more slots than cells
+    u = I.random_state(N, k, seed=110 + N + k, v_rms=0.6)
+    cfg = O.make_cfg(N, k, riemann="hllc", eps_diff=0.01)
+    a = ahat_for(N, k)
+    dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
+    s = Solver(N, k, precision=prec, riemann="hllc", diffusion=0.01)
+    got = s.rhs(u, a, dt).cpu().numpy()
+    assert rel_l2_fields(got, O.rhs(cfg, u, a, dt)).max() < TOL[prec]
+    s.set_state(u)
+    s.set_forcing(mach=1.0, zeta=0.5, seed=9)
+    s.step(2)
+    ref = u.copy()
+    rc, _, _, _ = O.run(cfg, ref, 2, forcing=O.Forcing(mach=1.0, zeta=0.5, seed=9))
+    assert rc == 0
+    assert rel_l2_fields(s.get_state().cpu().numpy(), ref).max() < (1e-12 if prec == "f64" else 3e-5)
+
+
+@pytest.mark.gpu
+def test_invalid_arguments_are_rejected():
+    from paper_2401_06841_gb300 import _lib as B
+    for kw in (dict(N=0, k=2), dict(N=4, k=4), dict(N=4, k=2, diffusion=-1.0), dict(N=4, k=2, cfl=0.0),
+               dict(N=4, k=2, rk_stages=4), dict(N=4, k=2, nu_gate=-0.5)):
+        with pytest.raises(B.DGError):
+            Solver(**kw)
+    s = Solver(4, 2)
+    with pytest.raises(B.DGError):
+        s.step(1)  # no state set
+    with pytest.raises(B.DGError):
+        s.density_pdf(0.0, -1.0, 10)  # empty bin range
+    with pytest.raises(B.DGError):
+        s.structure_function(nbins=0)
+
+
+@pytest.mark.gpu
 def test_limiter_parity():
     # states whose density dips below the floor: both sides rescale the same cells
     N, k = 4, 2
