@@ -533,7 +533,7 @@ static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, dou
 /* higher-order weights of all variables are scaled by                       */
 /*   theta = (rho_mean - eps) / (rho_mean - rho_min);                         */
 /* a mean at or below the floor is a failure (the step is retried with a     */
-/* smaller dt by the driver).                                                 */
+/* smaller dt by the time-step loop).                                        */
 /* ------------------------------------------------------------------------ */
 int orc_limit(const orc_cfg* cfg, double* u)
 {

@@ -23,7 +23,7 @@ def lib():
     return C.CDLL(build.OUT)
 
 
-def test_header_declares_the_north_star_entry_points():
+def test_header_declares_the_core_entry_points():
     names = declared_functions()
     for n in ("dg_init", "dg_rhs", "dg_step", "dg_set_forcing", "dg_diagnostics"):
         assert n in names
