@@ -285,14 +285,15 @@ constexpr int pick_tm(int M, int N, int NT)
     return 1;
 }
 
-template <typename T, int M, int N, int KK, int LDA, int LDB, int LDC, int NT>
+// WL: the product of one warp alone (NT = 32, its own rows), no block-wide split
+template <typename T, int M, int N, int KK, int LDA, int LDB, int LDC, int NT, bool WL = false>
 __device__ __forceinline__ void gemm_fma(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Cm)
 {
     constexpr int TN = pick_tn(N), TM = pick_tm(M, N, NT);
     constexpr int MT = M / TM, NCOL = N / TN;
     static_assert(M % TM == 0 && N % TN == 0 && KK % 4 == 0, "gemm shape");
     static_assert(LDA % 4 == 0 && LDB % 4 == 0 && LDC % 4 == 0, "gemm strides");
-    for (int t = threadIdx.x; t < MT * NCOL; t += NT) {
+    for (int t = WL ? (threadIdx.x & 31) : threadIdx.x; t < MT * NCOL; t += NT) {
         const int mt = t / NCOL, nt = t % NCOL;
         T acc[TM][TN];
 #pragma unroll
@@ -349,13 +350,14 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int M, int N, int KK, int LDA, int LDC, int NT>
+template <int M, int N, int KK, int LDA, int LDC, int NT, bool WL = false>
 __device__ __forceinline__ void gemm_x3(const float* __restrict__ A, const uint4* __restrict__ Bf,
                                         float* __restrict__ Cm)
 {
     constexpr int MT = M / 16, NTL = N / 8, KT = KK / 16, NW = NT / 32;
     static_assert(M % 16 == 0 && N % 8 == 0 && KK % 16 == 0 && LDA % 2 == 0 && LDC % 2 == 0, "x3 shape");
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    static_assert(!WL || NT == 32, "a warp-local product runs on one warp");
+    const int warp = WL ? 0 : (int)(threadIdx.x >> 5), lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     for (int mt = warp; mt < MT; mt += NW) {
         float acc[NTL][4];
 #pragma unroll
@@ -391,14 +393,14 @@ __device__ __forceinline__ void gemm_x3(const float* __restrict__ A, const uint4
 
 // C[M][N] = A[M][KK] B[KK][N] with the backend of the tile configuration;
 // B is the table at shared-memory offset OFF
-template <typename T, int BK, int M, int N, int KK, int LDA, int LDC, int NT>
+template <typename T, int BK, int M, int N, int KK, int LDA, int LDC, int NT, bool WL = false>
 __device__ __forceinline__ void mm(const T* A, const T* tabs, int off, T* Cm)
 {
     if constexpr (BK == BK_X3) {
-        gemm_x3<M, N, KK, LDA, LDC, NT>(reinterpret_cast<const float*>(A),
-                                        reinterpret_cast<const uint4*>(tabs + off), reinterpret_cast<float*>(Cm));
+        gemm_x3<M, N, KK, LDA, LDC, NT, WL>(reinterpret_cast<const float*>(A),
+                                            reinterpret_cast<const uint4*>(tabs + off), reinterpret_cast<float*>(Cm));
     } else {
-        gemm_fma<T, M, N, KK, LDA, N, LDC, NT>(A, tabs + off, Cm);
+        gemm_fma<T, M, N, KK, LDA, N, LDC, NT, WL>(A, tabs + off, Cm);
     }
 }
 
@@ -854,17 +856,21 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             // ---- projection of the flux tensor and the forcing density ----
             mm<T, BK, RP, NP, NQP, LDV, LDP, NT>(sBig, tabs, C::oWPhi, sP);
             __syncthreads();
-            // ---- neighbour coefficients of the face rows, fetched one face
-            // direction ahead so that their latency overlaps the work of the
-            // previous phase (rows r = tid + j NT; only "neighbour" rows load) ----
-            constexpr int NR = RC / NT;
-            static_assert(RC % NT == 0, "face rows per thread");
+            // ---- the face phase is warp-local: warp w owns the cells
+            // [w CPW, (w+1) CPW) of the tile, their RCW face rows r = w RCW + rl
+            // (rl = lane + 32 j) and their flux rows, so its steps need no
+            // block barrier; the neighbour coefficients of the face rows are
+            // fetched one face direction ahead, overlapping the previous phase ----
+            constexpr int NW = NT / 32, CPW = TC / NW, RCW = CPW * 16, RLW = CPW * 8, NR = RCW / 32;
+            static_assert(TC % NW == 0 && RCW % 32 == 0, "face rows per warp");
+            static_assert(RLW * LDT <= RCW * LDC2 && RLW * LDL <= RCW * LDT, "warp flux rows fit the row blocks");
+            const int wid = tid >> 5, lane = tid & 31;
             T nbr[NR][b];
             auto load_nbr = [&](auto dd) {
                 constexpr int Dd = decltype(dd)::value;
 #pragma unroll
                 for (int j = 0; j < NR; ++j) {
-                    const int r = tid + j * NT;
+                    const int r = wid * RCW + lane + 32 * j;
                     const int field = r & 3, who = (r >> 2) & 1, side = (r >> 3) & 1, c = r >> 4;
                     const long cc = c0 + c;
                     if (who == 1 && cc < a.ncell) {
@@ -935,13 +941,15 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     for (int l = 0; l < b; ++l) sR[(c * 4 + v) * b + l] = r[l];
                 }
             }
-            // (no barrier: the face collapse below touches other buffers; the
-            // barrier after it orders these writes before the face lift)
+            // the face lifts below add to these rows from other threads
+            __syncthreads();
             // ---- faces, one direction at a time (Sec. 3.2 face states, Rusanov) ----
-            T* sC2 = sBig + C::oC2;
-            T* sTr = sBig + C::oTr;
-            T* sFs = sBig + C::oFs;
-            T* sL2 = sBig + C::oL2;
+            // per warp: collapsed rows and (later) the face fluxes in one block,
+            // traces and (later) the lifted fluxes in another
+            T* sC2 = sBig + C::oC2 + wid * RCW * LDC2;
+            T* sTr = sBig + C::oTr + wid * RCW * LDT;
+            T* sFs = sC2;
+            T* sL2 = sTr;
             static_for<0, 3>([&](auto dd) {
                 constexpr int Dd = decltype(dd)::value;
                 // this direction's neighbour rows; start the next direction's loads
@@ -951,10 +959,10 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
 #pragma unroll
                     for (int l = 0; l < b; ++l) cur[j][l] = nbr[j][l];
                 if constexpr (Dd < 2) load_nbr(std::integral_constant<int, Dd + 1>{});
-                // collapse rows r = ((c*2 + side)*2 + who)*4 + field
+                // collapse rows r = ((c*2 + side)*2 + who)*4 + field (warp-local rl)
 #pragma unroll
                 for (int j = 0; j < NR; ++j) {
-                    const int r = tid + j * NT;
+                    const int rl = lane + 32 * j, r = wid * RCW + rl;
                     const int field = r & 3, who = (r >> 2) & 1, side = (r >> 3) & 1, c = r >> 4;
                     T cf[b];
                     int fside = side;
@@ -976,14 +984,14 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     collapse<T, K, Dd, B2K>(cf, fside, c2);
                     static_assert(B2K % 4 == 0 && LDC2 % 4 == 0, "row vectors");
 #pragma unroll
-                    for (int p = 0; p < B2K; p += 4) st4<T>(sC2 + r * LDC2 + p, c2 + p);
+                    for (int p = 0; p < B2K; p += 4) st4<T>(sC2 + rl * LDC2 + p, c2 + p);
                 }
-                __syncthreads();
-                mm<T, BK, RC, NSP, B2K, LDC2, LDT, NT>(sC2, tabs, C::oPsi, sTr);
-                __syncthreads();
-                // Rusanov at every face point; F* along +e_d with L = lower cell
-                for (int e = tid; e < TC * 2 * NSP; e += NT) {
-                    const int s = e % NSP, side = (e / NSP) & 1, c = e / (2 * NSP);
+                __syncwarp();
+                mm<T, BK, RCW, NSP, B2K, LDC2, LDT, 32, true>(sC2, tabs, C::oPsi, sTr);
+                __syncwarp();
+                // Riemann flux at every face point; F* along +e_d with L = lower cell
+                for (int e = lane; e < CPW * 2 * NSP; e += 32) {
+                    const int s = e % NSP, side = (e / NSP) & 1, c = e / (2 * NSP);  // c: the warp's cell
                     T F[4] = {T(0), T(0), T(0), T(0)};
                     if (s < ns) {
                         const int rs = ((c * 2 + side) * 2 + 0) * 4, rn = ((c * 2 + side) * 2 + 1) * 4;
@@ -1001,18 +1009,18 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) sFs[((c * 2 + side) * 4 + v) * LDT + s] = F[v];
                 }
-                __syncthreads();
-                mm<T, BK, RL, B2N, NSP, LDT, LDL, NT>(sFs, tabs, C::oPsiL, sL2);
-                __syncthreads();
-                for (int e = tid; e < TC * 4; e += NT) {
-                    const int c = e / 4, v = e % 4;
+                __syncwarp();
+                mm<T, BK, RLW, B2N, NSP, LDT, LDL, 32, true>(sFs, tabs, C::oPsiL, sL2);
+                __syncwarp();
+                for (int e = lane; e < CPW * 4; e += 32) {
+                    const int c = wid * CPW + e / 4, cl = e / 4, v = e % 4;
                     T* R = sR + (c * 4 + v) * b;
                     static_assert(LDL % 4 == 0 && B2N % 4 == 0, "row vectors");
                     T l1[B2N], l0[B2N];
 #pragma unroll
                     for (int p = 0; p < B2N; p += 4) {
-                        ld4<T>(sL2 + ((c * 2 + 1) * 4 + v) * LDL + p, l1 + p);
-                        ld4<T>(sL2 + ((c * 2 + 0) * 4 + v) * LDL + p, l0 + p);
+                        ld4<T>(sL2 + ((cl * 2 + 1) * 4 + v) * LDL + p, l1 + p);
+                        ld4<T>(sL2 + ((cl * 2 + 0) * 4 + v) * LDL + p, l0 + p);
                     }
                     // + face (side 1): -1/(4h); - face (side 0): +1/(4h)
                     T rr[b];
@@ -1055,10 +1063,8 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                         for (int l = 0; l < b; ++l) R[l] = rr[l];
                     }
                 }
-                // no barrier: the next direction's collapse writes the other face
-                // region, and the barrier after it orders this lift before the
-                // next trace product overwrites the lifted fluxes; both epilogues
-                // start with a barrier
+                // the next direction's collapse rewrites this warp's flux rows
+                __syncwarp();
             });
             // ---- epilogue ----
             if constexpr (MODE == TM_RHS) {
