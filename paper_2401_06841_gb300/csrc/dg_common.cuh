@@ -291,23 +291,6 @@ __device__ __forceinline__ void riemann_flux(int solver, T cs, T cs2, const T WL
         rusanov<T, D>(cs, cs2, WL, WR, F);
 }
 
-// ordered integer keys so that atomicMin/Max work on floating-point values
-__device__ __forceinline__ int float_key(float f)
-{
-    int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7fffffff;
-}
-__device__ __forceinline__ float key_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
-__device__ __forceinline__ long long double_key(double f)
-{
-    long long i = __double_as_longlong(f);
-    return i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
-}
-__device__ __forceinline__ double key_double(long long i)
-{
-    return __longlong_as_double(i >= 0 ? i : i ^ 0x7fffffffffffffffLL);
-}
-
 // ---------------------------------------------------------------------------
 // table layout (element type T) in the caller's scratch, per degree
 // ---------------------------------------------------------------------------

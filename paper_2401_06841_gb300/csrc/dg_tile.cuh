@@ -633,9 +633,6 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     T* sP = sm + C::oP;
     T* sBig = sm + C::oBig;
     __shared__ T s_nu[TC];
-    __shared__ int s_flag[TC];
-    __shared__ float s_minf[TC];
-    __shared__ double s_mind[TC];
     __shared__ unsigned int s_status;
     __shared__ double s_tot[8];
     // block reductions after the tile loop use the (then free) big region
@@ -644,6 +641,11 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     __shared__ unsigned long long s_smax;
 
     const int tid = threadIdx.x;
+    // sup |phi_m| of the mode m = lane (positivity bound), 0 past the modes
+    T my_sup = T(0);
+    static_for<0, b>([&](auto m) {
+        if ((int)(tid & 31) == decltype(m)::value) my_sup = T(sup_phi<K>(decltype(m)::value));
+    });
     // tables -> shared (once per block)
     for (int e = tid; e < C::smem_tabs; e += NT) sm[e] = a.tab[e];
     const T* tabs = sm;
@@ -1074,9 +1076,12 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 }
                 __syncthreads();
             } else {
-                // SSP-RK stage combine (Sec. 7), new state kept in sU; u^n was prefetched
-                __syncthreads();
-                for (int e = tid; e < TC * 4 * b; e += NT) {
+                // SSP-RK stage combine (Sec. 7), new state kept in sU; u^n was prefetched.
+                // Warp-local like the face phase: the warp's own cells, whose
+                // right-hand-side rows it has just finished (no block barrier)
+                const int e0 = wid * CPW * 4 * b;
+                for (int el = lane; el < CPW * 4 * b; el += 32) {
+                    const int e = e0 + el;
                     T w;
                     if (e / (4 * b) < nvalid) {
                         const T un = (a.rk_a != T(0)) ? sUn[e] : T(0);
@@ -1086,88 +1091,69 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     }
                     sU[e] = w;
                 }
-                __syncthreads();
+                __syncwarp();
                 // positivity (Sec. 3.1): a cell passes when rho_0 - sum_l |rho_l| sup|phi_l| >= eps;
-                // otherwise rho is evaluated at every volume and face Gauss point
+                // otherwise rho is evaluated at every volume and face Gauss point (lanes
+                // over modes for the bound, over points for the check; warp reductions)
                 const T eps = T(a.ph.floor_);
-                if (tid < TC) {
-                    const T* r = sU + tid * 4 * b;
-                    T bound = T(0);
-                    static_for<1, b>([&](auto m) {
-                        constexpr double sp = sup_phi<K>(decltype(m)::value);
-                        bound += fabs(r[decltype(m)::value]) * T(sp);
-                    });
-                    s_flag[tid] = (r[0] - bound < eps) ? 1 : 0;
-                    s_minf[tid] = 3.0e38f;
-                    s_mind[tid] = 1.0e300;
-                }
-                __syncthreads();
-                {
-                    constexpr int G = NT / TC;
-                    const int c = tid / G, g = tid % G;
-                    if (c < TC && s_flag[c]) {
-                        const T* r = sU + c * 4 * b;
+                T thr[CPW];  // rescaling factor of the modes l > 0 per cell (1: none)
+                unsigned int st = 0u;
+#pragma unroll
+                for (int cl = 0; cl < CPW; ++cl) {
+                    const int c = wid * CPW + cl;
+                    const T* r = sU + c * 4 * b;
+                    T part = (lane >= 1 && lane < b) ? fabs(r[lane < b ? lane : 0]) * my_sup : T(0);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    thr[cl] = T(1);
+                    if (r[0] - part < eps) {
                         const T* phiv = a.tab + TT::phiv;
                         const T* phif = a.tab + TT::phif;
                         T mn = T(1e30);
-                        for (int p = g; p < nq + nf; p += G) {
+                        for (int pt = lane; pt < nq + nf; pt += 32) {
                             T rho = T(0);
-                            if (p < nq) {
+                            if (pt < nq) {
 #pragma unroll
-                                for (int l = 0; l < b; ++l) rho += r[l] * __ldg(phiv + l * nq + p);
+                                for (int l = 0; l < b; ++l) rho += r[l] * __ldg(phiv + l * nq + pt);
                             } else {
 #pragma unroll
-                                for (int l = 0; l < b; ++l) rho += r[l] * __ldg(phif + l * nf + (p - nq));
+                                for (int l = 0; l < b; ++l) rho += r[l] * __ldg(phif + l * nf + (pt - nq));
                             }
                             mn = rho < mn ? rho : mn;
                         }
-                        if constexpr (sizeof(T) == 4)
-                            atomicMin(reinterpret_cast<int*>(&s_minf[c]), float_key((float)mn));
-                        else
-                            atomicMin(reinterpret_cast<long long*>(&s_mind[c]), double_key((double)mn));
-                    }
-                }
-                __syncthreads();
-                unsigned int st = 0u;
-                for (int e = tid; e < TC * 4 * b; e += NT) {
-                    const int c = e / (4 * b), l = e % b;
-                    T w = sU[e];
-                    if (s_flag[c]) {
-                        T rmin;
-                        if constexpr (sizeof(T) == 4)
-                            rmin = (T)key_float(*reinterpret_cast<int*>(&s_minf[c]));
-                        else
-                            rmin = (T)key_double(*reinterpret_cast<long long*>(&s_mind[c]));
-                        const T rbar = sU[c * 4 * b];
-                        if (rmin < eps) {
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const T other = __shfl_xor_sync(0xffffffffu, mn, o);
+                            mn = other < mn ? other : mn;
+                        }
+                        const T rbar = r[0];
+                        if (mn < eps) {
                             if (rbar > eps) {
-                                if (l > 0) w *= (rbar - eps) / (rbar - rmin);
+                                thr[cl] = (rbar - eps) / (rbar - mn);
                                 st |= DG_ST_LIMITED_;
                             } else {
                                 st |= DG_ST_FAIL_;
                             }
                         }
                     }
-                    if (c < nvalid) {
+                }
+                // rescale, store u^(s+1), keep the limited state for the fused projection
+                for (int el = lane; el < CPW * 4 * b; el += 32) {
+                    const int e = e0 + el, cl = el / (4 * b), l = e % b;
+                    T w = sU[e];
+                    T th = T(1);
+#pragma unroll
+                    for (int j = 0; j < CPW; ++j)
+                        if (j == cl) th = thr[j];
+                    if (l > 0) w *= th;
+                    sU[e] = w;
+                    if (e / (4 * b) < nvalid) {
                         if (!isfinite(w)) st |= DG_ST_NONFINITE_;
                         a.out[c0 * 4 * b + e] = w;
                     }
                 }
-                __syncthreads();
-                // the limited state is the input of the fused projection
-                for (int e = tid; e < TC * 4 * b; e += NT) {
-                    const int c = e / (4 * b), l = e % b;
-                    if (s_flag[c] && l > 0) {
-                        const T rbar = sU[c * 4 * b];
-                        T rmin;
-                        if constexpr (sizeof(T) == 4)
-                            rmin = (T)key_float(*reinterpret_cast<int*>(&s_minf[c]));
-                        else
-                            rmin = (T)key_double(*reinterpret_cast<long long*>(&s_mind[c]));
-                        if (rmin < eps && rbar > eps) sU[e] *= (rbar - eps) / (rbar - rmin);
-                    }
-                }
-                if (st) atomicOr(&s_status, st);
+                st = __reduce_or_sync(0xffffffffu, st);
+                if (lane == 0 && st) atomicOr(&s_status, st);
                 __syncthreads();
                 if (do_proj && force) {
                     forcing_sums<T, K, BK>(sm, sU, a, c0, sums);
