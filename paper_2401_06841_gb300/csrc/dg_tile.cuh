@@ -1169,7 +1169,8 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             }
         }
     }
-    // ---- block-level reductions ----
+    // ---- block-level reductions (their buffer is the big region) ----
+    __syncthreads();
     if constexpr (STAGE) {
         if (tid == 0 && s_status) atomicOr(&a.ctl->status, s_status);
     }

@@ -312,6 +312,26 @@ def test_invalid_arguments_are_rejected():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 3e-5), ("x3", 1e-4)])
+def test_multi_tile_driven_steps(prec, tol):
+    # 20^3 cells at k = 3: 500 tiles of 16 cells, more than the grid holds, so
+    # every block runs several tiles (the next tile's inputs prefetched during
+    # the fused projection, the state buffer refilled, the last tile's
+    # projection finished before the block's reductions)
+    N, k = 20, 3
+    u = I.random_state(N, k, seed=120, v_rms=0.8)
+    s = Solver(N, k, precision=prec)
+    s.set_state(u)
+    s.set_forcing(mach=3.0, zeta=0.5, seed=12)
+    s.step(2)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, _, _, _ = O.run(O.make_cfg(N, k), ref, 2, forcing=O.Forcing(mach=3.0, zeta=0.5, seed=12))
+    assert rc == 0
+    assert rel_l2_fields(got, ref).max() < tol
+
+
+@pytest.mark.gpu
 def test_limiter_parity():
     # states whose density dips below the floor: both sides rescale the same cells
     N, k = 4, 2
