@@ -1154,18 +1154,29 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 }
                 st = __reduce_or_sync(0xffffffffu, st);
                 if (lane == 0 && st) atomicOr(&s_status, st);
-                __syncthreads();
                 if (do_proj && force) {
-                    forcing_sums<T, K, BK>(sm, sU, a, c0, sums);
-                    __syncthreads();
+                    // per-cell forcing sums <rho a_h>, <rho> of the warp's cells (lane = (cell, i))
+                    __syncwarp();
+                    if (lane < CPW * 3) {
+                        const int c = wid * CPW + lane / 3, i = lane % 3;
+                        if (c < nvalid) {
+                            const T* u = sU + c * 4 * b;
+                            const T* ah = sAh + (c * 3 + i) * b;
+                            T sacc = T(0);
+#pragma unroll
+                            for (int l = 0; l < b; ++l) sacc += u[l] * ah[l];
+                            sums[i] += (double)sacc;
+                            if (i == 0) sums[3] += (double)u[0];
+                        }
+                    }
                 }
-                // the staging buffers of this tile are free: fetch the next tile
+                // every warp is done with this tile's staging buffers: fetch the next
+                // tile (the next iteration starts with a barrier after the projection)
+                __syncthreads();
                 if (tile + gridDim.x < ntile) issue(tile + gridDim.x, sR);
-                if (do_proj) {
+                if (do_proj)
                     tile_project<T, K, BK, MODE == TM_STAGE_VABS>(sm, sU, tabs, a, c0, (a.flags & F_DT) != 0, smax,
                                                                  sums, false);
-                    __syncthreads();
-                }
             }
         }
     }
