@@ -122,7 +122,7 @@ def profiled_traffic(args, variant):
     if not (m_t and m_h):
         return None
     h = hashlib.sha1()
-    for name in ("dg_tile.cuh", "dg_common.cuh", "dg_launch_impl.cuh"):
+    for name in ("dg_tile.cuh", "dg_mma.cuh", "dg_common.cuh", "dg_launch_impl.cuh"):
         with open(os.path.join(ROOT, "paper_2401_06841_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return int(m_t.group(1)) if h.hexdigest() == m_h.group(1) else None

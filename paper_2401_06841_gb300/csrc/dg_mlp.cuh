@@ -17,7 +17,6 @@
 
 namespace dg {
 
-constexpr int MLP_H = 64;
 constexpr int MLP_BMAX = 4096;  // largest training batch
 
 struct MlpLayout {
@@ -41,7 +40,6 @@ struct MlpLayout {
 enum { MW_Z1 = 0, MW_A1 = 1, MW_Z2 = 2, MW_A2 = 3, MW_DZ1 = 4, MW_DZ2 = 5, MW_R = 6 };
 constexpr size_t mlp_work_floats() { return (size_t)6 * MLP_H * MLP_BMAX + MLP_BMAX; }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_prime_f(float z)
 {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
@@ -175,22 +173,6 @@ static __global__ void k_mlp_adam(float* __restrict__ W, const float* __restrict
 // packed weights: B1 = W1^T [KD][64], B2 = W2^T [64][64], B3 = W3 as [64][8]
 // (column 0), each as fragments [K/16][N/8][32 lanes][2 words], then b1, b2, b3
 // ---------------------------------------------------------------------------
-template <int D>
-struct MlpPack {
-    static constexpr int KD = r16(D);
-    static constexpr int w1 = 0;                              // words
-    static constexpr int w2 = w1 + (KD / 16) * 8 * 64;
-    static constexpr int w3 = w2 + 4 * 8 * 64;
-    static constexpr int bias = w3 + 4 * 1 * 64;              // floats b1[64], b2[64], b3
-    static constexpr int words = bias + 2 * MLP_H + 1;
-};
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
-
 // x(r, k): FROMSTATE reads the cell's state (rho_l/rho_0) and |v|hat/cs,
 // otherwise an explicit feature matrix X [n][D]
 template <typename T, int K, bool FROMSTATE>
@@ -201,99 +183,27 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const T* __restrict__ u, cons
 {
     constexpr int b = Dims<K>::b, D = 2 * b;
     using PK = MlpPack<D>;
-    constexpr int KT1 = PK::KD / 16;
     __shared__ uint32_t sP[PK::words];
     for (int e = threadIdx.x; e < PK::words; e += blockDim.x) sP[e] = packed[e];
     __syncthreads();
-    const uint2* B1 = reinterpret_cast<const uint2*>(sP + PK::w1);
-    const uint2* B2 = reinterpret_cast<const uint2*>(sP + PK::w2);
-    const uint2* B3 = reinterpret_cast<const uint2*>(sP + PK::w3);
-    const float* bias = reinterpret_cast<const float*>(sP + PK::bias);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float inv_cs = 1.0f / cs;
-    auto feat = [&](long r, int k) -> float {
-        if (r >= n || k >= D) return 0.0f;
-        if constexpr (FROMSTATE) {
-            if (k < b) return (float)(u[r * 4 * b + k] / u[r * 4 * b]);
-            return (float)vabs[r * b + (k - b)] * inv_cs;
-        } else {
-            return X[r * D + k];
-        }
-    };
     const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
     for (long base = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * 16; base < n; base += nwarps * 16) {
+        auto feat = [&](int rl, int k) -> float {
+            const long r = base + rl;
+            if (r >= n || k >= D) return 0.0f;
+            if constexpr (FROMSTATE) {
+                if (k < b) return (float)(u[r * 4 * b + k] / u[r * 4 * b]);
+                return (float)vabs[r * b + (k - b)] * inv_cs;
+            } else {
+                return X[r * D + k];
+            }
+        };
+        float y0, y1;
+        mlp_infer_warp<D>(feat, sP, y0, y1);
         const long r0 = base + g, r1 = base + g + 8;
-        float acc1[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc1[j][0] = acc1[j][1] = acc1[j][2] = acc1[j][3] = 0.f;
-#pragma unroll
-        for (int kt = 0; kt < KT1; ++kt) {
-            const int k0 = kt * 16 + 2 * t;
-            uint32_t A[4];
-            A[0] = pack_bf16x2(feat(r0, k0), feat(r0, k0 + 1));
-            A[1] = pack_bf16x2(feat(r1, k0), feat(r1, k0 + 1));
-            A[2] = pack_bf16x2(feat(r0, k0 + 8), feat(r0, k0 + 9));
-            A[3] = pack_bf16x2(feat(r1, k0 + 8), feat(r1, k0 + 9));
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const uint2 bw = B1[(kt * 8 + nt) * 32 + lane];
-                mma_bf16(acc1[nt], A, bw.x, bw.y);
-            }
-        }
-        // bias + GELU; the m16n8 accumulator tiles 2j, 2j+1 form the A operand of k-chunk j
-        uint32_t A2[4][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float h[2][4];
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int nt = 2 * j + s, c = nt * 8 + 2 * t;
-                h[s][0] = gelu_f(acc1[nt][0] + bias[c]);
-                h[s][1] = gelu_f(acc1[nt][1] + bias[c + 1]);
-                h[s][2] = gelu_f(acc1[nt][2] + bias[c]);
-                h[s][3] = gelu_f(acc1[nt][3] + bias[c + 1]);
-            }
-            A2[j][0] = pack_bf16x2(h[0][0], h[0][1]);
-            A2[j][1] = pack_bf16x2(h[0][2], h[0][3]);
-            A2[j][2] = pack_bf16x2(h[1][0], h[1][1]);
-            A2[j][3] = pack_bf16x2(h[1][2], h[1][3]);
-        }
-        float acc2[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt)
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const uint2 bw = B2[(kt * 8 + nt) * 32 + lane];
-                mma_bf16(acc2[nt], A2[kt], bw.x, bw.y);
-            }
-        uint32_t A3[4][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float h[2][4];
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int nt = 2 * j + s, c = MLP_H + nt * 8 + 2 * t;
-                h[s][0] = gelu_f(acc2[nt][0] + bias[c]);
-                h[s][1] = gelu_f(acc2[nt][1] + bias[c + 1]);
-                h[s][2] = gelu_f(acc2[nt][2] + bias[c]);
-                h[s][3] = gelu_f(acc2[nt][3] + bias[c + 1]);
-            }
-            A3[j][0] = pack_bf16x2(h[0][0], h[0][1]);
-            A3[j][1] = pack_bf16x2(h[0][2], h[0][3]);
-            A3[j][2] = pack_bf16x2(h[1][0], h[1][1]);
-            A3[j][3] = pack_bf16x2(h[1][2], h[1][3]);
-        }
-        float acc3[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            const uint2 bw = B3[kt * 32 + lane];
-            mma_bf16(acc3, A3[kt], bw.x, bw.y);
-        }
         if (t == 0) {
-            const float b3 = bias[2 * MLP_H];
-            const float y0 = acc3[0] + b3, y1 = acc3[2] + b3;
             if (r0 < n) {
                 if (nu_out) nu_out[r0] = expf(y0) < gate ? 0.f : ref * expf(y0);
                 if (y_out) y_out[r0] = y0;
