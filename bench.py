@@ -208,7 +208,9 @@ def main():
     ap.add_argument("--sample-N", dest="sample_N", type=int, default=16)
     ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=4)
     ap.add_argument("--l1-steps", dest="l1_steps", type=int, default=20)
-    ap.add_argument("--variants", default="f32,x3,learned-f32,learned-x3")
+    ap.add_argument("--variants", default="f32,x3,learned-f32,learned-x3",
+                    help="comma list of f32, x3, learned-f32, learned-x3, learned-fused-f32, learned-fused-x3 "
+                         "(fused: the sensor network evaluated in the last stage's kernel)")
     ap.add_argument("--no-cpu", dest="no_cpu", action="store_true")
     ap.add_argument("--no-l1", dest="no_l1", action="store_true")
     ap.add_argument("--riemann", default="rusanov", choices=["rusanov", "hll", "hllc"])
@@ -278,7 +280,7 @@ def main():
     def make(v):
         prec = v.split("-")[-1]
         s = Solver(N, k, precision=prec, rk_stages=S, av="learned" if v.startswith("learned") else "vnr", device=dev,
-                   riemann=args.riemann, diffusion=args.diffusion)
+                   riemann=args.riemann, diffusion=args.diffusion, fused_infer="-fused-" in v)
         if weights is not None and v.startswith("learned"):
             s.set_av_weights(weights)
         return s

@@ -96,6 +96,9 @@ typedef struct {
     double nu_gate;        /* default 0 (no gating)                                */
     double diffusion;      /* eps of an added div(eps grad u) on all four variables
                               (Sec. 2, diffusion across cell boundaries); 0: off   */
+    int32_t fused_infer;   /* DG_AV_LEARNED steps: 1 = the last stage's kernel
+                              evaluates the next step's coefficient; 0 (default) =
+                              a separate inference launch per step.  Same values. */
 } dg_nu_params;
 
 typedef struct {
@@ -233,7 +236,11 @@ int dg_l1_density(dg_ctx* ctx, const void* uA, const void* uB, double* out);
  * output y = log(nu / (cs h/p)).  In DG_AV_LEARNED mode the viscous pressure
  * at a volume point is Pi = rho nu |div v| for div v < 0, capped at
  * rho (h/p)^2 |div v| / (2 dt) as in Sec. 3.1; nu is evaluated once per step
- * (BF16 tensor-core inference, FP32 accumulation) and kept for its stages.
+ * (BF16 tensor-core inference, FP32 accumulation) and kept for its stages:
+ * by a separate inference kernel at the start of the step, or (fused_infer)
+ * by the last stage of the previous step, in the same kernel, for the state
+ * it writes.  Both give the same values bit for bit; on GB300 the separate
+ * launch is the faster of the two.
  * Parameters: FP32 array of dg_av_param_count() floats in the order
  * W1 [64][D] row-major, b1 [64], W2 [64][64], b2 [64], W3 [64], b3. */
 typedef struct {
@@ -265,8 +272,18 @@ int dg_mlp_grad(dg_ctx* ctx, const float* x, const float* y, int64_t n, float* g
 /* Network output y for explicit inputs (device x [n][2b] -> y [n]), using the
  * BF16 inference kernel of the learned mode. */
 int dg_mlp_forward(dg_ctx* ctx, const float* x, int64_t n, float* y);
-/* Per-cell coefficient nu of the current state (device float [N^3]). */
+/* Per-cell coefficient nu of the current state (device float [N^3]),
+ * evaluated by the separate inference kernel. */
 int dg_av_nu(dg_ctx* ctx, float* nu_out);
+/* The coefficient the next dg_step will use for the current state, as the
+ * previous learned step left it (device float [N^3]): evaluated by its last
+ * stage (fused_infer), else by the inference kernel from the |v| projection
+ * that the last stage carried over.
+ * DG_ESTATE when none is carried: no successful learned-mode dg_step yet, or
+ * a call since then that sets the state, the forcing, the parameters or the
+ * network, or runs dg_rhs, dg_diagnostics or the network entry points.
+ * Leaves the context unchanged. */
+int dg_av_nu_carried(dg_ctx* ctx, float* nu_out);
 
 /* Kernel timing: with profiling on, every launch of the library is bracketed
  * by CUDA events on the context's stream and its duration accumulated per

@@ -27,7 +27,7 @@ class Mesh(C.Structure):
 
 class NuParams(C.Structure):
     _fields_ = [("mode", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double), ("rho_floor", C.c_double),
-                ("nu_gate", C.c_double), ("diffusion", C.c_double)]
+                ("nu_gate", C.c_double), ("diffusion", C.c_double), ("fused_infer", C.c_int32)]
 
 
 class Opts(C.Structure):
@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
         L.dg_mlp_grad.argtypes = [vp, vp, vp, C.c_int64, vp, C.POINTER(d)]
         L.dg_mlp_forward.argtypes = [vp, vp, C.c_int64, vp]
         L.dg_av_nu.argtypes = [vp, vp]
+        L.dg_av_nu_carried.argtypes = [vp, vp]
         L.dg_rhs_noalloc.argtypes = [C.POINTER(Mesh), i, d, C.POINTER(NuParams), i, vp, vp, vp, d, vp]
         L.dg_profile.argtypes = [vp, i]
         L.dg_profile_read.argtypes = [vp, C.POINTER(Prof)]
@@ -121,7 +122,7 @@ EXPORTS = ("dg_scratch_bytes", "dg_vhat_bytes", "dg_init", "dg_free", "dg_last_e
            "dg_project_velocity", "dg_step", "dg_set_forcing", "dg_set_forcing_coeffs", "dg_forcing_from_modes",
            "dg_diagnostics", "dg_l1_density", "dg_get_meta", "dg_set_meta", "dg_profile", "dg_profile_read",
            "dg_rhs_noalloc", "dg_av_param_count", "dg_set_av_weights", "dg_get_av_weights", "dg_generate_pairs",
-           "dg_mlp_train", "dg_mlp_grad", "dg_mlp_forward", "dg_av_nu", "dg_density_pdf", "dg_structure_function",
+           "dg_mlp_train", "dg_mlp_grad", "dg_mlp_forward", "dg_av_nu", "dg_av_nu_carried", "dg_density_pdf", "dg_structure_function",
            "dg_analysis_bytes", "dg_power_spectrum")
 
 MAX_BINS = 2000

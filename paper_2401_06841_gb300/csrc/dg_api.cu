@@ -574,6 +574,7 @@ struct dg_ctx {
     double* mloss = nullptr;
     float* mwork = nullptr;
     float* nu_cell = nullptr;  // per-cell coefficient (learned mode)
+    float* nu_next = nullptr;  // the next step's coefficient, written by the last stage (learned mode)
     void* vabs = nullptr;      // per-cell |v| projection (learned mode)
     int mlp_D = 0, mlp_P = 0;
     long adam_t = 0;
@@ -603,7 +604,7 @@ namespace {
 struct ScratchLayout {
     size_t ctl, partials, tab, ttab, kvec, amp, gtab;
     size_t mw, mm, mv, mg, mpack, mloss, mwork;  // learned sensor: weights, Adam moments, grad, packed, loss, work
-    size_t nu, vabs;                             // per-cell coefficient and |v| projection (learned mode)
+    size_t nu, nu2, vabs;                        // per-cell coefficients (this and the next step) and |v| projection (learned mode)
     size_t ana;                                  // turbulence statistics: 4 x DG_MAX_BINS doubles + 1
     size_t total;
 };
@@ -647,6 +648,8 @@ ScratchLayout scratch_layout(int K, int N, bool learned = false)
     s.ana = off;
     off = align256(off + sizeof(double) * (4 * DG_MAX_BINS + 1));
     s.nu = off;
+    if (learned) off = align256(off + sizeof(float) * (size_t)ncell);
+    s.nu2 = off;
     if (learned) off = align256(off + sizeof(float) * (size_t)ncell);
     s.vabs = off;
     const size_t b = (size_t)(K + 1) * (K + 2) * (K + 3) / 6;
@@ -903,7 +906,8 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     for (int d = 0; d < 3; ++d)
         if (mesh->L[d] != 1.0) return DG_EINVAL;
     if (!(cs > 0.0)) return DG_EINVAL;
-    if (nu->mode < 0 || nu->mode > 2 || !(nu->rho_floor >= 0.0) || !(nu->nu_gate >= 0.0) || !(nu->diffusion >= 0.0))
+    if (nu->mode < 0 || nu->mode > 2 || !(nu->rho_floor >= 0.0) || !(nu->nu_gate >= 0.0) || !(nu->diffusion >= 0.0) ||
+        (nu->fused_infer != 0 && nu->fused_infer != 1))
         return DG_EINVAL;
     if (opts->precision < 0 || opts->precision > 2) return DG_EINVAL;
     if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
@@ -961,6 +965,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->mloss = (double*)(ctx->scratch + sl.mloss);
     ctx->mwork = (float*)(ctx->scratch + sl.mwork);
     ctx->nu_cell = (float*)(ctx->scratch + sl.nu);
+    ctx->nu_next = (float*)(ctx->scratch + sl.nu2);
     ctx->vabs = ctx->scratch + sl.vabs;
     ctx->mlp_D = 2 * ctx->b;
     ctx->mlp_P = mlp_params(ctx->mlp_D);
@@ -1176,6 +1181,7 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
         double dt = 0.0;
         unsigned int status = 0u;
         const bool learned = ctx->nu.mode == DG_AV_LEARNED;
+        const bool fused = learned && ctx->nu.fused_infer;
         const int pb = ctx->pb;
         for (int retry = 0; retry <= 3 && !ok; ++retry) {
             struct {
@@ -1190,16 +1196,24 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
             // (double-buffered vhat / abar slots, alternating from slot pb)
             const bool use_carry = retry == 0 && ctx->carry;
             ctx->carry = false;
-            // learned mode: the coefficient once per step, cached for all stages (the
-            // carried projection includes |v|)
-            if (learned) CK(use_carry ? learned_infer(ctx, ctx->reg[A]) : learned_nu(ctx, ctx->reg[A]));
+            // learned mode: the coefficient once per step, cached for all stages; the
+            // last stage of the previous step evaluated it for u^n (carried), else the
+            // |v| projection and the inference run here
+            if (learned) {
+                if (use_carry && fused)
+                    std::swap(ctx->nu_cell, ctx->nu_next);
+                else
+                    CK(use_carry ? learned_infer(ctx, ctx->reg[A]) : learned_nu(ctx, ctx->reg[A]));
+            }
             if (!use_carry) CK(project(ctx, ctx->reg[A], vh_buf(ctx, pb), force ? ctx->ahat : nullptr, true, pb));
             for (int s = 0; s < ctx->rk; ++s) {
                 const bool last = s + 1 == ctx->rk;
                 TileLaunch t{};
                 t.nu = learned ? ctx->nu_cell : nullptr;
                 t.mode = (learned && last) ? 3 : 2;
-                t.vabs_out = (learned && last) ? ctx->vabs : nullptr;
+                t.nu_next = (learned && last && fused) ? ctx->nu_next : nullptr;
+                t.vabs_out = (learned && last && !fused) ? ctx->vabs : nullptr;
+                t.mlp = ctx->mpack;
                 t.u_in = ctx->reg[in[s]];
                 t.u_n = ctx->reg[A];
                 t.out = ctx->reg[out[s]];
@@ -1431,6 +1445,19 @@ int dg_generate_pairs(dg_ctx* ctx, double dt_for_pimax, float* x, float* y, int6
     }
     CK(cudaStreamSynchronize(ctx->st));
     *n_out = ctx->ncell;
+    return DG_OK;
+}
+
+int dg_av_nu_carried(dg_ctx* ctx, float* nu_out)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!nu_out) return fail(ctx, DG_EINVAL, "dg_av_nu_carried: null buffer");
+    if (ctx->nu.mode != DG_AV_LEARNED || !ctx->carry)
+        return fail(ctx, DG_ESTATE, "dg_av_nu_carried: no coefficient carried from a learned step");
+    if (!ctx->nu.fused_infer) CK(learned_infer(ctx, ctx->reg[ctx->cur]));
+    const float* src = ctx->nu.fused_infer ? ctx->nu_next : ctx->nu_cell;
+    CK(cudaMemcpyAsync(nu_out, src, sizeof(float) * ctx->ncell, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
     return DG_OK;
 }
 

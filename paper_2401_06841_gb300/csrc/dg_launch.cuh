@@ -46,6 +46,8 @@ struct TileLaunch {
     int abar_in, abar_out;
     const float* nu;     // learned sensor: per-cell coefficient
     void* vabs_out;      // learned sensor: projection of |v|
+    float* nu_next;      // learned sensor: coefficient of the output, evaluated in the kernel (mode 3)
+    const uint32_t* mlp; // learned sensor: packed network for nu_next
 };
 template <typename T>
 cudaError_t launch_tile(const Launch& L, const TileLaunch& t);

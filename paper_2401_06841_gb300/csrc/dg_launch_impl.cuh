@@ -123,6 +123,8 @@ static cudaError_t tile_kb(const Launch& L, const TileLaunch& t)
     a.abar_out = t.abar_out;
     a.nu = t.nu;
     a.vabs_out = static_cast<T*>(t.vabs_out);
+    a.nu_next = t.mode == TM_STAGE_VABS ? t.nu_next : nullptr;
+    a.mlp = t.mlp;
     using Cf = TileCfg<K, BK>;
     const long ntile = (L.ncell + Cf::TC - 1) / Cf::TC;
     const size_t sm = sizeof(T) * Cf::total;

@@ -488,7 +488,9 @@ struct TArgs {
     int abar_in;       // slot of ctl->abar2 read by this stage
     int abar_out;      // slot written by the projection
     const float* nu;   // per-cell viscous coefficient (learned sensor) or nullptr
-    T* vabs_out;       // projection of |v| (F_VABS) [c][b]
+    T* vabs_out;       // projection of |v| (F_VABS) [c][b] or nullptr
+    float* nu_next;    // last stage of a learned step: the coefficient of u^(n+1), or nullptr
+    const uint32_t* mlp;  // packed sensor network (MlpPack<2b>) for nu_next
 };
 
 // viscous pressure with a per-cell coefficient (learned sensor):
@@ -595,12 +597,128 @@ __device__ __forceinline__ void tile_project(T* sm, const T* sU, const T* tabs, 
         if (c0 + c < a.ncell) a.vh_out[c0 * 3 * b + e] = sP[(c * NPR + i) * LDP + l];
     }
     if constexpr (VABS) {
-        for (int e = threadIdx.x; e < TC * b; e += NT) {
-            const int c = e / b, l = e % b;
-            if (c0 + c < a.ncell) a.vabs_out[c0 * b + e] = sP[(c * NPR + 3) * LDP + l];
+        if (a.vabs_out) {
+            for (int e = threadIdx.x; e < TC * b; e += NT) {
+                const int c = e / b, l = e % b;
+                if (c0 + c < a.ncell) a.vabs_out[c0 * b + e] = sP[(c * NPR + 3) * LDP + l];
+            }
         }
     }
     if (with_sums && (a.flags & F_FORCE)) forcing_sums<T, K, BK>(sm, sU, a, c0, sums);
+}
+
+// --------------------------------------------------------------------------
+// learned sensor for the next step, evaluated in the last stage after the
+// projection of |v| of u^(n+1): features x = (rho_l/rho_0, |v|hat_l/cs) of the
+// tile's cells, nu = cs h/p exp(net(x)), 0 below the gate.  The network is the
+// one of the separate inference kernel (BF16 inputs, weights and hidden
+// activations, FP32 accumulation), spread over the block: warp w computes the
+// hidden units 8w..8w+7 of both layers (one n-tile) for all the tile's cells,
+// the BF16 activations pass through shared memory, and the first TC/16 warps
+// form the outputs.  Products, roundings and accumulation orders are those of
+// the separate kernel, so the coefficients agree bit for bit.
+// Needs the big region free (after the projection) and sP holding the
+// projections (rows cell x (v_x, v_y, v_z, |v|)).
+// --------------------------------------------------------------------------
+template <typename T, int K, int BK>
+__device__ __forceinline__ void tile_nu(T* sm, const T* sU, const TArgs<T>& a, long c0)
+{
+    using C = TileCfg<K, BK>;
+    constexpr int b = C::b, TC = C::TC, NT = C::NT, LDP = C::LDP, D = 2 * b;
+    using PK = MlpPack<D>;
+    constexpr int XW = PK::KD / 2, KT1 = PK::KD / 16, MT = TC / 16, HW = MLP_H / 2;
+    static_assert(NT / 32 == MLP_H / 8 && TC % 16 == 0, "one warp per 8 hidden units, 16-cell row blocks");
+    static_assert((TC * XW + 2 * TC * HW) * 4 <= C::BIG * (int)sizeof(T), "network buffers in the big region");
+    uint32_t* sX = reinterpret_cast<uint32_t*>(sm + C::oBig);  // [TC][XW] BF16 pairs of features
+    uint32_t* sH1 = sX + TC * XW;                              // [TC][HW] first hidden layer
+    uint32_t* sH2 = sH1 + TC * HW;                             // [TC][HW] second hidden layer
+    const T* sP = sm + C::oP;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const float inv_cs = 1.0f / (float)a.ph.cs;
+    auto feat = [&](int c, int k) -> float {
+        if (c0 + c >= a.ncell || k >= D) return 0.0f;
+        if (k < b) return (float)(sU[c * 4 * b + k] / sU[c * 4 * b]);
+        return (float)sP[(c * 4 + 3) * LDP + (k - b)] * inv_cs;
+    };
+    for (int e = tid; e < TC * XW; e += NT) {
+        const int c = e / XW, k0 = 2 * (e % XW);
+        sX[e] = pack_bf16x2(feat(c, k0), feat(c, k0 + 1));
+    }
+    // the warp's weight fragments and biases, loaded up front (their latency
+    // overlaps the feature phase)
+    const uint2* B1 = reinterpret_cast<const uint2*>(a.mlp + PK::w1);
+    const uint2* B2 = reinterpret_cast<const uint2*>(a.mlp + PK::w2);
+    const uint2* B3 = reinterpret_cast<const uint2*>(a.mlp + PK::w3);
+    const float* bias = reinterpret_cast<const float*>(a.mlp + PK::bias);
+    uint2 w1f[KT1], w2f[4], w3f[4];
+#pragma unroll
+    for (int kt = 0; kt < KT1; ++kt) w1f[kt] = __ldg(B1 + (kt * 8 + w) * 32 + lane);
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        w2f[kt] = __ldg(B2 + (kt * 8 + w) * 32 + lane);
+        w3f[kt] = __ldg(B3 + kt * 32 + lane);
+    }
+    const int col = w * 8 + 2 * t;
+    const float bs1[2] = {__ldg(bias + col), __ldg(bias + col + 1)};
+    const float bs2[2] = {__ldg(bias + MLP_H + col), __ldg(bias + MLP_H + col + 1)};
+    const float b3 = __ldg(bias + 2 * MLP_H);
+    // A fragment of rows mt*16 + (g, g+8), k-chunk kt, from a [rows][ld] array of BF16 pairs
+    auto frag = [&](const uint32_t* src, int ld, int mt, int kt, uint32_t* A) {
+        const uint32_t* p = src + (mt * 16 + g) * ld + kt * 8 + t;
+        A[0] = p[0];
+        A[1] = p[8 * ld];
+        A[2] = p[4];
+        A[3] = p[8 * ld + 4];
+    };
+    // bias + GELU of the warp's n-tile, stored as BF16 pairs (rows g, g+8; columns 8w+2t, +1)
+    auto act = [&](const float* acc, const float* bs, uint32_t* dst, int mt) {
+        dst[(mt * 16 + g) * HW + col / 2] = pack_bf16x2(gelu_f(acc[0] + bs[0]), gelu_f(acc[1] + bs[1]));
+        dst[(mt * 16 + g + 8) * HW + col / 2] = pack_bf16x2(gelu_f(acc[2] + bs[0]), gelu_f(acc[3] + bs[1]));
+    };
+    __syncthreads();
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < KT1; ++kt) {
+            uint32_t A[4];
+            frag(sX, XW, mt, kt, A);
+            mma_bf16(acc, A, w1f[kt].x, w1f[kt].y);
+        }
+        act(acc, bs1, sH1, mt);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            uint32_t A[4];
+            frag(sH1, HW, mt, kt, A);
+            mma_bf16(acc, A, w2f[kt].x, w2f[kt].y);
+        }
+        act(acc, bs2, sH2, mt);
+    }
+    __syncthreads();
+    if (w < MT) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            uint32_t A[4];
+            frag(sH2, HW, w, kt, A);
+            mma_bf16(acc, A, w3f[kt].x, w3f[kt].y);
+        }
+        const float ref = (float)(a.ph.cs * a.ph.hp), gate = (float)a.ph.nu_gate;
+        if (t == 0) {
+            const float y[2] = {acc[0] + b3, acc[2] + b3};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long r = c0 + w * 16 + g + 8 * h;
+                if (r < a.ncell) a.nu_next[r] = expf(y[h]) < gate ? 0.f : ref * expf(y[h]);
+            }
+        }
+    }
+    // the next tile starts with a barrier before it writes the big region
 }
 
 // DIFF: the diffusion operator div(eps grad u) is compiled in (a separate
@@ -614,7 +732,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     constexpr int b = C::b, nq = C::nq, ns = C::ns, nf = C::nf, TC = C::TC, NT = C::NT;
     constexpr int FE = C::FE, KP = C::KP, NQP = C::NQP, NP = C::NP, B2K = C::B2K, NSP = C::NSP, B2N = C::B2N;
     constexpr int LDA = C::LDA, LDV = C::LDV, LDP = C::LDP, LDC2 = C::LDC2, LDT = C::LDT, LDL = C::LDL;
-    constexpr int RE = C::RE, RP = C::RP, RC = C::RC, RL = C::RL;
+    constexpr int RE = C::RE, RP = C::RP;
     static_assert(BK == BK_FMA || sizeof(T) == 4, "the tensor-core path is FP32");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -1166,9 +1284,13 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 // tile (the next iteration starts with a barrier after the projection)
                 __syncthreads();
                 if (tile + gridDim.x < ntile) issue(tile + gridDim.x, sR);
-                if (do_proj)
+                if (do_proj) {
                     tile_project<T, K, BK, MODE == TM_STAGE_VABS>(sm, sU, tabs, a, c0, (a.flags & F_DT) != 0, smax,
                                                                  sums, false);
+                    if constexpr (MODE == TM_STAGE_VABS) {
+                        if (a.nu_next) tile_nu<T, K, BK>(sm, sU, a, c0);
+                    }
+                }
             }
         }
     }

@@ -24,7 +24,7 @@ class Solver:
     def __init__(self, N: int, k: int, cs: float = 1.0, precision: str = "f32", rk_stages: int | None = None,
                  cfl: float = 0.3, av: str = "vnr", alpha: float = 2.0, beta: float = 0.2, rho_floor: float = 1e-3,
                  nu_gate: float = 0.0, device: str | int = "cuda", stream: torch.cuda.Stream | None = None,
-                 riemann: str = "rusanov", diffusion: float = 0.0):
+                 riemann: str = "rusanov", diffusion: float = 0.0, fused_infer: bool = False):
         self.L = B.lib()
         self.N, self.k, self.cs = N, k, cs
         self.b = nmodes(k)
@@ -40,7 +40,7 @@ class Solver:
         self.rk = rk_stages
         av_mode = {"off": B.AV_OFF, "vnr": B.AV_VNR, "learned": B.AV_LEARNED}[av]
         self.mesh = B.Mesh((C.c_int32 * 3)(N, N, N), (C.c_double * 3)(1.0, 1.0, 1.0))
-        self.nu = B.NuParams(av_mode, alpha, beta, rho_floor, nu_gate, diffusion)
+        self.nu = B.NuParams(av_mode, alpha, beta, rho_floor, nu_gate, diffusion, int(fused_infer))
         nb = C.c_size_t(0)
         self._check(self.L.dg_scratch_bytes(C.byref(self.mesh), k, C.byref(self.nu), C.byref(nb)), None)
         with torch.cuda.device(self.device):
@@ -265,4 +265,10 @@ class Solver:
     def av_nu(self):
         nu = torch.empty(self.ncell, dtype=torch.float32, device=self.device)
         self._check(self.L.dg_av_nu(self.h, nu.data_ptr()), self.h)
+        return nu
+
+    def av_nu_carried(self):
+        """The coefficient the last learned step evaluated for the current state."""
+        nu = torch.empty(self.ncell, dtype=torch.float32, device=self.device)
+        self._check(self.L.dg_av_nu_carried(self.h, nu.data_ptr()), self.h)
         return nu

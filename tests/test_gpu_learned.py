@@ -187,3 +187,70 @@ def test_trained_sensor_beats_constant_predictor_on_held_out_cells():
     # constant predictor and the untrained network by a quarter
     assert mae < 0.75 * mae_const
     assert mae < 0.75 * mae_init
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("prec", ["f64", "f32", "x3"])
+@pytest.mark.parametrize("N,k,gated", [(5, 1, False), (5, 2, True), (5, 3, False), (7, 3, True)])
+def test_carried_coefficient_matches_the_inference_kernel(N, k, prec, gated, fused):
+    # the coefficient the next learned step uses for the current state: with
+    # fused_infer evaluated by the last stage for the state it writes, else by
+    # the inference kernel from the |v| projection the last stage carried.
+    # Either equals, bit for bit, the inference kernel's on a fresh projection
+    # of the same state (same BF16 roundings, products and accumulation
+    # orders).  125 and 343 cells leave ragged tiles (16 cells per tile, 32 at
+    # k = 1)
+    u = I.random_state(N, k, seed=40 + k, v_rms=0.8)
+    th = M.init_params(2 * I.nmodes(k), seed=9).astype(np.float32)
+    gate = 0.0
+    if gated:
+        s0 = Solver(N, k, precision=prec, av="learned")
+        s0.set_av_weights(th)
+        s0.set_state(u)
+        s0.step(1)
+        nu0 = s0.av_nu().cpu().numpy().astype(np.float64)
+        gate = float(np.median(nu0 / ((1.0 / N) / (k + 1))))
+    s = Solver(N, k, precision=prec, av="learned", nu_gate=gate, fused_infer=fused)
+    s.set_av_weights(th)
+    s.set_state(u)
+    with pytest.raises(Exception):
+        s.av_nu_carried()  # nothing carried before the first step
+    s.step(2)
+    carried = s.av_nu_carried().cpu().numpy()
+    fresh = s.av_nu().cpu().numpy()
+    assert np.array_equal(carried, fresh)
+    assert (carried > 0).any()
+    if gated:
+        assert (carried == 0).any()
+    with pytest.raises(Exception):
+        s.av_nu_carried()  # dg_av_nu recomputed it: the carry is gone
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 1e-6), ("x3", 1e-6)])
+def test_learned_steps_fused_and_separate_inference(prec, tol):
+    # three learned steps in a row with the coefficient evaluated in the last
+    # stage (fused_infer) equal, bit for bit, three steps with the separate
+    # inference launch; and both stay within rounding of three steps that
+    # each start from a freshly set state (projection and inference launched
+    # at the start of every step)
+    N, k = 6, 3
+    u = I.random_state(N, k, seed=77, v_rms=0.8)
+    th = M.init_params(2 * I.nmodes(k), seed=11).astype(np.float32)
+    runs = []
+    for fused in (True, False):
+        a = Solver(N, k, precision=prec, av="learned", fused_infer=fused)
+        a.set_av_weights(th)
+        a.set_state(u)
+        a.step(3)
+        runs.append(a.get_state().cpu().numpy().astype(np.float64))
+    assert np.array_equal(runs[0], runs[1])
+    b = Solver(N, k, precision=prec, av="learned")
+    b.set_av_weights(th)
+    b.set_state(u)
+    for _ in range(3):
+        b.step(1)
+        b.set_state(b.get_state())
+    ub = b.get_state().cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(runs[0] - ub) <= tol * np.linalg.norm(ub)
