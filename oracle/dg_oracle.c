@@ -359,24 +359,27 @@ double orc_dt(const orc_cfg* cfg, const double* u)
 /* primitive projection (Sec. 3.2, eq. weights_equation):                    */
 /*   vhat_l = (1/|K|) int_K (m/rho) phi_l dV  by (k+1)^3-point Gauss         */
 /* ------------------------------------------------------------------------ */
+/* projection of one cell's velocity: vc[i][l] = (1/8) sum_q w_q phi_l(xi_q) m_i/rho */
+static void project_cell(const tabs* T, const double* uc, double* vc)
+{
+    int b = T->b;
+    memset(vc, 0, sizeof(double) * 3 * b);
+    for (int q = 0; q < T->nq; ++q) {
+        const double* ph = T->phi + q * b;
+        double rho = eval(T, uc, ph);
+        for (int i = 0; i < 3; ++i) {
+            double vq = eval(T, uc + (1 + i) * b, ph) / rho;
+            for (int l = 0; l < b; ++l) vc[i * b + l] += 0.125 * T->wq[q] * ph[l] * vq;
+        }
+    }
+}
+
 void orc_project_velocity(const orc_cfg* cfg, const double* u, double* vhat)
 {
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
     int N = cfg->N, b = T.b, nc = N * N * N;
-    for (int c = 0; c < nc; ++c) {
-        const double* uc = u + (size_t)c * 4 * b;
-        double* vc = vhat + (size_t)c * 3 * b;
-        memset(vc, 0, sizeof(double) * 3 * b);
-        for (int q = 0; q < T.nq; ++q) {
-            const double* ph = T.phi + q * b;
-            double rho = eval(&T, uc, ph);
-            for (int i = 0; i < 3; ++i) {
-                double vq = eval(&T, uc + (1 + i) * b, ph) / rho;
-                for (int l = 0; l < b; ++l) vc[i * b + l] += 0.125 * T.wq[q] * ph[l] * vq;
-            }
-        }
-    }
+    for (int c = 0; c < nc; ++c) project_cell(&T, u + (size_t)c * 4 * b, vhat + (size_t)c * 3 * b);
     tabs_free(&T);
 }
 
@@ -440,14 +443,76 @@ int orc_rhs_nu(const orc_cfg* cfg, const double* u, const double* ahat, double d
     return rhs_impl(cfg, u, ahat, dt_pimax, nu_cell, dudt);
 }
 
+/* volume integral and forcing source of one cell, added to rc [4][b]; nu < 0:
+ * the vNR viscous pressure, else the per-cell coefficient nu */
+static void volume_cell(const tabs* Tp, const orc_cfg* cfg, const double* uc, const double* ac, const double abar[3],
+                        double nu, double dt_pimax, double* rc)
+{
+    const tabs T = *Tp;
+    int b = T.b, nq = T.nq;
+    double h = 1.0 / cfg->N, cs2 = cfg->cs * cfg->cs;
+    for (int q = 0; q < nq; ++q) {
+        const double* ph = T.phi + q * b;
+        double rho = eval(&T, uc, ph), m[3], v[3], drho[3], dmd[3];
+        for (int i = 0; i < 3; ++i) {
+            m[i] = eval(&T, uc + (1 + i) * b, ph);
+            v[i] = m[i] / rho;
+        }
+        for (int d = 0; d < 3; ++d) {
+            const double* dph = T.dphi + ((size_t)d * nq + q) * b;
+            drho[d] = (2.0 / h) * eval(&T, uc, dph);
+            dmd[d] = (2.0 / h) * eval(&T, uc + (1 + d) * b, dph);
+        }
+        /* div v = (div m - v . grad rho) / rho */
+        double divv = (dmd[0] + dmd[1] + dmd[2] - (v[0] * drho[0] + v[1] * drho[1] + v[2] * drho[2])) / rho;
+        double P = cs2 * rho + (nu >= 0.0 ? orc_pi_nu(cfg, rho, divv, nu, dt_pimax) : orc_vnr(cfg, rho, divv, dt_pimax));
+        double F[4][3]; /* F[var][d] */
+        for (int d = 0; d < 3; ++d) {
+            F[0][d] = m[d];
+            for (int i = 0; i < 3; ++i) F[1 + i][d] = m[i] * v[d] + (i == d ? P : 0.0);
+        }
+        for (int l = 0; l < b; ++l) {
+            double g[3];
+            for (int d = 0; d < 3; ++d) g[d] = T.dphi[((size_t)d * nq + q) * b + l];
+            for (int var = 0; var < 4; ++var)
+                rc[var * b + l] += T.wq[q] * (g[0] * F[var][0] + g[1] * F[var][1] + g[2] * F[var][2]) / (4.0 * h);
+        }
+        if (ac) {
+            for (int i = 0; i < 3; ++i) {
+                double src = rho * (eval(&T, ac + i * b, ph) - abar[i]);
+                for (int l = 0; l < b; ++l) rc[(1 + i) * b + l] += 0.125 * T.wq[q] * ph[l] * src;
+            }
+        }
+    }
+}
+
+/* numerical flux at face point s of the interface along d between the lower
+ * cell L (its xi_d = +1 face) and the upper cell R (its xi_d = -1 face); face
+ * states rho from the cells' own expansions, v from their projections */
+static void face_flux(const tabs* T, const orc_cfg* cfg, int d, int s, const double* uL, const double* vL,
+                      const double* uR, const double* vR, double Fs[4])
+{
+    int b = T->b, ns = T->ns;
+    const double* phL = T->phif + ((size_t)(d * 2 + 1) * ns + s) * b;
+    const double* phR = T->phif + ((size_t)(d * 2 + 0) * ns + s) * b;
+    double WL[4], WR[4];
+    WL[0] = eval(T, uL, phL);
+    WR[0] = eval(T, uR, phR);
+    for (int i = 0; i < 3; ++i) {
+        WL[1 + i] = eval(T, vL + i * b, phL);
+        WR[1 + i] = eval(T, vR + i * b, phR);
+    }
+    orc_riemann(cfg->riemann, cfg->cs, d, WL, WR, Fs);
+}
+
 static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, const double* nu_cell,
                     double* dudt)
 {
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
-    int N = cfg->N, b = T.b, nq = T.nq, ns = T.ns;
+    int N = cfg->N, b = T.b, ns = T.ns;
     size_t nc = (size_t)N * N * N;
-    double h = 1.0 / N, cs2 = cfg->cs * cfg->cs;
+    double h = 1.0 / N;
     double* vhat = (double*)malloc(sizeof(double) * nc * 3 * b);
     orc_project_velocity(cfg, u, vhat);
     double abar[3] = {0, 0, 0};
@@ -455,45 +520,9 @@ static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, dou
     memset(dudt, 0, sizeof(double) * nc * 4 * b);
 
     /* volume integral and forcing source, cell by cell */
-    for (size_t c = 0; c < nc; ++c) {
-        const double* uc = u + c * 4 * b;
-        double* rc = dudt + c * 4 * b;
-        for (int q = 0; q < nq; ++q) {
-            const double* ph = T.phi + q * b;
-            double rho = eval(&T, uc, ph), m[3], v[3], drho[3], dmd[3];
-            for (int i = 0; i < 3; ++i) {
-                m[i] = eval(&T, uc + (1 + i) * b, ph);
-                v[i] = m[i] / rho;
-            }
-            for (int d = 0; d < 3; ++d) {
-                const double* dph = T.dphi + ((size_t)d * nq + q) * b;
-                drho[d] = (2.0 / h) * eval(&T, uc, dph);
-                dmd[d] = (2.0 / h) * eval(&T, uc + (1 + d) * b, dph);
-            }
-            /* div v = (div m - v . grad rho) / rho */
-            double divv = (dmd[0] + dmd[1] + dmd[2] - (v[0] * drho[0] + v[1] * drho[1] + v[2] * drho[2])) / rho;
-            double P = cs2 * rho +
-                       (nu_cell ? orc_pi_nu(cfg, rho, divv, nu_cell[c], dt_pimax) : orc_vnr(cfg, rho, divv, dt_pimax));
-            double F[4][3]; /* F[var][d] */
-            for (int d = 0; d < 3; ++d) {
-                F[0][d] = m[d];
-                for (int i = 0; i < 3; ++i) F[1 + i][d] = m[i] * v[d] + (i == d ? P : 0.0);
-            }
-            for (int l = 0; l < b; ++l) {
-                double g[3];
-                for (int d = 0; d < 3; ++d) g[d] = T.dphi[((size_t)d * nq + q) * b + l];
-                for (int var = 0; var < 4; ++var)
-                    rc[var * b + l] += T.wq[q] * (g[0] * F[var][0] + g[1] * F[var][1] + g[2] * F[var][2]) / (4.0 * h);
-            }
-            if (ahat) {
-                const double* ac = ahat + c * 3 * b;
-                for (int i = 0; i < 3; ++i) {
-                    double src = rho * (eval(&T, ac + i * b, ph) - abar[i]);
-                    for (int l = 0; l < b; ++l) rc[(1 + i) * b + l] += 0.125 * T.wq[q] * ph[l] * src;
-                }
-            }
-        }
-    }
+    for (size_t c = 0; c < nc; ++c)
+        volume_cell(&T, cfg, u + c * 4 * b, ahat ? ahat + c * 3 * b : NULL, abar, nu_cell ? nu_cell[c] : -1.0,
+                    dt_pimax, dudt + c * 4 * b);
 
     /* surface integral: one pass over interfaces, each flux added to both cells */
     for (int iz = 0; iz < N; ++iz)
@@ -505,14 +534,9 @@ static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, dou
                     const double* phL = T.phif + ((size_t)(d * 2 + 1) * ns) * b; /* xi_d = +1 in L */
                     const double* phR = T.phif + ((size_t)(d * 2 + 0) * ns) * b; /* xi_d = -1 in R */
                     for (int s = 0; s < ns; ++s) {
-                        double WL[4], WR[4], Fs[4];
-                        WL[0] = eval(&T, u + (size_t)cL * 4 * b, phL + s * b);
-                        WR[0] = eval(&T, u + (size_t)cR * 4 * b, phR + s * b);
-                        for (int i = 0; i < 3; ++i) {
-                            WL[1 + i] = eval(&T, vhat + ((size_t)cL * 3 + i) * b, phL + s * b);
-                            WR[1 + i] = eval(&T, vhat + ((size_t)cR * 3 + i) * b, phR + s * b);
-                        }
-                        orc_riemann(cfg->riemann, cfg->cs, d, WL, WR, Fs);
+                        double Fs[4];
+                        face_flux(&T, cfg, d, s, u + (size_t)cL * 4 * b, vhat + (size_t)cL * 3 * b,
+                                  u + (size_t)cR * 4 * b, vhat + (size_t)cR * 3 * b, Fs);
                         for (int var = 0; var < 4; ++var)
                             for (int l = 0; l < b; ++l) {
                                 dudt[((size_t)cL * 4 + var) * b + l] -= T.ws[s] * phL[s * b + l] * Fs[var] / (4.0 * h);
@@ -524,6 +548,50 @@ static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, dou
     free(vhat);
     tabs_free(&T);
     orc_diffusion_rhs(cfg, u, dudt); /* + div(eps grad u) when eps > 0 */
+    return 0;
+}
+
+/* Right-hand side of single cells from their neighbourhoods: the same volume
+ * term, face fluxes and lifts as orc_rhs, for cells given with their six face
+ * neighbours.  patch [n][7][4][b]: the cell, then its neighbours across the
+ * faces -x, +x, -y, +y, -z, +z; ahat_c [n][3][b] or NULL with abar the mean
+ * acceleration of the whole field; nu [n] or NULL (vNR).  Without the
+ * diffusion operator (it returns -1 when eps_diff > 0). */
+int orc_rhs_local(const orc_cfg* cfg, const double* patch, const double* ahat_c, const double abar[3], double dt_pimax,
+                  const double* nu, int64_t n, double* out)
+{
+    if (cfg->eps_diff > 0.0) return -1;
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int b = T.b, ns = T.ns;
+    double h = 1.0 / cfg->N;
+    double* vh = (double*)malloc(sizeof(double) * 7 * 3 * b);
+    const double zero[3] = {0, 0, 0};
+    for (int64_t c = 0; c < n; ++c) {
+        const double* pc = patch + (size_t)c * 7 * 4 * b;
+        double* rc = out + (size_t)c * 4 * b;
+        memset(rc, 0, sizeof(double) * 4 * b);
+        for (int j = 0; j < 7; ++j) project_cell(&T, pc + j * 4 * b, vh + j * 3 * b);
+        volume_cell(&T, cfg, pc, ahat_c ? ahat_c + (size_t)c * 3 * b : NULL, abar ? abar : zero, nu ? nu[c] : -1.0,
+                    dt_pimax, rc);
+        for (int d = 0; d < 3; ++d) {
+            const int jm = 1 + 2 * d, jp = 2 + 2 * d;
+            const double* phL = T.phif + ((size_t)(d * 2 + 1) * ns) * b; /* + face of the cell */
+            const double* phR = T.phif + ((size_t)(d * 2 + 0) * ns) * b; /* - face of the cell */
+            for (int s = 0; s < ns; ++s) {
+                double Fp[4], Fm[4];
+                face_flux(&T, cfg, d, s, pc, vh, pc + jp * 4 * b, vh + jp * 3 * b, Fp);
+                face_flux(&T, cfg, d, s, pc + jm * 4 * b, vh + jm * 3 * b, pc, vh, Fm);
+                for (int var = 0; var < 4; ++var)
+                    for (int l = 0; l < b; ++l) {
+                        rc[var * b + l] -= T.ws[s] * phL[s * b + l] * Fp[var] / (4.0 * h);
+                        rc[var * b + l] += T.ws[s] * phR[s * b + l] * Fm[var] / (4.0 * h);
+                    }
+            }
+        }
+    }
+    free(vh);
+    tabs_free(&T);
     return 0;
 }
 

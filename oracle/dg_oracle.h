@@ -85,6 +85,8 @@ int orc_limit(const orc_cfg* cfg, double* u);
 double orc_pi_nu(const orc_cfg* cfg, double rho, double divv, double nu, double dt);
 int orc_rhs_nu(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, const double* nu_cell,
                double* dudt);
+int orc_rhs_local(const orc_cfg* cfg, const double* patch, const double* ahat_c, const double abar[3],
+                  double dt_pimax, const double* nu, int64_t n, double* out);
 void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, double* y);
 int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt);
 

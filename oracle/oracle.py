@@ -91,6 +91,7 @@ def lib():
         _lib.orc_diagnostics.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d]
         _lib.orc_forcing_project.argtypes = [C.POINTER(Cfg), C.c_int, C.POINTER(C.c_int32), d, d]
         _lib.orc_rhs_nu.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d, d]
+        _lib.orc_rhs_local.argtypes = [C.POINTER(Cfg), d, d, d, C.c_double, d, C.c_int64, d]
         _lib.orc_av_features.argtypes = [C.POINTER(Cfg), d, C.c_double, d, d]
         _lib.orc_pi_nu.restype = C.c_double
         _lib.orc_pi_nu.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double, C.c_double]
@@ -204,6 +205,34 @@ def rhs_nu(cfg: Cfg, u: np.ndarray, nu_cell: np.ndarray, ahat: np.ndarray | None
     out = np.zeros(_shape(cfg))
     nu = np.ascontiguousarray(nu_cell, dtype=np.float64)
     lib().orc_rhs_nu(C.byref(cfg), _p(u), _p(ahat), dt_pimax, _p(nu), _p(out))
+    return out
+
+
+def neighbourhood(N: int, cells) -> np.ndarray:
+    """[n][7] cell indices: each cell, then its periodic neighbours across the
+    faces -x, +x, -y, +y, -z, +z (cell = (iz*N + iy)*N + ix)."""
+    c = np.asarray(cells, dtype=np.int64)
+    ix, iy, iz = c % N, (c // N) % N, c // (N * N)
+    idx = lambda x, y, z: ((z % N) * N + (y % N)) * N + (x % N)  # noqa: E731
+    return np.stack([c, idx(ix - 1, iy, iz), idx(ix + 1, iy, iz), idx(ix, iy - 1, iz), idx(ix, iy + 1, iz),
+                     idx(ix, iy, iz - 1), idx(ix, iy, iz + 1)], axis=1)
+
+
+def rhs_cells(cfg: Cfg, u: np.ndarray, cells, ahat: np.ndarray | None = None, abar=None, dt_pimax: float = 0.0,
+              nu_cell: np.ndarray | None = None) -> np.ndarray:
+    """RHS of the listed cells only (the same per-cell arithmetic as rhs), from
+    each cell's face neighbourhood gathered out of u (any float array [N^3][4][b]).
+    With ahat, abar is the mean acceleration of the whole field (forcing_mean).
+    nu_cell: per-cell coefficients of the listed cells (learned mode) or None."""
+    nb = neighbourhood(cfg.N, cells)
+    patch = np.ascontiguousarray(np.asarray(u)[nb], dtype=np.float64)
+    ac = None if ahat is None else np.ascontiguousarray(np.asarray(ahat)[nb[:, 0]], dtype=np.float64)
+    ab = None if abar is None else np.ascontiguousarray(abar, dtype=np.float64)
+    nu = None if nu_cell is None else np.ascontiguousarray(nu_cell, dtype=np.float64)
+    out = np.zeros((len(nb), 4, patch.shape[-1]))
+    rc = lib().orc_rhs_local(C.byref(cfg), _p(patch), _p(ac), _p(ab), dt_pimax, _p(nu), len(nb), _p(out))
+    if rc != 0:
+        raise ValueError("rhs_cells: not available with the diffusion operator")
     return out
 
 
