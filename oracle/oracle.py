@@ -219,12 +219,18 @@ def neighbourhood(N: int, cells) -> np.ndarray:
 
 
 def rhs_cells(cfg: Cfg, u: np.ndarray, cells, ahat: np.ndarray | None = None, abar=None, dt_pimax: float = 0.0,
-              nu_cell: np.ndarray | None = None) -> np.ndarray:
+              nu_cell: np.ndarray | None = None, base_N: int | None = None) -> np.ndarray:
     """RHS of the listed cells only (the same per-cell arithmetic as rhs), from
     each cell's face neighbourhood gathered out of u (any float array [N^3][4][b]).
     With ahat, abar is the mean acceleration of the whole field (forcing_mean).
-    nu_cell: per-cell coefficients of the listed cells (learned mode) or None."""
+    nu_cell: per-cell coefficients of the listed cells (learned mode) or None.
+    base_N: u (and ahat) hold base_N^3 cells whose periodic tiling fills the
+    N^3 mesh (N a multiple of base_N); cells index the N^3 mesh."""
     nb = neighbourhood(cfg.N, cells)
+    if base_N is not None:
+        assert cfg.N % base_N == 0
+        x, y, z = nb % cfg.N, (nb // cfg.N) % cfg.N, nb // (cfg.N * cfg.N)
+        nb = ((z % base_N) * base_N + (y % base_N)) * base_N + (x % base_N)
     patch = np.ascontiguousarray(np.asarray(u)[nb], dtype=np.float64)
     ac = None if ahat is None else np.ascontiguousarray(np.asarray(ahat)[nb[:, 0]], dtype=np.float64)
     ab = None if abar is None else np.ascontiguousarray(abar, dtype=np.float64)

@@ -57,3 +57,17 @@ def test_neighbourhood_is_periodic():
     nb = O.neighbourhood(4, [0, 63])
     assert list(nb[0]) == [0, 3, 1, 12, 4, 48, 16]
     assert list(nb[1]) == [63, 62, 60, 59, 51, 47, 15]
+
+
+def test_tiled_state_gathers_from_the_base_mesh():
+    # a 2^3 tiling of a 3^3 state is a 6^3 state; the RHS of its cells equals
+    # the whole-mesh RHS of the tiled array
+    k, n = 2, 3
+    base = I.random_state(n, k, seed=21, v_rms=0.6)
+    b = base.shape[-1]
+    tiled = np.tile(base.reshape(n, n, n, 4, b), (2, 2, 2, 1, 1)).reshape(-1, 4, b)
+    cfg = O.make_cfg(2 * n, k)
+    full = O.rhs(cfg, tiled, None, 1e-3)
+    cells = np.array([0, 5, 17, 100, 215])
+    got = O.rhs_cells(cfg, base, cells, dt_pimax=1e-3, base_N=n)
+    assert rel(got, full[cells]) < 1e-13
