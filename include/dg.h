@@ -70,7 +70,8 @@ extern "C" {
 #define DG_ST_NONFINITE 4u /* a NaN/Inf was produced                              */
 
 typedef struct {
-    int32_t n[3];          /* cells per axis; this build requires n[0]=n[1]=n[2] */
+    int32_t n[3];          /* cells per axis; this build requires n[0]=n[1]=n[2],
+                              at most 1024 (cell indices fit in 32 bits)         */
     double L[3];           /* box size; this build requires L = 1                */
 } dg_mesh;
 

@@ -902,7 +902,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     if (!mesh || !nu || !opts) return DG_EINVAL;
     if (order < 1 || order > 3) return DG_EINVAL;
     if (mesh->n[0] < 1 || mesh->n[0] != mesh->n[1] || mesh->n[0] != mesh->n[2]) return DG_EINVAL;
-    if (mesh->n[0] > 2048) return DG_EINVAL;
+    if (mesh->n[0] > kMaxN) return DG_EINVAL;
     for (int d = 0; d < 3; ++d)
         if (mesh->L[d] != 1.0) return DG_EINVAL;
     if (!(cs > 0.0)) return DG_EINVAL;

@@ -13,6 +13,9 @@
 
 namespace dg {
 
+// largest mesh: N^3 cell indices fit in 32 bits
+constexpr int kMaxN = 1024;
+
 template <int K>
 struct Dims {
     static constexpr int n = K + 1;                          // Gauss points per axis

@@ -44,14 +44,23 @@ struct Tile {
     static constexpr int NT = TC * Dims<K>::nq;                  // threads per block
 };
 
-__device__ __forceinline__ long neighbour(long c, int f, int N)
+// coordinates of cell c = (z N + y) N + x; 32-bit arithmetic (N <= kMaxN)
+__device__ __forceinline__ void cell_xyz(long c, int N, int& x, int& y, int& z)
 {
-    int ix = (int)(c % N), iy = (int)((c / N) % N), iz = (int)(c / ((long)N * N));
-    int d = f >> 1, s = (f & 1) ? 1 : N - 1;
-    if (d == 0) ix = (ix + s) % N;
-    if (d == 1) iy = (iy + s) % N;
-    if (d == 2) iz = (iz + s) % N;
-    return ((long)iz * N + iy) * N + ix;
+    const unsigned int u = (unsigned int)c, n = (unsigned int)N, q = u / n;
+    x = (int)(u - q * n);
+    y = (int)(q % n);
+    z = (int)(q / n);
+}
+
+// periodic neighbour of cell c across its face along Dd (side 1: +, 0: -),
+// given c's coordinate co along Dd
+template <int Dd>
+__device__ __forceinline__ long neighbour_along(long c, int co, int side, int N)
+{
+    const long st = Dd == 0 ? 1L : (Dd == 1 ? (long)N : (long)N * N);
+    if (side) return co == N - 1 ? c - (long)(N - 1) * st : c + st;
+    return co == 0 ? c + (long)(N - 1) * st : c - st;
 }
 
 // deterministic reduction of per-block partials by the last block to finish

@@ -226,7 +226,8 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double cs, const d
 {
     if (!mesh || !nu || !u_in || !dudt || !stream) return report(DG_EINVAL, "null argument");
     if (order < 1 || order > 3 || precision < 0 || precision > 2) return report(DG_EINVAL, "order or precision");
-    if (mesh->n[0] < 1 || mesh->n[0] != mesh->n[1] || mesh->n[0] != mesh->n[2]) return report(DG_EINVAL, "mesh");
+    if (mesh->n[0] < 1 || mesh->n[0] != mesh->n[1] || mesh->n[0] != mesh->n[2] || mesh->n[0] > kMaxN)
+        return report(DG_EINVAL, "mesh");
     for (int d = 0; d < 3; ++d)
         if (mesh->L[d] != 1.0) return report(DG_EINVAL, "box size must be 1");
     if (nu->diffusion != 0.0) return report(DG_EINVAL, "the diffusion operator needs a context (dg_init)");

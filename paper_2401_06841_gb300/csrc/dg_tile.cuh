@@ -978,6 +978,11 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             static_assert(RLW * LDT <= RCW * LDC2 && RLW * LDL <= RCW * LDT, "warp flux rows fit the row blocks");
             const int wid = tid >> 5, lane = tid & 31;
             T nbr[NR][b];
+            // mesh coordinates of the cell of each of the lane's face rows
+            int cxyz[NR][3];
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+                cell_xyz(c0 + ((wid * RCW + lane + 32 * j) >> 4), a.N, cxyz[j][0], cxyz[j][1], cxyz[j][2]);
             auto load_nbr = [&](auto dd) {
                 constexpr int Dd = decltype(dd)::value;
 #pragma unroll
@@ -986,7 +991,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                     const int field = r & 3, who = (r >> 2) & 1, side = (r >> 3) & 1, c = r >> 4;
                     const long cc = c0 + c;
                     if (who == 1 && cc < a.ncell) {
-                        const long nc = neighbour(cc, 2 * Dd + side, a.N);
+                        const long nc = neighbour_along<Dd>(cc, cxyz[j][Dd], side, a.N);
                         const T* src = (field == 0) ? a.u_in + nc * 4 * b : a.vh_in + (nc * 3 + field - 1) * b;
                         if constexpr (b % 4 == 0) {
 #pragma unroll
@@ -1149,8 +1154,10 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                         if (c0 + c < a.ncell) {
                         // the variable's coefficient rows of both face neighbours
                         T um[b], up[b];
-                        const T* srcm = a.u_in + (neighbour(c0 + c, 2 * Dd, a.N) * 4 + v) * b;
-                        const T* srcp = a.u_in + (neighbour(c0 + c, 2 * Dd + 1, a.N) * 4 + v) * b;
+                        int xyz[3];
+                        cell_xyz(c0 + c, a.N, xyz[0], xyz[1], xyz[2]);
+                        const T* srcm = a.u_in + (neighbour_along<Dd>(c0 + c, xyz[Dd], 0, a.N) * 4 + v) * b;
+                        const T* srcp = a.u_in + (neighbour_along<Dd>(c0 + c, xyz[Dd], 1, a.N) * 4 + v) * b;
                         if constexpr (b % 4 == 0) {
 #pragma unroll
                             for (int l = 0; l < b; l += 4) {
