@@ -1272,3 +1272,330 @@ void orc_diffusion_rhs(const orc_cfg* cfg, const double* u, double* dudt)
     }
     tabs_free(&T);
 }
+
+/* ======================================================================== */
+/* Adiabatic system (Sec. 2.1: state vector, ideal-gas equation of state,    */
+/* flux matrix).  u = (rho, m, e) per cell, [c][5][b]; e is the total energy */
+/* density, p = (gamma - 1)(e - |m|^2 / (2 rho)), and the flux along d is    */
+/*   F_d = (m_d, m v_d + p e_d, (e + p) v_d).                                */
+/* Volume (Sec. 3.1): conserved values at the internal points; the viscous   */
+/* pressure Pi is added to p in the momentum and energy fluxes, its bulk     */
+/* term with the local sound speed c = sqrt(gamma p / rho).  Faces (Sec.     */
+/* 3.2): rho from its own expansion, v and p from their projections onto the */
+/* basis; Rusanov flux with lambda = max over both sides of |v_n| + c.       */
+/* Positivity (Sec. 3.1): density and pressure at every volume and face      */
+/* point; the higher modes of all variables are scaled toward the cell mean. */
+/* ======================================================================== */
+
+/* physical flux along d of the conserved state U = (rho, m, e) */
+void orc_adi_flux(double gamma, int d, const double U[5], double F[5])
+{
+    double rho = U[0], v[3] = {U[1] / rho, U[2] / rho, U[3] / rho};
+    double p = (gamma - 1.0) * (U[4] - 0.5 * (U[1] * v[0] + U[2] * v[1] + U[3] * v[2]));
+    F[0] = U[1 + d];
+    for (int i = 0; i < 3; ++i) F[1 + i] = U[1 + i] * v[d] + (i == d ? p : 0.0);
+    F[4] = (U[4] + p) * v[d];
+}
+
+/* Rusanov flux from primitive face states W = (rho, v_x, v_y, v_z, p) */
+void orc_adi_rusanov(double gamma, int d, const double WL[5], const double WR[5], double F[5])
+{
+    double UL[5], UR[5], FL[5], FR[5];
+    const double* W[2] = {WL, WR};
+    double* U[2] = {UL, UR};
+    for (int s = 0; s < 2; ++s) {
+        const double* w = W[s];
+        U[s][0] = w[0];
+        for (int i = 0; i < 3; ++i) U[s][1 + i] = w[0] * w[1 + i];
+        U[s][4] = w[4] / (gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+    }
+    orc_adi_flux(gamma, d, UL, FL);
+    orc_adi_flux(gamma, d, UR, FR);
+    double lL = fabs(WL[1 + d]) + sqrt(gamma * WL[4] / WL[0]);
+    double lR = fabs(WR[1 + d]) + sqrt(gamma * WR[4] / WR[0]);
+    double lam = lL > lR ? lL : lR;
+    for (int v = 0; v < 5; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+}
+
+/* vNR viscous pressure with the local sound speed in the bulk term */
+double orc_adi_vnr(const orc_cfg* cfg, double rho, double c, double divv, double dt)
+{
+    if (cfg->av_mode != 1 || !(divv < 0.0)) return 0.0;
+    double hp = (1.0 / cfg->N) / (cfg->k + 1);
+    double a = -divv;
+    double Pi = cfg->alpha * rho * hp * hp * a * a + cfg->beta * rho * c * hp * a;
+    if (dt > 0.0) {
+        double Pmax = 0.5 * rho * hp * hp * a / dt;
+        if (Pi > Pmax) Pi = Pmax;
+    }
+    return Pi;
+}
+
+static double adi_pressure(double gamma, double rho, const double m[3], double e)
+{
+    return (gamma - 1.0) * (e - 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho);
+}
+
+/* projections of v and p of one cell: pc[i][l], i = v_x, v_y, v_z, p */
+static void adi_project_cell(const tabs* T, double gamma, const double* uc, double* pc)
+{
+    int b = T->b;
+    memset(pc, 0, sizeof(double) * 4 * b);
+    for (int q = 0; q < T->nq; ++q) {
+        const double* ph = T->phi + q * b;
+        double rho = eval(T, uc, ph), m[3], f[4];
+        for (int i = 0; i < 3; ++i) {
+            m[i] = eval(T, uc + (1 + i) * b, ph);
+            f[i] = m[i] / rho;
+        }
+        f[3] = adi_pressure(gamma, rho, m, eval(T, uc + 4 * b, ph));
+        for (int i = 0; i < 4; ++i)
+            for (int l = 0; l < b; ++l) pc[i * b + l] += 0.125 * T->wq[q] * ph[l] * f[i];
+    }
+}
+
+void orc_adi_project(const orc_cfg* cfg, double gamma, const double* u, double* prim)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nc = N * N * N;
+    for (int c = 0; c < nc; ++c) adi_project_cell(&T, gamma, u + (size_t)c * 5 * b, prim + (size_t)c * 4 * b);
+    tabs_free(&T);
+}
+
+int orc_adi_rhs(const orc_cfg* cfg, double gamma, const double* u, double dt_pimax, double* dudt)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nq = T.nq, ns = T.ns;
+    size_t nc = (size_t)N * N * N;
+    double h = 1.0 / N;
+    double* prim = (double*)malloc(sizeof(double) * nc * 4 * b);
+    orc_adi_project(cfg, gamma, u, prim);
+    memset(dudt, 0, sizeof(double) * nc * 5 * b);
+
+    /* volume integral, cell by cell */
+    for (size_t c = 0; c < nc; ++c) {
+        const double* uc = u + c * 5 * b;
+        double* rc = dudt + c * 5 * b;
+        for (int q = 0; q < nq; ++q) {
+            const double* ph = T.phi + q * b;
+            double rho = eval(&T, uc, ph), m[3], v[3], drho[3], dmd[3];
+            for (int i = 0; i < 3; ++i) {
+                m[i] = eval(&T, uc + (1 + i) * b, ph);
+                v[i] = m[i] / rho;
+            }
+            double e = eval(&T, uc + 4 * b, ph);
+            double p = adi_pressure(gamma, rho, m, e);
+            for (int d = 0; d < 3; ++d) {
+                const double* dph = T.dphi + ((size_t)d * nq + q) * b;
+                drho[d] = (2.0 / h) * eval(&T, uc, dph);
+                dmd[d] = (2.0 / h) * eval(&T, uc + (1 + d) * b, dph);
+            }
+            double divv = (dmd[0] + dmd[1] + dmd[2] - (v[0] * drho[0] + v[1] * drho[1] + v[2] * drho[2])) / rho;
+            double c_s = sqrt(gamma * p / rho);
+            double P = p + orc_adi_vnr(cfg, rho, c_s, divv, dt_pimax);
+            double F[5][3]; /* F[var][d] */
+            for (int d = 0; d < 3; ++d) {
+                F[0][d] = m[d];
+                for (int i = 0; i < 3; ++i) F[1 + i][d] = m[i] * v[d] + (i == d ? P : 0.0);
+                F[4][d] = (e + P) * v[d];
+            }
+            for (int l = 0; l < b; ++l) {
+                double g[3];
+                for (int d = 0; d < 3; ++d) g[d] = T.dphi[((size_t)d * nq + q) * b + l];
+                for (int var = 0; var < 5; ++var)
+                    rc[var * b + l] += T.wq[q] * (g[0] * F[var][0] + g[1] * F[var][1] + g[2] * F[var][2]) / (4.0 * h);
+            }
+        }
+    }
+
+    /* surface integral: one pass over interfaces, each flux added to both cells */
+    for (int iz = 0; iz < N; ++iz)
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                int cL = cell_index(N, ix, iy, iz);
+                for (int d = 0; d < 3; ++d) {
+                    int cR = cell_index(N, ix + (d == 0), iy + (d == 1), iz + (d == 2));
+                    const double* phL = T.phif + ((size_t)(d * 2 + 1) * ns) * b; /* xi_d = +1 in L */
+                    const double* phR = T.phif + ((size_t)(d * 2 + 0) * ns) * b; /* xi_d = -1 in R */
+                    for (int s = 0; s < ns; ++s) {
+                        double WL[5], WR[5], Fs[5];
+                        WL[0] = eval(&T, u + (size_t)cL * 5 * b, phL + s * b);
+                        WR[0] = eval(&T, u + (size_t)cR * 5 * b, phR + s * b);
+                        for (int i = 0; i < 4; ++i) {
+                            WL[1 + i] = eval(&T, prim + ((size_t)cL * 4 + i) * b, phL + s * b);
+                            WR[1 + i] = eval(&T, prim + ((size_t)cR * 4 + i) * b, phR + s * b);
+                        }
+                        orc_adi_rusanov(gamma, d, WL, WR, Fs);
+                        for (int var = 0; var < 5; ++var)
+                            for (int l = 0; l < b; ++l) {
+                                dudt[((size_t)cL * 5 + var) * b + l] -= T.ws[s] * phL[s * b + l] * Fs[var] / (4.0 * h);
+                                dudt[((size_t)cR * 5 + var) * b + l] += T.ws[s] * phR[s * b + l] * Fs[var] / (4.0 * h);
+                            }
+                    }
+                }
+            }
+    free(prim);
+    tabs_free(&T);
+    return 0;
+}
+
+/* dt = cfl h / ((k+1) max over volume points of sum_d (|v_d| + c)) */
+double orc_adi_dt(const orc_cfg* cfg, double gamma, const double* u)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nc = N * N * N;
+    double smax = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        const double* uc = u + (size_t)c * 5 * b;
+        for (int q = 0; q < T.nq; ++q) {
+            const double* ph = T.phi + q * b;
+            double rho = eval(&T, uc, ph), m[3];
+            for (int i = 0; i < 3; ++i) m[i] = eval(&T, uc + (1 + i) * b, ph);
+            double p = adi_pressure(gamma, rho, m, eval(&T, uc + 4 * b, ph));
+            double cs = sqrt(gamma * p / rho), s = 0.0;
+            for (int d = 0; d < 3; ++d) s += fabs(m[d] / rho) + cs;
+            if (s > smax) smax = s;
+        }
+    }
+    tabs_free(&T);
+    return cfg->cfl * (1.0 / N) / ((cfg->k + 1) * smax);
+}
+
+/* smallest t in [0, 1] with p(ubar + t d) = eps, given p(ubar) > eps and
+ * p(ubar + d) < eps: the root of the quadratic rho(t) e(t) - |m(t)|^2/2 -
+ * eps rho(t)/(gamma-1) = 0 (positive at t = 0, negative at t = 1) */
+static double adi_pressure_root(double gamma, double eps, const double ub[5], const double dv[5])
+{
+    double g1 = eps / (gamma - 1.0);
+    double A = dv[0] * dv[4] - 0.5 * (dv[1] * dv[1] + dv[2] * dv[2] + dv[3] * dv[3]);
+    double B = ub[0] * dv[4] + dv[0] * ub[4] - (ub[1] * dv[1] + ub[2] * dv[2] + ub[3] * dv[3]) - g1 * dv[0];
+    double C = ub[0] * ub[4] - 0.5 * (ub[1] * ub[1] + ub[2] * ub[2] + ub[3] * ub[3]) - g1 * ub[0];
+    double t;
+    if (fabs(A) <= 1e-14 * (fabs(B) + fabs(C))) {
+        t = -C / B;
+    } else {
+        double disc = B * B - 4.0 * A * C;
+        if (disc < 0.0) disc = 0.0;
+        double sq = sqrt(disc);
+        double r1 = (-B - sq) / (2.0 * A), r2 = (-B + sq) / (2.0 * A);
+        double lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
+        t = (lo >= 0.0 && lo <= 1.0) ? lo : hi;
+    }
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    return t;
+}
+
+/* positivity of density and pressure at every volume and face point (floor
+ * eps = rho_floor for both): theta_rho = (rhobar - eps)/(rhobar - rho_min)
+ * as in the isothermal system, then on the rho-limited state the largest
+ * theta_p in [0, 1] keeping p >= eps at every point; all higher modes of all
+ * variables scaled by theta_rho theta_p.  A cell mean with rho or p at or
+ * below eps is a failure. */
+int orc_adi_limit(const orc_cfg* cfg, double gamma, double* u)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nq = T.nq, npt = T.nq + 6 * T.ns;
+    size_t nc = (size_t)N * N * N;
+    double eps = cfg->rho_floor;
+    int status = 0;
+    for (size_t c = 0; c < nc; ++c) {
+        double* uc = u + c * 5 * b;
+        double ub[5];
+        for (int v = 0; v < 5; ++v) ub[v] = uc[v * b];
+        double mb[3] = {ub[1], ub[2], ub[3]};
+        if (!(ub[0] > eps) || !(adi_pressure(gamma, ub[0], mb, ub[4]) > eps)) {
+            status |= ORC_FAIL;
+            continue;
+        }
+        double rmin = INFINITY;
+        for (int j = 0; j < npt; ++j) {
+            const double* ph = j < nq ? T.phi + j * b : T.phif + (size_t)(j - nq) * b;
+            double r = eval(&T, uc, ph);
+            if (r < rmin) rmin = r;
+        }
+        double th_r = rmin < eps ? (ub[0] - eps) / (ub[0] - rmin) : 1.0;
+        double th_p = 1.0;
+        for (int j = 0; j < npt; ++j) {
+            const double* ph = j < nq ? T.phi + j * b : T.phif + (size_t)(j - nq) * b;
+            double uq[5], dv[5];
+            for (int v = 0; v < 5; ++v) {
+                uq[v] = ub[v] + th_r * (eval(&T, uc + v * b, ph) - ub[v]);
+                dv[v] = uq[v] - ub[v];
+            }
+            double mq[3] = {uq[1], uq[2], uq[3]};
+            if (adi_pressure(gamma, uq[0], mq, uq[4]) < eps) {
+                double t = adi_pressure_root(gamma, eps, ub, dv);
+                if (t < th_p) th_p = t;
+            }
+        }
+        double th = th_r * th_p;
+        if (th < 1.0) {
+            for (int v = 0; v < 5; ++v)
+                for (int l = 1; l < b; ++l) uc[v * b + l] *= th;
+            status |= ORC_LIMITED;
+        }
+    }
+    tabs_free(&T);
+    return status;
+}
+
+int orc_adi_step(const orc_cfg* cfg, double gamma, double* u, double dt)
+{
+    int b = orc_nmodes(cfg->k);
+    size_t n = (size_t)cfg->N * cfg->N * cfg->N * 5 * b;
+    double* un = (double*)malloc(sizeof(double) * n);
+    double* us = (double*)malloc(sizeof(double) * n);
+    double* L = (double*)malloc(sizeof(double) * n);
+    memcpy(un, u, sizeof(double) * n);
+    memcpy(us, u, sizeof(double) * n);
+    int status = 0;
+    static const double a2[2] = {0.0, 0.5}, b2[2] = {1.0, 0.5};
+    static const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double* A = (cfg->rk_stages == 2) ? a2 : a3;
+    const double* B = (cfg->rk_stages == 2) ? b2 : b3;
+    for (int s = 0; s < cfg->rk_stages; ++s) {
+        orc_adi_rhs(cfg, gamma, us, dt, L);
+        for (size_t i = 0; i < n; ++i) us[i] = A[s] * un[i] + B[s] * (us[i] + dt * L[i]);
+        status |= orc_adi_limit(cfg, gamma, us);
+    }
+    memcpy(u, us, sizeof(double) * n);
+    free(un);
+    free(us);
+    free(L);
+    return status;
+}
+
+/* nsteps steps with dt from the CFL condition of each step's start (fixed_dt
+ * > 0: that dt), halved up to three times when a stage fails */
+int orc_adi_run(const orc_cfg* cfg, double gamma, double* u, int nsteps, double fixed_dt, double* t, double* dt_last)
+{
+    int b = orc_nmodes(cfg->k);
+    size_t n = (size_t)cfg->N * cfg->N * cfg->N * 5 * b;
+    double* bak = (double*)malloc(sizeof(double) * n);
+    int rc = 0;
+    for (int st = 0; st < nsteps; ++st) {
+        double dt = fixed_dt > 0.0 ? fixed_dt : orc_adi_dt(cfg, gamma, u);
+        int status = ORC_FAIL;
+        double dtt = dt;
+        memcpy(bak, u, sizeof(double) * n);
+        for (int r = 0; r <= 3; ++r) {
+            dtt = dt / (double)(1 << r);
+            status = orc_adi_step(cfg, gamma, u, dtt);
+            if (!(status & ORC_FAIL)) break;
+            memcpy(u, bak, sizeof(double) * n);
+        }
+        if (status & ORC_FAIL) {
+            rc = -1;
+            break;
+        }
+        *t += dtt;
+        if (dt_last) *dt_last = dtt;
+    }
+    free(bak);
+    return rc;
+}

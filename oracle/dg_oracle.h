@@ -85,6 +85,17 @@ int orc_limit(const orc_cfg* cfg, double* u);
 double orc_pi_nu(const orc_cfg* cfg, double rho, double divv, double nu, double dt);
 int orc_rhs_nu(const orc_cfg* cfg, const double* u, const double* ahat, double dt_pimax, const double* nu_cell,
                double* dudt);
+/* adiabatic system: state [c][5][b] (rho, m, e), primitives [c][4][b] (v, p) */
+void orc_adi_flux(double gamma, int d, const double U[5], double F[5]);
+void orc_adi_rusanov(double gamma, int d, const double WL[5], const double WR[5], double F[5]);
+double orc_adi_vnr(const orc_cfg* cfg, double rho, double c, double divv, double dt);
+void orc_adi_project(const orc_cfg* cfg, double gamma, const double* u, double* prim);
+int orc_adi_rhs(const orc_cfg* cfg, double gamma, const double* u, double dt_pimax, double* dudt);
+double orc_adi_dt(const orc_cfg* cfg, double gamma, const double* u);
+int orc_adi_limit(const orc_cfg* cfg, double gamma, double* u);
+int orc_adi_step(const orc_cfg* cfg, double gamma, double* u, double dt);
+int orc_adi_run(const orc_cfg* cfg, double gamma, double* u, int nsteps, double fixed_dt, double* t,
+                double* dt_last);
 int orc_rhs_local(const orc_cfg* cfg, const double* patch, const double* ahat_c, const double abar[3],
                   double dt_pimax, const double* nu, int64_t n, double* out);
 void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, double* y);

@@ -92,6 +92,17 @@ def lib():
         _lib.orc_forcing_project.argtypes = [C.POINTER(Cfg), C.c_int, C.POINTER(C.c_int32), d, d]
         _lib.orc_rhs_nu.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d, d]
         _lib.orc_rhs_local.argtypes = [C.POINTER(Cfg), d, d, d, C.c_double, d, C.c_int64, d]
+        _lib.orc_adi_flux.argtypes = [C.c_double, C.c_int, d, d]
+        _lib.orc_adi_rusanov.argtypes = [C.c_double, C.c_int, d, d, d]
+        _lib.orc_adi_vnr.restype = C.c_double
+        _lib.orc_adi_vnr.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double, C.c_double]
+        _lib.orc_adi_project.argtypes = [C.POINTER(Cfg), C.c_double, d, d]
+        _lib.orc_adi_rhs.argtypes = [C.POINTER(Cfg), C.c_double, d, C.c_double, d]
+        _lib.orc_adi_dt.restype = C.c_double
+        _lib.orc_adi_dt.argtypes = [C.POINTER(Cfg), C.c_double, d]
+        _lib.orc_adi_limit.argtypes = [C.POINTER(Cfg), C.c_double, d]
+        _lib.orc_adi_step.argtypes = [C.POINTER(Cfg), C.c_double, d, C.c_double]
+        _lib.orc_adi_run.argtypes = [C.POINTER(Cfg), C.c_double, d, C.c_int, C.c_double, d, d]
         _lib.orc_av_features.argtypes = [C.POINTER(Cfg), d, C.c_double, d, d]
         _lib.orc_pi_nu.restype = C.c_double
         _lib.orc_pi_nu.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double, C.c_double]
@@ -377,3 +388,57 @@ def power_spectrum(cfg: Cfg, u: np.ndarray, nbins: int):
 def splitmix64(state: int, n: int) -> list[int]:
     s = C.c_uint64(state)
     return [lib().orc_splitmix64(C.byref(s)) for _ in range(n)]
+
+
+# ---- adiabatic system: u [N^3][5][b] = (rho, m, e), primitives [N^3][4][b] = (v, p) ----
+def adi_flux(gamma: float, d: int, U) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    F = np.zeros(5)
+    lib().orc_adi_flux(gamma, d, _p(U), _p(F))
+    return F
+
+
+def adi_rusanov(gamma: float, d: int, WL, WR) -> np.ndarray:
+    """Rusanov flux from primitive face states (rho, v_x, v_y, v_z, p)."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.zeros(5)
+    lib().orc_adi_rusanov(gamma, d, _p(WL), _p(WR), _p(F))
+    return F
+
+
+def adi_vnr(cfg: Cfg, rho: float, c: float, divv: float, dt_: float) -> float:
+    return lib().orc_adi_vnr(C.byref(cfg), rho, c, divv, dt_)
+
+
+def adi_project(cfg: Cfg, gamma: float, u: np.ndarray) -> np.ndarray:
+    out = np.zeros((cfg.N ** 3, 4, nmodes(cfg.k)))
+    lib().orc_adi_project(C.byref(cfg), gamma, _p(u), _p(out))
+    return out
+
+
+def adi_rhs(cfg: Cfg, gamma: float, u: np.ndarray, dt_pimax: float = 0.0) -> np.ndarray:
+    out = np.zeros((cfg.N ** 3, 5, nmodes(cfg.k)))
+    lib().orc_adi_rhs(C.byref(cfg), gamma, _p(u), dt_pimax, _p(out))
+    return out
+
+
+def adi_dt(cfg: Cfg, gamma: float, u: np.ndarray) -> float:
+    return lib().orc_adi_dt(C.byref(cfg), gamma, _p(u))
+
+
+def adi_limit(cfg: Cfg, gamma: float, u: np.ndarray) -> int:
+    """Positivity of density and pressure, in place; returns the status bits."""
+    return lib().orc_adi_limit(C.byref(cfg), gamma, _p(u))
+
+
+def adi_step(cfg: Cfg, gamma: float, u: np.ndarray, dt_: float) -> int:
+    return lib().orc_adi_step(C.byref(cfg), gamma, _p(u), dt_)
+
+
+def adi_run(cfg: Cfg, gamma: float, u: np.ndarray, nsteps: int, fixed_dt: float = 0.0, t: float = 0.0):
+    """Advance u in place; returns (rc, t, dt_last)."""
+    tt = C.c_double(t)
+    dl = C.c_double(0.0)
+    rc = lib().orc_adi_run(C.byref(cfg), gamma, _p(u), nsteps, fixed_dt, C.byref(tt), C.byref(dl))
+    return rc, tt.value, dl.value

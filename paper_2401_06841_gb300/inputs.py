@@ -78,6 +78,28 @@ def _axis_factors(N: int, k: int, kap: int) -> np.ndarray:
     return np.exp(2j * np.pi * kap * xc)[:, None] * g[None, :]
 
 
+def random_energy_state(N: int, k: int, seed: int, p_mean: float = 1.5, p_spread: float = 0.5,
+                        wiggle: float = 0.05, gamma: float = 1.4, **kw) -> np.ndarray:
+    """Random coefficients [N^3][5][b] for a five-variable state (rho, m, e):
+    rho and m from ``random_state`` (same seed and keywords); the cell mean of
+    e gives a mean pressure p uniform in p_mean*[1-p_spread/2, 1+p_spread/2]
+    with the cell-mean kinetic energy density |m_0|^2/(2 rho_0); the higher
+    modes of e are Gaussian, wiggle * e_0 times decay**degree."""
+    u4 = random_state(N, k, seed, **kw)
+    rng = np.random.default_rng(seed + 7919)
+    b = nmodes(k)
+    nc = N ** 3
+    deg = mode_degrees(k).sum(axis=1)
+    u = np.zeros((nc, 5, b))
+    u[:, :4] = u4
+    p0 = p_mean * (1.0 + p_spread * (rng.random(nc) - 0.5))
+    e0 = p0 / (gamma - 1.0) + 0.5 * (u4[:, 1:, 0] ** 2).sum(axis=1) / u4[:, 0, 0]
+    u[:, 4, 0] = e0
+    if b > 1:
+        u[:, 4, 1:] = rng.standard_normal((nc, b - 1)) * wiggle * kw.get("decay", 0.6) ** deg[1:] * e0[:, None]
+    return u
+
+
 def fourier_coeffs(N: int, k: int, kvec) -> np.ndarray:
     """Exact modal coefficients [N^3][b] (complex) of exp(2 pi i kvec . x)."""
     ijl = mode_degrees(k)
