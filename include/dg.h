@@ -374,6 +374,61 @@ int dg_analysis_bytes(const dg_mesh* mesh, int order, size_t* bytes);
 int dg_power_spectrum(dg_ctx* ctx, void* work, size_t work_bytes, int nbins, double* kmean, double* power,
                       int64_t* count);
 
+/* ---- adiabatic system (Sec. 2.1) -----------------------------------------
+ * Five conserved variables per cell, u[cell][var][mode] with var = (rho,
+ * m_x, m_y, m_z, e), e the total energy density; ideal-gas equation of state
+ * p = (gamma - 1)(e - |m|^2/(2 rho)); flux F_d = (m_d, m v_d + p e_d,
+ * (e + p) v_d).  Same mesh, basis, quadrature, SSP-RK schemes and CFL rule
+ * as the isothermal context, with the local sound speed c = sqrt(gamma p /
+ * rho) in the CFL bound sum_d(|v_d| + c) and in the bulk term of the vNR
+ * viscous pressure, which is added to p in the momentum and energy fluxes at
+ * the volume points (Sec. 3.1).  Face states: rho from its own expansion, v
+ * and p from their Gauss projections (Sec. 3.2); Rusanov flux with lambda =
+ * max(|v_n| + c).  Positivity after every stage: density and pressure at all
+ * volume and face points at or above nu->rho_floor (the floor of both); the
+ * higher modes of all five variables are scaled by theta_rho theta_p toward
+ * the cell mean (theta_p the largest factor keeping p at the floor, from the
+ * quadratic in theta); a cell mean at or below the floor fails the step,
+ * which is retried with dt/2 up to three times.  FP32 or FP64 (no x3, no
+ * forcing, no learned sensor, no diffusion: DG_EINVAL). */
+typedef struct dg_adi_ctx dg_adi_ctx;
+typedef struct {
+    int32_t precision;     /* DG_PREC_F32 or DG_PREC_F64                          */
+    int32_t rk_stages;     /* 2 or 3                                              */
+    double cfl;            /* dt = cfl h / ((k+1) max sum_d(|v_d| + c))           */
+    double gamma;          /* adiabatic index, > 1                                */
+    void* stream;          /* cudaStream_t; must not be NULL                      */
+    void* u[3];            /* three state registers of N^3*5*b elements           */
+    void* prim;            /* N^3*4*b elements: projections of v_x, v_y, v_z, p   */
+    void* scratch;         /* >= scratch bytes of dg_adi_buffer_bytes, 256-aligned */
+    size_t scratch_bytes;
+} dg_adi_opts;
+/* Sizes in bytes of one state register, the projection buffer and the scratch. */
+int dg_adi_buffer_bytes(const dg_mesh* mesh, int order, int precision, size_t* state_bytes, size_t* prim_bytes,
+                        size_t* scratch_bytes);
+/* nu: mode DG_AV_OFF or DG_AV_VNR (alpha, beta, rho_floor); the buffers are
+ * caller-owned device memory that must outlive the context. */
+int dg_adi_init(dg_adi_ctx** ctx, const dg_mesh* mesh, int order, const dg_nu_params* nu, const dg_adi_opts* opts);
+void dg_adi_free(dg_adi_ctx* ctx);
+const char* dg_adi_last_error(const dg_adi_ctx* ctx);
+/* Copy a state [N^3][5][b] in (resets the time) or out; host or device memory. */
+int dg_adi_set_state(dg_adi_ctx* ctx, const void* src, int src_on_host);
+int dg_adi_get_state(dg_adi_ctx* ctx, void* dst, int to_host);
+/* Projections of v and p of a device state into prim_out [N^3][4][b]. */
+int dg_adi_project(dg_adi_ctx* ctx, const void* u_in, void* prim_out);
+/* Right-hand side du/dt of a device state (dt_pimax: dt of the viscous-pressure
+ * cap, 0 = uncapped); uses the context's projection buffer. */
+int dg_adi_rhs(dg_adi_ctx* ctx, const void* u_in, void* dudt, double dt_pimax);
+/* nsteps SSP-RK steps (fixed_dt > 0 replaces the CFL dt); *t_out the time
+ * since dg_adi_set_state, *dt_last the last step's dt.  Synchronises once per
+ * step to read the positivity status; DG_EPOSITIVITY leaves the state at the
+ * start of the failed step. */
+int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_last);
+/* FP64 diagnostics of the current state: out[0..7] = mass, momentum (3),
+ * total energy (integrals over the box), kinetic energy (volume quadrature of
+ * |m|^2/(2 rho)), minimum density and minimum pressure at the volume points. */
+int dg_adi_totals(dg_adi_ctx* ctx, double* out);
+
 #ifdef __cplusplus
 }
 #endif

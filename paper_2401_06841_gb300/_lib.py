@@ -36,6 +36,12 @@ class Opts(C.Structure):
                 ("scratch_bytes", C.c_size_t), ("riemann", C.c_int32)]
 
 
+class AdiOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("rk_stages", C.c_int32), ("cfl", C.c_double), ("gamma", C.c_double),
+                ("stream", C.c_void_p), ("u", C.c_void_p * 3), ("prim", C.c_void_p), ("scratch", C.c_void_p),
+                ("scratch_bytes", C.c_size_t)]
+
+
 class Forcing(C.Structure):
     _fields_ = [("on", C.c_int32), ("kmin2", C.c_int32), ("kmax2", C.c_int32), ("zeta", C.c_double),
                 ("mach", C.c_double), ("seed", C.c_uint64), ("t_off", C.c_double)]
@@ -106,6 +112,19 @@ def lib() -> C.CDLL:
         L.dg_mlp_forward.argtypes = [vp, vp, C.c_int64, vp]
         L.dg_av_nu.argtypes = [vp, vp]
         L.dg_av_nu_carried.argtypes = [vp, vp]
+        sz = C.POINTER(C.c_size_t)
+        L.dg_adi_buffer_bytes.argtypes = [C.POINTER(Mesh), i, i, sz, sz, sz]
+        L.dg_adi_init.argtypes = [C.POINTER(vp), C.POINTER(Mesh), i, C.POINTER(NuParams), C.POINTER(AdiOpts)]
+        L.dg_adi_free.argtypes = [vp]
+        L.dg_adi_free.restype = None
+        L.dg_adi_last_error.argtypes = [vp]
+        L.dg_adi_last_error.restype = C.c_char_p
+        L.dg_adi_set_state.argtypes = [vp, vp, i]
+        L.dg_adi_get_state.argtypes = [vp, vp, i]
+        L.dg_adi_project.argtypes = [vp, vp, vp]
+        L.dg_adi_rhs.argtypes = [vp, vp, vp, d]
+        L.dg_adi_step.argtypes = [vp, i, d, C.POINTER(d), C.POINTER(d)]
+        L.dg_adi_totals.argtypes = [vp, C.POINTER(d)]
         L.dg_rhs_noalloc.argtypes = [C.POINTER(Mesh), i, d, C.POINTER(NuParams), i, vp, vp, vp, d, vp]
         L.dg_profile.argtypes = [vp, i]
         L.dg_profile_read.argtypes = [vp, C.POINTER(Prof)]
@@ -123,7 +142,9 @@ EXPORTS = ("dg_scratch_bytes", "dg_vhat_bytes", "dg_init", "dg_free", "dg_last_e
            "dg_diagnostics", "dg_l1_density", "dg_get_meta", "dg_set_meta", "dg_profile", "dg_profile_read",
            "dg_rhs_noalloc", "dg_av_param_count", "dg_set_av_weights", "dg_get_av_weights", "dg_generate_pairs",
            "dg_mlp_train", "dg_mlp_grad", "dg_mlp_forward", "dg_av_nu", "dg_av_nu_carried", "dg_density_pdf", "dg_structure_function",
-           "dg_analysis_bytes", "dg_power_spectrum")
+           "dg_analysis_bytes", "dg_power_spectrum", "dg_adi_buffer_bytes", "dg_adi_init", "dg_adi_free",
+           "dg_adi_last_error", "dg_adi_set_state", "dg_adi_get_state", "dg_adi_project", "dg_adi_rhs",
+           "dg_adi_step", "dg_adi_totals")
 
 MAX_BINS = 2000
 

@@ -1,0 +1,96 @@
+// dg_adi.cu -- launchers of the adiabatic-system kernels (FP32, FP64; k = 1..3).
+#include "dg_adi.cuh"
+#include "dg_launch.cuh"
+
+namespace dg {
+
+namespace {
+
+template <typename T, int K, int MODE>
+int adi_blocks_per_sm()
+{
+    static int occ = -1;
+    if (occ < 0) {
+        const int sm = (int)(sizeof(T) * AdiCfg<K>::total);
+        cudaFuncSetAttribute(k_adi<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_adi<T, K, MODE>, AdiCfg<K>::NT, sm) != cudaSuccess)
+            o = 1;
+        occ = o < 1 ? 1 : o;
+    }
+    return occ;
+}
+
+template <typename T, int K, int MODE>
+cudaError_t adi_launch(const Launch& L, const AdiArgs<T>& a)
+{
+    using A = AdiCfg<K>;
+    const long ntile = (L.ncell + A::TC - 1) / A::TC;
+    long g = (long)adi_blocks_per_sm<T, K, MODE>() * L.nsm;
+    if (g > ntile) g = ntile;
+    if (g < 1) g = 1;
+    k_adi<T, K, MODE><<<(int)g, A::NT, sizeof(T) * A::total, L.st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int K>
+cudaError_t adi_k(const Launch& L, double gamma, const AdiLaunch& t)
+{
+    AdiArgs<T> a{};
+    a.u_in = static_cast<const T*>(t.u_in);
+    a.u_n = static_cast<const T*>(t.u_n);
+    a.out = static_cast<T*>(t.out);
+    a.pr_in = static_cast<const T*>(t.pr_in);
+    a.pr_out = static_cast<T*>(t.pr_out);
+    a.tab = static_cast<const T*>(L.ttab);
+    a.ctl = L.ctl;
+    a.ncell = L.ncell;
+    a.N = L.N;
+    a.ph = L.ph;
+    a.gamma = gamma;
+    a.rk_a = T(t.rk_a);
+    a.rk_b = T(t.rk_b);
+    a.dt_pimax = t.dt_pimax;
+    a.flags = t.flags;
+    if (t.mode == ADI_PROJECT) return adi_launch<T, K, ADI_PROJECT>(L, a);
+    if (t.mode == ADI_RHS) return adi_launch<T, K, ADI_RHS>(L, a);
+    return adi_launch<T, K, ADI_STAGE>(L, a);
+}
+
+template <typename T, int K>
+cudaError_t adi_totals_k(const Launch& L, double gamma, const void* u, double* partials, int* nblocks)
+{
+    long g = (L.ncell + 255) / 256;
+    if (g > 4L * L.nsm) g = 4L * L.nsm;
+    if (g > kMaxGrid) g = kMaxGrid;
+    if (g < 1) g = 1;
+    *nblocks = (int)g;
+    k_adi_totals<T, K><<<(int)g, 256, 0, L.st>>>(static_cast<const T*>(u), static_cast<const T*>(L.ttab), L.ncell,
+                                                 gamma, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_adi(const Launch& L, double gamma, const AdiLaunch& t)
+{
+    if (L.K == 1) return adi_k<T, 1>(L, gamma, t);
+    if (L.K == 2) return adi_k<T, 2>(L, gamma, t);
+    return adi_k<T, 3>(L, gamma, t);
+}
+
+template <typename T>
+cudaError_t launch_adi_totals(const Launch& L, double gamma, const void* u, double* partials, int* nblocks)
+{
+    if (L.K == 1) return adi_totals_k<T, 1>(L, gamma, u, partials, nblocks);
+    if (L.K == 2) return adi_totals_k<T, 2>(L, gamma, u, partials, nblocks);
+    return adi_totals_k<T, 3>(L, gamma, u, partials, nblocks);
+}
+
+template cudaError_t launch_adi<float>(const Launch&, double, const AdiLaunch&);
+template cudaError_t launch_adi<double>(const Launch&, double, const AdiLaunch&);
+template cudaError_t launch_adi_totals<float>(const Launch&, double, const void*, double*, int*);
+template cudaError_t launch_adi_totals<double>(const Launch&, double, const void*, double*, int*);
+
+}  // namespace dg

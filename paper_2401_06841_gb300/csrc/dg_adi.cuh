@@ -1,0 +1,651 @@
+// dg_adi.cuh -- kernels of the adiabatic system (Sec. 2.1): five conserved
+// variables u = (rho, m, e) per cell with the ideal-gas equation of state
+// p = (gamma - 1)(e - |m|^2 / (2 rho)) and the flux
+//   F_d = (m_d, m v_d + p e_d, (e + p) v_d).
+// Tile-batched like the isothermal kernels (TC cells per block iteration,
+// CUDA-core block products against the same basis tables), FP32 or FP64.
+//
+// Modes of k_adi:
+//   ADI_PROJECT  projections of v and p of u_in (Sec. 3.2) -> pr_out, with the
+//                CFL bound max sum_d(|v_d| + c) over the volume points (F_DT)
+//   ADI_RHS      right-hand side of u_in -> out
+//   ADI_STAGE    right-hand side, SSP-RK stage combine, positivity of density
+//                and pressure (Sec. 3.1) -> out = u^(s+1)
+// The right-hand side needs the projections of u_in in pr_in.
+#pragma once
+
+#include "dg_launch.cuh"
+#include "dg_tile.cuh"
+
+namespace dg {
+
+template <typename T>
+struct AdiArgs {
+    const T* u_in;   // [c][5][b]
+    const T* u_n;    // u^n (stage mode)
+    T* out;          // dudt or u^(s+1) [c][5][b]
+    const T* pr_in;  // [c][4][b] projections of v_x, v_y, v_z, p of u_in
+    T* pr_out;       // projection mode output [c][4][b]
+    const T* tab;    // TileTab<K, BK_FMA> tables of the element type
+    Ctl* ctl;
+    long ncell;
+    int N;
+    Phys ph;         // h, hp, alpha, beta, floor_ (density and pressure floor), av_mode
+    double gamma;
+    T rk_a, rk_b;
+    double dt_pimax; // right-hand-side mode: dt of the viscous-pressure cap
+    int flags;       // F_DT (projection mode)
+};
+
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+template <int K>
+struct AdiCfg {
+    using C = TileCfg<K, BK_FMA>;
+    static constexpr int b = C::b, nq = C::nq, ns = C::ns, nf = C::nf, TC = C::TC, NT = C::NT;
+    static constexpr int KP = C::KP, NQP = C::NQP, NP = C::NP, B2K = C::B2K, NSP = C::NSP, B2N = C::B2N;
+    static constexpr int FE = 12;  // rho, m_x, m_y, m_z, e, grad rho (3), div m, 3 zero rows
+    static constexpr int FP = 9;   // m v + P (6 symmetric components), (e + P) v (3)
+    static constexpr int LDA = KP, LDV = NQP + 4, LDP = NP, LDC2 = B2K, LDT = NSP + 4, LDL = B2N;
+    static constexpr int RE = TC * FE, RP = TC * FP;
+    static constexpr int RC = TC * 20;  // face rows ((cell, side, self/neighbour), (rho, v_x, v_y, v_z, p))
+    static constexpr int RL = TC * 10;  // flux rows ((cell, side), variable)
+    static constexpr int oU = r4(C::tabsz);
+    static constexpr int oPr = oU + r4(TC * 5 * b);
+    static constexpr int oR = oPr + r4(TC * 4 * b);
+    static constexpr int oUn = oR + r4(TC * 5 * b);
+    static constexpr int oA = oUn + r4(TC * 5 * b);
+    static constexpr int SZA = cmax(RE * LDA, RP * LDP);
+    static constexpr int oBig = oA + r4(SZA);
+    static constexpr int FA = cmax(RC * LDC2, RL * LDT);
+    static constexpr int FB = cmax(RC * LDT, RL * LDL);
+    static constexpr int BIG = cmax(RE * LDV, FA + FB);
+    static constexpr int total = oBig + BIG;
+};
+
+// Rusanov flux along Dd from primitive face states W = (rho, v_x, v_y, v_z, p):
+// 1/2 (F(U_L) + F(U_R)) - 1/2 lambda (U_R - U_L), lambda = max(|v_n| + c)
+template <typename T, int Dd>
+__device__ __forceinline__ void adi_rusanov(T gamma, const T* WL, const T* WR, T* F)
+{
+    const T g1 = gamma - T(1);
+    T UL[5], UR[5], FL[5], FR[5], ls[2];
+    const T* W[2] = {WL, WR};
+    T* U[2] = {UL, UR};
+    T* Fx[2] = {FL, FR};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const T* w = W[s];
+        const T rho = w[0], vn = w[1 + Dd], p = w[4];
+        U[s][0] = rho;
+        U[s][1] = rho * w[1];
+        U[s][2] = rho * w[2];
+        U[s][3] = rho * w[3];
+        U[s][4] = p / g1 + T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        Fx[s][0] = U[s][1 + Dd];
+        Fx[s][1] = U[s][1] * vn;
+        Fx[s][2] = U[s][2] * vn;
+        Fx[s][3] = U[s][3] * vn;
+        Fx[s][1 + Dd] += p;
+        Fx[s][4] = (U[s][4] + p) * vn;
+        ls[s] = fabs(vn) + sqrt(gamma * p / rho);
+    }
+    // the larger of the two (a NaN of the right state propagates, as in the oracle)
+    const T lam = ls[0] > ls[1] ? ls[0] : ls[1];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] = T(0.5) * (FL[v] + FR[v]) - T(0.5) * lam * (UR[v] - UL[v]);
+}
+
+// vNR viscous pressure with the local sound speed c in the bulk term
+template <typename T>
+__device__ __forceinline__ T adi_vnr(const Phys& P, T rho, T c, T divv, T dt)
+{
+    if (P.av_mode != 1 || !(divv < T(0))) return T(0);
+    const T a = -divv, hp = T(P.hp);
+    T Pi = T(P.alpha) * rho * hp * hp * a * a + T(P.beta) * rho * c * hp * a;
+    if (dt > T(0)) {
+        const T Pm = T(0.5) * rho * hp * hp * a / dt;
+        Pi = Pi > Pm ? Pm : Pi;
+    }
+    return Pi;
+}
+
+// smallest t in [0, 1] with p(ub + t d) = eps (p(ub) > eps > p(ub + d)): the
+// root of rho e - |m|^2/2 - eps rho/(gamma-1), quadratic in t
+template <typename T>
+__device__ __forceinline__ T adi_pressure_root(T gamma, T eps, const T* ub, const T* dv)
+{
+    const T g1 = eps / (gamma - T(1));
+    const T A = dv[0] * dv[4] - T(0.5) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[3] * dv[3]);
+    const T B = ub[0] * dv[4] + dv[0] * ub[4] - (ub[1] * dv[1] + ub[2] * dv[2] + ub[3] * dv[3]) - g1 * dv[0];
+    const T C = ub[0] * ub[4] - T(0.5) * (ub[1] * ub[1] + ub[2] * ub[2] + ub[3] * ub[3]) - g1 * ub[0];
+    T t;
+    if (fabs(A) <= T(1e-14) * (fabs(B) + fabs(C))) {
+        t = -C / B;
+    } else {
+        T disc = B * B - T(4) * A * C;
+        disc = disc < T(0) ? T(0) : disc;
+        const T sq = sqrt(disc);
+        const T r1 = (-B - sq) / (T(2) * A), r2 = (-B + sq) / (T(2) * A);
+        const T lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
+        t = (lo >= T(0) && lo <= T(1)) ? lo : hi;
+    }
+    t = t < T(0) ? T(0) : t;
+    return t > T(1) ? T(1) : t;
+}
+
+template <typename T>
+__device__ __forceinline__ T adi_p(T gamma, T rho, T mx, T my, T mz, T e)
+{
+    return (gamma - T(1)) * (e - T(0.5) * (mx * mx + my * my + mz * mz) / rho);
+}
+
+// copy n elements (a multiple of 4) of a tile from global to shared; elements
+// past `valid` get the filler state of a cell (rho = 1, e = 1/(gamma-1): p = 1)
+template <typename T, int NT, int NV, int B>
+__device__ __forceinline__ void adi_load(T* dst, const T* src, int n, int valid, T fill_e)
+{
+    for (int e = 4 * threadIdx.x; e < n; e += 4 * NT) {
+        T v[4];
+        ld4_guard<T>(src, e, valid, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (e + j >= valid) {
+                const int r = (e + j) % (NV * B);
+                v[j] = (r == 0) ? T(1) : (NV == 5 && r == 4 * B) ? fill_e : T(0);
+            }
+        }
+        st4<T>(dst + e, v);
+    }
+}
+
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(256) k_adi(AdiArgs<T> a)
+{
+    using A = AdiCfg<K>;
+    using C = TileCfg<K, BK_FMA>;
+    using TT = TileTab<K, BK_FMA>;
+    constexpr int b = A::b, nq = A::nq, ns = A::ns, nf = A::nf, TC = A::TC, NT = A::NT;
+    constexpr int KP = A::KP, NQP = A::NQP, NP = A::NP, B2K = A::B2K, NSP = A::NSP, B2N = A::B2N;
+    constexpr int FE = A::FE, LDA = A::LDA, LDV = A::LDV, LDP = A::LDP, LDC2 = A::LDC2, LDT = A::LDT;
+    constexpr int LDL = A::LDL, RE = A::RE, RP = A::RP, RC = A::RC, RL = A::RL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    T* sU = sm + A::oU;
+    T* sPr = sm + A::oPr;
+    T* sR = sm + A::oR;
+    T* sUn = sm + A::oUn;
+    T* sA = sm + A::oA;
+    T* sP = sA;
+    T* sBig = sm + A::oBig;
+    __shared__ unsigned int s_status;
+    __shared__ unsigned long long s_smax;
+
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < C::tabsz; e += NT) sm[e] = a.tab[e];
+    const T* tabs = sm;
+    if (tid == 0) {
+        s_status = 0u;
+        s_smax = 0ull;
+    }
+    const T gamma = T(a.gamma), g1 = gamma - T(1), fill_e = T(1) / g1;
+    const T two_h = T(2.0 / a.ph.h), inv4h = T(0.25 / a.ph.h);
+    const T eps = T(a.ph.floor_);
+    T dt = T(a.dt_pimax);
+    if constexpr (MODE == ADI_STAGE) {
+        // the step's dt: CFL bound of u^n (projection of stage 1), prescribed dt, retry factor
+        const double smax = __longlong_as_double((long long)a.ctl->smax);
+        const double dtd = (a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / smax) * a.ctl->dt_scale;
+        dt = T(dtd);
+        if (blockIdx.x == 0 && tid == 0) a.ctl->dt = dtd;
+    }
+    // sup |phi_m| of the mode m = lane (positivity bound), 0 past the modes
+    T my_sup = T(0);
+    static_for<0, b>([&](auto m) {
+        if (lane == decltype(m)::value) my_sup = T(sup_phi<K>(decltype(m)::value));
+    });
+    T smax = T(0);
+    __syncthreads();
+
+    const long ntile = (a.ncell + TC - 1) / TC;
+    for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const long c0 = tile * TC;
+        const int nvalid = (int)((a.ncell - c0) < TC ? (a.ncell - c0) : TC);
+        adi_load<T, NT, 5, b>(sU, a.u_in + c0 * 5 * b, TC * 5 * b, nvalid * 5 * b, fill_e);
+        if constexpr (MODE == ADI_PROJECT) {
+            __syncthreads();
+            // rho, m, e at the volume points
+            for (int e = tid; e < TC * 5 * KP; e += NT) {
+                const int r = e / KP, l = e % KP;
+                sA[r * LDA + l] = l < b ? sU[r * b + l] : T(0);
+            }
+            __syncthreads();
+            mm<T, BK_FMA, TC * 5, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sBig);
+            __syncthreads();
+            constexpr int PER = (TC * NQP + NT - 1) / NT;
+            T f[PER][4];
+#pragma unroll
+            for (int it = 0; it < PER; ++it) {
+                const int e = tid + it * NT;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) f[it][i] = T(0);
+                if (e < TC * NQP) {
+                    const int c = e / NQP, q = e % NQP;
+                    if (q < nq) {
+                        const T* v = sBig + (c * 5) * LDV + q;
+                        const T rho = v[0], ir = rcp<T>(rho);
+                        const T mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV];
+                        f[it][0] = mx * ir;
+                        f[it][1] = my * ir;
+                        f[it][2] = mz * ir;
+                        f[it][3] = adi_p<T>(gamma, rho, mx, my, mz, v[4 * LDV]);
+                        if ((a.flags & F_DT) && c < nvalid) {
+                            const T cs = sqrt(gamma * f[it][3] * ir);
+                            const T sp = fabs(f[it][0]) + fabs(f[it][1]) + fabs(f[it][2]) + T(3) * cs;
+                            smax = sp > smax ? sp : smax;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int it = 0; it < PER; ++it) {
+                const int e = tid + it * NT;
+                if (e < TC * NQP) {
+                    const int c = e / NQP, q = e % NQP;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) sBig[(c * 4 + i) * LDV + q] = f[it][i];
+                }
+            }
+            __syncthreads();
+            mm<T, BK_FMA, TC * 4, NP, NQP, LDV, LDP, NT>(sBig, tabs, C::oWPhi, sP);
+            __syncthreads();
+            for (int e = tid; e < nvalid * 4 * b; e += NT) {
+                const int r = e / b, l = e % b;
+                a.pr_out[c0 * 4 * b + e] = sP[r * LDP + l];
+            }
+            __syncthreads();
+        } else {
+        // ---- right-hand side: stage the projections (and u^n) of the tile ----
+        for (int e = 4 * tid; e < TC * 4 * b; e += 4 * NT) {
+            T v[4];
+            ld4_guard<T>(a.pr_in + c0 * 4 * b, e, nvalid * 4 * b, v);
+            st4<T>(sPr + e, v);
+        }
+        if constexpr (MODE == ADI_STAGE) {
+            if (a.rk_a != T(0)) adi_load<T, NT, 5, b>(sUn, a.u_n + c0 * 5 * b, TC * 5 * b, nvalid * 5 * b, fill_e);
+        }
+        __syncthreads();
+        // ---- evaluation coefficients: rho, m, e, grad rho, div m (field-major threads) ----
+        for (int e = tid; e < RE; e += NT) {
+            const int f = e / TC, c = e % TC;
+            const T* u = sU + c * 5 * b;
+            T* row = sA + (c * FE + f) * LDA;
+            T out[KP];
+#pragma unroll
+            for (int l = 0; l < KP; ++l) out[l] = T(0);
+            if (f < 5) {
+#pragma unroll
+                for (int l = 0; l < b; ++l) out[l] = u[f * b + l];
+            } else if (f == 5) {
+                modal_grad<T, K, 0>(u, out, two_h);
+            } else if (f == 6) {
+                modal_grad<T, K, 1>(u, out, two_h);
+            } else if (f == 7) {
+                modal_grad<T, K, 2>(u, out, two_h);
+            } else if (f == 8) {
+                T t2[b];
+                modal_grad<T, K, 0>(u + b, out, two_h);
+                modal_grad<T, K, 1>(u + 2 * b, t2, two_h);
+#pragma unroll
+                for (int l = 0; l < b; ++l) out[l] += t2[l];
+                modal_grad<T, K, 2>(u + 3 * b, t2, two_h);
+#pragma unroll
+                for (int l = 0; l < b; ++l) out[l] += t2[l];
+            }
+#pragma unroll
+            for (int l = 0; l < KP; l += 4) st4<T>(row + l, out + l);
+        }
+        __syncthreads();
+        mm<T, BK_FMA, RE, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sBig);
+        __syncthreads();
+        // ---- pointwise volume physics (Sec. 3.1: Pi at the internal points) ----
+        {
+            constexpr int PER = (TC * NQP + NT - 1) / NT;
+            T fl[PER][9];
+#pragma unroll
+            for (int it = 0; it < PER; ++it) {
+                const int e = tid + it * NT;
+#pragma unroll
+                for (int g = 0; g < 9; ++g) fl[it][g] = T(0);
+                if (e < TC * NQP) {
+                    const int c = e / NQP, q = e % NQP;
+                    if (q < nq) {
+                        const T* v = sBig + (c * FE) * LDV + q;
+                        const T rho = v[0], ir = rcp<T>(rho);
+                        const T mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV], en = v[4 * LDV];
+                        const T vx = mx * ir, vy = my * ir, vz = mz * ir;
+                        const T p = g1 * (en - T(0.5) * (mx * vx + my * vy + mz * vz));
+                        const T divv = (v[8 * LDV] - (vx * v[5 * LDV] + vy * v[6 * LDV] + vz * v[7 * LDV])) * ir;
+                        const T cs = sqrt(gamma * p * ir);
+                        const T P = p + adi_vnr<T>(a.ph, rho, cs, divv, dt);
+                        fl[it][0] = mx * vx + P;
+                        fl[it][1] = my * vy + P;
+                        fl[it][2] = mz * vz + P;
+                        fl[it][3] = mx * vy;
+                        fl[it][4] = mx * vz;
+                        fl[it][5] = my * vz;
+                        fl[it][6] = (en + P) * vx;
+                        fl[it][7] = (en + P) * vy;
+                        fl[it][8] = (en + P) * vz;
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int it = 0; it < PER; ++it) {
+                const int e = tid + it * NT;
+                if (e < TC * NQP) {
+                    const int c = e / NQP, q = e % NQP;
+#pragma unroll
+                    for (int g = 0; g < 9; ++g) sBig[(c * 9 + g) * LDV + q] = fl[it][g];
+                }
+            }
+        }
+        __syncthreads();
+        mm<T, BK_FMA, RP, NP, NQP, LDV, LDP, NT>(sBig, tabs, C::oWPhi, sP);
+        __syncthreads();
+        // ---- volume term in modal space: (2/h) sum_d D_d^T (projected flux along d) ----
+        for (int e = tid; e < TC * 5; e += NT) {
+            const int v = e / TC, c = e % TC;
+            T r[b];
+#pragma unroll
+            for (int l = 0; l < b; ++l) r[l] = T(0);
+            const T* P = sP + c * 9 * LDP;
+            if (v == 0) {
+                const T* u = sU + c * 5 * b;
+                modal_grad_T_acc<T, K, 0>(u + b, r, two_h);
+                modal_grad_T_acc<T, K, 1>(u + 2 * b, r, two_h);
+                modal_grad_T_acc<T, K, 2>(u + 3 * b, r, two_h);
+            } else if (v < 4) {
+                const int i = v - 1;
+                const int cx = (i == 0) ? 0 : (i == 1 ? 3 : 4);
+                const int cy = (i == 0) ? 3 : (i == 1 ? 1 : 5);
+                const int cz = (i == 0) ? 4 : (i == 1 ? 5 : 2);
+                modal_grad_T_acc<T, K, 0>(P + cx * LDP, r, two_h);
+                modal_grad_T_acc<T, K, 1>(P + cy * LDP, r, two_h);
+                modal_grad_T_acc<T, K, 2>(P + cz * LDP, r, two_h);
+            } else {
+                modal_grad_T_acc<T, K, 0>(P + 6 * LDP, r, two_h);
+                modal_grad_T_acc<T, K, 1>(P + 7 * LDP, r, two_h);
+                modal_grad_T_acc<T, K, 2>(P + 8 * LDP, r, two_h);
+            }
+#pragma unroll
+            for (int l = 0; l < b; ++l) sR[(c * 5 + v) * b + l] = r[l];
+        }
+        __syncthreads();
+        // ---- faces, one direction at a time (Sec. 3.2 face states, Rusanov) ----
+        T* sC2 = sBig;
+        T* sTr = sBig + A::FA;
+        T* sFs = sC2;
+        T* sL2 = sTr;
+        static_for<0, 3>([&](auto dd) {
+            constexpr int Dd = decltype(dd)::value;
+            // collapse rows r = ((c*2 + side)*2 + who)*5 + field: field 0 rho (own
+            // expansion), 1..4 the projections of v and p; who 1: the neighbour
+            for (int r = tid; r < RC; r += NT) {
+                const int field = r % 5, who = (r / 5) & 1, side = (r / 10) & 1, c = r / 20;
+                T cf[b];
+                int fside = side;
+                if (who == 0) {
+                    const T* src = field == 0 ? sU + c * 5 * b : sPr + (c * 4 + field - 1) * b;
+#pragma unroll
+                    for (int l = 0; l < b; ++l) cf[l] = src[l];
+                } else {
+                    fside = 1 - side;
+                    const long cc = c0 + c;
+                    if (cc < a.ncell) {
+                        int xyz[3];
+                        cell_xyz(cc, a.N, xyz[0], xyz[1], xyz[2]);
+                        const long nc = neighbour_along<Dd>(cc, xyz[Dd], side, a.N);
+                        const T* src = field == 0 ? a.u_in + nc * 5 * b : a.pr_in + (nc * 4 + field - 1) * b;
+                        if constexpr (b % 4 == 0) {
+#pragma unroll
+                            for (int l = 0; l < b; l += 4) ld4<T>(src + l, cf + l);
+                        } else {
+#pragma unroll
+                            for (int l = 0; l < b; ++l) cf[l] = __ldg(src + l);
+                        }
+                    } else {
+                        // past the end: a quiet filler state (rho = 1, v = 0, p = 1)
+#pragma unroll
+                        for (int l = 0; l < b; ++l) cf[l] = (l == 0 && (field == 0 || field == 4)) ? T(1) : T(0);
+                    }
+                }
+                T c2[B2K];
+                collapse<T, K, Dd, B2K>(cf, fside, c2);
+#pragma unroll
+                for (int p = 0; p < B2K; p += 4) st4<T>(sC2 + r * LDC2 + p, c2 + p);
+            }
+            __syncthreads();
+            mm<T, BK_FMA, RC, NSP, B2K, LDC2, LDT, NT>(sC2, tabs, C::oPsi, sTr);
+            __syncthreads();
+            // Rusanov flux at every face point, along +e_d with L the lower cell
+            for (int e = tid; e < TC * 2 * NSP; e += NT) {
+                const int s = e % NSP, side = (e / NSP) & 1, c = e / (2 * NSP);
+                T F[5] = {T(0), T(0), T(0), T(0), T(0)};
+                if (s < ns) {
+                    const int rs = ((c * 2 + side) * 2 + 0) * 5, rn = ((c * 2 + side) * 2 + 1) * 5;
+                    T Ws[5], Wn[5];
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) {
+                        Ws[f] = sTr[(rs + f) * LDT + s];
+                        Wn[f] = sTr[(rn + f) * LDT + s];
+                    }
+                    if (side)
+                        adi_rusanov<T, Dd>(gamma, Ws, Wn, F);
+                    else
+                        adi_rusanov<T, Dd>(gamma, Wn, Ws, F);
+                }
+                // written after every thread has read its traces (the flux rows alias nothing read here)
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sFs[((c * 2 + side) * 5 + v) * LDT + s] = F[v];
+            }
+            __syncthreads();
+            mm<T, BK_FMA, RL, B2N, NSP, LDT, LDL, NT>(sFs, tabs, C::oPsiL, sL2);
+            __syncthreads();
+            // + face (side 1): -1/(4h); - face (side 0): +1/(4h)
+            for (int e = tid; e < TC * 5; e += NT) {
+                const int c = e / 5, v = e % 5;
+                T* R = sR + (c * 5 + v) * b;
+                T rr[b];
+#pragma unroll
+                for (int l = 0; l < b; ++l) rr[l] = R[l];
+                expand_acc<T, K, Dd>(sL2 + ((c * 2 + 1) * 5 + v) * LDL, 1, -inv4h, rr);
+                expand_acc<T, K, Dd>(sL2 + ((c * 2 + 0) * 5 + v) * LDL, 0, inv4h, rr);
+#pragma unroll
+                for (int l = 0; l < b; ++l) R[l] = rr[l];
+            }
+            __syncthreads();
+        });
+        if constexpr (MODE == ADI_RHS) {
+            for (int e = tid; e < nvalid * 5 * b; e += NT) a.out[c0 * 5 * b + e] = sR[e];
+            __syncthreads();
+        } else {
+            // ---- SSP-RK stage combine (Sec. 7) ----
+            for (int e = tid; e < TC * 5 * b; e += NT) {
+                const T un = (a.rk_a != T(0)) ? sUn[e] : T(0);
+                sU[e] = a.rk_a * un + a.rk_b * (sU[e] + dt * sR[e]);
+            }
+            __syncthreads();
+            // ---- positivity of density and pressure (Sec. 3.1), warp per cells ----
+            constexpr int NW = NT / 32, CPW = TC / NW, NPT = nq + nf, NPW = (NPT + 31) / 32;
+            static_assert(TC % NW == 0, "cells per warp");
+            unsigned int st = 0u;
+            for (int cl = 0; cl < CPW; ++cl) {
+                const int c = wid * CPW + cl;
+                T* u = sU + c * 5 * b;
+                T ub[5], dl[5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    ub[v] = u[v * b];
+                    T part = (lane >= 1 && lane < b) ? fabs(u[v * b + (lane < b ? lane : 0)]) * my_sup : T(0);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    dl[v] = part;
+                }
+                if (c >= nvalid) continue;  // warp-uniform
+                const T pbar = adi_p<T>(gamma, ub[0], ub[1], ub[2], ub[3], ub[4]);
+                if (!(ub[0] > eps) || !(pbar > eps)) {
+                    st |= DG_ST_FAIL_;
+                    continue;
+                }
+                // sufficient condition on the box ubar +- delta: no point can be below a floor
+                bool ok = ub[0] - dl[0] >= eps;
+                if (ok) {
+                    const T lr = ub[0] - dl[0], le = ub[4] - dl[4];
+                    T mm2 = T(0);
+#pragma unroll
+                    for (int i = 1; i < 4; ++i) {
+                        const T mi = fabs(ub[i]) + dl[i];
+                        mm2 += mi * mi;
+                    }
+                    ok = le > T(0) && lr * le - T(0.5) * mm2 - eps * (ub[0] + dl[0]) / g1 > T(0);
+                }
+                if (ok) continue;
+                // exact check at every volume and face point
+                const T* phiv = a.tab + TT::phiv;
+                const T* phif = a.tab + TT::phif;
+                T val[NPW][5];
+                T rmin = T(1e30);
+#pragma unroll
+                for (int j = 0; j < NPW; ++j) {
+                    const int pt = lane + 32 * j;
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) val[j][v] = ub[v];
+                    if (pt < NPT) {
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) {
+                            T s = T(0);
+                            if (pt < nq) {
+#pragma unroll
+                                for (int l = 0; l < b; ++l) s += u[v * b + l] * __ldg(phiv + l * nq + pt);
+                            } else {
+#pragma unroll
+                                for (int l = 0; l < b; ++l) s += u[v * b + l] * __ldg(phif + l * nf + (pt - nq));
+                            }
+                            val[j][v] = s;
+                        }
+                        rmin = val[j][0] < rmin ? val[j][0] : rmin;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const T other = __shfl_xor_sync(0xffffffffu, rmin, o);
+                    rmin = other < rmin ? other : rmin;
+                }
+                const T th_r = rmin < eps ? (ub[0] - eps) / (ub[0] - rmin) : T(1);
+                T th_p = T(1);
+#pragma unroll
+                for (int j = 0; j < NPW; ++j) {
+                    const int pt = lane + 32 * j;
+                    if (pt < NPT) {
+                        T uq[5], dv[5];
+#pragma unroll
+                        for (int v = 0; v < 5; ++v) {
+                            uq[v] = ub[v] + th_r * (val[j][v] - ub[v]);
+                            dv[v] = uq[v] - ub[v];
+                        }
+                        if (adi_p<T>(gamma, uq[0], uq[1], uq[2], uq[3], uq[4]) < eps) {
+                            const T t = adi_pressure_root<T>(gamma, eps, ub, dv);
+                            th_p = t < th_p ? t : th_p;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const T other = __shfl_xor_sync(0xffffffffu, th_p, o);
+                    th_p = other < th_p ? other : th_p;
+                }
+                const T th = th_r * th_p;
+                if (th < T(1)) {
+                    st |= DG_ST_LIMITED_;
+                    for (int e = lane; e < 5 * b; e += 32)
+                        if (e % b) u[e] *= th;
+                }
+                __syncwarp();
+            }
+            st = __reduce_or_sync(0xffffffffu, st);
+            if (lane == 0 && st) atomicOr(&s_status, st);
+            __syncthreads();
+            for (int e = tid; e < nvalid * 5 * b; e += NT) {
+                const T w = sU[e];
+                if (!isfinite(w)) atomicOr(&s_status, DG_ST_NONFINITE_);
+                a.out[c0 * 5 * b + e] = w;
+            }
+            __syncthreads();
+        }
+        }  // right-hand-side modes
+    }
+    // ---- block reductions ----
+    if constexpr (MODE == ADI_PROJECT) {
+        if (a.flags & F_DT) {
+            const double sp = (double)smax;
+            atomicMax(&s_smax, (unsigned long long)__double_as_longlong(sp));
+            __syncthreads();
+            if (tid == 0) atomicMax(&a.ctl->smax, s_smax);
+        }
+    } else {
+        __syncthreads();
+        if (tid == 0 && s_status) atomicOr(&a.ctl->status, s_status);
+    }
+}
+
+// FP64 totals for the diagnostics: per block [mass, m_x, m_y, m_z, energy,
+// kinetic energy (volume quadrature of |m|^2/(2 rho)), min rho, min p at the
+// volume points], summed over blocks on the host in block order
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_adi_totals(const T* __restrict__ u, const T* __restrict__ tab, long ncell,
+                                                   double gamma, double* __restrict__ partials)
+{
+    using TT = TileTab<K, BK_FMA>;
+    constexpr int b = Dims<K>::b, nq = Dims<K>::nq, n = K + 1;
+    __shared__ double s_red[256];
+    __shared__ double s_w[nq];
+    // Gauss weights (per-point volume weights w_q / 8) from the mass identity: the
+    // projection weights are the phi_0 = 1 row of the weighted transpose table
+    if (threadIdx.x < nq) s_w[threadIdx.x] = (double)tab[TileCfg<K, BK_FMA>::oWPhi + threadIdx.x * TileCfg<K, BK_FMA>::NP];
+    __syncthreads();
+    (void)n;
+    double acc[6] = {0, 0, 0, 0, 0, 0}, rmin = 1e300, pmin = 1e300;
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell; c += (long)gridDim.x * blockDim.x) {
+        const T* uc = u + c * 5 * b;
+        for (int v = 0; v < 5; ++v) acc[v] += (double)uc[v * b];
+        for (int q = 0; q < nq; ++q) {
+            double w[5];
+            for (int v = 0; v < 5; ++v) {
+                double s = 0.0;
+                for (int l = 0; l < b; ++l) s += (double)uc[v * b + l] * (double)tab[TT::phiv + l * nq + q];
+                w[v] = s;
+            }
+            const double ke = 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0];
+            acc[5] += s_w[q] * ke;
+            const double p = (gamma - 1.0) * (w[4] - ke);
+            rmin = w[0] < rmin ? w[0] : rmin;
+            pmin = p < pmin ? p : pmin;
+        }
+    }
+    double vals[8] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], rmin, pmin};
+    for (int i = 0; i < 8; ++i) {
+        s_red[threadIdx.x] = vals[i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = i < 6 ? 0.0 : 1e300;
+            for (int j = 0; j < (int)blockDim.x; ++j) t = i < 6 ? t + s_red[j] : (s_red[j] < t ? s_red[j] : t);
+            partials[blockIdx.x * 8 + i] = t;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace dg

@@ -1666,3 +1666,326 @@ int dg_power_spectrum(dg_ctx* ctx, void* work, size_t work_bytes, int nbins, dou
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// adiabatic system (Sec. 2.1): five conserved variables, ideal-gas equation
+// of state; the same basis, tables, quadrature and SSP-RK schemes
+// ===========================================================================
+struct dg_adi_ctx {
+    int N = 0, K = 0, b = 0, prec = DG_PREC_F32, rk = 3;
+    long ncell = 0;
+    double h = 0.0, gamma = 1.4, cfl = 0.3;
+    dg_nu_params nu{};
+    cudaStream_t st = nullptr;
+    void* reg[3] = {nullptr, nullptr, nullptr};
+    int cur = 0;
+    void* prim = nullptr;
+    char* scratch = nullptr;
+    Ctl* ctl = nullptr;
+    void* ttab = nullptr;
+    double* partials = nullptr;
+    int nsm = 1;
+    bool state_set = false;
+    double t = 0.0, dt_last = 0.0;
+    long steps = 0;
+    unsigned int status = 0u;
+    std::string err;
+};
+
+namespace {
+
+int afail(dg_adi_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define ACK(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return afail(ctx, DG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+struct AdiScratch {
+    size_t ctl, ttab, partials, total;
+};
+
+AdiScratch adi_scratch(int K)
+{
+    AdiScratch s{};
+    size_t off = 0;
+    s.ctl = off;
+    off = align256(off + sizeof(Ctl));
+    s.ttab = off;
+    off = align256(off + sizeof(double) * ttab_total(K));
+    s.partials = off;
+    off = align256(off + sizeof(double) * 8 * kMaxGrid);
+    s.total = off;
+    return s;
+}
+
+size_t adi_elem(const dg_adi_ctx* c) { return c->prec == DG_PREC_F64 ? sizeof(double) : sizeof(float); }
+size_t adi_state_bytes(const dg_adi_ctx* c) { return adi_elem(c) * (size_t)c->ncell * 5 * c->b; }
+
+Launch adi_make_launch(const dg_adi_ctx* c)
+{
+    Launch L{};
+    L.st = c->st;
+    L.K = c->K;
+    L.N = c->N;
+    L.ncell = c->ncell;
+    L.ph.h = c->h;
+    L.ph.hp = c->h / (c->K + 1);
+    L.ph.alpha = c->nu.alpha;
+    L.ph.beta = c->nu.beta;
+    L.ph.floor_ = c->nu.rho_floor;
+    L.ph.av_mode = c->nu.mode;
+    L.ttab = c->ttab;
+    L.ctl = c->ctl;
+    L.partials = c->partials;
+    L.nsm = c->nsm;
+    L.bk = 0;
+    return L;
+}
+
+cudaError_t adi_go(const dg_adi_ctx* c, const AdiLaunch& t)
+{
+    const Launch L = adi_make_launch(c);
+    return c->prec == DG_PREC_F64 ? launch_adi<double>(L, c->gamma, t) : launch_adi<float>(L, c->gamma, t);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_adi_buffer_bytes(const dg_mesh* mesh, int order, int precision, size_t* state_bytes, size_t* prim_bytes,
+                        size_t* scratch_bytes)
+{
+    if (!mesh || order < 1 || order > 3 || (precision != DG_PREC_F32 && precision != DG_PREC_F64)) return DG_EINVAL;
+    if (mesh->n[0] < 1 || mesh->n[0] > kMaxN) return DG_EINVAL;
+    const size_t n = (size_t)mesh->n[0] * mesh->n[1] * mesh->n[2];
+    const size_t b = (size_t)(order + 1) * (order + 2) * (order + 3) / 6;
+    const size_t el = precision == DG_PREC_F64 ? sizeof(double) : sizeof(float);
+    if (state_bytes) *state_bytes = n * 5 * b * el;
+    if (prim_bytes) *prim_bytes = n * 4 * b * el;
+    if (scratch_bytes) *scratch_bytes = adi_scratch(order).total;
+    return DG_OK;
+}
+
+int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_params* nu, const dg_adi_opts* opts)
+{
+    if (!out) return DG_EINVAL;
+    *out = nullptr;
+    if (!mesh || !nu || !opts) return DG_EINVAL;
+    if (order < 1 || order > 3) return DG_EINVAL;
+    if (mesh->n[0] < 1 || mesh->n[0] != mesh->n[1] || mesh->n[0] != mesh->n[2] || mesh->n[0] > kMaxN) return DG_EINVAL;
+    for (int d = 0; d < 3; ++d)
+        if (mesh->L[d] != 1.0) return DG_EINVAL;
+    if (nu->mode < 0 || nu->mode > 1 || !(nu->rho_floor >= 0.0) || nu->diffusion != 0.0) return DG_EINVAL;
+    if (opts->precision != DG_PREC_F32 && opts->precision != DG_PREC_F64) return DG_EINVAL;
+    if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
+    if (!(opts->cfl > 0.0) || !(opts->gamma > 1.0) || !opts->stream || !opts->prim || !opts->scratch) return DG_EINVAL;
+    for (int i = 0; i < 3; ++i)
+        if (!opts->u[i]) return DG_EINVAL;
+    const AdiScratch sl = adi_scratch(order);
+    if (opts->scratch_bytes < sl.total) return DG_ENOMEM;
+    if (((uintptr_t)opts->scratch & 255u) != 0) return DG_EINVAL;
+    dg_adi_ctx* ctx = new (std::nothrow) dg_adi_ctx();
+    if (!ctx) return DG_ENOMEM;
+    ctx->N = mesh->n[0];
+    ctx->K = order;
+    ctx->b = (order + 1) * (order + 2) * (order + 3) / 6;
+    ctx->prec = opts->precision;
+    ctx->rk = opts->rk_stages;
+    ctx->ncell = (long)ctx->N * ctx->N * ctx->N;
+    ctx->h = 1.0 / ctx->N;
+    ctx->gamma = opts->gamma;
+    ctx->cfl = opts->cfl;
+    ctx->nu = *nu;
+    ctx->st = static_cast<cudaStream_t>(opts->stream);
+    for (int i = 0; i < 3; ++i) ctx->reg[i] = opts->u[i];
+    ctx->prim = opts->prim;
+    ctx->scratch = static_cast<char*>(opts->scratch);
+    ctx->ctl = reinterpret_cast<Ctl*>(ctx->scratch + sl.ctl);
+    ctx->ttab = ctx->scratch + sl.ttab;
+    ctx->partials = reinterpret_cast<double*>(ctx->scratch + sl.partials);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
+    const std::vector<char> tt = tile_tables_for(order, ctx->prec);
+    Ctl c0{};
+    c0.dt_scale = 1.0;
+    c0.dt_num = ctx->cfl * ctx->h / (ctx->K + 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ttab, tt.data(), tt.size(), cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return DG_ECUDA;
+    }
+    *out = ctx;
+    return DG_OK;
+}
+
+void dg_adi_free(dg_adi_ctx* ctx) { delete ctx; }
+
+const char* dg_adi_last_error(const dg_adi_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int dg_adi_set_state(dg_adi_ctx* ctx, const void* src, int src_on_host)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!src) return afail(ctx, DG_EINVAL, "dg_adi_set_state: null source");
+    ctx->cur = 0;
+    ACK(cudaMemcpyAsync(ctx->reg[0], src, adi_state_bytes(ctx),
+                        src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->st));
+    ACK(cudaStreamSynchronize(ctx->st));
+    ctx->state_set = true;
+    ctx->t = 0.0;
+    ctx->steps = 0;
+    ctx->status = 0u;
+    return DG_OK;
+}
+
+int dg_adi_get_state(dg_adi_ctx* ctx, void* dst, int to_host)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!dst) return afail(ctx, DG_EINVAL, "dg_adi_get_state: null destination");
+    if (!ctx->state_set) return afail(ctx, DG_ESTATE, "dg_adi_get_state: no state set");
+    ACK(cudaMemcpyAsync(dst, ctx->reg[ctx->cur], adi_state_bytes(ctx),
+                        to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->st));
+    ACK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_adi_project(dg_adi_ctx* ctx, const void* u_in, void* prim_out)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!u_in || !prim_out) return afail(ctx, DG_EINVAL, "dg_adi_project: null buffer");
+    AdiLaunch p{};
+    p.mode = ADI_PROJECT;
+    p.u_in = u_in;
+    p.pr_out = prim_out;
+    ACK(adi_go(ctx, p));
+    ACK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_adi_rhs(dg_adi_ctx* ctx, const void* u_in, void* dudt, double dt_pimax)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!u_in || !dudt) return afail(ctx, DG_EINVAL, "dg_adi_rhs: null buffer");
+    if (!(dt_pimax >= 0.0)) return afail(ctx, DG_EINVAL, "dg_adi_rhs: negative dt");
+    AdiLaunch p{};
+    p.mode = ADI_PROJECT;
+    p.u_in = u_in;
+    p.pr_out = ctx->prim;
+    ACK(adi_go(ctx, p));
+    AdiLaunch r{};
+    r.mode = ADI_RHS;
+    r.u_in = u_in;
+    r.out = dudt;
+    r.pr_in = ctx->prim;
+    r.dt_pimax = dt_pimax;
+    ACK(adi_go(ctx, r));
+    ACK(cudaStreamSynchronize(ctx->st));
+    return DG_OK;
+}
+
+int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_last)
+{
+    if (!ctx) return DG_EINVAL;
+    if (nsteps < 0 || !(fixed_dt >= 0.0)) return afail(ctx, DG_EINVAL, "dg_adi_step: bad arguments");
+    if (!ctx->state_set) return afail(ctx, DG_ESTATE, "dg_adi_step: no state set");
+    static const double A2[2] = {0.0, 0.5}, B2[2] = {1.0, 0.5};
+    static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double* RA = ctx->rk == 2 ? A2 : A3;
+    const double* RB = ctx->rk == 2 ? B2 : B3;
+    for (int n = 0; n < nsteps; ++n) {
+        const int A = ctx->cur, B = (ctx->cur + 1) % 3, C = (ctx->cur + 2) % 3;
+        const int in3[3] = {A, B, C}, out3[3] = {B, C, B};
+        const int in2[2] = {A, B}, out2[2] = {B, C};
+        const int* in = ctx->rk == 2 ? in2 : in3;
+        const int* out = ctx->rk == 2 ? out2 : out3;
+        bool ok = false;
+        unsigned int status = 0u;
+        double dt = 0.0;
+        for (int retry = 0; retry <= 3 && !ok; ++retry) {
+            struct {
+                double dt_scale, fixed_dt;
+            } hs = {1.0 / (double)(1 << retry), fixed_dt};
+            ACK(cudaMemcpyAsync(&ctx->ctl->dt_scale, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->st));
+            ACK(cudaMemsetAsync(&ctx->ctl->status, 0, sizeof(unsigned int), ctx->st));
+            ACK(cudaMemsetAsync(&ctx->ctl->smax, 0, sizeof(unsigned long long), ctx->st));
+            for (int s = 0; s < ctx->rk; ++s) {
+                // projections of v and p of the stage's input (with the CFL bound of u^n)
+                AdiLaunch p{};
+                p.mode = ADI_PROJECT;
+                p.u_in = ctx->reg[in[s]];
+                p.pr_out = ctx->prim;
+                p.flags = s == 0 ? F_DT : 0;
+                ACK(adi_go(ctx, p));
+                AdiLaunch t{};
+                t.mode = ADI_STAGE;
+                t.u_in = ctx->reg[in[s]];
+                t.u_n = ctx->reg[A];
+                t.out = ctx->reg[out[s]];
+                t.pr_in = ctx->prim;
+                t.rk_a = RA[s];
+                t.rk_b = RB[s];
+                ACK(adi_go(ctx, t));
+            }
+            struct {
+                unsigned int status;
+                double dt;
+            } back{};
+            ACK(cudaMemcpyAsync(&back.status, &ctx->ctl->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+            ACK(cudaMemcpyAsync(&back.dt, &ctx->ctl->dt, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            ACK(cudaStreamSynchronize(ctx->st));
+            status = back.status;
+            dt = back.dt;
+            ok = !(status & DG_ST_FAIL);
+        }
+        ctx->status |= status;
+        if (!ok) return afail(ctx, DG_EPOSITIVITY, "dg_adi_step: positivity retries exhausted");
+        ctx->cur = out[ctx->rk - 1];
+        ctx->t += dt;
+        ctx->dt_last = dt;
+        ctx->steps += 1;
+        if (status & DG_ST_NONFINITE) return afail(ctx, DG_ENONFINITE, "dg_adi_step: non-finite coefficient");
+    }
+    if (t_out) *t_out = ctx->t;
+    if (dt_last) *dt_last = ctx->dt_last;
+    return DG_OK;
+}
+
+int dg_adi_totals(dg_adi_ctx* ctx, double* out)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!out) return afail(ctx, DG_EINVAL, "dg_adi_totals: null output");
+    if (!ctx->state_set) return afail(ctx, DG_ESTATE, "dg_adi_totals: no state set");
+    const Launch L = adi_make_launch(ctx);
+    int nb = 0;
+    const void* u = ctx->reg[ctx->cur];
+    ACK(ctx->prec == DG_PREC_F64 ? launch_adi_totals<double>(L, ctx->gamma, u, ctx->partials, &nb)
+                                 : launch_adi_totals<float>(L, ctx->gamma, u, ctx->partials, &nb));
+    std::vector<double> part((size_t)nb * 8);
+    ACK(cudaMemcpyAsync(part.data(), ctx->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    ACK(cudaStreamSynchronize(ctx->st));
+    const double vol = ctx->h * ctx->h * ctx->h;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 1e300, 1e300};
+    for (int blk = 0; blk < nb; ++blk)
+        for (int i = 0; i < 8; ++i) {
+            const double v = part[(size_t)blk * 8 + i];
+            if (i < 6)
+                acc[i] += v;
+            else
+                acc[i] = v < acc[i] ? v : acc[i];
+        }
+    for (int i = 0; i < 6; ++i) out[i] = acc[i] * vol;
+    out[6] = acc[6];
+    out[7] = acc[7];
+    return DG_OK;
+}
+
+}  // extern "C"

@@ -58,6 +58,28 @@ cudaError_t launch_diag(const Launch& L, const T* u, const T* ahat, double dt_pi
 template <typename T>
 cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB);
 
+// adiabatic system (dg_adi.cu): mode 0 projection of v and p (+ CFL bound
+// with F_DT), 1 right-hand side, 2 stage (right-hand side, SSP-RK combine,
+// positivity of density and pressure)
+enum { ADI_PROJECT = 0, ADI_RHS = 1, ADI_STAGE = 2 };
+struct AdiLaunch {
+    int mode;
+    const void* u_in;
+    const void* u_n;
+    void* out;
+    const void* pr_in;
+    void* pr_out;
+    double rk_a, rk_b;
+    double dt_pimax;
+    int flags;
+};
+template <typename T>
+cudaError_t launch_adi(const Launch& L, double gamma, const AdiLaunch& t);
+// per-block FP64 totals [nblocks][8]: mass, momentum (3), energy, kinetic
+// energy, min rho and min p at the volume points
+template <typename T>
+cudaError_t launch_adi_totals(const Launch& L, double gamma, const void* u, double* partials, int* nblocks);
+
 // turbulence statistics (dg_analysis.cu)
 template <typename T>
 cudaError_t launch_density_pdf(const Launch& L, const T* u, double lo, double hi, int nbins, double* mean,

@@ -1,0 +1,215 @@
+"""Parity of the GPU adiabatic system (dg_adi_*; Sec. 2.1 state, equation of
+state and flux, Sec. 3.1 viscous pressure and positivity, Sec. 3.2 projected
+face states) with the oracle on the same seeded inputs: projections, the
+right-hand side, steps with and without the limiter, conservation, the Sod
+pair, and the step's failure path.  Tolerances as for the isothermal system:
+FP64 to 1e-12, FP32 to 1e-5 for a right-hand side and 3e-5 for a few steps
+(relative L2 per field)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = pytest.mark.skip(reason="no CUDA device")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2401_06841_gb300 import AdiabaticSolver  # noqa: E402
+from paper_2401_06841_gb300 import _lib as B  # noqa: E402
+from paper_2401_06841_gb300 import inputs as I  # noqa: E402
+
+G = 1.4
+TOL_RHS = {"f64": 1e-12, "f32": 1e-5}
+TOL_STEPS = {"f64": 1e-12, "f32": 3e-5}
+
+
+def rel_fields(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    out = []
+    for v in range(ref.shape[1]):
+        den = np.linalg.norm(ref[:, v])
+        out.append(np.linalg.norm(got[:, v] - ref[:, v]) / (den if den > 0 else 1.0))
+    return np.array(out)
+
+
+def state(N, k, seed, prec, p_mean=5.0):
+    u = I.random_energy_state(N, k, seed=seed, v_rms=0.3, p_mean=p_mean, gamma=G)
+    if prec == "f32":
+        u = u.astype(np.float32).astype(np.float64)
+    return u
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_projection_parity(k, prec):
+    N = 5  # 125 cells: ragged tiles
+    u = state(N, k, 10 + k, prec)
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec)
+    got = s.project(u).cpu().numpy()
+    ref = O.adi_project(O.make_cfg(N, k), G, u)
+    err = rel_fields(got, ref)
+    assert err.max() < TOL_RHS[prec], err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_rhs_parity(k, prec):
+    N = 5
+    u = state(N, k, 20 + k, prec)
+    dt = 2e-3
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec)
+    got = s.rhs(u, dt).cpu().numpy()
+    ref = O.adi_rhs(O.make_cfg(N, k), G, u, dt)
+    err = rel_fields(got, ref)
+    assert err.max() < TOL_RHS[prec], err
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rhs_parity_32_k3(prec):
+    # several full tiles per block at a mesh the whole-mesh oracle still covers in seconds
+    N, k = 32, 3
+    u = state(N, k, 33, prec, p_mean=20.0)  # positive pressure at every point and face of the random state
+    dt = 1e-3
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec)
+    got = s.rhs(u, dt).cpu().numpy()
+    ref = O.adi_rhs(O.make_cfg(N, k), G, u, dt)
+    err = rel_fields(got, ref)
+    assert err.max() < TOL_RHS[prec], err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("k,rk", [(1, 2), (2, 3), (3, 3)])
+def test_steps_parity(k, rk, prec):
+    N = 5
+    u = state(N, k, 40 + k, prec)
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec, rk_stages=rk)
+    s.set_state(u)
+    t, dtl = s.step(3)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, tr, dr = O.adi_run(O.make_cfg(N, k, rk_stages=rk), G, ref, 3)
+    assert rc == 0
+    assert t == pytest.approx(tr, rel=1e-12 if prec == "f64" else 1e-6)
+    err = rel_fields(got, ref)
+    assert err.max() < TOL_STEPS[prec], err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_steps_through_the_limiter(prec):
+    # a state limited to the floor 0.05 (density and pressure positive at every
+    # point, many points close to it), stepped with the floor 0.5: the stages
+    # find points below the floor and both implementations rescale them
+    N, k = 5, 2
+    u = state(N, k, 61, prec)
+    u[::7, 4, 1:] *= 40.0
+    u[3::11, 0, 1:] *= 2.5
+    assert O.adi_limit(O.make_cfg(N, k, rho_floor=0.05), G, u) & O.ORC_LIMITED
+    if prec == "f32":
+        u = u.astype(np.float32).astype(np.float64)
+    cfg = O.make_cfg(N, k, rho_floor=0.5)
+    dt = 5e-4
+    probe = u.copy()
+    assert O.adi_step(cfg, G, probe, dt) & O.ORC_LIMITED
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec, floor=0.5)
+    s.set_state(u)
+    s.step(2, fixed_dt=dt)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, _, _ = O.adi_run(cfg, G, ref, 2, fixed_dt=dt)
+    assert rc == 0
+    err = rel_fields(got, ref)
+    assert err.max() < TOL_STEPS[prec], err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 2e-6)])
+def test_totals_are_conserved(prec, tol):
+    N, k = 6, 2
+    u = state(N, k, 70, prec)
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec)
+    s.set_state(u)
+    a = s.totals()
+    s.step(5)
+    b = s.totals()
+    for key in ("mass", "energy"):
+        assert abs(b[key] - a[key]) < tol * abs(a[key]), (key, a[key], b[key])
+    scale = max(abs(a["mom_x"]), abs(a["mom_y"]), abs(a["mom_z"]), a["mass"])
+    for key in ("mom_x", "mom_y", "mom_z"):
+        assert abs(b[key] - a[key]) < tol * scale, (key, a[key], b[key])
+    h3 = (1.0 / N) ** 3
+    assert a["mass"] == pytest.approx(u[:, 0, 0].sum() * h3, rel=1e-12 if prec == "f64" else 1e-6)
+    assert b["p_min"] > 0 and b["rho_min"] > 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_sod_pair_parity(prec, tol):
+    # two shock tubes in the periodic box (shocks, contacts, rarefactions, the
+    # viscous pressure active): 15 steps against the oracle
+    N, k = 16, 2
+    b = I.nmodes(k)
+    u = np.zeros((N ** 3, 5, b))
+    ix = np.arange(N ** 3) % N
+    high = (ix >= N // 4) & (ix < 3 * N // 4)
+    u[high, 0, 0], u[high, 4, 0] = 1.0, 1.0 / (G - 1)
+    u[~high, 0, 0], u[~high, 4, 0] = 0.125, 0.1 / (G - 1)
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec)
+    s.set_state(u)
+    t, _ = s.step(15)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, tr, _ = O.adi_run(O.make_cfg(N, k), G, ref, 15)
+    assert rc == 0
+    assert t == pytest.approx(tr, rel=1e-10 if prec == "f64" else 1e-5)
+    err = rel_fields(got, ref)
+    print("Sod pair %s rel-L2 per field %s" % (prec, err))
+    assert err.max() < tol, err
+
+
+@pytest.mark.gpu
+def test_failure_is_reported_after_retries():
+    # a cell whose mean pressure is below the floor cannot be repaired by the
+    # limiter: every retry fails and the state stays at its start
+    N, k = 4, 1
+    u = state(N, k, 80, "f64")
+    u[5, 4, 0] = 0.5 * (u[5, 1:4, 0] ** 2).sum() / u[5, 0, 0] - 1.0  # mean p = -0.4
+    s = AdiabaticSolver(N, k, gamma=G, precision="f64")
+    s.set_state(u)
+    with pytest.raises(B.DGError) as e:
+        s.step(1)
+    assert e.value.code == 4  # DG_EPOSITIVITY
+    assert np.array_equal(s.get_state().cpu().numpy(), u)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mean_pressure_below_the_floor_fails(prec):
+    # a valid state whose cell 9 has mean pressure 0.3 under the floor 0.5:
+    # no rescaling can lift a cell mean, every retry fails
+    N, k = 4, 2
+    u = state(N, k, 81, "f64")
+    u[9, 4, 0] = 0.5 * (u[9, 1:4, 0] ** 2).sum() / u[9, 0, 0] + 0.3 / (G - 1)
+    u[9, 4, 1:] = 0.0
+    u[9, 1:4, 1:] = 0.0
+    cfg = O.make_cfg(N, k, rho_floor=0.5)
+    ref = u.copy()
+    assert O.adi_run(cfg, G, ref, 1)[0] == -1
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec, floor=0.5)
+    s.set_state(u)
+    with pytest.raises(B.DGError) as e:
+        s.step(1)
+    assert e.value.code == 4  # DG_EPOSITIVITY
+    assert np.allclose(s.get_state().cpu().numpy(), u, rtol=0, atol=0 if prec == "f64" else 1e-6 * np.abs(u).max())
+
+
+@pytest.mark.gpu
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(B.DGError):
+        AdiabaticSolver(4, 2, gamma=1.0)
+    with pytest.raises(KeyError):
+        AdiabaticSolver(4, 2, precision="x3")
