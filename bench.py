@@ -128,6 +128,56 @@ def profiled_traffic(args, variant):
     return int(m_t.group(1)) if h.hexdigest() == m_h.group(1) else None
 
 
+def adiabatic_arm(args, dev, seed, flush, world):
+    """The five-variable adiabatic system (Sec. 2.1) on the same mesh and
+    degree: decaying turbulence at rms Mach 0.5, gamma 1.4, FP32; steps timed
+    like the main variants (L2 flushed before each, CUDA events on the
+    solver's stream).  Algorithmic bytes per DOF and stage: u^(s), u^n (2/3 on
+    average over the SSP-RK3 stages) and u^(s+1), one word each."""
+    import torch
+    from paper_2401_06841_gb300 import AdiabaticSolver
+    from paper_2401_06841_gb300 import inputs as I
+    N, k, S = args.N, args.k, 3
+    b = (k + 1) * (k + 2) * (k + 3) // 6
+    dof = 5 * b * N ** 3
+    s = AdiabaticSolver(N, k, gamma=1.4, precision="f32", rk_stages=S, device=dev)
+    s.set_state(I.adiabatic_turbulent_state(N, k, seed=seed + 2, mach=0.5))
+    t0 = s.totals()
+
+    def flush_l2():
+        with torch.cuda.stream(s.stream):
+            flush.fill_(1.0)
+
+    for _ in range(args.warmup):
+        flush_l2()
+        s.step(1)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush_l2()
+        starts[i].record(s.stream)
+        s.step(1)
+        ends[i].record(s.stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(e) for a, e in zip(starts, ends)) / args.steps, world, dev)
+    t1 = s.totals()
+    s.close()
+    hbm, _, src = peaks()
+    bytes_stage = dof * 4 * (1 + 2.0 / 3.0 + 1)
+    achieved = bytes_stage / (ms / S * 1e-3) / 1e9
+    return {"workload": "decaying turbulence, %d^3 cells, DG k=%d, SSP-RK3, rms Mach 0.5, gamma 1.4 "
+                        "(five variables)" % (N, k),
+            "value": job_value(dof, S, world, ms), "unit": UNIT, "ms_per_step": ms, "dtype": "f32", "dof": dof,
+            "launches_per_step": 2 * S,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_source": src, "bytes_per_stage": bytes_stage,
+                         "timed": "whole stages (projection + stage kernel)"},
+            "relative_drift": {"mass": (t1["mass"] - t0["mass"]) / t0["mass"],
+                               "energy": (t1["energy"] - t0["energy"]) / t0["energy"]},
+            "p_min": t1["p_min"], "rho_min": t1["rho_min"]}
+
+
 def oracle_arm(args, steps, warmup):
     """FP64 CPU oracle on a bounded sample: a 16^3 box at the workload's degree."""
     from oracle import oracle as O
@@ -216,6 +266,8 @@ def main():
     ap.add_argument("--riemann", default="rusanov", choices=["rusanov", "hll", "hllc"])
     ap.add_argument("--train-epochs", dest="train_epochs", type=int, default=20)
     ap.add_argument("--diffusion", type=float, default=0.0, help="eps of an added div(eps grad u)")
+    ap.add_argument("--no-adiabatic", dest="no_adiabatic", action="store_true",
+                    help="skip the timing of the five-variable adiabatic system")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -417,6 +469,8 @@ def main():
         if name == "power_spectrum_ms":
             ana["spectrum_total_power"] = float(out[1].sum())
     line["analysis"] = ana
+    if not args.no_adiabatic:
+        line["adiabatic"] = adiabatic_arm(args, dev, state_seed, flush, world)
     if rank == 0 and not args.no_cpu:
         v, wall, cb = oracle_arm(args, args.cpu_steps, 1)
         cb["value"] = v

@@ -100,6 +100,23 @@ def random_energy_state(N: int, k: int, seed: int, p_mean: float = 1.5, p_spread
     return u
 
 
+def adiabatic_turbulent_state(N: int, k: int, seed: int, mach: float, gamma: float = 1.4, p0: float = 1.0,
+                              zeta: float = 0.5) -> np.ndarray:
+    """Coefficients [N^3][5][b] of a synthetic turbulent state of the
+    five-variable system: rho = 1, m = v from ``turbulent_velocity`` with rms
+    speed mach * sqrt(gamma p0), e = p0/(gamma-1) + v_rms^2/2 in the cell mean
+    (higher modes of e zero): mean pressure p0, with the local kinetic energy
+    taken out of it point by point."""
+    c0 = float(np.sqrt(gamma * p0))
+    v = turbulent_velocity(N, k, seed, mach, zeta, c0)
+    u = np.zeros((N ** 3, 5, v.shape[2]))
+    u[:, 0, 0] = 1.0
+    u[:, 1:4, :] = v
+    vrms2 = (v[:, :, 0] ** 2).sum(axis=1).mean()
+    u[:, 4, 0] = p0 / (gamma - 1.0) + 0.5 * vrms2
+    return u
+
+
 def fourier_coeffs(N: int, k: int, kvec) -> np.ndarray:
     """Exact modal coefficients [N^3][b] (complex) of exp(2 pi i kvec . x)."""
     ijl = mode_degrees(k)
