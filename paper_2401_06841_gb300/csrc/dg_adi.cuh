@@ -10,7 +10,8 @@
 //                CFL bound max sum_d(|v_d| + c) over the volume points (F_DT)
 //   ADI_RHS      right-hand side of u_in -> out
 //   ADI_STAGE    right-hand side, SSP-RK stage combine, positivity of density
-//                and pressure (Sec. 3.1) -> out = u^(s+1)
+//                and pressure (Sec. 3.1) -> out = u^(s+1); with F_NEXTPROJ also
+//                the projections of u^(s+1) -> pr_out (the next stage's pr_in)
 // The right-hand side needs the projections of u_in in pr_in.
 #pragma once
 
@@ -34,7 +35,7 @@ struct AdiArgs {
     double gamma;
     T rk_a, rk_b;
     double dt_pimax; // right-hand-side mode: dt of the viscous-pressure cap
-    int flags;       // F_DT (projection mode)
+    int flags;       // F_DT (projection mode), F_NEXTPROJ (stage mode)
 };
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
@@ -159,8 +160,77 @@ __device__ __forceinline__ void adi_load(T* dst, const T* src, int n, int valid,
     }
 }
 
+// projections of v and p of the TC states in sU (Sec. 3.2) -> a.pr_out, and
+// with F_DT the CFL bound max sum_d(|v_d| + c) over the volume points of the
+// valid cells into smax.  Starts and ends with the block in step.
+template <typename T, int K>
+__device__ __forceinline__ void adi_project_tile(T* sm, const T* sU, const T* tabs, const AdiArgs<T>& a, long c0,
+                                                 int nvalid, T gamma, T& smax)
+{
+    using A = AdiCfg<K>;
+    using C = TileCfg<K, BK_FMA>;
+    constexpr int b = A::b, nq = A::nq, TC = A::TC, NT = A::NT, KP = A::KP, NQP = A::NQP, NP = A::NP;
+    constexpr int LDA = A::LDA, LDV = A::LDV, LDP = A::LDP;
+    const int tid = threadIdx.x;
+    T* sA = sm + A::oA;
+    T* sP = sA;
+    T* sBig = sm + A::oBig;
+    // rho, m, e at the volume points
+    for (int e = tid; e < TC * 5 * KP; e += NT) {
+        const int r = e / KP, l = e % KP;
+        sA[r * LDA + l] = l < b ? sU[r * b + l] : T(0);
+    }
+    __syncthreads();
+    mm<T, BK_FMA, TC * 5, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sBig);
+    __syncthreads();
+    constexpr int PER = (TC * NQP + NT - 1) / NT;
+    T f[PER][4];
+#pragma unroll
+    for (int it = 0; it < PER; ++it) {
+        const int e = tid + it * NT;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) f[it][i] = T(0);
+        if (e < TC * NQP) {
+            const int c = e / NQP, q = e % NQP;
+            if (q < nq) {
+                const T* v = sBig + (c * 5) * LDV + q;
+                const T rho = v[0], ir = rcp<T>(rho);
+                const T mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV];
+                f[it][0] = mx * ir;
+                f[it][1] = my * ir;
+                f[it][2] = mz * ir;
+                f[it][3] = adi_p<T>(gamma, rho, mx, my, mz, v[4 * LDV]);
+                if ((a.flags & F_DT) && c < nvalid) {
+                    const T cs = sqrt(gamma * f[it][3] * ir);
+                    const T sp = fabs(f[it][0]) + fabs(f[it][1]) + fabs(f[it][2]) + T(3) * cs;
+                    smax = sp > smax ? sp : smax;
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PER; ++it) {
+        const int e = tid + it * NT;
+        if (e < TC * NQP) {
+            const int c = e / NQP, q = e % NQP;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sBig[(c * 4 + i) * LDV + q] = f[it][i];
+        }
+    }
+    __syncthreads();
+    mm<T, BK_FMA, TC * 4, NP, NQP, LDV, LDP, NT>(sBig, tabs, C::oWPhi, sP);
+    __syncthreads();
+    for (int e = tid; e < nvalid * 4 * b; e += NT) {
+        const int r = e / b, l = e % b;
+        a.pr_out[c0 * 4 * b + e] = sP[r * LDP + l];
+    }
+    __syncthreads();
+}
+
+// FP32: two blocks per SM (128 registers); FP64 fits one block in shared memory
 template <typename T, int K, int MODE>
-__global__ void __launch_bounds__(256) k_adi(AdiArgs<T> a)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> a)
 {
     using A = AdiCfg<K>;
     using C = TileCfg<K, BK_FMA>;
@@ -214,57 +284,7 @@ __global__ void __launch_bounds__(256) k_adi(AdiArgs<T> a)
         adi_load<T, NT, 5, b>(sU, a.u_in + c0 * 5 * b, TC * 5 * b, nvalid * 5 * b, fill_e);
         if constexpr (MODE == ADI_PROJECT) {
             __syncthreads();
-            // rho, m, e at the volume points
-            for (int e = tid; e < TC * 5 * KP; e += NT) {
-                const int r = e / KP, l = e % KP;
-                sA[r * LDA + l] = l < b ? sU[r * b + l] : T(0);
-            }
-            __syncthreads();
-            mm<T, BK_FMA, TC * 5, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sBig);
-            __syncthreads();
-            constexpr int PER = (TC * NQP + NT - 1) / NT;
-            T f[PER][4];
-#pragma unroll
-            for (int it = 0; it < PER; ++it) {
-                const int e = tid + it * NT;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) f[it][i] = T(0);
-                if (e < TC * NQP) {
-                    const int c = e / NQP, q = e % NQP;
-                    if (q < nq) {
-                        const T* v = sBig + (c * 5) * LDV + q;
-                        const T rho = v[0], ir = rcp<T>(rho);
-                        const T mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV];
-                        f[it][0] = mx * ir;
-                        f[it][1] = my * ir;
-                        f[it][2] = mz * ir;
-                        f[it][3] = adi_p<T>(gamma, rho, mx, my, mz, v[4 * LDV]);
-                        if ((a.flags & F_DT) && c < nvalid) {
-                            const T cs = sqrt(gamma * f[it][3] * ir);
-                            const T sp = fabs(f[it][0]) + fabs(f[it][1]) + fabs(f[it][2]) + T(3) * cs;
-                            smax = sp > smax ? sp : smax;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int it = 0; it < PER; ++it) {
-                const int e = tid + it * NT;
-                if (e < TC * NQP) {
-                    const int c = e / NQP, q = e % NQP;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) sBig[(c * 4 + i) * LDV + q] = f[it][i];
-                }
-            }
-            __syncthreads();
-            mm<T, BK_FMA, TC * 4, NP, NQP, LDV, LDP, NT>(sBig, tabs, C::oWPhi, sP);
-            __syncthreads();
-            for (int e = tid; e < nvalid * 4 * b; e += NT) {
-                const int r = e / b, l = e % b;
-                a.pr_out[c0 * 4 * b + e] = sP[r * LDP + l];
-            }
-            __syncthreads();
+            adi_project_tile<T, K>(sm, sU, tabs, a, c0, nvalid, gamma, smax);
         } else {
         // ---- right-hand side: stage the projections (and u^n) of the tile ----
         for (int e = 4 * tid; e < TC * 4 * b; e += 4 * NT) {
@@ -584,6 +604,8 @@ __global__ void __launch_bounds__(256) k_adi(AdiArgs<T> a)
                 a.out[c0 * 5 * b + e] = w;
             }
             __syncthreads();
+            // the next stage's projections of v and p, from the new state in shared memory
+            if (a.flags & F_NEXTPROJ) adi_project_tile<T, K>(sm, sU, tabs, a, c0, nvalid, gamma, smax);
         }
         }  // right-hand-side modes
     }

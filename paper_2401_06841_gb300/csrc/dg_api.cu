@@ -1680,6 +1680,7 @@ struct dg_adi_ctx {
     void* reg[3] = {nullptr, nullptr, nullptr};
     int cur = 0;
     void* prim = nullptr;
+    void* prim2 = nullptr;  // second projection buffer (scratch)
     char* scratch = nullptr;
     Ctl* ctl = nullptr;
     void* ttab = nullptr;
@@ -1708,10 +1709,12 @@ int afail(dg_adi_ctx* c, int code, const std::string& msg)
     } while (0)
 
 struct AdiScratch {
-    size_t ctl, ttab, partials, total;
+    size_t ctl, ttab, partials, prim2, total;
 };
 
-AdiScratch adi_scratch(int K)
+// control block, tables, reduction partials, and the second projection buffer
+// (stages alternate between it and the caller's)
+AdiScratch adi_scratch(int K, size_t prim_bytes)
 {
     AdiScratch s{};
     size_t off = 0;
@@ -1721,6 +1724,8 @@ AdiScratch adi_scratch(int K)
     off = align256(off + sizeof(double) * ttab_total(K));
     s.partials = off;
     off = align256(off + sizeof(double) * 8 * kMaxGrid);
+    s.prim2 = off;
+    off = align256(off + prim_bytes);
     s.total = off;
     return s;
 }
@@ -1769,7 +1774,7 @@ int dg_adi_buffer_bytes(const dg_mesh* mesh, int order, int precision, size_t* s
     const size_t el = precision == DG_PREC_F64 ? sizeof(double) : sizeof(float);
     if (state_bytes) *state_bytes = n * 5 * b * el;
     if (prim_bytes) *prim_bytes = n * 4 * b * el;
-    if (scratch_bytes) *scratch_bytes = adi_scratch(order).total;
+    if (scratch_bytes) *scratch_bytes = adi_scratch(order, n * 4 * b * el).total;
     return DG_OK;
 }
 
@@ -1788,7 +1793,10 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     if (!(opts->cfl > 0.0) || !(opts->gamma > 1.0) || !opts->stream || !opts->prim || !opts->scratch) return DG_EINVAL;
     for (int i = 0; i < 3; ++i)
         if (!opts->u[i]) return DG_EINVAL;
-    const AdiScratch sl = adi_scratch(order);
+    const size_t nc = (size_t)mesh->n[0] * mesh->n[1] * mesh->n[2];
+    const size_t bb = (size_t)(order + 1) * (order + 2) * (order + 3) / 6;
+    const AdiScratch sl =
+        adi_scratch(order, nc * 4 * bb * (opts->precision == DG_PREC_F64 ? sizeof(double) : sizeof(float)));
     if (opts->scratch_bytes < sl.total) return DG_ENOMEM;
     if (((uintptr_t)opts->scratch & 255u) != 0) return DG_EINVAL;
     dg_adi_ctx* ctx = new (std::nothrow) dg_adi_ctx();
@@ -1810,6 +1818,7 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     ctx->ctl = reinterpret_cast<Ctl*>(ctx->scratch + sl.ctl);
     ctx->ttab = ctx->scratch + sl.ttab;
     ctx->partials = reinterpret_cast<double*>(ctx->scratch + sl.partials);
+    ctx->prim2 = ctx->scratch + sl.prim2;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1917,20 +1926,24 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
             ACK(cudaMemcpyAsync(&ctx->ctl->dt_scale, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->st));
             ACK(cudaMemsetAsync(&ctx->ctl->status, 0, sizeof(unsigned int), ctx->st));
             ACK(cudaMemsetAsync(&ctx->ctl->smax, 0, sizeof(unsigned long long), ctx->st));
+            // projections of v and p of u^n (with its CFL bound); every stage but the
+            // last projects its output for the next one (alternating buffers)
+            void* pr[2] = {ctx->prim, ctx->prim2};
+            AdiLaunch p{};
+            p.mode = ADI_PROJECT;
+            p.u_in = ctx->reg[A];
+            p.pr_out = pr[0];
+            p.flags = F_DT;
+            ACK(adi_go(ctx, p));
             for (int s = 0; s < ctx->rk; ++s) {
-                // projections of v and p of the stage's input (with the CFL bound of u^n)
-                AdiLaunch p{};
-                p.mode = ADI_PROJECT;
-                p.u_in = ctx->reg[in[s]];
-                p.pr_out = ctx->prim;
-                p.flags = s == 0 ? F_DT : 0;
-                ACK(adi_go(ctx, p));
                 AdiLaunch t{};
                 t.mode = ADI_STAGE;
                 t.u_in = ctx->reg[in[s]];
                 t.u_n = ctx->reg[A];
                 t.out = ctx->reg[out[s]];
-                t.pr_in = ctx->prim;
+                t.pr_in = pr[s & 1];
+                t.pr_out = pr[(s + 1) & 1];
+                t.flags = s + 1 < ctx->rk ? F_NEXTPROJ : 0;
                 t.rk_a = RA[s];
                 t.rk_b = RB[s];
                 ACK(adi_go(ctx, t));
