@@ -385,14 +385,22 @@ void orc_project_velocity(const orc_cfg* cfg, const double* u, double* vhat)
 
 /* mean acceleration abar = <rho a_h> / <rho>, removed so that the forcing adds
  * no net momentum (both averages are volume integrals by quadrature). */
+static void forcing_mean_nv(const orc_cfg* cfg, const double* u, int nv, const double* ahat, double abar[3]);
+
 void orc_forcing_mean(const orc_cfg* cfg, const double* u, const double* ahat, double abar[3])
+{
+    forcing_mean_nv(cfg, u, 4, ahat, abar);
+}
+
+/* the same for a state of nv variables per cell (rho first) */
+static void forcing_mean_nv(const orc_cfg* cfg, const double* u, int nv, const double* ahat, double abar[3])
 {
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
     int N = cfg->N, b = T.b, nc = N * N * N;
     double num[3] = {0, 0, 0}, den = 0.0;
     for (int c = 0; c < nc; ++c) {
-        const double* uc = u + (size_t)c * 4 * b;
+        const double* uc = u + (size_t)c * nv * b;
         const double* ac = ahat + (size_t)c * 3 * b;
         for (int q = 0; q < T.nq; ++q) {
             const double* ph = T.phi + q * b;
@@ -1363,7 +1371,25 @@ void orc_adi_project(const orc_cfg* cfg, double gamma, const double* u, double* 
     tabs_free(&T);
 }
 
+static int adi_rhs_impl(const orc_cfg* cfg, double gamma, const double* u, const double* ahat, double dt_pimax,
+                        double* dudt, double* work);
+
 int orc_adi_rhs(const orc_cfg* cfg, double gamma, const double* u, double dt_pimax, double* dudt)
+{
+    return adi_rhs_impl(cfg, gamma, u, NULL, dt_pimax, dudt, NULL);
+}
+
+/* with the driving a_h [c][3][b] (Sec. 4.2): momentum source rho (a_h - abar)
+ * and its work m.(a_h - abar) in the energy equation, abar = <rho a_h>/<rho>;
+ * *work = the volume integral of the energy source (its cell means times h^3) */
+int orc_adi_rhs_forced(const orc_cfg* cfg, double gamma, const double* u, const double* ahat, double dt_pimax,
+                       double* dudt, double* work)
+{
+    return adi_rhs_impl(cfg, gamma, u, ahat, dt_pimax, dudt, work);
+}
+
+static int adi_rhs_impl(const orc_cfg* cfg, double gamma, const double* u, const double* ahat, double dt_pimax,
+                        double* dudt, double* work)
 {
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
@@ -1373,6 +1399,8 @@ int orc_adi_rhs(const orc_cfg* cfg, double gamma, const double* u, double dt_pim
     double* prim = (double*)malloc(sizeof(double) * nc * 4 * b);
     orc_adi_project(cfg, gamma, u, prim);
     memset(dudt, 0, sizeof(double) * nc * 5 * b);
+    double abar[3] = {0, 0, 0};
+    if (ahat) forcing_mean_nv(cfg, u, 5, ahat, abar);
 
     /* volume integral, cell by cell */
     for (size_t c = 0; c < nc; ++c) {
@@ -1407,7 +1435,24 @@ int orc_adi_rhs(const orc_cfg* cfg, double gamma, const double* u, double dt_pim
                 for (int var = 0; var < 5; ++var)
                     rc[var * b + l] += T.wq[q] * (g[0] * F[var][0] + g[1] * F[var][1] + g[2] * F[var][2]) / (4.0 * h);
             }
+            if (ahat) {
+                const double* ac = ahat + c * 3 * b;
+                double se = 0.0;
+                for (int i = 0; i < 3; ++i) {
+                    double da = eval(&T, ac + i * b, ph) - abar[i];
+                    for (int l = 0; l < b; ++l) rc[(1 + i) * b + l] += 0.125 * T.wq[q] * ph[l] * rho * da;
+                    se += m[i] * da;
+                }
+                for (int l = 0; l < b; ++l) rc[4 * b + l] += 0.125 * T.wq[q] * ph[l] * se;
+            }
         }
+    }
+    if (work) {
+        /* the volume term of mode 0 vanishes (grad phi_0 = 0): dudt[c][4][0] is the
+         * cell mean of the energy source here, before the surface terms */
+        double w = 0.0;
+        for (size_t c = 0; c < nc; ++c) w += ahat ? dudt[c * 5 * b + 4 * b] : 0.0;
+        *work = w * h * h * h;
     }
 
     /* surface integral: one pass over interfaces, each flux added to both cells */
@@ -1544,7 +1589,23 @@ int orc_adi_limit(const orc_cfg* cfg, double gamma, double* u)
     return status;
 }
 
+static int adi_step_impl(const orc_cfg* cfg, double gamma, double* u, const double* ahat, double dt, double* injected);
+
 int orc_adi_step(const orc_cfg* cfg, double gamma, double* u, double dt)
+{
+    return adi_step_impl(cfg, gamma, u, NULL, dt, NULL);
+}
+
+/* one step with the driving; *injected = dt sum_s beta_s W_s, the work of the
+ * driving with the weights the SSP-RK scheme gives each stage's right-hand side
+ * in u^(n+1) (RK2: 1/2, 1/2; RK3: 1/6, 1/6, 2/3): the change of the total
+ * energy over the step */
+int orc_adi_step_forced(const orc_cfg* cfg, double gamma, double* u, const double* ahat, double dt, double* injected)
+{
+    return adi_step_impl(cfg, gamma, u, ahat, dt, injected);
+}
+
+static int adi_step_impl(const orc_cfg* cfg, double gamma, double* u, const double* ahat, double dt, double* injected)
 {
     int b = orc_nmodes(cfg->k);
     size_t n = (size_t)cfg->N * cfg->N * cfg->N * 5 * b;
@@ -1558,11 +1619,17 @@ int orc_adi_step(const orc_cfg* cfg, double gamma, double* u, double dt)
     static const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
     const double* A = (cfg->rk_stages == 2) ? a2 : a3;
     const double* B = (cfg->rk_stages == 2) ? b2 : b3;
+    static const double w2[2] = {0.5, 0.5}, w3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+    const double* W = (cfg->rk_stages == 2) ? w2 : w3;
+    double inj = 0.0;
     for (int s = 0; s < cfg->rk_stages; ++s) {
-        orc_adi_rhs(cfg, gamma, us, dt, L);
+        double work = 0.0;
+        adi_rhs_impl(cfg, gamma, us, ahat, dt, L, &work);
+        inj += dt * W[s] * work;
         for (size_t i = 0; i < n; ++i) us[i] = A[s] * un[i] + B[s] * (us[i] + dt * L[i]);
         status |= orc_adi_limit(cfg, gamma, us);
     }
+    if (injected) *injected = inj;
     memcpy(u, us, sizeof(double) * n);
     free(un);
     free(us);
@@ -1597,5 +1664,88 @@ int orc_adi_run(const orc_cfg* cfg, double gamma, double* u, int nsteps, double 
         if (dt_last) *dt_last = dtt;
     }
     free(bak);
+    return rc;
+}
+
+/* Uniform temperature restored after a step (Sec. 4.2: the gas is run with an
+ * adiabatic index close to 1 and its thermal energy reset): in every cell e
+ * becomes the projection of rho cs^2/(gamma-1) + |m|^2/(2 rho), i.e. p = cs^2 rho
+ * in the projected sense.  Returns the thermal energy taken out (the volume
+ * integral of the old minus the new e): the dissipated energy. */
+double orc_adi_reset(const orc_cfg* cfg, double gamma, double cs, double* u)
+{
+    tabs T;
+    tabs_init(&T, cfg->k, cfg->k + 1);
+    int N = cfg->N, b = T.b, nc = N * N * N;
+    double h = 1.0 / N, diss = 0.0;
+    double* en = (double*)malloc(sizeof(double) * b);
+    for (int c = 0; c < nc; ++c) {
+        double* uc = u + (size_t)c * 5 * b;
+        memset(en, 0, sizeof(double) * b);
+        for (int q = 0; q < T.nq; ++q) {
+            const double* ph = T.phi + q * b;
+            double rho = eval(&T, uc, ph), m[3];
+            for (int i = 0; i < 3; ++i) m[i] = eval(&T, uc + (1 + i) * b, ph);
+            double e = rho * cs * cs / (gamma - 1.0) + 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho;
+            for (int l = 0; l < b; ++l) en[l] += 0.125 * T.wq[q] * ph[l] * e;
+        }
+        diss += uc[4 * b] - en[0];
+        memcpy(uc + 4 * b, en, sizeof(double) * b);
+    }
+    free(en);
+    tabs_free(&T);
+    return diss * h * h * h;
+}
+
+/* driven run of the adiabatic system with the isothermal reset (cs > 0) after
+ * every step: the driving schedule of orc_run, dt from the CFL condition (or
+ * fixed_dt), retries on failure; accumulates the injected and dissipated
+ * energies */
+int orc_adi_run_driven(const orc_cfg* cfg, double gamma, double cs, double* u, orc_ou* ou, int use_forcing,
+                       double* ahat, int nsteps, double fixed_dt, double* t, double* dt_last, double* injected,
+                       double* dissipated)
+{
+    int b = orc_nmodes(cfg->k);
+    size_t n = (size_t)cfg->N * cfg->N * cfg->N * 5 * b;
+    double* bak = (double*)malloc(sizeof(double) * n);
+    double* amp = (double*)malloc(sizeof(double) * ORC_MAX_MODES * 6);
+    int rc = 0;
+    for (int st = 0; st < nsteps; ++st) {
+        const double* force = NULL;
+        if (use_forcing && ou->on && ou->t_off > 0.0 && *t > ou->t_off) ou->on = 0;
+        if (use_forcing && ou->on) {
+            while (*t >= ou->t_next) {
+                orc_ou_advance(ou);
+                ou->t_next += ou->dt_drive;
+                ou->dirty = 1;
+            }
+            if (ou->dirty) {
+                orc_ou_amplitudes(ou, amp);
+                orc_forcing_project(cfg, ou->nmodes, &ou->kvec[0][0], amp, ahat);
+                ou->dirty = 0;
+            }
+            force = ahat;
+        }
+        double dt = fixed_dt > 0.0 ? fixed_dt : orc_adi_dt(cfg, gamma, u);
+        int status = ORC_FAIL;
+        double dtt = dt, inj = 0.0;
+        memcpy(bak, u, sizeof(double) * n);
+        for (int r = 0; r <= 3; ++r) {
+            dtt = dt / (double)(1 << r);
+            status = adi_step_impl(cfg, gamma, u, force, dtt, &inj);
+            if (!(status & ORC_FAIL)) break;
+            memcpy(u, bak, sizeof(double) * n);
+        }
+        if (status & ORC_FAIL) {
+            rc = -1;
+            break;
+        }
+        *injected += inj;
+        if (cs > 0.0) *dissipated += orc_adi_reset(cfg, gamma, cs, u);
+        *t += dtt;
+        if (dt_last) *dt_last = dtt;
+    }
+    free(bak);
+    free(amp);
     return rc;
 }

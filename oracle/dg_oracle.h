@@ -96,6 +96,11 @@ int orc_adi_limit(const orc_cfg* cfg, double gamma, double* u);
 int orc_adi_step(const orc_cfg* cfg, double gamma, double* u, double dt);
 int orc_adi_run(const orc_cfg* cfg, double gamma, double* u, int nsteps, double fixed_dt, double* t,
                 double* dt_last);
+int orc_adi_rhs_forced(const orc_cfg* cfg, double gamma, const double* u, const double* ahat, double dt_pimax,
+                       double* dudt, double* work);
+int orc_adi_step_forced(const orc_cfg* cfg, double gamma, double* u, const double* ahat, double dt,
+                        double* injected);
+double orc_adi_reset(const orc_cfg* cfg, double gamma, double cs, double* u);
 int orc_rhs_local(const orc_cfg* cfg, const double* patch, const double* ahat_c, const double abar[3],
                   double dt_pimax, const double* nu, int64_t n, double* out);
 void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, double* y);
@@ -112,6 +117,11 @@ double orc_velocity_at(const orc_cfg* cfg, const double* u, const double x[3], d
 void orc_ou_init(orc_ou* ou, int kmin2, int kmax2, double zeta, double mach,
                  double cs, double L, uint64_t seed, double t_off);
 void orc_ou_advance(orc_ou* ou);
+/* driven adiabatic run with the isothermal reset (cs > 0) after every step;
+ * accumulates the injected and dissipated energies */
+int orc_adi_run_driven(const orc_cfg* cfg, double gamma, double cs, double* u, orc_ou* ou, int use_forcing,
+                       double* ahat, int nsteps, double fixed_dt, double* t, double* dt_last, double* injected,
+                       double* dissipated);
 void orc_ou_amplitudes(const orc_ou* ou, double* ahat_modes /* [nm][3][2] */);
 void orc_forcing_project(const orc_cfg* cfg, int nmodes, const int32_t* kvec,
                          const double* amp, double* ahat);

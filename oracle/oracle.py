@@ -103,6 +103,12 @@ def lib():
         _lib.orc_adi_limit.argtypes = [C.POINTER(Cfg), C.c_double, d]
         _lib.orc_adi_step.argtypes = [C.POINTER(Cfg), C.c_double, d, C.c_double]
         _lib.orc_adi_run.argtypes = [C.POINTER(Cfg), C.c_double, d, C.c_int, C.c_double, d, d]
+        _lib.orc_adi_rhs_forced.argtypes = [C.POINTER(Cfg), C.c_double, d, d, C.c_double, d, d]
+        _lib.orc_adi_step_forced.argtypes = [C.POINTER(Cfg), C.c_double, d, d, C.c_double, d]
+        _lib.orc_adi_reset.restype = C.c_double
+        _lib.orc_adi_reset.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, d]
+        _lib.orc_adi_run_driven.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, d, C.POINTER(OU), C.c_int, d,
+                                            C.c_int, C.c_double, d, d, d, d]
         _lib.orc_av_features.argtypes = [C.POINTER(Cfg), d, C.c_double, d, d]
         _lib.orc_pi_nu.restype = C.c_double
         _lib.orc_pi_nu.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double, C.c_double]
@@ -442,3 +448,32 @@ def adi_run(cfg: Cfg, gamma: float, u: np.ndarray, nsteps: int, fixed_dt: float 
     dl = C.c_double(0.0)
     rc = lib().orc_adi_run(C.byref(cfg), gamma, _p(u), nsteps, fixed_dt, C.byref(tt), C.byref(dl))
     return rc, tt.value, dl.value
+
+
+def adi_rhs_forced(cfg: Cfg, gamma: float, u: np.ndarray, ahat: np.ndarray, dt_pimax: float = 0.0):
+    """RHS with the driving a_h; returns (dudt, work integral of the energy source)."""
+    out = np.zeros((cfg.N ** 3, 5, nmodes(cfg.k)))
+    w = C.c_double(0.0)
+    lib().orc_adi_rhs_forced(C.byref(cfg), gamma, _p(u), _p(ahat), dt_pimax, _p(out), C.byref(w))
+    return out, w.value
+
+
+def adi_reset(cfg: Cfg, gamma: float, cs: float, u: np.ndarray) -> float:
+    """Isothermal reset of the thermal energy in place; returns the energy taken out."""
+    return lib().orc_adi_reset(C.byref(cfg), gamma, cs, _p(u))
+
+
+def adi_run_driven(cfg: Cfg, gamma: float, cs: float, u: np.ndarray, nsteps: int, forcing: Forcing | None = None,
+                   fixed_dt: float = 0.0, t: float = 0.0, ahat: np.ndarray | None = None, budget=(0.0, 0.0)):
+    """Driven adiabatic run with the isothermal reset (cs > 0); returns
+    (rc, t, dt_last, ahat, (injected, dissipated))."""
+    if ahat is None:
+        ahat = np.zeros(_shape(cfg, 3))
+    tt = C.c_double(t)
+    dl = C.c_double(0.0)
+    inj = C.c_double(budget[0])
+    dis = C.c_double(budget[1])
+    ou = forcing.ou if forcing is not None else OU()
+    rc = lib().orc_adi_run_driven(C.byref(cfg), gamma, cs, _p(u), C.byref(ou), 1 if forcing is not None else 0,
+                                  _p(ahat), nsteps, fixed_dt, C.byref(tt), C.byref(dl), C.byref(inj), C.byref(dis))
+    return rc, tt.value, dl.value, ahat, (inj.value, dis.value)

@@ -293,3 +293,72 @@ def test_sod_pair_converges_to_the_exact_solution():
     # discontinuities: first order at best (measured 0.034 -> 0.018, rate 0.88)
     assert errs[1] < 0.6 * errs[0], errs
     assert errs[1] < 0.025, errs
+
+
+# ---- driving and the near-isothermal energy accounting (Sec. 4.2) ----
+def rest_state(N, k, cs=1.0, gamma=G):
+    b = I.nmodes(k)
+    u = np.zeros((N ** 3, 5, b))
+    u[:, 0, 0] = 1.0
+    u[:, 4, 0] = cs * cs / (gamma - 1)
+    return u
+
+
+def totals(N, u):
+    h3 = (1.0 / N) ** 3
+    return u[:, :, 0].sum(axis=0) * h3
+
+
+def test_driven_energy_budget_closes():
+    # from rest, driven, with the isothermal reset after every step:
+    # E(t) = E(0) + injected - dissipated to round-off, momentum unchanged
+    N, k, g, cs = 4, 2, 1.0001, 1.0
+    u = rest_state(N, k, cs, g)
+    cfg = O.make_cfg(N, k)
+    E0 = totals(N, u)[4]
+    rc, t, _, _, (inj, dis) = O.adi_run_driven(cfg, g, cs, u, 8, forcing=O.Forcing(mach=1.0, zeta=0.5, seed=3))
+    assert rc == 0 and inj > 0 and dis >= 0
+    tot = totals(N, u)
+    assert abs(tot[4] - (E0 + inj - dis)) < 1e-12 * E0
+    assert np.abs(tot[1:4]).max() < 1e-13
+    # without the reset the total energy changes by the injected work alone
+    u2 = rest_state(N, k, cs, g)
+    rc, _, _, _, (inj2, dis2) = O.adi_run_driven(cfg, g, 0.0, u2, 8, forcing=O.Forcing(mach=1.0, zeta=0.5, seed=3))
+    assert rc == 0 and dis2 == 0.0
+    assert abs(totals(N, u2)[4] - (E0 + inj2)) < 1e-12 * E0
+
+
+def test_reset_of_a_state_at_rest_is_exact():
+    N, k, g, cs = 3, 2, 1.4, 0.7
+    u = I.random_energy_state(N, k, seed=9, v_rms=0.0, p_mean=2.0, gamma=g)
+    u[:, 1:4, :] = 0.0
+    cfg = O.make_cfg(N, k)
+    e_before = totals(N, u)[4]
+    d = O.adi_reset(cfg, g, cs, u)
+    # rho in P_k, v = 0: e = rho cs^2/(gamma-1) exactly
+    assert np.allclose(u[:, 4, :], u[:, 0, :] * cs * cs / (g - 1), rtol=1e-13, atol=1e-15)
+    assert d == pytest.approx(e_before - totals(N, u)[4], rel=1e-12)
+
+
+def test_near_isothermal_gas_with_reset_follows_the_isothermal_system():
+    # an adiabatic gas with the uniform-temperature reset against the
+    # isothermal oracle, same driving: the fields differ by O(gamma - 1)
+    # (measured 1.4e-5 at gamma = 1.0001, 100x that at 1.01)
+    N, k, cs = 4, 2, 1.0
+    fo = dict(mach=2.0, zeta=0.5, seed=5)
+    cfg = O.make_cfg(N, k)
+    u4 = I.random_state(N, k, seed=17, v_rms=0.5)
+    ref = u4.copy()
+    rc, t4, _, _ = O.run(cfg, ref, 5, forcing=O.Forcing(**fo))
+    assert rc == 0
+    dev = {}
+    for g in (1.0001, 1.01):
+        u5 = np.zeros((N ** 3, 5, u4.shape[2]))
+        u5[:, :4] = u4
+        O.adi_reset(cfg, g, cs, u5)
+        rc, t5, _, _, _ = O.adi_run_driven(cfg, g, cs, u5, 5, forcing=O.Forcing(**fo))
+        assert rc == 0
+        assert t5 == pytest.approx(t4, rel=1e-4 if g < 1.001 else 1e-2)
+        dev[g] = max(np.linalg.norm(u5[:, v] - ref[:, v]) / np.linalg.norm(ref[:, v]) for v in range(4))
+    assert dev[1.0001] < 1e-4, dev
+    assert 30 < dev[1.01] / dev[1.0001] < 300, dev
