@@ -390,7 +390,7 @@ int dg_power_spectrum(dg_ctx* ctx, void* work, size_t work_bytes, int nbins, dou
  * the cell mean (theta_p the largest factor keeping p at the floor, from the
  * quadratic in theta); a cell mean at or below the floor fails the step,
  * which is retried with dt/2 up to three times.  FP32 or FP64 (no x3, no
- * forcing, no learned sensor, no diffusion: DG_EINVAL). */
+ * learned sensor, no diffusion: DG_EINVAL). */
 typedef struct dg_adi_ctx dg_adi_ctx;
 typedef struct {
     int32_t precision;     /* DG_PREC_F32 or DG_PREC_F64                          */
@@ -424,6 +424,21 @@ int dg_adi_rhs(dg_adi_ctx* ctx, const void* u_in, void* dudt, double dt_pimax);
  * step to read the positivity status; DG_EPOSITIVITY leaves the state at the
  * start of the failed step. */
 int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_last);
+/* Driving of the adiabatic system (Sec. 4.2), the same OU process and forcing
+ * projection as dg_set_forcing with the sound speed cs_ref in its time scale
+ * and amplitude; the momentum source rho (a_h - abar) (abar = <rho a_h>/<rho>
+ * of each stage's state) and its work m.(a_h - abar) in the energy equation.
+ * The injected energy of a step is dt sum_s beta_s W_s with W_s the volume
+ * integral of the energy source of stage s and beta_s its weight in u^(n+1)
+ * (RK2: 1/2, 1/2; RK3: 1/6, 1/6, 2/3): exactly the change of the total energy. */
+int dg_adi_set_forcing(dg_adi_ctx* ctx, const dg_forcing* f, double cs_ref);
+/* cs > 0: after every step the uniform temperature p = cs^2 rho is restored (e
+ * becomes the projection of rho cs^2/(gamma-1) + |m|^2/(2 rho)); with gamma
+ * close to 1 this emulates the isothermal gas and the thermal energy taken out
+ * measures the dissipation (Sec. 4.2).  0: off (default). */
+int dg_adi_set_reset(dg_adi_ctx* ctx, double cs);
+/* out[0] = injected, out[1] = dissipated energy since dg_adi_set_state. */
+int dg_adi_energy_budget(dg_adi_ctx* ctx, double* out);
 /* FP64 diagnostics of the current state: out[0..7] = mass, momentum (3),
  * total energy (integrals over the box), kinetic energy (volume quadrature of
  * |m|^2/(2 rho)), minimum density and minimum pressure at the volume points. */

@@ -125,6 +125,9 @@ def lib() -> C.CDLL:
         L.dg_adi_rhs.argtypes = [vp, vp, vp, d]
         L.dg_adi_step.argtypes = [vp, i, d, C.POINTER(d), C.POINTER(d)]
         L.dg_adi_totals.argtypes = [vp, C.POINTER(d)]
+        L.dg_adi_set_forcing.argtypes = [vp, C.POINTER(Forcing), d]
+        L.dg_adi_set_reset.argtypes = [vp, d]
+        L.dg_adi_energy_budget.argtypes = [vp, C.POINTER(d)]
         L.dg_rhs_noalloc.argtypes = [C.POINTER(Mesh), i, d, C.POINTER(NuParams), i, vp, vp, vp, d, vp]
         L.dg_profile.argtypes = [vp, i]
         L.dg_profile_read.argtypes = [vp, C.POINTER(Prof)]
@@ -144,7 +147,7 @@ EXPORTS = ("dg_scratch_bytes", "dg_vhat_bytes", "dg_init", "dg_free", "dg_last_e
            "dg_mlp_train", "dg_mlp_grad", "dg_mlp_forward", "dg_av_nu", "dg_av_nu_carried", "dg_density_pdf", "dg_structure_function",
            "dg_analysis_bytes", "dg_power_spectrum", "dg_adi_buffer_bytes", "dg_adi_init", "dg_adi_free",
            "dg_adi_last_error", "dg_adi_set_state", "dg_adi_get_state", "dg_adi_project", "dg_adi_rhs",
-           "dg_adi_step", "dg_adi_totals")
+           "dg_adi_step", "dg_adi_totals", "dg_adi_set_forcing", "dg_adi_set_reset", "dg_adi_energy_budget")
 
 MAX_BINS = 2000
 

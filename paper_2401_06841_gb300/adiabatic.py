@@ -109,6 +109,21 @@ class AdiabaticSolver:
         self._check(self.L.dg_adi_step(self.h, nsteps, fixed_dt, C.byref(t), C.byref(dtl)), self.h)
         return t.value, dtl.value
 
+    def set_forcing(self, mach: float, zeta: float = 0.5, seed: int = 0, kmin2: int = 1, kmax2: int = 9,
+                    t_off: float = 0.0, on: bool = True, cs_ref: float = 1.0):
+        f = B.Forcing(1 if on else 0, kmin2, kmax2, zeta, mach, seed, t_off)
+        self._check(self.L.dg_adi_set_forcing(self.h, C.byref(f), cs_ref), self.h)
+
+    def set_reset(self, cs: float):
+        """cs > 0: restore the uniform temperature p = cs^2 rho after every step."""
+        self._check(self.L.dg_adi_set_reset(self.h, cs), self.h)
+
+    def energy_budget(self):
+        """(injected, dissipated) energy since set_state."""
+        out = (C.c_double * 2)()
+        self._check(self.L.dg_adi_energy_budget(self.h, out), self.h)
+        return out[0], out[1]
+
     def totals(self) -> dict:
         out = (C.c_double * 8)()
         self._check(self.L.dg_adi_totals(self.h, out), self.h)

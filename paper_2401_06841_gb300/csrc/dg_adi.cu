@@ -52,8 +52,16 @@ cudaError_t adi_k(const Launch& L, double gamma, const AdiLaunch& t)
     a.rk_b = T(t.rk_b);
     a.dt_pimax = t.dt_pimax;
     a.flags = t.flags;
+    a.ahat = static_cast<const T*>(t.ahat);
+    a.partials = L.partials;
+    a.abar_in = t.abar_in;
+    a.abar_out = t.abar_out;
+    a.beta = t.beta;
+    a.cs_reset = t.cs_reset;
+    if ((t.flags & F_FORCE) && !t.ahat) return cudaErrorInvalidValue;
     if (t.mode == ADI_PROJECT) return adi_launch<T, K, ADI_PROJECT>(L, a);
     if (t.mode == ADI_RHS) return adi_launch<T, K, ADI_RHS>(L, a);
+    if (t.mode == ADI_RESET) return adi_launch<T, K, ADI_RESET>(L, a);
     return adi_launch<T, K, ADI_STAGE>(L, a);
 }
 

@@ -12,7 +12,15 @@
 //   ADI_STAGE    right-hand side, SSP-RK stage combine, positivity of density
 //                and pressure (Sec. 3.1) -> out = u^(s+1); with F_NEXTPROJ also
 //                the projections of u^(s+1) -> pr_out (the next stage's pr_in)
-// The right-hand side needs the projections of u_in in pr_in.
+//   ADI_RESET    uniform temperature restored in place (Sec. 4.2): e becomes the
+//                projection of rho cs^2/(gamma-1) + |m|^2/(2 rho)
+// The right-hand side needs the projections of u_in in pr_in.  With the
+// driving (F_FORCE, a_h in ahat) the right-hand side adds rho (a_h - abar) to
+// the momentum and its work m.(a_h - abar) to the energy; abar = <rho a_h> /
+// <rho> comes from the projections (FP64 sums, deterministic last-block
+// reduction into ctl->abar2[abar_out]).  FP64 accumulators in ctl->diag:
+// [1] injected energy (stage: beta_s dt times the volume integral of the energy
+// source), [2] dissipated energy (reset: the thermal energy taken out).
 #pragma once
 
 #include "dg_launch.cuh"
@@ -35,7 +43,12 @@ struct AdiArgs {
     double gamma;
     T rk_a, rk_b;
     double dt_pimax; // right-hand-side mode: dt of the viscous-pressure cap
-    int flags;       // F_DT (projection mode), F_NEXTPROJ (stage mode)
+    int flags;       // F_DT (projection mode), F_NEXTPROJ (stage mode), F_FORCE
+    const T* ahat;   // [c][3][b] driving (F_FORCE)
+    double* partials;  // [grid][16] block partials of the last-block reductions
+    int abar_in, abar_out;  // slots of ctl->abar2 read by the right-hand side / written by a projection
+    double beta;     // stage mode: weight of this stage's right-hand side in u^(n+1)
+    double cs_reset; // reset mode: the isothermal sound speed
 };
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
@@ -46,7 +59,7 @@ struct AdiCfg {
     static constexpr int b = C::b, nq = C::nq, ns = C::ns, nf = C::nf, TC = C::TC, NT = C::NT;
     static constexpr int KP = C::KP, NQP = C::NQP, NP = C::NP, B2K = C::B2K, NSP = C::NSP, B2N = C::B2N;
     static constexpr int FE = 12;  // rho, m_x, m_y, m_z, e, grad rho (3), div m, 3 zero rows
-    static constexpr int FP = 9;   // m v + P (6 symmetric components), (e + P) v (3)
+    static constexpr int FP = 13;  // m v + P (6), (e + P) v (3), rho (a - abar) (3), m.(a - abar)
     static constexpr int LDA = KP, LDV = NQP + 4, LDP = NP, LDC2 = B2K, LDT = NSP + 4, LDL = B2N;
     static constexpr int RE = TC * FE, RP = TC * FP;
     static constexpr int RC = TC * 20;  // face rows ((cell, side, self/neighbour), (rho, v_x, v_y, v_z, p))
@@ -54,13 +67,13 @@ struct AdiCfg {
     static constexpr int oU = r4(C::tabsz);
     static constexpr int oPr = oU + r4(TC * 5 * b);
     static constexpr int oR = oPr + r4(TC * 4 * b);
-    static constexpr int oUn = oR + r4(TC * 5 * b);
-    static constexpr int oA = oUn + r4(TC * 5 * b);
+    static constexpr int oAh = oR + r4(TC * 5 * b);
+    static constexpr int oA = oAh + r4(TC * 3 * b);
     static constexpr int SZA = cmax(RE * LDA, RP * LDP);
     static constexpr int oBig = oA + r4(SZA);
     static constexpr int FA = cmax(RC * LDC2, RL * LDT);
     static constexpr int FB = cmax(RC * LDT, RL * LDL);
-    static constexpr int BIG = cmax(RE * LDV, FA + FB);
+    static constexpr int BIG = cmax(cmax(RE * LDV, RP * LDV), FA + FB);
     static constexpr int total = oBig + BIG;
 };
 
@@ -165,7 +178,7 @@ __device__ __forceinline__ void adi_load(T* dst, const T* src, int n, int valid,
 // valid cells into smax.  Starts and ends with the block in step.
 template <typename T, int K>
 __device__ __forceinline__ void adi_project_tile(T* sm, const T* sU, const T* tabs, const AdiArgs<T>& a, long c0,
-                                                 int nvalid, T gamma, T& smax)
+                                                 int nvalid, T gamma, T& smax, double* sums)
 {
     using A = AdiCfg<K>;
     using C = TileCfg<K, BK_FMA>;
@@ -225,7 +238,40 @@ __device__ __forceinline__ void adi_project_tile(T* sm, const T* sU, const T* ta
         const int r = e / b, l = e % b;
         a.pr_out[c0 * 4 * b + e] = sP[r * LDP + l];
     }
+    // driving: <rho a_h> = sum_l rho_l a_l per cell (orthonormal basis) and <rho>
+    if ((a.flags & F_FORCE) && tid < TC * 3) {
+        const int c = tid / 3, i = tid % 3;
+        if (c < nvalid) {
+            const T* ah = sm + A::oAh + (c * 3 + i) * b;
+            T s = T(0);
+#pragma unroll
+            for (int l = 0; l < b; ++l) s += sU[c * 5 * b + l] * ah[l];
+            sums[i] += (double)s;
+            if (i == 0) sums[3] += (double)sU[c * 5 * b];
+        }
+    }
     __syncthreads();
+}
+
+// sum over the block of one FP64 value per thread, then over the blocks in a
+// fixed order (last-block reduction, no waiting): true in the last block, with
+// the total in *tot
+template <int NT>
+__device__ __forceinline__ bool adi_reduce(double* partials, double* s_buf, double* s_tot, unsigned int* counter,
+                                           const double* v, int nv)
+{
+    double mine[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < nv; ++i) {
+        s_buf[threadIdx.x] = v[i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int j = 0; j < NT; ++j) t += s_buf[j];
+            mine[i] = t;
+        }
+        __syncthreads();
+    }
+    return last_block_reduce<NT>(partials, mine, nv, counter, s_tot, s_buf);
 }
 
 // FP32: two blocks per SM (128 registers); FP64 fits one block in shared memory
@@ -244,12 +290,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
     T* sU = sm + A::oU;
     T* sPr = sm + A::oPr;
     T* sR = sm + A::oR;
-    T* sUn = sm + A::oUn;
     T* sA = sm + A::oA;
     T* sP = sA;
     T* sBig = sm + A::oBig;
     __shared__ unsigned int s_status;
     __shared__ unsigned long long s_smax;
+    __shared__ double s_tot[8];
+    T* sAh = sm + A::oAh;
+    const bool force = (a.flags & F_FORCE) != 0;
+    double sums[4] = {0.0, 0.0, 0.0, 0.0};  // <rho a_h> (3), <rho> of the projected tiles
+    double work = 0.0;                      // stage: volume integral of the energy source / h^3
+    double diss = 0.0;                      // reset: thermal energy taken out / h^3
 
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     for (int e = tid; e < C::tabsz; e += NT) sm[e] = a.tab[e];
@@ -261,13 +312,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
     const T gamma = T(a.gamma), g1 = gamma - T(1), fill_e = T(1) / g1;
     const T two_h = T(2.0 / a.ph.h), inv4h = T(0.25 / a.ph.h);
     const T eps = T(a.ph.floor_);
-    T dt = T(a.dt_pimax);
+    double dtd = a.dt_pimax;
     if constexpr (MODE == ADI_STAGE) {
         // the step's dt: CFL bound of u^n (projection of stage 1), prescribed dt, retry factor
         const double smax = __longlong_as_double((long long)a.ctl->smax);
-        const double dtd = (a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / smax) * a.ctl->dt_scale;
-        dt = T(dtd);
+        dtd = (a.ctl->fixed_dt > 0.0 ? a.ctl->fixed_dt : a.ctl->dt_num / smax) * a.ctl->dt_scale;
         if (blockIdx.x == 0 && tid == 0) a.ctl->dt = dtd;
+    }
+    const T dt = T(dtd);
+    T ab0 = T(0), ab1 = T(0), ab2 = T(0);
+    if (force && (MODE == ADI_RHS || MODE == ADI_STAGE)) {
+        ab0 = T(a.ctl->abar2[a.abar_in][0]);
+        ab1 = T(a.ctl->abar2[a.abar_in][1]);
+        ab2 = T(a.ctl->abar2[a.abar_in][2]);
     }
     // sup |phi_m| of the mode m = lane (positivity bound), 0 past the modes
     T my_sup = T(0);
@@ -282,18 +339,63 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
         const long c0 = tile * TC;
         const int nvalid = (int)((a.ncell - c0) < TC ? (a.ncell - c0) : TC);
         adi_load<T, NT, 5, b>(sU, a.u_in + c0 * 5 * b, TC * 5 * b, nvalid * 5 * b, fill_e);
+        if (force && MODE != ADI_RESET) {
+            for (int e = 4 * tid; e < TC * 3 * b; e += 4 * NT) {
+                T v[4];
+                ld4_guard<T>(a.ahat + c0 * 3 * b, e, nvalid * 3 * b, v);
+                st4<T>(sAh + e, v);
+            }
+        }
         if constexpr (MODE == ADI_PROJECT) {
             __syncthreads();
-            adi_project_tile<T, K>(sm, sU, tabs, a, c0, nvalid, gamma, smax);
+            adi_project_tile<T, K>(sm, sU, tabs, a, c0, nvalid, gamma, smax, sums);
+        } else if constexpr (MODE == ADI_RESET) {
+            __syncthreads();
+            // rho, m at the volume points; e = rho cs^2/(gamma-1) + |m|^2/(2 rho) there; projected
+            for (int e = tid; e < TC * 4 * KP; e += NT) {
+                const int r = e / KP, l = e % KP, c = r / 4, f = r % 4;
+                sA[r * LDA + l] = l < b ? sU[(c * 5 + f) * b + l] : T(0);
+            }
+            __syncthreads();
+            mm<T, BK_FMA, TC * 4, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sBig);
+            __syncthreads();
+            const T cth = T(a.cs_reset * a.cs_reset) / g1;
+            constexpr int PER = (TC * NQP + NT - 1) / NT;
+            T ev[PER];
+#pragma unroll
+            for (int it = 0; it < PER; ++it) {
+                const int e = tid + it * NT;
+                ev[it] = T(0);
+                if (e < TC * NQP) {
+                    const int c = e / NQP, q = e % NQP;
+                    if (q < nq) {
+                        const T* v = sBig + (c * 4) * LDV + q;
+                        const T rho = v[0], mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV];
+                        ev[it] = rho * cth + T(0.5) * (mx * mx + my * my + mz * mz) / rho;
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int it = 0; it < PER; ++it) {
+                const int e = tid + it * NT;
+                if (e < TC * NQP) sBig[(e / NQP) * LDV + e % NQP] = ev[it];
+            }
+            __syncthreads();
+            mm<T, BK_FMA, TC, NP, NQP, LDV, LDP, NT>(sBig, tabs, C::oWPhi, sP);
+            __syncthreads();
+            if (tid < TC && tid < nvalid) diss += (double)sU[(tid * 5 + 4) * b] - (double)sP[tid * LDP];
+            for (int e = tid; e < nvalid * b; e += NT) {
+                const int c = e / b, l = e % b;
+                a.out[(c0 + c) * 5 * b + 4 * b + l] = sP[c * LDP + l];
+            }
+            __syncthreads();
         } else {
         // ---- right-hand side: stage the projections (and u^n) of the tile ----
         for (int e = 4 * tid; e < TC * 4 * b; e += 4 * NT) {
             T v[4];
             ld4_guard<T>(a.pr_in + c0 * 4 * b, e, nvalid * 4 * b, v);
             st4<T>(sPr + e, v);
-        }
-        if constexpr (MODE == ADI_STAGE) {
-            if (a.rk_a != T(0)) adi_load<T, NT, 5, b>(sUn, a.u_n + c0 * 5 * b, TC * 5 * b, nvalid * 5 * b, fill_e);
         }
         __syncthreads();
         // ---- evaluation coefficients: rho, m, e, grad rho, div m (field-major threads) ----
@@ -322,6 +424,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 modal_grad<T, K, 2>(u + 3 * b, t2, two_h);
 #pragma unroll
                 for (int l = 0; l < b; ++l) out[l] += t2[l];
+            } else if (f < 12 && force) {
+#pragma unroll
+                for (int l = 0; l < b; ++l) out[l] = sAh[(c * 3 + f - 9) * b + l];
             }
 #pragma unroll
             for (int l = 0; l < KP; l += 4) st4<T>(row + l, out + l);
@@ -332,12 +437,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
         // ---- pointwise volume physics (Sec. 3.1: Pi at the internal points) ----
         {
             constexpr int PER = (TC * NQP + NT - 1) / NT;
-            T fl[PER][9];
+            T fl[PER][13];
 #pragma unroll
             for (int it = 0; it < PER; ++it) {
                 const int e = tid + it * NT;
 #pragma unroll
-                for (int g = 0; g < 9; ++g) fl[it][g] = T(0);
+                for (int g = 0; g < 13; ++g) fl[it][g] = T(0);
                 if (e < TC * NQP) {
                     const int c = e / NQP, q = e % NQP;
                     if (q < nq) {
@@ -358,6 +463,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                         fl[it][6] = (en + P) * vx;
                         fl[it][7] = (en + P) * vy;
                         fl[it][8] = (en + P) * vz;
+                        if (force) {
+                            const T dx = v[9 * LDV] - ab0, dy = v[10 * LDV] - ab1, dz = v[11 * LDV] - ab2;
+                            fl[it][9] = rho * dx;
+                            fl[it][10] = rho * dy;
+                            fl[it][11] = rho * dz;
+                            fl[it][12] = mx * dx + my * dy + mz * dz;
+                        }
                     }
                 }
             }
@@ -368,7 +480,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 if (e < TC * NQP) {
                     const int c = e / NQP, q = e % NQP;
 #pragma unroll
-                    for (int g = 0; g < 9; ++g) sBig[(c * 9 + g) * LDV + q] = fl[it][g];
+                    for (int g = 0; g < 13; ++g) sBig[(c * 13 + g) * LDV + q] = fl[it][g];
                 }
             }
         }
@@ -381,7 +493,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
             T r[b];
 #pragma unroll
             for (int l = 0; l < b; ++l) r[l] = T(0);
-            const T* P = sP + c * 9 * LDP;
+            const T* P = sP + c * 13 * LDP;
             if (v == 0) {
                 const T* u = sU + c * 5 * b;
                 modal_grad_T_acc<T, K, 0>(u + b, r, two_h);
@@ -395,10 +507,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 modal_grad_T_acc<T, K, 0>(P + cx * LDP, r, two_h);
                 modal_grad_T_acc<T, K, 1>(P + cy * LDP, r, two_h);
                 modal_grad_T_acc<T, K, 2>(P + cz * LDP, r, two_h);
+                if (force) {
+#pragma unroll
+                    for (int l = 0; l < b; ++l) r[l] += P[(9 + i) * LDP + l];
+                }
             } else {
                 modal_grad_T_acc<T, K, 0>(P + 6 * LDP, r, two_h);
                 modal_grad_T_acc<T, K, 1>(P + 7 * LDP, r, two_h);
                 modal_grad_T_acc<T, K, 2>(P + 8 * LDP, r, two_h);
+                if (force) {
+#pragma unroll
+                    for (int l = 0; l < b; ++l) r[l] += P[12 * LDP + l];
+                    if (MODE == ADI_STAGE && c < nvalid) work += (double)P[12 * LDP];  // cell mean of the work
+                }
             }
 #pragma unroll
             for (int l = 0; l < b; ++l) sR[(c * 5 + v) * b + l] = r[l];
@@ -493,8 +614,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
             __syncthreads();
         } else {
             // ---- SSP-RK stage combine (Sec. 7) ----
+            // u^n straight from global memory (read once, coalesced)
             for (int e = tid; e < TC * 5 * b; e += NT) {
-                const T un = (a.rk_a != T(0)) ? sUn[e] : T(0);
+                const T un = (a.rk_a != T(0) && e < nvalid * 5 * b) ? a.u_n[c0 * 5 * b + e] : T(0);
                 sU[e] = a.rk_a * un + a.rk_b * (sU[e] + dt * sR[e]);
             }
             __syncthreads();
@@ -605,11 +727,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
             }
             __syncthreads();
             // the next stage's projections of v and p, from the new state in shared memory
-            if (a.flags & F_NEXTPROJ) adi_project_tile<T, K>(sm, sU, tabs, a, c0, nvalid, gamma, smax);
+            if (a.flags & F_NEXTPROJ) adi_project_tile<T, K>(sm, sU, tabs, a, c0, nvalid, gamma, smax, sums);
         }
         }  // right-hand-side modes
     }
-    // ---- block reductions ----
+    // ---- block reductions (their buffer is the big region, free after the tile loop) ----
+    __syncthreads();
+    double* s_buf = reinterpret_cast<double*>(sm + A::oBig);
+    static_assert(A::BIG * sizeof(T) >= NT * sizeof(double), "reduction buffer");
+    const double h3 = a.ph.h * a.ph.h * a.ph.h;
     if constexpr (MODE == ADI_PROJECT) {
         if (a.flags & F_DT) {
             const double sp = (double)smax;
@@ -617,9 +743,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
             __syncthreads();
             if (tid == 0) atomicMax(&a.ctl->smax, s_smax);
         }
-    } else {
-        __syncthreads();
+    }
+    if constexpr (MODE == ADI_RHS || MODE == ADI_STAGE) {
         if (tid == 0 && s_status) atomicOr(&a.ctl->status, s_status);
+    }
+    // abar of the projected states: <rho a_h> / <rho>
+    if (force && (MODE == ADI_PROJECT || (MODE == ADI_STAGE && (a.flags & F_NEXTPROJ)))) {
+        if (adi_reduce<NT>(a.partials, s_buf, s_tot, &a.ctl->cnt_proj, sums, 4) && tid == 0)
+            for (int i = 0; i < 3; ++i) a.ctl->abar2[a.abar_out][i] = s_tot[i] / s_tot[3];
+    }
+    // injected energy of the stage, dissipated energy of the reset (FP64 accumulators)
+    if constexpr (MODE == ADI_STAGE) {
+        if (force && adi_reduce<NT>(a.partials + 8, s_buf, s_tot, &a.ctl->cnt_diag, &work, 1) && tid == 0)
+            a.ctl->diag[1] += a.beta * dtd * s_tot[0] * h3;
+    }
+    if constexpr (MODE == ADI_RESET) {
+        if (adi_reduce<NT>(a.partials + 8, s_buf, s_tot, &a.ctl->cnt_diag, &diss, 1) && tid == 0)
+            a.ctl->diag[2] += s_tot[0] * h3;
     }
 }
 

@@ -1681,6 +1681,16 @@ struct dg_adi_ctx {
     int cur = 0;
     void* prim = nullptr;
     void* prim2 = nullptr;  // second projection buffer (scratch)
+    void* ahat = nullptr;   // driving a_h [c][3][b] (scratch)
+    int* d_kvec = nullptr;
+    double* d_amp = nullptr;
+    void* gtab = nullptr;
+    Rule1 r1{};
+    Driver drv;
+    bool forcing_active = false;
+    double cs_ref = 0.0;    // sound speed the driving is scaled with
+    double cs_reset = 0.0;  // > 0: uniform temperature restored after every step
+    double injected = 0.0, dissipated = 0.0;
     char* scratch = nullptr;
     Ctl* ctl = nullptr;
     void* ttab = nullptr;
@@ -1709,13 +1719,15 @@ int afail(dg_adi_ctx* c, int code, const std::string& msg)
     } while (0)
 
 struct AdiScratch {
-    size_t ctl, ttab, partials, prim2, total;
+    size_t ctl, ttab, partials, prim2, ahat, kvec, amp, gtab, total;
 };
 
-// control block, tables, reduction partials, and the second projection buffer
-// (stages alternate between it and the caller's)
-AdiScratch adi_scratch(int K, size_t prim_bytes)
+// control block, tables, reduction partials, the second projection buffer
+// (stages alternate between it and the caller's), the driving a_h and the
+// forcing projection's mode list, amplitudes and 1D factors
+AdiScratch adi_scratch(int K, int N, size_t elem)
 {
+    const size_t nc = (size_t)N * N * N, b = (size_t)(K + 1) * (K + 2) * (K + 3) / 6;
     AdiScratch s{};
     size_t off = 0;
     s.ctl = off;
@@ -1723,9 +1735,17 @@ AdiScratch adi_scratch(int K, size_t prim_bytes)
     s.ttab = off;
     off = align256(off + sizeof(double) * ttab_total(K));
     s.partials = off;
-    off = align256(off + sizeof(double) * 8 * kMaxGrid);
+    off = align256(off + sizeof(double) * 16 * kMaxGrid);
     s.prim2 = off;
-    off = align256(off + prim_bytes);
+    off = align256(off + nc * 4 * b * elem);
+    s.ahat = off;
+    off = align256(off + nc * 3 * b * elem);
+    s.kvec = off;
+    off = align256(off + sizeof(int) * 3 * kMaxModes);
+    s.amp = off;
+    off = align256(off + sizeof(double) * 6 * kMaxModes);
+    s.gtab = off;
+    off = align256(off + sizeof(double) * 2 * (size_t)N * kForceNK * (K + 1));
     s.total = off;
     return s;
 }
@@ -1751,6 +1771,8 @@ Launch adi_make_launch(const dg_adi_ctx* c)
     L.partials = c->partials;
     L.nsm = c->nsm;
     L.bk = 0;
+    L.r1 = c->r1;
+    L.gtab = c->gtab;
     return L;
 }
 
@@ -1774,7 +1796,7 @@ int dg_adi_buffer_bytes(const dg_mesh* mesh, int order, int precision, size_t* s
     const size_t el = precision == DG_PREC_F64 ? sizeof(double) : sizeof(float);
     if (state_bytes) *state_bytes = n * 5 * b * el;
     if (prim_bytes) *prim_bytes = n * 4 * b * el;
-    if (scratch_bytes) *scratch_bytes = adi_scratch(order, n * 4 * b * el).total;
+    if (scratch_bytes) *scratch_bytes = adi_scratch(order, mesh->n[0], el).total;
     return DG_OK;
 }
 
@@ -1793,10 +1815,8 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     if (!(opts->cfl > 0.0) || !(opts->gamma > 1.0) || !opts->stream || !opts->prim || !opts->scratch) return DG_EINVAL;
     for (int i = 0; i < 3; ++i)
         if (!opts->u[i]) return DG_EINVAL;
-    const size_t nc = (size_t)mesh->n[0] * mesh->n[1] * mesh->n[2];
-    const size_t bb = (size_t)(order + 1) * (order + 2) * (order + 3) / 6;
     const AdiScratch sl =
-        adi_scratch(order, nc * 4 * bb * (opts->precision == DG_PREC_F64 ? sizeof(double) : sizeof(float)));
+        adi_scratch(order, mesh->n[0], opts->precision == DG_PREC_F64 ? sizeof(double) : sizeof(float));
     if (opts->scratch_bytes < sl.total) return DG_ENOMEM;
     if (((uintptr_t)opts->scratch & 255u) != 0) return DG_EINVAL;
     dg_adi_ctx* ctx = new (std::nothrow) dg_adi_ctx();
@@ -1819,6 +1839,18 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     ctx->ttab = ctx->scratch + sl.ttab;
     ctx->partials = reinterpret_cast<double*>(ctx->scratch + sl.partials);
     ctx->prim2 = ctx->scratch + sl.prim2;
+    ctx->ahat = ctx->scratch + sl.ahat;
+    ctx->d_kvec = reinterpret_cast<int*>(ctx->scratch + sl.kvec);
+    ctx->d_amp = reinterpret_cast<double*>(ctx->scratch + sl.amp);
+    ctx->gtab = ctx->scratch + sl.gtab;
+    {
+        long double xg[4], wg[4];
+        gauss_rule(order + 1, xg, wg);
+        for (int q = 0; q <= order; ++q) {
+            ctx->r1.x[q] = (double)xg[q];
+            ctx->r1.w[q] = (double)wg[q];
+        }
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1828,6 +1860,9 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     c0.dt_num = ctx->cfl * ctx->h / (ctx->K + 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ttab, tt.data(), tt.size(), cudaMemcpyHostToDevice, ctx->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ctx->ahat, 0, (size_t)ctx->ncell * 3 * ctx->b * adi_elem(ctx), ctx->st);
+    if (e == cudaSuccess) e = (ctx->prec == DG_PREC_F64) ? setup_kernels<double>(order) : setup_kernels<float>(order);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
     if (e != cudaSuccess) {
         delete ctx;
@@ -1853,6 +1888,8 @@ int dg_adi_set_state(dg_adi_ctx* ctx, const void* src, int src_on_host)
     ctx->t = 0.0;
     ctx->steps = 0;
     ctx->status = 0u;
+    ctx->injected = 0.0;
+    ctx->dissipated = 0.0;
     return DG_OK;
 }
 
@@ -1910,7 +1947,40 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
     static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
     const double* RA = ctx->rk == 2 ? A2 : A3;
     const double* RB = ctx->rk == 2 ? B2 : B3;
+    static const double W2[2] = {0.5, 0.5}, W3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+    const double* RW = ctx->rk == 2 ? W2 : W3;
+    const size_t ahat_bytes = (size_t)ctx->ncell * 3 * ctx->b * adi_elem(ctx);
     for (int n = 0; n < nsteps; ++n) {
+        // driving schedule (Sec. 4.2): OU updates every dt_drive, switched off after t_off
+        if (ctx->drv.on && ctx->drv.t_off > 0.0 && ctx->t > ctx->drv.t_off) {
+            ctx->drv.on = false;
+            ctx->forcing_active = false;
+            ACK(cudaMemsetAsync(ctx->ahat, 0, ahat_bytes, ctx->st));
+        }
+        if (ctx->drv.on) {
+            while (ctx->t >= ctx->drv.t_next) {
+                ctx->drv.advance();
+                ctx->drv.t_next += ctx->drv.dtd;
+                ctx->drv.dirty = true;
+            }
+            if (ctx->drv.dirty) {
+                std::vector<double> amp;
+                std::vector<int> kv;
+                ctx->drv.amplitudes(amp, kv);
+                ACK(cudaMemcpyAsync(ctx->d_kvec, kv.data(), sizeof(int) * kv.size(), cudaMemcpyHostToDevice, ctx->st));
+                ACK(cudaMemcpyAsync(ctx->d_amp, amp.data(), sizeof(double) * amp.size(), cudaMemcpyHostToDevice,
+                                    ctx->st));
+                const Launch L = adi_make_launch(ctx);
+                ACK(ctx->prec == DG_PREC_F64 ? launch_force<double>(L, ctx->drv.nm, ctx->d_kvec, ctx->d_amp,
+                                                                    ctx->drv.kmaxc, (double*)ctx->ahat)
+                                             : launch_force<float>(L, ctx->drv.nm, ctx->d_kvec, ctx->d_amp,
+                                                                   ctx->drv.kmaxc, (float*)ctx->ahat));
+                ACK(cudaStreamSynchronize(ctx->st));  // the host amplitude buffers are reused
+                ctx->drv.dirty = false;
+                ctx->forcing_active = true;
+            }
+        }
+        const bool force = ctx->forcing_active;
         const int A = ctx->cur, B = (ctx->cur + 1) % 3, C = (ctx->cur + 2) % 3;
         const int in3[3] = {A, B, C}, out3[3] = {B, C, B};
         const int in2[2] = {A, B}, out2[2] = {B, C};
@@ -1918,7 +1988,7 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
         const int* out = ctx->rk == 2 ? out2 : out3;
         bool ok = false;
         unsigned int status = 0u;
-        double dt = 0.0;
+        double dt = 0.0, inj = 0.0;
         for (int retry = 0; retry <= 3 && !ok; ++retry) {
             struct {
                 double dt_scale, fixed_dt;
@@ -1926,6 +1996,7 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
             ACK(cudaMemcpyAsync(&ctx->ctl->dt_scale, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->st));
             ACK(cudaMemsetAsync(&ctx->ctl->status, 0, sizeof(unsigned int), ctx->st));
             ACK(cudaMemsetAsync(&ctx->ctl->smax, 0, sizeof(unsigned long long), ctx->st));
+            ACK(cudaMemsetAsync(&ctx->ctl->diag[1], 0, sizeof(double), ctx->st));
             // projections of v and p of u^n (with its CFL bound); every stage but the
             // last projects its output for the next one (alternating buffers)
             void* pr[2] = {ctx->prim, ctx->prim2};
@@ -1933,7 +2004,9 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
             p.mode = ADI_PROJECT;
             p.u_in = ctx->reg[A];
             p.pr_out = pr[0];
-            p.flags = F_DT;
+            p.flags = F_DT | (force ? F_FORCE : 0);
+            p.ahat = ctx->ahat;
+            p.abar_out = 0;
             ACK(adi_go(ctx, p));
             for (int s = 0; s < ctx->rk; ++s) {
                 AdiLaunch t{};
@@ -1943,25 +2016,46 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
                 t.out = ctx->reg[out[s]];
                 t.pr_in = pr[s & 1];
                 t.pr_out = pr[(s + 1) & 1];
-                t.flags = s + 1 < ctx->rk ? F_NEXTPROJ : 0;
+                t.flags = (s + 1 < ctx->rk ? F_NEXTPROJ : 0) | (force ? F_FORCE : 0);
+                t.ahat = ctx->ahat;
+                t.abar_in = s & 1;
+                t.abar_out = (s + 1) & 1;
+                t.beta = RW[s];
                 t.rk_a = RA[s];
                 t.rk_b = RB[s];
                 ACK(adi_go(ctx, t));
             }
             struct {
                 unsigned int status;
-                double dt;
+                double dt, inj;
             } back{};
             ACK(cudaMemcpyAsync(&back.status, &ctx->ctl->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
             ACK(cudaMemcpyAsync(&back.dt, &ctx->ctl->dt, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            ACK(cudaMemcpyAsync(&back.inj, &ctx->ctl->diag[1], sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
             ACK(cudaStreamSynchronize(ctx->st));
             status = back.status;
             dt = back.dt;
+            inj = back.inj;
             ok = !(status & DG_ST_FAIL);
         }
         ctx->status |= status;
         if (!ok) return afail(ctx, DG_EPOSITIVITY, "dg_adi_step: positivity retries exhausted");
         ctx->cur = out[ctx->rk - 1];
+        if (force) ctx->injected += inj;
+        if (ctx->cs_reset > 0.0) {
+            // uniform temperature restored; the thermal energy taken out is the dissipation
+            ACK(cudaMemsetAsync(&ctx->ctl->diag[2], 0, sizeof(double), ctx->st));
+            AdiLaunch r{};
+            r.mode = ADI_RESET;
+            r.u_in = ctx->reg[ctx->cur];
+            r.out = ctx->reg[ctx->cur];
+            r.cs_reset = ctx->cs_reset;
+            ACK(adi_go(ctx, r));
+            double d = 0.0;
+            ACK(cudaMemcpyAsync(&d, &ctx->ctl->diag[2], sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            ACK(cudaStreamSynchronize(ctx->st));
+            ctx->dissipated += d;
+        }
         ctx->t += dt;
         ctx->dt_last = dt;
         ctx->steps += 1;
@@ -1969,6 +2063,45 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
     }
     if (t_out) *t_out = ctx->t;
     if (dt_last) *dt_last = ctx->dt_last;
+    return DG_OK;
+}
+
+int dg_adi_set_forcing(dg_adi_ctx* ctx, const dg_forcing* f, double cs_ref)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!f) return afail(ctx, DG_EINVAL, "dg_adi_set_forcing: null");
+    const size_t ahat_bytes = (size_t)ctx->ncell * 3 * ctx->b * adi_elem(ctx);
+    if (!f->on) {
+        ctx->drv.on = false;
+        ctx->forcing_active = false;
+        ACK(cudaMemsetAsync(ctx->ahat, 0, ahat_bytes, ctx->st));
+        ACK(cudaStreamSynchronize(ctx->st));
+        return DG_OK;
+    }
+    if (!(cs_ref > 0.0) || !(f->mach > 0.0) || f->kmin2 < 1 || f->kmax2 < f->kmin2 || f->kmax2 > 64 ||
+        f->zeta < 0.0 || f->zeta > 1.0)
+        return afail(ctx, DG_EINVAL, "dg_adi_set_forcing: bad parameters");
+    ctx->drv.init(*f, cs_ref);
+    if (ctx->drv.nm > kMaxModes) return afail(ctx, DG_EINVAL, "dg_adi_set_forcing: too many modes");
+    ctx->cs_ref = cs_ref;
+    ctx->forcing_active = false;
+    return DG_OK;
+}
+
+int dg_adi_set_reset(dg_adi_ctx* ctx, double cs)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!(cs >= 0.0)) return afail(ctx, DG_EINVAL, "dg_adi_set_reset: negative sound speed");
+    ctx->cs_reset = cs;
+    return DG_OK;
+}
+
+int dg_adi_energy_budget(dg_adi_ctx* ctx, double* out)
+{
+    if (!ctx) return DG_EINVAL;
+    if (!out) return afail(ctx, DG_EINVAL, "dg_adi_energy_budget: null output");
+    out[0] = ctx->injected;
+    out[1] = ctx->dissipated;
     return DG_OK;
 }
 

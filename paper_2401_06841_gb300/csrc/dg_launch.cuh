@@ -59,9 +59,10 @@ template <typename T>
 cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB);
 
 // adiabatic system (dg_adi.cu): mode 0 projection of v and p (+ CFL bound
-// with F_DT), 1 right-hand side, 2 stage (right-hand side, SSP-RK combine,
-// positivity of density and pressure)
-enum { ADI_PROJECT = 0, ADI_RHS = 1, ADI_STAGE = 2 };
+// with F_DT, forcing sums with F_FORCE), 1 right-hand side, 2 stage
+// (right-hand side, SSP-RK combine, positivity of density and pressure),
+// 3 isothermal reset of the thermal energy (in place)
+enum { ADI_PROJECT = 0, ADI_RHS = 1, ADI_STAGE = 2, ADI_RESET = 3 };
 struct AdiLaunch {
     int mode;
     const void* u_in;
@@ -72,6 +73,10 @@ struct AdiLaunch {
     double rk_a, rk_b;
     double dt_pimax;
     int flags;
+    const void* ahat;       // driving (F_FORCE)
+    int abar_in, abar_out;  // ctl->abar2 slots
+    double beta;            // stage weight of the injected energy
+    double cs_reset;        // reset mode
 };
 template <typename T>
 cudaError_t launch_adi(const Launch& L, double gamma, const AdiLaunch& t);

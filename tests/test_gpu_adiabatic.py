@@ -213,3 +213,42 @@ def test_invalid_arguments_are_rejected():
         AdiabaticSolver(4, 2, gamma=1.0)
     with pytest.raises(KeyError):
         AdiabaticSolver(4, 2, precision="x3")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,g,cs,v_rms,tol", [("f64", 1.0001, 1.0, 0.5, 1e-12), ("f64", 1.4, 2.0, 0.3, 1e-12),
+                                                ("f32", 1.4, 2.0, 0.3, 3e-5)])
+def test_driven_steps_with_reset_parity(prec, g, cs, v_rms, tol):
+    # OU driving (momentum source and its work), the uniform-temperature reset
+    # after every step, and the energy budget, against the oracle's driven run.
+    # (At gamma = 1.0001 the thermal energy is ~1e4 times the kinetic one:
+    # compared in FP64 only.)
+    N, k = 5, 2
+    fo = dict(mach=2.0, zeta=0.5, seed=5)
+    u4 = I.random_state(N, k, seed=17, v_rms=v_rms)
+    u = np.zeros((N ** 3, 5, u4.shape[2]))
+    u[:, :4] = u4
+    cfg = O.make_cfg(N, k)
+    O.adi_reset(cfg, g, cs, u)  # start at the uniform temperature
+    if prec == "f32":
+        u = u.astype(np.float32).astype(np.float64)
+    s = AdiabaticSolver(N, k, gamma=g, precision=prec)
+    s.set_state(u)
+    s.set_forcing(cs_ref=cs, **fo)
+    s.set_reset(cs)
+    t, _ = s.step(6)
+    got = s.get_state().cpu().numpy()
+    inj, dis = s.energy_budget()
+    ref = u.copy()
+    rc, tr, _, _, (ri, rd) = O.adi_run_driven(cfg, g, cs, ref, 6, forcing=O.Forcing(cs=cs, **fo))
+    assert rc == 0
+    assert t == pytest.approx(tr, rel=1e-12 if prec == "f64" else 1e-6)
+    err = rel_fields(got, ref)
+    assert err.max() < tol, err
+    assert ri > 0 and inj == pytest.approx(ri, rel=1e-10 if prec == "f64" else 1e-4)
+    assert dis == pytest.approx(rd, rel=1e-9 if prec == "f64" else 1e-3)
+    if prec == "f64":
+        # the budget closes on the GPU as well: E(t) = E(0) + injected - dissipated
+        h3 = (1.0 / N) ** 3
+        E0 = u[:, 4, 0].sum() * h3
+        assert abs(s.totals()["energy"] - (E0 + inj - dis)) < 1e-12 * E0
