@@ -6,30 +6,31 @@ namespace dg {
 
 namespace {
 
-template <typename T, int K, int MODE>
+template <typename T, int K, int MODE, bool DRIVEN>
 int adi_blocks_per_sm()
 {
     static int occ = -1;
     if (occ < 0) {
-        const int sm = (int)(sizeof(T) * AdiCfg<K>::total);
-        cudaFuncSetAttribute(k_adi<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        const int sm = (int)(sizeof(T) * AdiCfg<K, DRIVEN>::total);
+        cudaFuncSetAttribute(k_adi<T, K, MODE, DRIVEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_adi<T, K, MODE>, AdiCfg<K>::NT, sm) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_adi<T, K, MODE, DRIVEN>, AdiCfg<K, DRIVEN>::NT, sm) !=
+            cudaSuccess)
             o = 1;
         occ = o < 1 ? 1 : o;
     }
     return occ;
 }
 
-template <typename T, int K, int MODE>
+template <typename T, int K, int MODE, bool DRIVEN = false>
 cudaError_t adi_launch(const Launch& L, const AdiArgs<T>& a)
 {
-    using A = AdiCfg<K>;
+    using A = AdiCfg<K, DRIVEN>;
     const long ntile = (L.ncell + A::TC - 1) / A::TC;
-    long g = (long)adi_blocks_per_sm<T, K, MODE>() * L.nsm;
+    long g = (long)adi_blocks_per_sm<T, K, MODE, DRIVEN>() * L.nsm;
     if (g > ntile) g = ntile;
     if (g < 1) g = 1;
-    k_adi<T, K, MODE><<<(int)g, A::NT, sizeof(T) * A::total, L.st>>>(a);
+    k_adi<T, K, MODE, DRIVEN><<<(int)g, A::NT, sizeof(T) * A::total, L.st>>>(a);
     return cudaGetLastError();
 }
 
@@ -59,10 +60,11 @@ cudaError_t adi_k(const Launch& L, double gamma, const AdiLaunch& t)
     a.beta = t.beta;
     a.cs_reset = t.cs_reset;
     if ((t.flags & F_FORCE) && !t.ahat) return cudaErrorInvalidValue;
+    const bool driven = (t.flags & F_FORCE) != 0;
     if (t.mode == ADI_PROJECT) return adi_launch<T, K, ADI_PROJECT>(L, a);
-    if (t.mode == ADI_RHS) return adi_launch<T, K, ADI_RHS>(L, a);
     if (t.mode == ADI_RESET) return adi_launch<T, K, ADI_RESET>(L, a);
-    return adi_launch<T, K, ADI_STAGE>(L, a);
+    if (t.mode == ADI_RHS) return driven ? adi_launch<T, K, ADI_RHS, true>(L, a) : adi_launch<T, K, ADI_RHS>(L, a);
+    return driven ? adi_launch<T, K, ADI_STAGE, true>(L, a) : adi_launch<T, K, ADI_STAGE>(L, a);
 }
 
 template <typename T, int K>

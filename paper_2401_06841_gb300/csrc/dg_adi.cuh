@@ -53,13 +53,16 @@ struct AdiArgs {
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-template <int K>
+// DRIVEN: the right-hand side carries the driving's source rows (4 more
+// projected rows per cell); the undriven kernels are compiled without them
+template <int K, bool DRIVEN = false>
 struct AdiCfg {
     using C = TileCfg<K, BK_FMA>;
     static constexpr int b = C::b, nq = C::nq, ns = C::ns, nf = C::nf, TC = C::TC, NT = C::NT;
     static constexpr int KP = C::KP, NQP = C::NQP, NP = C::NP, B2K = C::B2K, NSP = C::NSP, B2N = C::B2N;
     static constexpr int FE = 12;  // rho, m_x, m_y, m_z, e, grad rho (3), div m, 3 zero rows
-    static constexpr int FP = 13;  // m v + P (6), (e + P) v (3), rho (a - abar) (3), m.(a - abar)
+    // m v + P (6), (e + P) v (3); driven: rho (a - abar) (3), m.(a - abar)
+    static constexpr int FP = DRIVEN ? 13 : 9;
     static constexpr int LDA = KP, LDV = NQP + 4, LDP = NP, LDC2 = B2K, LDT = NSP + 4, LDL = B2N;
     static constexpr int RE = TC * FE, RP = TC * FP;
     static constexpr int RC = TC * 20;  // face rows ((cell, side, self/neighbour), (rho, v_x, v_y, v_z, p))
@@ -176,11 +179,11 @@ __device__ __forceinline__ void adi_load(T* dst, const T* src, int n, int valid,
 // projections of v and p of the TC states in sU (Sec. 3.2) -> a.pr_out, and
 // with F_DT the CFL bound max sum_d(|v_d| + c) over the volume points of the
 // valid cells into smax.  Starts and ends with the block in step.
-template <typename T, int K>
+template <typename T, int K, bool DRIVEN>
 __device__ __forceinline__ void adi_project_tile(T* sm, const T* sU, const T* tabs, const AdiArgs<T>& a, long c0,
                                                  int nvalid, T gamma, T& smax, double* sums)
 {
-    using A = AdiCfg<K>;
+    using A = AdiCfg<K, DRIVEN>;
     using C = TileCfg<K, BK_FMA>;
     constexpr int b = A::b, nq = A::nq, TC = A::TC, NT = A::NT, KP = A::KP, NQP = A::NQP, NP = A::NP;
     constexpr int LDA = A::LDA, LDV = A::LDV, LDP = A::LDP;
@@ -274,11 +277,13 @@ __device__ __forceinline__ bool adi_reduce(double* partials, double* s_buf, doub
     return last_block_reduce<NT>(partials, mine, nv, counter, s_tot, s_buf);
 }
 
-// FP32: two blocks per SM (128 registers); FP64 fits one block in shared memory
-template <typename T, int K, int MODE>
+// FP32: two blocks per SM (128 registers); FP64 fits one block in shared memory.
+// DRIVEN (right-hand-side modes): the driving's source rows are compiled in
+template <typename T, int K, int MODE, bool DRIVEN = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> a)
 {
-    using A = AdiCfg<K>;
+    using A = AdiCfg<K, DRIVEN>;
+    static_assert(AdiCfg<K, false>::oAh == A::oAh && AdiCfg<K, false>::oA == A::oA, "same leading layout");
     using C = TileCfg<K, BK_FMA>;
     using TT = TileTab<K, BK_FMA>;
     constexpr int b = A::b, nq = A::nq, ns = A::ns, nf = A::nf, TC = A::TC, NT = A::NT;
@@ -297,7 +302,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
     __shared__ unsigned long long s_smax;
     __shared__ double s_tot[8];
     T* sAh = sm + A::oAh;
+    // force: a_h staged and the projections' forcing sums (any mode); the
+    // right-hand side's source rows exist only in the DRIVEN kernels
     const bool force = (a.flags & F_FORCE) != 0;
+    constexpr bool SRC = DRIVEN && (MODE == ADI_RHS || MODE == ADI_STAGE);
     double sums[4] = {0.0, 0.0, 0.0, 0.0};  // <rho a_h> (3), <rho> of the projected tiles
     double work = 0.0;                      // stage: volume integral of the energy source / h^3
     double diss = 0.0;                      // reset: thermal energy taken out / h^3
@@ -321,7 +329,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
     }
     const T dt = T(dtd);
     T ab0 = T(0), ab1 = T(0), ab2 = T(0);
-    if (force && (MODE == ADI_RHS || MODE == ADI_STAGE)) {
+    if (SRC) {
         ab0 = T(a.ctl->abar2[a.abar_in][0]);
         ab1 = T(a.ctl->abar2[a.abar_in][1]);
         ab2 = T(a.ctl->abar2[a.abar_in][2]);
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
         }
         if constexpr (MODE == ADI_PROJECT) {
             __syncthreads();
-            adi_project_tile<T, K>(sm, sU, tabs, a, c0, nvalid, gamma, smax, sums);
+            adi_project_tile<T, K, DRIVEN>(sm, sU, tabs, a, c0, nvalid, gamma, smax, sums);
         } else if constexpr (MODE == ADI_RESET) {
             __syncthreads();
             // rho, m at the volume points; e = rho cs^2/(gamma-1) + |m|^2/(2 rho) there; projected
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 modal_grad<T, K, 2>(u + 3 * b, t2, two_h);
 #pragma unroll
                 for (int l = 0; l < b; ++l) out[l] += t2[l];
-            } else if (f < 12 && force) {
+            } else if (f < 12 && SRC) {
 #pragma unroll
                 for (int l = 0; l < b; ++l) out[l] = sAh[(c * 3 + f - 9) * b + l];
             }
@@ -437,12 +445,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
         // ---- pointwise volume physics (Sec. 3.1: Pi at the internal points) ----
         {
             constexpr int PER = (TC * NQP + NT - 1) / NT;
-            T fl[PER][13];
+            constexpr int FP = A::FP;
+            T fl[PER][FP];
 #pragma unroll
             for (int it = 0; it < PER; ++it) {
                 const int e = tid + it * NT;
 #pragma unroll
-                for (int g = 0; g < 13; ++g) fl[it][g] = T(0);
+                for (int g = 0; g < FP; ++g) fl[it][g] = T(0);
                 if (e < TC * NQP) {
                     const int c = e / NQP, q = e % NQP;
                     if (q < nq) {
@@ -463,7 +472,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                         fl[it][6] = (en + P) * vx;
                         fl[it][7] = (en + P) * vy;
                         fl[it][8] = (en + P) * vz;
-                        if (force) {
+                        if constexpr (SRC) {
                             const T dx = v[9 * LDV] - ab0, dy = v[10 * LDV] - ab1, dz = v[11 * LDV] - ab2;
                             fl[it][9] = rho * dx;
                             fl[it][10] = rho * dy;
@@ -480,7 +489,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 if (e < TC * NQP) {
                     const int c = e / NQP, q = e % NQP;
 #pragma unroll
-                    for (int g = 0; g < 13; ++g) sBig[(c * 13 + g) * LDV + q] = fl[it][g];
+                    for (int g = 0; g < FP; ++g) sBig[(c * FP + g) * LDV + q] = fl[it][g];
                 }
             }
         }
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
             T r[b];
 #pragma unroll
             for (int l = 0; l < b; ++l) r[l] = T(0);
-            const T* P = sP + c * 13 * LDP;
+            const T* P = sP + c * A::FP * LDP;
             if (v == 0) {
                 const T* u = sU + c * 5 * b;
                 modal_grad_T_acc<T, K, 0>(u + b, r, two_h);
@@ -507,7 +516,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 modal_grad_T_acc<T, K, 0>(P + cx * LDP, r, two_h);
                 modal_grad_T_acc<T, K, 1>(P + cy * LDP, r, two_h);
                 modal_grad_T_acc<T, K, 2>(P + cz * LDP, r, two_h);
-                if (force) {
+                if constexpr (SRC) {
 #pragma unroll
                     for (int l = 0; l < b; ++l) r[l] += P[(9 + i) * LDP + l];
                 }
@@ -515,7 +524,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 modal_grad_T_acc<T, K, 0>(P + 6 * LDP, r, two_h);
                 modal_grad_T_acc<T, K, 1>(P + 7 * LDP, r, two_h);
                 modal_grad_T_acc<T, K, 2>(P + 8 * LDP, r, two_h);
-                if (force) {
+                if constexpr (SRC) {
 #pragma unroll
                     for (int l = 0; l < b; ++l) r[l] += P[12 * LDP + l];
                     if (MODE == ADI_STAGE && c < nvalid) work += (double)P[12 * LDP];  // cell mean of the work
@@ -727,7 +736,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
             }
             __syncthreads();
             // the next stage's projections of v and p, from the new state in shared memory
-            if (a.flags & F_NEXTPROJ) adi_project_tile<T, K>(sm, sU, tabs, a, c0, nvalid, gamma, smax, sums);
+            if (a.flags & F_NEXTPROJ) adi_project_tile<T, K, DRIVEN>(sm, sU, tabs, a, c0, nvalid, gamma, smax, sums);
         }
         }  // right-hand-side modes
     }
@@ -754,7 +763,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
     }
     // injected energy of the stage, dissipated energy of the reset (FP64 accumulators)
     if constexpr (MODE == ADI_STAGE) {
-        if (force && adi_reduce<NT>(a.partials + 8, s_buf, s_tot, &a.ctl->cnt_diag, &work, 1) && tid == 0)
+        if (SRC && adi_reduce<NT>(a.partials + 8, s_buf, s_tot, &a.ctl->cnt_diag, &work, 1) && tid == 0)
             a.ctl->diag[1] += a.beta * dtd * s_tot[0] * h3;
     }
     if constexpr (MODE == ADI_RESET) {
