@@ -230,7 +230,7 @@ int dg_diagnostics(dg_ctx* ctx, double dt_for_pimax, dg_diag* out);
 int dg_l1_density(dg_ctx* ctx, const void* uA, const void* uB, double* out);
 
 /* ---- learned viscosity sensor (not in the paper: a small network stands in
- * for the shock sensor and is judged against it) ------------------------------
+ * for the shock sensor and is checked against it) -----------------------------
  * Network y = W3 . gelu(W2 gelu(W1 x + b1) + b2) + b3, gelu(z) = z/2 (1 +
  * erf(z/sqrt 2)), 64 hidden units, D = 2b inputs per cell
  *   x = (rho_l / rho_0, |v|hat_l / cs),  |v|hat the Gauss projection of |v|,
