@@ -224,6 +224,30 @@ def oracle_arm(args, steps, warmup):
                                    % (n, args.k, steps)}
 
 
+def adiabatic_oracle_arm(args, near_isothermal, steps=2):
+    """The adiabatic oracle on a bounded sample: 16^3 cells at the workload's
+    degree, the same kind of state (and driving with the reset), FP64 C."""
+    from oracle import oracle as O
+    from paper_2401_06841_gb300 import inputs as I
+    n = args.sample_N
+    cfg = O.make_cfg(n, args.k, rk_stages=3)
+    if near_isothermal:
+        g, cs = 1.0001, 1.0
+        u = I.adiabatic_turbulent_state(n, args.k, seed=103, mach=1.0, gamma=g)
+        fo = O.Forcing(mach=args.mach, zeta=0.5, seed=0, cs=cs)
+    else:
+        g, cs, fo = 1.4, 0.0, None
+        u = I.adiabatic_turbulent_state(n, args.k, seed=102, mach=0.5)
+    t0 = time.perf_counter()
+    rc, _, _, _, _ = O.adi_run_driven(cfg, g, cs, u, steps, forcing=fo)
+    wall = time.perf_counter() - t0
+    assert rc == 0
+    dofs = 5 * O.nmodes(args.k) * n ** 3
+    return {"kind": "oracle", "cores": 1, "unit": UNIT, "value": dofs * 3 * steps / wall,
+            "sample": "%d^3 cells at k=%d, SSP-RK3, %d steps of the same workload (single-threaded FP64 C)"
+                      % (n, args.k, steps)}
+
+
 # ---- one process per GPU (torchrun): independent replicas, no data-path collective ----
 def rank_info():
     """(world size, rank, local rank) from the launcher's environment."""
@@ -495,6 +519,9 @@ def main():
     if not args.no_adiabatic:
         line["adiabatic"] = adiabatic_arm(args, dev, state_seed, flush, world)
         line["adiabatic_near_isothermal"] = adiabatic_arm(args, dev, state_seed, flush, world, near_isothermal=True)
+        if rank == 0 and not args.no_cpu:
+            line["adiabatic"]["cpu_baseline"] = adiabatic_oracle_arm(args, False)
+            line["adiabatic_near_isothermal"]["cpu_baseline"] = adiabatic_oracle_arm(args, True)
     if rank == 0 and not args.no_cpu:
         v, wall, cb = oracle_arm(args, args.cpu_steps, 1)
         cb["value"] = v

@@ -774,7 +774,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
 
 // FP64 totals for the diagnostics: per block [mass, m_x, m_y, m_z, energy,
 // kinetic energy (volume quadrature of |m|^2/(2 rho)), min rho, min p at the
-// volume points], summed over blocks on the host in block order
+// volume points], summed over blocks on the host in block order.  Point values
+// in the state's precision, sums in FP64.
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_adi_totals(const T* __restrict__ u, const T* __restrict__ tab, long ncell,
                                                    double gamma, double* __restrict__ partials)
@@ -793,16 +794,16 @@ __global__ void __launch_bounds__(256) k_adi_totals(const T* __restrict__ u, con
         const T* uc = u + c * 5 * b;
         for (int v = 0; v < 5; ++v) acc[v] += (double)uc[v * b];
         for (int q = 0; q < nq; ++q) {
-            double w[5];
+            T w[5];
             for (int v = 0; v < 5; ++v) {
-                double s = 0.0;
-                for (int l = 0; l < b; ++l) s += (double)uc[v * b + l] * (double)tab[TT::phiv + l * nq + q];
+                T s = T(0);
+                for (int l = 0; l < b; ++l) s += uc[v * b + l] * tab[TT::phiv + l * nq + q];
                 w[v] = s;
             }
-            const double ke = 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0];
+            const double ke = 0.5 * ((double)w[1] * w[1] + (double)w[2] * w[2] + (double)w[3] * w[3]) / (double)w[0];
             acc[5] += s_w[q] * ke;
-            const double p = (gamma - 1.0) * (w[4] - ke);
-            rmin = w[0] < rmin ? w[0] : rmin;
+            const double p = (gamma - 1.0) * ((double)w[4] - ke);
+            rmin = (double)w[0] < rmin ? (double)w[0] : rmin;
             pmin = p < pmin ? p : pmin;
         }
     }
