@@ -1325,6 +1325,58 @@ void orc_adi_rusanov(double gamma, int d, const double WL[5], const double WR[5]
     for (int v = 0; v < 5; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
 }
 
+/* HLLC flux of the Euler equations (the contact wave restored in the HLL
+ * two-wave model) from primitive face states W = (rho, v_x, v_y, v_z, p):
+ * Davis bounds S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R),
+ * contact speed S* = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R))
+ *                    / (rho_L (S_L - u_L) - rho_R (S_R - u_R)),
+ * star states U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S* along d, the tangential
+ * velocities, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))),
+ * F = F_L, F_L + S_L (U*_L - U_L), F_R + S_R (U*_R - U_R) or F_R by the sign of
+ * S_L, S*, S_R (u the normal velocity) */
+void orc_adi_hllc(double gamma, int d, const double WL[5], const double WR[5], double F[5])
+{
+    double U[2][5], Fx[2][5], c[2], un[2];
+    const double* W[2] = {WL, WR};
+    for (int s = 0; s < 2; ++s) {
+        const double* w = W[s];
+        U[s][0] = w[0];
+        for (int i = 0; i < 3; ++i) U[s][1 + i] = w[0] * w[1 + i];
+        U[s][4] = w[4] / (gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        orc_adi_flux(gamma, d, U[s], Fx[s]);
+        c[s] = sqrt(gamma * w[4] / w[0]);
+        un[s] = w[1 + d];
+    }
+    double SL = fmin(un[0] - c[0], un[1] - c[1]), SR = fmax(un[0] + c[0], un[1] + c[1]);
+    if (SL >= 0.0) {
+        for (int v = 0; v < 5; ++v) F[v] = Fx[0][v];
+        return;
+    }
+    if (SR <= 0.0) {
+        for (int v = 0; v < 5; ++v) F[v] = Fx[1][v];
+        return;
+    }
+    double qL = WL[0] * (SL - un[0]), qR = WR[0] * (SR - un[1]);
+    double Ss = (WR[4] - WL[4] + un[0] * qL - un[1] * qR) / (qL - qR);
+    int s = Ss >= 0.0 ? 0 : 1;
+    double SK = s == 0 ? SL : SR, qK = s == 0 ? qL : qR;
+    const double* w = W[s];
+    double f = qK / (SK - Ss), Us[5];
+    Us[0] = f;
+    for (int i = 0; i < 3; ++i) Us[1 + i] = f * (i == d ? Ss : w[1 + i]);
+    Us[4] = f * (U[s][4] / w[0] + (Ss - un[s]) * (Ss + w[4] / qK));
+    for (int v = 0; v < 5; ++v) F[v] = Fx[s][v] + SK * (Us[v] - U[s][v]);
+}
+
+/* face flux of the adiabatic system by cfg->riemann: HLLC, else Rusanov */
+static void adi_face_flux(int solver, double gamma, int d, const double WL[5], const double WR[5], double F[5])
+{
+    if (solver == ORC_HLLC)
+        orc_adi_hllc(gamma, d, WL, WR, F);
+    else
+        orc_adi_rusanov(gamma, d, WL, WR, F);
+}
+
 /* vNR viscous pressure with the local sound speed in the bulk term */
 double orc_adi_vnr(const orc_cfg* cfg, double rho, double c, double divv, double dt)
 {
@@ -1472,7 +1524,7 @@ static int adi_rhs_impl(const orc_cfg* cfg, double gamma, const double* u, const
                             WL[1 + i] = eval(&T, prim + ((size_t)cL * 4 + i) * b, phL + s * b);
                             WR[1 + i] = eval(&T, prim + ((size_t)cR * 4 + i) * b, phR + s * b);
                         }
-                        orc_adi_rusanov(gamma, d, WL, WR, Fs);
+                        adi_face_flux(cfg->riemann, gamma, d, WL, WR, Fs);
                         for (int var = 0; var < 5; ++var)
                             for (int l = 0; l < b; ++l) {
                                 dudt[((size_t)cL * 5 + var) * b + l] -= T.ws[s] * phL[s * b + l] * Fs[var] / (4.0 * h);

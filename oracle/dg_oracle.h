@@ -88,6 +88,7 @@ int orc_rhs_nu(const orc_cfg* cfg, const double* u, const double* ahat, double d
 /* adiabatic system: state [c][5][b] (rho, m, e), primitives [c][4][b] (v, p) */
 void orc_adi_flux(double gamma, int d, const double U[5], double F[5]);
 void orc_adi_rusanov(double gamma, int d, const double WL[5], const double WR[5], double F[5]);
+void orc_adi_hllc(double gamma, int d, const double WL[5], const double WR[5], double F[5]);
 double orc_adi_vnr(const orc_cfg* cfg, double rho, double c, double divv, double dt);
 void orc_adi_project(const orc_cfg* cfg, double gamma, const double* u, double* prim);
 int orc_adi_rhs(const orc_cfg* cfg, double gamma, const double* u, double dt_pimax, double* dudt);

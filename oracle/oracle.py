@@ -94,6 +94,7 @@ def lib():
         _lib.orc_rhs_local.argtypes = [C.POINTER(Cfg), d, d, d, C.c_double, d, C.c_int64, d]
         _lib.orc_adi_flux.argtypes = [C.c_double, C.c_int, d, d]
         _lib.orc_adi_rusanov.argtypes = [C.c_double, C.c_int, d, d, d]
+        _lib.orc_adi_hllc.argtypes = [C.c_double, C.c_int, d, d, d]
         _lib.orc_adi_vnr.restype = C.c_double
         _lib.orc_adi_vnr.argtypes = [C.POINTER(Cfg), C.c_double, C.c_double, C.c_double, C.c_double]
         _lib.orc_adi_project.argtypes = [C.POINTER(Cfg), C.c_double, d, d]
@@ -410,6 +411,15 @@ def adi_rusanov(gamma: float, d: int, WL, WR) -> np.ndarray:
     WR = np.ascontiguousarray(WR, dtype=np.float64)
     F = np.zeros(5)
     lib().orc_adi_rusanov(gamma, d, _p(WL), _p(WR), _p(F))
+    return F
+
+
+def adi_hllc(gamma: float, d: int, WL, WR) -> np.ndarray:
+    """HLLC flux of the Euler equations from primitive face states (rho, v_x, v_y, v_z, p)."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.zeros(5)
+    lib().orc_adi_hllc(gamma, d, _p(WL), _p(WR), _p(F))
     return F
 
 

@@ -362,3 +362,64 @@ def test_near_isothermal_gas_with_reset_follows_the_isothermal_system():
         dev[g] = max(np.linalg.norm(u5[:, v] - ref[:, v]) / np.linalg.norm(ref[:, v]) for v in range(4))
     assert dev[1.0001] < 1e-4, dev
     assert 30 < dev[1.01] / dev[1.0001] < 300, dev
+
+
+# ---- HLLC for the Euler equations (the contact wave restored) ----
+def test_hllc_consistency_and_upwinding():
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        W = np.array([rng.uniform(0.2, 3), *rng.normal(size=3), rng.uniform(0.1, 5)])
+        U = prim_to_cons(W)
+        for d in range(3):
+            assert np.allclose(O.adi_hllc(G, d, W, W), flux_exact(U, d), rtol=1e-13, atol=1e-13)
+    # supersonic to the right: the left state's flux alone
+    WL = np.array([1.0, 3.0, 0.2, -0.1, 1.0])
+    WR = np.array([0.5, 2.8, 0.0, 0.3, 0.7])
+    assert np.allclose(O.adi_hllc(G, 0, WL, WR), flux_exact(prim_to_cons(WL), 0), rtol=1e-14, atol=1e-14)
+
+
+def test_hllc_resolves_a_stationary_contact():
+    # density jump at rest, equal pressures: no mass or energy flux, only p
+    WL = np.array([1.0, 0.0, 0.0, 0.0, 0.8])
+    WR = np.array([0.125, 0.0, 0.0, 0.0, 0.8])
+    F = O.adi_hllc(G, 0, WL, WR)
+    assert np.allclose(F, [0.0, 0.8, 0.0, 0.0, 0.0], rtol=0, atol=1e-15)
+    assert abs(O.adi_rusanov(G, 0, WL, WR)[0]) > 0.1  # the two-wave solver smears it
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_hllc_keeps_a_contact_between_cells_steady(k):
+    N = 4
+    b = I.nmodes(k)
+    u = np.zeros((N ** 3, 5, b))
+    ix = np.arange(N ** 3) % N
+    u[:, 0, 0] = np.where(ix < N // 2, 1.0, 0.2)
+    u[:, 4, 0] = 1.0 / (G - 1)
+    r_h = O.adi_rhs(O.make_cfg(N, k, riemann="hllc"), G, u, 1e-3)
+    r_r = O.adi_rhs(O.make_cfg(N, k), G, u, 1e-3)
+    assert np.abs(r_h).max() < 1e-13
+    assert np.abs(r_r).max() > 1e-2
+
+
+def test_hllc_sod_pair_is_more_accurate_than_rusanov():
+    T, N, k = 0.1, 16, 1
+    WL, WR = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+
+    def exact(x):
+        out = np.empty_like(x)
+        right = x >= 0.5
+        out[right] = sod_exact_rho((x[right] - 0.75) / T, WL, WR)
+        out[~right] = sod_exact_rho(-(x[~right] - 0.25) / T, WL, WR)
+        return out
+
+    errs = {}
+    for solver in ("rusanov", "hllc"):
+        u = sod_pair(N, k)
+        cfg = O.make_cfg(N, k, riemann=solver)
+        t = 0.0
+        while t < T - 1e-14:
+            dt = min(O.adi_dt(cfg, G, u), T - t)
+            rc, t, _ = O.adi_run(cfg, G, u, 1, fixed_dt=dt, t=t)
+            assert rc == 0
+        errs[solver] = l1_rho_vs(N, k, u, exact)
+    assert errs["hllc"] < 0.9 * errs["rusanov"], errs
