@@ -384,8 +384,9 @@ int dg_power_spectrum(dg_ctx* ctx, void* work, size_t work_bytes, int nbins, dou
  * viscous pressure, which is added to p in the momentum and energy fluxes at
  * the volume points (Sec. 3.1).  Face states: rho from its own expansion, v
  * and p from their Gauss projections (Sec. 3.2); Rusanov flux with lambda =
- * max(|v_n| + c).  Positivity after every stage: density and pressure at all
- * volume and face points at or above nu->rho_floor (the floor of both); the
+ * max(|v_n| + c), or HLLC (opts->riemann).  Positivity after every stage:
+ * density and pressure at all volume and face points at or above
+ * nu->rho_floor (the floor of both); the
  * higher modes of all five variables are scaled by theta_rho theta_p toward
  * the cell mean (theta_p the largest factor keeping p at the floor, from the
  * quadratic in theta); a cell mean at or below the floor fails the step,
@@ -402,6 +403,9 @@ typedef struct {
     void* prim;            /* N^3*4*b elements: projections of v_x, v_y, v_z, p   */
     void* scratch;         /* >= scratch bytes of dg_adi_buffer_bytes, 256-aligned */
     size_t scratch_bytes;
+    int32_t riemann;       /* DG_RIEMANN_RUSANOV (0, default) or DG_RIEMANN_HLLC:
+                              HLLC of the Euler equations (Davis bounds, contact
+                              speed and star states); DG_RIEMANN_HLL: DG_EINVAL */
 } dg_adi_opts;
 /* Sizes in bytes of one state register, the projection buffer and the scratch. */
 int dg_adi_buffer_bytes(const dg_mesh* mesh, int order, int precision, size_t* state_bytes, size_t* prim_bytes,

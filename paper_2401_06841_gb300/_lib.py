@@ -39,7 +39,7 @@ class Opts(C.Structure):
 class AdiOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rk_stages", C.c_int32), ("cfl", C.c_double), ("gamma", C.c_double),
                 ("stream", C.c_void_p), ("u", C.c_void_p * 3), ("prim", C.c_void_p), ("scratch", C.c_void_p),
-                ("scratch_bytes", C.c_size_t)]
+                ("scratch_bytes", C.c_size_t), ("riemann", C.c_int32)]
 
 
 class Forcing(C.Structure):

@@ -113,6 +113,63 @@ __device__ __forceinline__ void adi_rusanov(T gamma, const T* WL, const T* WR, T
     for (int v = 0; v < 5; ++v) F[v] = T(0.5) * (FL[v] + FR[v]) - T(0.5) * lam * (UR[v] - UL[v]);
 }
 
+// HLLC flux along Dd from primitive face states (the contact wave restored in
+// the two-wave model): Davis bounds S_L = min(u - c), S_R = max(u + c) over the
+// two states, the contact speed S* from the pressures and the mass fluxes
+// relative to the bounds, star states U*_K = rho_K (S_K - u_K)/(S_K - S*)
+// (1, S* along Dd, the tangential velocities, E_K/rho_K + (S* - u_K)(S* +
+// p_K/(rho_K (S_K - u_K)))), and the flux of the region x/t = 0 falls in
+template <typename T, int Dd>
+__device__ __forceinline__ void adi_hllc(T gamma, const T* WL, const T* WR, T* F)
+{
+    const T g1 = gamma - T(1);
+    T U[2][5], Fx[2][5], c[2], un[2];
+    const T* W[2] = {WL, WR};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const T* w = W[s];
+        const T rho = w[0], p = w[4];
+        un[s] = w[1 + Dd];
+        U[s][0] = rho;
+        U[s][1] = rho * w[1];
+        U[s][2] = rho * w[2];
+        U[s][3] = rho * w[3];
+        U[s][4] = p / g1 + T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        Fx[s][0] = U[s][1 + Dd];
+        Fx[s][1] = U[s][1] * un[s];
+        Fx[s][2] = U[s][2] * un[s];
+        Fx[s][3] = U[s][3] * un[s];
+        Fx[s][1 + Dd] += p;
+        Fx[s][4] = (U[s][4] + p) * un[s];
+        c[s] = sqrt(gamma * p / rho);
+    }
+    const T a0 = un[0] - c[0], a1 = un[1] - c[1], b0 = un[0] + c[0], b1 = un[1] + c[1];
+    const T SL = a0 < a1 ? a0 : a1, SR = b0 > b1 ? b0 : b1;
+    if (SL >= T(0)) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[v] = Fx[0][v];
+        return;
+    }
+    if (SR <= T(0)) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[v] = Fx[1][v];
+        return;
+    }
+    const T qL = WL[0] * (SL - un[0]), qR = WR[0] * (SR - un[1]);
+    const T Ss = (WR[4] - WL[4] + un[0] * qL - un[1] * qR) / (qL - qR);
+    const int s = Ss >= T(0) ? 0 : 1;
+    const T SK = s == 0 ? SL : SR, qK = s == 0 ? qL : qR;
+    const T* w = W[s];
+    const T f = qK / (SK - Ss);
+    T Us[5];
+    Us[0] = f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Us[1 + i] = f * (i == Dd ? Ss : w[1 + i]);
+    Us[4] = f * (U[s][4] / w[0] + (Ss - un[s]) * (Ss + w[4] / qK));
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] = Fx[s][v] + SK * (Us[v] - U[s][v]);
+}
+
 // vNR viscous pressure with the local sound speed c in the bulk term
 template <typename T>
 __device__ __forceinline__ T adi_vnr(const Phys& P, T rho, T c, T divv, T dt)
@@ -592,10 +649,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                         Ws[f] = sTr[(rs + f) * LDT + s];
                         Wn[f] = sTr[(rn + f) * LDT + s];
                     }
-                    if (side)
-                        adi_rusanov<T, Dd>(gamma, Ws, Wn, F);
+                    const T* WLf = side ? Ws : Wn;
+                    const T* WRf = side ? Wn : Ws;
+                    if (a.ph.riemann == 2)
+                        adi_hllc<T, Dd>(gamma, WLf, WRf, F);
                     else
-                        adi_rusanov<T, Dd>(gamma, Wn, Ws, F);
+                        adi_rusanov<T, Dd>(gamma, WLf, WRf, F);
                 }
                 // written after every thread has read its traces (the flux rows alias nothing read here)
 #pragma unroll

@@ -1672,7 +1672,7 @@ int dg_power_spectrum(dg_ctx* ctx, void* work, size_t work_bytes, int nbins, dou
 // of state; the same basis, tables, quadrature and SSP-RK schemes
 // ===========================================================================
 struct dg_adi_ctx {
-    int N = 0, K = 0, b = 0, prec = DG_PREC_F32, rk = 3;
+    int N = 0, K = 0, b = 0, prec = DG_PREC_F32, rk = 3, riemann = DG_RIEMANN_RUSANOV;
     long ncell = 0;
     double h = 0.0, gamma = 1.4, cfl = 0.3;
     dg_nu_params nu{};
@@ -1766,6 +1766,7 @@ Launch adi_make_launch(const dg_adi_ctx* c)
     L.ph.beta = c->nu.beta;
     L.ph.floor_ = c->nu.rho_floor;
     L.ph.av_mode = c->nu.mode;
+    L.ph.riemann = c->riemann;
     L.ttab = c->ttab;
     L.ctl = c->ctl;
     L.partials = c->partials;
@@ -1812,6 +1813,7 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     if (nu->mode < 0 || nu->mode > 1 || !(nu->rho_floor >= 0.0) || nu->diffusion != 0.0) return DG_EINVAL;
     if (opts->precision != DG_PREC_F32 && opts->precision != DG_PREC_F64) return DG_EINVAL;
     if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
+    if (opts->riemann != DG_RIEMANN_RUSANOV && opts->riemann != DG_RIEMANN_HLLC) return DG_EINVAL;
     if (!(opts->cfl > 0.0) || !(opts->gamma > 1.0) || !opts->stream || !opts->prim || !opts->scratch) return DG_EINVAL;
     for (int i = 0; i < 3; ++i)
         if (!opts->u[i]) return DG_EINVAL;
@@ -1826,6 +1828,7 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     ctx->b = (order + 1) * (order + 2) * (order + 3) / 6;
     ctx->prec = opts->precision;
     ctx->rk = opts->rk_stages;
+    ctx->riemann = opts->riemann;
     ctx->ncell = (long)ctx->N * ctx->N * ctx->N;
     ctx->h = 1.0 / ctx->N;
     ctx->gamma = opts->gamma;

@@ -252,3 +252,51 @@ def test_driven_steps_with_reset_parity(prec, g, cs, v_rms, tol):
         h3 = (1.0 / N) ** 3
         E0 = u[:, 4, 0].sum() * h3
         assert abs(s.totals()["energy"] - (E0 + inj - dis)) < 1e-12 * E0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_rhs_parity_hllc(k, prec):
+    N = 5
+    u = state(N, k, 90 + k, prec)
+    dt = 2e-3
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec, riemann="hllc")
+    got = s.rhs(u, dt).cpu().numpy()
+    ref = O.adi_rhs(O.make_cfg(N, k, riemann="hllc"), G, u, dt)
+    err = rel_fields(got, ref)
+    assert err.max() < TOL_RHS[prec], err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_sod_pair_parity_hllc(prec, tol):
+    N, k = 16, 2
+    b = I.nmodes(k)
+    u = np.zeros((N ** 3, 5, b))
+    ix = np.arange(N ** 3) % N
+    high = (ix >= N // 4) & (ix < 3 * N // 4)
+    u[high, 0, 0], u[high, 4, 0] = 1.0, 1.0 / (G - 1)
+    u[~high, 0, 0], u[~high, 4, 0] = 0.125, 0.1 / (G - 1)
+    s = AdiabaticSolver(N, k, gamma=G, precision=prec, riemann="hllc")
+    s.set_state(u)
+    t, _ = s.step(15)
+    got = s.get_state().cpu().numpy()
+    ref = u.copy()
+    rc, tr, _ = O.adi_run(O.make_cfg(N, k, riemann="hllc"), G, ref, 15)
+    assert rc == 0
+    assert t == pytest.approx(tr, rel=1e-10 if prec == "f64" else 1e-5)
+    err = rel_fields(got, ref)
+    assert err.max() < tol, err
+
+
+@pytest.mark.gpu
+def test_hllc_keeps_a_contact_steady_on_the_gpu():
+    N, k = 6, 2
+    b = I.nmodes(k)
+    u = np.zeros((N ** 3, 5, b))
+    ix = np.arange(N ** 3) % N
+    u[:, 0, 0] = np.where(ix < N // 2, 1.0, 0.2)
+    u[:, 4, 0] = 1.0 / (G - 1)
+    r = AdiabaticSolver(N, k, gamma=G, precision="f64", riemann="hllc").rhs(u, 1e-3).cpu().numpy()
+    assert np.abs(r).max() < 1e-13
