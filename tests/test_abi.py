@@ -78,3 +78,34 @@ def test_scratch_query_and_argument_validation(lib):
     assert L.dg_init(C.byref(h), C.byref(bad), 3, 1.0, C.byref(nu), C.byref(opts)) == B.DG_EINVAL
     assert L.dg_step(None, 1, 0.0, None, None) == B.DG_EINVAL
     assert L.dg_rhs(None, None, None, None, 0.0) == B.DG_EINVAL
+
+
+def test_adiabatic_buffer_sizes_and_argument_validation(lib):
+    # host-only paths of the dg_adi_* entry points: no device is touched
+    from paper_2401_06841_gb300 import _lib as B
+    L = B.lib()
+    sz = [C.c_size_t(0) for _ in range(3)]
+    N, k = 8, 3
+    b = (k + 1) * (k + 2) * (k + 3) // 6
+    mesh = B.Mesh((C.c_int32 * 3)(N, N, N), (C.c_double * 3)(1, 1, 1))
+    for prec, el in ((B.PREC_F32, 4), (B.PREC_F64, 8)):
+        assert L.dg_adi_buffer_bytes(C.byref(mesh), k, prec, *[C.byref(x) for x in sz]) == 0
+        assert sz[0].value == N ** 3 * 5 * b * el  # state register
+        assert sz[1].value == N ** 3 * 4 * b * el  # projections of v and p
+        # scratch: the second projection buffer and the driving a_h plus fixed parts
+        assert sz[2].value > N ** 3 * 7 * b * el
+    assert L.dg_adi_buffer_bytes(C.byref(mesh), k, B.PREC_X3, *[C.byref(x) for x in sz]) == B.DG_EINVAL
+    assert L.dg_adi_buffer_bytes(C.byref(mesh), 4, B.PREC_F32, *[C.byref(x) for x in sz]) == B.DG_EINVAL
+    big = B.Mesh((C.c_int32 * 3)(1025, 1025, 1025), (C.c_double * 3)(1, 1, 1))
+    assert L.dg_adi_buffer_bytes(C.byref(big), k, B.PREC_F32, *[C.byref(x) for x in sz]) == B.DG_EINVAL
+    h = C.c_void_p(0)
+    nu = B.NuParams(1, 2.0, 0.2, 1e-3, 0.0, 0.0, 0)
+    opts = B.AdiOpts()  # null buffers, gamma 0: rejected before any device call
+    assert L.dg_adi_init(C.byref(h), C.byref(mesh), k, C.byref(nu), C.byref(opts)) == B.DG_EINVAL
+    assert not h.value
+    learned = B.NuParams(2, 2.0, 0.2, 1e-3, 0.0, 0.0, 0)
+    assert L.dg_adi_init(C.byref(h), C.byref(mesh), k, C.byref(learned), C.byref(opts)) == B.DG_EINVAL
+    assert L.dg_adi_step(None, 1, 0.0, None, None) == B.DG_EINVAL
+    assert L.dg_adi_rhs(None, None, None, 0.0) == B.DG_EINVAL
+    assert L.dg_adi_set_reset(None, 1.0) == B.DG_EINVAL
+    assert L.dg_adi_energy_budget(None, None) == B.DG_EINVAL
