@@ -420,8 +420,9 @@ int dg_adi_set_state(dg_adi_ctx* ctx, const void* src, int src_on_host);
 int dg_adi_get_state(dg_adi_ctx* ctx, void* dst, int to_host);
 /* Projections of v and p of a device state into prim_out [N^3][4][b]. */
 int dg_adi_project(dg_adi_ctx* ctx, const void* u_in, void* prim_out);
-/* Right-hand side du/dt of a device state (dt_pimax: dt of the viscous-pressure
- * cap, 0 = uncapped); uses the context's projection buffer. */
+/* Right-hand side du/dt of a device state without the driving (dt_pimax: dt
+ * of the viscous-pressure cap, 0 = uncapped); uses the context's projection
+ * buffer. */
 int dg_adi_rhs(dg_adi_ctx* ctx, const void* u_in, void* dudt, double dt_pimax);
 /* nsteps SSP-RK steps (fixed_dt > 0 replaces the CFL dt); *t_out the time
  * since dg_adi_set_state, *dt_last the last step's dt.  Synchronises once per
