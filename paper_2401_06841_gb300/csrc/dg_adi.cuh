@@ -60,7 +60,8 @@ struct AdiCfg {
     using C = TileCfg<K, BK_FMA>;
     static constexpr int b = C::b, nq = C::nq, ns = C::ns, nf = C::nf, TC = C::TC, NT = C::NT;
     static constexpr int KP = C::KP, NQP = C::NQP, NP = C::NP, B2K = C::B2K, NSP = C::NSP, B2N = C::B2N;
-    static constexpr int FE = 12;  // rho, m_x, m_y, m_z, e, grad rho (3), div m, 3 zero rows
+    // evaluated rows per cell: rho, m_x, m_y, m_z, e, grad rho (3), div m; driven: a_h (3)
+    static constexpr int FE = DRIVEN ? 12 : 9;
     // m v + P (6), (e + P) v (3); driven: rho (a - abar) (3), m.(a - abar)
     static constexpr int FP = DRIVEN ? 13 : 9;
     static constexpr int LDA = KP, LDV = NQP + 4, LDP = NP, LDC2 = B2K, LDT = NSP + 4, LDL = B2N;
@@ -157,17 +158,24 @@ __device__ __forceinline__ void adi_hllc(T gamma, const T* WL, const T* WR, T* F
     }
     const T qL = WL[0] * (SL - un[0]), qR = WR[0] * (SR - un[1]);
     const T Ss = (WR[4] - WL[4] + un[0] * qL - un[1] * qR) / (qL - qR);
-    const int s = Ss >= T(0) ? 0 : 1;
-    const T SK = s == 0 ? SL : SR, qK = s == 0 ? qL : qR;
-    const T* w = W[s];
+    // the side of the contact x/t = 0 lies on (selects keep everything in registers)
+    const bool lft = Ss >= T(0);
+    const T SK = lft ? SL : SR, qK = lft ? qL : qR, uK = lft ? un[0] : un[1];
+    T wK[5], UK[5], FK[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        wK[v] = lft ? WL[v] : WR[v];
+        UK[v] = lft ? U[0][v] : U[1][v];
+        FK[v] = lft ? Fx[0][v] : Fx[1][v];
+    }
     const T f = qK / (SK - Ss);
     T Us[5];
     Us[0] = f;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) Us[1 + i] = f * (i == Dd ? Ss : w[1 + i]);
-    Us[4] = f * (U[s][4] / w[0] + (Ss - un[s]) * (Ss + w[4] / qK));
+    for (int i = 0; i < 3; ++i) Us[1 + i] = f * (i == Dd ? Ss : wK[1 + i]);
+    Us[4] = f * (UK[4] / wK[0] + (Ss - uK) * (Ss + wK[4] / qK));
 #pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] = Fx[s][v] + SK * (Us[v] - U[s][v]);
+    for (int v = 0; v < 5; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
 }
 
 // vNR viscous pressure with the local sound speed c in the bulk term
@@ -489,7 +497,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 modal_grad<T, K, 2>(u + 3 * b, t2, two_h);
 #pragma unroll
                 for (int l = 0; l < b; ++l) out[l] += t2[l];
-            } else if (f < 12 && SRC) {
+            } else if (SRC && f < 12) {
 #pragma unroll
                 for (int l = 0; l < b; ++l) out[l] = sAh[(c * 3 + f - 9) * b + l];
             }
