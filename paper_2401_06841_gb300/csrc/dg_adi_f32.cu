@@ -1,0 +1,7 @@
+// dg_adi_f32.cu -- FP32 instantiation of the adiabatic-system launchers.
+#include "dg_adi_impl.cuh"
+
+namespace dg {
+template cudaError_t launch_adi<float>(const Launch&, double, const AdiLaunch&);
+template cudaError_t launch_adi_totals<float>(const Launch&, double, const void*, double*, int*);
+}  // namespace dg

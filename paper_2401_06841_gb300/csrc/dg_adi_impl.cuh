@@ -1,4 +1,7 @@
-// dg_adi.cu -- launchers of the adiabatic-system kernels (FP32, FP64; k = 1..3).
+// dg_adi_impl.cuh -- launchers of the adiabatic-system kernels (k = 1..3);
+// instantiated per element type in dg_adi_f32.cu and dg_adi_f64.cu.
+#pragma once
+
 #include "dg_adi.cuh"
 #include "dg_launch.cuh"
 
@@ -97,10 +100,5 @@ cudaError_t launch_adi_totals(const Launch& L, double gamma, const void* u, doub
     if (L.K == 2) return adi_totals_k<T, 2>(L, gamma, u, partials, nblocks);
     return adi_totals_k<T, 3>(L, gamma, u, partials, nblocks);
 }
-
-template cudaError_t launch_adi<float>(const Launch&, double, const AdiLaunch&);
-template cudaError_t launch_adi<double>(const Launch&, double, const AdiLaunch&);
-template cudaError_t launch_adi_totals<float>(const Launch&, double, const void*, double*, int*);
-template cudaError_t launch_adi_totals<double>(const Launch&, double, const void*, double*, int*);
 
 }  // namespace dg
