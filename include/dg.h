@@ -166,9 +166,12 @@ typedef struct {
 
 typedef struct dg_ctx dg_ctx;
 
-/* Bytes of device scratch a context with these parameters needs. */
+/* Bytes of device scratch a context with these parameters needs.  DG_EINVAL
+ * for a mesh dg_init rejects (not n x n x n, or n outside 1..1024) or an
+ * order outside 1..3; no device is touched. */
 int dg_scratch_bytes(const dg_mesh* mesh, int order, const dg_nu_params* nu, size_t* bytes);
-/* Bytes of the projected-velocity buffer dg_opts.vhat must provide. */
+/* Bytes of the projected-velocity buffer dg_opts.vhat must provide (same
+ * mesh and order checks; precision 0..2). */
 int dg_vhat_bytes(const dg_mesh* mesh, int order, int precision, size_t* bytes);
 
 /* Create a context.  Builds the basis/quadrature tables (Sec. 2.1-2.2),
@@ -407,7 +410,9 @@ typedef struct {
                               HLLC of the Euler equations (Davis bounds, contact
                               speed and star states); DG_RIEMANN_HLL: DG_EINVAL */
 } dg_adi_opts;
-/* Sizes in bytes of one state register, the projection buffer and the scratch. */
+/* Sizes in bytes of one state register, the projection buffer and the scratch
+ * (null outputs skipped).  DG_EINVAL for a mesh that is not n x n x n with
+ * 1 <= n <= 1024, an order outside 1..3 or a precision other than F32/F64. */
 int dg_adi_buffer_bytes(const dg_mesh* mesh, int order, int precision, size_t* state_bytes, size_t* prim_bytes,
                         size_t* scratch_bytes);
 /* nu: mode DG_AV_OFF or DG_AV_VNR (alpha, beta, rho_floor); the buffers are

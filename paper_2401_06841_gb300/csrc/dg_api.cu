@@ -874,20 +874,26 @@ int upload_forcing(dg_ctx* ctx)
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+
+// The meshes every entry point accepts: n x n x n cells with 1 <= n <= kMaxN.
+static bool cubic_mesh(const dg_mesh* m)
+{
+    return m->n[0] >= 1 && m->n[0] <= kMaxN && m->n[1] == m->n[0] && m->n[2] == m->n[0];
+}
+
 extern "C" {
 
 int dg_scratch_bytes(const dg_mesh* mesh, int order, const dg_nu_params* nu, size_t* bytes)
 {
-    if (!bytes || !mesh || !nu || order < 1 || order > 3) return DG_EINVAL;
-    const int N = std::max(mesh->n[0], std::max(mesh->n[1], mesh->n[2]));
-    if (N < 1) return DG_EINVAL;
-    *bytes = scratch_layout(order, N, nu->mode == DG_AV_LEARNED).total;
+    if (!bytes || !mesh || !nu || order < 1 || order > 3 || !cubic_mesh(mesh)) return DG_EINVAL;
+    *bytes = scratch_layout(order, mesh->n[0], nu->mode == DG_AV_LEARNED).total;
     return DG_OK;
 }
 
 int dg_vhat_bytes(const dg_mesh* mesh, int order, int precision, size_t* bytes)
 {
-    if (!mesh || !bytes || order < 1 || order > 3 || precision < 0 || precision > 2) return DG_EINVAL;
+    if (!mesh || !bytes || order < 1 || order > 3 || precision < 0 || precision > 2 || !cubic_mesh(mesh))
+        return DG_EINVAL;
     const size_t n = (size_t)mesh->n[0] * mesh->n[1] * mesh->n[2];
     const size_t b = (size_t)(order + 1) * (order + 2) * (order + 3) / 6;
     const size_t v = n * 3 * b * (precision == DG_PREC_F64 ? sizeof(double) : sizeof(float));
@@ -901,8 +907,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     *out = nullptr;
     if (!mesh || !nu || !opts) return DG_EINVAL;
     if (order < 1 || order > 3) return DG_EINVAL;
-    if (mesh->n[0] < 1 || mesh->n[0] != mesh->n[1] || mesh->n[0] != mesh->n[2]) return DG_EINVAL;
-    if (mesh->n[0] > kMaxN) return DG_EINVAL;
+    if (!cubic_mesh(mesh)) return DG_EINVAL;
     for (int d = 0; d < 3; ++d)
         if (mesh->L[d] != 1.0) return DG_EINVAL;
     if (!(cs > 0.0)) return DG_EINVAL;
@@ -1791,7 +1796,7 @@ int dg_adi_buffer_bytes(const dg_mesh* mesh, int order, int precision, size_t* s
                         size_t* scratch_bytes)
 {
     if (!mesh || order < 1 || order > 3 || (precision != DG_PREC_F32 && precision != DG_PREC_F64)) return DG_EINVAL;
-    if (mesh->n[0] < 1 || mesh->n[0] > kMaxN) return DG_EINVAL;
+    if (!cubic_mesh(mesh)) return DG_EINVAL;
     const size_t n = (size_t)mesh->n[0] * mesh->n[1] * mesh->n[2];
     const size_t b = (size_t)(order + 1) * (order + 2) * (order + 3) / 6;
     const size_t el = precision == DG_PREC_F64 ? sizeof(double) : sizeof(float);
@@ -1807,7 +1812,7 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     *out = nullptr;
     if (!mesh || !nu || !opts) return DG_EINVAL;
     if (order < 1 || order > 3) return DG_EINVAL;
-    if (mesh->n[0] < 1 || mesh->n[0] != mesh->n[1] || mesh->n[0] != mesh->n[2] || mesh->n[0] > kMaxN) return DG_EINVAL;
+    if (!cubic_mesh(mesh)) return DG_EINVAL;
     for (int d = 0; d < 3; ++d)
         if (mesh->L[d] != 1.0) return DG_EINVAL;
     if (nu->mode < 0 || nu->mode > 1 || !(nu->rho_floor >= 0.0) || nu->diffusion != 0.0) return DG_EINVAL;

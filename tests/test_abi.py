@@ -70,6 +70,13 @@ def test_scratch_query_and_argument_validation(lib):
     n = C.c_size_t(0)
     assert L.dg_scratch_bytes(C.byref(mesh), 3, C.byref(nu), C.byref(n)) == 0 and n.value > 0
     assert L.dg_scratch_bytes(C.byref(mesh), 7, C.byref(nu), C.byref(n)) == B.DG_EINVAL
+    # the size queries reject the meshes dg_init rejects: too fine, empty, not cubic
+    for dims in ((1025, 1025, 1025), (0, 0, 0), (8, 8, 4)):
+        m = B.Mesh((C.c_int32 * 3)(*dims), (C.c_double * 3)(1, 1, 1))
+        assert L.dg_scratch_bytes(C.byref(m), 3, C.byref(nu), C.byref(n)) == B.DG_EINVAL, dims
+        assert L.dg_vhat_bytes(C.byref(m), 3, 0, C.byref(n)) == B.DG_EINVAL, dims
+    top = B.Mesh((C.c_int32 * 3)(1024, 1024, 1024), (C.c_double * 3)(1, 1, 1))
+    assert L.dg_scratch_bytes(C.byref(top), 3, C.byref(nu), C.byref(n)) == 0 and n.value > 0
     h = C.c_void_p(0)
     opts = B.Opts()
     assert L.dg_init(C.byref(h), C.byref(mesh), 3, 1.0, C.byref(nu), C.byref(opts)) == B.DG_EINVAL
@@ -98,6 +105,8 @@ def test_adiabatic_buffer_sizes_and_argument_validation(lib):
     assert L.dg_adi_buffer_bytes(C.byref(mesh), 4, B.PREC_F32, *[C.byref(x) for x in sz]) == B.DG_EINVAL
     big = B.Mesh((C.c_int32 * 3)(1025, 1025, 1025), (C.c_double * 3)(1, 1, 1))
     assert L.dg_adi_buffer_bytes(C.byref(big), k, B.PREC_F32, *[C.byref(x) for x in sz]) == B.DG_EINVAL
+    flat = B.Mesh((C.c_int32 * 3)(8, 8, 4), (C.c_double * 3)(1, 1, 1))
+    assert L.dg_adi_buffer_bytes(C.byref(flat), k, B.PREC_F32, *[C.byref(x) for x in sz]) == B.DG_EINVAL
     h = C.c_void_p(0)
     nu = B.NuParams(1, 2.0, 0.2, 1e-3, 0.0, 0.0, 0)
     opts = B.AdiOpts()  # null buffers, gamma 0: rejected before any device call
