@@ -372,6 +372,25 @@ std::vector<char> tile_tables_for(int K, int prec)
     return tile_tables_bytes<3>(prec);
 }
 
+// Weights (a, b) of an SSP-RK stage out = a u^n + b (u + dt L) as the kernels
+// receive them.  In single precision b is rounded to float and a = 1 - b is
+// formed exactly, so that a + b = 1 in the kernels' arithmetic: the float
+// roundings of 1/3 and 2/3 add up to 1 + 2^-25, and with them every SSP-RK3
+// step would scale the state by 1 + 3e-8 on average, a steady drift of mass,
+// momentum and energy.  Double precision keeps the rounded fractions (their
+// sum is 1 - 2^-54).
+static void rk_weights(int rk, int s, bool single, double& a, double& b)
+{
+    static const double A2[2] = {0.0, 0.5}, B2[2] = {1.0, 0.5};
+    static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
+    a = rk == 2 ? A2[s] : A3[s];
+    b = rk == 2 ? B2[s] : B3[s];
+    if (single && a != 0.0) {
+        b = (double)(float)b;
+        a = 1.0 - b;  // exact: b is in [1/4, 1) with a 24-bit significand
+    }
+}
+
 int ttab_total(int K)
 {
     // words of the larger of the two backends' layouts
@@ -1148,10 +1167,6 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
     if (!ctx) return DG_EINVAL;
     if (nsteps < 0) return fail(ctx, DG_EINVAL, "dg_step: nsteps < 0");
     if (!ctx->state_set) return fail(ctx, DG_ESTATE, "dg_step: no state set");
-    static const double A2[2] = {0.0, 0.5}, B2[2] = {1.0, 0.5};
-    static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
-    const double* RA = ctx->rk == 2 ? A2 : A3;
-    const double* RB = ctx->rk == 2 ? B2 : B3;
     if (ctx->nu.mode == DG_AV_LEARNED && !ctx->weights_set)
         return fail(ctx, DG_ESTATE, "dg_step: learned mode needs dg_set_av_weights");
     for (int st = 0; st < nsteps; ++st) {
@@ -1225,8 +1240,7 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
                 t.vh_in = vh_buf(ctx, (pb + s) & 1);
                 t.vh_out = vh_buf(ctx, (pb + s + 1) & 1);
                 t.ahat = force ? ctx->ahat : nullptr;
-                t.rk_a = RA[s];
-                t.rk_b = RB[s];
+                rk_weights(ctx->rk, s, ctx->prec != DG_PREC_F64, t.rk_a, t.rk_b);
                 // every stage projects its output; the last one for the next step,
                 // with the CFL bound (and |v| in learned mode)
                 t.flags = (force ? F_FORCE : 0) | F_NEXTPROJ | (last ? F_DT : 0);
@@ -1951,10 +1965,6 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
     if (!ctx) return DG_EINVAL;
     if (nsteps < 0 || !(fixed_dt >= 0.0)) return afail(ctx, DG_EINVAL, "dg_adi_step: bad arguments");
     if (!ctx->state_set) return afail(ctx, DG_ESTATE, "dg_adi_step: no state set");
-    static const double A2[2] = {0.0, 0.5}, B2[2] = {1.0, 0.5};
-    static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
-    const double* RA = ctx->rk == 2 ? A2 : A3;
-    const double* RB = ctx->rk == 2 ? B2 : B3;
     static const double W2[2] = {0.5, 0.5}, W3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
     const double* RW = ctx->rk == 2 ? W2 : W3;
     const size_t ahat_bytes = (size_t)ctx->ncell * 3 * ctx->b * adi_elem(ctx);
@@ -2029,8 +2039,7 @@ int dg_adi_step(dg_adi_ctx* ctx, int nsteps, double fixed_dt, double* t_out, dou
                 t.abar_in = s & 1;
                 t.abar_out = (s + 1) & 1;
                 t.beta = RW[s];
-                t.rk_a = RA[s];
-                t.rk_b = RB[s];
+                rk_weights(ctx->rk, s, ctx->prec != DG_PREC_F64, t.rk_a, t.rk_b);
                 ACK(adi_go(ctx, t));
             }
             struct {
