@@ -104,7 +104,10 @@ typedef struct {
 
 typedef struct {
     int32_t precision;     /* DG_PREC_*                                           */
-    int32_t rk_stages;     /* 2 (SSP-RK2) or 3 (SSP-RK3), Sec. 7                   */
+    int32_t rk_stages;     /* 2 (SSP-RK2) or 3 (SSP-RK3), Sec. 7; in FP32 and x3
+                              the third RK3 stage uses b = float(2/3), a = 1 - b,
+                              whose sum is exactly one (no steady scaling of the
+                              state by the rounded fractions)                    */
     double cfl;            /* dt = cfl h / ((k+1) max sum_d(|v_d| + cs))           */
     void* stream;          /* cudaStream_t; must not be NULL                       */
     void* u[3];            /* three state registers, each N^3*4*b elements; the
@@ -398,7 +401,7 @@ int dg_power_spectrum(dg_ctx* ctx, void* work, size_t work_bytes, int nbins, dou
 typedef struct dg_adi_ctx dg_adi_ctx;
 typedef struct {
     int32_t precision;     /* DG_PREC_F32 or DG_PREC_F64                          */
-    int32_t rk_stages;     /* 2 or 3                                              */
+    int32_t rk_stages;     /* 2 or 3; stage weights as for dg_opts.rk_stages      */
     double cfl;            /* dt = cfl h / ((k+1) max sum_d(|v_d| + c))           */
     double gamma;          /* adiabatic index, > 1                                */
     void* stream;          /* cudaStream_t; must not be NULL                      */
