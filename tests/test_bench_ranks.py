@@ -73,3 +73,26 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["config"]["workload"]
+
+
+def test_profiled_traffic_is_dropped_when_the_kernel_changes(tmp_path, monkeypatch):
+    # the stage kernel's DRAM bytes come from the committed ncu summary only
+    # while the kernel sources hash to the value recorded beside them
+    import argparse
+    import shutil
+    prof = os.path.join("profiles", "k_tile_x3_stage_64c_k3.md")
+    csrc = os.path.join("paper_2401_06841_gb300", "csrc")
+    os.makedirs(tmp_path / "profiles")
+    os.makedirs(tmp_path / csrc)
+    shutil.copy(os.path.join(ROOT, prof), tmp_path / prof)
+    for name in ("dg_tile.cuh", "dg_mma.cuh", "dg_common.cuh", "dg_launch_impl.cuh"):
+        shutil.copy(os.path.join(ROOT, csrc, name), tmp_path / csrc / name)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    args = argparse.Namespace(N=64, k=3)
+    got = bench.profiled_traffic(args, "x3")
+    assert isinstance(got, int) and got > 0
+    assert "traffic_per_launch_bytes: %d" % got in open(tmp_path / prof).read()
+    with open(tmp_path / csrc / "dg_tile.cuh", "a") as fh:
+        fh.write("\n")
+    assert bench.profiled_traffic(args, "x3") is None
+    assert bench.profiled_traffic(argparse.Namespace(N=32, k=3), "x3") is None  # no summary for that mesh
