@@ -118,3 +118,53 @@ def test_adiabatic_buffer_sizes_and_argument_validation(lib):
     assert L.dg_adi_rhs(None, None, None, 0.0) == B.DG_EINVAL
     assert L.dg_adi_set_reset(None, 1.0) == B.DG_EINVAL
     assert L.dg_adi_energy_budget(None, None) == B.DG_EINVAL
+
+
+def test_a_c_program_links_and_queries_sizes(lib):
+    # the header's prototypes used from C itself, linked against libdg.so:
+    # the size queries (no device touched) agree with the ctypes binding and
+    # reject the meshes the constructors reject
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_2401_06841_gb300 import _lib as B
+    from paper_2401_06841_gb300 import build
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    prog = r'''
+#include <stdio.h>
+#include "dg.h"
+int main(void) {
+    dg_mesh m = {{64, 64, 64}, {1.0, 1.0, 1.0}}, bad = {{64, 64, 32}, {1.0, 1.0, 1.0}};
+    dg_nu_params nu = {0};
+    size_t s = 0, v = 0, us = 0, up = 0, usc = 0;
+    nu.mode = DG_AV_LEARNED;
+    int r1 = dg_scratch_bytes(&m, 3, &nu, &s);
+    int r2 = dg_vhat_bytes(&m, 3, DG_PREC_X3, &v);
+    int r3 = dg_adi_buffer_bytes(&m, 3, DG_PREC_F32, &us, &up, &usc);
+    int r4 = dg_scratch_bytes(&bad, 3, &nu, &s);
+    printf("%d %d %d %d %zu %zu %zu %zu %zu\n", r1, r2, r3, r4, s, v, us, up, usc);
+    return 0;
+}
+'''
+    pkg = os.path.dirname(build.OUT)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "q.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "q")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe, "-L", pkg, "-ldg",
+                               "-Wl,-rpath," + pkg, "-L/usr/local/cuda/lib64", "-Wl,-rpath-link,/usr/local/cuda/lib64"])
+        out = subprocess.check_output([exe]).split()
+    r1, r2, r3, r4, s, v, us, up, usc = [int(x) for x in out]
+    assert (r1, r2, r3) == (0, 0, 0) and r4 == B.DG_EINVAL
+    L = B.lib()
+    mesh = B.Mesh((C.c_int32 * 3)(64, 64, 64), (C.c_double * 3)(1, 1, 1))
+    nu = B.NuParams(B.AV_LEARNED, 0.0, 0.0, 0.0, 0.0)
+    n = C.c_size_t(0)
+    assert L.dg_scratch_bytes(C.byref(mesh), 3, C.byref(nu), C.byref(n)) == 0 and n.value == s
+    assert L.dg_vhat_bytes(C.byref(mesh), 3, B.PREC_X3, C.byref(n)) == 0 and n.value == v
+    sz = [C.c_size_t(0) for _ in range(3)]
+    assert L.dg_adi_buffer_bytes(C.byref(mesh), 3, B.PREC_F32, *[C.byref(x) for x in sz]) == 0
+    assert [x.value for x in sz] == [us, up, usc]
+    b = 20
+    assert us == 64 ** 3 * 5 * b * 4 and up == 64 ** 3 * 4 * b * 4
