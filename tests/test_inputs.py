@@ -3,7 +3,9 @@ they promise, by brute force: the turbulent velocity's per-cell coefficients
 are the L2 projection of a band-limited Fourier field (its amplitudes
 recovered from the cell means alone, then projected cell by cell with a
 12-point Gauss rule), the Helmholtz weight zeta selects the transverse or the
-longitudinal part, and the rms cell-mean speed is the requested Mach number.
+longitudinal part, and the rms cell-mean speed is the requested Mach number;
+the random parity states keep the density above its stated bound at every
+point and the five-variable ones their cell-mean pressure inside its band.
 CPU only."""
 import numpy as np
 import pytest
@@ -93,3 +95,34 @@ def test_rms_cell_mean_speed_is_the_mach_number():
     for mach, cs in ((0.5, 1.0), (3.0, 2.0)):
         v = I.turbulent_velocity(8, 2, seed=3, mach=mach, cs=cs)
         assert np.sqrt((v[:, :, 0] ** 2).sum(axis=1).mean()) == pytest.approx(mach * cs, rel=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_random_state_density_stays_above_its_bound(k):
+    # sum_l |rho_l| sup|phi_l| = wiggle * rho_0 for the higher modes, so at
+    # any point of the cell rho >= (1 - wiggle) rho_0: sampled at random points
+    N, wiggle = 4, 0.6
+    u = I.random_state(N, k, seed=21 + k, rho_wiggle=wiggle)
+    rng = np.random.default_rng(k)
+    xi = rng.uniform(-1, 1, (3, 4000))
+    ijl = I.mode_degrees(k)
+    phi = np.stack([legendre_orthonormal(i, xi[0]) * legendre_orthonormal(j, xi[1]) * legendre_orthonormal(l, xi[2])
+                    for (i, j, l) in ijl])  # [b][points]
+    rho = u[:, 0, :] @ phi  # [cells][points]
+    r0 = u[:, 0, 0][:, None]
+    assert (rho >= (1 - wiggle) * r0 - 1e-12).all()
+    assert (rho <= (1 + wiggle) * r0 + 1e-12).all()
+    # and the bound is not loose: the sampled dip below rho_0 reaches at
+    # least 40% of it (random points rarely hit the corner where it is attained)
+    assert ((r0 - rho) / r0).max() > 0.4 * wiggle
+
+
+def test_random_energy_state_cell_mean_pressure():
+    # cell-mean pressure (gamma-1)(e_0 - |m_0|^2 / (2 rho_0)) inside p_mean [1 -+ spread/2]
+    g, pm, sp = 1.4, 5.0, 0.5
+    u = I.random_energy_state(6, 2, seed=8, p_mean=pm, p_spread=sp, gamma=g, v_rms=0.4)
+    p = (g - 1) * (u[:, 4, 0] - 0.5 * (u[:, 1:4, 0] ** 2).sum(axis=1) / u[:, 0, 0])
+    assert p.min() >= pm * (1 - sp / 2) - 1e-12 and p.max() <= pm * (1 + sp / 2) + 1e-12
+    assert p.max() - p.min() > 0.5 * pm * sp  # spread over the band
+    ref = I.random_state(6, 2, seed=8, v_rms=0.4)
+    assert np.array_equal(u[:, :4], ref)  # rho and m as the isothermal recipe draws them
