@@ -364,9 +364,10 @@ def test_fullsize_64_k3_driven_f64():
     # FP64: the driving's mean, the injected work and the dissipated energy
     # are reduced over every block of the grid, and the budget closes.
     # (In FP32 the dissipated energy of this one step comes out 4% below
-    # the oracle's while the injected work agrees to 1e-4: it is the
-    # difference of two energies near 10 per unit volume, so the FP32
-    # rounding of the stored state enters it amplified.)
+    # the oracle's while the injected work agrees to 1e-4: the first FP32
+    # reset lifts a start state reset in FP64 (10 rho) to the FP32 value of
+    # c_s^2/(gamma - 1), 10.00000095 rho, and books the difference as
+    # negative dissipation; later resets target the same constant.)
     N, k = 64, 3
     cs, fo = 2.0, dict(mach=2.0, zeta=0.5, seed=8)
     u = I.adiabatic_turbulent_state(N, k, seed=71, mach=0.5, gamma=G)
