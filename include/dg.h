@@ -214,8 +214,15 @@ int dg_project_velocity(dg_ctx* ctx, const void* u_in, void* vhat_out);
  * fixed_dt > 0 replaces the CFL dt (used to replay a recorded sequence). */
 int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_last);
 
-/* Configure the driving; draws the initial OU state from its stationary law
- * and projects the acceleration onto the basis before the next step. */
+/* Configure the driving (Sec. 4.2, eq. ornstein_uhlenbeck_process_time_evolution
+ * and the eddy turnover time t_c = L/(2 cs M)): an OU process of the integer
+ * modes kmin2 <= |k|^2 <= kmax2 (one of each +-k pair), Helmholtz weight zeta,
+ * advanced every t_c/100 at the first step whose time has reached the next
+ * update time, switched off after t_off (> 0).  Draws the initial OU state
+ * from its stationary law (SplitMix64(seed), Box-Muller) and projects the
+ * acceleration onto the basis before the next step.  f->on == 0 switches the
+ * driving off (zero acceleration).  DG_EINVAL for mach <= 0, kmin2 < 1,
+ * kmax2 < kmin2, kmax2 > 64, zeta outside [0, 1] or more than 512 modes. */
 int dg_set_forcing(dg_ctx* ctx, const dg_forcing* f);
 
 /* Use an explicit projected acceleration (device or host, [c][3][b]) and
@@ -262,10 +269,12 @@ int dg_av_param_count(dg_ctx* ctx, int64_t* n);
 int dg_set_av_weights(dg_ctx* ctx, const float* w, size_t n);
 int dg_get_av_weights(dg_ctx* ctx, float* w, size_t n);
 /* Inputs and plain-sensor targets of every cell of the current state (device
- * buffers x [N^3][2b], y [N^3] FP32): y = log(max(nu_cell, nu_f) / (cs h/p)),
- * nu_cell the largest Pi/(rho |div v|) of the vNR pressure over the cell's
- * compressive volume points (dt_for_pimax fixes the cap), nu_f = max(beta,
- * 0.05) cs h/p the coefficient of the linear term.  Needs a
+ * buffers x [N^3][2b], y [N^3] FP32): x = (rho_l/rho_0, |v|hat_l/cs) with
+ * |v|hat the Gauss projection of |m/rho|; y = log(max(nu_cell, nu_f) /
+ * (cs h/p)), nu_cell the Gauss-weighted mean, over the cell's volume points
+ * with div v < 0, of the pointwise coefficient Pi/(rho |div v|) of the vNR
+ * pressure of Sec. 3.1 (dt_for_pimax fixes the cap), 0 without such points;
+ * nu_f = max(beta, 0.05) cs h/p the coefficient of the linear term.  Needs a
  * context created in DG_AV_LEARNED mode (it holds the |v| projection). */
 int dg_generate_pairs(dg_ctx* ctx, double dt_for_pimax, float* x, float* y, int64_t cap, int64_t* n_out);
 /* Minibatch Adam on the mean squared error of y over (x [n][2b], y [n]),
@@ -323,13 +332,14 @@ int dg_set_meta(dg_ctx* ctx, const dg_meta* in);
  * (control block, reduction partials, basis tables, projected velocity)
  * lives in one fixed 64 MiB device array of the library, held by every GPU
  * that loads it until the process exits.  Limit: N^3 * 3 * b * element size
- * plus about 1.2 MiB must fit in 64 MiB (for example N <= 64 at k = 3 in
- * FP32); larger meshes return DG_ENOMEM and nothing runs.  Artificial
+ * plus a 1,180,160-byte head must fit in 64 MiB (N <= 65 at k = 3 in FP32,
+ * N <= 51 in FP64); larger meshes return DG_ENOMEM and nothing runs.  Artificial
  * viscosity modes DG_AV_OFF and DG_AV_VNR only, no diffusion operator (nu->diffusion
- * must be 0).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) and the first
- * call for a given order and precision uploads the tables: make that first
- * call before any stream capture.  All calls share the array and it keeps the
+ * must be 0), Rusanov face fluxes only (it equals dg_rhs of a context created
+ * with riemann = DG_RIEMANN_RUSANOV).  Every call looks up the array's device
+ * address (cudaGetSymbolAddress, a host-side query); the first call for a
+ * given order and precision at that address uploads the tables (again after a
+ * device reset): make that first call before any stream capture.  All calls share the array and it keeps the
  * last call's contents; its control block is cleared at every call.  Calls
  * whose GPU work overlaps (other streams, other host threads) race on the
  * array and must be serialised.  Work is enqueued on `stream` (a

@@ -28,6 +28,17 @@
 
 namespace dg {
 
+// gas constants in the element type, each rounded once from its double value on
+// the host: near gamma = 1 the difference gamma - 1 formed in single precision
+// would carry the rounding of gamma (float(1.0001) - 1 = 1.000166e-4)
+template <typename T>
+struct AdiGas {
+    T gamma;   // gamma
+    T g1;      // gamma - 1
+    T ig1;     // 1 / (gamma - 1)
+    T cth;     // reset mode: cs^2 / (gamma - 1), the thermal energy per unit mass
+};
+
 template <typename T>
 struct AdiArgs {
     const T* u_in;   // [c][5][b]
@@ -41,6 +52,7 @@ struct AdiArgs {
     int N;
     Phys ph;         // h, hp, alpha, beta, floor_ (density and pressure floor), av_mode
     double gamma;
+    AdiGas<T> gas;   // gamma, gamma - 1, 1/(gamma - 1), cs_reset^2/(gamma - 1) rounded from doubles
     T rk_a, rk_b;
     double dt_pimax; // right-hand-side mode: dt of the viscous-pressure cap
     int flags;       // F_DT (projection mode), F_NEXTPROJ (stage mode), F_FORCE
@@ -84,9 +96,9 @@ struct AdiCfg {
 // Rusanov flux along Dd from primitive face states W = (rho, v_x, v_y, v_z, p):
 // 1/2 (F(U_L) + F(U_R)) - 1/2 lambda (U_R - U_L), lambda = max(|v_n| + c)
 template <typename T, int Dd>
-__device__ __forceinline__ void adi_rusanov(T gamma, const T* WL, const T* WR, T* F)
+__device__ __forceinline__ void adi_rusanov(const AdiGas<T>& G, const T* WL, const T* WR, T* F)
 {
-    const T g1 = gamma - T(1);
+    const T g1 = G.g1, gamma = G.gamma;
     T UL[5], UR[5], FL[5], FR[5], ls[2];
     const T* W[2] = {WL, WR};
     T* U[2] = {UL, UR};
@@ -121,9 +133,9 @@ __device__ __forceinline__ void adi_rusanov(T gamma, const T* WL, const T* WR, T
 // (1, S* along Dd, the tangential velocities, E_K/rho_K + (S* - u_K)(S* +
 // p_K/(rho_K (S_K - u_K)))), and the flux of the region x/t = 0 falls in
 template <typename T, int Dd>
-__device__ __forceinline__ void adi_hllc(T gamma, const T* WL, const T* WR, T* F)
+__device__ __forceinline__ void adi_hllc(const AdiGas<T>& G, const T* WL, const T* WR, T* F)
 {
-    const T g1 = gamma - T(1);
+    const T g1 = G.g1, gamma = G.gamma;
     T U[2][5], Fx[2][5], c[2], un[2];
     const T* W[2] = {WL, WR};
 #pragma unroll
@@ -195,9 +207,9 @@ __device__ __forceinline__ T adi_vnr(const Phys& P, T rho, T c, T divv, T dt)
 // smallest t in [0, 1] with p(ub + t d) = eps (p(ub) > eps > p(ub + d)): the
 // root of rho e - |m|^2/2 - eps rho/(gamma-1), quadratic in t
 template <typename T>
-__device__ __forceinline__ T adi_pressure_root(T gamma, T eps, const T* ub, const T* dv)
+__device__ __forceinline__ T adi_pressure_root(const AdiGas<T>& G, T eps, const T* ub, const T* dv)
 {
-    const T g1 = eps / (gamma - T(1));
+    const T g1 = eps / G.g1;
     const T A = dv[0] * dv[4] - T(0.5) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[3] * dv[3]);
     const T B = ub[0] * dv[4] + dv[0] * ub[4] - (ub[1] * dv[1] + ub[2] * dv[2] + ub[3] * dv[3]) - g1 * dv[0];
     const T C = ub[0] * ub[4] - T(0.5) * (ub[1] * ub[1] + ub[2] * ub[2] + ub[3] * ub[3]) - g1 * ub[0];
@@ -217,9 +229,9 @@ __device__ __forceinline__ T adi_pressure_root(T gamma, T eps, const T* ub, cons
 }
 
 template <typename T>
-__device__ __forceinline__ T adi_p(T gamma, T rho, T mx, T my, T mz, T e)
+__device__ __forceinline__ T adi_p(const AdiGas<T>& G, T rho, T mx, T my, T mz, T e)
 {
-    return (gamma - T(1)) * (e - T(0.5) * (mx * mx + my * my + mz * mz) / rho);
+    return G.g1 * (e - T(0.5) * (mx * mx + my * my + mz * mz) / rho);
 }
 
 // copy n elements (a multiple of 4) of a tile from global to shared; elements
@@ -280,7 +292,7 @@ __device__ __forceinline__ void adi_project_tile(T* sm, const T* sU, const T* ta
                 f[it][0] = mx * ir;
                 f[it][1] = my * ir;
                 f[it][2] = mz * ir;
-                f[it][3] = adi_p<T>(gamma, rho, mx, my, mz, v[4 * LDV]);
+                f[it][3] = adi_p<T>(a.gas, rho, mx, my, mz, v[4 * LDV]);
                 if ((a.flags & F_DT) && c < nvalid) {
                     const T cs = sqrt(gamma * f[it][3] * ir);
                     const T sp = fabs(f[it][0]) + fabs(f[it][1]) + fabs(f[it][2]) + T(3) * cs;
@@ -382,7 +394,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
         s_status = 0u;
         s_smax = 0ull;
     }
-    const T gamma = T(a.gamma), g1 = gamma - T(1), fill_e = T(1) / g1;
+    const T gamma = a.gas.gamma, g1 = a.gas.g1, fill_e = a.gas.ig1;
     const T two_h = T(2.0 / a.ph.h), inv4h = T(0.25 / a.ph.h);
     const T eps = T(a.ph.floor_);
     double dtd = a.dt_pimax;
@@ -432,7 +444,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
             __syncthreads();
             mm<T, BK_FMA, TC * 4, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sBig);
             __syncthreads();
-            const T cth = T(a.cs_reset * a.cs_reset) / g1;
+            const T cth = a.gas.cth;
             constexpr int PER = (TC * NQP + NT - 1) / NT;
             T ev[PER];
 #pragma unroll
@@ -660,9 +672,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                     const T* WLf = side ? Ws : Wn;
                     const T* WRf = side ? Wn : Ws;
                     if (a.ph.riemann == 2)
-                        adi_hllc<T, Dd>(gamma, WLf, WRf, F);
+                        adi_hllc<T, Dd>(a.gas, WLf, WRf, F);
                     else
-                        adi_rusanov<T, Dd>(gamma, WLf, WRf, F);
+                        adi_rusanov<T, Dd>(a.gas, WLf, WRf, F);
                 }
                 // written after every thread has read its traces (the flux rows alias nothing read here)
 #pragma unroll
@@ -713,7 +725,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                     dl[v] = part;
                 }
                 if (c >= nvalid) continue;  // warp-uniform
-                const T pbar = adi_p<T>(gamma, ub[0], ub[1], ub[2], ub[3], ub[4]);
+                const T pbar = adi_p<T>(a.gas, ub[0], ub[1], ub[2], ub[3], ub[4]);
                 if (!(ub[0] > eps) || !(pbar > eps)) {
                     st |= DG_ST_FAIL_;
                     continue;
@@ -774,8 +786,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                             uq[v] = ub[v] + th_r * (val[j][v] - ub[v]);
                             dv[v] = uq[v] - ub[v];
                         }
-                        if (adi_p<T>(gamma, uq[0], uq[1], uq[2], uq[3], uq[4]) < eps) {
-                            const T t = adi_pressure_root<T>(gamma, eps, ub, dv);
+                        if (adi_p<T>(a.gas, uq[0], uq[1], uq[2], uq[3], uq[4]) < eps) {
+                            const T t = adi_pressure_root<T>(a.gas, eps, ub, dv);
                             th_p = t < th_p ? t : th_p;
                         }
                     }

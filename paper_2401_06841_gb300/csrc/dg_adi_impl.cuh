@@ -52,6 +52,10 @@ cudaError_t adi_k(const Launch& L, double gamma, const AdiLaunch& t)
     a.N = L.N;
     a.ph = L.ph;
     a.gamma = gamma;
+    a.gas.gamma = T(gamma);
+    a.gas.g1 = T(gamma - 1.0);
+    a.gas.ig1 = T(1.0 / (gamma - 1.0));
+    a.gas.cth = T(t.cs_reset * t.cs_reset / (gamma - 1.0));
     a.rk_a = T(t.rk_a);
     a.rk_b = T(t.rk_b);
     a.dt_pimax = t.dt_pimax;

@@ -17,11 +17,14 @@
 // or any host allocator: the tables are built in fixed-size static host
 // buffers and copied in.
 //
-// Set-up: the first call on a device (with that device current) looks up the
-// device address of the array with cudaGetSymbolAddress -- in host code the
-// array's name is only a host-side stand-in, never a device address -- and
-// the first call for a given degree and precision builds and uploads the
-// basis tables.  Make that first call before any stream capture.
+// Set-up: every call looks up the device address of the array on the current
+// device with cudaGetSymbolAddress -- in host code the array's name is only a
+// host-side stand-in, never a device address -- and the first call for a given
+// degree and precision at that address builds and uploads the basis tables
+// (again after a device reset has moved the array).  Make the first call of
+// each degree and precision before any stream capture.
+//
+// Face flux: Rusanov only (there is no context to carry a choice of solver).
 //
 // Sharing: all calls on a device use the same array and it keeps the last
 // call's contents.  The control block (whose counters and sums must start at
@@ -49,8 +52,7 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 struct DevState {
-    bool ready = false;
-    unsigned char* base = nullptr;  // device address of g_noalloc_scratch
+    unsigned char* base = nullptr;  // device address of g_noalloc_scratch at the last call
     int tab_K = 0, tab_prec = -1;   // degree / precision of the uploaded tables
 };
 DevState g_dev[kMaxDevices];
@@ -249,14 +251,18 @@ extern "C" int dg_rhs_noalloc(const dg_mesh* mesh, int order, double cs, const d
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return report(DG_ECUDA, "cudaGetDevice");
     DevState& S = g_dev[dev];
     cudaStream_t st = (cudaStream_t)stream;
-    if (!S.ready) {
+    {
+        // looked up at every call (a host-side query, no synchronisation): after a
+        // device reset the module loads again and the array may sit elsewhere,
+        // with no tables in it
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return report(DG_ECUDA, cudaGetErrorString(e));
-        S.base = static_cast<unsigned char*>(p);
-        S.ready = true;
-        S.tab_K = 0;
-        S.tab_prec = -1;
+        if (static_cast<unsigned char*>(p) != S.base) {
+            S.base = static_cast<unsigned char*>(p);
+            S.tab_K = 0;
+            S.tab_prec = -1;
+        }
     }
     if (S.tab_K != order || S.tab_prec != precision) {
         const size_t nb = fill_tables_for(order, precision);

@@ -170,22 +170,20 @@ int main(void) {
     assert us == 64 ** 3 * 5 * b * 4 and up == 64 ** 3 * 4 * b * 4
 
 
-def test_readme_c_example_compiles_and_links(lib):
-    # the C example of README.md against the header, libdg.so and the CUDA
-    # runtime (compiled and linked only: running it needs a GPU)
+def test_c_example_compiles_and_links(lib):
+    # the C example of the ABI (tests/c/run_ten_steps.c) against the header,
+    # libdg.so and the CUDA runtime (compiled and linked only: running it needs a GPU)
     import shutil
     import subprocess
     import tempfile
     from paper_2401_06841_gb300 import build
     if shutil.which("gcc") is None or not os.path.isdir("/usr/local/cuda/include"):
         pytest.skip("no C compiler or CUDA headers")
-    text = open(os.path.join(ROOT, "README.md")).read()
-    m = re.search(r"```c\n(.*?)```", text, flags=re.S)
-    assert m, "README.md has no C example"
+    src = open(os.path.join(ROOT, "tests", "c", "run_ten_steps.c")).read()
     pkg = os.path.dirname(build.OUT)
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "example.c")
-        open(c, "w").write(m.group(1) + "\nint main(void) { return 0; }\n")
+        open(c, "w").write(src + "\nint main(void) { return 0; }\n")
         subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
                                "-I", "/usr/local/cuda/include", c, "-o", os.path.join(d, "example"),
                                "-L", pkg, "-ldg", "-Wl,-rpath," + pkg, "-L/usr/local/cuda/lib64", "-lcudart"])

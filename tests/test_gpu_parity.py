@@ -366,6 +366,57 @@ def test_positivity_failure_is_retried_then_reported():
     assert np.array_equal(s.get_state().cpu().numpy(), u)
 
 
+def _expanding_thin_gas(N, k, rho0=1.12e-3, V=12.0):
+    """rho = rho0 near the floor, m_x = rho0 V sin(2 pi x): the cells around x = 0
+    lose mass fast.  With the CFL dt a stage takes a cell mean to the floor
+    (the oracle's full-dt step fails with the smallest mean 2% below it); with
+    dt/2 every mean stays 4% above it."""
+    u = np.zeros((N ** 3, 4, O.nmodes(k)))
+    u[:, 0, 0] = rho0
+    u[:, 1, :] = rho0 * V * I.fourier_coeffs(N, k, (1, 0, 0)).imag
+    return u
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_failed_step_succeeds_on_the_halved_retry(prec):
+    # Sec. 3.1 positivity: the first attempt with the CFL dt fails, the step is
+    # redone from u^n with dt/2 and succeeds; state and dt as the oracle's run
+    N, k = 4, 1
+    u = _expanding_thin_gas(N, k)
+    cfg = O.make_cfg(N, k)
+    dt_cfl = O.dt(cfg, u)
+    w = u.copy()
+    assert O.step(cfg, w, None, dt_cfl) & O.ORC_FAIL
+    ref = u.copy()
+    rc, t_ref, dl_ref, _ = O.run(cfg, ref, 1)
+    assert rc == 0 and dl_ref == 0.5 * dt_cfl
+    s = Solver(N, k, precision=prec)
+    s.set_state(u)
+    t, dl = s.step(1)
+    tol_dt = 1e-13 if prec == "f64" else 1e-6
+    assert dl == pytest.approx(0.5 * dt_cfl, rel=tol_dt) and t == pytest.approx(t_ref, rel=tol_dt)
+    err = rel_l2_fields(s.get_state().cpu().numpy(), ref)
+    assert err.max() < (1e-12 if prec == "f64" else 3e-5), err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32", "x3"])
+def test_non_finite_coefficient_is_reported(prec):
+    # a NaN written into the state through dg_set_state (host copy): the step
+    # that reads it reports DG_ENONFINITE
+    from paper_2401_06841_gb300 import _lib as B
+    N, k = 5, 2
+    u = I.random_state(N, k, seed=41)
+    u[17, 2, 3] = np.nan
+    s = Solver(N, k, precision=prec)
+    s.set_state(u)
+    with pytest.raises(B.DGError) as ei:
+        s.step(1)
+    assert ei.value.code == B.DG_ENONFINITE
+    assert "non-finite" in str(ei.value)
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_diagnostics_parity(prec):

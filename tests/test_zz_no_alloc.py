@@ -1,8 +1,10 @@
 """dg_rhs_noalloc: the right-hand side for callers that cannot allocate device
 memory (their memory is held by their own pool, or cudaMalloc/cudaFree would
 synchronise a pipeline that must not stall).  Its working memory is a fixed
-device array inside the library; these tests call it through the C ABI and
-compare it with dg_rhs, which works on a context with caller-owned scratch.
+device array inside the library.  These tests call it through the C ABI and
+compare it with the FP64 oracle on the same inputs (whole mesh on small
+meshes, sampled cells at the largest mesh the array holds), on consecutive
+calls, and with dg_rhs on a context; both sides of the size limit are checked.
 
 The file name makes pytest collect it last; it also passes on its own in a
 fresh process."""
@@ -48,32 +50,66 @@ def noalloc_rhs(N, k, prec, u, ahat, dt, stream):
 
 
 @pytest.mark.gpu
-def test_noalloc_rhs_matches_dg_rhs_on_consecutive_calls():
+def test_noalloc_rhs_matches_the_oracle_on_consecutive_calls():
     stream = torch.cuda.Stream()
-    cases = [("f64", 5, 2, True), ("f32", 6, 3, False), ("x3", 6, 3, True), ("f64", 5, 2, False)]
+    cases = [("f64", 5, 2, True), ("f32", 6, 3, False), ("x3", 6, 3, True), ("f64", 5, 2, False), ("x3", 7, 1, True)]
     for i, (prec, N, k, forced) in enumerate(cases):
         u = I.random_state(N, k, seed=200 + i)
+        cfg = O.make_cfg(N, k)
         a = None
         if forced:
             fo = O.Forcing(mach=2.0, zeta=0.5, seed=i)
-            a = O.forcing_project(O.make_cfg(N, k), fo.kvec(), fo.amplitudes())
+            a = O.forcing_project(cfg, fo.kvec(), fo.amplitudes())
         dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
-        got = noalloc_rhs(N, k, prec, u, a, dt, stream)
-        ref = Solver(N, k, precision=prec).rhs(u, a, dt).cpu().numpy()
-        assert np.isfinite(got).all()
-        err = rel_l2_fields(got, ref)
-        assert err.max() <= PREC[prec][2], (prec, err)
+        ref = O.rhs(cfg, u, a, dt)
+        for call in range(2):
+            got = noalloc_rhs(N, k, prec, u, a, dt, stream)
+            assert np.isfinite(got).all()
+            err = rel_l2_fields(got, ref)
+            assert err.max() <= PREC[prec][2], (prec, call, err)
+        # and the context path (Rusanov faces) on the same inputs
+        ctx = Solver(N, k, precision=prec).rhs(u, a, dt).cpu().numpy()
+        assert rel_l2_fields(got, ctx).max() <= PREC[prec][2]
+
+
+# the array holds N^3 * 3 * b * element size bytes of projected velocity after a
+# fixed 1,180,160-byte head (control block, reduction partials, tables)
+LIMIT, HEAD = 64 << 20, 1180160
+
+
+@pytest.mark.gpu
+def test_noalloc_at_the_largest_mesh_it_holds():
+    # k = 3 in FP32: N = 65 fits (66.0 MB + head <= 64 MiB), N = 66 does not
+    N, k = 65, 3
+    assert N ** 3 * 3 * 20 * 4 + HEAD <= LIMIT < (N + 1) ** 3 * 3 * 20 * 4 + HEAD
+    stream = torch.cuda.Stream()
+    u = I.random_state(N, k, seed=7)
+    cfg = O.make_cfg(N, k)
+    fo = O.Forcing(mach=2.0, zeta=0.5, seed=3)
+    a = O.forcing_project(cfg, fo.kvec(), fo.amplitudes())
+    dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
+    got = noalloc_rhs(N, k, "f32", u, a, dt, stream)
+    assert np.isfinite(got).all()
+    # sampled cells against the oracle (including the first and last cells and a
+    # periodic corner), with the whole field's mean acceleration
+    rng = np.random.default_rng(0)
+    cells = np.unique(np.concatenate([[0, N - 1, N * N * N - 1, N * N * (N - 1)],
+                                      rng.integers(0, N ** 3, 300)]))
+    abar = O.forcing_mean(cfg, u, a)
+    ref = O.rhs_cells(cfg, u, cells, a, abar, dt)
+    assert rel_l2_fields(got[cells], ref).max() <= PREC["f32"][2]
 
 
 @pytest.mark.gpu
 def test_noalloc_rejects_meshes_beyond_the_fixed_array():
     L = B.lib()
-    mesh = B.Mesh((C.c_int32 * 3)(128, 128, 128), (C.c_double * 3)(1.0, 1.0, 1.0))
     nu = B.NuParams(B.AV_VNR, 2.0, 0.2, 1e-3, 0.0)
     s = torch.cuda.Stream()
-    # 128^3 cells x 60 floats of projected velocity = 503 MB > 64 MiB: refused
-    # before any device work, so the buffers are never touched
     small = torch.zeros(16, device="cuda")
-    rc = L.dg_rhs_noalloc(C.byref(mesh), 3, 1.0, C.byref(nu), B.PREC_F32, small.data_ptr(), None, small.data_ptr(),
-                          0.0, s.cuda_stream)
-    assert rc == B.DG_ENOMEM
+    # refused before any device work, so the (too small) buffers are never touched
+    for N, k, prec in [(66, 3, B.PREC_F32), (128, 3, B.PREC_F32), (52, 3, B.PREC_F64)]:
+        assert N ** 3 * 3 * 20 * (8 if prec == B.PREC_F64 else 4) + HEAD > LIMIT
+        mesh = B.Mesh((C.c_int32 * 3)(N, N, N), (C.c_double * 3)(1.0, 1.0, 1.0))
+        rc = L.dg_rhs_noalloc(C.byref(mesh), k, 1.0, C.byref(nu), prec, small.data_ptr(), None,
+                              small.data_ptr(), 0.0, s.cuda_stream)
+        assert rc == B.DG_ENOMEM, (N, k, prec)
