@@ -68,6 +68,8 @@ extern "C" {
 #define DG_ST_LIMITED 1u   /* positivity rescaling happened in some cell         */
 #define DG_ST_FAIL 2u      /* a cell mean reached the density floor              */
 #define DG_ST_NONFINITE 4u /* a NaN/Inf was produced                              */
+#define DG_ST_TIMEOUT 8u   /* a tensor-core completion wait gave up (the launch
+                              stopped early; reported as DG_ECUDA)              */
 
 typedef struct {
     int32_t n[3];          /* cells per axis; this build requires n[0]=n[1]=n[2],
@@ -122,6 +124,16 @@ typedef struct {
     void* scratch;         /* >= dg_scratch_bytes(), 256-byte aligned              */
     size_t scratch_bytes;
     int32_t riemann;       /* DG_RIEMANN_*; 0 (Rusanov) when zero-initialised     */
+    int32_t x3_backend;    /* DG_PREC_X3 at order 3 without diffusion: 0 (default)
+                              = 5th-generation tensor-core kernels (tcgen05 with
+                              TMEM accumulators: volume, face and projection
+                              kernels per stage, the volume term through a
+                              caller-scratch buffer); 1 = the single fused stage
+                              kernel on warp-level mma.sync.  Other precisions,
+                              orders and the diffusion operator use the fused
+                              kernel either way; the learned sensor evaluated
+                              inside the stage (fused_infer = 1) takes the fused
+                              kernel for the last stage of each step           */
 } dg_opts;
 
 /* Driving (Sec. 4.2, eq. ornstein_uhlenbeck_process_time_evolution).  Modes:

@@ -33,7 +33,7 @@ class NuParams(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rk_stages", C.c_int32), ("cfl", C.c_double), ("stream", C.c_void_p),
                 ("u", C.c_void_p * 3), ("vhat", C.c_void_p), ("ahat", C.c_void_p), ("scratch", C.c_void_p),
-                ("scratch_bytes", C.c_size_t), ("riemann", C.c_int32)]
+                ("scratch_bytes", C.c_size_t), ("riemann", C.c_int32), ("x3_backend", C.c_int32)]
 
 
 class AdiOpts(C.Structure):

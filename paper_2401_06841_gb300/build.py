@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdg.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["dg_api.cu", "dg_f64.cu", "dg_f64_k3.cu", "dg_f32.cu", "dg_f32_k3.cu", "dg_noalloc.cu", "dg_mlp.cu",
-           "dg_analysis.cu", "dg_adi_f32.cu", "dg_adi_f64.cu"]
+           "dg_analysis.cu", "dg_adi_f32.cu", "dg_adi_f64.cu", "dg_tc5.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2"]

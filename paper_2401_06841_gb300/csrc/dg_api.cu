@@ -595,6 +595,10 @@ struct dg_ctx {
     float* nu_cell = nullptr;  // per-cell coefficient (learned mode)
     float* nu_next = nullptr;  // the next step's coefficient, written by the last stage (learned mode)
     void* vabs = nullptr;      // per-cell |v| projection (learned mode)
+    // x3 at order 3: tcgen05 kernels (volume, faces, projection)
+    bool tc5 = false;
+    void* t5tab = nullptr;
+    void* rvol = nullptr;
     int mlp_D = 0, mlp_P = 0;
     long adam_t = 0;
     bool weights_set = false;
@@ -625,6 +629,7 @@ struct ScratchLayout {
     size_t mw, mm, mv, mg, mpack, mloss, mwork;  // learned sensor: weights, Adam moments, grad, packed, loss, work
     size_t nu, nu2, vabs;                        // per-cell coefficients (this and the next step) and |v| projection (learned mode)
     size_t ana;                                  // turbulence statistics: 4 x DG_MAX_BINS doubles + 1
+    size_t t5tab, rvol;                          // order 3: tensor-core table block, FP32 volume term [c][4][b]
     size_t total;
 };
 
@@ -673,6 +678,12 @@ ScratchLayout scratch_layout(int K, int N, bool learned = false)
     s.vabs = off;
     const size_t b = (size_t)(K + 1) * (K + 2) * (K + 3) / 6;
     if (learned) off = align256(off + sizeof(double) * (size_t)ncell * b);
+    // order 3: the tables and the volume-term buffer of the tcgen05 x3 kernels
+    // (reserved for every precision: the size query does not take one)
+    s.t5tab = off;
+    if (K == 3) off = align256(off + tc5_table_bytes());
+    s.rvol = off;
+    if (K == 3) off = align256(off + sizeof(float) * (size_t)ncell * 4 * b);
     s.total = off;
     return s;
 }
@@ -775,8 +786,62 @@ void drop_carry(dg_ctx* c)
     if (c) c->carry = false;
 }
 
+// the x3 stage of order 3 on the tcgen05 kernels: a projection launch, or the
+// volume + face launches of a right-hand side / stage followed by the
+// projection of the stage's output (F_NEXTPROJ)
+cudaError_t tile_tc5(dg_ctx* c, const TileLaunch& t)
+{
+    Launch L = make_launch(c);
+    using TT = TileTab<3, BK_X3>;
+    T5Launch p{};
+    p.tab5 = c->t5tab;
+    p.rvol = c->rvol;
+    p.phiv = static_cast<const float*>(c->ttab) + TT::phiv;
+    p.phif = static_cast<const float*>(c->ttab) + TT::phif;
+    p.nu = t.nu;
+    p.ahat = t.ahat;
+    p.rk_a = t.rk_a;
+    p.rk_b = t.rk_b;
+    p.dt_pimax = t.dt_pimax;
+    if (t.mode == TM_PROJECT) {
+        Timed tm(c, KIND_PROJECT);
+        p.kind = T5_PROJECT;
+        p.u_in = t.u_in;
+        p.vh_out = t.vh_out;
+        p.vabs_out = t.vabs_out;
+        p.flags = t.flags;
+        p.abar_out = t.abar_out;
+        return launch_tc5(L, p);
+    }
+    {
+        Timed tm(c, KIND_RHS);
+        p.kind = (t.mode == TM_RHS) ? T5_RHS : T5_STAGE;
+        p.u_in = t.u_in;
+        p.u_n = t.u_n;
+        p.out = t.out;
+        p.vh_in = t.vh_in;
+        p.flags = t.flags & F_FORCE;
+        p.abar_in = t.abar_in;
+        cudaError_t e = launch_tc5(L, p);
+        if (e != cudaSuccess) return e;
+    }
+    if (t.mode != TM_RHS && (t.flags & F_NEXTPROJ)) {
+        Timed tm(c, KIND_PROJECT);
+        T5Launch q = p;
+        q.kind = T5_PROJECT;
+        q.u_in = t.out;
+        q.vh_out = t.vh_out;
+        q.vabs_out = t.vabs_out;
+        q.flags = t.flags & (F_FORCE | F_DT);
+        q.abar_out = t.abar_out;
+        return launch_tc5(L, q);
+    }
+    return cudaSuccess;
+}
+
 cudaError_t tile(dg_ctx* c, const TileLaunch& t)
 {
+    if (c->tc5 && t.nu_next == nullptr) return tile_tc5(c, t);
     Timed tm(c, t.mode == 0 ? KIND_PROJECT : KIND_RHS);
     Launch L = make_launch(c);
     return (c->prec == DG_PREC_F64) ? launch_tile<double>(L, t) : launch_tile<float>(L, t);
@@ -991,6 +1056,9 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->nu_cell = (float*)(ctx->scratch + sl.nu);
     ctx->nu_next = (float*)(ctx->scratch + sl.nu2);
     ctx->vabs = ctx->scratch + sl.vabs;
+    ctx->t5tab = ctx->scratch + sl.t5tab;
+    ctx->rvol = ctx->scratch + sl.rvol;
+    ctx->tc5 = ctx->prec == DG_PREC_X3 && order == 3 && nu->diffusion == 0.0 && opts->x3_backend == 0;
     ctx->mlp_D = 2 * ctx->b;
     ctx->mlp_P = mlp_params(ctx->mlp_D);
 
@@ -998,6 +1066,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = (ctx->prec == DG_PREC_F64) ? setup_kernels<double>(order) : setup_kernels<float>(order);
+    if (e == cudaSuccess && ctx->tc5) e = tc5_setup();
     if (e != cudaSuccess) {
         fprintf(stderr, "dg_init: %s\n", cudaGetErrorString(e));
         delete ctx;
@@ -1022,6 +1091,12 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
             e = cudaMemcpyAsync(ctx->tab, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice, ctx->st);
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ttab, tt.data(), tt.size(), cudaMemcpyHostToDevice, ctx->st);
+        std::vector<unsigned char> t5;
+        if (e == cudaSuccess && ctx->tc5) {
+            t5.resize(tc5_table_bytes());
+            if (tc5_build_tables(ctx->r1.x, ctx->r1.w, t5.data(), t5.size()) != 0) e = cudaErrorInvalidValue;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->t5tab, t5.data(), t5.size(), cudaMemcpyHostToDevice, ctx->st);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ahat, 0, vec_bytes(ctx), ctx->st);
@@ -1096,7 +1171,10 @@ int dg_rhs(dg_ctx* ctx, const void* u_in, const void* ahat, void* dudt, double d
     t.flags = ahat ? F_FORCE : 0;
     t.abar_in = 0;
     CK(tile(ctx, t));
+    unsigned int st = 0u;
+    CK(cudaMemcpyAsync(&st, &ctx->ctl->status, sizeof(st), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    if (st & DG_ST_TIMEOUT) return fail(ctx, DG_ECUDA, "dg_rhs: a tensor-core completion wait timed out");
     return DG_OK;
 }
 
@@ -1270,6 +1348,7 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
         ctx->t += dt;
         ctx->dt_last = dt;
         ctx->steps += 1;
+        if (status & DG_ST_TIMEOUT) return fail(ctx, DG_ECUDA, "dg_step: a tensor-core completion wait timed out");
         if (status & DG_ST_NONFINITE) return fail(ctx, DG_ENONFINITE, "dg_step: non-finite coefficient");
     }
     if (t_out) *t_out = ctx->t;

@@ -58,6 +58,34 @@ cudaError_t launch_diag(const Launch& L, const T* u, const T* ahat, double dt_pi
 template <typename T>
 cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB);
 
+// x3 stage of degree 3 on the tcgen05 tensor cores (dg_tc5.cu): the
+// projection kernel, or the volume and face kernels of a right-hand side /
+// an SSP-RK stage
+enum { T5_PROJECT = 0, T5_RHS = 1, T5_STAGE = 2 };
+struct T5Launch {
+    int kind;
+    const void* u_in;
+    const void* u_n;
+    void* out;
+    const void* vh_in;
+    void* vh_out;
+    void* vabs_out;
+    const void* ahat;
+    const float* nu;
+    void* rvol;          // volume term [c][4][b] FP32 (caller's scratch)
+    const void* tab5;    // table block (tc5_build_tables)
+    const void* phiv;    // [b][nq] FP32 phi at the volume points
+    const void* phif;    // [b][nf] FP32 phi at the face points
+    double rk_a, rk_b;
+    double dt_pimax;
+    int flags;
+    int abar_in, abar_out;
+};
+size_t tc5_table_bytes();
+int tc5_build_tables(const double* x, const double* w, unsigned char* out, size_t cap);
+cudaError_t tc5_setup();
+cudaError_t launch_tc5(const Launch& L, const T5Launch& t);
+
 // adiabatic system (dg_adi.cu): mode 0 projection of v and p (+ CFL bound
 // with F_DT, forcing sums with F_FORCE), 1 right-hand side, 2 stage
 // (right-hand side, SSP-RK combine, positivity of density and pressure),

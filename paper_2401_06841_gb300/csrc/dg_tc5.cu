@@ -1,0 +1,203 @@
+// dg_tc5.cu -- host side of the degree-3 x3 tensor-core kernels: the table
+// block (basis values at the volume and face Gauss points, weighted basis
+// derivatives, quadrature weights) in the operand layouts of the products,
+// kernel set-up and launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <algorithm>
+#include <cstring>
+
+#include "dg_launch.cuh"
+#include "dg_tc5_kernels.cuh"
+
+namespace dg {
+
+namespace {
+
+int g_occ_vol = 0, g_occ_face = 0, g_occ_proj = 0;
+
+// scaled Legendre polynomial Pn_m = sqrt(2m+1) P_m and its derivative, by the
+// three-term recurrence and P'_{m+1} = P'_{m-1} + (2m+1) P_m
+void legendre(int m, double x, double& p, double& dp)
+{
+    double P[5] = {1.0, x, 0, 0, 0}, D[5] = {0.0, 1.0, 0, 0, 0};
+    for (int j = 1; j < m; ++j) {
+        P[j + 1] = ((2.0 * j + 1.0) * x * P[j] - j * P[j - 1]) / (j + 1.0);
+        D[j + 1] = D[j - 1] + (2.0 * j + 1.0) * P[j];
+    }
+    const double s = std::sqrt(2.0 * m + 1.0);
+    p = s * P[m];
+    dp = s * D[m];
+}
+
+uint16_t bf16_rne(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_to_float(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// hi and lo BF16 components of value v at byte offset o of two component planes
+void put(unsigned char* plane0, unsigned char* plane1, int o, double v)
+{
+    const float f = (float)v;
+    const uint16_t hi = bf16_rne(f);
+    const uint16_t lo = bf16_rne(f - bf16_to_float(hi));
+    std::memcpy(plane0 + o, &hi, 2);
+    std::memcpy(plane1 + o, &lo, 2);
+}
+
+}  // namespace
+
+size_t tc5_table_bytes() { return (size_t)C5::tab_bytes; }
+
+// x, w: the 4-point Gauss-Legendre rule on [-1, 1]
+int tc5_build_tables(const double* x, const double* w, unsigned char* out, size_t cap)
+{
+    if (cap < (size_t)C5::tab_bytes) return -1;
+    std::memset(out, 0, C5::tab_bytes);
+    constexpr int n = C5::n, b = C5::b;
+    constexpr Modes<3> M{};
+    double P[4][4], dP[4][4];  // [degree][point]
+    double Pe[4][2];           // [degree][end: -1, +1]
+    for (int m = 0; m <= 3; ++m) {
+        for (int a = 0; a < n; ++a) legendre(m, x[a], P[m][a], dP[m][a]);
+        double d;
+        legendre(m, -1.0, Pe[m][0], d);
+        legendre(m, 1.0, Pe[m][1], d);
+    }
+    float* wq = reinterpret_cast<float*>(out + C5::oWq);
+    float* ws = reinterpret_cast<float*>(out + C5::oWs);
+    // volume points q = ia + n ib + n^2 ic
+    for (int q = 0; q < C5::nq; ++q) {
+        const int ia = q % n, ib = (q / n) % n, ic = q / (n * n);
+        const double wv = w[ia] * w[ib] * w[ic];
+        wq[q] = (float)wv;
+        for (int l = 0; l < b; ++l) {
+            const int i = M.i[l], j = M.j[l], k = M.l[l];
+            const double phi = P[i][ia] * P[j][ib] * P[k][ic];
+            // Phi blocks [Z, Phi_hi, Z, Phi_lo, Z]: row q, K = l
+            const int o = tc5::koff(q, l, 128, 512);
+            put(out + C5::oPhi + 1 * C5::PHI_BLK, out + C5::oPhi + 3 * C5::PHI_BLK, o, phi);
+            // G_d: row l, K = q, w_q dphi_l / dxi_d
+            const double g[3] = {wv * dP[i][ia] * P[j][ib] * P[k][ic], wv * P[i][ia] * dP[j][ib] * P[k][ic],
+                                 wv * P[i][ia] * P[j][ib] * dP[k][ic]};
+            const int og = tc5::koff(l, q, 128, 1024);
+            for (int d = 0; d < 3; ++d)
+                put(out + C5::oG + (2 * d) * C5::G_BLK, out + C5::oG + (2 * d + 1) * C5::G_BLK, og, g[d]);
+        }
+    }
+    // face points (F, s): F = 2 d + side (side 1: xi_d = +1), s = a + n c along the
+    // tangential axes t1 < t2; table row 16 + 16 F + s
+    for (int F = 0; F < 6; ++F) {
+        const int d = F >> 1, side = F & 1, t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+        for (int s = 0; s < C5::ns; ++s) {
+            const int ia = s % n, ic = s / n;
+            if (F == 0) ws[s] = (float)(w[ia] * w[ic]);
+            for (int l = 0; l < b; ++l) {
+                const int deg[3] = {M.i[l], M.j[l], M.l[l]};
+                double phi = Pe[deg[d]][side];
+                phi *= P[deg[t1]][ia] * P[deg[t2]][ic];
+                const int o = tc5::koff(16 + 16 * F + s, l, 128, 512);
+                put(out + C5::oF, out + C5::oF + C5::F_BLK, o, phi);
+            }
+        }
+    }
+    return 0;
+}
+
+// blocks of a kernel an SM holds at once, from its registers, shared memory
+// and warps, and from the TMEM columns each block allocates for the whole
+// launch (the runtime's occupancy query counts one block per SM for kernels
+// that allocate tensor memory)
+static cudaError_t resident_blocks(const void* fn, int dyn_smem, int tmem_cols, int& out)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem))) return e;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)))
+        return e;
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, fn))) return e;
+    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, warps_sm = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&warps_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev))) return e;
+    const int regs = (fa.numRegs + 7) & ~7;
+    int n = smem_sm / (dyn_smem + (int)fa.sharedSizeBytes + resv);
+    n = std::min(n, regs_sm / (regs * C5::NT));
+    n = std::min(n, warps_sm / C5::NT);
+    n = std::min(n, 512 / tmem_cols);
+    out = n < 1 ? 1 : n;
+    return cudaSuccess;
+}
+
+cudaError_t tc5_setup()
+{
+    cudaError_t e;
+    if ((e = resident_blocks((const void*)k5_volume, C5::Vol::total, C5::TM_VOL, g_occ_vol))) return e;
+    if ((e = resident_blocks((const void*)k5_faces, C5::Face::total, C5::TM_FACE, g_occ_face))) return e;
+    return resident_blocks((const void*)k5_project, C5::Proj::total, C5::TM_PROJ, g_occ_proj);
+}
+
+static int grid5(long ntile, int occ, int nsm)
+{
+    long g = (long)(occ > 0 ? occ : 1) * nsm;
+    if (g > ntile) g = ntile;
+    if (g > kMaxGrid) g = kMaxGrid;
+    return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
+{
+    if (L.K != 3) return cudaErrorInvalidValue;
+    T5Args a{};
+    a.u_in = static_cast<const float*>(t.u_in);
+    a.u_n = static_cast<const float*>(t.u_n);
+    a.out = static_cast<float*>(t.out);
+    a.vh_in = static_cast<const float*>(t.vh_in);
+    a.vh_out = static_cast<float*>(t.vh_out);
+    a.vabs_out = static_cast<float*>(t.vabs_out);
+    a.ahat = static_cast<const float*>(t.ahat);
+    a.nu = t.nu;
+    a.rvol = static_cast<float*>(t.rvol);
+    a.tab = static_cast<const unsigned char*>(t.tab5);
+    a.phiv = static_cast<const float*>(t.phiv);
+    a.phif = static_cast<const float*>(t.phif);
+    a.ctl = L.ctl;
+    a.partials = L.partials;
+    a.ncell = L.ncell;
+    a.N = L.N;
+    a.ph = L.ph;
+    a.rk_a = (float)t.rk_a;
+    a.rk_b = (float)t.rk_b;
+    a.dt_pimax = t.dt_pimax;
+    a.flags = t.flags;
+    a.abar_in = t.abar_in;
+    a.abar_out = t.abar_out;
+    if ((t.flags & F_FORCE) && !t.ahat) return cudaErrorInvalidValue;
+    const long ntile = (L.ncell + C5::TC - 1) / C5::TC;
+    if (t.kind == T5_PROJECT) {
+        k5_project<<<grid5(ntile, g_occ_proj, L.nsm), C5::NT, C5::Proj::total, L.st>>>(a);
+        return cudaGetLastError();
+    }
+    a.stage = (t.kind == T5_STAGE) ? 1 : 0;
+    k5_volume<<<grid5(ntile, g_occ_vol, L.nsm), C5::NT, C5::Vol::total, L.st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k5_faces<<<grid5(ntile, g_occ_face, L.nsm), C5::NT, C5::Face::total, L.st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -24,7 +24,8 @@ class Solver:
     def __init__(self, N: int, k: int, cs: float = 1.0, precision: str = "f32", rk_stages: int | None = None,
                  cfl: float = 0.3, av: str = "vnr", alpha: float = 2.0, beta: float = 0.2, rho_floor: float = 1e-3,
                  nu_gate: float = 0.0, device: str | int = "cuda", stream: torch.cuda.Stream | None = None,
-                 riemann: str = "rusanov", diffusion: float = 0.0, fused_infer: bool = False):
+                 riemann: str = "rusanov", diffusion: float = 0.0, fused_infer: bool = False,
+                 x3_backend: str = "tcgen05"):
         self.L = B.lib()
         self.N, self.k, self.cs = N, k, cs
         self.b = nmodes(k)
@@ -54,7 +55,8 @@ class Solver:
         off = (-base) % 256
         opts = B.Opts(self.prec, rk_stages, cfl, C.c_void_p(self.stream.cuda_stream),
                       (C.c_void_p * 3)(*[r.data_ptr() for r in self.regs]), self.vhat.data_ptr(),
-                      self.ahat.data_ptr(), base + off, int(nb.value), B.RIEMANN[riemann])
+                      self.ahat.data_ptr(), base + off, int(nb.value), B.RIEMANN[riemann],
+                      {"tcgen05": 0, "mma": 1}[x3_backend])
         torch.cuda.synchronize(self.device)
         h = C.c_void_p(0)
         rc = self.L.dg_init(C.byref(h), C.byref(self.mesh), k, cs, C.byref(self.nu), C.byref(opts))
