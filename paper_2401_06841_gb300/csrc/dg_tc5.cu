@@ -15,7 +15,7 @@ namespace dg {
 
 namespace {
 
-int g_occ_vol = 0, g_occ_face = 0, g_occ_proj = 0;
+int g_occ_vol = 0, g_occ_face[3] = {0, 0, 0}, g_occ_proj = 0;
 
 // scaled Legendre polynomial Pn_m = sqrt(2m+1) P_m and its derivative, by the
 // three-term recurrence and P'_{m+1} = P'_{m-1} + (2m+1) P_m
@@ -147,7 +147,9 @@ cudaError_t tc5_setup()
 {
     cudaError_t e;
     if ((e = resident_blocks((const void*)k5_volume, C5::Vol::total, C5::TM_VOL, g_occ_vol))) return e;
-    if ((e = resident_blocks((const void*)k5_faces, C5::Face::total, C5::TM_FACE, g_occ_face))) return e;
+    if ((e = resident_blocks((const void*)k5_faces<0>, C5::Face::total, C5::TM_FACE, g_occ_face[0]))) return e;
+    if ((e = resident_blocks((const void*)k5_faces<1>, C5::Face::total, C5::TM_FACE, g_occ_face[1]))) return e;
+    if ((e = resident_blocks((const void*)k5_faces<2>, C5::Face::total, C5::TM_FACE, g_occ_face[2]))) return e;
     return resident_blocks((const void*)k5_project, C5::Proj::total, C5::TM_PROJ, g_occ_proj);
 }
 
@@ -196,7 +198,14 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
     k5_volume<<<grid5(ntile, g_occ_vol, L.nsm), C5::NT, C5::Vol::total, L.st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k5_faces<<<grid5(ntile, g_occ_face, L.nsm), C5::NT, C5::Face::total, L.st>>>(a);
+    const int rs = L.ph.riemann;
+    const int gf = grid5(ntile, g_occ_face[rs], L.nsm);
+    if (rs == 2)
+        k5_faces<2><<<gf, C5::NT, C5::Face::total, L.st>>>(a);
+    else if (rs == 1)
+        k5_faces<1><<<gf, C5::NT, C5::Face::total, L.st>>>(a);
+    else
+        k5_faces<0><<<gf, C5::NT, C5::Face::total, L.st>>>(a);
     return cudaGetLastError();
 }
 

@@ -457,6 +457,8 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
 // --------------------------------------------------------------------------
 // faces: traces, Riemann fluxes, lift; + rvol; stage combine and positivity
 // --------------------------------------------------------------------------
+// RS: the face flux (0 Rusanov, 1 HLL, 2 HLLC), one instantiation each
+template <int RS>
 __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
 {
     using Fc = C5::Face;
@@ -507,35 +509,53 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
         cp_async_commit();
         // ---- operands: rows 4 c + fld (rho, v_x, v_y, v_z) of each cell (self)
         // and of its neighbour across each face F ----
-        for (int e = tid; e < 7 * 64; e += C5::NT) {
-            const int F = e / 64 - 1, rr = e & 63, fld = rr >> 4, c = rr & 15;  // F = -1: self
-            float x[20];
-            const long cc = c0 + c;
-            if (c < nvalid) {
-                long src = cc;
-                if (F >= 0) {
+        {
+            // two rows per thread (448 rows), all ten 16-byte loads in flight before
+            // the conversion
+            const float* src[2];
+            bool valid[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = tid + u * C5::NT;
+                const int F = e / 64 - 1, rr = e & 63, fld = rr >> 4, c = rr & 15;  // F = -1: self
+                const long cc = c0 + c;
+                valid[u] = e < 7 * 64 && c < nvalid;
+                long sc = cc;
+                if (valid[u] && F >= 0) {
                     int xyz[3];
                     cell_xyz(cc, a.N, xyz[0], xyz[1], xyz[2]);
                     const int d = F >> 1, co = xyz[d];
                     const long stp = d == 0 ? 1L : (d == 1 ? (long)a.N : (long)a.N * a.N);
-                    src = (F & 1) ? (co == a.N - 1 ? cc - (long)(a.N - 1) * stp : cc + stp)
-                                  : (co == 0 ? cc + (long)(a.N - 1) * stp : cc - stp);
+                    sc = (F & 1) ? (co == a.N - 1 ? cc - (long)(a.N - 1) * stp : cc + stp)
+                                 : (co == 0 ? cc + (long)(a.N - 1) * stp : cc - stp);
                 }
-                const float* g = fld == 0 ? a.u_in + src * 80 : a.vh_in + src * 60 + (fld - 1) * 20;
-#pragma unroll
-                for (int j = 0; j < 5; ++j) {
-                    const float4 v = __ldg(reinterpret_cast<const float4*>(g) + j);
-                    x[4 * j] = v.x;
-                    x[4 * j + 1] = v.y;
-                    x[4 * j + 2] = v.z;
-                    x[4 * j + 3] = v.w;
-                }
-            } else {
-#pragma unroll
-                for (int l = 0; l < 20; ++l) x[l] = (fld == 0 && l == 0) ? 1.f : 0.f;
+                src[u] = fld == 0 ? a.u_in + sc * 80 : a.vh_in + sc * 60 + (fld - 1) * 20;
             }
-            unsigned char* base = F < 0 ? sSelf : sNbr + 2 * F * Fc::SB;
-            k5::put_row(base, Fc::SB, 4 * c + fld, x);
+            float4 raw[2][5];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    raw[u][j] = valid[u] ? __ldg(reinterpret_cast<const float4*>(src[u]) + j)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = tid + u * C5::NT;
+                if (e < 7 * 64) {
+                    const int F = e / 64 - 1, rr = e & 63, fld = rr >> 4, c = rr & 15;
+                    float x[20];
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) {
+                        x[4 * j] = raw[u][j].x;
+                        x[4 * j + 1] = raw[u][j].y;
+                        x[4 * j + 2] = raw[u][j].z;
+                        x[4 * j + 3] = raw[u][j].w;
+                    }
+                    if (!valid[u] && fld == 0) x[0] = 1.f;  // cells past the end: rho = 1, v = 0
+                    unsigned char* base = F < 0 ? sSelf : sNbr + 2 * F * Fc::SB;
+                    k5::put_row(base, Fc::SB, 4 * c + fld, x);
+                }
+            }
         }
         tc5::fence_async_smem();
         tc5::fence_before();
@@ -590,11 +610,11 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
                 const float* L = side ? S : Nb;
                 const float* Rr = side ? Nb : S;
                 if (qw == 0)
-                    riemann_flux<float, 0>(a.ph.riemann, cs, cs2, L, Rr, Fl);
+                    riemann_flux<float, 0>(RS, cs, cs2, L, Rr, Fl);
                 else if (qw == 1)
-                    riemann_flux<float, 1>(a.ph.riemann, cs, cs2, L, Rr, Fl);
+                    riemann_flux<float, 1>(RS, cs, cs2, L, Rr, Fl);
                 else
-                    riemann_flux<float, 2>(a.ph.riemann, cs, cs2, L, Rr, Fl);
+                    riemann_flux<float, 2>(RS, cs, cs2, L, Rr, Fl);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) x[4 * cc + v] = scale * Fl[v];
             }
