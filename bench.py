@@ -1,26 +1,37 @@
 """Throughput benchmark: DOF-updates per second per SSP-RK stage, mixed /
 learned variants vs plain FP32 at fixed L1 error.
 
-Workload: 64^3 cells, degree k=3 (20 modes x 4 fields = 20,971,520 DOF),
-SSP-RK3, isothermal cs=1, CFL 0.3, vNR artificial viscosity (alpha=2,
-beta=0.2), Rusanov faces, OU driving at Mach 3 (|k| in [1,3], zeta=0.5,
-seed 0).  The timed state is synthetic driven turbulence: a Gaussian random
-velocity field with E(k) ~ k^-2 at rms Mach 3 (seed 102, exact Legendre
-coefficients), rho = 1, relaxed by the method itself (plain FP32) for 30
-driven steps so that shocks and density contrasts form.
+Headline workload (the largest configuration, one GPU): 256^3 cells, degree
+k=3 (20 modes x 4 fields = 1,342,177,280 DOF), SSP-RK3, isothermal cs=1, CFL
+0.3, vNR artificial viscosity (alpha=2, beta=0.2), Rusanov faces, OU driving
+at Mach 3 (|k| in [1,3], zeta=0.5, seed 0) switched off after one eddy time
+T = L/(2 cs M).  The timed state is synthetic developed turbulence: a Gaussian
+random velocity field with E(k) ~ k^-2 at rms Mach 3 (seed 105, exact Legendre
+coefficients, built on the GPU), rho = 1, relaxed by the method itself (plain
+FP32, driven) so that shocks and density contrasts form, then taken as the
+state at t = T: the timed steps are the undriven decay.
 
-One step = the whole hot path: driving update when due, CFL dt, and per
-stage the velocity projection, the RHS with viscous pressure, Riemann fluxes
-and forcing, the stage combine and the positivity rescaling.  L2 is flushed
-(a 256 MB write) before every timed step, outside the timed interval.
+One step = the whole hot path: CFL dt, and per stage the RHS with viscous
+pressure, Riemann fluxes and the stage combine with positivity, and the
+velocity projection for the next stage.  L2 is flushed (a 256 MB write)
+before every timed step, outside the timed interval (the state, 5.4 GB, is
+larger than L2 as well).
 
-Variants: plain FP32, split-BF16 x3 tensor-core transforms ("x3"), and the
-learned viscosity sensor (network trained here, untimed: 20 epochs of Adam
-over the plain-sensor pairs of three relaxation snapshots).  Fixed L1: from the relaxed state each variant
-runs 20 undriven steps at a fixed dt; the reference is the plain FP32 scheme
-on the 2N^3 mesh from the exactly prolonged state (40 steps at dt/2),
-restricted back by L2 projection; a variant counts when its density L1 error
-is within 1.1x of plain FP32's.  `value` is the fastest counting variant.
+Variants: plain FP32, split-BF16 x3 tensor-core products ("x3": tcgen05
+kernels), and the learned viscosity sensor (learned-f32, learned-x3; network
+trained here, untimed, on plain-sensor pairs of separate driven runs at Mach 3
+and Mach 10, seeds 2 and 3, never the evaluation seeds).
+
+Fixed L1 (density, eq. l1_norm):
+  precision variants (x3): against an FP64 run of the same mesh from the same
+  state with the same dt sequence (recorded by the FP64 run and replayed), as
+  is plain FP32;
+  learned variants: on the learned-sensor configuration (128^3, k=3, Mach-6
+  driven state, seed 104), against the plain scheme on the 2N^3 mesh from the
+  exactly prolonged state (2n steps at dt/2), restricted back by L2
+  projection; plain FP32 at N against the same reference.
+A variant counts when its L1 is within 1.1x of plain FP32's; `value` is the
+fastest counting variant.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (a 16^3 sub-box at the same degree and scheme).
@@ -42,14 +53,16 @@ UNIT = "DOF-updates/s"
 
 
 def workload(args):
-    return {"workload": "driven isothermal turbulence, %d^3 cells, DG k=%d (P%d), SSP-RK3, Mach %g"
-                        % (args.N, args.k, args.k, args.mach),
+    T = 1.0 / (2.0 * args.mach)
+    return {"workload": "decaying isothermal turbulence after Mach-%g OU driving switched off at T, %d^3 cells, "
+                        "DG k=%d (P%d), SSP-RK3" % (args.mach, args.N, args.k, args.k),
             "N": args.N, "k": args.k, "dof": 4 * ((args.k + 1) * (args.k + 2) * (args.k + 3) // 6) * args.N ** 3,
             "rk_stages": 3, "mach": args.mach, "cs": 1.0, "cfl": 0.3, "av": "vNR alpha=2 beta=0.2",
             "riemann": {"rusanov": "Rusanov", "hll": "HLL", "hllc": "HLLC"}[args.riemann],
-            "forcing": "OU |k|<=3 zeta=0.5 seed 0", "diffusion": args.diffusion,
-            "state": "synthetic k^-2 velocity (seed 102) relaxed %d driven steps" % args.relax,
-            "l2": "flushed (256 MB write) before every timed step"}
+            "forcing": "OU |k|<=3 zeta=0.5 seed 0, off after T=%.4f" % T, "diffusion": args.diffusion,
+            "state": "synthetic k^-2 velocity (seed 105) relaxed %d driven FP32 steps, taken as the state at t=T"
+                     % args.relax,
+            "l2": "flushed (256 MB write) before every timed step; state larger than L2"}
 
 
 class Clocks:
@@ -107,25 +120,38 @@ def peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-def profiled_traffic(args, variant):
-    """DRAM bytes per launch of the stage kernel from the committed ncu summary
-    of this workload, or None when there is none or the kernel sources changed
-    since the capture (their SHA-1 is recorded next to the figure)."""
+# committed ncu summaries of the stage kernels, per variant: (file, kernel sources)
+PROFILE = {"x3": ("k5_stage_x3_64c_k3.md", ("dg_tc5_kernels.cuh", "dg_tc5.cuh", "dg_tc5.cu", "dg_common.cuh")),
+           "f32": ("k_tile_f32_stage_64c_k3.md", ("dg_tile.cuh", "dg_mma.cuh", "dg_common.cuh",
+                                                   "dg_launch_impl.cuh"))}
+
+
+def profiled_traffic(variant, N):
+    """DRAM bytes per stage from the committed ncu summary of the variant's stage
+    kernels (captured at 64^3, scaled by the cells), or None when there is none
+    or the kernel sources changed since the capture (their SHA-1 is recorded
+    next to the figure)."""
     import hashlib
     import re
-    f = os.path.join(ROOT, "profiles", "k_tile_%s_stage_%dc_k%d.md" % (variant, args.N, args.k))
+    key = variant.split("-")[-1]
+    if key not in PROFILE:
+        return None
+    name, srcs = PROFILE[key]
+    f = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(f):
         return None
     txt = open(f).read()
-    m_t = re.search(r"traffic_per_launch_bytes:\s*(\d+)", txt)
+    m_t = re.search(r"traffic_per_stage_bytes:\s*(\d+)", txt)
     m_h = re.search(r"kernel_sources_sha1:\s*([0-9a-f]{40})", txt)
     if not (m_t and m_h):
         return None
     h = hashlib.sha1()
-    for name in ("dg_tile.cuh", "dg_mma.cuh", "dg_common.cuh", "dg_launch_impl.cuh"):
+    for name in srcs:
         with open(os.path.join(ROOT, "paper_2401_06841_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
-    return int(m_t.group(1)) if h.hexdigest() == m_h.group(1) else None
+    if h.hexdigest() != m_h.group(1):
+        return None
+    return int(m_t.group(1)) * (N / 64) ** 3
 
 
 def adiabatic_arm(args, dev, seed, flush, world, near_isothermal=False):
@@ -141,7 +167,7 @@ def adiabatic_arm(args, dev, seed, flush, world, near_isothermal=False):
     import torch
     from paper_2401_06841_gb300 import AdiabaticSolver
     from paper_2401_06841_gb300 import inputs as I
-    N, k, S = args.N, args.k, 3
+    N, k, S = args.adi_N, args.k, 3
     b = (k + 1) * (k + 2) * (k + 3) // 6
     dof = 5 * b * N ** 3
     gamma = 1.0001 if near_isothermal else 1.4
@@ -292,19 +318,186 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def train_sensor(args, dev):
+    """The learned sensor's network, trained (untimed) on plain-sensor pairs of
+    separate driven runs: Mach 3 (seed 2) and Mach 10 (seed 3) at k=3, snapshots
+    every 10 steps, AV-active and inactive cells balanced 1:1."""
+    import torch
+    from paper_2401_06841_gb300 import Solver
+    from paper_2401_06841_gb300 import inputs as I
+    N, k = args.train_N, args.k
+    b = (k + 1) * (k + 2) * (k + 3) // 6
+    trainer = Solver(N, k, precision="f32", av="learned", device=dev, riemann=args.riemann)
+    trainer.set_av_weights(I.mlp_init(2 * b, seed=1))
+    xs, ys = [], []
+    for mach, seed in ((3.0, 2), (10.0, 3)):
+        run = Solver(N, k, precision="f32", rk_stages=3, device=dev, riemann=args.riemann)
+        run.set_state(I.turbulent_state_device(N, k, seed=seed, mach=mach, device=dev))
+        run.set_forcing(mach=mach, zeta=0.5, seed=seed)
+        for i in range(30):
+            _, dtl = run.step(1)
+            if i % 10 == 9:
+                trainer.set_state(run.get_state())
+                x, y = trainer.generate_pairs(dtl)
+                xs.append(x)
+                ys.append(y)
+        run.close()
+    X, Y = torch.cat(xs), torch.cat(ys)
+    g = torch.Generator(device=X.device).manual_seed(0)
+    floor = float(Y.min())
+    act = torch.nonzero(Y > floor + 1e-3).flatten()
+    ina = torch.nonzero(Y <= floor + 1e-3).flatten()
+    ina = ina[torch.randperm(len(ina), device=X.device, generator=g)[: max(len(act), 1)]]
+    sel = torch.cat([act, ina])
+    sel = sel[torch.randperm(len(sel), device=X.device, generator=g)]
+    t0 = time.perf_counter()
+    loss = trainer.mlp_train(X[sel], Y[sel], epochs=args.train_epochs, batch=4096, lr=2e-3)
+    info = {"pairs": int(len(sel)), "active": int(len(act)), "epochs": args.train_epochs, "batch": 4096,
+            "final_loss": loss, "seconds": time.perf_counter() - t0,
+            "runs": "k=%d %d^3 driven Mach 3 (seed 2) and Mach 10 (seed 3), snapshots every 10 steps" % (k, N)}
+    w = trainer.get_av_weights()
+    trainer.close()
+    return w, info
+
+
+def make_solver(v, N, k, args, dev, weights):
+    from paper_2401_06841_gb300 import Solver
+    prec = v.split("-")[-1]
+    s = Solver(N, k, precision=prec, rk_stages=3, av="learned" if v.startswith("learned") else "vnr", device=dev,
+               riemann=args.riemann, diffusion=args.diffusion, fused_infer="-fused-" in v)
+    if v.startswith("learned"):
+        s.set_av_weights(weights)
+    return s
+
+
+def time_variant(v, S0, meta0, args, dev, weights, flush, world):
+    import torch
+    N, k = args.N, args.k
+    b = (k + 1) * (k + 2) * (k + 3) // 6
+    dof = 4 * b * N ** 3
+    s = make_solver(v, N, k, args, dev, weights)
+    s.set_forcing(mach=args.mach, zeta=0.5, seed=0, t_off=1.0 / (2.0 * args.mach))
+    s.set_state(S0)
+    s.set_meta(meta0)
+    stream = s.stream
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+
+    for _ in range(args.warmup):
+        flush_l2()
+        s.step(1)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.profile(True)
+    for i in range(args.steps):
+        flush_l2()
+        starts[i].record(stream)
+        s.step(1)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    per_step = sorted(a.elapsed_time(e) for a, e in zip(starts, ends))
+    ms = max_over_ranks(sum(per_step) / args.steps, world, dev)
+    n_st = max(prof["n_rhs"], 1)
+    stage_ms = (prof["ms_rhs"] + prof["ms_project"]) / n_st
+    out = {"value": job_value(dof, 3, world, ms), "ms_per_step": ms, "step_ms_best": per_step[0],
+           "step_ms_median": per_step[len(per_step) // 2], "stage_ms": stage_ms,
+           "rhs_kernels_ms": prof["ms_rhs"] / n_st, "projection_ms": prof["ms_project"] / n_st,
+           "other_ms_per_step": (prof["ms_other"] + prof["ms_force"]) / args.steps,
+           "launches": int(prof["launches"]), "launches_per_step": prof["launches"] / args.steps}
+    return s, out
+
+
+def precision_gate(variants, S0, meta0, args, dev):
+    """L1 density error of the precision variants and of plain FP32 against an FP64
+    run of the same mesh from the same state, the FP64 run's dt sequence replayed."""
+    from paper_2401_06841_gb300 import Solver
+    N, k = args.N, args.k
+    T = 1.0 / (2.0 * args.mach)
+    ref = Solver(N, k, precision="f64", rk_stages=3, device=dev, riemann=args.riemann, diffusion=args.diffusion)
+    ref.set_forcing(mach=args.mach, zeta=0.5, seed=0, t_off=T)
+    ref.set_state(S0.double())
+    ref.set_meta(meta0)
+    dts = []
+    t0 = time.perf_counter()
+    for _ in range(args.l1_steps):
+        _, d = ref.step(1)
+        dts.append(d)
+    ref_s = time.perf_counter() - t0
+    R = ref.get_state()
+    out = {}
+    for v in ["f32"] + [v for v in variants if not v.startswith("learned") and v != "f32"]:
+        s = make_solver(v, N, k, args, dev, None)
+        s.set_forcing(mach=args.mach, zeta=0.5, seed=0, t_off=T)
+        s.set_state(S0)
+        s.set_meta(meta0)
+        for d in dts:
+            s.step(1, fixed_dt=d)
+        out[v] = ref.l1_density(s.get_state().double(), R)
+        s.close()
+    ref.close()
+    return out, {"reference": "FP64 GPU run, same mesh and state, dt sequence replayed", "steps": args.l1_steps,
+                 "dt": dts, "reference_seconds": ref_s}
+
+
+def learned_gate(variants, args, dev, weights):
+    """L1 density error of plain FP32 and the learned variants on the learned-sensor
+    configuration (N_l^3, k=3, Mach-6 driven state, seed 104) against the plain
+    FP32 scheme on the 2N_l^3 mesh from the exactly prolonged state."""
+    from paper_2401_06841_gb300 import Solver
+    from paper_2401_06841_gb300 import inputs as I
+    from paper_2401_06841_gb300 import transfer as Tr
+    N, k = args.l_N, args.k
+    base = Solver(N, k, precision="f32", rk_stages=3, device=dev, riemann=args.riemann)
+    base.set_state(I.turbulent_state_device(N, k, seed=104, mach=6.0, device=dev))
+    base.set_forcing(mach=6.0, zeta=0.5, seed=4)
+    base.step(args.l_relax)
+    S4 = base.get_state().clone()
+    dt = 0.8 * 0.3 * (1.0 / N) / ((k + 1) * base.diagnostics()["max_speed"])
+    base.close()
+    fine = Solver(2 * N, k, precision="f32", rk_stages=3, device=dev, riemann=args.riemann)
+    fine.set_state(Tr.prolong(S4, N, k))
+    fine.step(2 * args.l1_steps_learned, fixed_dt=dt / 2)
+    ref = Tr.restrict(fine.get_state(), N, k).contiguous()
+    fine.close()
+    out = {}
+    for v in ["f32"] + [v for v in variants if v.startswith("learned")]:
+        s = make_solver(v, N, k, args, dev, weights)
+        s.set_state(S4)
+        s.step(args.l1_steps_learned, fixed_dt=dt)
+        out[v] = s.l1_density(s.get_state(), ref)
+        s.close()
+    return out, {"reference": "plain FP32 on the 2N^3 mesh from the prolonged state (2n steps at dt/2), "
+                              "restricted by L2 projection", "mesh": N, "steps": args.l1_steps_learned,
+                 "state": "synthetic k^-2 velocity, Mach 6 (seed 104), %d driven steps" % args.l_relax}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--N", type=int, default=64)
+    ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--mach", type=float, default=3.0)
     ap.add_argument("--relax", type=int, default=30)
     ap.add_argument("--sample-N", dest="sample_N", type=int, default=16)
     ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=4)
-    ap.add_argument("--l1-steps", dest="l1_steps", type=int, default=20)
+    ap.add_argument("--l1-steps", dest="l1_steps", type=int, default=3,
+                    help="steps of the FP64 same-mesh reference (precision variants)")
+    ap.add_argument("--l-N", dest="l_N", type=int, default=128, help="mesh of the learned-sensor configuration")
+    ap.add_argument("--l-relax", dest="l_relax", type=int, default=20)
+    ap.add_argument("--l1-steps-learned", dest="l1_steps_learned", type=int, default=10)
+    ap.add_argument("--train-N", dest="train_N", type=int, default=64)
+    ap.add_argument("--adi-N", dest="adi_N", type=int, default=64)
     ap.add_argument("--variants", default="f32,x3,learned-f32,learned-x3",
                     help="comma list of f32, x3, learned-f32, learned-x3, learned-fused-f32, learned-fused-x3 "
                          "(fused: the sensor network evaluated in the last stage's kernel)")
@@ -331,148 +524,85 @@ def main():
     dev = "cuda:%d" % local
     from paper_2401_06841_gb300 import Solver
     from paper_2401_06841_gb300 import inputs as I
-    from paper_2401_06841_gb300 import transfer as Tr
 
     N, k = args.N, args.k
     b = (k + 1) * (k + 2) * (k + 3) // 6
     S = 3
     dof = 4 * b * N ** 3
-    # the relaxed driven state (independent replica per rank)
+    T = 1.0 / (2.0 * args.mach)
+    variants = [v for v in args.variants.split(",") if v]
+    # ---- the learned sensor: trained first, on runs of its own seeds (untimed) ----
+    weights, training = (None, None)
+    if any(v.startswith("learned") for v in variants):
+        weights, training = train_sensor(args, dev)
+    # ---- the timing state: synthetic turbulence relaxed by the driven method, then
+    # taken as the state at t = T (driving off from the first timed step on) ----
     base = Solver(N, k, precision="f32", rk_stages=S, device=dev, riemann=args.riemann, diffusion=args.diffusion)
-    base.set_state(I.turbulent_state(N, k, seed=state_seed, mach=args.mach))
-    base.set_forcing(mach=args.mach, zeta=0.5, seed=force_seed)
-    snaps = []
-    for i in range(args.relax):
-        _, dtl = base.step(1)
-        if i % 10 == 9:
-            snaps.append((base.get_state().clone(), dtl))
+    base.set_state(I.turbulent_state_device(N, k, seed=state_seed + 3, mach=args.mach, device=dev))
+    base.set_forcing(mach=args.mach, zeta=0.5, seed=force_seed, t_off=T)
+    base.step(args.relax)
     S0 = base.get_state().clone()
     meta0 = base.get_meta()
-
-    variants = [v for v in args.variants.split(",") if v]
-    weights = None
-    training = None
-    if any(v.startswith("learned") for v in variants):
-        # plain-sensor pairs of the relaxed snapshots -> trained weights (untimed)
-        trainer = Solver(N, k, precision="f32", av="learned", device=dev, riemann=args.riemann,
-                         diffusion=args.diffusion)
-        trainer.set_av_weights(I.mlp_init(2 * b, seed=1))
-        xs, ys = [], []
-        for u, dtl in snaps:
-            trainer.set_state(u)
-            x, y = trainer.generate_pairs(dtl)
-            xs.append(x)
-            ys.append(y)
-        X, Y = torch.cat(xs), torch.cat(ys)
-        perm = torch.randperm(len(Y), device=X.device, generator=torch.Generator(device=X.device).manual_seed(0))
-        t_train = time.perf_counter()
-        train_loss = trainer.mlp_train(X[perm], Y[perm], epochs=args.train_epochs, batch=4096, lr=2e-3)
-        t_train = time.perf_counter() - t_train
-        training = {"pairs": int(len(Y)), "epochs": args.train_epochs, "batch": 4096,
-                    "final_loss": train_loss, "seconds": t_train}
-        weights = trainer.get_av_weights()
-        trainer.close()
-        del X, Y, xs, ys
+    meta0.t = T * (1.0 + 1e-9)
+    diag0 = {k_: v for k_, v in base.diagnostics().items() if k_ in ("mach", "rho_min", "rho_max", "av_frac")}
+    base.close()
+    del base
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-
-    def make(v):
-        prec = v.split("-")[-1]
-        s = Solver(N, k, precision=prec, rk_stages=S, av="learned" if v.startswith("learned") else "vnr", device=dev,
-                   riemann=args.riemann, diffusion=args.diffusion, fused_infer="-fused-" in v)
-        if weights is not None and v.startswith("learned"):
-            s.set_av_weights(weights)
-        return s
-
     clocks = Clocks(local)
     res = {}
     clocks.start()
     time.sleep(0.2)
     for v in variants:
-        s = make(v)
-        s.set_forcing(mach=args.mach, zeta=0.5, seed=force_seed)
-        s.set_state(S0)
-        s.set_meta(meta0)
-        stream = s.stream
-
-        def flush_l2():
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-
-        for _ in range(args.warmup):
-            flush_l2()
-            s.step(1)
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        s.profile(True)
-        for i in range(args.steps):
-            flush_l2()
-            starts[i].record(stream)
-            s.step(1)
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-        prof = s.profile_read()
-        s.profile(False)
-        per_step = sorted(a.elapsed_time(e) for a, e in zip(starts, ends))
-        ms = sum(per_step) / args.steps
-        ms = max_over_ranks(ms, world, dev)
-        res[v] = {"value": job_value(dof, S, world, ms), "ms_per_step": ms, "prof": prof, "solver": s,
-                  "step_ms_best": per_step[0], "step_ms_median": per_step[len(per_step) // 2]}
+        s, res[v] = time_variant(v, S0, meta0, args, dev, weights, flush, world)
+        s.close()
     clk = clocks.stop()
 
-    # ---- fixed L1: undriven decay from the relaxed state, fixed dt ----
+    # ---- fixed L1 error ----
+    gates = {}
     if not args.no_l1:
-        dt0 = 0.3 * (1.0 / N) / ((k + 1) * base.diagnostics()["max_speed"])
-        dt = 0.8 * dt0
-        fine = Solver(2 * N, k, precision="f32", rk_stages=S, device=dev, riemann=args.riemann,
-                      diffusion=args.diffusion)
-        fine.set_state(Tr.prolong(S0, N, k))
-        fine.step(2 * args.l1_steps, fixed_dt=dt / 2)
-        ref = Tr.restrict(fine.get_state(), N, k).contiguous()
-        fine.close()
-        del fine
-        for v in variants:
-            s = res[v]["solver"]
-            s.set_forcing(mach=args.mach, on=False)
-            s.set_state(S0)
-            s.step(args.l1_steps, fixed_dt=dt)
-            res[v]["l1"] = s.l1_density(s.get_state(), ref)
-        l1_f32 = res["f32"]["l1"] if "f32" in res else None
-        for v in variants:
-            res[v]["at_fixed_l1"] = (l1_f32 is not None and res[v]["l1"] <= 1.1 * l1_f32)
+        l1p, ginfo = precision_gate(variants, S0, meta0, args, dev)
+        gates["precision"] = dict(ginfo, l1=l1p)
+        for v, l1 in l1p.items():
+            if v in res:
+                res[v]["l1_rho"] = l1
+                res[v]["at_fixed_l1"] = l1 <= 1.1 * l1p["f32"]
+        if any(v.startswith("learned") for v in variants):
+            l1l, linfo = learned_gate(variants, args, dev, weights)
+            gates["learned"] = dict(linfo, l1=l1l)
+            for v in variants:
+                if v.startswith("learned"):
+                    res[v]["l1_rho"] = l1l[v]
+                    res[v]["l1_rho_plain_f32"] = l1l["f32"]
+                    res[v]["at_fixed_l1"] = l1l[v] <= 1.1 * l1l["f32"]
     else:
         for v in variants:
-            res[v]["l1"] = None
+            res[v]["l1_rho"] = None
             res[v]["at_fixed_l1"] = v == "f32"
 
     counting = [v for v in variants if res[v]["at_fixed_l1"]]
     head = max(counting, key=lambda v: res[v]["value"]) if counting else variants[0]
-    hs = res[head]["solver"]
-    prof = res[head]["prof"]
-    # dominant kernel: RHS + stage update; algorithmic bytes per DOF per stage
-    # (SSP-RK3 average): u^(s) 1 word + u^n 2/3 word + u^(s+1) 1 word + a_h 3/4 word
-    esz = 4
-    n_stage = prof["n_rhs"]
-    rhs_ms = prof["ms_rhs"] / max(n_stage, 1)
-    bytes_per_launch = dof * esz * (1 + 2.0 / 3.0 + 1 + 0.75)
+    r = res[head]
+    # roofline of the stage (all its launches): algorithmic bytes per DOF and stage
+    # (SSP-RK3 average): u^(s) 1 word + u^n 2/3 word + u^(s+1) 1 word (undriven: no a_h)
+    bytes_per_stage = dof * 4 * (1 + 2.0 / 3.0 + 1)
     hbm, bf16, src = peaks()
-    achieved = bytes_per_launch / (rhs_ms * 1e-3) / 1e9
+    achieved = bytes_per_stage / (r["stage_ms"] * 1e-3) / 1e9
+    tr = profiled_traffic(head, N)
+    kern = ("k5_volume + k5_faces + k5_project (tcgen05)" if head.endswith("x3")
+            else "k_tile stage (RHS + SSP-RK stage + positivity + next projection)")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": profiled_traffic(args, head),
-            "kernel": "k_tile stage (RHS + SSP-RK stage + positivity + next projection), %s" % head,
-            "peak_source": src, "launches_timed": int(n_stage),
-            "kernel_ms": rhs_ms, "bytes_per_launch": bytes_per_launch}
+            "traffic": tr, "kernel": "%s, %s; one launch = one RK stage" % (kern, head), "peak_source": src,
+            "stage_ms": r["stage_ms"], "bytes_per_stage": bytes_per_stage}
 
-    # end to end through the C ABI with pinned host buffers: H2D state, one step, D2H state
-    hs.set_forcing(mach=args.mach, zeta=0.5, seed=force_seed)
-    hs.set_state(S0)
+    # ---- end to end through the C ABI with pinned host buffers: H2D state, one step, D2H state ----
+    hs = make_solver(head, N, k, args, dev, weights)
+    hs.set_forcing(mach=args.mach, zeta=0.5, seed=0, t_off=T)
     host_in = S0.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     e2e_ms = []
-    for _ in range(max(3, args.steps // 4)):
+    for i in range(max(3, args.steps // 5)):
+        hs.set_meta(meta0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hs.L.dg_set_state(hs.h, host_in.data_ptr(), 1)
@@ -482,40 +612,40 @@ def main():
     e2e_ms.sort()
     e2e_v = job_value(dof, S, world, max_over_ranks(e2e_ms[len(e2e_ms) // 2], world, dev))
     nbytes = host_in.numel() * host_in.element_size()
+    del host_in, host_out
 
-    line = {"metric": METRIC, "value": res[head]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": res[head]["ms_per_step"], "higher_is_better": True,
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"f32": "f32", "x3": "bf16x3+f32"}[head.split("-")[-1]], "data": "synthetic",
             "config": dict(workload(args), variant=head), "roofline": roof, "clocks": clk,
-            "gpu_launches": int(prof["launches"]),
+            "gpu_launches": int(r["launches"]),
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "variants": {v: {"value": res[v]["value"], "ms_per_step": res[v]["ms_per_step"],
-                             "step_ms_best": res[v]["step_ms_best"], "step_ms_median": res[v]["step_ms_median"],
-                             "l1_rho": res[v]["l1"],
-                             "at_fixed_l1": res[v]["at_fixed_l1"],
-                             "stage_kernel_ms": res[v]["prof"]["ms_rhs"] / max(res[v]["prof"]["n_rhs"], 1),
-                             "project_kernel_ms": res[v]["prof"]["ms_project"] / max(res[v]["prof"]["n_project"], 1),
-                             "other_ms_per_step": res[v]["prof"]["ms_other"] / args.steps}
+            "variants": {v: {k_: res[v].get(k_) for k_ in ("value", "ms_per_step", "step_ms_best", "step_ms_median",
+                                                           "stage_ms", "rhs_kernels_ms", "projection_ms",
+                                                           "other_ms_per_step", "launches_per_step", "l1_rho",
+                                                           "l1_rho_plain_f32", "at_fixed_l1")}
                          for v in variants},
-            "diag": {k_: v for k_, v in hs.diagnostics().items() if k_ in ("mach", "rho_min", "rho_max", "av_frac")}}
+            "fixed_l1": gates, "diag_start": diag0}
     if training is not None:
         line["learned_training"] = training
-    # turbulence statistics of the final state (paper's measurement settings):
-    # density PDF (200 bins), structure function (100 bins x 1e5 pairs),
-    # velocity power spectrum on the (k+1)N grid (2000 shells); wall ms per call
+    # turbulence statistics of the headline solver's state after one step:
+    # density PDF (200 bins), structure function (100 bins x 1e5 pairs); wall ms per call
+    hs.set_state(S0)
+    hs.set_meta(meta0)
+    hs.step(1)
     ana = {}
     for name, fn in (("density_pdf_ms", lambda: hs.density_pdf(-2.0, 2.0, 200)),
-                     ("structure_function_ms", lambda: hs.structure_function(100, 100000, 0)),
-                     ("power_spectrum_ms", lambda: hs.power_spectrum(2000))):
+                     ("structure_function_ms", lambda: hs.structure_function(100, 100000, 0))):
         fn()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = fn()
+        fn()
         ana[name] = 1e3 * (time.perf_counter() - t0)
-        if name == "power_spectrum_ms":
-            ana["spectrum_total_power"] = float(out[1].sum())
     line["analysis"] = ana
+    hs.close()
+    del hs, S0
+    torch.cuda.empty_cache()
     if not args.no_adiabatic:
         line["adiabatic"] = adiabatic_arm(args, dev, state_seed, flush, world)
         line["adiabatic_near_isothermal"] = adiabatic_arm(args, dev, state_seed, flush, world, near_isothermal=True)

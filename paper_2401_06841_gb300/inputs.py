@@ -201,6 +201,60 @@ def turbulent_velocity(N: int, k: int, seed: int, mach: float, zeta: float = 0.5
     return out
 
 
+def turbulent_state_device(N: int, k: int, seed: int, mach: float, zeta: float = 0.5, cs: float = 1.0,
+                           device="cuda", dtype=None, kmin: float = 2.0, kmax: float | None = None,
+                           slope: float = -2.0):
+    """``turbulent_state`` built with torch on ``device`` (the inverse FFTs run
+    there; meshes of 256^3 and more): the same random draws (numpy, same seed)
+    and the same recipe, returned as a torch tensor [N^3][4][b] of ``dtype``
+    (float32 by default)."""
+    import torch
+    dtype = torch.float32 if dtype is None else dtype
+    if kmax is None:
+        kmax = N / 4
+    rng = np.random.default_rng(seed)
+    kk = np.fft.fftfreq(N, d=1.0 / N)
+    KZ, KY, KX = np.meshgrid(kk, kk, kk, indexing="ij")
+    K = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
+    band = (K >= kmin) & (K <= kmax)
+    amp = np.zeros_like(K)
+    amp[band] = K[band] ** ((slope - 2.0) / 2.0)
+    del band
+    # the draws in the numpy recipe's order: real parts of all three components, then imaginary
+    re = rng.standard_normal((3,) + K.shape)
+    im = rng.standard_normal((3,) + K.shape)
+    A = torch.complex(torch.from_numpy(re), torch.from_numpy(im)).to(device) * torch.from_numpy(amp).to(device)
+    del re, im
+    Kd = torch.from_numpy(K).to(device)
+    Ks = torch.where(Kd > 0, Kd, torch.ones_like(Kd))
+    kx, ky, kz = (torch.from_numpy(x).to(device) for x in (KX, KY, KZ))
+    del KX, KY, KZ, K
+    kh = torch.stack([kx / Ks, ky / Ks, kz / Ks])
+    del kx, ky, kz, Ks
+    kdotA = (kh * A).sum(dim=0)
+    comp = kh * kdotA
+    A = zeta * (A - comp) + (1.0 - zeta) * comp
+    del kh, kdotA, comp
+    ijl = mode_degrees(k)
+    b = len(ijl)
+    h = 1.0 / N
+    m = np.arange(k + 1)
+    # per-axis factors sqrt(2m+1) i^m j_m(pi kappa h) and the half-cell shift exp(i pi kappa / N)
+    g1 = np.sqrt(2 * m + 1)[None, :] * (1j ** m)[None, :] * spherical_jn(m[None, :], np.pi * kk[:, None] * h)
+    g1 = g1 * np.exp(1j * np.pi * kk / N)[:, None]
+    g = torch.from_numpy(g1).to(device)
+    u = torch.zeros(N ** 3, 4, b, dtype=dtype, device=device)
+    u[:, 0, 0] = 1.0
+    for l, (i, j, lz) in enumerate(ijl):
+        G = g[:, lz][:, None, None] * g[:, j][None, :, None] * g[:, i][None, None, :]
+        for c in range(3):
+            f = torch.fft.ifftn(A[c] * G) * (N ** 3)
+            u[:, 1 + c, l] = f.real.reshape(-1).to(dtype)
+    rms = torch.sqrt((u[:, 1:, 0].double() ** 2).sum(dim=1).mean())
+    u[:, 1:, :] *= float(mach * cs / rms)
+    return u
+
+
 def turbulent_state(N: int, k: int, seed: int, mach: float, zeta: float = 0.5, cs: float = 1.0) -> np.ndarray:
     """rho = 1 and m = v from ``turbulent_velocity``: the start of a relaxation run."""
     v = turbulent_velocity(N, k, seed, mach, zeta, cs)

@@ -76,23 +76,25 @@ def test_reference_arm_prints_the_contract_line():
 
 
 def test_profiled_traffic_is_dropped_when_the_kernel_changes(tmp_path, monkeypatch):
-    # the stage kernel's DRAM bytes come from the committed ncu summary only
-    # while the kernel sources hash to the value recorded beside them
-    import argparse
+    # the stage's DRAM bytes come from the ncu summary only while the kernel
+    # sources hash to the value recorded beside them; captured at 64^3, scaled by
+    # the number of cells
+    import hashlib
     import shutil
-    prof = os.path.join("profiles", "k_tile_x3_stage_64c_k3.md")
+    name, srcs = bench.PROFILE["x3"]
     csrc = os.path.join("paper_2401_06841_gb300", "csrc")
     os.makedirs(tmp_path / "profiles")
     os.makedirs(tmp_path / csrc)
-    shutil.copy(os.path.join(ROOT, prof), tmp_path / prof)
-    for name in ("dg_tile.cuh", "dg_mma.cuh", "dg_common.cuh", "dg_launch_impl.cuh"):
-        shutil.copy(os.path.join(ROOT, csrc, name), tmp_path / csrc / name)
+    h = hashlib.sha1()
+    for src in srcs:
+        shutil.copy(os.path.join(ROOT, csrc, src), tmp_path / csrc / src)
+        h.update(open(os.path.join(ROOT, csrc, src), "rb").read())
+    with open(tmp_path / "profiles" / name, "w") as fh:
+        fh.write("traffic_per_stage_bytes: 300000000\nkernel_sources_sha1: %s\n" % h.hexdigest())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    args = argparse.Namespace(N=64, k=3)
-    got = bench.profiled_traffic(args, "x3")
-    assert isinstance(got, int) and got > 0
-    assert "traffic_per_launch_bytes: %d" % got in open(tmp_path / prof).read()
-    with open(tmp_path / csrc / "dg_tile.cuh", "a") as fh:
+    assert bench.profiled_traffic("x3", 64) == 300000000
+    assert bench.profiled_traffic("learned-x3", 128) == 8 * 300000000
+    assert bench.profiled_traffic("f32", 64) is None  # no summary for that kernel here
+    with open(tmp_path / csrc / srcs[0], "a") as fh:
         fh.write("\n")
-    assert bench.profiled_traffic(args, "x3") is None
-    assert bench.profiled_traffic(argparse.Namespace(N=32, k=3), "x3") is None  # no summary for that mesh
+    assert bench.profiled_traffic("x3", 64) is None

@@ -126,3 +126,13 @@ def test_random_energy_state_cell_mean_pressure():
     assert p.max() - p.min() > 0.5 * pm * sp  # spread over the band
     ref = I.random_state(6, 2, seed=8, v_rms=0.4)
     assert np.array_equal(u[:, :4], ref)  # rho and m as the isothermal recipe draws them
+
+
+def test_device_turbulent_state_equals_the_numpy_recipe():
+    # the torch build of the turbulent start state (used for the 256^3 benchmark)
+    # draws the same numbers and follows the same recipe as turbulent_state
+    torch = pytest.importorskip("torch")
+    for N, k, zeta in [(8, 3, 0.3), (12, 2, 1.0)]:
+        a = I.turbulent_state(N, k, seed=5, mach=2.0, zeta=zeta)
+        b = I.turbulent_state_device(N, k, seed=5, mach=2.0, zeta=zeta, device="cpu", dtype=torch.float64).numpy()
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
