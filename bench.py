@@ -227,27 +227,43 @@ def adiabatic_arm(args, dev, seed, flush, world, near_isothermal=False):
     return out
 
 
-def oracle_arm(args, steps, warmup):
-    """FP64 CPU oracle on a bounded sample: a 16^3 box at the workload's degree."""
+def cpu_model():
+    """The host CPU's model name (lscpu), or the platform's processor string."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_arm(args, steps, warmup, threads=0):
+    """FP64 CPU oracle on a bounded sample: a 16^3 box at the workload's degree,
+    the undriven decay of a synthetic turbulent state (as the timed GPU steps),
+    on `threads` host threads (0: all cores; OpenMP over cells, the interface
+    loop in parity colours)."""
     from oracle import oracle as O
     from paper_2401_06841_gb300 import inputs as I
+    used = O.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
     n = args.sample_N
     cfg = O.make_cfg(n, args.k, rk_stages=3, riemann=args.riemann, eps_diff=args.diffusion)
     u = I.turbulent_state(n, args.k, seed=102, mach=args.mach)
-    fo = O.Forcing(mach=args.mach, zeta=0.5, seed=0)
-    t, ahat = 0.0, None
+    t = 0.0
     for _ in range(warmup):
-        rc, t, _, ahat = O.run(cfg, u, 1, forcing=fo, t=t, ahat=ahat)
+        rc, t, _, _ = O.run(cfg, u, 1, t=t)
     t0 = time.perf_counter()
     for _ in range(steps):
-        rc, t, _, ahat = O.run(cfg, u, 1, forcing=fo, t=t, ahat=ahat)
+        rc, t, _, _ = O.run(cfg, u, 1, t=t)
         assert rc == 0
     wall = time.perf_counter() - t0
     dofs = 4 * O.nmodes(args.k) * n ** 3
     value = dofs * 3 * steps / wall
-    return value, wall, {"kind": "oracle", "cores": 1,
-                         "sample": "%d^3 cells at k=%d, SSP-RK3, driven, %d steps (single-threaded FP64 C)"
-                                   % (n, args.k, steps)}
+    return value, wall, {"kind": "oracle", "cores": used, "cpu": cpu_model(), "nproc": os.cpu_count(),
+                         "sample": "%d^3 cells at k=%d, SSP-RK3, undriven decay, %d steps (FP64 C, %d thread%s)"
+                                   % (n, args.k, steps, used, "" if used == 1 else "s")}
 
 
 def adiabatic_oracle_arm(args, near_isothermal, steps=2):
@@ -656,6 +672,8 @@ def main():
         v, wall, cb = oracle_arm(args, args.cpu_steps, 1)
         cb["value"] = v
         cb["unit"] = UNIT
+        v1, _, cb1 = oracle_arm(args, max(1, args.cpu_steps // 2), 1, threads=1)
+        cb["single_thread"] = dict(cb1, value=v1, unit=UNIT)
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line))

@@ -24,6 +24,10 @@
  */
 #include "dg_oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -337,6 +341,7 @@ double orc_dt(const orc_cfg* cfg, const double* u)
     tabs_init(&T, cfg->k, cfg->k + 1);
     int N = cfg->N, b = T.b, nc = N * N * N;
     double smax = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : smax)
     for (int c = 0; c < nc; ++c) {
         const double* uc = u + (size_t)c * 4 * b;
         for (int q = 0; q < T.nq; ++q) {
@@ -379,6 +384,7 @@ void orc_project_velocity(const orc_cfg* cfg, const double* u, double* vhat)
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
     int N = cfg->N, b = T.b, nc = N * N * N;
+#pragma omp parallel for schedule(static)
     for (int c = 0; c < nc; ++c) project_cell(&T, u + (size_t)c * 4 * b, vhat + (size_t)c * 3 * b);
     tabs_free(&T);
 }
@@ -398,16 +404,29 @@ static void forcing_mean_nv(const orc_cfg* cfg, const double* u, int nv, const d
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
     int N = cfg->N, b = T.b, nc = N * N * N;
-    double num[3] = {0, 0, 0}, den = 0.0;
-    for (int c = 0; c < nc; ++c) {
-        const double* uc = u + (size_t)c * nv * b;
-        const double* ac = ahat + (size_t)c * 3 * b;
-        for (int q = 0; q < T.nq; ++q) {
-            const double* ph = T.phi + q * b;
-            double rho = eval(&T, uc, ph);
-            den += 0.125 * T.wq[q] * rho;
-            for (int i = 0; i < 3; ++i) num[i] += 0.125 * T.wq[q] * rho * eval(&T, ac + i * b, ph);
+    /* sums over 64 fixed blocks of cells, added in block order: the same
+     * result for any number of threads */
+    enum { NBLK = 64 };
+    double part[NBLK][4];
+#pragma omp parallel for schedule(static)
+    for (int blk = 0; blk < NBLK; ++blk) {
+        double acc[4] = {0, 0, 0, 0};
+        for (int c = (int)((long)nc * blk / NBLK); c < (int)((long)nc * (blk + 1) / NBLK); ++c) {
+            const double* uc = u + (size_t)c * nv * b;
+            const double* ac = ahat + (size_t)c * 3 * b;
+            for (int q = 0; q < T.nq; ++q) {
+                const double* ph = T.phi + q * b;
+                double rho = eval(&T, uc, ph);
+                acc[3] += 0.125 * T.wq[q] * rho;
+                for (int i = 0; i < 3; ++i) acc[i] += 0.125 * T.wq[q] * rho * eval(&T, ac + i * b, ph);
+            }
         }
+        for (int i = 0; i < 4; ++i) part[blk][i] = acc[i];
+    }
+    double num[3] = {0, 0, 0}, den = 0.0;
+    for (int blk = 0; blk < NBLK; ++blk) {
+        for (int i = 0; i < 3; ++i) num[i] += part[blk][i];
+        den += part[blk][3];
     }
     for (int i = 0; i < 3; ++i) abar[i] = num[i] / den;
     tabs_free(&T);
@@ -528,31 +547,41 @@ static int rhs_impl(const orc_cfg* cfg, const double* u, const double* ahat, dou
     memset(dudt, 0, sizeof(double) * nc * 4 * b);
 
     /* volume integral and forcing source, cell by cell */
+#pragma omp parallel for schedule(static)
     for (size_t c = 0; c < nc; ++c)
         volume_cell(&T, cfg, u + c * 4 * b, ahat ? ahat + c * 3 * b : NULL, abar, nu_cell ? nu_cell[c] : -1.0,
                     dt_pimax, dudt + c * 4 * b);
 
-    /* surface integral: one pass over interfaces, each flux added to both cells */
-    for (int iz = 0; iz < N; ++iz)
-        for (int iy = 0; iy < N; ++iy)
-            for (int ix = 0; ix < N; ++ix) {
-                int cL = cell_index(N, ix, iy, iz);
-                for (int d = 0; d < 3; ++d) {
-                    int cR = cell_index(N, ix + (d == 0), iy + (d == 1), iz + (d == 2));
-                    const double* phL = T.phif + ((size_t)(d * 2 + 1) * ns) * b; /* xi_d = +1 in L */
-                    const double* phR = T.phif + ((size_t)(d * 2 + 0) * ns) * b; /* xi_d = -1 in R */
-                    for (int s = 0; s < ns; ++s) {
-                        double Fs[4];
-                        face_flux(&T, cfg, d, s, u + (size_t)cL * 4 * b, vhat + (size_t)cL * 3 * b,
-                                  u + (size_t)cR * 4 * b, vhat + (size_t)cR * 3 * b, Fs);
-                        for (int var = 0; var < 4; ++var)
-                            for (int l = 0; l < b; ++l) {
-                                dudt[((size_t)cL * 4 + var) * b + l] -= T.ws[s] * phL[s * b + l] * Fs[var] / (4.0 * h);
-                                dudt[((size_t)cR * 4 + var) * b + l] += T.ws[s] * phR[s * b + l] * Fs[var] / (4.0 * h);
-                            }
-                    }
+    /* surface integral: one pass over interfaces, each flux added to both cells.
+     * Per direction d the interfaces are taken in colours by the coordinate i
+     * of their lower cell along d (i even, i odd, and for odd N the wrap-around
+     * interface i = N - 1 alone), so that no two interfaces of a colour share a
+     * cell and the cells of a colour can be updated in parallel; the order of
+     * the updates of every cell is the same for any number of threads. */
+    for (int d = 0; d < 3; ++d) {
+        const double* phL = T.phif + ((size_t)(d * 2 + 1) * ns) * b; /* xi_d = +1 in L */
+        const double* phR = T.phif + ((size_t)(d * 2 + 0) * ns) * b; /* xi_d = -1 in R */
+        for (int colour = 0; colour < 3; ++colour) {
+#pragma omp parallel for schedule(static)
+            for (int cL = 0; cL < (int)nc; ++cL) {
+                const int ix = cL % N, iy = (cL / N) % N, iz = cL / (N * N);
+                const int i = d == 0 ? ix : (d == 1 ? iy : iz);
+                const int col = ((N & 1) && i == N - 1) ? 2 : (i & 1);
+                if (col != colour) continue;
+                int cR = cell_index(N, ix + (d == 0), iy + (d == 1), iz + (d == 2));
+                for (int s = 0; s < ns; ++s) {
+                    double Fs[4];
+                    face_flux(&T, cfg, d, s, u + (size_t)cL * 4 * b, vhat + (size_t)cL * 3 * b,
+                              u + (size_t)cR * 4 * b, vhat + (size_t)cR * 3 * b, Fs);
+                    for (int var = 0; var < 4; ++var)
+                        for (int l = 0; l < b; ++l) {
+                            dudt[((size_t)cL * 4 + var) * b + l] -= T.ws[s] * phL[s * b + l] * Fs[var] / (4.0 * h);
+                            dudt[((size_t)cR * 4 + var) * b + l] += T.ws[s] * phR[s * b + l] * Fs[var] / (4.0 * h);
+                        }
                 }
             }
+        }
+    }
     free(vhat);
     tabs_free(&T);
     orc_diffusion_rhs(cfg, u, dudt); /* + div(eps grad u) when eps > 0 */
@@ -619,6 +648,7 @@ int orc_limit(const orc_cfg* cfg, double* u)
     size_t nc = (size_t)N * N * N;
     double eps = cfg->rho_floor;
     int status = 0;
+#pragma omp parallel for schedule(static) reduction(| : status)
     for (size_t c = 0; c < nc; ++c) {
         double* uc = u + c * 4 * b;
         double rmin = INFINITY;
@@ -664,6 +694,7 @@ int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt)
     const double* B = (cfg->rk_stages == 2) ? b2 : b3;
     for (int s = 0; s < cfg->rk_stages; ++s) {
         orc_rhs(cfg, us, ahat, dt, L);
+#pragma omp parallel for schedule(static)
         for (size_t i = 0; i < n; ++i) us[i] = A[s] * un[i] + B[s] * (us[i] + dt * L[i]);
         status |= orc_limit(cfg, us);
     }
@@ -1800,4 +1831,16 @@ int orc_adi_run_driven(const orc_cfg* cfg, double gamma, double cs, double* u, o
     free(bak);
     free(amp);
     return rc;
+}
+
+/* number of threads of the parallel loops (OpenMP; 1 without it) */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

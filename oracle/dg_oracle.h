@@ -135,4 +135,9 @@ void orc_diagnostics(const orc_cfg* cfg, const double* u, const double* ahat,
 double orc_l1_density(const orc_cfg* cfg, const double* uA, const double* uB);
 
 uint64_t orc_splitmix64(uint64_t* state);
+/* threads of the parallel loops (OpenMP over cells; the interface loop in
+ * parity colours): n > 0 sets it; returns the number in use.  Results do not
+ * depend on it. */
+int orc_set_threads(int n);
+
 #endif

@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 def test_two_ranks_time_value_and_seeds():
     world, port = 2, 29500 + os.getpid() % 1000
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)

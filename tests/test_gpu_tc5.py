@@ -1,0 +1,146 @@
+"""Order-3 x3 products on both back ends: the 5th-generation tensor-core
+kernels (tcgen05, TMEM accumulators: volume, face and projection kernels per
+stage) and the fused warp-level kernel (mma.sync), each against the FP64 oracle
+on the same seeded inputs.
+
+Meshes: N = 1, 2, 3 (a cell is its own neighbour across periodic faces), 5
+and 7 (tiles of 16 cells with a ragged last tile), 17 (many tiles per block);
+every face flux; forced and unforced; the viscous pressure capped at part of
+the points.  Bounds: 5e-5 relative L2 per field for one right-hand side (the
+2^-16 error of the split products times the cancellation of random
+discontinuous states), 1e-4 after three steps."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = pytest.mark.skip(reason="no CUDA device")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2401_06841_gb300 import Solver  # noqa: E402
+from paper_2401_06841_gb300 import inputs as I  # noqa: E402
+
+BACKENDS = ["tcgen05", "mma"]
+K = 3
+
+
+def rel_l2_fields(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    return np.array([np.linalg.norm(got[:, v] - ref[:, v]) / max(np.linalg.norm(ref[:, v]), 1e-300)
+                     for v in range(ref.shape[1])])
+
+
+def ahat_for(N, seed=3, mach=2.0):
+    fo = O.Forcing(mach=mach, zeta=0.5, seed=seed)
+    return O.forcing_project(O.make_cfg(N, K), fo.kvec(), fo.amplitudes())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("backend", BACKENDS)
+@pytest.mark.parametrize("N,forced,av,riemann", [(1, False, "vnr", "rusanov"), (2, True, "vnr", "rusanov"),
+                                                 (3, True, "off", "hllc"), (5, True, "vnr", "hll"),
+                                                 (7, False, "vnr", "hllc"), (17, True, "vnr", "rusanov")])
+def test_rhs(backend, N, forced, av, riemann):
+    u = I.random_state(N, K, seed=300 + N)
+    cfg = O.make_cfg(N, K, av_mode={"off": 0, "vnr": 1}[av], riemann=riemann)
+    a = ahat_for(N) if forced else None
+    dt = 0.3 * (1 / N) / ((K + 1) * 6.0)
+    ref = O.rhs(cfg, u, a, dt)
+    s = Solver(N, K, precision="x3", av=av, riemann=riemann, x3_backend=backend)
+    got = s.rhs(u, a, dt).cpu().numpy()
+    s.close()
+    assert np.isfinite(got).all()
+    err = rel_l2_fields(got, ref)
+    assert err.max() < 5e-5, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("backend", BACKENDS)
+def test_projection(backend):
+    N = 7
+    u = I.random_state(N, K, seed=310)
+    s = Solver(N, K, precision="x3", x3_backend=backend)
+    got = s.project_velocity(u).cpu().numpy()
+    s.close()
+    err = rel_l2_fields(got, O.project_velocity(O.make_cfg(N, K), u))
+    assert err.max() < 5e-5, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("backend", BACKENDS)
+@pytest.mark.parametrize("rk", [2, 3])
+def test_driven_steps(backend, rk):
+    # every stage projects its output for the next one; the last stage's
+    # projection carries the CFL bound and the forcing sums into the next step
+    N = 6
+    u = I.random_state(N, K, seed=320 + rk, v_rms=0.8)
+    s = Solver(N, K, precision="x3", rk_stages=rk, x3_backend=backend)
+    s.set_state(u)
+    s.set_forcing(mach=3.0, zeta=0.5, seed=7)
+    t, _ = s.step(3)
+    got = s.get_state().cpu().numpy()
+    s.close()
+    ref = u.copy()
+    rc, tr, _, _ = O.run(O.make_cfg(N, K, rk_stages=rk), ref, 3, forcing=O.Forcing(mach=3.0, zeta=0.5, seed=7))
+    assert rc == 0 and t == pytest.approx(tr, rel=1e-6)
+    err = rel_l2_fields(got, ref)
+    assert err.max() < 1e-4, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("backend", BACKENDS)
+def test_limited_step(backend):
+    # densities below the floor in two cells: both sides rescale the same cells
+    N = 5
+    u = I.random_state(N, K, seed=330, rho_wiggle=0.5)
+    u[0, 0, 1] = 0.9 * u[0, 0, 0]
+    u[37, 0, 1] = -0.8 * u[37, 0, 0]
+    s = Solver(N, K, precision="x3", x3_backend=backend)
+    s.set_state(u)
+    s.step(1)
+    got = s.get_state().cpu().numpy()
+    status = s.diagnostics()["status"]
+    s.close()
+    ref = u.copy()
+    cfg = O.make_cfg(N, K)
+    assert O.step(cfg, ref, None, O.dt(cfg, ref)) & O.ORC_LIMITED
+    assert status & 1
+    err = rel_l2_fields(got, ref)
+    assert err.max() < 1e-4, err
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("backend", BACKENDS)
+def test_learned_rhs(backend):
+    # the per-cell coefficient of the learned sensor in the viscous pressure
+    N = 5
+    u = I.random_state(N, K, seed=340)
+    s = Solver(N, K, precision="x3", av="learned", x3_backend=backend)
+    s.set_av_weights(I.mlp_init(2 * O.nmodes(K), seed=5))
+    s.set_state(u)
+    nu = s.av_nu().cpu().numpy().astype(np.float64)
+    assert np.isfinite(nu).all() and (nu > 0).all()
+    dt = 0.3 * (1 / N) / ((K + 1) * 6.0)
+    got = s.rhs(u, None, dt).cpu().numpy()
+    s.close()
+    ref = O.rhs_nu(O.make_cfg(N, K), u, nu, None, dt)
+    err = rel_l2_fields(got, ref)
+    assert err.max() < 5e-5, err
+
+
+@pytest.mark.gpu
+def test_backends_agree_on_the_benchmark_mesh():
+    # 64^3 turbulence, two driven steps: the two back ends differ only by the
+    # rounding of their split products
+    N = 64
+    u = I.turbulent_state(N, K, seed=102, mach=3.0)
+    out = {}
+    for be in BACKENDS:
+        s = Solver(N, K, precision="x3", x3_backend=be)
+        s.set_state(u)
+        s.set_forcing(mach=3.0, zeta=0.5, seed=0)
+        s.step(2)
+        out[be] = s.get_state().double()
+        s.close()
+    d = ((out["tcgen05"] - out["mma"]).norm() / out["mma"].norm()).item()
+    assert d < 1e-5, d

@@ -538,3 +538,19 @@ def test_l1_density_norm():
     diff[:, 0, 5] = -0.05
     want = l1_vs_exact(diff, N, k, lambda X: 0.0 * X[..., 0], nq=k + 3)
     assert O.l1_density(cfg, c, a) == pytest.approx(want, rel=1e-12)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_oracle_is_independent_of_the_thread_count(N):
+    # the parallel loops (cells; interfaces in parity colours; fixed-block sums)
+    # give the same bits for any number of threads, odd meshes included
+    k = 2
+    out = []
+    for th in (1, 3):
+        O.set_threads(th)
+        u = I.random_state(N, k, seed=8, v_rms=0.6)
+        rc, t, _, _ = O.run(O.make_cfg(N, k), u, 2, forcing=O.Forcing(mach=2.0, zeta=0.5, seed=1))
+        assert rc == 0
+        out.append((u, t))
+    O.set_threads(os.cpu_count() or 1)
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
