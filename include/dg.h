@@ -130,10 +130,9 @@ typedef struct {
                               kernels per stage, the volume term through a
                               caller-scratch buffer); 1 = the single fused stage
                               kernel on warp-level mma.sync.  Other precisions,
-                              orders and the diffusion operator use the fused
-                              kernel either way; the learned sensor evaluated
-                              inside the stage (fused_infer = 1) takes the fused
-                              kernel for the last stage of each step           */
+                              orders, the diffusion operator and the learned
+                              sensor evaluated inside the stage (fused_infer = 1)
+                              use the fused kernel either way                  */
 } dg_opts;
 
 /* Driving (Sec. 4.2, eq. ornstein_uhlenbeck_process_time_evolution).  Modes:

@@ -841,7 +841,7 @@ cudaError_t tile_tc5(dg_ctx* c, const TileLaunch& t)
 
 cudaError_t tile(dg_ctx* c, const TileLaunch& t)
 {
-    if (c->tc5 && t.nu_next == nullptr) return tile_tc5(c, t);
+    if (c->tc5) return tile_tc5(c, t);
     Timed tm(c, t.mode == 0 ? KIND_PROJECT : KIND_RHS);
     Launch L = make_launch(c);
     return (c->prec == DG_PREC_F64) ? launch_tile<double>(L, t) : launch_tile<float>(L, t);
@@ -1058,7 +1058,10 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->vabs = ctx->scratch + sl.vabs;
     ctx->t5tab = ctx->scratch + sl.t5tab;
     ctx->rvol = ctx->scratch + sl.rvol;
-    ctx->tc5 = ctx->prec == DG_PREC_X3 && order == 3 && nu->diffusion == 0.0 && opts->x3_backend == 0;
+    // the in-stage sensor evaluation (fused_infer) lives in the fused kernel: such a
+    // context runs every launch there, so that carried and fresh coefficients agree
+    ctx->tc5 = ctx->prec == DG_PREC_X3 && order == 3 && nu->diffusion == 0.0 && opts->x3_backend == 0 &&
+               !(nu->mode == DG_AV_LEARNED && nu->fused_infer);
     ctx->mlp_D = 2 * ctx->b;
     ctx->mlp_P = mlp_params(ctx->mlp_D);
 

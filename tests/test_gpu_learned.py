@@ -232,15 +232,16 @@ def test_carried_coefficient_matches_the_inference_kernel(N, k, prec, gated, fus
 def test_learned_steps_fused_and_separate_inference(prec, tol):
     # three learned steps in a row with the coefficient evaluated in the last
     # stage (fused_infer) equal, bit for bit, three steps with the separate
-    # inference launch; and both stay within rounding of three steps that
-    # each start from a freshly set state (projection and inference launched
-    # at the start of every step)
+    # inference launch on the same stage kernel (in x3 the in-stage evaluation
+    # lives in the fused mma.sync kernel); and both stay within rounding of
+    # three steps that each start from a freshly set state (projection and
+    # inference launched at the start of every step)
     N, k = 6, 3
     u = I.random_state(N, k, seed=77, v_rms=0.8)
     th = M.init_params(2 * I.nmodes(k), seed=11).astype(np.float32)
     runs = []
     for fused in (True, False):
-        a = Solver(N, k, precision=prec, av="learned", fused_infer=fused)
+        a = Solver(N, k, precision=prec, av="learned", fused_infer=fused, x3_backend="mma")
         a.set_av_weights(th)
         a.set_state(u)
         a.step(3)

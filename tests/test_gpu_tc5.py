@@ -82,7 +82,8 @@ def test_driven_steps(backend, rk):
     s.close()
     ref = u.copy()
     rc, tr, _, _ = O.run(O.make_cfg(N, K, rk_stages=rk), ref, 3, forcing=O.Forcing(mach=3.0, zeta=0.5, seed=7))
-    assert rc == 0 and t == pytest.approx(tr, rel=1e-6)
+    # dt follows the CFL bound of velocities evaluated with the split products
+    assert rc == 0 and t == pytest.approx(tr, rel=5e-5)
     err = rel_l2_fields(got, ref)
     assert err.max() < 1e-4, err
 
