@@ -247,7 +247,7 @@ def test_learned_steps_fused_and_separate_inference(prec, tol):
         a.step(3)
         runs.append(a.get_state().cpu().numpy().astype(np.float64))
     assert np.array_equal(runs[0], runs[1])
-    b = Solver(N, k, precision=prec, av="learned")
+    b = Solver(N, k, precision=prec, av="learned", x3_backend="mma")
     b.set_av_weights(th)
     b.set_state(u)
     for _ in range(3):
