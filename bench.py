@@ -380,7 +380,8 @@ def make_solver(v, N, k, args, dev, weights):
     from paper_2401_06841_gb300 import Solver
     prec = v.split("-")[-1]
     s = Solver(N, k, precision=prec, rk_stages=3, av="learned" if v.startswith("learned") else "vnr", device=dev,
-               riemann=args.riemann, diffusion=args.diffusion, fused_infer="-fused-" in v)
+               riemann=args.riemann, diffusion=args.diffusion, fused_infer="-fused-" in v,
+               x3_backend=args.x3_backend)
     if v.startswith("learned"):
         s.set_av_weights(weights)
     return s
@@ -522,6 +523,8 @@ def main():
     ap.add_argument("--riemann", default="rusanov", choices=["rusanov", "hll", "hllc"])
     ap.add_argument("--train-epochs", dest="train_epochs", type=int, default=20)
     ap.add_argument("--diffusion", type=float, default=0.0, help="eps of an added div(eps grad u)")
+    ap.add_argument("--x3-backend", dest="x3_backend", default="tcgen05", choices=["tcgen05", "mma"],
+                    help="order-3 x3 stage: the tcgen05 kernels or the fused mma.sync kernel")
     ap.add_argument("--no-adiabatic", dest="no_adiabatic", action="store_true",
                     help="skip the timing of the five-variable adiabatic system")
     args = ap.parse_args()
