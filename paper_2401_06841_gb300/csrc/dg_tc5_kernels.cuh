@@ -139,16 +139,19 @@ __device__ __forceinline__ void load_state(float* s, const float* g, long c0, in
     }
 }
 
-// asynchronous 16-byte copies of a tile with `per` floats per cell (cells
-// past nvalid get the filler: first element fill0, the rest 0; plain stores)
-__device__ __forceinline__ void fetch_tile(float* s, const float* g, long c0, int nvalid, int per, float fill0)
+// TMA bulk copy of the valid cells of a tile with `per` floats per cell,
+// issued by the calling thread on mbarrier `bar` (which must expect the bytes);
+// returns the bytes
+__device__ __forceinline__ uint32_t bulk_tile(float* s, const float* g, long c0, int nvalid, int per, uint64_t* bar)
 {
-    for (int e = 4 * threadIdx.x; e < C5::TC * per; e += 4 * blockDim.x) {
-        if (e / per < nvalid)
-            cp_async16(s + e, g + c0 * per + e);
-        else
-            *reinterpret_cast<float4*>(s + e) = make_float4((e % per) == 0 ? fill0 : 0.f, 0.f, 0.f, 0.f);
-    }
+    const uint32_t bytes = (uint32_t)(nvalid * per * 4);
+    tc5::bulk_g2s(s, g + c0 * per, bytes, bar);
+    return bytes;
+}
+// the filler of the cells past the end (plain stores of all threads)
+__device__ __forceinline__ void fill_tail(float* s, int nvalid, int per, float fill0)
+{
+    for (int e = nvalid * per + threadIdx.x; e < C5::TC * per; e += blockDim.x) s[e] = (e % per) == 0 ? fill0 : 0.f;
 }
 
 __device__ __forceinline__ int tile_cells(long ncell, long c0)
@@ -182,8 +185,23 @@ __device__ __forceinline__ void prod(int pr, int& ca, int& cb)
     cb = (pr == 1) ? 1 : 0;
 }
 
-// bounded wait for the block's product barrier, agreed over the block (a
+// bounded wait for phase `parity` of an mbarrier, agreed over the block (a
 // barrier): false when any thread gave up, which the status records
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, Ctl* ctl, int* s_abort)
+{
+    const bool ok = tc5::mbar_wait(bar, parity);
+    const bool any_failed = __syncthreads_or(!ok) != 0;
+    if (any_failed) {
+        if (threadIdx.x == 0) {
+            atomicOr(&ctl->status, DG_ST_TIMEOUT_);
+            *s_abort = 1;
+        }
+        return false;
+    }
+    return true;
+}
+
+// the same for the block's product barrier, whose phase it advances
 __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, Ctl* ctl, int* s_abort)
 {
     const bool ok = tc5::mbar_wait(bar, phase);
@@ -211,6 +229,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     constexpr int TC = C5::TC;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t lbar[2];  // tile copies into buffer 0 / 1
     __shared__ uint32_t tslot;
     __shared__ float s_nu[TC];
     __shared__ int s_abort;
@@ -224,6 +243,8 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     if (w == 0) tc5::tmem_alloc(&tslot, C5::TM_VOL);
     if (tid == 0) {
         tc5::mbar_init(&bar, 1);
+        tc5::mbar_init(&lbar[0], 1);
+        tc5::mbar_init(&lbar[1], 1);
         s_abort = 0;
     }
     tc5::fence_async_smem();
@@ -243,23 +264,33 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     const int qw = w & 3, hp = w >> 2, r = 32 * qw + lane, h = r >> 6, q = r & 63;
     const uint32_t tl = tc5::tmem_addr(tm, 32 * qw, 0);
     const long ntile = (a.ncell + TC - 1) / TC;
+    // TMA bulk copies of a tile's u (and a_h) into buffer buf, completing on lbar[buf];
+    // the cells past the end get the filler from plain stores of all threads
     auto fetch = [&](long t, int buf) {
         const long cb = t * TC;
         const int nv = k5::tile_cells(a.ncell, cb);
-        k5::fetch_tile(sUb + buf * TC * 80, a.u_in, cb, nv, 80, 1.f);
-        if (force) k5::fetch_tile(sAhb + buf * TC * 60, a.ahat, cb, nv, 60, 0.f);
-        cp_async_commit();
+        float* su = sUb + buf * TC * 80;
+        float* sa = sAhb + buf * TC * 60;
+        k5::fill_tail(su, nv, 80, 1.f);
+        if (force) k5::fill_tail(sa, nv, 60, 0.f);
+        if (tid == 0) {
+            tc5::fence_async_smem();
+            tc5::mbar_expect_tx(&lbar[buf], (uint32_t)(nv * 80 * 4 + (force ? nv * 60 * 4 : 0)));
+            k5::bulk_tile(su, a.u_in, cb, nv, 80, &lbar[buf]);
+            if (force) k5::bulk_tile(sa, a.ahat, cb, nv, 60, &lbar[buf]);
+        }
     };
     if (!force)
         for (int e = tid; e < 2 * TC * 60; e += C5::NT) sAhb[e] = 0.f;
     if (blockIdx.x < ntile) fetch(blockIdx.x, 0);
     int cur = 0;
+    uint32_t lph = 0;  // bit b: phase of lbar[b]
     for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x, cur ^= 1) {
         const long c0 = tile * TC;
         const int nvalid = k5::tile_cells(a.ncell, c0);
         if (tid < TC) s_nu[tid] = (a.ph.av_mode == 2 && tid < nvalid) ? a.nu[c0 + tid] : 0.f;
-        cp_async_wait_all();
-        __syncthreads();
+        if (!k5::wait_bar(&lbar[cur], (lph >> cur) & 1u, a.ctl, &s_abort)) break;
+        lph ^= 1u << cur;
         // the other buffer was consumed by the previous tile: fetch the next one into it
         if (tile + gridDim.x < ntile) fetch(tile + gridDim.x, cur ^ 1);
         const float* sU = sUb + cur * TC * 80;
@@ -465,6 +496,7 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
     constexpr int TC = C5::TC, b = C5::b, nq = C5::nq, nf = 96;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t ebar;  // the epilogue's inputs
     __shared__ uint32_t tslot;
     __shared__ int s_abort;
     __shared__ unsigned int s_status;
@@ -479,6 +511,7 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
     if (w == 0) tc5::tmem_alloc(&tslot, C5::TM_FACE);
     if (tid == 0) {
         tc5::mbar_init(&bar, 1);
+        tc5::mbar_init(&ebar, 1);
         s_abort = 0;
         s_status = 0u;
     }
@@ -499,14 +532,22 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
     const int qw = w & 3, hw = w >> 2;
     const uint32_t tl = tc5::tmem_addr(tm, 32 * qw, 0);
     const long ntile = (a.ncell + TC - 1) / TC;
+    const bool need_un = a.stage && a.rk_a != 0.f;
+    uint32_t eph = 0;
     for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const long c0 = tile * TC;
         const int nvalid = k5::tile_cells(a.ncell, c0);
-        // the epilogue's inputs arrive while the faces are computed
-        k5::fetch_tile(sEpi, a.u_in, c0, nvalid, 80, 1.f);
-        if (a.stage && a.rk_a != 0.f) k5::fetch_tile(sEpi + TC * 80, a.u_n, c0, nvalid, 80, 1.f);
-        k5::fetch_tile(sEpi + 2 * TC * 80, a.rvol, c0, nvalid, 80, 0.f);
-        cp_async_commit();
+        // the epilogue's inputs (TMA bulk copies) arrive while the faces are computed
+        k5::fill_tail(sEpi, nvalid, 80, 1.f);
+        if (need_un) k5::fill_tail(sEpi + TC * 80, nvalid, 80, 1.f);
+        k5::fill_tail(sEpi + 2 * TC * 80, nvalid, 80, 0.f);
+        if (tid == 0) {
+            tc5::fence_async_smem();
+            tc5::mbar_expect_tx(&ebar, (uint32_t)(nvalid * 80 * 4 * (need_un ? 3 : 2)));
+            k5::bulk_tile(sEpi, a.u_in, c0, nvalid, 80, &ebar);
+            if (need_un) k5::bulk_tile(sEpi + TC * 80, a.u_n, c0, nvalid, 80, &ebar);
+            k5::bulk_tile(sEpi + 2 * TC * 80, a.rvol, c0, nvalid, 80, &ebar);
+        }
         // ---- operands: rows 4 c + fld (rho, v_x, v_y, v_z) of each cell (self)
         // and of its neighbour across each face F ----
         {
@@ -648,8 +689,8 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
         }
         __syncwarp();
         if (!k5::wait_mma(&bar, phase, a.ctl, &s_abort)) break;
-        cp_async_wait_all();
-        __syncthreads();
+        if (!k5::wait_bar(&ebar, eph, a.ctl, &s_abort)) break;
+        eph ^= 1u;
         // ---- right-hand side = surface + rvol; stage combine (Sec. 7) ----
         if (w < 4) {
             float R[20];
@@ -769,6 +810,7 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
     constexpr int TC = C5::TC, NT = C5::NT;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t lbar[2];
     __shared__ uint32_t tslot;
     __shared__ int s_abort;
     __shared__ unsigned long long s_smax;
@@ -785,6 +827,8 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
     if (w == 0) tc5::tmem_alloc(&tslot, C5::TM_PROJ);
     if (tid == 0) {
         tc5::mbar_init(&bar, 1);
+        tc5::mbar_init(&lbar[0], 1);
+        tc5::mbar_init(&lbar[1], 1);
         s_abort = 0;
         s_smax = 0ull;
     }
@@ -803,17 +847,25 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
     auto fetch = [&](long t, int buf) {
         const long cb = t * TC;
         const int nv = k5::tile_cells(a.ncell, cb);
-        k5::fetch_tile(sUb + buf * TC * 80, a.u_in, cb, nv, 80, 1.f);
-        if (force) k5::fetch_tile(sAhb + buf * TC * 60, a.ahat, cb, nv, 60, 0.f);
-        cp_async_commit();
+        float* su = sUb + buf * TC * 80;
+        float* sa = sAhb + buf * TC * 60;
+        k5::fill_tail(su, nv, 80, 1.f);
+        if (force) k5::fill_tail(sa, nv, 60, 0.f);
+        if (tid == 0) {
+            tc5::fence_async_smem();
+            tc5::mbar_expect_tx(&lbar[buf], (uint32_t)(nv * 80 * 4 + (force ? nv * 60 * 4 : 0)));
+            k5::bulk_tile(su, a.u_in, cb, nv, 80, &lbar[buf]);
+            if (force) k5::bulk_tile(sa, a.ahat, cb, nv, 60, &lbar[buf]);
+        }
     };
     if (blockIdx.x < ntile) fetch(blockIdx.x, 0);
     int cur = 0;
+    uint32_t lph = 0;
     for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x, cur ^= 1) {
         const long c0 = tile * TC;
         const int nvalid = k5::tile_cells(a.ncell, c0);
-        cp_async_wait_all();
-        __syncthreads();
+        if (!k5::wait_bar(&lbar[cur], (lph >> cur) & 1u, a.ctl, &s_abort)) break;
+        lph ^= 1u << cur;
         if (tile + gridDim.x < ntile) fetch(tile + gridDim.x, cur ^ 1);
         const float* sU = sUb + cur * TC * 80;
         const float* sAh = sAhb + cur * TC * 60;
