@@ -62,7 +62,9 @@ def workload(args):
             "forcing": "OU |k|<=3 zeta=0.5 seed 0, off after T=%.4f" % T, "diffusion": args.diffusion,
             "state": "synthetic k^-2 velocity (seed 105) relaxed %d driven FP32 steps, taken as the state at t=T"
                      % args.relax,
-            "l2": "flushed (256 MB write) before every timed step; state larger than L2"}
+            "l2": "flushed (256 MB write) before every timed step; state larger than L2",
+            "learned_gate": "learned variants: nu/(cs h/p) < %g -> nu = 0 (tiles of 16 such cells skip div v)"
+                            % args.nu_gate}
 
 
 class Clocks:
@@ -379,9 +381,10 @@ def train_sensor(args, dev):
 def make_solver(v, N, k, args, dev, weights):
     from paper_2401_06841_gb300 import Solver
     prec = v.split("-")[-1]
-    s = Solver(N, k, precision=prec, rk_stages=3, av="learned" if v.startswith("learned") else "vnr", device=dev,
+    learned = v.startswith("learned")
+    s = Solver(N, k, precision=prec, rk_stages=3, av="learned" if learned else "vnr", device=dev,
                riemann=args.riemann, diffusion=args.diffusion, fused_infer="-fused-" in v,
-               x3_backend=args.x3_backend)
+               x3_backend=args.x3_backend, nu_gate=args.nu_gate if learned else 0.0)
     if v.startswith("learned"):
         s.set_av_weights(weights)
     return s
@@ -428,7 +431,8 @@ def time_variant(v, S0, meta0, args, dev, weights, flush, world):
            "step_ms_median": per_step[len(per_step) // 2], "stage_ms": stage_ms,
            "rhs_kernels_ms": prof["ms_rhs"] / n_st, "projection_ms": prof["ms_project"] / n_st,
            "other_ms_per_step": (prof["ms_other"] + prof["ms_force"]) / args.steps,
-           "launches": int(prof["launches"]), "launches_per_step": prof["launches"] / args.steps}
+           "launches": int(prof["launches"]), "launches_per_step": prof["launches"] / args.steps,
+           "gated_tile_frac": prof["tiles_gated"] / max(prof["tiles_volume"], 1)}
     return s, out
 
 
@@ -525,6 +529,9 @@ def main():
     ap.add_argument("--diffusion", type=float, default=0.0, help="eps of an added div(eps grad u)")
     ap.add_argument("--x3-backend", dest="x3_backend", default="tcgen05", choices=["tcgen05", "mma"],
                     help="order-3 x3 stage: the tcgen05 kernels or the fused mma.sync kernel")
+    ap.add_argument("--nu-gate", dest="nu_gate", type=float, default=1.0,
+                    help="learned variants: cells with nu/(cs h/p) below this get no viscous pressure, and "
+                         "tiles of 16 such cells skip div v")
     ap.add_argument("--no-adiabatic", dest="no_adiabatic", action="store_true",
                     help="skip the timing of the five-variable adiabatic system")
     args = ap.parse_args()
@@ -643,7 +650,7 @@ def main():
             "variants": {v: {k_: res[v].get(k_) for k_ in ("value", "ms_per_step", "step_ms_best", "step_ms_median",
                                                            "stage_ms", "rhs_kernels_ms", "projection_ms",
                                                            "other_ms_per_step", "launches_per_step", "l1_rho",
-                                                           "l1_rho_plain_f32", "at_fixed_l1")}
+                                                           "l1_rho_plain_f32", "at_fixed_l1", "gated_tile_frac")}
                          for v in variants},
             "fixed_l1": gates, "diag_start": diag0}
     if training is not None:

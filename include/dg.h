@@ -83,8 +83,9 @@ typedef struct {
  * nu_gate (>= 0): in DG_AV_LEARNED mode a cell whose predicted coefficient
  * nu/(cs h/p) is below nu_gate gets nu = 0, i.e. no viscous pressure at any of
  * its points (the sensor's "no shock here" decision); 0 disables the gate.
- * The tile kernels evaluate div v for every cell of a tile either way, so the
- * gate changes the result, not the work.
+ * A tile of 16 consecutive cells whose coefficients are all zero skips the
+ * gradient evaluation and div v at its points (the result is the same as
+ * with the work done: Pi = 0 there); dg_prof counts those tiles.
  * diffusion (>= 0): eps of div(eps grad u).  The interface gradient is the
  * normal derivative at the face of the polynomial recovered over the face's
  * two cells (degree 2K+1 in the normal direction from the K+1 normal
@@ -323,6 +324,11 @@ typedef struct {
     double ms_rhs;         /* RHS + stage update kernel (K_B)                     */
     double ms_force;       /* forcing projection                                  */
     double ms_other;       /* diagnostics, L1                                     */
+    /* volume-term tiles (16 consecutive cells each) the stage kernels ran since
+     * the last reset, and those among them that skipped div v and the viscous
+     * pressure because every cell's coefficient was zero (DG_AV_LEARNED with
+     * nu_gate, or DG_AV_OFF); counted whether or not profiling is on */
+    int64_t tiles_volume, tiles_gated;
 } dg_prof;
 int dg_profile(dg_ctx* ctx, int enable);          /* enable/disable; resets counts */
 int dg_profile_read(dg_ctx* ctx, dg_prof* out);   /* synchronises the stream       */

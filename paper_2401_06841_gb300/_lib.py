@@ -69,7 +69,8 @@ class TrainOpts(C.Structure):
 class Prof(C.Structure):
     _fields_ = [("launches", C.c_int64), ("n_project", C.c_int64), ("n_rhs", C.c_int64), ("n_force", C.c_int64),
                 ("n_other", C.c_int64), ("ms_project", C.c_double), ("ms_rhs", C.c_double),
-                ("ms_force", C.c_double), ("ms_other", C.c_double)]
+                ("ms_force", C.c_double), ("ms_other", C.c_double), ("tiles_volume", C.c_int64),
+                ("tiles_gated", C.c_int64)]
 
 
 _lib = None

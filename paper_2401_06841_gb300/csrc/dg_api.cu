@@ -1587,6 +1587,8 @@ int dg_profile(dg_ctx* ctx, int enable)
     ctx->pending.clear();
     ctx->counts = dg_prof{};
     ctx->prof = enable != 0;
+    CK(cudaMemsetAsync(&ctx->ctl->tiles_vol, 0, 2 * sizeof(unsigned long long), ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
     return DG_OK;
 }
 
@@ -1605,6 +1607,10 @@ int dg_profile_read(dg_ctx* ctx, dg_prof* out)
         ctx->pool.push_back(p.b);
     }
     ctx->pending.clear();
+    unsigned long long tiles[2] = {0ull, 0ull};
+    CK(cudaMemcpy(tiles, &ctx->ctl->tiles_vol, sizeof(tiles), cudaMemcpyDeviceToHost));
+    ctx->counts.tiles_volume = (int64_t)tiles[0];
+    ctx->counts.tiles_gated = (int64_t)tiles[1];
     *out = ctx->counts;
     return DG_OK;
 }

@@ -131,7 +131,7 @@ struct Ctl {
     double l1;               // L1 result
     double sn;               // max sum_d(|v_d|+cs) of the state the next step starts from
     double dt_diff;          // explicit diffusion limit cfl (h/(k+1))^2 / (2 eps), 0: none
-    double pad[2];
+    unsigned long long tiles_vol, tiles_gated;  // volume-term tiles, and those the learned gate spared div v
 };
 
 // kernel flags

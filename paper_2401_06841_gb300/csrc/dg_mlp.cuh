@@ -184,19 +184,40 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const T* __restrict__ u, cons
     constexpr int b = Dims<K>::b, D = 2 * b;
     using PK = MlpPack<D>;
     __shared__ uint32_t sP[PK::words];
+    __shared__ float sF[FROMSTATE ? 8 * 16 * D : 1];  // a warp's 16 feature rows (state input)
     for (int e = threadIdx.x; e < PK::words; e += blockDim.x) sP[e] = packed[e];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float inv_cs = 1.0f / cs;
     const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
     for (long base = ((long)blockIdx.x * (blockDim.x >> 5) + warp) * 16; base < n; base += nwarps * 16) {
-        auto feat = [&](int rl, int k) -> float {
+        float* sf = sF + (FROMSTATE ? warp * 16 * D : 0);
+        if constexpr (FROMSTATE) {
+            // the 16 rows: lane 2 rl + h loads row rl's rho coefficients (h = 0) or its
+            // |v| projection (h = 1), all b loads in flight
+            __syncwarp();
+            const int rl = lane >> 1, h = lane & 1;
             const long r = base + rl;
-            if (r >= n || k >= D) return 0.0f;
+            T x[b];
+#pragma unroll
+            for (int l = 0; l < b; ++l) x[l] = T(0);
+            if (r < n) {
+                const T* src = h == 0 ? u + r * 4 * b : vabs + r * b;
+#pragma unroll
+                for (int l = 0; l < b; ++l) x[l] = src[l];
+            }
+            float* dst = sf + rl * D + h * b;
+#pragma unroll
+            for (int l = 0; l < b; ++l)
+                dst[l] = r >= n ? 0.0f : (h == 0 ? (float)(x[l] / x[0]) : (float)x[l] * inv_cs);
+            __syncwarp();
+        }
+        auto feat = [&](int rl, int k) -> float {
             if constexpr (FROMSTATE) {
-                if (k < b) return (float)(u[r * 4 * b + k] / u[r * 4 * b]);
-                return (float)vabs[r * b + (k - b)] * inv_cs;
+                return k < D ? sf[rl * D + k] : 0.0f;
             } else {
+                const long r = base + rl;
+                if (r >= n || k >= D) return 0.0f;
                 return X[r * D + k];
             }
         };

@@ -27,6 +27,24 @@ constexpr int MLP_H = 64;
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
+// GELU of the BF16 inference paths, with erf from Abramowitz & Stegun 7.1.26
+// (Hastings' approximation: for x >= 0, erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 +
+// t a5)))) exp(-x^2), t = 1/(1 + p x), absolute error <= 1.5e-7), far below the
+// BF16 rounding (2^-9 relative) that the activation then takes:
+//   gelu(z) = z - z erfc(|z|/sqrt 2)/2  (z >= 0),   z erfc(|z|/sqrt 2)/2  (z < 0)
+__device__ __forceinline__ float gelu_infer(float z)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float q = fmaf(t, 1.061405429f, -1.453152027f);
+    q = fmaf(t, q, 1.421413741f);
+    q = fmaf(t, q, -0.284496736f);
+    q = fmaf(t, q, 0.254829592f);
+    q *= t * __expf(-x * x);
+    const float hz = 0.5f * z * q;
+    return z >= 0.f ? z - hz : hz;
+}
+
 // packed inference weights: B1 = W1^T [KD][64], B2 = W2^T [64][64], B3 = W3 as
 // [64][8] (column 0), each as fragments [K/16][N/8][32 lanes][2 words], then
 // b1, b2, b3 as floats
@@ -80,10 +98,10 @@ __device__ __forceinline__ void mlp_infer_warp(F&& feat, const uint32_t* packed,
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const int nt = 2 * j + s, c = nt * 8 + 2 * t;
-            h[s][0] = gelu_f(acc1[nt][0] + bias[c]);
-            h[s][1] = gelu_f(acc1[nt][1] + bias[c + 1]);
-            h[s][2] = gelu_f(acc1[nt][2] + bias[c]);
-            h[s][3] = gelu_f(acc1[nt][3] + bias[c + 1]);
+            h[s][0] = gelu_infer(acc1[nt][0] + bias[c]);
+            h[s][1] = gelu_infer(acc1[nt][1] + bias[c + 1]);
+            h[s][2] = gelu_infer(acc1[nt][2] + bias[c]);
+            h[s][3] = gelu_infer(acc1[nt][3] + bias[c + 1]);
         }
         A2[j][0] = pack_bf16x2(h[0][0], h[0][1]);
         A2[j][1] = pack_bf16x2(h[0][2], h[0][3]);
@@ -107,10 +125,10 @@ __device__ __forceinline__ void mlp_infer_warp(F&& feat, const uint32_t* packed,
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const int nt = 2 * j + s, c = MLP_H + nt * 8 + 2 * t;
-            h[s][0] = gelu_f(acc2[nt][0] + bias[c]);
-            h[s][1] = gelu_f(acc2[nt][1] + bias[c + 1]);
-            h[s][2] = gelu_f(acc2[nt][2] + bias[c]);
-            h[s][3] = gelu_f(acc2[nt][3] + bias[c + 1]);
+            h[s][0] = gelu_infer(acc2[nt][0] + bias[c]);
+            h[s][1] = gelu_infer(acc2[nt][1] + bias[c + 1]);
+            h[s][2] = gelu_infer(acc2[nt][2] + bias[c]);
+            h[s][3] = gelu_infer(acc2[nt][3] + bias[c + 1]);
         }
         A3[j][0] = pack_bf16x2(h[0][0], h[0][1]);
         A3[j][1] = pack_bf16x2(h[0][2], h[0][3]);

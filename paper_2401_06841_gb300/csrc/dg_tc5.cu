@@ -15,7 +15,7 @@ namespace dg {
 
 namespace {
 
-int g_occ_vol = 0, g_occ_face[3] = {0, 0, 0}, g_occ_proj = 0;
+int g_occ_vol[4] = {0, 0, 0, 0}, g_occ_face[3] = {0, 0, 0}, g_occ_proj = 0;
 
 // scaled Legendre polynomial Pn_m = sqrt(2m+1) P_m and its derivative, by the
 // three-term recurrence and P'_{m+1} = P'_{m-1} + (2m+1) P_m
@@ -146,7 +146,10 @@ static cudaError_t resident_blocks(const void* fn, int dyn_smem, int tmem_cols, 
 cudaError_t tc5_setup()
 {
     cudaError_t e;
-    if ((e = resident_blocks((const void*)k5_volume, C5::Vol::total, C5::TM_VOL, g_occ_vol))) return e;
+    if ((e = resident_blocks((const void*)k5_volume<false, false>, C5::Vol::total, C5::TM_VOL, g_occ_vol[0]))) return e;
+    if ((e = resident_blocks((const void*)k5_volume<false, true>, C5::Vol::total, C5::TM_VOL, g_occ_vol[1]))) return e;
+    if ((e = resident_blocks((const void*)k5_volume<true, false>, C5::Vol::total, C5::TM_VOL, g_occ_vol[2]))) return e;
+    if ((e = resident_blocks((const void*)k5_volume<true, true>, C5::Vol::total, C5::TM_VOL, g_occ_vol[3]))) return e;
     if ((e = resident_blocks((const void*)k5_faces<0>, C5::Face::total, C5::TM_FACE, g_occ_face[0]))) return e;
     if ((e = resident_blocks((const void*)k5_faces<1>, C5::Face::total, C5::TM_FACE, g_occ_face[1]))) return e;
     if ((e = resident_blocks((const void*)k5_faces<2>, C5::Face::total, C5::TM_FACE, g_occ_face[2]))) return e;
@@ -195,7 +198,14 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
         return cudaGetLastError();
     }
     a.stage = (t.kind == T5_STAGE) ? 1 : 0;
-    k5_volume<<<grid5(ntile, g_occ_vol, L.nsm), C5::NT, C5::Vol::total, L.st>>>(a);
+    const int vv = ((t.flags & F_FORCE) ? 2 : 0) + (L.ph.av_mode != 1 ? 1 : 0);
+    const int gv = grid5(ntile, g_occ_vol[vv], L.nsm);
+    switch (vv) {
+    case 0: k5_volume<false, false><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
+    case 1: k5_volume<false, true><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
+    case 2: k5_volume<true, false><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
+    default: k5_volume<true, true><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int rs = L.ph.riemann;

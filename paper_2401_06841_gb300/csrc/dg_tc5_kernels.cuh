@@ -71,6 +71,12 @@ struct C5 {
         static constexpr int oNew = oNbr + 12 * SB;
         static constexpr int oEpi = oNew + TC * 80 * 4;    // u^(s), u^n, rvol of the tile, fetched asynchronously
         static constexpr int total = oEpi + 3 * TC * 80 * 4;
+        // the next tile's rows (self and six neighbours: rho 20, v 60 floats per
+        // cell) land by asynchronous copies in the self and neighbour operand
+        // region once its products are done; entries 84 floats apart (bank spread)
+        static constexpr int RAWS = 84;
+        static_assert(7 * TC * RAWS * 4 <= 14 * SB, "staging fits the operand region");
+        static_assert(oSelf % 16 == 0 && (RAWS * 4) % 16 == 0, "16-byte copies");
     };
     struct Proj {  // Phi + w_q, the tile, evaluation B, projection A
         static constexpr int oPhi = 0, oWq = szPhi, oU = oWq + 256, oAh = oU + 2 * TC * 80 * 4;  // u, a_h: double
@@ -223,6 +229,10 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, Ctl* ct
 // --------------------------------------------------------------------------
 // volume term + driving source -> rvol
 // --------------------------------------------------------------------------
+// FORCE: the driving source is added (a_h rows, source slot); GATE: the
+// coefficients may vanish on whole tiles (learned sensor, or no viscosity), so
+// that div v is evaluated only where a cell of the tile needs it
+template <bool FORCE, bool GATE>
 __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
 {
     using V = C5::Vol;
@@ -253,7 +263,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     tc5::fence_after();
     const uint32_t tm = tslot;
     uint32_t phase = 0;
-    const bool force = (a.flags & F_FORCE) != 0;
+    constexpr bool force = FORCE;
     const double dtd = k5::step_dt(a);
     const AvCoef<float> avc = av_coef<float>(a.ph, dtd);
     const float two_h = (float)(2.0 / a.ph.h), i4h = (float)(0.25 / a.ph.h), cs2 = (float)a.ph.cs2;
@@ -280,74 +290,99 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
             if (force) k5::bulk_tile(sa, a.ahat, cb, nv, 60, &lbar[buf]);
         }
     };
-    if (!force)
-        for (int e = tid; e < 2 * TC * 60; e += C5::NT) sAhb[e] = 0.f;
     if (blockIdx.x < ntile) fetch(blockIdx.x, 0);
     int cur = 0;
-    uint32_t lph = 0;  // bit b: phase of lbar[b]
+    uint32_t lph = 0;                                   // bit b: phase of lbar[b]
+    uint32_t inflight = blockIdx.x < ntile ? 1u : 0u;   // bit b: copies into buffer b not waited for
+    uint32_t ntiles = 0, gated = 0;                     // tiles done, and those without div v
     for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x, cur ^= 1) {
         const long c0 = tile * TC;
         const int nvalid = k5::tile_cells(a.ncell, c0);
         if (tid < TC) s_nu[tid] = (a.ph.av_mode == 2 && tid < nvalid) ? a.nu[c0 + tid] : 0.f;
         if (!k5::wait_bar(&lbar[cur], (lph >> cur) & 1u, a.ctl, &s_abort)) break;
         lph ^= 1u << cur;
+        inflight &= ~(1u << cur);
         // the other buffer was consumed by the previous tile: fetch the next one into it
-        if (tile + gridDim.x < ntile) fetch(tile + gridDim.x, cur ^ 1);
+        if (tile + gridDim.x < ntile) {
+            fetch(tile + gridDim.x, cur ^ 1);
+            inflight |= 1u << (cur ^ 1);
+        }
+        ++ntiles;
         const float* sU = sUb + cur * TC * 80;
         const float* sAh = sAhb + cur * TC * 60;
-        // ---- evaluation operand: rows (p, f) of cell 2p + h in half h; f: rho,
-        // m (3), D_d rho (3), sum_d D_d m_d, a_h (3), 0 (field-major threads) ----
+        // the divergence rows and the viscous pressure are needed unless every
+        // cell of the tile has a zero coefficient (learned sensor gated off, or
+        // no viscosity): a tile-uniform decision
+        bool need_div = !GATE;
+        if (GATE && a.ph.av_mode == 2)
+            for (int c = 0; c < TC; ++c) need_div |= s_nu[c] != 0.f;
+        gated += need_div ? 0u : 1u;
+        // ---- evaluation operand: three blocks of 32 rows 32 j + 4 p + f' for the
+        // pair p = (cells 2p, 2p+1; half h = cell parity): j = 0 rho, m (3);
+        // j = 1 D_d rho (3), sum_d D_d m_d (needed for div v only); j = 2 a_h (3),
+        // 0 (driven steps only).  Field-major threads f = 4 j + f' ----
         if (tid < TC * 12) {
-            const int f = tid >> 4, c = tid & 15;
-            const float* u = sU + c * 80;
-            float x[20];
-            if (f < 4) {
+            const int f = tid >> 4, c = tid & 15, j = f >> 2;
+            if (j == 0 || (j == 1 && need_div) || (j == 2 && force)) {
+                const float* u = sU + c * 80;
+                float x[20];
+                if (f < 4) {
 #pragma unroll
-                for (int l = 0; l < 20; ++l) x[l] = u[f * 20 + l];
-            } else if (f == 4) {
-                modal_grad<float, 3, 0>(u, x, 1.f);
-            } else if (f == 5) {
-                modal_grad<float, 3, 1>(u, x, 1.f);
-            } else if (f == 6) {
-                modal_grad<float, 3, 2>(u, x, 1.f);
-            } else if (f == 7) {
-                float t[20];
-                modal_grad<float, 3, 0>(u + 20, x, 1.f);
-                modal_grad<float, 3, 1>(u + 40, t, 1.f);
+                    for (int l = 0; l < 20; ++l) x[l] = u[f * 20 + l];
+                } else if (f == 4) {
+                    modal_grad<float, 3, 0>(u, x, 1.f);
+                } else if (f == 5) {
+                    modal_grad<float, 3, 1>(u, x, 1.f);
+                } else if (f == 6) {
+                    modal_grad<float, 3, 2>(u, x, 1.f);
+                } else if (f == 7) {
+                    float t[20];
+                    modal_grad<float, 3, 0>(u + 20, x, 1.f);
+                    modal_grad<float, 3, 1>(u + 40, t, 1.f);
 #pragma unroll
-                for (int l = 0; l < 20; ++l) x[l] += t[l];
-                modal_grad<float, 3, 2>(u + 60, t, 1.f);
+                    for (int l = 0; l < 20; ++l) x[l] += t[l];
+                    modal_grad<float, 3, 2>(u + 60, t, 1.f);
 #pragma unroll
-                for (int l = 0; l < 20; ++l) x[l] += t[l];
-            } else if (f < 11) {
+                    for (int l = 0; l < 20; ++l) x[l] += t[l];
+                } else if (f < 11) {
 #pragma unroll
-                for (int l = 0; l < 20; ++l) x[l] = sAh[c * 60 + (f - 8) * 20 + l];
-            } else {
+                    for (int l = 0; l < 20; ++l) x[l] = sAh[c * 60 + (f - 8) * 20 + l];
+                } else {
 #pragma unroll
-                for (int l = 0; l < 20; ++l) x[l] = 0.f;
+                    for (int l = 0; l < 20; ++l) x[l] = 0.f;
+                }
+                k5::put_row(sW + (c & 1) * 2 * V::EB, V::EB, 32 * j + 4 * (c >> 1) + (f & 3), x);
             }
-            k5::put_row(sW + (c & 1) * 2 * V::EB, V::EB, 12 * (c >> 1) + f, x);
         }
         tc5::fence_async_smem();
         tc5::fence_before();
         __syncthreads();
         if (tid == 0) {
             tc5::fence_after();
-            constexpr uint32_t ID = tc5::idesc_bf16(128, C5::NEV, 0, 0);
             const uint32_t sphi = tc5::saddr(sm + V::oPhi), seb = tc5::saddr(sW);
-            bool acc = false;
-            for (int hh = 0; hh < 2; ++hh)
-                for (int pr = 0; pr < 3; ++pr) {
-                    int ca, cb;
-                    k5::prod(pr, ca, cb);
-                    const uint32_t ab0 = sphi + (hh == 0 ? 1 + 2 * ca : 2 * ca) * C5::PHI_BLK;
-                    const uint32_t bb0 = seb + (hh * 2 + cb) * V::EB;
-                    for (int ks = 0; ks < 2; ++ks) {
-                        tc5::mma(tm, tc5::sdesc(ab0 + ks * 256, 128, 512), tc5::sdesc(bb0 + ks * 256, 128, 512), ID,
-                                 acc);
-                        acc = true;
+            // blocks j0 .. j0 + nj - 1 into TMEM columns 32 j0 ..
+            auto eval = [&](int j0, int nj) {
+                const uint32_t ID = tc5::idesc_bf16(128, 32 * nj, 0, 0);
+                bool acc = false;
+                for (int hh = 0; hh < 2; ++hh)
+                    for (int pr = 0; pr < 3; ++pr) {
+                        int ca, cb;
+                        k5::prod(pr, ca, cb);
+                        const uint32_t ab0 = sphi + (hh == 0 ? 1 + 2 * ca : 2 * ca) * C5::PHI_BLK;
+                        const uint32_t bb0 = seb + (hh * 2 + cb) * V::EB + j0 * 2048;
+                        for (int ks = 0; ks < 2; ++ks) {
+                            tc5::mma(tm + 32 * j0, tc5::sdesc(ab0 + ks * 256, 128, 512),
+                                     tc5::sdesc(bb0 + ks * 256, 128, 512), ID, acc);
+                            acc = true;
+                        }
                     }
-                }
+            };
+            if (need_div) {
+                eval(0, force ? 3 : 2);
+            } else {
+                eval(0, 1);
+                if (force) eval(2, 1);
+            }
             tc5::commit(&bar);
         }
         __syncwarp();
@@ -359,9 +394,10 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
 #pragma unroll
             for (int pp = 0; pp < 4; ++pp) {
                 const int p = 4 * hp + pp;
-                tc5::ld4(tl + 12 * p, ev[pp]);
-                tc5::ld4(tl + 12 * p + 4, ev[pp] + 4);
-                tc5::ld4(tl + 12 * p + 8, ev[pp] + 8);
+                // columns of blocks that were not evaluated are read too (and not used)
+                tc5::ld4(tl + 4 * p, ev[pp]);
+                tc5::ld4(tl + 32 + 4 * p, ev[pp] + 4);
+                tc5::ld4(tl + 64 + 4 * p, ev[pp] + 8);
             }
             tc5::ld_wait();
             const float wq8 = sWq[q] * 0.125f;
@@ -373,10 +409,12 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                 const float vx = v[1] * ir, vy = v[2] * ir, vz = v[3] * ir;
                 const float divv = (v[7] * two_h - (vx * v[4] + vy * v[5] + vz * v[6]) * two_h) * ir;
                 float Pi = 0.f;
-                if (a.ph.av_mode == 1)
-                    Pi = vnr_pressure<float>(avc, rho, divv);
-                else if (a.ph.av_mode == 2)
-                    Pi = nu_pressure<float>(avc, rho, divv, s_nu[c]);
+                if (need_div) {
+                    if (a.ph.av_mode == 1)
+                        Pi = vnr_pressure<float>(avc, rho, divv);
+                    else
+                        Pi = nu_pressure<float>(avc, rho, divv, s_nu[c]);
+                }
                 float* s = st[pp];
                 s[0] = rho;
                 s[1] = v[1];
@@ -386,9 +424,9 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                 s[5] = vy;
                 s[6] = vz;
                 s[7] = cs2 * rho + Pi;
-                s[8] = rho * (v[8] - ab[0]) * wq8;
-                s[9] = rho * (v[9] - ab[1]) * wq8;
-                s[10] = rho * (v[10] - ab[2]) * wq8;
+                s[8] = force ? rho * (v[8] - ab[0]) * wq8 : 0.f;
+                s[9] = force ? rho * (v[9] - ab[1]) * wq8 : 0.f;
+                s[10] = force ? rho * (v[10] - ab[2]) * wq8 : 0.f;
             }
         }
         tc5::fence_before();
@@ -399,6 +437,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
 #pragma unroll
             for (int sl = 0; sl < 2; ++sl) {
                 const int d = 2 * rnd + sl, k = 64 * sl + q;
+                if (d == 3 && !force) break;  // no source without driving
 #pragma unroll
                 for (int pp = 0; pp < 4; pp += 2) {
                     float x[8];
@@ -436,6 +475,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                 const uint32_t sw = tc5::saddr(sW), sg = tc5::saddr(sm + V::oG), sphi = tc5::saddr(sm + V::oPhi);
                 for (int sl = 0; sl < 2; ++sl) {
                     const int d = 2 * rnd + sl;
+                    if (d == 3 && !force) break;
                     for (int pr = 0; pr < 3; ++pr) {
                         int ca, cb;
                         k5::prod(pr, ca, cb);
@@ -479,6 +519,14 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
         __syncthreads();
         tc5::fence_after();
     }
+    // a loop left early: no bulk copy may still write into this block's shared memory
+    if (tid == 0)
+        for (int bb = 0; bb < 2; ++bb)
+            if ((inflight >> bb) & 1u) tc5::mbar_wait(&lbar[bb], (lph >> bb) & 1u);
+    if (tid == 0 && ntiles > 0) {
+        atomicAdd(&a.ctl->tiles_vol, (unsigned long long)ntiles);
+        if (gated) atomicAdd(&a.ctl->tiles_gated, (unsigned long long)gated);
+    }
     tc5::fence_before();
     __syncthreads();
     tc5::fence_after();
@@ -497,6 +545,7 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ __align__(8) uint64_t ebar;  // the epilogue's inputs
+    __shared__ int s_nb[7 * C5::TC];
     __shared__ uint32_t tslot;
     __shared__ int s_abort;
     __shared__ unsigned int s_status;
@@ -534,6 +583,31 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
     const long ntile = (a.ncell + TC - 1) / TC;
     const bool need_un = a.stage && a.rk_a != 0.f;
     uint32_t eph = 0;
+    bool epi_pending = false;  // the epilogue's copies issued and not waited for
+    // neighbour cells of the tile's cells: s_nb[16 fi + c] (fi = 0: the cell, fi = F + 1:
+    // across face F), computed for the next tile by warps 4-7 during the epilogue
+    auto neighbours = [&](long t, int i) {
+        const long cb = t * TC;
+        const int fi = i >> 4, c = i & 15;
+        const long cc = cb + c;
+        long sc = cc < a.ncell ? cc : 0;  // cells past the end: not read
+        if (fi > 0 && cc < a.ncell) {
+            const int F = fi - 1;
+            int xyz[3];
+            cell_xyz(cc, a.N, xyz[0], xyz[1], xyz[2]);
+            const int d = F >> 1, co = xyz[d];
+            const long stp = d == 0 ? 1L : (d == 1 ? (long)a.N : (long)a.N * a.N);
+            sc = (F & 1) ? (co == a.N - 1 ? cc - (long)(a.N - 1) * stp : cc + stp)
+                         : (co == 0 ? cc + (long)(a.N - 1) * stp : cc - stp);
+        }
+        s_nb[i] = (int)sc;
+    };
+    if (blockIdx.x < ntile && tid < 7 * TC) neighbours(blockIdx.x, tid);
+    // the K padding (modes 20-31) of the self and neighbour operands is never
+    // written by the gathers: zero once (the lift operand that later shares the
+    // region leaves finite values there, and the table's padding is zero)
+    for (int e = 16 * tid; e < 14 * Fc::SB; e += 16 * C5::NT) *reinterpret_cast<uint4*>(sSelf + e) = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
     for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const long c0 = tile * TC;
         const int nvalid = k5::tile_cells(a.ncell, c0);
@@ -548,53 +622,37 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
             if (need_un) k5::bulk_tile(sEpi + TC * 80, a.u_n, c0, nvalid, 80, &ebar);
             k5::bulk_tile(sEpi + 2 * TC * 80, a.rvol, c0, nvalid, 80, &ebar);
         }
-        // ---- operands: rows 4 c + fld (rho, v_x, v_y, v_z) of each cell (self)
-        // and of its neighbour across each face F ----
+        epi_pending = true;
+        // ---- operands: rows 4 c + fld (rho, v_x, v_y, v_z) of each cell (self) and
+        // of its neighbour across each face F.  Coalesced: consecutive threads take
+        // consecutive 16-byte chunks of a (cell, face) pair's 20 (rho 5, v 15), all
+        // loads in flight before the split ----
         {
-            // two rows per thread (448 rows), all ten 16-byte loads in flight before
-            // the conversion
-            const float* src[2];
-            bool valid[2];
+            constexpr int NCH = 7 * TC * 20, PER = (NCH + C5::NT - 1) / C5::NT;
+            float4 raw[PER];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int e = tid + u * C5::NT;
-                const int F = e / 64 - 1, rr = e & 63, fld = rr >> 4, c = rr & 15;  // F = -1: self
-                const long cc = c0 + c;
-                valid[u] = e < 7 * 64 && c < nvalid;
-                long sc = cc;
-                if (valid[u] && F >= 0) {
-                    int xyz[3];
-                    cell_xyz(cc, a.N, xyz[0], xyz[1], xyz[2]);
-                    const int d = F >> 1, co = xyz[d];
-                    const long stp = d == 0 ? 1L : (d == 1 ? (long)a.N : (long)a.N * a.N);
-                    sc = (F & 1) ? (co == a.N - 1 ? cc - (long)(a.N - 1) * stp : cc + stp)
-                                 : (co == 0 ? cc + (long)(a.N - 1) * stp : cc - stp);
+            for (int i = 0; i < PER; ++i) {
+                const int g = tid + i * C5::NT, pi = g / 20, ch = g - 20 * (g / 20), c = pi & 15;
+                raw[i] = make_float4(ch == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);  // past the end: rho = 1, v = 0
+                if (g < NCH && c < nvalid) {
+                    const long sc = s_nb[pi];
+                    const float* src = ch < 5 ? a.u_in + sc * 80 + 4 * ch : a.vh_in + sc * 60 + 4 * (ch - 5);
+                    raw[i] = __ldg(reinterpret_cast<const float4*>(src));
                 }
-                src[u] = fld == 0 ? a.u_in + sc * 80 : a.vh_in + sc * 60 + (fld - 1) * 20;
             }
-            float4 raw[2][5];
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int j = 0; j < 5; ++j)
-                    raw[u][j] = valid[u] ? __ldg(reinterpret_cast<const float4*>(src[u]) + j)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int e = tid + u * C5::NT;
-                if (e < 7 * 64) {
-                    const int F = e / 64 - 1, rr = e & 63, fld = rr >> 4, c = rr & 15;
-                    float x[20];
-#pragma unroll
-                    for (int j = 0; j < 5; ++j) {
-                        x[4 * j] = raw[u][j].x;
-                        x[4 * j + 1] = raw[u][j].y;
-                        x[4 * j + 2] = raw[u][j].z;
-                        x[4 * j + 3] = raw[u][j].w;
-                    }
-                    if (!valid[u] && fld == 0) x[0] = 1.f;  // cells past the end: rho = 1, v = 0
-                    unsigned char* base = F < 0 ? sSelf : sNbr + 2 * F * Fc::SB;
-                    k5::put_row(base, Fc::SB, 4 * c + fld, x);
+            for (int i = 0; i < PER; ++i) {
+                const int g = tid + i * C5::NT, pi = g / 20, ch = g - 20 * (g / 20);
+                if (g < NCH) {
+                    const int fi = pi >> 4, c = pi & 15, fld = ch < 5 ? 0 : 1 + (ch - 5) / 5;
+                    const int k = 4 * (ch < 5 ? ch : (ch - 5) % 5);
+                    const float x[4] = {raw[i].x, raw[i].y, raw[i].z, raw[i].w};
+                    uint2 hi, lo;
+                    tc5::split4(x, hi, lo);
+                    unsigned char* base = fi == 0 ? sSelf : sNbr + 2 * (fi - 1) * Fc::SB;
+                    const int o = tc5::koff(4 * c + fld, k, 128, 512);
+                    *reinterpret_cast<uint2*>(base + o) = hi;
+                    *reinterpret_cast<uint2*>(base + Fc::SB + o) = lo;
                 }
             }
         }
@@ -691,8 +749,11 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
         if (!k5::wait_mma(&bar, phase, a.ctl, &s_abort)) break;
         if (!k5::wait_bar(&ebar, eph, a.ctl, &s_abort)) break;
         eph ^= 1u;
+        epi_pending = false;
         // ---- right-hand side = surface + rvol; stage combine (Sec. 7) ----
-        if (w < 4) {
+        if (w >= 4) {
+            if (tid - 128 < 7 * TC && tile + gridDim.x < ntile) neighbours(tile + gridDim.x, tid - 128);
+        } else {
             float R[20];
             tc5::ld16(tl + 128, R);
             tc5::ld4(tl + 144, R + 16);
@@ -794,6 +855,8 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
         __syncthreads();
         tc5::fence_after();
     }
+    // a loop left early: no bulk copy may still write into this block's shared memory
+    if (tid == 0 && epi_pending) tc5::mbar_wait(&ebar, eph);
     tc5::fence_before();
     __syncthreads();
     tc5::fence_after();
@@ -861,12 +924,17 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
     if (blockIdx.x < ntile) fetch(blockIdx.x, 0);
     int cur = 0;
     uint32_t lph = 0;
+    uint32_t inflight = blockIdx.x < ntile ? 1u : 0u;
     for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x, cur ^= 1) {
         const long c0 = tile * TC;
         const int nvalid = k5::tile_cells(a.ncell, c0);
         if (!k5::wait_bar(&lbar[cur], (lph >> cur) & 1u, a.ctl, &s_abort)) break;
         lph ^= 1u << cur;
-        if (tile + gridDim.x < ntile) fetch(tile + gridDim.x, cur ^ 1);
+        inflight &= ~(1u << cur);
+        if (tile + gridDim.x < ntile) {
+            fetch(tile + gridDim.x, cur ^ 1);
+            inflight |= 1u << (cur ^ 1);
+        }
         const float* sU = sUb + cur * TC * 80;
         const float* sAh = sAhb + cur * TC * 60;
         if (tid < TC * 4) {
@@ -983,6 +1051,9 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
         __syncthreads();
         tc5::fence_after();
     }
+    if (tid == 0)
+        for (int bb = 0; bb < 2; ++bb)
+            if ((inflight >> bb) & 1u) tc5::mbar_wait(&lbar[bb], (lph >> bb) & 1u);
     tc5::fence_before();
     __syncthreads();
     tc5::fence_after();

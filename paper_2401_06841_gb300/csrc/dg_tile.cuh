@@ -672,8 +672,8 @@ __device__ __forceinline__ void tile_nu(T* sm, const T* sU, const TArgs<T>& a, l
     };
     // bias + GELU of the warp's n-tile, stored as BF16 pairs (rows g, g+8; columns 8w+2t, +1)
     auto act = [&](const float* acc, const float* bs, uint32_t* dst, int mt) {
-        dst[(mt * 16 + g) * HW + col / 2] = pack_bf16x2(gelu_f(acc[0] + bs[0]), gelu_f(acc[1] + bs[1]));
-        dst[(mt * 16 + g + 8) * HW + col / 2] = pack_bf16x2(gelu_f(acc[2] + bs[0]), gelu_f(acc[3] + bs[1]));
+        dst[(mt * 16 + g) * HW + col / 2] = pack_bf16x2(gelu_infer(acc[0] + bs[0]), gelu_infer(acc[1] + bs[1]));
+        dst[(mt * 16 + g + 8) * HW + col / 2] = pack_bf16x2(gelu_infer(acc[2] + bs[0]), gelu_infer(acc[3] + bs[1]));
     };
     __syncthreads();
 #pragma unroll
@@ -772,6 +772,8 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     const T cs = T(a.ph.cs), cs2 = T(a.ph.cs2);
     T smax = T(0);
     double sums[4] = {0.0, 0.0, 0.0, 0.0};
+    bool need_div = true;
+    uint32_t ntiles = 0, gated = 0;  // volume tiles done, and those without div v
     constexpr bool STAGE = (MODE == TM_STAGE || MODE == TM_STAGE_VABS);
     const bool do_proj = (MODE == TM_PROJECT) || (STAGE && (a.flags & F_NEXTPROJ));
     T dt = T(0), ab0 = T(0), ab1 = T(0), ab2 = T(0);
@@ -869,6 +871,15 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 const int c = e / (3 * b), i = (e / b) % 3, l = e % b;
                 sA[(c * FE + 8 + i) * LDA + l] = (force && c < nvalid) ? sAh[e] : T(0);
             }
+            // the gradient rows and the viscous pressure are needed unless every
+            // cell of the tile has a zero coefficient (learned sensor gated off,
+            // or no viscosity): a tile-uniform decision (s_nu was written before
+            // the last barrier)
+            need_div = a.ph.av_mode == 1;
+            if (a.ph.av_mode == 2)
+                for (int c = 0; c < TC; ++c) need_div |= s_nu[c] != T(0);
+            ++ntiles;
+            gated += need_div ? 0u : 1u;
             // ---- evaluation coefficients: rho, m, grad rho, div m, (a_h staged above) ----
             // threads run field-major (a warp covers one or two fields, so the
             // per-field branches below do not diverge within it)
@@ -876,6 +887,11 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 const int f = e / TC, c = e % TC;
                 const T* u = sU + c * 4 * b;
                 T* row = sA + (c * FE + f) * LDA;
+                if (f >= 4 && f < 8 && !need_div) {
+#pragma unroll
+                    for (int l = 0; l < KP; ++l) row[l] = T(0);
+                    continue;
+                }
                 if (f >= 8 && f < 11) {
 #pragma unroll
                     for (int l = b; l < KP; ++l) row[l] = T(0);
@@ -934,12 +950,15 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                         const T rho = v[0], ir = rcp<T>(rho);
                         const T mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV];
                         const T vx = mx * ir, vy = my * ir, vz = mz * ir;
-                        const T divv = (v[7 * LDV] - (vx * v[4 * LDV] + vy * v[5 * LDV] + vz * v[6 * LDV])) * ir;
                         T Pi = T(0);
-                        if (a.ph.av_mode == 1)
-                            Pi = vnr_pressure<T>(avc, rho, divv);
-                        else if (a.ph.av_mode == 2)
-                            Pi = nu_pressure<T>(avc, rho, divv, s_nu[c]);
+                        if (need_div) {
+                            const T divv =
+                                (v[7 * LDV] - (vx * v[4 * LDV] + vy * v[5 * LDV] + vz * v[6 * LDV])) * ir;
+                            if (a.ph.av_mode == 1)
+                                Pi = vnr_pressure<T>(avc, rho, divv);
+                            else
+                                Pi = nu_pressure<T>(avc, rho, divv, s_nu[c]);
+                        }
                         const T P = cs2 * rho + Pi;
                         fl[it][0] = mx * vx + P;
                         fl[it][1] = my * vy + P;
@@ -1305,6 +1324,12 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     __syncthreads();
     if constexpr (STAGE) {
         if (tid == 0 && s_status) atomicOr(&a.ctl->status, s_status);
+    }
+    if constexpr (MODE != TM_PROJECT) {
+        if (tid == 0 && ntiles > 0) {
+            atomicAdd(&a.ctl->tiles_vol, (unsigned long long)ntiles);
+            if (gated) atomicAdd(&a.ctl->tiles_gated, (unsigned long long)gated);
+        }
     }
     if (do_proj) {
         if (a.flags & F_DT) {

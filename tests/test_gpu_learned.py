@@ -129,6 +129,61 @@ def test_learned_gate_zeroes_the_coefficient_of_quiet_cells():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("forced", [False, True])
+@pytest.mark.parametrize("prec,backend,tol", [("f64", "tcgen05", 1e-12), ("f32", "tcgen05", 2e-5),
+                                              ("x3", "tcgen05", 5e-5), ("x3", "mma", 5e-5)])
+def test_gate_skips_the_divergence_of_quiet_tiles(prec, backend, tol, forced):
+    # half of the mesh at rest (cells iz < N/2: whole tiles of consecutive cells),
+    # the other half random.  The gate sits above the resting cells' coefficient
+    # and at the median of the others, so that the resting tiles have no
+    # viscous pressure anywhere: the kernels skip their gradient rows and div v.
+    # The right-hand side still equals the oracle's with the gated coefficients,
+    # and the profile counts the skipped tiles.
+    N, k = 8, 3
+    u = I.random_state(N, k, seed=71)
+    rest = np.arange(N ** 3) // (N * N) < N // 2
+    u[rest] = 0.0
+    u[rest, 0, 0] = 1.0
+    # a random network under which the resting cells' coefficient lies below a
+    # quarter of the others (the first such seed)
+    ref_scale = (1.0 / N) / (k + 1)
+    s0 = Solver(N, k, precision="f64", av="learned")
+    s0.set_state(u)
+    for seed in range(6, 64):
+        th = M.init_params(2 * I.nmodes(k), seed=seed).astype(np.float32)
+        s0.set_av_weights(th)
+        nu0 = s0.av_nu().cpu().numpy().astype(np.float64) / ref_scale
+        v_rest = nu0[rest].max()
+        if np.mean(nu0[~rest] > v_rest) > 0.25:
+            break
+    s0.close()
+    assert np.ptp(nu0[rest]) <= 1e-12 * v_rest and np.mean(nu0[~rest] > v_rest) > 0.25
+    gate = max(float(v_rest) * (1 + 1e-6), float(np.median(nu0[~rest])))
+    s = Solver(N, k, precision=prec, av="learned", nu_gate=gate, x3_backend=backend)
+    s.set_av_weights(th)
+    s.set_state(u)
+    nu = s.av_nu().cpu().numpy().astype(np.float64)
+    assert (nu[rest] == 0).all() and (nu[~rest] > 0).any()
+    a = None
+    if forced:
+        fo = O.Forcing(mach=2.0, zeta=0.5, seed=4)
+        a = O.forcing_project(O.make_cfg(N, k), fo.kvec(), fo.amplitudes())
+    dt = 0.3 * (1 / N) / ((k + 1) * 6.0)
+    s.profile(True)
+    got = s.rhs(u, a, dt).cpu().numpy()
+    p = s.profile_read()
+    s.close()
+    ref = O.rhs_nu(O.make_cfg(N, k), u, nu, a, dt)
+    err = max(np.linalg.norm(got[:, v] - ref[:, v]) / np.linalg.norm(ref[:, v]) for v in range(4))
+    assert err < tol, err
+    # tiles of 16 consecutive cells: every tile of the resting half is skipped, a tile
+    # with a coefficient above zero is not
+    assert p["tiles_volume"] >= (N ** 3) // 16
+    assert p["tiles_gated"] >= rest.sum() // 16
+    assert p["tiles_gated"] < p["tiles_volume"]
+
+
+@pytest.mark.gpu
 def test_gpu_training_follows_fp64_adam():
     k = 2
     D = 2 * I.nmodes(k)
