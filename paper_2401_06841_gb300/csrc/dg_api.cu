@@ -820,6 +820,7 @@ cudaError_t tile_tc5(dg_ctx* c, const TileLaunch& t)
         p.u_n = t.u_n;
         p.out = t.out;
         p.vh_in = t.vh_in;
+        p.vh_self = (t.flags & F_SELFPROJ) ? const_cast<void*>(t.vh_in) : nullptr;
         p.flags = t.flags & F_FORCE;
         p.abar_in = t.abar_in;
         cudaError_t e = launch_tc5(L, p);
@@ -1323,8 +1324,13 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
                 t.ahat = force ? ctx->ahat : nullptr;
                 rk_weights(ctx->rk, s, ctx->prec != DG_PREC_F64, t.rk_a, t.rk_b);
                 // every stage projects its output; the last one for the next step,
-                // with the CFL bound (and |v| in learned mode)
-                t.flags = (force ? F_FORCE : 0) | F_NEXTPROJ | (last ? F_DT : 0);
+                // with the CFL bound (and |v| in learned mode).  Undriven stages on the
+                // tcgen05 kernels: stages after the first project their own input in
+                // the volume kernel instead (no forcing sums needed), so only the last
+                // stage's output gets a projection launch
+                const bool fold = ctx->tc5 && !force;
+                t.flags = (force ? F_FORCE : 0) | ((fold && !last) ? 0 : F_NEXTPROJ) | (last ? F_DT : 0) |
+                          ((fold && s > 0) ? F_SELFPROJ : 0);
                 t.abar_in = (pb + s) & 1;
                 t.abar_out = (pb + s + 1) & 1;
                 CK(tile(ctx, t));

@@ -73,6 +73,7 @@ struct T5Launch {
     const void* ahat;
     const float* nu;
     void* rvol;          // volume term [c][4][b] FP32 (caller's scratch)
+    void* vh_self;       // undriven stages: the volume kernel projects v of u_in here (or nullptr)
     const void* tab5;    // table block (tc5_build_tables)
     const void* phiv;    // [b][nq] FP32 phi at the volume points
     const void* phif;    // [b][nf] FP32 phi at the face points

@@ -53,7 +53,7 @@ struct C5 {
     static constexpr int oWs = oWq + 256;      // [16] float: w_s (sum 4)
     static constexpr int tab_bytes = oWs + 64;
     // TMEM columns per CTA
-    static constexpr int TM_VOL = 128, TM_FACE = 256, TM_PROJ = 64;
+    static constexpr int TM_VOL = 128, TM_VOLP = 256, TM_FACE = 256, TM_PROJ = 64;
     // shared memory of the kernels
     struct Vol {  // tables Phi + G + w_q, the tile, the work region
         // the tile (u, a_h) double-buffered: the next tile's copy lands while this one runs
@@ -98,6 +98,7 @@ struct T5Args {
     const float* ahat;   // forcing [c][3][b] or nullptr
     const float* nu;     // per-cell coefficient (learned sensor) or nullptr
     float* rvol;         // volume term [c][4][b]
+    float* vh_self;      // projection of v of u_in [c][3][b] by the volume kernel (undriven stages)
     const unsigned char* tab;  // C5 table block
     const float* phiv;   // [b][nq] phi at the volume points (exact positivity check)
     const float* phif;   // [b][nf] phi at the face points
@@ -231,10 +232,15 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, Ctl* ct
 // --------------------------------------------------------------------------
 // FORCE: the driving source is added (a_h rows, source slot); GATE: the
 // coefficients may vanish on whole tiles (learned sensor, or no viscosity), so
-// that div v is evaluated only where a cell of the tile needs it
-template <bool FORCE, bool GATE>
+// that div v is evaluated only where a cell of the tile needs it; PROJ (undriven
+// only): the slot of the source projects v = m/rho of the tile's state onto the
+// basis instead (Sec. 3.2, the primitive projection the face kernel then reads),
+// into an accumulator of its own -- the projection launch between stages drops
+template <bool FORCE, bool GATE, bool PROJ>
 __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
 {
+    static_assert(!(FORCE && PROJ), "the source slot carries the projection only without driving");
+    constexpr int TMC = PROJ ? C5::TM_VOLP : C5::TM_VOL;
     using V = C5::Vol;
     constexpr int TC = C5::TC;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     float* const sAhb = reinterpret_cast<float*>(sm + V::oAh);
     const float* sWq = reinterpret_cast<const float*>(sm + V::oWq);
     unsigned char* sW = sm + V::oW;
-    if (w == 0) tc5::tmem_alloc(&tslot, C5::TM_VOL);
+    if (w == 0) tc5::tmem_alloc(&tslot, TMC);
     if (tid == 0) {
         tc5::mbar_init(&bar, 1);
         tc5::mbar_init(&lbar[0], 1);
@@ -389,6 +395,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
         if (!k5::wait_mma(&bar, phase, a.ctl, &s_abort)) break;
         // ---- pointwise volume physics (Sec. 3.1: Pi at the volume points) ----
         float st[4][11];  // rho, m (3), v (3), P, source (3) of the thread's 4 (cell, point) items
+        const float wq8 = sWq[q] * 0.125f;
         {
             float ev[4][12];
 #pragma unroll
@@ -400,7 +407,6 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                 tc5::ld4(tl + 64 + 4 * p, ev[pp] + 8);
             }
             tc5::ld_wait();
-            const float wq8 = sWq[q] * 0.125f;
 #pragma unroll
             for (int pp = 0; pp < 4; ++pp) {
                 const int c = 2 * (4 * hp + pp) + h;
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
 #pragma unroll
             for (int sl = 0; sl < 2; ++sl) {
                 const int d = 2 * rnd + sl, k = 64 * sl + q;
-                if (d == 3 && !force) break;  // no source without driving
+                if (d == 3 && !force && !PROJ) break;  // no source without driving
 #pragma unroll
                 for (int pp = 0; pp < 4; pp += 2) {
                     float x[8];
@@ -451,6 +457,12 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                             y[1] = (s[1] * vd + (d == 0 ? s[7] : 0.f)) * i4h;
                             y[2] = (s[2] * vd + (d == 1 ? s[7] : 0.f)) * i4h;
                             y[3] = (s[3] * vd + (d == 2 ? s[7] : 0.f)) * i4h;
+                        } else if (PROJ) {
+                            // rows i = v_x, v_y, v_z, (none) weighted by w_q/8
+                            y[0] = s[4] * wq8;
+                            y[1] = s[5] * wq8;
+                            y[2] = s[6] * wq8;
+                            y[3] = 0.f;
                         } else {
                             y[0] = 0.f;
                             y[1] = s[8];
@@ -475,7 +487,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                 const uint32_t sw = tc5::saddr(sW), sg = tc5::saddr(sm + V::oG), sphi = tc5::saddr(sm + V::oPhi);
                 for (int sl = 0; sl < 2; ++sl) {
                     const int d = 2 * rnd + sl;
-                    if (d == 3 && !force) break;
+                    if (d == 3 && !force && !PROJ) break;
                     for (int pr = 0; pr < 3; ++pr) {
                         int ca, cb;
                         k5::prod(pr, ca, cb);
@@ -486,9 +498,9 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                                 tc5::mma(tm + 96, ad, tc5::sdesc(sg + (d * 2 + cb) * C5::G_BLK + ks * 256, 128, 1024),
                                          IDG, acc);
                             else
-                                tc5::mma(tm + 96, ad,
+                                tc5::mma(PROJ ? tm + 128 : tm + 96, ad,
                                          tc5::sdesc(sphi + (1 + 2 * cb) * C5::PHI_BLK + ks * 1024, 512, 128), IDS,
-                                         acc);
+                                         PROJ ? (pr + ks > 0) : acc);
                         }
                     }
                 }
@@ -500,7 +512,22 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
         bool ok = volume_round(std::integral_constant<int, 0>{});
         if (ok) ok = volume_round(std::integral_constant<int, 1>{});
         if (!ok) break;
-        // ---- rvol: rows m = 16 w + j (j < 16) of the M = 64 accumulator ----
+        // ---- rvol: rows m = 16 w + j (j < 16) of the M = 64 accumulator (warps
+        // 0-3); the projection of v from its own accumulator (warps 4-7) ----
+        if (PROJ && w >= 4) {
+            float R[20];
+            tc5::ld16(tl + 128, R);
+            tc5::ld4(tl + 144, R + 16);
+            tc5::ld_wait();
+            if (lane < 16) {
+                const int m = 16 * (w - 4) + lane, c = 2 * ((m & 31) >> 2) + (m >> 5), i = m & 3;
+                if (i < 3 && c < nvalid) {
+                    float4* dst = reinterpret_cast<float4*>(a.vh_self + (c0 + c) * 60 + i * 20);
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) dst[j] = make_float4(R[4 * j], R[4 * j + 1], R[4 * j + 2], R[4 * j + 3]);
+                }
+            }
+        }
         if (w < 4) {
             float R[20];
             tc5::ld16(tl + 96, R);
@@ -530,7 +557,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     tc5::fence_before();
     __syncthreads();
     tc5::fence_after();
-    if (w == 0) tc5::tmem_dealloc(tm, C5::TM_VOL);
+    if (w == 0) tc5::tmem_dealloc(tm, TMC);
 }
 
 // --------------------------------------------------------------------------

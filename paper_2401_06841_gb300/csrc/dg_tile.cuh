@@ -466,7 +466,7 @@ __device__ __forceinline__ void diffusion_faces(const Phys& ph, const T* self, c
 }
 
 enum { TM_PROJECT = 0, TM_RHS = 1, TM_STAGE = 2, TM_STAGE_VABS = 3 };
-enum { F_NEXTPROJ = 4, F_VABS = 8 };
+enum { F_NEXTPROJ = 4, F_VABS = 8, F_SELFPROJ = 16 };
 
 template <typename T>
 struct TArgs {

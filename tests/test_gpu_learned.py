@@ -244,6 +244,82 @@ def test_trained_sensor_beats_constant_predictor_on_held_out_cells():
     assert mae < 0.75 * mae_init
 
 
+def _train_k3_sensor(N, dev="cuda"):
+    """network trained on plain-sensor pairs of driven k=3 runs at Mach 3 (seed 2)
+    and Mach 10 (seed 3), snapshots every 10 steps, active and inactive cells 1:1"""
+    k = 3
+    trainer, _ = learned_solver(N, k, "f32", seed=1)
+    xs, ys = [], []
+    for mach, seed in ((3.0, 2), (10.0, 3)):
+        run = Solver(N, k, precision="f32", av="vnr")
+        run.set_state(I.turbulent_state(N, k, seed=seed, mach=mach))
+        run.set_forcing(mach=mach, zeta=0.5, seed=seed)
+        for i in range(30):
+            _, dt = run.step(1)
+            if i % 10 == 9:
+                trainer.set_state(run.get_state())
+                x, y = trainer.generate_pairs(dt)
+                xs.append(x)
+                ys.append(y)
+        run.close()
+    X, Y = torch.cat(xs), torch.cat(ys)
+    g = torch.Generator(device=X.device).manual_seed(0)
+    floor = float(Y.min())
+    act = torch.nonzero(Y > floor + 1e-3).flatten()
+    ina = torch.nonzero(Y <= floor + 1e-3).flatten()
+    ina = ina[torch.randperm(len(ina), device=X.device, generator=g)[: max(len(act), 1)]]
+    sel = torch.cat([act, ina])
+    sel = sel[torch.randperm(len(sel), device=X.device, generator=g)]
+    trainer.mlp_train(X[sel], Y[sel], epochs=20, batch=2048, lr=2e-3)
+    w = trainer.get_av_weights()
+    trainer.close()
+    return w
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f32", "x3"])
+def test_trained_sensor_gains_over_the_plain_sensor(prec):
+    # what the network gains over the method without it (Sec. 5 error-cost
+    # comparison): on a held-out Mach-6 state (seed 17; training used seeds 2
+    # and 3) and against the FP64 plain scheme on the 2N mesh (discretisation
+    # error), the gated learned sensor reaches a density L1 no larger than the
+    # plain sensor's while a large share of the tiles skips the div v work (half
+    # of them on this Mach-6 state at 24^3); same mesh, precision,
+    # steps and dt for both
+    from paper_2401_06841_gb300 import transfer as Tr
+    N, k, n = 24, 3, 10
+    w = _train_k3_sensor(N)
+    base = Solver(N, k, precision="f32", av="vnr")
+    base.set_state(I.turbulent_state(N, k, seed=17, mach=6.0))
+    base.set_forcing(mach=6.0, zeta=0.5, seed=17)
+    base.step(20)
+    S = base.get_state().clone()
+    dt = 0.8 * 0.3 * (1.0 / N) / ((k + 1) * base.diagnostics()["max_speed"])
+    base.close()
+    fine = Solver(2 * N, k, precision="f64", av="vnr")
+    fine.set_state(Tr.prolong(S.double(), N, k))
+    fine.step(2 * n, fixed_dt=dt / 2)
+    ref = Tr.restrict(fine.get_state(), N, k).contiguous()
+    fine.close()
+    l1, gated = {}, {}
+    for v in ("plain", "learned"):
+        s = Solver(N, k, precision=prec, av="vnr" if v == "plain" else "learned", nu_gate=1.0 if v == "learned" else 0.0)
+        if v == "learned":
+            s.set_av_weights(w)
+        s.set_state(S)
+        s.profile(True)
+        s.step(n, fixed_dt=dt)
+        p = s.profile_read()
+        l1[v] = s.l1_density(s.get_state().double(), ref)
+        gated[v] = p["tiles_gated"] / p["tiles_volume"]
+        s.close()
+    print("density L1 vs FP64 on 2N: plain %.4e, learned %.4e (ratio %.3f); gated tiles %.3f"
+          % (l1["plain"], l1["learned"], l1["learned"] / l1["plain"], gated["learned"]))
+    assert gated["plain"] == 0.0
+    assert gated["learned"] > 0.3
+    assert l1["learned"] <= l1["plain"]
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("prec", ["f64", "f32", "x3"])

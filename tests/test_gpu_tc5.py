@@ -90,6 +90,33 @@ def test_driven_steps(backend, rk):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("backend", BACKENDS)
+@pytest.mark.parametrize("rk,av", [(2, "vnr"), (3, "vnr"), (3, "off")])
+def test_undriven_steps(backend, rk, av):
+    # without driving the tcgen05 stages after the first project their own input
+    # in the volume kernel (no projection launch between stages); N = 7: ragged
+    # last tile
+    N = 7
+    u = I.random_state(N, K, seed=330 + rk, v_rms=0.8)
+    s = Solver(N, K, precision="x3", rk_stages=rk, av=av, x3_backend=backend)
+    s.set_state(u)
+    s.profile(True)
+    t, _ = s.step(3)
+    p = s.profile_read()
+    got = s.get_state().cpu().numpy()
+    s.close()
+    ref = u.copy()
+    rc, tr, _, _ = O.run(O.make_cfg(N, K, rk_stages=rk, av_mode={"off": 0, "vnr": 1}[av]), ref, 3)
+    assert rc == 0 and t == pytest.approx(tr, rel=5e-5)
+    err = rel_l2_fields(got, ref)
+    assert err.max() < 1e-4, err
+    # projection launches: one before the first step, then one per step (tcgen05) or
+    # the fused kernel's own (mma back end: none counted separately)
+    if backend == "tcgen05":
+        assert p["n_project"] == 1 + 3, p
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("backend", BACKENDS)
 def test_limited_step(backend):
     # densities below the floor in two cells: both sides rescale the same cells
     N = 5
