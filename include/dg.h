@@ -127,13 +127,14 @@ typedef struct {
     int32_t riemann;       /* DG_RIEMANN_*; 0 (Rusanov) when zero-initialised     */
     int32_t x3_backend;    /* DG_PREC_X3 at order 3 without diffusion: 0 (default)
                               = 5th-generation tensor-core kernels (tcgen05 with
-                              TMEM accumulators: volume, face and projection
-                              kernels per stage, the volume term through a
-                              caller-scratch buffer); 1 = the single fused stage
-                              kernel on warp-level mma.sync.  Other precisions,
-                              orders, the diffusion operator and the learned
-                              sensor evaluated inside the stage (fused_infer = 1)
-                              use the fused kernel either way                  */
+                              TMEM accumulators: volume and face kernels per
+                              stage, the projection kernel after the last stage
+                              and, in driven steps, after every stage; the volume
+                              term through a caller-scratch buffer; fused_infer
+                              evaluates the sensor in that last projection);
+                              1 = the single fused stage kernel on warp-level
+                              mma.sync.  Other precisions, orders and the
+                              diffusion operator use the fused kernel either way */
 } dg_opts;
 
 /* Driving (Sec. 4.2, eq. ornstein_uhlenbeck_process_time_evolution).  Modes:

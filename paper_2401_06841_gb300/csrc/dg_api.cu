@@ -833,6 +833,8 @@ cudaError_t tile_tc5(dg_ctx* c, const TileLaunch& t)
         q.u_in = t.out;
         q.vh_out = t.vh_out;
         q.vabs_out = t.vabs_out;
+        q.nu_next = t.nu_next;
+        q.mlp = t.mlp;
         q.flags = t.flags & (F_FORCE | F_DT);
         q.abar_out = t.abar_out;
         return launch_tc5(L, q);
@@ -1059,10 +1061,9 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->vabs = ctx->scratch + sl.vabs;
     ctx->t5tab = ctx->scratch + sl.t5tab;
     ctx->rvol = ctx->scratch + sl.rvol;
-    // the in-stage sensor evaluation (fused_infer) lives in the fused kernel: such a
-    // context runs every launch there, so that carried and fresh coefficients agree
-    ctx->tc5 = ctx->prec == DG_PREC_X3 && order == 3 && nu->diffusion == 0.0 && opts->x3_backend == 0 &&
-               !(nu->mode == DG_AV_LEARNED && nu->fused_infer);
+    // order-3 x3 on the tcgen05 kernels (the learned sensor's in-step evaluation,
+    // fused_infer, runs in their last projection)
+    ctx->tc5 = ctx->prec == DG_PREC_X3 && order == 3 && nu->diffusion == 0.0 && opts->x3_backend == 0;
     ctx->mlp_D = 2 * ctx->b;
     ctx->mlp_P = mlp_params(ctx->mlp_D);
 

@@ -74,6 +74,8 @@ struct T5Launch {
     const float* nu;
     void* rvol;          // volume term [c][4][b] FP32 (caller's scratch)
     void* vh_self;       // undriven stages: the volume kernel projects v of u_in here (or nullptr)
+    float* nu_next;      // projection: the learned sensor's coefficient of u_in (or nullptr)
+    const uint32_t* mlp; // its packed network
     const void* tab5;    // table block (tc5_build_tables)
     const void* phiv;    // [b][nq] FP32 phi at the volume points
     const void* phif;    // [b][nf] FP32 phi at the face points

@@ -192,6 +192,9 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
     a.flags = t.flags;
     a.abar_in = t.abar_in;
     a.abar_out = t.abar_out;
+    a.nu_next = t.nu_next;
+    a.mlp = t.mlp;
+    if (t.nu_next && (t.kind != T5_PROJECT || !t.mlp)) return cudaErrorInvalidValue;
     if ((t.flags & F_FORCE) && !t.ahat) return cudaErrorInvalidValue;
     const long ntile = (L.ncell + C5::TC - 1) / C5::TC;
     if (t.kind == T5_PROJECT) {

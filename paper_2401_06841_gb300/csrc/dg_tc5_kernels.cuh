@@ -99,6 +99,8 @@ struct T5Args {
     const float* nu;     // per-cell coefficient (learned sensor) or nullptr
     float* rvol;         // volume term [c][4][b]
     float* vh_self;      // projection of v of u_in [c][3][b] by the volume kernel (undriven stages)
+    float* nu_next;      // projection kernel: learned coefficient of u_in [c] (or nullptr)
+    const uint32_t* mlp; // packed network of the learned sensor
     const unsigned char* tab;  // C5 table block
     const float* phiv;   // [b][nq] phi at the volume points (exact positivity check)
     const float* phif;   // [b][nf] phi at the face points
@@ -914,6 +916,7 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
     const float* sWq = reinterpret_cast<const float*>(sm + P::oWq);
     unsigned char* sEB = sm + P::oEB;
     unsigned char* sPA = sm + P::oPA;
+    float* const sVa = reinterpret_cast<float*>(sEB);  // |v| rows of the tile (learned sensor), after the products
     if (w == 0) tc5::tmem_alloc(&tslot, C5::TM_PROJ);
     if (tid == 0) {
         tc5::mbar_init(&bar, 1);
@@ -1059,7 +1062,30 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
                         for (int j = 0; j < 5; ++j) d4[j] = make_float4(R[4 * j], R[4 * j + 1], R[4 * j + 2], R[4 * j + 3]);
                     }
                 }
+                if (a.nu_next && i == 3) {
+#pragma unroll
+                    for (int l = 0; l < 20; ++l) sVa[c * 20 + l] = R[l];
+                }
             }
+        }
+        if (a.nu_next) {
+            // the learned sensor's coefficient of this state (Sec. 7 learned AV), for the
+            // next step: features (rho_l/rho_0, |v|hat_l/cs), the network of the
+            // inference kernel (same products and roundings); its buffers use the free
+            // evaluation region
+            __syncthreads();
+            using PK = MlpPack<40>;
+            uint32_t* sX = reinterpret_cast<uint32_t*>(sEB) + 512;  // after the |v| rows
+            uint32_t* sH1 = sX + TC * (PK::KD / 2);
+            uint32_t* sH2 = sH1 + TC * (MLP_H / 2);
+            const float inv_cs = 1.0f / (float)a.ph.cs;
+            auto feat = [&](int c, int k) -> float {
+                if (c0 + c >= a.ncell || k >= 40) return 0.0f;
+                if (k < 20) return sU[c * 80 + k] / sU[c * 80];
+                return sVa[c * 20 + (k - 20)] * inv_cs;
+            };
+            block_mlp<40, TC, C5::NT>(feat, sX, sH1, sH2, a.mlp, (float)(a.ph.cs * a.ph.hp), (float)a.ph.nu_gate, c0,
+                                      a.ncell, a.nu_next);
         }
         // per-cell forcing sums <rho a_h> = sum_l rho_l a_l (orthonormal basis) and <rho>
         if (force && tid < TC * 3) {

@@ -617,39 +617,29 @@ __device__ __forceinline__ void tile_project(T* sm, const T* sU, const T* tabs, 
 // the BF16 activations pass through shared memory, and the first TC/16 warps
 // form the outputs.  Products, roundings and accumulation orders are those of
 // the separate kernel, so the coefficients agree bit for bit.
-// Needs the big region free (after the projection) and sP holding the
-// projections (rows cell x (v_x, v_y, v_z, |v|)).
 // --------------------------------------------------------------------------
-template <typename T, int K, int BK>
-__device__ __forceinline__ void tile_nu(T* sm, const T* sU, const TArgs<T>& a, long c0)
+// the network of the learned sensor for TC cells, spread over a block of NT =
+// 256 threads: feat(c, k) gives input k of cell c (called for c < TC, k < KD);
+// sX, sH1, sH2 are shared buffers of TC*KD/2, TC*32 and TC*32 words; writes
+// nu_out[c0 + c] for the cells below ncell.  Ends without a trailing barrier.
+template <int D, int TC, int NT, typename F>
+__device__ __forceinline__ void block_mlp(F&& feat, uint32_t* sX, uint32_t* sH1, uint32_t* sH2, const uint32_t* mlp,
+                                          float ref, float gate, long c0, long ncell, float* nu_out)
 {
-    using C = TileCfg<K, BK>;
-    constexpr int b = C::b, TC = C::TC, NT = C::NT, LDP = C::LDP, D = 2 * b;
     using PK = MlpPack<D>;
     constexpr int XW = PK::KD / 2, KT1 = PK::KD / 16, MT = TC / 16, HW = MLP_H / 2;
     static_assert(NT / 32 == MLP_H / 8 && TC % 16 == 0, "one warp per 8 hidden units, 16-cell row blocks");
-    static_assert((TC * XW + 2 * TC * HW) * 4 <= C::BIG * (int)sizeof(T), "network buffers in the big region");
-    uint32_t* sX = reinterpret_cast<uint32_t*>(sm + C::oBig);  // [TC][XW] BF16 pairs of features
-    uint32_t* sH1 = sX + TC * XW;                              // [TC][HW] first hidden layer
-    uint32_t* sH2 = sH1 + TC * HW;                             // [TC][HW] second hidden layer
-    const T* sP = sm + C::oP;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const float inv_cs = 1.0f / (float)a.ph.cs;
-    auto feat = [&](int c, int k) -> float {
-        if (c0 + c >= a.ncell || k >= D) return 0.0f;
-        if (k < b) return (float)(sU[c * 4 * b + k] / sU[c * 4 * b]);
-        return (float)sP[(c * 4 + 3) * LDP + (k - b)] * inv_cs;
-    };
     for (int e = tid; e < TC * XW; e += NT) {
         const int c = e / XW, k0 = 2 * (e % XW);
         sX[e] = pack_bf16x2(feat(c, k0), feat(c, k0 + 1));
     }
     // the warp's weight fragments and biases, loaded up front (their latency
     // overlaps the feature phase)
-    const uint2* B1 = reinterpret_cast<const uint2*>(a.mlp + PK::w1);
-    const uint2* B2 = reinterpret_cast<const uint2*>(a.mlp + PK::w2);
-    const uint2* B3 = reinterpret_cast<const uint2*>(a.mlp + PK::w3);
-    const float* bias = reinterpret_cast<const float*>(a.mlp + PK::bias);
+    const uint2* B1 = reinterpret_cast<const uint2*>(mlp + PK::w1);
+    const uint2* B2 = reinterpret_cast<const uint2*>(mlp + PK::w2);
+    const uint2* B3 = reinterpret_cast<const uint2*>(mlp + PK::w3);
+    const float* bias = reinterpret_cast<const float*>(mlp + PK::bias);
     uint2 w1f[KT1], w2f[4], w3f[4];
 #pragma unroll
     for (int kt = 0; kt < KT1; ++kt) w1f[kt] = __ldg(B1 + (kt * 8 + w) * 32 + lane);
@@ -708,16 +698,39 @@ __device__ __forceinline__ void tile_nu(T* sm, const T* sU, const TArgs<T>& a, l
             frag(sH2, HW, w, kt, A);
             mma_bf16(acc, A, w3f[kt].x, w3f[kt].y);
         }
-        const float ref = (float)(a.ph.cs * a.ph.hp), gate = (float)a.ph.nu_gate;
         if (t == 0) {
             const float y[2] = {acc[0] + b3, acc[2] + b3};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const long r = c0 + w * 16 + g + 8 * h;
-                if (r < a.ncell) a.nu_next[r] = expf(y[h]) < gate ? 0.f : ref * expf(y[h]);
+                if (r < ncell) nu_out[r] = expf(y[h]) < gate ? 0.f : ref * expf(y[h]);
             }
         }
     }
+}
+
+// the fused stage kernel's tile: needs the big region free (after the
+// projection) and sP holding the projections (rows cell x (v_x, v_y, v_z, |v|))
+template <typename T, int K, int BK>
+__device__ __forceinline__ void tile_nu(T* sm, const T* sU, const TArgs<T>& a, long c0)
+{
+    using C = TileCfg<K, BK>;
+    constexpr int b = C::b, TC = C::TC, NT = C::NT, LDP = C::LDP, D = 2 * b;
+    using PK = MlpPack<D>;
+    constexpr int XW = PK::KD / 2, HW = MLP_H / 2;
+    static_assert((TC * XW + 2 * TC * HW) * 4 <= C::BIG * (int)sizeof(T), "network buffers in the big region");
+    uint32_t* sX = reinterpret_cast<uint32_t*>(sm + C::oBig);  // [TC][XW] BF16 pairs of features
+    uint32_t* sH1 = sX + TC * XW;                              // [TC][HW] first hidden layer
+    uint32_t* sH2 = sH1 + TC * HW;                             // [TC][HW] second hidden layer
+    const T* sP = sm + C::oP;
+    const float inv_cs = 1.0f / (float)a.ph.cs;
+    auto feat = [&](int c, int k) -> float {
+        if (c0 + c >= a.ncell || k >= D) return 0.0f;
+        if (k < b) return (float)(sU[c * 4 * b + k] / sU[c * 4 * b]);
+        return (float)sP[(c * 4 + 3) * LDP + (k - b)] * inv_cs;
+    };
+    block_mlp<D, TC, NT>(feat, sX, sH1, sH2, a.mlp, (float)(a.ph.cs * a.ph.hp), (float)a.ph.nu_gate, c0, a.ncell,
+                         a.nu_next);
     // the next tile starts with a barrier before it writes the big region
 }
 
