@@ -469,35 +469,103 @@ def precision_gate(variants, S0, meta0, args, dev):
 
 
 def learned_gate(variants, args, dev, weights):
-    """L1 density error of plain FP32 and the learned variants on the learned-sensor
-    configuration (N_l^3, k=3, Mach-6 driven state, seed 104) against the plain
-    FP32 scheme on the 2N_l^3 mesh from the exactly prolonged state."""
+    """The learned-sensor configuration (N_l^3, k=3, Mach-6 OU-driven turbulence,
+    seed 104): plain and learned variants stepped from the same driven state with
+    the driving continued (same OU state) and the same dt, each timed, and their
+    density L1 error against the plain FP32 scheme on the 2N_l^3 mesh from the
+    exactly prolonged state (driven likewise)."""
+    import torch
     from paper_2401_06841_gb300 import Solver
     from paper_2401_06841_gb300 import inputs as I
     from paper_2401_06841_gb300 import transfer as Tr
     N, k = args.l_N, args.k
+    b = (k + 1) * (k + 2) * (k + 3) // 6
+    n = args.l1_steps_learned
     base = Solver(N, k, precision="f32", rk_stages=3, device=dev, riemann=args.riemann)
     base.set_state(I.turbulent_state_device(N, k, seed=104, mach=6.0, device=dev))
     base.set_forcing(mach=6.0, zeta=0.5, seed=4)
     base.step(args.l_relax)
     S4 = base.get_state().clone()
+    meta4 = base.get_meta()
+    diag = {k_: v for k_, v in base.diagnostics().items() if k_ in ("mach", "rho_min", "rho_max", "av_frac")}
     dt = 0.8 * 0.3 * (1.0 / N) / ((k + 1) * base.diagnostics()["max_speed"])
     base.close()
     fine = Solver(2 * N, k, precision="f32", rk_stages=3, device=dev, riemann=args.riemann)
+    fine.set_forcing(mach=6.0, zeta=0.5, seed=4)
     fine.set_state(Tr.prolong(S4, N, k))
-    fine.step(2 * args.l1_steps_learned, fixed_dt=dt / 2)
+    fine.set_meta(meta4)
+    fine.step(2 * n, fixed_dt=dt / 2)
     ref = Tr.restrict(fine.get_state(), N, k).contiguous()
     fine.close()
-    out = {}
-    for v in ["f32"] + [v for v in variants if v.startswith("learned")]:
+    out, timing = {}, {}
+    names = ["f32"] + (["x3"] if any(v.endswith("x3") for v in variants) else []) + \
+        [v for v in variants if v.startswith("learned")]
+    for v in names:
         s = make_solver(v, N, k, args, dev, weights)
+        s.set_forcing(mach=6.0, zeta=0.5, seed=4)
         s.set_state(S4)
-        s.step(args.l1_steps_learned, fixed_dt=dt)
+        s.set_meta(meta4)
+        s.step(1, fixed_dt=dt)  # warm-up (and the first learned coefficient)
+        s.set_state(S4)
+        s.set_meta(meta4)
+        torch.cuda.synchronize()
+        s.profile(True)
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(s.stream)
+        s.step(n, fixed_dt=dt)
+        b_ev.record(s.stream)
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        ms = a_ev.elapsed_time(b_ev) / n
         out[v] = s.l1_density(s.get_state(), ref)
+        timing[v] = {"value": 3 * 4 * b * N ** 3 / (3 * ms * 1e-3), "ms_per_step": ms,
+                     "gated_tile_frac": prof["tiles_gated"] / max(prof["tiles_volume"], 1), "l1_rho": out[v]}
         s.close()
     return out, {"reference": "plain FP32 on the 2N^3 mesh from the prolonged state (2n steps at dt/2), "
-                              "restricted by L2 projection", "mesh": N, "steps": args.l1_steps_learned,
-                 "state": "synthetic k^-2 velocity, Mach 6 (seed 104), %d driven steps" % args.l_relax}
+                              "restricted by L2 projection; every run driven on (the relaxation's OU state)",
+                 "mesh": N, "steps": n, "dt": dt, "diag_start": diag,
+                 "state": "synthetic k^-2 velocity, Mach 6 (seed 104), %d driven steps" % args.l_relax,
+                 "timing": timing, "unit": UNIT}
+
+
+def config3_arm(args, dev):
+    """The strong-shock configuration: 128^3 cells (--c3-N), k=2, SSP-RK3, FP32,
+    plain sensor and projection, driven towards Mach 10 by solenoidal OU forcing
+    (seed 1) from rho = 1, v = 0; training pairs generated from the state every
+    50 steps.  Timed: c3-steps steps (L2 not flushed: the run as a run) with the
+    pair generations they contain."""
+    import torch
+    from paper_2401_06841_gb300 import Solver
+    N, k = args.c3_N, 2
+    b = (k + 1) * (k + 2) * (k + 3) // 6
+    s = Solver(N, k, precision="f32", rk_stages=3, av="vnr", device=dev, riemann=args.riemann)
+    pairs = Solver(N, k, precision="f32", av="learned", device=dev, riemann=args.riemann)
+    u0 = torch.zeros(N ** 3, 4, b, dtype=torch.float32, device=dev)
+    u0[:, 0, 0] = 1.0
+    s.set_state(u0)
+    s.set_forcing(mach=10.0, zeta=1.0, seed=1)
+    s.step(3)
+    torch.cuda.synchronize()
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_ev.record(s.stream)
+    npairs = 0
+    for i in range(args.c3_steps):
+        _, dt = s.step(1)
+        if (i + 4) % 50 == 0:
+            pairs.set_state(s.get_state())
+            x, y = pairs.generate_pairs(dt)
+            npairs += int(y.numel())
+    b_ev.record(s.stream)
+    torch.cuda.synchronize()
+    ms = a_ev.elapsed_time(b_ev) / args.c3_steps
+    d = s.diagnostics()
+    s.close()
+    pairs.close()
+    return {"workload": "driven to Mach 10 (solenoidal OU, seed 1) from rest, %d^3 cells, DG k=2 (P2), SSP-RK3, "
+                        "FP32, plain vNR sensor; pairs every 50 steps" % N,
+            "value": 3 * 4 * b * N ** 3 / (3 * ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "steps": args.c3_steps, "warmup": 3, "pairs": npairs,
+            "state_after": {k_: d[k_] for k_ in ("mach", "rho_min", "rho_max", "av_frac")}}
 
 
 def main():
@@ -529,6 +597,9 @@ def main():
     ap.add_argument("--diffusion", type=float, default=0.0, help="eps of an added div(eps grad u)")
     ap.add_argument("--x3-backend", dest="x3_backend", default="tcgen05", choices=["tcgen05", "mma"],
                     help="order-3 x3 stage: the tcgen05 kernels or the fused mma.sync kernel")
+    ap.add_argument("--c3-N", dest="c3_N", type=int, default=128, help="mesh of the strong-shock configuration")
+    ap.add_argument("--c3-steps", dest="c3_steps", type=int, default=100)
+    ap.add_argument("--no-c3", dest="no_c3", action="store_true")
     ap.add_argument("--nu-gate", dest="nu_gate", type=float, default=1.0,
                     help="learned variants: cells with nu/(cs h/p) below this get no viscous pressure, and "
                          "tiles of 16 such cells skip div v")
@@ -672,6 +743,8 @@ def main():
     hs.close()
     del hs, S0
     torch.cuda.empty_cache()
+    if not args.no_c3:
+        line["config3"] = config3_arm(args, dev)
     if not args.no_adiabatic:
         line["adiabatic"] = adiabatic_arm(args, dev, state_seed, flush, world)
         line["adiabatic_near_isothermal"] = adiabatic_arm(args, dev, state_seed, flush, world, near_isothermal=True)

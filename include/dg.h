@@ -480,6 +480,19 @@ int dg_adi_set_forcing(dg_adi_ctx* ctx, const dg_forcing* f, double cs_ref);
 int dg_adi_set_reset(dg_adi_ctx* ctx, double cs);
 /* out[0] = injected, out[1] = dissipated energy since dg_adi_set_state. */
 int dg_adi_energy_budget(dg_adi_ctx* ctx, double* out);
+/* Checkpoint metadata of the adiabatic system: time, steps and the driving's
+ * OU state (as dg_meta), and the energy budget of the run (Sec. 4.2).  Resume:
+ * dg_adi_set_forcing (same modes) and dg_adi_set_reset as before, then
+ * dg_adi_set_state (which zeroes time and budget), then dg_adi_set_meta; the
+ * following steps are bit-identical to the uninterrupted run's.  set_meta
+ * returns DG_EINVAL when the number of driven modes differs. */
+typedef struct {
+    dg_meta m;
+    double injected;       /* energy injected by the driving since the start     */
+    double dissipated;     /* energy taken out by the temperature reset           */
+} dg_adi_meta;
+int dg_adi_get_meta(dg_adi_ctx* ctx, dg_adi_meta* out);
+int dg_adi_set_meta(dg_adi_ctx* ctx, const dg_adi_meta* in);
 /* FP64 diagnostics of the current state: out[0..7] = mass, momentum (3),
  * total energy (integrals over the box), kinetic energy (volume quadrature of
  * |m|^2/(2 rho)), minimum density and minimum pressure at the volume points. */

@@ -61,6 +61,10 @@ class Meta(C.Structure):
                 ("x", C.c_double * 2 * 3 * 512)]
 
 
+class AdiMeta(C.Structure):
+    _fields_ = [("m", Meta), ("injected", C.c_double), ("dissipated", C.c_double)]
+
+
 class TrainOpts(C.Structure):
     _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
                 ("batch", C.c_int32), ("epochs", C.c_int32)]
@@ -129,6 +133,8 @@ def lib() -> C.CDLL:
         L.dg_adi_set_forcing.argtypes = [vp, C.POINTER(Forcing), d]
         L.dg_adi_set_reset.argtypes = [vp, d]
         L.dg_adi_energy_budget.argtypes = [vp, C.POINTER(d)]
+        L.dg_adi_get_meta.argtypes = [vp, C.POINTER(AdiMeta)]
+        L.dg_adi_set_meta.argtypes = [vp, C.POINTER(AdiMeta)]
         L.dg_rhs_noalloc.argtypes = [C.POINTER(Mesh), i, d, C.POINTER(NuParams), i, vp, vp, vp, d, vp]
         L.dg_profile.argtypes = [vp, i]
         L.dg_profile_read.argtypes = [vp, C.POINTER(Prof)]
@@ -148,7 +154,8 @@ EXPORTS = ("dg_scratch_bytes", "dg_vhat_bytes", "dg_init", "dg_free", "dg_last_e
            "dg_mlp_train", "dg_mlp_grad", "dg_mlp_forward", "dg_av_nu", "dg_av_nu_carried", "dg_density_pdf", "dg_structure_function",
            "dg_analysis_bytes", "dg_power_spectrum", "dg_adi_buffer_bytes", "dg_adi_init", "dg_adi_free",
            "dg_adi_last_error", "dg_adi_set_state", "dg_adi_get_state", "dg_adi_project", "dg_adi_rhs",
-           "dg_adi_step", "dg_adi_totals", "dg_adi_set_forcing", "dg_adi_set_reset", "dg_adi_energy_budget")
+           "dg_adi_step", "dg_adi_totals", "dg_adi_set_forcing", "dg_adi_set_reset", "dg_adi_energy_budget",
+           "dg_adi_get_meta", "dg_adi_set_meta")
 
 MAX_BINS = 2000
 

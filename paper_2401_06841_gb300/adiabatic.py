@@ -124,6 +124,14 @@ class AdiabaticSolver:
         self._check(self.L.dg_adi_energy_budget(self.h, out), self.h)
         return out[0], out[1]
 
+    def get_meta(self):
+        m = B.AdiMeta()
+        self._check(self.L.dg_adi_get_meta(self.h, C.byref(m)), self.h)
+        return m
+
+    def set_meta(self, m):
+        self._check(self.L.dg_adi_set_meta(self.h, C.byref(m)), self.h)
+
     def totals(self) -> dict:
         out = (C.c_double * 8)()
         self._check(self.L.dg_adi_totals(self.h, out), self.h)

@@ -2217,6 +2217,48 @@ int dg_adi_energy_budget(dg_adi_ctx* ctx, double* out)
     return DG_OK;
 }
 
+int dg_adi_get_meta(dg_adi_ctx* ctx, dg_adi_meta* m)
+{
+    if (!ctx || !m) return DG_EINVAL;
+    std::memset(m, 0, sizeof(*m));
+    m->m.t = ctx->t;
+    m->m.steps = ctx->steps;
+    m->m.dt_last = ctx->dt_last;
+    m->m.forcing_on = ctx->drv.on ? 1 : 0;
+    m->m.forcing_dirty = ctx->drv.dirty ? 1 : 0;
+    m->m.t_next = ctx->drv.t_next;
+    m->m.rng = ctx->drv.rng;
+    m->m.have_spare = ctx->drv.have_spare ? 1 : 0;
+    m->m.spare = ctx->drv.spare;
+    m->m.nmodes = ctx->drv.nm;
+    std::memcpy(m->m.x, ctx->drv.x, sizeof(double) * 6 * ctx->drv.nm);
+    m->injected = ctx->injected;
+    m->dissipated = ctx->dissipated;
+    return DG_OK;
+}
+
+int dg_adi_set_meta(dg_adi_ctx* ctx, const dg_adi_meta* m)
+{
+    if (!ctx || !m) return DG_EINVAL;
+    if (m->m.nmodes != ctx->drv.nm)
+        return afail(ctx, DG_EINVAL, "dg_adi_set_meta: call dg_adi_set_forcing with the same modes first");
+    ctx->t = m->m.t;
+    ctx->steps = m->m.steps;
+    ctx->dt_last = m->m.dt_last;
+    ctx->drv.on = m->m.forcing_on != 0;
+    ctx->drv.t_next = m->m.t_next;
+    ctx->drv.rng = m->m.rng;
+    ctx->drv.have_spare = m->m.have_spare != 0;
+    ctx->drv.spare = m->m.spare;
+    std::memcpy(ctx->drv.x, m->m.x, sizeof(double) * 6 * m->m.nmodes);
+    // the forcing is projected again from these OU amplitudes before the next step
+    ctx->drv.dirty = ctx->drv.on;
+    if (!ctx->drv.on) ctx->forcing_active = false;
+    ctx->injected = m->injected;
+    ctx->dissipated = m->dissipated;
+    return DG_OK;
+}
+
 int dg_adi_totals(dg_adi_ctx* ctx, double* out)
 {
     if (!ctx) return DG_EINVAL;

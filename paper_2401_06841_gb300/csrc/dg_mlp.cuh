@@ -203,8 +203,19 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const T* __restrict__ u, cons
             for (int l = 0; l < b; ++l) x[l] = T(0);
             if (r < n) {
                 const T* src = h == 0 ? u + r * 4 * b : vabs + r * b;
+                if constexpr (sizeof(T) == 4 && b % 4 == 0) {
 #pragma unroll
-                for (int l = 0; l < b; ++l) x[l] = src[l];
+                    for (int l = 0; l < b; l += 4) {
+                        const float4 q = __ldg(reinterpret_cast<const float4*>(src + l));
+                        x[l] = q.x;
+                        x[l + 1] = q.y;
+                        x[l + 2] = q.z;
+                        x[l + 3] = q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int l = 0; l < b; ++l) x[l] = src[l];
+                }
             }
             float* dst = sf + rl * D + h * b;
 #pragma unroll

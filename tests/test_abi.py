@@ -47,8 +47,9 @@ def test_struct_sizes_match_header():
     prog = r'''
 #include <stdio.h>
 #include "dg.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dg_mesh), sizeof(dg_nu_params), sizeof(dg_opts),
- sizeof(dg_forcing), sizeof(dg_diag), sizeof(dg_meta), sizeof(dg_prof), sizeof(dg_adi_opts)); return 0;}
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dg_mesh), sizeof(dg_nu_params), sizeof(dg_opts),
+ sizeof(dg_forcing), sizeof(dg_diag), sizeof(dg_meta), sizeof(dg_prof), sizeof(dg_adi_opts), sizeof(dg_adi_meta));
+ return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "s.c")
@@ -57,7 +58,7 @@ int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dg_mesh), size
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = [int(x) for x in subprocess.check_output([exe]).split()]
     mine = [C.sizeof(B.Mesh), C.sizeof(B.NuParams), C.sizeof(B.Opts), C.sizeof(B.Forcing), C.sizeof(B.Diag),
-            C.sizeof(B.Meta), C.sizeof(B.Prof), C.sizeof(B.AdiOpts)]
+            C.sizeof(B.Meta), C.sizeof(B.Prof), C.sizeof(B.AdiOpts), C.sizeof(B.AdiMeta)]
     assert sizes == mine
 
 

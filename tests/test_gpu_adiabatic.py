@@ -256,6 +256,56 @@ def test_driven_steps_with_reset_parity(prec, g, cs, v_rms, tol):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_checkpoint_resume_is_bit_identical(prec):
+    # a driven run with the temperature reset, interrupted after 3 steps: the
+    # state and dg_adi_get_meta (time, steps, OU variables, energy budget) go into
+    # a fresh context, which continues for 3 more steps.  State, time and budget
+    # equal the uninterrupted 6-step run's bit for bit.
+    N, k, g, cs = 5, 2, 1.4, 2.0
+    fo = dict(mach=2.0, zeta=0.5, seed=9)
+    u4 = I.random_state(N, k, seed=23, v_rms=0.3)
+    u = np.zeros((N ** 3, 5, u4.shape[2]))
+    u[:, :4] = u4
+    O.adi_reset(O.make_cfg(N, k), g, cs, u)
+    full = AdiabaticSolver(N, k, gamma=g, precision=prec)
+    full.set_forcing(cs_ref=cs, **fo)
+    full.set_reset(cs)
+    full.set_state(u)
+    t_full, _ = full.step(6)
+    ref = full.get_state().cpu().numpy()
+    budget_full = full.energy_budget()
+    full.close()
+    first = AdiabaticSolver(N, k, gamma=g, precision=prec)
+    first.set_forcing(cs_ref=cs, **fo)
+    first.set_reset(cs)
+    first.set_state(u)
+    first.step(3)
+    ck_state = first.get_state().cpu().numpy().copy()
+    ck_meta = first.get_meta()
+    first.close()
+    assert ck_meta.m.steps == 3 and ck_meta.injected > 0 and ck_meta.m.forcing_on == 1
+    second = AdiabaticSolver(N, k, gamma=g, precision=prec)
+    second.set_forcing(cs_ref=cs, **fo)
+    second.set_reset(cs)
+    second.set_state(ck_state)
+    second.set_meta(ck_meta)
+    t_res, _ = second.step(3)
+    got = second.get_state().cpu().numpy()
+    assert second.get_meta().m.steps == 6
+    assert t_res == t_full
+    assert np.array_equal(got, ref)
+    assert second.energy_budget() == budget_full
+    # a metadata record of other driven modes is refused
+    other = AdiabaticSolver(N, k, gamma=g, precision=prec)
+    other.set_forcing(cs_ref=cs, mach=2.0, zeta=0.5, seed=9, kmax2=4)
+    with pytest.raises(RuntimeError):
+        other.set_meta(ck_meta)
+    other.close()
+    second.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_rhs_parity_hllc(k, prec):
     N = 5
