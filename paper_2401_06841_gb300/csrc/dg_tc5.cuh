@@ -38,6 +38,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
     return d;
 }
 
+// the descriptor of the same layout `off` bytes further (off a multiple of 16;
+// shared-memory addresses stay below 2^18, so the start-address field does not
+// carry): one add per product instead of a descriptor built from scratch
+__device__ __forceinline__ uint64_t dadd(uint64_t d, uint32_t off) { return d + (uint64_t)(off >> 4); }
+
 // instruction descriptor: D FP32, A and B BF16, A/B K-major (0) or MN-major (1)
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn)
 {

@@ -367,22 +367,23 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
         __syncthreads();
         if (tid == 0) {
             tc5::fence_after();
-            const uint32_t sphi = tc5::saddr(sm + V::oPhi), seb = tc5::saddr(sW);
+            const uint64_t dphi = tc5::sdesc(tc5::saddr(sm + V::oPhi), 128, 512);
+            const uint64_t deb = tc5::sdesc(tc5::saddr(sW), 128, 512);
             // blocks j0 .. j0 + nj - 1 into TMEM columns 32 j0 ..
             auto eval = [&](int j0, int nj) {
                 const uint32_t ID = tc5::idesc_bf16(128, 32 * nj, 0, 0);
-                bool acc = false;
+#pragma unroll
                 for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
                     for (int pr = 0; pr < 3; ++pr) {
                         int ca, cb;
                         k5::prod(pr, ca, cb);
-                        const uint32_t ab0 = sphi + (hh == 0 ? 1 + 2 * ca : 2 * ca) * C5::PHI_BLK;
-                        const uint32_t bb0 = seb + (hh * 2 + cb) * V::EB + j0 * 2048;
-                        for (int ks = 0; ks < 2; ++ks) {
-                            tc5::mma(tm + 32 * j0, tc5::sdesc(ab0 + ks * 256, 128, 512),
-                                     tc5::sdesc(bb0 + ks * 256, 128, 512), ID, acc);
-                            acc = true;
-                        }
+                        const uint32_t ao = (hh == 0 ? 1 + 2 * ca : 2 * ca) * C5::PHI_BLK;
+                        const uint32_t bo = (hh * 2 + cb) * V::EB + j0 * 2048;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks)
+                            tc5::mma(tm + 32 * j0, tc5::dadd(dphi, ao + ks * 256), tc5::dadd(deb, bo + ks * 256), ID,
+                                     hh + pr + ks > 0);
                     }
             };
             if (need_div) {
@@ -486,22 +487,26 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
             if (tid == 0) {
                 tc5::fence_after();
                 constexpr uint32_t IDG = tc5::idesc_bf16(64, 32, 1, 0), IDS = tc5::idesc_bf16(64, 32, 1, 1);
-                const uint32_t sw = tc5::saddr(sW), sg = tc5::saddr(sm + V::oG), sphi = tc5::saddr(sm + V::oPhi);
+                const uint64_t dw = tc5::sdesc(tc5::saddr(sW), 1024, 128);
+                const uint64_t dg = tc5::sdesc(tc5::saddr(sm + V::oG), 128, 1024);
+                const uint64_t dpm = tc5::sdesc(tc5::saddr(sm + V::oPhi), 512, 128);
+#pragma unroll
                 for (int sl = 0; sl < 2; ++sl) {
                     const int d = 2 * rnd + sl;
                     if (d == 3 && !force && !PROJ) break;
+#pragma unroll
                     for (int pr = 0; pr < 3; ++pr) {
                         int ca, cb;
                         k5::prod(pr, ca, cb);
+#pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
-                            const uint64_t ad = tc5::sdesc(sw + ca * V::PA + (8 * sl + 2 * ks) * 1024, 1024, 128);
+                            const uint64_t ad = tc5::dadd(dw, ca * V::PA + (8 * sl + 2 * ks) * 1024);
                             const bool acc = !(rnd == 0 && sl == 0 && pr == 0 && ks == 0);
                             if (d < 3)
-                                tc5::mma(tm + 96, ad, tc5::sdesc(sg + (d * 2 + cb) * C5::G_BLK + ks * 256, 128, 1024),
-                                         IDG, acc);
+                                tc5::mma(tm + 96, ad, tc5::dadd(dg, (d * 2 + cb) * C5::G_BLK + ks * 256), IDG, acc);
                             else
                                 tc5::mma(PROJ ? tm + 128 : tm + 96, ad,
-                                         tc5::sdesc(sphi + (1 + 2 * cb) * C5::PHI_BLK + ks * 1024, 512, 128), IDS,
+                                         tc5::dadd(dpm, (1 + 2 * cb) * C5::PHI_BLK + ks * 1024), IDS,
                                          PROJ ? (pr + ks > 0) : acc);
                         }
                     }
@@ -691,27 +696,35 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
         if (tid == 0) {
             tc5::fence_after();
             constexpr uint32_t ID = tc5::idesc_bf16(128, 64, 0, 0);
-            const uint32_t sf = tc5::saddr(sm + Fc::oF), ss = tc5::saddr(sSelf), sn = tc5::saddr(sNbr);
+            const uint64_t df = tc5::sdesc(tc5::saddr(sm + Fc::oF), 128, 512);
+            const uint64_t ds = tc5::sdesc(tc5::saddr(sSelf), 128, 512);
+            const uint64_t dn = tc5::sdesc(tc5::saddr(sNbr), 128, 512);
             // self traces on all six faces (table rows from 16)
+#pragma unroll
             for (int pr = 0; pr < 3; ++pr) {
                 int ca, cb;
                 k5::prod(pr, ca, cb);
+#pragma unroll
                 for (int ks = 0; ks < 2; ++ks)
-                    tc5::mma(tm, tc5::sdesc(sf + ca * C5::F_BLK + 2 * 512 + ks * 256, 128, 512),
-                             tc5::sdesc(ss + cb * Fc::SB + ks * 256, 128, 512), ID, pr + ks > 0);
+                    tc5::mma(tm, tc5::dadd(df, ca * C5::F_BLK + 2 * 512 + ks * 256), tc5::dadd(ds, cb * Fc::SB + ks * 256),
+                             ID, pr + ks > 0);
             }
             // neighbour across F: its trace on the opposite face, into the lanes of F
+#pragma unroll
             for (int F = 0; F < 6; ++F) {
                 const int row0 = (F & 1) ? 0 : 32;  // 16 + 16 (opp(F) - F)
-                uint32_t mk[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-                mk[F >> 1] = (F & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+                const uint32_t m0 = F >> 1 == 0 ? ((F & 1) ? 0x0000FFFFu : 0xFFFF0000u) : 0xFFFFFFFFu;
+                const uint32_t m1 = F >> 1 == 1 ? ((F & 1) ? 0x0000FFFFu : 0xFFFF0000u) : 0xFFFFFFFFu;
+                const uint32_t m2 = F >> 1 == 2 ? ((F & 1) ? 0x0000FFFFu : 0xFFFF0000u) : 0xFFFFFFFFu;
+#pragma unroll
                 for (int pr = 0; pr < 3; ++pr) {
                     int ca, cb;
                     k5::prod(pr, ca, cb);
+#pragma unroll
                     for (int ks = 0; ks < 2; ++ks)
-                        tc5::mma_masked(tm + 64, tc5::sdesc(sf + ca * C5::F_BLK + (row0 / 8) * 512 + ks * 256, 128, 512),
-                                        tc5::sdesc(sn + (2 * F + cb) * Fc::SB + ks * 256, 128, 512), ID, pr + ks > 0,
-                                        mk[0], mk[1], mk[2], mk[3]);
+                        tc5::mma_masked(tm + 64, tc5::dadd(df, ca * C5::F_BLK + (row0 / 8) * 512 + ks * 256),
+                                        tc5::dadd(dn, (2 * F + cb) * Fc::SB + ks * 256), ID, pr + ks > 0, m0, m1, m2,
+                                        0xFFFFFFFFu);
                 }
             }
             tc5::commit(&bar);
@@ -764,13 +777,16 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
         if (tid == 0) {
             tc5::fence_after();
             constexpr uint32_t ID = tc5::idesc_bf16(64, 32, 1, 1);
-            const uint32_t sf = tc5::saddr(sm + Fc::oF), sl = tc5::saddr(sNbr);
+            const uint64_t dl = tc5::sdesc(tc5::saddr(sNbr), 1024, 128);
+            const uint64_t dfm = tc5::sdesc(tc5::saddr(sm + Fc::oF), 512, 128);
+#pragma unroll
             for (int pr = 0; pr < 3; ++pr) {
                 int ca, cb;
                 k5::prod(pr, ca, cb);
+#pragma unroll
                 for (int ks = 0; ks < 6; ++ks)
-                    tc5::mma(tm + 128, tc5::sdesc(sl + ca * Fc::LA + 2 * ks * 1024, 1024, 128),
-                             tc5::sdesc(sf + cb * C5::F_BLK + 2 * 512 + ks * 1024, 512, 128), ID, pr + ks > 0);
+                    tc5::mma(tm + 128, tc5::dadd(dl, ca * Fc::LA + 2 * ks * 1024),
+                             tc5::dadd(dfm, cb * C5::F_BLK + 2 * 512 + ks * 1024), ID, pr + ks > 0);
             }
             tc5::commit(&bar);
         }
@@ -977,19 +993,18 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
         if (tid == 0) {
             tc5::fence_after();
             constexpr uint32_t ID = tc5::idesc_bf16(128, C5::NEP, 0, 0);
-            const uint32_t sphi = tc5::saddr(sm + P::oPhi), seb = tc5::saddr(sEB);
-            bool acc = false;
+            const uint64_t dphi = tc5::sdesc(tc5::saddr(sm + P::oPhi), 128, 512);
+            const uint64_t deb = tc5::sdesc(tc5::saddr(sEB), 128, 512);
+#pragma unroll
             for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
                 for (int pr = 0; pr < 3; ++pr) {
                     int ca, cb;
                     k5::prod(pr, ca, cb);
-                    const uint32_t ab0 = sphi + (hh == 0 ? 1 + 2 * ca : 2 * ca) * C5::PHI_BLK;
-                    const uint32_t bb0 = seb + (hh * 2 + cb) * P::EB;
-                    for (int ks = 0; ks < 2; ++ks) {
-                        tc5::mma(tm, tc5::sdesc(ab0 + ks * 256, 128, 512), tc5::sdesc(bb0 + ks * 256, 128, 512), ID,
-                                 acc);
-                        acc = true;
-                    }
+                    const uint32_t ao = (hh == 0 ? 1 + 2 * ca : 2 * ca) * C5::PHI_BLK, bo = (hh * 2 + cb) * P::EB;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks)
+                        tc5::mma(tm, tc5::dadd(dphi, ao + ks * 256), tc5::dadd(deb, bo + ks * 256), ID, hh + pr + ks > 0);
                 }
             tc5::commit(&bar);
         }
@@ -1035,13 +1050,16 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
         if (tid == 0) {
             tc5::fence_after();
             constexpr uint32_t ID = tc5::idesc_bf16(64, 32, 1, 1);
-            const uint32_t sphi = tc5::saddr(sm + P::oPhi), spa = tc5::saddr(sPA);
+            const uint64_t dpa = tc5::sdesc(tc5::saddr(sPA), 1024, 128);
+            const uint64_t dpm = tc5::sdesc(tc5::saddr(sm + P::oPhi), 512, 128);
+#pragma unroll
             for (int pr = 0; pr < 3; ++pr) {
                 int ca, cb;
                 k5::prod(pr, ca, cb);
+#pragma unroll
                 for (int ks = 0; ks < 4; ++ks)
-                    tc5::mma(tm + 32, tc5::sdesc(spa + ca * P::PA + 2 * ks * 1024, 1024, 128),
-                             tc5::sdesc(sphi + (1 + 2 * cb) * C5::PHI_BLK + ks * 1024, 512, 128), ID, pr + ks > 0);
+                    tc5::mma(tm + 32, tc5::dadd(dpa, ca * P::PA + 2 * ks * 1024),
+                             tc5::dadd(dpm, (1 + 2 * cb) * C5::PHI_BLK + ks * 1024), ID, pr + ks > 0);
             }
             tc5::commit(&bar);
         }
