@@ -1325,11 +1325,11 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
                 t.ahat = force ? ctx->ahat : nullptr;
                 rk_weights(ctx->rk, s, ctx->prec != DG_PREC_F64, t.rk_a, t.rk_b);
                 // every stage projects its output; the last one for the next step,
-                // with the CFL bound (and |v| in learned mode).  Undriven stages on the
-                // tcgen05 kernels: stages after the first project their own input in
-                // the volume kernel instead (no forcing sums needed), so only the last
+                // with the CFL bound (and |v| in learned mode).  On the tcgen05 kernels
+                // the stages after the first project their own input in the volume
+                // kernel instead (driven: with the forcing sums), so only the last
                 // stage's output gets a projection launch
-                const bool fold = ctx->tc5 && !force;
+                const bool fold = ctx->tc5;
                 t.flags = (force ? F_FORCE : 0) | ((fold && !last) ? 0 : F_NEXTPROJ) | (last ? F_DT : 0) |
                           ((fold && s > 0) ? F_SELFPROJ : 0);
                 t.abar_in = (pb + s) & 1;

@@ -15,7 +15,7 @@ namespace dg {
 
 namespace {
 
-int g_occ_vol[6] = {0, 0, 0, 0, 0, 0}, g_occ_face[3] = {0, 0, 0}, g_occ_proj = 0;
+int g_occ_vol[8] = {0, 0, 0, 0, 0, 0, 0, 0}, g_occ_face[3] = {0, 0, 0}, g_occ_proj = 0;
 
 // scaled Legendre polynomial Pn_m = sqrt(2m+1) P_m and its derivative, by the
 // three-term recurrence and P'_{m+1} = P'_{m-1} + (2m+1) P_m
@@ -146,11 +146,14 @@ static cudaError_t resident_blocks(const void* fn, int dyn_smem, int tmem_cols, 
 cudaError_t tc5_setup()
 {
     cudaError_t e;
-    const void* vol[6] = {(const void*)k5_volume<false, false, false>, (const void*)k5_volume<false, true, false>,
+    const void* vol[8] = {(const void*)k5_volume<false, false, false>, (const void*)k5_volume<false, true, false>,
                           (const void*)k5_volume<true, false, false>,  (const void*)k5_volume<true, true, false>,
-                          (const void*)k5_volume<false, false, true>,  (const void*)k5_volume<false, true, true>};
-    for (int i = 0; i < 6; ++i)
-        if ((e = resident_blocks(vol[i], C5::Vol::total, i < 4 ? C5::TM_VOL : C5::TM_VOLP, g_occ_vol[i]))) return e;
+                          (const void*)k5_volume<false, false, true>,  (const void*)k5_volume<false, true, true>,
+                          (const void*)k5_volume<true, false, true>,   (const void*)k5_volume<true, true, true>};
+    for (int i = 0; i < 8; ++i)
+        if ((e = resident_blocks(vol[i], i < 6 ? C5::Vol::total : C5::Vol::total3, i < 4 ? C5::TM_VOL : C5::TM_VOLP,
+                                 g_occ_vol[i])))
+            return e;
     if ((e = resident_blocks((const void*)k5_faces<0>, C5::Face::total, C5::TM_FACE, g_occ_face[0]))) return e;
     if ((e = resident_blocks((const void*)k5_faces<1>, C5::Face::total, C5::TM_FACE, g_occ_face[1]))) return e;
     if ((e = resident_blocks((const void*)k5_faces<2>, C5::Face::total, C5::TM_FACE, g_occ_face[2]))) return e;
@@ -202,20 +205,27 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
         return cudaGetLastError();
     }
     a.stage = (t.kind == T5_STAGE) ? 1 : 0;
-    // variants: driving (2), gating (1); the self-projection (4) only without driving
-    const bool proj = t.vh_self != nullptr;
-    if (proj && (t.flags & F_FORCE)) return cudaErrorInvalidValue;
+    // variants: gating (1); driving (2), the self-projection (4, 6 driven); a driven
+    // self-projection also reduces the state's mean acceleration into abar_out,
+    // which the face kernel then subtracts (abar_fix, read from abar_in)
+    const bool proj = t.vh_self != nullptr, force = (t.flags & F_FORCE) != 0;
     a.vh_self = static_cast<float*>(t.vh_self);
-    const int vv = proj ? 4 + (L.ph.av_mode != 1 ? 1 : 0) : ((t.flags & F_FORCE) ? 2 : 0) + (L.ph.av_mode != 1 ? 1 : 0);
+    const int gate = L.ph.av_mode != 1 ? 1 : 0;
+    const int vv = proj ? (force ? 6 : 4) + gate : (force ? 2 : 0) + gate;
     const int gv = grid5(ntile, g_occ_vol[vv], L.nsm);
+    const int sv = (proj && force) ? C5::Vol::total3 : C5::Vol::total;
+    if (proj && force) a.abar_out = a.abar_in;
     switch (vv) {
-    case 0: k5_volume<false, false, false><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
-    case 1: k5_volume<false, true, false><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
-    case 2: k5_volume<true, false, false><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
-    case 3: k5_volume<true, true, false><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
-    case 4: k5_volume<false, false, true><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
-    default: k5_volume<false, true, true><<<gv, C5::NT, C5::Vol::total, L.st>>>(a); break;
+    case 0: k5_volume<false, false, false><<<gv, C5::NT, sv, L.st>>>(a); break;
+    case 1: k5_volume<false, true, false><<<gv, C5::NT, sv, L.st>>>(a); break;
+    case 2: k5_volume<true, false, false><<<gv, C5::NT, sv, L.st>>>(a); break;
+    case 3: k5_volume<true, true, false><<<gv, C5::NT, sv, L.st>>>(a); break;
+    case 4: k5_volume<false, false, true><<<gv, C5::NT, sv, L.st>>>(a); break;
+    case 5: k5_volume<false, true, true><<<gv, C5::NT, sv, L.st>>>(a); break;
+    case 6: k5_volume<true, false, true><<<gv, C5::NT, sv, L.st>>>(a); break;
+    default: k5_volume<true, true, true><<<gv, C5::NT, sv, L.st>>>(a); break;
     }
+    a.abar_fix = (proj && force) ? 1 : 0;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int rs = L.ph.riemann;

@@ -63,6 +63,10 @@ struct C5 {
         static constexpr int PA = 16 * 1024;               // volume A per comp: 64 rows x 2 slots x 64 q (MN-major)
         static constexpr int work = (4 * EB > 2 * PA) ? 4 * EB : 2 * PA;
         static constexpr int total = oW + work;
+        // driven stages that project their input: the second round carries three
+        // slots (flux along z, source, projection)
+        static constexpr int PA3 = 24 * 1024;
+        static constexpr int total3 = oW + ((4 * EB > 2 * PA3) ? 4 * EB : 2 * PA3);
     };
     struct Face {  // face table + w_s, self and neighbour operands (the lift operand reuses them), new state
         static constexpr int oF = 0, oWs = szF, oSelf = oWs + 64, SB = 8 * 512;  // [64 rows][32] per comp
@@ -98,9 +102,11 @@ struct T5Args {
     const float* ahat;   // forcing [c][3][b] or nullptr
     const float* nu;     // per-cell coefficient (learned sensor) or nullptr
     float* rvol;         // volume term [c][4][b]
-    float* vh_self;      // projection of v of u_in [c][3][b] by the volume kernel (undriven stages)
+    float* vh_self;      // projection of v of u_in [c][3][b] by the volume kernel (stages after the first)
     float* nu_next;      // projection kernel: learned coefficient of u_in [c] (or nullptr)
     const uint32_t* mlp; // packed network of the learned sensor
+    int abar_fix;        // face kernel: subtract abar_in's mean acceleration times rho_l from the momentum
+                         // right-hand side (the volume kernel's source left it out)
     const unsigned char* tab;  // C5 table block
     const float* phiv;   // [b][nq] phi at the volume points (exact positivity check)
     const float* phif;   // [b][nf] phi at the face points
@@ -234,14 +240,17 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, Ctl* ct
 // --------------------------------------------------------------------------
 // FORCE: the driving source is added (a_h rows, source slot); GATE: the
 // coefficients may vanish on whole tiles (learned sensor, or no viscosity), so
-// that div v is evaluated only where a cell of the tile needs it; PROJ (undriven
-// only): the slot of the source projects v = m/rho of the tile's state onto the
-// basis instead (Sec. 3.2, the primitive projection the face kernel then reads),
-// into an accumulator of its own -- the projection launch between stages drops
+// that div v is evaluated only where a cell of the tile needs it; PROJ: a slot of
+// the second round projects v = m/rho of the tile's state onto the basis (Sec.
+// 3.2, the primitive projection the face kernel then reads) into an accumulator
+// of its own -- the projection launch between stages drops.  Undriven, that slot
+// is the source's; driven, a third slot of the round, and the source leaves out
+// the mean acceleration (which depends on the whole state): the kernel reduces
+// <rho a_h>/<rho> into the abar_out slot and the face kernel subtracts abar rho_l
 template <bool FORCE, bool GATE, bool PROJ>
 __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
 {
-    static_assert(!(FORCE && PROJ), "the source slot carries the projection only without driving");
+    constexpr bool P3 = FORCE && PROJ;  // three slots in the second round
     constexpr int TMC = PROJ ? C5::TM_VOLP : C5::TM_VOL;
     using V = C5::Vol;
     constexpr int TC = C5::TC;
@@ -251,6 +260,8 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     __shared__ uint32_t tslot;
     __shared__ float s_nu[TC];
     __shared__ int s_abort;
+    __shared__ double s_tot[8];
+    constexpr int PAX = P3 ? V::PA3 : V::PA;  // bytes per split component of the round operand
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     k5::copy16(sm + V::oPhi, a.tab + C5::oPhi, C5::szPhi + C5::szG);
     if (tid < 64) reinterpret_cast<float*>(sm + V::oWq)[tid] = reinterpret_cast<const float*>(a.tab + C5::oWq)[tid];
@@ -276,8 +287,9 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     const AvCoef<float> avc = av_coef<float>(a.ph, dtd);
     const float two_h = (float)(2.0 / a.ph.h), i4h = (float)(0.25 / a.ph.h), cs2 = (float)a.ph.cs2;
     float ab[3] = {0.f, 0.f, 0.f};
-    if (force)
+    if (force && !P3)
         for (int i = 0; i < 3; ++i) ab[i] = (float)a.ctl->abar2[a.abar_in][i];
+    double sums[4] = {0.0, 0.0, 0.0, 0.0};  // P3: <rho a_h> (3) and <rho> of the thread's (cell, component)
     // point-major thread: TMEM lane r = 32 (w % 4) + lane = (h, q); pairs p = 4 (w / 4) + 0..3
     const int qw = w & 3, hp = w >> 2, r = 32 * qw + lane, h = r >> 6, q = r & 63;
     const uint32_t tl = tc5::tmem_addr(tm, 32 * qw, 0);
@@ -316,6 +328,19 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
             inflight |= 1u << (cur ^ 1);
         }
         ++ntiles;
+        if (P3 && tid < TC * 3) {
+            // per-cell forcing sums <rho a_h> = sum_l rho_l a_l (orthonormal basis) and <rho>
+            const int c = tid / 3, i = tid % 3;
+            if (c < k5::tile_cells(a.ncell, tile * TC)) {
+                const float* u = sUb + cur * TC * 80 + c * 80;
+                const float* ah = sAhb + cur * TC * 60 + c * 60 + i * 20;
+                float sacc = 0.f;
+#pragma unroll
+                for (int l = 0; l < 20; ++l) sacc += u[l] * ah[l];
+                sums[i] += (double)sacc;
+                if (i == 0) sums[3] += (double)u[0];
+            }
+        }
         const float* sU = sUb + cur * TC * 80;
         const float* sAh = sAhb + cur * TC * 60;
         // the divergence rows and the viscous pressure are needed unless every
@@ -441,12 +466,15 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
         tc5::fence_before();
         // ---- volume operand, two slots per round (slot d < 3: flux along d /(4h);
         // slot 3: source w_q/8), rows m = 32 h + 4 p + v, MN-major ----
+        // slot kinds: 0 flux along d, 1 source, 2 projection of v, -1 none
+        auto kind = [](int d) { return d < 3 ? 0 : d == 3 ? (FORCE ? 1 : (PROJ ? 2 : -1)) : (P3 ? 2 : -1); };
         auto volume_round = [&](auto R_) -> bool {
             constexpr int rnd = decltype(R_)::value;
+            constexpr int NSL = (rnd == 1 && P3) ? 3 : 2;
 #pragma unroll
-            for (int sl = 0; sl < 2; ++sl) {
-                const int d = 2 * rnd + sl, k = 64 * sl + q;
-                if (d == 3 && !force && !PROJ) break;  // no source without driving
+            for (int sl = 0; sl < NSL; ++sl) {
+                const int d = 2 * rnd + sl, k = 64 * sl + q, kd = kind(d);
+                if (kd < 0) break;  // no source without driving
 #pragma unroll
                 for (int pp = 0; pp < 4; pp += 2) {
                     float x[8];
@@ -454,13 +482,13 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                     for (int e = 0; e < 2; ++e) {
                         const float* s = st[pp + e];
                         float* y = x + 4 * e;
-                        if (d < 3) {
+                        if (kd == 0) {
                             const float vd = s[4 + d];
                             y[0] = s[1 + d] * i4h;
                             y[1] = (s[1] * vd + (d == 0 ? s[7] : 0.f)) * i4h;
                             y[2] = (s[2] * vd + (d == 1 ? s[7] : 0.f)) * i4h;
                             y[3] = (s[3] * vd + (d == 2 ? s[7] : 0.f)) * i4h;
-                        } else if (PROJ) {
+                        } else if (kd == 2) {
                             // rows i = v_x, v_y, v_z, (none) weighted by w_q/8
                             y[0] = s[4] * wq8;
                             y[1] = s[5] * wq8;
@@ -478,7 +506,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                     const int p = 4 * hp + pp;
                     const int o = (4 * h + (p >> 1)) * 128 + (k >> 3) * 1024 + (k & 7) * 16;
                     *reinterpret_cast<uint4*>(sW + o) = hi;
-                    *reinterpret_cast<uint4*>(sW + V::PA + o) = lo;
+                    *reinterpret_cast<uint4*>(sW + PAX + o) = lo;
                 }
             }
             tc5::fence_async_smem();
@@ -491,23 +519,23 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
                 const uint64_t dg = tc5::sdesc(tc5::saddr(sm + V::oG), 128, 1024);
                 const uint64_t dpm = tc5::sdesc(tc5::saddr(sm + V::oPhi), 512, 128);
 #pragma unroll
-                for (int sl = 0; sl < 2; ++sl) {
-                    const int d = 2 * rnd + sl;
-                    if (d == 3 && !force && !PROJ) break;
+                for (int sl = 0; sl < NSL; ++sl) {
+                    const int d = 2 * rnd + sl, kd = kind(d);
+                    if (kd < 0) break;
 #pragma unroll
                     for (int pr = 0; pr < 3; ++pr) {
                         int ca, cb;
                         k5::prod(pr, ca, cb);
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
-                            const uint64_t ad = tc5::dadd(dw, ca * V::PA + (8 * sl + 2 * ks) * 1024);
+                            const uint64_t ad = tc5::dadd(dw, ca * PAX + (8 * sl + 2 * ks) * 1024);
                             const bool acc = !(rnd == 0 && sl == 0 && pr == 0 && ks == 0);
-                            if (d < 3)
+                            if (kd == 0)
                                 tc5::mma(tm + 96, ad, tc5::dadd(dg, (d * 2 + cb) * C5::G_BLK + ks * 256), IDG, acc);
                             else
-                                tc5::mma(PROJ ? tm + 128 : tm + 96, ad,
+                                tc5::mma(kd == 2 ? tm + 128 : tm + 96, ad,
                                          tc5::dadd(dpm, (1 + 2 * cb) * C5::PHI_BLK + ks * 1024), IDS,
-                                         PROJ ? (pr + ks > 0) : acc);
+                                         kd == 2 ? (pr + ks > 0) : acc);
                         }
                     }
                 }
@@ -565,6 +593,25 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
     __syncthreads();
     tc5::fence_after();
     if (w == 0) tc5::tmem_dealloc(tm, TMC);
+    if constexpr (P3) {
+        // mean acceleration <rho a_h>/<rho> of this state into the abar_out slot (the
+        // face kernel of the stage subtracts it); the work region is free now
+        double* s_buf = reinterpret_cast<double*>(sW);
+        double mine[4];
+        for (int i = 0; i < 4; ++i) {
+            s_buf[tid] = sums[i];
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int j = 0; j < C5::NT; ++j) t += s_buf[j];
+                mine[i] = t;
+            }
+            __syncthreads();
+        }
+        if (last_block_reduce<C5::NT>(a.partials, mine, 4, &a.ctl->cnt_proj, s_tot, s_buf))
+            if (tid == 0)
+                for (int i = 0; i < 3; ++i) a.ctl->abar2[a.abar_out][i] = s_tot[i] / s_tot[3];
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -616,6 +663,9 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
     const uint32_t tl = tc5::tmem_addr(tm, 32 * qw, 0);
     const long ntile = (a.ncell + TC - 1) / TC;
     const bool need_un = a.stage && a.rk_a != 0.f;
+    float abar_fix[3] = {0.f, 0.f, 0.f};
+    if (a.abar_fix)
+        for (int i = 0; i < 3; ++i) abar_fix[i] = (float)a.ctl->abar2[a.abar_in][i];
     uint32_t eph = 0;
     bool epi_pending = false;  // the epilogue's copies issued and not waited for
     // neighbour cells of the tile's cells: s_nb[16 fi + c] (fi = 0: the cell, fi = F + 1:
@@ -816,6 +866,14 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
                         R[4 * j + 1] += t.y;
                         R[4 * j + 2] += t.z;
                         R[4 * j + 3] += t.w;
+                    }
+                    if (a.abar_fix && v > 0) {
+                        // the source's mean-acceleration part: -abar_i rho_l (the volume
+                        // kernel's quadrature of rho abar against phi_l, orthonormal basis)
+                        const float abv = abar_fix[v - 1];
+                        const float* rho = sEpi + c * 80;
+#pragma unroll
+                        for (int l = 0; l < 20; ++l) R[l] -= abv * rho[l];
                     }
                     if (!a.stage) {
                         float4* o4 = reinterpret_cast<float4*>(a.out + e0);
