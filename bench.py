@@ -175,9 +175,12 @@ def adiabatic_arm(args, dev, seed, flush, world, near_isothermal=False):
     gamma = 1.0001 if near_isothermal else 1.4
     s = AdiabaticSolver(N, k, gamma=gamma, precision="f32", rk_stages=S, device=dev)
     if near_isothermal:
-        s.set_state(I.adiabatic_turbulent_state(N, k, seed=seed + 3, mach=1.0, gamma=gamma))
+        # reset mode: states carry the energy offset e - rho cs^2/(gamma - 1), formed here in FP64
         s.set_forcing(mach=args.mach, zeta=0.5, seed=seed, cs_ref=1.0)
         s.set_reset(1.0)
+        u0 = I.adiabatic_turbulent_state(N, k, seed=seed + 3, mach=1.0, gamma=gamma)
+        u0[:, 4] -= 1.0 / (gamma - 1.0) * u0[:, 0]
+        s.set_state(u0)
     else:
         s.set_state(I.adiabatic_turbulent_state(N, k, seed=seed + 2, mach=0.5))
 

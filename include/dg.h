@@ -476,7 +476,16 @@ int dg_adi_set_forcing(dg_adi_ctx* ctx, const dg_forcing* f, double cs_ref);
 /* cs > 0: after every step the uniform temperature p = cs^2 rho is restored (e
  * becomes the projection of rho cs^2/(gamma-1) + |m|^2/(2 rho)); with gamma
  * close to 1 this emulates the isothermal gas and the thermal energy taken out
- * measures the dissipation (Sec. 4.2).  0: off (default). */
+ * measures the dissipation (Sec. 4.2).  0: off (default).
+ * Energy offset: while cs > 0, the fifth variable of every state that
+ * dg_adi_set_state, dg_adi_get_state, dg_adi_rhs and dg_adi_project take or give
+ * is e - kap rho with kap = cs^2/(gamma - 1) (the energy relative to the
+ * isothermal reference), and the pressure projection is that of p - cs^2 rho:
+ * near gamma = 1 the reference is 1/(gamma - 1) times the kinetic energy, which
+ * single precision would otherwise carry in every coefficient.  The scheme is
+ * linear in the state, so this changes the variables, not the discretisation.
+ * A state already set is carried to the new offset (e += (kap_old - kap) rho);
+ * dg_adi_totals and dg_adi_energy_budget report the energy itself. */
 int dg_adi_set_reset(dg_adi_ctx* ctx, double cs);
 /* out[0] = injected, out[1] = dissipated energy since dg_adi_set_state. */
 int dg_adi_energy_budget(dg_adi_ctx* ctx, double* out);

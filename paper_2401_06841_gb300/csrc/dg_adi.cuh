@@ -30,13 +30,24 @@ namespace dg {
 
 // gas constants in the element type, each rounded once from its double value on
 // the host: near gamma = 1 the difference gamma - 1 formed in single precision
-// would carry the rounding of gamma (float(1.0001) - 1 = 1.000166e-4)
+// would carry the rounding of gamma (float(1.0001) - 1 = 1.000166e-4).
+// Energy offset: the fifth variable is stored as e_s = e - kap rho (kap = cs^2 /
+// (gamma - 1) in reset mode, 0 otherwise), so that the thermal energy of the
+// isothermal reference, 1/(gamma - 1) times larger than the kinetic energy, is
+// not carried in the state: p = (gamma - 1)(e_s - |m|^2/(2 rho)) + c0 rho with
+// c0 = (gamma - 1) kap, the energy flux (e_s + p) v, and the projected pressure
+// is the deviation p - c0 rho.  The scheme is linear in the state, so this is
+// the same discretisation in other variables.
 template <typename T>
 struct AdiGas {
     T gamma;   // gamma
     T g1;      // gamma - 1
     T ig1;     // 1 / (gamma - 1)
     T cth;     // reset mode: cs^2 / (gamma - 1), the thermal energy per unit mass
+    T kap;     // energy offset per unit mass
+    T c0;      // (gamma - 1) kap: the pressure of the offset per unit density
+    T cres;    // cth - kap: the thermal energy per unit mass the reset leaves in e_s
+    T fill_e;  // e_s of the filler state rho = 1, v = 0, p = 1: (1 - c0)/(gamma - 1)
 };
 
 template <typename T>
@@ -93,7 +104,7 @@ struct AdiCfg {
     static constexpr int total = oBig + BIG;
 };
 
-// Rusanov flux along Dd from primitive face states W = (rho, v_x, v_y, v_z, p):
+// Rusanov flux along Dd from primitive face states W = (rho, v_x, v_y, v_z, p - c0 rho):
 // 1/2 (F(U_L) + F(U_R)) - 1/2 lambda (U_R - U_L), lambda = max(|v_n| + c)
 template <typename T, int Dd>
 __device__ __forceinline__ void adi_rusanov(const AdiGas<T>& G, const T* WL, const T* WR, T* F)
@@ -106,12 +117,12 @@ __device__ __forceinline__ void adi_rusanov(const AdiGas<T>& G, const T* WL, con
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const T* w = W[s];
-        const T rho = w[0], vn = w[1 + Dd], p = w[4];
+        const T rho = w[0], vn = w[1 + Dd], p = w[4] + G.c0 * rho;  // w[4]: the pressure deviation
         U[s][0] = rho;
         U[s][1] = rho * w[1];
         U[s][2] = rho * w[2];
         U[s][3] = rho * w[3];
-        U[s][4] = p / g1 + T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        U[s][4] = w[4] / g1 + T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
         Fx[s][0] = U[s][1 + Dd];
         Fx[s][1] = U[s][1] * vn;
         Fx[s][2] = U[s][2] * vn;
@@ -136,18 +147,19 @@ template <typename T, int Dd>
 __device__ __forceinline__ void adi_hllc(const AdiGas<T>& G, const T* WL, const T* WR, T* F)
 {
     const T g1 = G.g1, gamma = G.gamma;
-    T U[2][5], Fx[2][5], c[2], un[2];
+    T U[2][5], Fx[2][5], c[2], un[2], pp[2];
     const T* W[2] = {WL, WR};
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const T* w = W[s];
-        const T rho = w[0], p = w[4];
+        const T rho = w[0], p = w[4] + G.c0 * rho;  // w[4]: the pressure deviation
+        pp[s] = p;
         un[s] = w[1 + Dd];
         U[s][0] = rho;
         U[s][1] = rho * w[1];
         U[s][2] = rho * w[2];
         U[s][3] = rho * w[3];
-        U[s][4] = p / g1 + T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        U[s][4] = w[4] / g1 + T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
         Fx[s][0] = U[s][1 + Dd];
         Fx[s][1] = U[s][1] * un[s];
         Fx[s][2] = U[s][2] * un[s];
@@ -169,10 +181,10 @@ __device__ __forceinline__ void adi_hllc(const AdiGas<T>& G, const T* WL, const 
         return;
     }
     const T qL = WL[0] * (SL - un[0]), qR = WR[0] * (SR - un[1]);
-    const T Ss = (WR[4] - WL[4] + un[0] * qL - un[1] * qR) / (qL - qR);
+    const T Ss = (pp[1] - pp[0] + un[0] * qL - un[1] * qR) / (qL - qR);
     // the side of the contact x/t = 0 lies on (selects keep everything in registers)
     const bool lft = Ss >= T(0);
-    const T SK = lft ? SL : SR, qK = lft ? qL : qR, uK = lft ? un[0] : un[1];
+    const T SK = lft ? SL : SR, qK = lft ? qL : qR, uK = lft ? un[0] : un[1], pK = lft ? pp[0] : pp[1];
     T wK[5], UK[5], FK[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -185,7 +197,7 @@ __device__ __forceinline__ void adi_hllc(const AdiGas<T>& G, const T* WL, const 
     Us[0] = f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) Us[1 + i] = f * (i == Dd ? Ss : wK[1 + i]);
-    Us[4] = f * (UK[4] / wK[0] + (Ss - uK) * (Ss + wK[4] / qK));
+    Us[4] = f * (UK[4] / wK[0] + (Ss - uK) * (Ss + pK / qK));
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
 }
@@ -205,14 +217,17 @@ __device__ __forceinline__ T adi_vnr(const Phys& P, T rho, T c, T divv, T dt)
 }
 
 // smallest t in [0, 1] with p(ub + t d) = eps (p(ub) > eps > p(ub + d)): the
-// root of rho e - |m|^2/2 - eps rho/(gamma-1), quadratic in t
+// root of rho p - eps rho = (gamma-1)(rho e_s - |m|^2/2) + c0 rho^2 - eps rho,
+// quadratic in t
 template <typename T>
 __device__ __forceinline__ T adi_pressure_root(const AdiGas<T>& G, T eps, const T* ub, const T* dv)
 {
-    const T g1 = eps / G.g1;
-    const T A = dv[0] * dv[4] - T(0.5) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[3] * dv[3]);
-    const T B = ub[0] * dv[4] + dv[0] * ub[4] - (ub[1] * dv[1] + ub[2] * dv[2] + ub[3] * dv[3]) - g1 * dv[0];
-    const T C = ub[0] * ub[4] - T(0.5) * (ub[1] * ub[1] + ub[2] * ub[2] + ub[3] * ub[3]) - g1 * ub[0];
+    const T g1 = G.g1, c0 = G.c0;
+    const T A = g1 * (dv[0] * dv[4] - T(0.5) * (dv[1] * dv[1] + dv[2] * dv[2] + dv[3] * dv[3])) + c0 * dv[0] * dv[0];
+    const T B = g1 * (ub[0] * dv[4] + dv[0] * ub[4] - (ub[1] * dv[1] + ub[2] * dv[2] + ub[3] * dv[3])) +
+                T(2) * c0 * ub[0] * dv[0] - eps * dv[0];
+    const T C = g1 * (ub[0] * ub[4] - T(0.5) * (ub[1] * ub[1] + ub[2] * ub[2] + ub[3] * ub[3])) + c0 * ub[0] * ub[0] -
+                eps * ub[0];
     T t;
     if (fabs(A) <= T(1e-14) * (fabs(B) + fabs(C))) {
         t = -C / B;
@@ -228,14 +243,21 @@ __device__ __forceinline__ T adi_pressure_root(const AdiGas<T>& G, T eps, const 
     return t > T(1) ? T(1) : t;
 }
 
+// pressure from the stored variables (e: the offset energy e_s), and its
+// deviation p - c0 rho
 template <typename T>
-__device__ __forceinline__ T adi_p(const AdiGas<T>& G, T rho, T mx, T my, T mz, T e)
+__device__ __forceinline__ T adi_pdev(const AdiGas<T>& G, T rho, T mx, T my, T mz, T e)
 {
     return G.g1 * (e - T(0.5) * (mx * mx + my * my + mz * mz) / rho);
 }
+template <typename T>
+__device__ __forceinline__ T adi_p(const AdiGas<T>& G, T rho, T mx, T my, T mz, T e)
+{
+    return adi_pdev<T>(G, rho, mx, my, mz, e) + G.c0 * rho;
+}
 
 // copy n elements (a multiple of 4) of a tile from global to shared; elements
-// past `valid` get the filler state of a cell (rho = 1, e = 1/(gamma-1): p = 1)
+// past `valid` get the filler state of a cell (rho = 1, v = 0, p = 1)
 template <typename T, int NT, int NV, int B>
 __device__ __forceinline__ void adi_load(T* dst, const T* src, int n, int valid, T fill_e)
 {
@@ -292,9 +314,9 @@ __device__ __forceinline__ void adi_project_tile(T* sm, const T* sU, const T* ta
                 f[it][0] = mx * ir;
                 f[it][1] = my * ir;
                 f[it][2] = mz * ir;
-                f[it][3] = adi_p<T>(a.gas, rho, mx, my, mz, v[4 * LDV]);
+                f[it][3] = adi_pdev<T>(a.gas, rho, mx, my, mz, v[4 * LDV]);  // projected: p - c0 rho
                 if ((a.flags & F_DT) && c < nvalid) {
-                    const T cs = sqrt(gamma * f[it][3] * ir);
+                    const T cs = sqrt(gamma * (f[it][3] + a.gas.c0 * rho) * ir);
                     const T sp = fabs(f[it][0]) + fabs(f[it][1]) + fabs(f[it][2]) + T(3) * cs;
                     smax = sp > smax ? sp : smax;
                 }
@@ -394,7 +416,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
         s_status = 0u;
         s_smax = 0ull;
     }
-    const T gamma = a.gas.gamma, g1 = a.gas.g1, fill_e = a.gas.ig1;
+    const T gamma = a.gas.gamma, g1 = a.gas.g1, fill_e = a.gas.fill_e;
     const T two_h = T(2.0 / a.ph.h), inv4h = T(0.25 / a.ph.h);
     const T eps = T(a.ph.floor_);
     double dtd = a.dt_pimax;
@@ -444,7 +466,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
             __syncthreads();
             mm<T, BK_FMA, TC * 4, NQP, KP, LDA, LDV, NT>(sA, tabs, C::oPhi, sBig);
             __syncthreads();
-            const T cth = a.gas.cth;
+            const T cres = a.gas.cres;
             constexpr int PER = (TC * NQP + NT - 1) / NT;
             T ev[PER];
 #pragma unroll
@@ -456,7 +478,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                     if (q < nq) {
                         const T* v = sBig + (c * 4) * LDV + q;
                         const T rho = v[0], mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV];
-                        ev[it] = rho * cth + T(0.5) * (mx * mx + my * my + mz * mz) / rho;
+                        ev[it] = rho * cres + T(0.5) * (mx * mx + my * my + mz * mz) / rho;
                     }
                 }
             }
@@ -536,7 +558,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                         const T rho = v[0], ir = rcp<T>(rho);
                         const T mx = v[LDV], my = v[2 * LDV], mz = v[3 * LDV], en = v[4 * LDV];
                         const T vx = mx * ir, vy = my * ir, vz = mz * ir;
-                        const T p = g1 * (en - T(0.5) * (mx * vx + my * vy + mz * vz));
+                        const T p = g1 * (en - T(0.5) * (mx * vx + my * vy + mz * vz)) + a.gas.c0 * rho;
                         const T divv = (v[8 * LDV] - (vx * v[5 * LDV] + vy * v[6 * LDV] + vz * v[7 * LDV])) * ir;
                         const T cs = sqrt(gamma * p * ir);
                         const T P = p + adi_vnr<T>(a.ph, rho, cs, divv, dt);
@@ -644,9 +666,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                             for (int l = 0; l < b; ++l) cf[l] = __ldg(src + l);
                         }
                     } else {
-                        // past the end: a quiet filler state (rho = 1, v = 0, p = 1)
+                        // past the end: a quiet filler state (rho = 1, v = 0, p = 1: deviation 1 - c0)
 #pragma unroll
-                        for (int l = 0; l < b; ++l) cf[l] = (l == 0 && (field == 0 || field == 4)) ? T(1) : T(0);
+                        for (int l = 0; l < b; ++l)
+                            cf[l] = l != 0 ? T(0) : field == 0 ? T(1) : field == 4 ? T(1) - a.gas.c0 : T(0);
                     }
                 }
                 T c2[B2K];
@@ -733,14 +756,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 // sufficient condition on the box ubar +- delta: no point can be below a floor
                 bool ok = ub[0] - dl[0] >= eps;
                 if (ok) {
-                    const T lr = ub[0] - dl[0], le = ub[4] - dl[4];
+                    // rho p = (gamma-1)(rho e_s - |m|^2/2) + c0 rho^2 >= eps rho on the box
+                    const T lr = ub[0] - dl[0], ur = ub[0] + dl[0], le = ub[4] - dl[4];
                     T mm2 = T(0);
 #pragma unroll
                     for (int i = 1; i < 4; ++i) {
                         const T mi = fabs(ub[i]) + dl[i];
                         mm2 += mi * mi;
                     }
-                    ok = le > T(0) && lr * le - T(0.5) * mm2 - eps * (ub[0] + dl[0]) / g1 > T(0);
+                    const T re = le >= T(0) ? lr * le : ur * le;
+                    ok = g1 * (re - T(0.5) * mm2) + a.gas.c0 * lr * lr - eps * ur > T(0);
                 }
                 if (ok) continue;
                 // exact check at every volume and face point
@@ -851,13 +876,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
     }
 }
 
-// FP64 totals for the diagnostics: per block [mass, m_x, m_y, m_z, energy,
-// kinetic energy (volume quadrature of |m|^2/(2 rho)), min rho, min p at the
-// volume points], summed over blocks on the host in block order.  Point values
-// in the state's precision, sums in FP64.
+// FP64 totals for the diagnostics: per block [mass, m_x, m_y, m_z, energy of
+// the stored variable (offset energy e_s), kinetic energy (volume quadrature of
+// |m|^2/(2 rho)), min rho, min p at the volume points], summed over blocks on the
+// host in block order.  Point values in the state's precision, sums in FP64; c0 =
+// (gamma - 1) kap the pressure of the energy offset per unit density.
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_adi_totals(const T* __restrict__ u, const T* __restrict__ tab, long ncell,
-                                                   double gamma, double* __restrict__ partials)
+                                                   double gamma, double c0, double* __restrict__ partials)
 {
     using TT = TileTab<K, BK_FMA>;
     constexpr int b = Dims<K>::b, nq = Dims<K>::nq, n = K + 1;
@@ -871,7 +897,7 @@ __global__ void __launch_bounds__(256) k_adi_totals(const T* __restrict__ u, con
     double acc[6] = {0, 0, 0, 0, 0, 0}, rmin = 1e300, pmin = 1e300;
     for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell; c += (long)gridDim.x * blockDim.x) {
         const T* uc = u + c * 5 * b;
-        for (int v = 0; v < 5; ++v) acc[v] += (double)uc[v * b];
+        for (int v = 0; v < 5; ++v) acc[v] += (double)uc[v * b];  // mode 0: the cell mean
         for (int q = 0; q < nq; ++q) {
             T w[5];
             for (int v = 0; v < 5; ++v) {
@@ -881,7 +907,7 @@ __global__ void __launch_bounds__(256) k_adi_totals(const T* __restrict__ u, con
             }
             const double ke = 0.5 * ((double)w[1] * w[1] + (double)w[2] * w[2] + (double)w[3] * w[3]) / (double)w[0];
             acc[5] += s_w[q] * ke;
-            const double p = (gamma - 1.0) * ((double)w[4] - ke);
+            const double p = (gamma - 1.0) * ((double)w[4] - ke) + c0 * (double)w[0];
             rmin = (double)w[0] < rmin ? (double)w[0] : rmin;
             pmin = p < pmin ? p : pmin;
         }

@@ -56,6 +56,10 @@ cudaError_t adi_k(const Launch& L, double gamma, const AdiLaunch& t)
     a.gas.g1 = T(gamma - 1.0);
     a.gas.ig1 = T(1.0 / (gamma - 1.0));
     a.gas.cth = T(t.cs_reset * t.cs_reset / (gamma - 1.0));
+    a.gas.kap = T(t.kap);
+    a.gas.c0 = T((gamma - 1.0) * t.kap);
+    a.gas.cres = T(t.cs_reset * t.cs_reset / (gamma - 1.0) - t.kap);
+    a.gas.fill_e = T((1.0 - (gamma - 1.0) * t.kap) / (gamma - 1.0));
     a.rk_a = T(t.rk_a);
     a.rk_b = T(t.rk_b);
     a.dt_pimax = t.dt_pimax;
@@ -75,7 +79,7 @@ cudaError_t adi_k(const Launch& L, double gamma, const AdiLaunch& t)
 }
 
 template <typename T, int K>
-cudaError_t adi_totals_k(const Launch& L, double gamma, const void* u, double* partials, int* nblocks)
+cudaError_t adi_totals_k(const Launch& L, double gamma, double kap, const void* u, double* partials, int* nblocks)
 {
     long g = (L.ncell + 255) / 256;
     if (g > 4L * L.nsm) g = 4L * L.nsm;
@@ -83,7 +87,7 @@ cudaError_t adi_totals_k(const Launch& L, double gamma, const void* u, double* p
     if (g < 1) g = 1;
     *nblocks = (int)g;
     k_adi_totals<T, K><<<(int)g, 256, 0, L.st>>>(static_cast<const T*>(u), static_cast<const T*>(L.ttab), L.ncell,
-                                                 gamma, partials);
+                                                 gamma, (gamma - 1.0) * kap, partials);
     return cudaGetLastError();
 }
 
@@ -98,11 +102,34 @@ cudaError_t launch_adi(const Launch& L, double gamma, const AdiLaunch& t)
 }
 
 template <typename T>
-cudaError_t launch_adi_totals(const Launch& L, double gamma, const void* u, double* partials, int* nblocks)
+cudaError_t launch_adi_totals(const Launch& L, double gamma, double kap, const void* u, double* partials, int* nblocks)
 {
-    if (L.K == 1) return adi_totals_k<T, 1>(L, gamma, u, partials, nblocks);
-    if (L.K == 2) return adi_totals_k<T, 2>(L, gamma, u, partials, nblocks);
-    return adi_totals_k<T, 3>(L, gamma, u, partials, nblocks);
+    if (L.K == 1) return adi_totals_k<T, 1>(L, gamma, kap, u, partials, nblocks);
+    if (L.K == 2) return adi_totals_k<T, 2>(L, gamma, kap, u, partials, nblocks);
+    return adi_totals_k<T, 3>(L, gamma, kap, u, partials, nblocks);
+}
+
+// e_s += d rho, coefficient by coefficient (a change of the energy offset)
+template <typename T>
+__global__ void k_adi_shift(T* u, long ncell, int b, T d)
+{
+    const long n = ncell * b;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const long c = i / b;
+        const int l = (int)(i % b);
+        u[(c * 5 + 4) * b + l] += d * u[c * 5 * b + l];
+    }
+}
+
+template <typename T>
+cudaError_t launch_adi_shift(const Launch& L, void* u, double d)
+{
+    const int b = (L.K + 1) * (L.K + 2) * (L.K + 3) / 6;
+    long g = (L.ncell * b + 255) / 256;
+    if (g > 8L * L.nsm) g = 8L * L.nsm;
+    if (g < 1) g = 1;
+    k_adi_shift<T><<<(int)g, 256, 0, L.st>>>(static_cast<T*>(u), L.ncell, b, T(d));
+    return cudaGetLastError();
 }
 
 }  // namespace dg

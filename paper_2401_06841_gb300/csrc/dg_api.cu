@@ -1804,6 +1804,7 @@ struct dg_adi_ctx {
     bool forcing_active = false;
     double cs_ref = 0.0;    // sound speed the driving is scaled with
     double cs_reset = 0.0;  // > 0: uniform temperature restored after every step
+    double kap = 0.0;       // energy offset of the stored state (e_s = e - kap rho): cs_reset^2/(gamma - 1)
     double injected = 0.0, dissipated = 0.0;
     char* scratch = nullptr;
     Ctl* ctl = nullptr;
@@ -1894,7 +1895,9 @@ Launch adi_make_launch(const dg_adi_ctx* c)
 cudaError_t adi_go(const dg_adi_ctx* c, const AdiLaunch& t)
 {
     const Launch L = adi_make_launch(c);
-    return c->prec == DG_PREC_F64 ? launch_adi<double>(L, c->gamma, t) : launch_adi<float>(L, c->gamma, t);
+    AdiLaunch u = t;
+    u.kap = c->kap;
+    return c->prec == DG_PREC_F64 ? launch_adi<double>(L, c->gamma, u) : launch_adi<float>(L, c->gamma, u);
 }
 
 }  // namespace
@@ -2205,6 +2208,17 @@ int dg_adi_set_reset(dg_adi_ctx* ctx, double cs)
     if (!ctx) return DG_EINVAL;
     if (!(cs >= 0.0)) return afail(ctx, DG_EINVAL, "dg_adi_set_reset: negative sound speed");
     ctx->cs_reset = cs;
+    // the energy offset of the stored state follows the reset's thermal energy; a
+    // state already set is carried over to the new offset
+    const double kap = cs > 0.0 ? cs * cs / (ctx->gamma - 1.0) : 0.0;
+    if (ctx->state_set && kap != ctx->kap) {
+        const Launch L = adi_make_launch(ctx);
+        void* u = ctx->reg[ctx->cur];
+        ACK(ctx->prec == DG_PREC_F64 ? launch_adi_shift<double>(L, u, ctx->kap - kap)
+                                     : launch_adi_shift<float>(L, u, ctx->kap - kap));
+        ACK(cudaStreamSynchronize(ctx->st));
+    }
+    ctx->kap = kap;
     return DG_OK;
 }
 
@@ -2267,8 +2281,8 @@ int dg_adi_totals(dg_adi_ctx* ctx, double* out)
     const Launch L = adi_make_launch(ctx);
     int nb = 0;
     const void* u = ctx->reg[ctx->cur];
-    ACK(ctx->prec == DG_PREC_F64 ? launch_adi_totals<double>(L, ctx->gamma, u, ctx->partials, &nb)
-                                 : launch_adi_totals<float>(L, ctx->gamma, u, ctx->partials, &nb));
+    ACK(ctx->prec == DG_PREC_F64 ? launch_adi_totals<double>(L, ctx->gamma, ctx->kap, u, ctx->partials, &nb)
+                                 : launch_adi_totals<float>(L, ctx->gamma, ctx->kap, u, ctx->partials, &nb));
     std::vector<double> part((size_t)nb * 8);
     ACK(cudaMemcpyAsync(part.data(), ctx->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     ACK(cudaStreamSynchronize(ctx->st));
@@ -2282,6 +2296,8 @@ int dg_adi_totals(dg_adi_ctx* ctx, double* out)
             else
                 acc[i] = v < acc[i] ? v : acc[i];
         }
+    // the energy: that of the stored variable plus the offset's kap times the mass
+    acc[4] += ctx->kap * acc[0];
     for (int i = 0; i < 6; ++i) out[i] = acc[i] * vol;
     out[6] = acc[6];
     out[7] = acc[7];

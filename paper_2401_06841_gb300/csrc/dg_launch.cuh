@@ -108,13 +108,17 @@ struct AdiLaunch {
     int abar_in, abar_out;  // ctl->abar2 slots
     double beta;            // stage weight of the injected energy
     double cs_reset;        // reset mode
+    double kap;             // energy offset of the stored states: e_s = e - kap rho
 };
 template <typename T>
 cudaError_t launch_adi(const Launch& L, double gamma, const AdiLaunch& t);
 // per-block FP64 totals [nblocks][8]: mass, momentum (3), energy, kinetic
 // energy, min rho and min p at the volume points
 template <typename T>
-cudaError_t launch_adi_totals(const Launch& L, double gamma, const void* u, double* partials, int* nblocks);
+cudaError_t launch_adi_totals(const Launch& L, double gamma, double kap, const void* u, double* partials, int* nblocks);
+// e_s += d rho on a state (a change of the energy offset)
+template <typename T>
+cudaError_t launch_adi_shift(const Launch& L, void* u, double d);
 
 // turbulence statistics (dg_analysis.cu)
 template <typename T>
