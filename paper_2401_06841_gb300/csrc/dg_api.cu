@@ -598,6 +598,7 @@ struct dg_ctx {
     // x3 at order 3: tcgen05 kernels (volume, faces, projection)
     bool tc5 = false;
     void* t5tab = nullptr;
+    T5Maps t5maps{};  // tiled TMA descriptors of the state registers, rvol and a_h (tcgen05 kernels)
     void* rvol = nullptr;
     int mlp_D = 0, mlp_P = 0;
     long adam_t = 0;
@@ -795,6 +796,7 @@ cudaError_t tile_tc5(dg_ctx* c, const TileLaunch& t)
     using TT = TileTab<3, BK_X3>;
     T5Launch p{};
     p.tab5 = c->t5tab;
+    p.maps = &c->t5maps;
     p.rvol = c->rvol;
     p.phiv = static_cast<const float*>(c->ttab) + TT::phiv;
     p.phif = static_cast<const float*>(c->ttab) + TT::phif;
@@ -1072,6 +1074,12 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = (ctx->prec == DG_PREC_F64) ? setup_kernels<double>(order) : setup_kernels<float>(order);
     if (e == cudaSuccess && ctx->tc5) e = tc5_setup();
+    if (e == cudaSuccess && ctx->tc5) {
+        // whole tiles by tiled TMA loads (1D bulk copies where no descriptor could be made)
+        const void* bases[5] = {ctx->reg[0], ctx->reg[1], ctx->reg[2], ctx->rvol, ctx->ahat};
+        const int per[5] = {80, 80, 80, 80, 60};
+        if (tc5_make_maps(&ctx->t5maps, bases, per, 5, ctx->ncell) != cudaSuccess) ctx->t5maps.n = 0;
+    }
     if (e != cudaSuccess) {
         fprintf(stderr, "dg_init: %s\n", cudaGetErrorString(e));
         delete ctx;

@@ -62,6 +62,21 @@ cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB);
 // projection kernel, or the volume and face kernels of a right-hand side /
 // an SSP-RK stage
 enum { T5_PROJECT = 0, T5_RHS = 1, T5_STAGE = 2 };
+// tiled TMA descriptors (CUtensorMap, 128 bytes each) of the buffers whose whole
+// tiles the tcgen05 kernels stage: a context's state registers, the volume term
+// and the driving; a launch finds them by base address
+struct T5Map {
+    const void* base;
+    alignas(64) unsigned char map[128];
+};
+struct T5Maps {
+    int n;
+    T5Map m[8];
+};
+// one map per buffer [ncell][per] FP32 (boxes of 16 cells); DG_EINVAL-like
+// cudaErrorInvalidValue when the driver's encoder is missing or refuses
+cudaError_t tc5_make_maps(T5Maps* out, const void* const* bases, const int* per, int n, long ncell);
+
 struct T5Launch {
     int kind;
     const void* u_in;
@@ -76,6 +91,7 @@ struct T5Launch {
     void* vh_self;       // undriven stages: the volume kernel projects v of u_in here (or nullptr)
     float* nu_next;      // projection: the learned sensor's coefficient of u_in (or nullptr)
     const uint32_t* mlp; // its packed network
+    const T5Maps* maps;  // tiled TMA descriptors of the context's buffers (or nullptr)
     const void* tab5;    // table block (tc5_build_tables)
     const void* phiv;    // [b][nq] FP32 phi at the volume points
     const void* phif;    // [b][nf] FP32 phi at the face points

@@ -2,6 +2,8 @@
 // block (basis values at the volume and face Gauss points, weighted basis
 // derivatives, quadrature weights) in the operand layouts of the products,
 // kernel set-up and launches.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -160,6 +162,58 @@ cudaError_t tc5_setup()
     return resident_blocks((const void*)k5_project, C5::Proj::total, C5::TM_PROJ, g_occ_proj);
 }
 
+// the driver's tensor-map encoder, found once through the runtime (no link to the
+// driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+cudaError_t tc5_make_maps(T5Maps* out, const void* const* bases, const int* per, int n, long ncell)
+{
+    static_assert(sizeof(CUtensorMap) == sizeof(T5Map::map), "tensor map size");
+    out->n = 0;
+    if (n > 8 || ncell < C5::TC || ncell > 0x7fffffffL) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    if (!enc) return cudaErrorInvalidValue;
+    for (int i = 0; i < n; ++i) {
+        // rows of `per` floats, boxes of 16 rows: the row pitch and the box's inner
+        // extent are multiples of 16 bytes, the base 256-byte aligned by the caller
+        if ((reinterpret_cast<uintptr_t>(bases[i]) & 15u) || (per[i] * 4) % 16) return cudaErrorInvalidValue;
+        const cuuint64_t dims[2] = {(cuuint64_t)per[i], (cuuint64_t)ncell};
+        const cuuint64_t strides[1] = {(cuuint64_t)per[i] * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)per[i], (cuuint32_t)C5::TC};
+        const cuuint32_t es[2] = {1, 1};
+        CUtensorMap* m = reinterpret_cast<CUtensorMap*>(out->m[i].map);
+        if (enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(bases[i]), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        out->m[i].base = bases[i];
+    }
+    out->n = n;
+    return cudaSuccess;
+}
+
+static const CUtensorMap* find_map(const T5Maps* maps, const void* p)
+{
+    if (!maps || !p) return nullptr;
+    for (int i = 0; i < maps->n; ++i)
+        if (maps->m[i].base == p) return reinterpret_cast<const CUtensorMap*>(maps->m[i].map);
+    return nullptr;
+}
+
 static int grid5(long ntile, int occ, int nsm)
 {
     long g = (long)(occ > 0 ? occ : 1) * nsm;
@@ -197,6 +251,12 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
     a.abar_out = t.abar_out;
     a.nu_next = t.nu_next;
     a.mlp = t.mlp;
+    // tiled TMA descriptors of the buffers whose whole tiles the kernels stage
+    a.tmask = 0;
+    if (const CUtensorMap* m = find_map(t.maps, t.u_in)) { a.tu = *m; a.tmask |= 1; }
+    if (const CUtensorMap* m = find_map(t.maps, t.u_n)) { a.tn = *m; a.tmask |= 2; }
+    if (const CUtensorMap* m = find_map(t.maps, t.rvol)) { a.tr = *m; a.tmask |= 4; }
+    if (const CUtensorMap* m = find_map(t.maps, t.ahat)) { a.ta = *m; a.tmask |= 8; }
     if (t.nu_next && (t.kind != T5_PROJECT || !t.mlp)) return cudaErrorInvalidValue;
     if ((t.flags & F_FORCE) && !t.ahat) return cudaErrorInvalidValue;
     const long ntile = (L.ncell + C5::TC - 1) / C5::TC;

@@ -19,6 +19,7 @@
 // every term accumulated in FP32 in TMEM.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cstdint>
 
@@ -112,6 +113,17 @@ __device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, uint32_t 
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(saddr(smem)),
         "l"(gmem), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+
+// tiled TMA load of the box at (x, y) of a 2D tensor map (the map in kernel
+// parameter space: a __grid_constant__ argument), completing on the mbarrier
+__device__ __forceinline__ void tma_2d(void* smem, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(saddr(smem)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
         : "memory");
 }
 

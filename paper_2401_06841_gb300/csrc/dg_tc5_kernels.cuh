@@ -73,7 +73,8 @@ struct C5 {
         static constexpr int oNbr = oSelf + 2 * SB;        // [face][comp]
         static constexpr int LA = 12 * 1024;               // lift A per comp: 64 rows x 96 (MN-major)
         static constexpr int oNew = oNbr + 12 * SB;
-        static constexpr int oEpi = oNew + TC * 80 * 4;    // u^(s), u^n, rvol of the tile, fetched asynchronously
+        static constexpr int oEpi = (oNew + TC * 80 * 4 + 127) / 128 * 128;  // u^(s), u^n, rvol of the tile, fetched
+                                                                        // asynchronously (128-byte aligned: TMA)
         static constexpr int total = oEpi + 3 * TC * 80 * 4;
         // the next tile's rows (self and six neighbours: rho 20, v 60 floats per
         // cell) land by asynchronous copies in the self and neighbour operand
@@ -82,12 +83,17 @@ struct C5 {
         static_assert(7 * TC * RAWS * 4 <= 14 * SB, "staging fits the operand region");
         static_assert(oSelf % 16 == 0 && (RAWS * 4) % 16 == 0, "16-byte copies");
     };
+    // tiled TMA destinations are 128-byte aligned (the dynamic shared memory starts 1024-aligned)
+    static_assert((Vol::oU % 128) == 0 && (Vol::oAh % 128) == 0 && ((TC * 80 * 4) % 128) == 0 &&
+                      ((TC * 60 * 4) % 128) == 0 && (Face::oEpi % 128) == 0,
+                  "TMA destinations");
     struct Proj {  // Phi + w_q, the tile, evaluation B, projection A
         static constexpr int oPhi = 0, oWq = szPhi, oU = oWq + 256, oAh = oU + 2 * TC * 80 * 4;  // u, a_h: double
         static constexpr int oEB = oAh + 2 * TC * 60 * 4, EB = 4 * 512;
         static constexpr int oPA = oEB + 4 * EB, PA = 8 * 1024;  // 64 rows x 64 q (MN-major)
         static constexpr int total = oPA + 2 * PA;
     };
+    static_assert((Proj::oU % 128) == 0 && (Proj::oAh % 128) == 0, "TMA destinations");
 };
 
 #define DG_ST_TIMEOUT_ 8u
@@ -107,6 +113,8 @@ struct T5Args {
     const uint32_t* mlp; // packed network of the learned sensor
     int abar_fix;        // face kernel: subtract abar_in's mean acceleration times rho_l from the momentum
                          // right-hand side (the volume kernel's source left it out)
+    int tmask;           // tiled TMA descriptors present: 1 u_in, 2 u_n, 4 rvol, 8 ahat
+    CUtensorMap tu, tn, tr, ta;  // of u_in, u_n, rvol [c][80] and ahat [c][60]: boxes of 16 cells
     const unsigned char* tab;  // C5 table block
     const float* phiv;   // [b][nq] phi at the volume points (exact positivity check)
     const float* phif;   // [b][nf] phi at the face points
@@ -162,6 +170,16 @@ __device__ __forceinline__ uint32_t bulk_tile(float* s, const float* g, long c0,
     const uint32_t bytes = (uint32_t)(nvalid * per * 4);
     tc5::bulk_g2s(s, g + c0 * per, bytes, bar);
     return bytes;
+}
+// the same for a full tile through a tiled TMA descriptor when there is one
+// (the box of 16 cells at row c0), else the 1D bulk copy
+__device__ __forceinline__ void tile_copy(float* s, const float* g, const CUtensorMap* map, bool use_map, long c0,
+                                          int nvalid, int per, uint64_t* bar)
+{
+    if (use_map && nvalid == C5::TC)
+        tc5::tma_2d(s, map, 0, (int)c0, bar);
+    else
+        bulk_tile(s, g, c0, nvalid, per, bar);
 }
 // the filler of the cells past the end (plain stores of all threads)
 __device__ __forceinline__ void fill_tail(float* s, int nvalid, int per, float fill0)
@@ -248,7 +266,7 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, Ctl* ct
 // the mean acceleration (which depends on the whole state): the kernel reduces
 // <rho a_h>/<rho> into the abar_out slot and the face kernel subtracts abar rho_l
 template <bool FORCE, bool GATE, bool PROJ>
-__global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
+__global__ void __launch_bounds__(256, 2) k5_volume(const __grid_constant__ T5Args a)
 {
     constexpr bool P3 = FORCE && PROJ;  // three slots in the second round
     constexpr int TMC = PROJ ? C5::TM_VOLP : C5::TM_VOL;
@@ -306,8 +324,8 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
         if (tid == 0) {
             tc5::fence_async_smem();
             tc5::mbar_expect_tx(&lbar[buf], (uint32_t)(nv * 80 * 4 + (force ? nv * 60 * 4 : 0)));
-            k5::bulk_tile(su, a.u_in, cb, nv, 80, &lbar[buf]);
-            if (force) k5::bulk_tile(sa, a.ahat, cb, nv, 60, &lbar[buf]);
+            k5::tile_copy(su, a.u_in, &a.tu, a.tmask & 1, cb, nv, 80, &lbar[buf]);
+            if (force) k5::tile_copy(sa, a.ahat, &a.ta, a.tmask & 8, cb, nv, 60, &lbar[buf]);
         }
     };
     if (blockIdx.x < ntile) fetch(blockIdx.x, 0);
@@ -619,7 +637,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(T5Args a)
 // --------------------------------------------------------------------------
 // RS: the face flux (0 Rusanov, 1 HLL, 2 HLLC), one instantiation each
 template <int RS>
-__global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
+__global__ void __launch_bounds__(256, 2) k5_faces(const __grid_constant__ T5Args a)
 {
     using Fc = C5::Face;
     constexpr int TC = C5::TC, b = C5::b, nq = C5::nq, nf = 96;
@@ -702,9 +720,9 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
         if (tid == 0) {
             tc5::fence_async_smem();
             tc5::mbar_expect_tx(&ebar, (uint32_t)(nvalid * 80 * 4 * (need_un ? 3 : 2)));
-            k5::bulk_tile(sEpi, a.u_in, c0, nvalid, 80, &ebar);
-            if (need_un) k5::bulk_tile(sEpi + TC * 80, a.u_n, c0, nvalid, 80, &ebar);
-            k5::bulk_tile(sEpi + 2 * TC * 80, a.rvol, c0, nvalid, 80, &ebar);
+            k5::tile_copy(sEpi, a.u_in, &a.tu, a.tmask & 1, c0, nvalid, 80, &ebar);
+            if (need_un) k5::tile_copy(sEpi + TC * 80, a.u_n, &a.tn, a.tmask & 2, c0, nvalid, 80, &ebar);
+            k5::tile_copy(sEpi + 2 * TC * 80, a.rvol, &a.tr, a.tmask & 4, c0, nvalid, 80, &ebar);
         }
         epi_pending = true;
         // ---- operands: rows 4 c + fld (rho, v_x, v_y, v_z) of each cell (self) and
@@ -970,7 +988,7 @@ __global__ void __launch_bounds__(256, 2) k5_faces(T5Args a)
 // --------------------------------------------------------------------------
 // projection of v (and |v|) of a state, CFL bound, forcing sums
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
+__global__ void __launch_bounds__(256, 3) k5_project(const __grid_constant__ T5Args a)
 {
     using P = C5::Proj;
     constexpr int TC = C5::TC, NT = C5::NT;
@@ -1021,8 +1039,8 @@ __global__ void __launch_bounds__(256, 3) k5_project(T5Args a)
         if (tid == 0) {
             tc5::fence_async_smem();
             tc5::mbar_expect_tx(&lbar[buf], (uint32_t)(nv * 80 * 4 + (force ? nv * 60 * 4 : 0)));
-            k5::bulk_tile(su, a.u_in, cb, nv, 80, &lbar[buf]);
-            if (force) k5::bulk_tile(sa, a.ahat, cb, nv, 60, &lbar[buf]);
+            k5::tile_copy(su, a.u_in, &a.tu, a.tmask & 1, cb, nv, 80, &lbar[buf]);
+            if (force) k5::tile_copy(sa, a.ahat, &a.ta, a.tmask & 8, cb, nv, 60, &lbar[buf]);
         }
     };
     if (blockIdx.x < ntile) fetch(blockIdx.x, 0);
