@@ -13,6 +13,7 @@
  *   - Gauss quadrature with (k+1) points per axis ... Sec. 2.2 and Sec. 7 (v_k, s_k)
  *   - von Neumann-Richtmyer viscous pressure ........ Sec. 3.1 (quadratic + linear term, Pi_max)
  *   - positivity check and rescaling ............... Sec. 3.1, last paragraph before 3.1.1
+ *   - step repetition with troubled cells flattened . the same paragraph (orc_step_repeat)
  *   - primitive-variable projection ................ Sec. 3.2, eq. (weights_equation)
  *   - Ornstein-Uhlenbeck driving ................... Sec. 4.2, eqs. (ornstein_uhlenbeck...), (eddy_turnover_time)
  *   - SSP Runge-Kutta stages and dt ~ h/(k+1) ....... Sec. 7
@@ -335,7 +336,17 @@ void orc_riemann(int solver, double cs, int d, const double WL[4], const double 
 /* CFL time step (Sec. 7: dt proportional to h/(k+1))                        */
 /*   dt = cfl h / ((k+1) max_{cells, volume points} sum_d (|v_d| + cs))     */
 /* ------------------------------------------------------------------------ */
-double orc_dt(const orc_cfg* cfg, const double* u)
+/* sum_d(|v_d| + cs) at volume point q of cell uc */
+static double point_speed(const tabs* T, const orc_cfg* cfg, const double* uc, int q)
+{
+    const int b = T->b;
+    double rho = eval(T, uc, T->phi + q * b), s = 0.0;
+    for (int d = 0; d < 3; ++d) s += fabs(eval(T, uc + (1 + d) * b, T->phi + q * b) / rho) + cfg->cs;
+    return s;
+}
+
+/* S = max over cells and volume points of sum_d(|v_d| + cs) */
+double orc_speed_bound(const orc_cfg* cfg, const double* u)
 {
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
@@ -345,12 +356,18 @@ double orc_dt(const orc_cfg* cfg, const double* u)
     for (int c = 0; c < nc; ++c) {
         const double* uc = u + (size_t)c * 4 * b;
         for (int q = 0; q < T.nq; ++q) {
-            double rho = eval(&T, uc, T.phi + q * b), s = 0.0;
-            for (int d = 0; d < 3; ++d) s += fabs(eval(&T, uc + (1 + d) * b, T.phi + q * b) / rho) + cfg->cs;
+            double s = point_speed(&T, cfg, uc, q);
             if (s > smax) smax = s;
         }
     }
     tabs_free(&T);
+    return smax;
+}
+
+double orc_dt(const orc_cfg* cfg, const double* u)
+{
+    int N = cfg->N;
+    double smax = orc_speed_bound(cfg, u);
     double dt = cfg->cfl * (1.0 / N) / ((cfg->k + 1) * smax);
     if (cfg->eps_diff > 0.0) {
         /* explicit diffusion: dt <= cfl (h/(k+1))^2 / (2 eps) */
@@ -640,7 +657,7 @@ int orc_rhs_local(const orc_cfg* cfg, const double* patch, const double* ahat_c,
 /* a mean at or below the floor is a failure (the step is retried with a     */
 /* smaller dt by the time-step loop).                                        */
 /* ------------------------------------------------------------------------ */
-int orc_limit(const orc_cfg* cfg, double* u)
+static int limit_impl(const orc_cfg* cfg, double* u, uint8_t* flag)
 {
     tabs T;
     tabs_init(&T, cfg->k, cfg->k + 1);
@@ -656,6 +673,7 @@ int orc_limit(const orc_cfg* cfg, double* u)
         for (int f = 0; f < 6; ++f)
             for (int s = 0; s < T.ns; ++s) rmin = fmin(rmin, eval(&T, uc, T.phif + ((size_t)f * T.ns + s) * b));
         if (rmin < eps) {
+            if (flag) flag[c] = 1;
             double rbar = uc[0];
             if (rbar > eps) {
                 double theta = (rbar - eps) / (rbar - rmin);
@@ -671,6 +689,8 @@ int orc_limit(const orc_cfg* cfg, double* u)
     return status;
 }
 
+int orc_limit(const orc_cfg* cfg, double* u) { return limit_impl(cfg, u, NULL); }
+
 /* ------------------------------------------------------------------------ */
 /* one SSP Runge-Kutta step (Sec. 7) with the limiter after every stage      */
 /*   RK2: u1 = un + dt L(un);  un+1 = un/2 + (u1 + dt L(u1))/2               */
@@ -679,6 +699,14 @@ int orc_limit(const orc_cfg* cfg, double* u)
 /* dt also fixes Pi_max for every stage.                                      */
 /* ------------------------------------------------------------------------ */
 int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt)
+{
+    return orc_step_flags(cfg, u, ahat, dt, 0.0, NULL);
+}
+
+/* orc_step; with flag != NULL also marks (flag[c] = 1) every cell that a stage
+ * troubles: rho < eps at one of its volume or face points before the
+ * rescaling, or after it a volume point with sum_d(|v_d| + cs) > vlim */
+int orc_step_flags(const orc_cfg* cfg, double* u, const double* ahat, double dt, double vlim, uint8_t* flag)
 {
     int b = orc_nmodes(cfg->k);
     size_t n = (size_t)cfg->N * cfg->N * cfg->N * 4 * b;
@@ -696,13 +724,89 @@ int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt)
         orc_rhs(cfg, us, ahat, dt, L);
 #pragma omp parallel for schedule(static)
         for (size_t i = 0; i < n; ++i) us[i] = A[s] * un[i] + B[s] * (us[i] + dt * L[i]);
-        status |= orc_limit(cfg, us);
+        status |= limit_impl(cfg, us, flag);
+        if (flag) {
+            tabs T;
+            tabs_init(&T, cfg->k, cfg->k + 1);
+            const int nc = cfg->N * cfg->N * cfg->N;
+#pragma omp parallel for schedule(static)
+            for (int c = 0; c < nc; ++c)
+                for (int q = 0; q < T.nq; ++q)
+                    if (point_speed(&T, cfg, us + (size_t)c * 4 * b, q) > vlim) flag[c] = 1;
+            tabs_free(&T);
+        }
     }
     memcpy(u, us, sizeof(double) * n);
     free(un);
     free(us);
     free(L);
     return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* positivity by repetition of the step (Sec. 3.1, last paragraph, read as   */
+/* the troubled-cell procedure the same section gives for the finite-volume */
+/* scheme, with "scale all high-order weights" applied to the step's input): */
+/*   attempt: S = speed bound of u, dt = cfl h / ((k+1) S) (or fixed_dt)     */
+/*   times 2^-h; the step as orc_step_flags with vlim = ORC_REPEAT_SPEED S.   */
+/*   No troubled cell and no failed mean: accepted.  Otherwise the higher    */
+/*   modes of every troubled cell of u are multiplied by 1/2 (its first two  */
+/*   times in this step) or 0 (the third), and the step is attempted again   */
+/*   from the modified u; a troubled cell that is already flat, or a cell    */
+/*   mean at or below the floor, increments h.                               */
+/* The speed test (a stage output breaking the Courant condition that set    */
+/* its dt) is an addition to the paper's text.  Returns the status bits (with */
+/* ORC_REPEATED after more than one attempt), or -1 when the attempts or the */
+/* halvings run out; u then holds u^n with its troubled cells flattened.    */
+/* level [nc] (optional) receives how often each cell was scaled.            */
+/* ------------------------------------------------------------------------ */
+int orc_step_repeat(const orc_cfg* cfg, double* u, const double* ahat, double fixed_dt, double* dt_used,
+                    int* attempts, uint8_t* level)
+{
+    const int b = orc_nmodes(cfg->k);
+    const size_t nc = (size_t)cfg->N * cfg->N * cfg->N, n = nc * 4 * b;
+    double* w = (double*)malloc(sizeof(double) * n);
+    uint8_t* flag = (uint8_t*)malloc(nc);
+    uint8_t* lev = (uint8_t*)calloc(nc, 1);
+    int h = 0, rc = -1;
+    for (int att = 0; att < ORC_REPEAT_MAX && h <= ORC_REPEAT_HALVINGS; ++att) {
+        const double S = orc_speed_bound(cfg, u);
+        const double dt = (fixed_dt > 0.0 ? fixed_dt : orc_dt(cfg, u)) * ldexp(1.0, -h);
+        memcpy(w, u, sizeof(double) * n);
+        memset(flag, 0, nc);
+        const int st = orc_step_flags(cfg, w, ahat, dt, ORC_REPEAT_SPEED * S, flag);
+        int any = 0;
+        for (size_t c = 0; c < nc; ++c) any |= flag[c];
+        if (!any && !(st & ORC_FAIL)) {
+            memcpy(u, w, sizeof(double) * n);
+            if (dt_used) *dt_used = dt;
+            if (attempts) *attempts = att + 1;
+            rc = st | (att > 0 ? ORC_REPEATED : 0);
+            break;
+        }
+        int flat = 0;
+        for (size_t c = 0; c < nc; ++c) {
+            if (!flag[c]) continue;
+            double* uc = u + c * 4 * b;
+            int nonzero = 0;
+            for (int var = 0; var < 4; ++var)
+                for (int l = 1; l < b; ++l) nonzero |= uc[var * b + l] != 0.0;
+            if (!nonzero) {
+                flat = 1;
+                continue;
+            }
+            const double f = lev[c] < 2 ? 0.5 : 0.0;
+            for (int var = 0; var < 4; ++var)
+                for (int l = 1; l < b; ++l) uc[var * b + l] *= f;
+            lev[c] += 1;
+        }
+        if (flat || (st & ORC_FAIL)) ++h;
+    }
+    if (level) memcpy(level, lev, nc);
+    free(w);
+    free(flag);
+    free(lev);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -849,6 +953,7 @@ void orc_forcing_project(const orc_cfg* cfg, int nmodes, const int32_t* kvec, co
 /* (if > 0) the forcing is switched off.  A step whose stages report a       */
 /* failure is redone from the same state with dt/2, at most 3 times.         */
 /* Returns 0, or -1 when the retries are exhausted (state left at u^n).     */
+/* pos_mode 1: every step by orc_step_repeat (-1 when it gives up).         */
 /* ------------------------------------------------------------------------ */
 int orc_run(const orc_cfg* cfg, double* u, orc_ou* ou, int use_forcing, double* ahat, int nsteps, double* t,
             double* dt_last)
@@ -873,6 +978,16 @@ int orc_run(const orc_cfg* cfg, double* u, orc_ou* ou, int use_forcing, double* 
                 ou->dirty = 0;
             }
             force = ahat;
+        }
+        if (cfg->pos_mode == 1) {
+            double dtu = 0.0;
+            if (orc_step_repeat(cfg, u, force, 0.0, &dtu, NULL, NULL) < 0) {
+                rc = -1;
+                break;
+            }
+            *t += dtu;
+            if (dt_last) *dt_last = dtu;
+            continue;
         }
         double dt = orc_dt(cfg, u);
         int status = ORC_FAIL;

@@ -36,6 +36,9 @@ typedef struct {
     int32_t rk_stages;  /* 2 (SSP-RK2) or 3 (SSP-RK3)                        */
     int32_t riemann;    /* face flux: 0 Rusanov, 1 HLL, 2 HLLC               */
     double eps_diff;    /* diffusion coefficient of div(eps grad u), 0: off  */
+    int32_t pos_mode;   /* positivity: 0 rescale the stage outputs, 1 also
+                           repeat the step with troubled cells flattened
+                           (orc_step_repeat)                                  */
 } orc_cfg;
 
 #define ORC_RUSANOV 0
@@ -45,6 +48,16 @@ typedef struct {
 /* status bits of a stage / step */
 #define ORC_LIMITED 1   /* at least one cell was rescaled by the limiter    */
 #define ORC_FAIL    2   /* a cell mean fell to or below the floor           */
+#define ORC_REPEATED 4  /* the step was repeated with troubled cells
+                           flattened (pos_mode 1)                            */
+
+/* positivity by repetition (pos_mode 1): a stage output whose volume-point
+ * wave speed sum_d(|v_d| + cs) exceeds ORC_REPEAT_SPEED times the bound that
+ * set dt troubles its cell; at most ORC_REPEAT_MAX attempts per step and
+ * ORC_REPEAT_HALVINGS halvings of dt */
+#define ORC_REPEAT_SPEED 1.5
+#define ORC_REPEAT_MAX 32
+#define ORC_REPEAT_HALVINGS 6
 
 /* OU driving state (host side, Sec. 4.2) */
 #define ORC_MAX_MODES 512
@@ -106,6 +119,10 @@ int orc_rhs_local(const orc_cfg* cfg, const double* patch, const double* ahat_c,
                   double dt_pimax, const double* nu, int64_t n, double* out);
 void orc_av_features(const orc_cfg* cfg, const double* u, double dt, double* x, double* y);
 int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt);
+int orc_step_flags(const orc_cfg* cfg, double* u, const double* ahat, double dt, double vlim, uint8_t* flag);
+double orc_speed_bound(const orc_cfg* cfg, const double* u);
+int orc_step_repeat(const orc_cfg* cfg, double* u, const double* ahat, double fixed_dt, double* dt_used,
+                    int* attempts, uint8_t* level);
 
 /* turbulence statistics (Sec. 4.1 structure function and power spectrum,
  * Sec. 4.3 density PDF) */

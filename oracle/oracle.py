@@ -40,10 +40,14 @@ def build(force: bool = False) -> str:
 class Cfg(C.Structure):
     _fields_ = [("N", C.c_int32), ("k", C.c_int32), ("cs", C.c_double), ("av_mode", C.c_int32),
                 ("alpha", C.c_double), ("beta", C.c_double), ("rho_floor", C.c_double), ("cfl", C.c_double),
-                ("rk_stages", C.c_int32), ("riemann", C.c_int32), ("eps_diff", C.c_double)]
+                ("rk_stages", C.c_int32), ("riemann", C.c_int32), ("eps_diff", C.c_double),
+                ("pos_mode", C.c_int32)]
 
 
 RIEMANN = {"rusanov": 0, "hll": 1, "hllc": 2}
+POSITIVITY = {"scale": 0, "repeat": 1}
+REPEAT_SPEED = 1.5
+ST_LIMITED, ST_FAIL, ST_REPEATED = 1, 2, 4
 
 
 MAX_MODES = 512
@@ -87,6 +91,11 @@ def lib():
                                      C.c_double, C.c_uint64, C.c_double]
         _lib.orc_rhs.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d]
         _lib.orc_step.argtypes = [C.POINTER(Cfg), d, d, C.c_double]
+        u8 = C.POINTER(C.c_uint8)
+        _lib.orc_step_flags.argtypes = [C.POINTER(Cfg), d, d, C.c_double, C.c_double, u8]
+        _lib.orc_speed_bound.restype = C.c_double
+        _lib.orc_speed_bound.argtypes = [C.POINTER(Cfg), d]
+        _lib.orc_step_repeat.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d, C.POINTER(C.c_int), u8]
         _lib.orc_run.argtypes = [C.POINTER(Cfg), d, C.POINTER(OU), C.c_int, d, C.c_int, d, d]
         _lib.orc_diagnostics.argtypes = [C.POINTER(Cfg), d, d, C.c_double, d]
         _lib.orc_forcing_project.argtypes = [C.POINTER(Cfg), C.c_int, C.POINTER(C.c_int32), d, d]
@@ -155,10 +164,11 @@ def legendre_deriv(m: int, x: float) -> float:
 
 
 def make_cfg(N, k, cs=1.0, av_mode=1, alpha=2.0, beta=0.2, rho_floor=1e-3, cfl=0.3, rk_stages=None,
-             riemann="rusanov", eps_diff=0.0) -> Cfg:
+             riemann="rusanov", eps_diff=0.0, positivity="scale") -> Cfg:
     if rk_stages is None:
         rk_stages = 2 if k == 1 else 3
-    return Cfg(N, k, cs, av_mode, alpha, beta, rho_floor, cfl, rk_stages, RIEMANN[riemann], eps_diff)
+    return Cfg(N, k, cs, av_mode, alpha, beta, rho_floor, cfl, rk_stages, RIEMANN[riemann], eps_diff,
+               POSITIVITY[positivity])
 
 
 def _shape(cfg, nvar=4):
@@ -285,6 +295,32 @@ def limit(cfg: Cfg, u: np.ndarray) -> int:
 def step(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None, dt_: float) -> int:
     """One SSP-RK step in place; returns the OR of the stage limiter statuses."""
     return lib().orc_step(C.byref(cfg), _p(u), _p(ahat), dt_)
+
+
+def speed_bound(cfg: Cfg, u: np.ndarray) -> float:
+    """S = max over cells and volume points of sum_d(|v_d| + cs)."""
+    return lib().orc_speed_bound(C.byref(cfg), _p(u))
+
+
+def step_flags(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None, dt_: float, vlim: float):
+    """One SSP-RK step in place as ``step``; returns (status, flag[nc]) with the
+    cells a stage troubled (rho < floor at a point, or a wave speed above vlim)."""
+    flag = np.zeros(cfg.N ** 3, dtype=np.uint8)
+    st = lib().orc_step_flags(C.byref(cfg), _p(u), _p(ahat), dt_, vlim,
+                              flag.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return st, flag
+
+
+def step_repeat(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None, fixed_dt: float = 0.0):
+    """One step with positivity by repetition (Sec. 3.1), in place; returns
+    (status or -1, dt used, attempts, level[nc] = how often each cell of u^n was
+    scaled)."""
+    dtu = C.c_double(0.0)
+    att = C.c_int(0)
+    level = np.zeros(cfg.N ** 3, dtype=np.uint8)
+    st = lib().orc_step_repeat(C.byref(cfg), _p(u), _p(ahat), fixed_dt, C.byref(dtu), C.byref(att),
+                               level.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return st, dtu.value, att.value, level
 
 
 class Forcing:
