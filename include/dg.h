@@ -70,6 +70,14 @@ extern "C" {
 #define DG_ST_NONFINITE 4u /* a NaN/Inf was produced                              */
 #define DG_ST_TIMEOUT 8u   /* a tensor-core completion wait gave up (the launch
                               stopped early; reported as DG_ECUDA)              */
+#define DG_ST_REPEATED 16u /* positivity by repetition: a step was computed
+                              again with troubled cells flattened               */
+
+/* positivity treatment of dg_step (Sec. 3.1, last paragraph) */
+#define DG_POS_SCALE 0     /* rescale the high-order weights of every stage
+                              output below the floor (default)                  */
+#define DG_POS_REPEAT 1    /* also repeat the step from a modified u^n: see
+                              dg_step                                           */
 
 typedef struct {
     int32_t n[3];          /* cells per axis; this build requires n[0]=n[1]=n[2],
@@ -135,6 +143,7 @@ typedef struct {
                               1 = the single fused stage kernel on warp-level
                               mma.sync.  Other precisions, orders and the
                               diffusion operator use the fused kernel either way */
+    int32_t positivity;    /* DG_POS_*; DG_POS_SCALE when zero-initialised        */
 } dg_opts;
 
 /* Driving (Sec. 4.2, eq. ornstein_uhlenbeck_process_time_evolution).  Modes:
@@ -224,7 +233,21 @@ int dg_project_velocity(dg_ctx* ctx, const void* u_in, void* vhat_out);
  * combine, positivity rescaling).  A step in which a cell mean reaches the
  * floor is redone from u^n with dt/2, at most 3 times; then DG_EPOSITIVITY
  * with the state left at u^n.  Synchronises the stream once per step.
- * fixed_dt > 0 replaces the CFL dt (used to replay a recorded sequence). */
+ * fixed_dt > 0 replaces the CFL dt (used to replay a recorded sequence).
+ *
+ * DG_POS_REPEAT (Sec. 3.1, last paragraph, read as the troubled-cell
+ * procedure the paper gives for its finite-volume scheme): a cell is troubled
+ * when a stage output has rho below the floor at one of its volume or face
+ * Gauss points, or a volume point with sum_d(|v_d| + cs) above 1.5 times the
+ * bound S that set dt (the stage breaks its step's Courant condition; this
+ * test is an addition to the paper's text).  If any cell is troubled, the
+ * modes l > 0 of every troubled cell of u^n are multiplied by 1/2 (the first
+ * two times in the step) or 0 (the third) and the step is computed again from
+ * the modified u^n, with dt from its own S; a troubled cell that is already
+ * flat, or a cell mean at the floor, halves dt for the following attempts.
+ * At most 32 attempts and 6 halvings, then DG_EPOSITIVITY with the state left
+ * at u^n with its troubled cells flattened.  One more stream synchronisation
+ * per repeated attempt; DG_ST_REPEATED reports that a step was repeated. */
 int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_last);
 
 /* Configure the driving (Sec. 4.2, eq. ornstein_uhlenbeck_process_time_evolution

@@ -16,7 +16,7 @@ DG_OK, DG_EINVAL, DG_ECUDA, DG_ENOMEM, DG_EPOSITIVITY, DG_ENONFINITE, DG_ESTATE 
 PREC_F64, PREC_F32, PREC_X3 = 0, 1, 2
 AV_OFF, AV_VNR, AV_LEARNED = 0, 1, 2
 RIEMANN = {"rusanov": 0, "hll": 1, "hllc": 2}
-ST_LIMITED, ST_FAIL, ST_NONFINITE = 1, 2, 4
+ST_LIMITED, ST_FAIL, ST_NONFINITE, ST_TIMEOUT, ST_REPEATED = 1, 2, 4, 8, 16
 ERROR_NAMES = {DG_EINVAL: "DG_EINVAL", DG_ECUDA: "DG_ECUDA", DG_ENOMEM: "DG_ENOMEM",
                DG_EPOSITIVITY: "DG_EPOSITIVITY", DG_ENONFINITE: "DG_ENONFINITE", DG_ESTATE: "DG_ESTATE"}
 
@@ -33,7 +33,8 @@ class NuParams(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rk_stages", C.c_int32), ("cfl", C.c_double), ("stream", C.c_void_p),
                 ("u", C.c_void_p * 3), ("vhat", C.c_void_p), ("ahat", C.c_void_p), ("scratch", C.c_void_p),
-                ("scratch_bytes", C.c_size_t), ("riemann", C.c_int32), ("x3_backend", C.c_int32)]
+                ("scratch_bytes", C.c_size_t), ("riemann", C.c_int32), ("x3_backend", C.c_int32),
+                ("positivity", C.c_int32)]
 
 
 class AdiOpts(C.Structure):

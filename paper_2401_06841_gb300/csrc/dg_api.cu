@@ -595,6 +595,12 @@ struct dg_ctx {
     float* nu_cell = nullptr;  // per-cell coefficient (learned mode)
     float* nu_next = nullptr;  // the next step's coefficient, written by the last stage (learned mode)
     void* vabs = nullptr;      // per-cell |v| projection (learned mode)
+    // positivity by repetition (dg_opts.positivity): per-cell marks of an
+    // attempt and how often each cell of u^n was scaled in this step
+    bool repeat = false;
+    unsigned char* trouble = nullptr;
+    unsigned char* level = nullptr;
+    bool marks_dirty = false;  // marks or levels may be non-zero
     // x3 at order 3: tcgen05 kernels (volume, faces, projection)
     bool tc5 = false;
     void* t5tab = nullptr;
@@ -631,11 +637,15 @@ struct ScratchLayout {
     size_t nu, nu2, vabs;                        // per-cell coefficients (this and the next step) and |v| projection (learned mode)
     size_t ana;                                  // turbulence statistics: 4 x DG_MAX_BINS doubles + 1
     size_t t5tab, rvol;                          // order 3: tensor-core table block, FP32 volume term [c][4][b]
+    size_t trouble, level;                       // positivity by repetition: per-cell marks and levels (bytes)
     size_t total;
 };
 
 constexpr int kMlpMaxParams = 64 * 40 + 64 + 64 * 64 + 64 + 64 + 1;
 constexpr int kMlpPackWords = 8192;
+// positivity by repetition: attempts per step and halvings of dt before DG_EPOSITIVITY
+constexpr int kRepeatAttempts = 32;
+constexpr int kRepeatHalvings = 6;
 
 ScratchLayout scratch_layout(int K, int N, bool learned = false)
 {
@@ -685,6 +695,10 @@ ScratchLayout scratch_layout(int K, int N, bool learned = false)
     if (K == 3) off = align256(off + tc5_table_bytes());
     s.rvol = off;
     if (K == 3) off = align256(off + sizeof(float) * (size_t)ncell * 4 * b);
+    s.trouble = off;
+    off = align256(off + (size_t)ncell);
+    s.level = off;
+    off = align256(off + (size_t)ncell);
     s.total = off;
     return s;
 }
@@ -805,6 +819,7 @@ cudaError_t tile_tc5(dg_ctx* c, const TileLaunch& t)
     p.rk_a = t.rk_a;
     p.rk_b = t.rk_b;
     p.dt_pimax = t.dt_pimax;
+    p.trouble = t.mode == TM_RHS ? nullptr : t.trouble;
     if (t.mode == TM_PROJECT) {
         Timed tm(c, KIND_PROJECT);
         p.kind = T5_PROJECT;
@@ -1007,6 +1022,7 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
     if (!(opts->cfl > 0.0)) return DG_EINVAL;
     if (opts->riemann < DG_RIEMANN_RUSANOV || opts->riemann > DG_RIEMANN_HLLC) return DG_EINVAL;
+    if (opts->positivity != DG_POS_SCALE && opts->positivity != DG_POS_REPEAT) return DG_EINVAL;
     if (!opts->stream) return DG_EINVAL;
     for (int i = 0; i < 3; ++i)
         if (!opts->u[i]) return DG_EINVAL;
@@ -1063,6 +1079,10 @@ int dg_init(dg_ctx** out, const dg_mesh* mesh, int order, double cs, const dg_nu
     ctx->vabs = ctx->scratch + sl.vabs;
     ctx->t5tab = ctx->scratch + sl.t5tab;
     ctx->rvol = ctx->scratch + sl.rvol;
+    ctx->repeat = opts->positivity == DG_POS_REPEAT;
+    ctx->trouble = reinterpret_cast<unsigned char*>(ctx->scratch + sl.trouble);
+    ctx->level = reinterpret_cast<unsigned char*>(ctx->scratch + sl.level);
+    ctx->marks_dirty = true;
     // order-3 x3 on the tcgen05 kernels (the learned sensor's in-step evaluation,
     // fused_infer, runs in their last projection)
     ctx->tc5 = ctx->prec == DG_PREC_X3 && order == 3 && nu->diffusion == 0.0 && opts->x3_backend == 0;
@@ -1294,10 +1314,25 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
         const bool learned = ctx->nu.mode == DG_AV_LEARNED;
         const bool fused = learned && ctx->nu.fused_infer;
         const int pb = ctx->pb;
-        for (int retry = 0; retry <= 3 && !ok; ++retry) {
+        // positivity by repetition (Sec. 3.1, last paragraph): the stages mark the
+        // cells they trouble; the marked cells of u^n (register A) are scaled towards
+        // their flat expansion and the step is attempted again; a marked cell that
+        // is already flat, or a failed cell mean, halves dt.  Otherwise the
+        // rescaled stage outputs stand and a failed mean retries with dt/2, dt/4, dt/8
+        const bool repeat = ctx->repeat;
+        unsigned char* marks = repeat ? ctx->trouble : nullptr;
+        if (repeat && ctx->marks_dirty) {
+            CK(cudaMemsetAsync(ctx->trouble, 0, (size_t)ctx->ncell, ctx->st));
+            CK(cudaMemsetAsync(ctx->level, 0, (size_t)ctx->ncell, ctx->st));
+            ctx->marks_dirty = false;
+        }
+        const int max_attempts = repeat ? kRepeatAttempts : 4, max_halvings = repeat ? kRepeatHalvings : 3;
+        int halvings = 0, attempts = 0;
+        for (int retry = 0; retry < max_attempts && halvings <= max_halvings && !ok; ++retry) {
+            attempts = retry + 1;
             struct {
                 double dt_scale, fixed_dt;
-            } hs = {1.0 / (double)(1 << retry), fixed_dt};
+            } hs = {1.0 / (double)(1 << halvings), fixed_dt};
             CK(cudaMemcpyAsync(&ctx->ctl->dt_scale, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->st));
             unsigned int zero = 0u;
             CK(cudaMemcpyAsync(&ctx->ctl->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->st));
@@ -1342,6 +1377,7 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
                           ((fold && s > 0) ? F_SELFPROJ : 0);
                 t.abar_in = (pb + s) & 1;
                 t.abar_out = (pb + s + 1) & 1;
+                t.trouble = marks;
                 CK(tile(ctx, t));
             }
             struct {
@@ -1353,11 +1389,34 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
             CK(cudaStreamSynchronize(ctx->st));
             status = back.status;
             dt = back.dt;
-            ok = !(status & DG_ST_FAIL);
+            ok = !(status & (DG_ST_FAIL | DG_ST_TROUBLED_));
+            if (ok) break;
+            if (!repeat) {
+                ++halvings;
+                continue;
+            }
+            // flatten the marked cells of u^n; a flat one (or a failed mean) halves dt
+            ctx->marks_dirty = true;
+            CK(cudaMemcpyAsync(&ctx->ctl->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->st));
+            {
+                Timed tm(ctx, KIND_OTHER);
+                Launch L = make_launch(ctx);
+                cudaError_t e = (ctx->prec == DG_PREC_F64)
+                                    ? launch_flatten<double>(L, (double*)ctx->reg[A], ctx->trouble, ctx->level)
+                                    : launch_flatten<float>(L, (float*)ctx->reg[A], ctx->trouble, ctx->level);
+                CK(e);
+            }
+            unsigned int fst = 0u;
+            CK(cudaMemcpyAsync(&fst, &ctx->ctl->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            if ((fst & DG_ST_FLAT_) || (status & DG_ST_FAIL)) ++halvings;
         }
+        status &= 0xffu;
+        if (repeat && attempts > 1) status |= DG_ST_REPEATED;
         if (!ok) {
             ctx->status |= status;
-            return fail(ctx, DG_EPOSITIVITY, "dg_step: positivity retries exhausted");
+            return fail(ctx, DG_EPOSITIVITY, repeat ? "dg_step: positivity repetitions exhausted"
+                                                    : "dg_step: positivity retries exhausted");
         }
         ctx->status |= status;
         ctx->cur = out[ctx->rk - 1];

@@ -140,6 +140,13 @@ enum { F_DT = 1, F_FORCE = 2 };
 #define DG_ST_LIMITED_ 1u
 #define DG_ST_FAIL_ 2u
 #define DG_ST_NONFINITE_ 4u
+// positivity by repetition (internal, never reported): a stage marked a
+// troubled cell; the flattening found a troubled cell that was already flat
+#define DG_ST_TROUBLED_ 0x100u
+#define DG_ST_FLAT_ 0x200u
+// a stage output whose volume-point sum_d(|v_d| + cs) exceeds this factor times
+// the bound that set dt troubles its cell
+#define DG_REPEAT_SPEED 1.5
 #define DG_NDIAG 13
 
 // ---------------------------------------------------------------------------

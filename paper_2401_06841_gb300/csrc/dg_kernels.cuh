@@ -378,4 +378,33 @@ __global__ void __launch_bounds__(256) k_l1(const T* tab, const T* uA, const T* 
     }
 }
 
+// ---------------------------------------------------------------------------
+// K_flatten: positivity by repetition (Sec. 3.1, last paragraph): the high-order
+// weights of every cell a stage marked are scaled towards the flat expansion
+// before the step is computed again.  One thread per cell; cells are rare.
+// ---------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_flatten(T* u, unsigned char* trouble, unsigned char* level, long ncell,
+                                                 Ctl* ctl)
+{
+    constexpr int b = Dims<K>::b;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (long)gridDim.x * blockDim.x) {
+        if (!trouble[c]) continue;
+        trouble[c] = 0;
+        T* uc = u + c * 4 * b;
+        bool nonzero = false;
+        for (int var = 0; var < 4; ++var)
+            for (int l = 1; l < b; ++l) nonzero |= uc[var * b + l] != T(0);
+        if (!nonzero) {
+            atomicOr(&ctl->status, DG_ST_FLAT_);
+            continue;
+        }
+        const unsigned char lv = level[c];
+        const T f = lv < 2 ? T(0.5) : T(0);
+        for (int var = 0; var < 4; ++var)
+            for (int l = 1; l < b; ++l) uc[var * b + l] *= f;
+        level[c] = (unsigned char)(lv + 1);
+    }
+}
+
 }  // namespace dg

@@ -48,6 +48,7 @@ struct TileLaunch {
     void* vabs_out;      // learned sensor: projection of |v|
     float* nu_next;      // learned sensor: coefficient of the output, evaluated in the kernel (mode 3)
     const uint32_t* mlp; // learned sensor: packed network for nu_next
+    unsigned char* trouble;  // positivity by repetition: per-cell marks of the stage (or nullptr)
 };
 template <typename T>
 cudaError_t launch_tile(const Launch& L, const TileLaunch& t);
@@ -57,6 +58,11 @@ template <typename T>
 cudaError_t launch_diag(const Launch& L, const T* u, const T* ahat, double dt_pimax, int flags);
 template <typename T>
 cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB);
+// positivity by repetition: every marked cell of u [c][4][b] is unmarked and its
+// modes l > 0 scaled by 1/2 (level 0, 1) or 0 (level 2), its level incremented;
+// a marked cell whose modes l > 0 are all zero sets DG_ST_FLAT_ instead
+template <typename T>
+cudaError_t launch_flatten(const Launch& L, T* u, unsigned char* trouble, unsigned char* level);
 
 // x3 stage of degree 3 on the tcgen05 tensor cores (dg_tc5.cu): the
 // projection kernel, or the volume and face kernels of a right-hand side /
@@ -92,6 +98,7 @@ struct T5Launch {
     float* nu_next;      // projection: the learned sensor's coefficient of u_in (or nullptr)
     const uint32_t* mlp; // its packed network
     const T5Maps* maps;  // tiled TMA descriptors of the context's buffers (or nullptr)
+    unsigned char* trouble;  // positivity by repetition: per-cell marks (or nullptr)
     const void* tab5;    // table block (tc5_build_tables)
     const void* phiv;    // [b][nq] FP32 phi at the volume points
     const void* phif;    // [b][nf] FP32 phi at the face points

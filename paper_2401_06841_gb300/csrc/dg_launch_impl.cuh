@@ -125,6 +125,7 @@ static cudaError_t tile_kb(const Launch& L, const TileLaunch& t)
     a.vabs_out = static_cast<T*>(t.vabs_out);
     a.nu_next = t.mode == TM_STAGE_VABS ? t.nu_next : nullptr;
     a.mlp = t.mlp;
+    a.trouble = t.mode == TM_PROJECT || t.mode == TM_RHS ? nullptr : t.trouble;
     using Cf = TileCfg<K, BK>;
     const long ntile = (L.ncell + Cf::TC - 1) / Cf::TC;
     const size_t sm = sizeof(T) * Cf::total;
@@ -190,6 +191,16 @@ static cudaError_t l1_k(const Launch& L, const T* uA, const T* uB)
     return cudaGetLastError();
 }
 
+template <typename T, int K>
+static cudaError_t flatten_k(const Launch& L, T* u, unsigned char* trouble, unsigned char* level)
+{
+    long g = (L.ncell + 255) / 256;
+    if (g > 4L * L.nsm) g = 4L * L.nsm;
+    if (g < 1) g = 1;
+    k_flatten<T, K><<<(int)g, 256, 0, L.st>>>(u, trouble, level, L.ncell, L.ctl);
+    return cudaGetLastError();
+}
+
 #define DG_DISPATCH(fn, ...)                                   \
     do {                                                       \
         if (L.K == 1) return fn<T, 1>(L, __VA_ARGS__);         \
@@ -218,6 +229,11 @@ cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB)
 {
     DG_DISPATCH(l1_k, uA, uB);
 }
+template <typename T>
+cudaError_t launch_flatten(const Launch& L, T* u, unsigned char* trouble, unsigned char* level)
+{
+    DG_DISPATCH(flatten_k, u, trouble, level);
+}
 
 #define DG_TILES_EXTERN(T, K)                                                   \
     extern template cudaError_t tile_k<T, K>(const Launch&, const TileLaunch&); \
@@ -231,6 +247,7 @@ cudaError_t launch_l1(const Launch& L, const T* uA, const T* uB)
     template cudaError_t launch_tile<T>(const Launch&, const TileLaunch&);                                       \
     template cudaError_t launch_force<T>(const Launch&, int, const int*, const double*, int, T*);               \
     template cudaError_t launch_diag<T>(const Launch&, const T*, const T*, double, int);                        \
-    template cudaError_t launch_l1<T>(const Launch&, const T*, const T*);
+    template cudaError_t launch_l1<T>(const Launch&, const T*, const T*);                                       \
+    template cudaError_t launch_flatten<T>(const Launch&, T*, unsigned char*, unsigned char*);
 
 }  // namespace dg

@@ -17,7 +17,7 @@ namespace dg {
 
 namespace {
 
-int g_occ_vol[8] = {0, 0, 0, 0, 0, 0, 0, 0}, g_occ_face[3] = {0, 0, 0}, g_occ_proj = 0;
+int g_occ_vol[12] = {}, g_occ_face[3] = {0, 0, 0}, g_occ_proj[2] = {0, 0};
 
 // scaled Legendre polynomial Pn_m = sqrt(2m+1) P_m and its derivative, by the
 // three-term recurrence and P'_{m+1} = P'_{m-1} + (2m+1) P_m
@@ -148,18 +148,26 @@ static cudaError_t resident_blocks(const void* fn, int dyn_smem, int tmem_cols, 
 cudaError_t tc5_setup()
 {
     cudaError_t e;
-    const void* vol[8] = {(const void*)k5_volume<false, false, false>, (const void*)k5_volume<false, true, false>,
-                          (const void*)k5_volume<true, false, false>,  (const void*)k5_volume<true, true, false>,
-                          (const void*)k5_volume<false, false, true>,  (const void*)k5_volume<false, true, true>,
-                          (const void*)k5_volume<true, false, true>,   (const void*)k5_volume<true, true, true>};
-    for (int i = 0; i < 8; ++i)
-        if ((e = resident_blocks(vol[i], i < 6 ? C5::Vol::total : C5::Vol::total3, i < 4 ? C5::TM_VOL : C5::TM_VOLP,
+    // [0, 8): gate (1), driving (2), self-projection (4); [8, 12): the self-projecting
+    // variants 4-7 with the wave-speed marks of positivity by repetition
+    const void* vol[12] = {
+        (const void*)k5_volume<false, false, false>,      (const void*)k5_volume<false, true, false>,
+        (const void*)k5_volume<true, false, false>,       (const void*)k5_volume<true, true, false>,
+        (const void*)k5_volume<false, false, true>,       (const void*)k5_volume<false, true, true>,
+        (const void*)k5_volume<true, false, true>,        (const void*)k5_volume<true, true, true>,
+        (const void*)k5_volume<false, false, true, true>, (const void*)k5_volume<false, true, true, true>,
+        (const void*)k5_volume<true, false, true, true>,  (const void*)k5_volume<true, true, true, true>};
+    for (int i = 0; i < 12; ++i) {
+        const int v = i < 8 ? i : i - 4;
+        if ((e = resident_blocks(vol[i], v < 6 ? C5::Vol::total : C5::Vol::total3, v < 4 ? C5::TM_VOL : C5::TM_VOLP,
                                  g_occ_vol[i])))
             return e;
+    }
     if ((e = resident_blocks((const void*)k5_faces<0>, C5::Face::total, C5::TM_FACE, g_occ_face[0]))) return e;
     if ((e = resident_blocks((const void*)k5_faces<1>, C5::Face::total, C5::TM_FACE, g_occ_face[1]))) return e;
     if ((e = resident_blocks((const void*)k5_faces<2>, C5::Face::total, C5::TM_FACE, g_occ_face[2]))) return e;
-    return resident_blocks((const void*)k5_project, C5::Proj::total, C5::TM_PROJ, g_occ_proj);
+    if ((e = resident_blocks((const void*)k5_project<false>, C5::Proj::total, C5::TM_PROJ, g_occ_proj[0]))) return e;
+    return resident_blocks((const void*)k5_project<true>, C5::Proj::total, C5::TM_PROJ, g_occ_proj[1]);
 }
 
 // the driver's tensor-map encoder, found once through the runtime (no link to the
@@ -251,6 +259,7 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
     a.abar_out = t.abar_out;
     a.nu_next = t.nu_next;
     a.mlp = t.mlp;
+    a.trouble = t.trouble;
     // tiled TMA descriptors of the buffers whose whole tiles the kernels stage
     a.tmask = 0;
     if (const CUtensorMap* m = find_map(t.maps, t.u_in)) { a.tu = *m; a.tmask |= 1; }
@@ -261,7 +270,10 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
     if ((t.flags & F_FORCE) && !t.ahat) return cudaErrorInvalidValue;
     const long ntile = (L.ncell + C5::TC - 1) / C5::TC;
     if (t.kind == T5_PROJECT) {
-        k5_project<<<grid5(ntile, g_occ_proj, L.nsm), C5::NT, C5::Proj::total, L.st>>>(a);
+        if (t.trouble)
+            k5_project<true><<<grid5(ntile, g_occ_proj[1], L.nsm), C5::NT, C5::Proj::total, L.st>>>(a);
+        else
+            k5_project<false><<<grid5(ntile, g_occ_proj[0], L.nsm), C5::NT, C5::Proj::total, L.st>>>(a);
         return cudaGetLastError();
     }
     a.stage = (t.kind == T5_STAGE) ? 1 : 0;
@@ -272,7 +284,8 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
     a.vh_self = static_cast<float*>(t.vh_self);
     const int gate = L.ph.av_mode != 1 ? 1 : 0;
     const int vv = proj ? (force ? 6 : 4) + gate : (force ? 2 : 0) + gate;
-    const int gv = grid5(ntile, g_occ_vol[vv], L.nsm);
+    const bool marks = proj && t.trouble;  // wave-speed marks of the self-projected stage output
+    const int gv = grid5(ntile, g_occ_vol[marks ? vv + 4 : vv], L.nsm);
     const int sv = (proj && force) ? C5::Vol::total3 : C5::Vol::total;
     if (proj && force) a.abar_out = a.abar_in;
     switch (vv) {
@@ -280,10 +293,22 @@ cudaError_t launch_tc5(const Launch& L, const T5Launch& t)
     case 1: k5_volume<false, true, false><<<gv, C5::NT, sv, L.st>>>(a); break;
     case 2: k5_volume<true, false, false><<<gv, C5::NT, sv, L.st>>>(a); break;
     case 3: k5_volume<true, true, false><<<gv, C5::NT, sv, L.st>>>(a); break;
-    case 4: k5_volume<false, false, true><<<gv, C5::NT, sv, L.st>>>(a); break;
-    case 5: k5_volume<false, true, true><<<gv, C5::NT, sv, L.st>>>(a); break;
-    case 6: k5_volume<true, false, true><<<gv, C5::NT, sv, L.st>>>(a); break;
-    default: k5_volume<true, true, true><<<gv, C5::NT, sv, L.st>>>(a); break;
+    case 4:
+        marks ? k5_volume<false, false, true, true><<<gv, C5::NT, sv, L.st>>>(a)
+              : k5_volume<false, false, true><<<gv, C5::NT, sv, L.st>>>(a);
+        break;
+    case 5:
+        marks ? k5_volume<false, true, true, true><<<gv, C5::NT, sv, L.st>>>(a)
+              : k5_volume<false, true, true><<<gv, C5::NT, sv, L.st>>>(a);
+        break;
+    case 6:
+        marks ? k5_volume<true, false, true, true><<<gv, C5::NT, sv, L.st>>>(a)
+              : k5_volume<true, false, true><<<gv, C5::NT, sv, L.st>>>(a);
+        break;
+    default:
+        marks ? k5_volume<true, true, true, true><<<gv, C5::NT, sv, L.st>>>(a)
+              : k5_volume<true, true, true><<<gv, C5::NT, sv, L.st>>>(a);
+        break;
     }
     a.abar_fix = (proj && force) ? 1 : 0;
     cudaError_t e = cudaGetLastError();

@@ -128,6 +128,7 @@ struct T5Args {
     int flags;           // F_FORCE, F_DT
     int abar_in, abar_out;
     int stage;           // 1: the step's dt (stage), 0: dt_pimax (right-hand side)
+    unsigned char* trouble;  // positivity by repetition: per-cell marks of the stage outputs (or nullptr)
 };
 
 namespace k5 {
@@ -265,9 +266,10 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, Ctl* ct
 // is the source's; driven, a third slot of the round, and the source leaves out
 // the mean acceleration (which depends on the whole state): the kernel reduces
 // <rho a_h>/<rho> into the abar_out slot and the face kernel subtracts abar rho_l
-template <bool FORCE, bool GATE, bool PROJ>
+template <bool FORCE, bool GATE, bool PROJ, bool CHK = false>
 __global__ void __launch_bounds__(256, 2) k5_volume(const __grid_constant__ T5Args a)
 {
+    static_assert(PROJ || !CHK, "the wave-speed marks come with the self-projection");
     constexpr bool P3 = FORCE && PROJ;  // three slots in the second round
     constexpr int TMC = PROJ ? C5::TM_VOLP : C5::TM_VOL;
     using V = C5::Vol;
@@ -304,6 +306,10 @@ __global__ void __launch_bounds__(256, 2) k5_volume(const __grid_constant__ T5Ar
     const double dtd = k5::step_dt(a);
     const AvCoef<float> avc = av_coef<float>(a.ph, dtd);
     const float two_h = (float)(2.0 / a.ph.h), i4h = (float)(0.25 / a.ph.h), cs2 = (float)a.ph.cs2;
+    // positivity by repetition: the input of a self-projecting stage is the previous
+    // stage's output; a point with sum_d |v_d| above this bound marks its cell
+    constexpr bool chk = CHK;
+    const float vlim = chk ? (float)(DG_REPEAT_SPEED * a.ctl->sn - 3.0 * a.ph.cs) : 0.f;
     float ab[3] = {0.f, 0.f, 0.f};
     if (force && !P3)
         for (int i = 0; i < 3; ++i) ab[i] = (float)a.ctl->abar2[a.abar_in][i];
@@ -460,6 +466,10 @@ __global__ void __launch_bounds__(256, 2) k5_volume(const __grid_constant__ T5Ar
                 const float rho = v[0], ir = rcp<float>(rho);
                 const float vx = v[1] * ir, vy = v[2] * ir, vz = v[3] * ir;
                 const float divv = (v[7] * two_h - (vx * v[4] + vy * v[5] + vz * v[6]) * two_h) * ir;
+                if (chk && c < nvalid && fabsf(vx) + fabsf(vy) + fabsf(vz) > vlim) {
+                    a.trouble[c0 + c] = 1;
+                    atomicOr(&a.ctl->status, DG_ST_TROUBLED_);
+                }
                 float Pi = 0.f;
                 if (need_div) {
                     if (a.ph.av_mode == 1)
@@ -951,6 +961,11 @@ __global__ void __launch_bounds__(256, 2) k5_faces(const __grid_constant__ T5Arg
                     }
                     const float rbar = rr[0];
                     if (mn < eps) {
+                        if (a.trouble) {
+                            const long cc = c0 + 2 * w + cl;
+                            if (lane == 0 && cc < a.ncell) a.trouble[cc] = 1;
+                            st |= DG_ST_TROUBLED_;
+                        }
                         if (rbar > eps) {
                             thr[cl] = (rbar - eps) / (rbar - mn);
                             st |= DG_ST_LIMITED_;
@@ -988,6 +1003,7 @@ __global__ void __launch_bounds__(256, 2) k5_faces(const __grid_constant__ T5Arg
 // --------------------------------------------------------------------------
 // projection of v (and |v|) of a state, CFL bound, forcing sums
 // --------------------------------------------------------------------------
+template <bool CHK = false>
 __global__ void __launch_bounds__(256, 3) k5_project(const __grid_constant__ T5Args a)
 {
     using P = C5::Proj;
@@ -1027,6 +1043,9 @@ __global__ void __launch_bounds__(256, 3) k5_project(const __grid_constant__ T5A
     const int qw = w & 3, hp = w >> 2, r = 32 * qw + lane, h = r >> 6, q = r & 63;
     const uint32_t tl = tc5::tmem_addr(tm, 32 * qw, 0);
     float smax = 0.f;
+    // positivity by repetition (projection of a stage output): read before this
+    // launch's last block replaces ctl->sn
+    const float vlim = CHK ? (float)(DG_REPEAT_SPEED * a.ctl->sn - 3.0 * a.ph.cs) : 0.f;
     double sums[4] = {0.0, 0.0, 0.0, 0.0};
     const long ntile = (a.ncell + TC - 1) / TC;
     auto fetch = [&](long t, int buf) {
@@ -1104,6 +1123,10 @@ __global__ void __launch_bounds__(256, 3) k5_project(const __grid_constant__ T5A
                 if (dtf && c < nvalid) {
                     const float sp = fabsf(vx) + fabsf(vy) + fabsf(vz);
                     smax = sp > smax ? sp : smax;
+                }
+                if (CHK && c < nvalid && fabsf(vx) + fabsf(vy) + fabsf(vz) > vlim) {
+                    a.trouble[c0 + c] = 1;
+                    atomicOr(&a.ctl->status, DG_ST_TROUBLED_);
                 }
                 x[pp][0] = vx * wq8;
                 x[pp][1] = vy * wq8;

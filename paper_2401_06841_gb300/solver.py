@@ -19,13 +19,15 @@ class Solver:
     """DG solver context on one GPU.
 
     N cells per axis, degree k (1..3), sound speed cs; precision 'f64', 'f32'
-    or 'x3'; av 'off' | 'vnr' | 'learned'; face flux riemann 'rusanov' | 'hll' | 'hllc'."""
+    or 'x3'; av 'off' | 'vnr' | 'learned'; face flux riemann 'rusanov' | 'hll' | 'hllc';
+    positivity 'scale' (rescale stage outputs) | 'repeat' (also repeat the step
+    with troubled cells of u^n flattened, Sec. 3.1)."""
 
     def __init__(self, N: int, k: int, cs: float = 1.0, precision: str = "f32", rk_stages: int | None = None,
                  cfl: float = 0.3, av: str = "vnr", alpha: float = 2.0, beta: float = 0.2, rho_floor: float = 1e-3,
                  nu_gate: float = 0.0, device: str | int = "cuda", stream: torch.cuda.Stream | None = None,
                  riemann: str = "rusanov", diffusion: float = 0.0, fused_infer: bool = False,
-                 x3_backend: str = "tcgen05"):
+                 x3_backend: str = "tcgen05", positivity: str = "scale"):
         self.L = B.lib()
         self.N, self.k, self.cs = N, k, cs
         self.b = nmodes(k)
@@ -56,7 +58,7 @@ class Solver:
         opts = B.Opts(self.prec, rk_stages, cfl, C.c_void_p(self.stream.cuda_stream),
                       (C.c_void_p * 3)(*[r.data_ptr() for r in self.regs]), self.vhat.data_ptr(),
                       self.ahat.data_ptr(), base + off, int(nb.value), B.RIEMANN[riemann],
-                      {"tcgen05": 0, "mma": 1}[x3_backend])
+                      {"tcgen05": 0, "mma": 1}[x3_backend], {"scale": 0, "repeat": 1}[positivity])
         torch.cuda.synchronize(self.device)
         h = C.c_void_p(0)
         rc = self.L.dg_init(C.byref(h), C.byref(self.mesh), k, cs, C.byref(self.nu), C.byref(opts))
