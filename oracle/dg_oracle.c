@@ -655,7 +655,8 @@ int orc_rhs_local(const orc_cfg* cfg, const double* patch, const double* ahat_c,
 /* higher-order weights of all variables are scaled by                       */
 /*   theta = (rho_mean - eps) / (rho_mean - rho_min);                         */
 /* a mean at or below the floor is a failure (the step is retried with a     */
-/* smaller dt by the time-step loop).                                        */
+/* smaller dt by the time-step loop); with pos_mode 1 only a mean at or      */
+/* below zero is.                                                            */
 /* ------------------------------------------------------------------------ */
 static int limit_impl(const orc_cfg* cfg, double* u, uint8_t* flag)
 {
@@ -672,15 +673,17 @@ static int limit_impl(const orc_cfg* cfg, double* u, uint8_t* flag)
         for (int q = 0; q < T.nq; ++q) rmin = fmin(rmin, eval(&T, uc, T.phi + q * b));
         for (int f = 0; f < 6; ++f)
             for (int s = 0; s < T.ns; ++s) rmin = fmin(rmin, eval(&T, uc, T.phif + ((size_t)f * T.ns + s) * b));
+        if (flag && rmin < 0.0) flag[c] |= ORC_MARK_NEGATIVE;
         if (rmin < eps) {
-            if (flag) flag[c] = 1;
             double rbar = uc[0];
             if (rbar > eps) {
                 double theta = (rbar - eps) / (rbar - rmin);
                 for (int var = 0; var < 4; ++var)
                     for (int l = 1; l < b; ++l) uc[var * b + l] *= theta;
                 status |= ORC_LIMITED;
-            } else {
+            } else if (cfg->pos_mode != 1 || rbar <= 0.0) {
+                /* pos_mode 1: only a mean that is not positive fails; a mean in
+                   (0, eps] is left as it is (its negative points mark the cell) */
                 status |= ORC_FAIL;
             }
         }
@@ -703,9 +706,10 @@ int orc_step(const orc_cfg* cfg, double* u, const double* ahat, double dt)
     return orc_step_flags(cfg, u, ahat, dt, 0.0, NULL);
 }
 
-/* orc_step; with flag != NULL also marks (flag[c] = 1) every cell that a stage
- * troubles: rho < eps at one of its volume or face points before the
- * rescaling, or after it a volume point with sum_d(|v_d| + cs) > vlim */
+/* orc_step; with flag != NULL also marks every cell that a stage troubles:
+ * ORC_MARK_NEGATIVE when rho < 0 at one of its volume or face points before the
+ * rescaling, ORC_MARK_FAST when after it a volume point has sum_d(|v_d| + cs)
+ * > vlim */
 int orc_step_flags(const orc_cfg* cfg, double* u, const double* ahat, double dt, double vlim, uint8_t* flag)
 {
     int b = orc_nmodes(cfg->k);
@@ -732,7 +736,7 @@ int orc_step_flags(const orc_cfg* cfg, double* u, const double* ahat, double dt,
 #pragma omp parallel for schedule(static)
             for (int c = 0; c < nc; ++c)
                 for (int q = 0; q < T.nq; ++q)
-                    if (point_speed(&T, cfg, us + (size_t)c * 4 * b, q) > vlim) flag[c] = 1;
+                    if (point_speed(&T, cfg, us + (size_t)c * 4 * b, q) > vlim) flag[c] |= ORC_MARK_FAST;
             tabs_free(&T);
         }
     }
@@ -749,16 +753,18 @@ int orc_step_flags(const orc_cfg* cfg, double* u, const double* ahat, double dt,
 /* scheme, with "scale all high-order weights" applied to the step's input): */
 /*   attempt: S = speed bound of u, dt = cfl h / ((k+1) S) (or fixed_dt)     */
 /*   times 2^-h; the step as orc_step_flags with vlim = ORC_REPEAT_SPEED S.   */
-/*   No troubled cell and no failed mean: accepted.  Otherwise the higher    */
-/*   modes of every troubled cell of u are multiplied by 1/2 (its first two  */
-/*   times in this step) or 0 (the third), and the step is attempted again   */
-/*   from the modified u; a troubled cell that is already flat, or a cell    */
-/*   mean at or below the floor, increments h.                               */
+/*   Every marked cell of u that is not flat has its higher modes multiplied  */
+/*   by 1/2 (its first two times in this step) or 0 (the third); a flat cell */
+/*   with negative density, or a cell mean at or below the floor, increments  */
+/*   h.  If nothing was scaled and h did not change, the attempt is accepted */
+/*   (the stage outputs keep their rescaling, as in orc_step); otherwise the  */
+/*   step is attempted again from the modified u.                            */
 /* The speed test (a stage output breaking the Courant condition that set    */
-/* its dt) is an addition to the paper's text.  Returns the status bits (with */
-/* ORC_REPEATED after more than one attempt), or -1 when the attempts or the */
-/* halvings run out; u then holds u^n with its troubled cells flattened.    */
-/* level [nc] (optional) receives how often each cell was scaled.            */
+/* its dt) is an addition to the paper's text; a flat cell's speed is its    */
+/* mean velocity, which the next step's dt takes into account.  Returns the  */
+/* status bits (with ORC_REPEATED after more than one attempt), or -1 when   */
+/* the attempts or the halvings run out; u then holds u^n with its troubled  */
+/* cells flattened.  level [nc] (optional): how often each cell was scaled.   */
 /* ------------------------------------------------------------------------ */
 int orc_step_repeat(const orc_cfg* cfg, double* u, const double* ahat, double fixed_dt, double* dt_used,
                     int* attempts, uint8_t* level)
@@ -775,16 +781,7 @@ int orc_step_repeat(const orc_cfg* cfg, double* u, const double* ahat, double fi
         memcpy(w, u, sizeof(double) * n);
         memset(flag, 0, nc);
         const int st = orc_step_flags(cfg, w, ahat, dt, ORC_REPEAT_SPEED * S, flag);
-        int any = 0;
-        for (size_t c = 0; c < nc; ++c) any |= flag[c];
-        if (!any && !(st & ORC_FAIL)) {
-            memcpy(u, w, sizeof(double) * n);
-            if (dt_used) *dt_used = dt;
-            if (attempts) *attempts = att + 1;
-            rc = st | (att > 0 ? ORC_REPEATED : 0);
-            break;
-        }
-        int flat = 0;
+        int flat = 0, scaled = 0;
         for (size_t c = 0; c < nc; ++c) {
             if (!flag[c]) continue;
             double* uc = u + c * 4 * b;
@@ -792,13 +789,21 @@ int orc_step_repeat(const orc_cfg* cfg, double* u, const double* ahat, double fi
             for (int var = 0; var < 4; ++var)
                 for (int l = 1; l < b; ++l) nonzero |= uc[var * b + l] != 0.0;
             if (!nonzero) {
-                flat = 1;
+                if (flag[c] & ORC_MARK_NEGATIVE) flat = 1;
                 continue;
             }
             const double f = lev[c] < 2 ? 0.5 : 0.0;
             for (int var = 0; var < 4; ++var)
                 for (int l = 1; l < b; ++l) uc[var * b + l] *= f;
             lev[c] += 1;
+            scaled = 1;
+        }
+        if (!scaled && !flat && !(st & ORC_FAIL)) {
+            memcpy(u, w, sizeof(double) * n);
+            if (dt_used) *dt_used = dt;
+            if (attempts) *attempts = att + 1;
+            rc = st | (att > 0 ? ORC_REPEATED : 0);
+            break;
         }
         if (flat || (st & ORC_FAIL)) ++h;
     }

@@ -51,11 +51,13 @@ typedef struct {
 #define ORC_REPEATED 4  /* the step was repeated with troubled cells
                            flattened (pos_mode 1)                            */
 
-/* positivity by repetition (pos_mode 1): a stage output whose volume-point
- * wave speed sum_d(|v_d| + cs) exceeds ORC_REPEAT_SPEED times the bound that
- * set dt troubles its cell; at most ORC_REPEAT_MAX attempts per step and
- * ORC_REPEAT_HALVINGS halvings of dt */
+/* positivity by repetition (pos_mode 1): a stage output with negative density
+ * at a Gauss point, or whose volume-point wave speed sum_d(|v_d| + cs) exceeds
+ * ORC_REPEAT_SPEED times the bound that set dt, troubles its cell; at most
+ * ORC_REPEAT_MAX attempts per step and ORC_REPEAT_HALVINGS halvings of dt */
 #define ORC_REPEAT_SPEED 1.5
+#define ORC_MARK_NEGATIVE 1  /* marks: rho < 0 at a point of a stage output   */
+#define ORC_MARK_FAST 2      /* a point faster than the bound                */
 #define ORC_REPEAT_MAX 32
 #define ORC_REPEAT_HALVINGS 6
 

@@ -48,6 +48,7 @@ RIEMANN = {"rusanov": 0, "hll": 1, "hllc": 2}
 POSITIVITY = {"scale": 0, "repeat": 1}
 REPEAT_SPEED = 1.5
 ST_LIMITED, ST_FAIL, ST_REPEATED = 1, 2, 4
+MARK_NEGATIVE, MARK_FAST = 1, 2
 
 
 MAX_MODES = 512
@@ -304,7 +305,8 @@ def speed_bound(cfg: Cfg, u: np.ndarray) -> float:
 
 def step_flags(cfg: Cfg, u: np.ndarray, ahat: np.ndarray | None, dt_: float, vlim: float):
     """One SSP-RK step in place as ``step``; returns (status, flag[nc]) with the
-    cells a stage troubled (rho < floor at a point, or a wave speed above vlim)."""
+    cells a stage troubled: MARK_NEGATIVE (rho < 0 at a point before the
+    rescaling) | MARK_FAST (after it, a wave speed above vlim)."""
     flag = np.zeros(cfg.N ** 3, dtype=np.uint8)
     st = lib().orc_step_flags(C.byref(cfg), _p(u), _p(ahat), dt_, vlim,
                               flag.ctypes.data_as(C.POINTER(C.c_uint8)))

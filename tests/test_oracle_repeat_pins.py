@@ -6,7 +6,8 @@ The flagged step is checked against the SSP-RK stages rebuilt here from the
 oracle's right-hand side and limiter, with the densities and wave speeds at the
 Gauss points evaluated independently (numpy's Legendre series); the repeated
 step against the plain step from the flattened input it reports; the halving of
-dt on a troubled flat cell against a hand-built state; and the whole procedure
+dt on a flat cell with negative density and the failure rule (a mean that is not
+positive) against hand-built states; and the whole procedure
 against the driven start from rest that the plain rescaling does not survive.
 """
 import math
@@ -59,24 +60,25 @@ def driven_start(N, k, nsteps, seed=11):
 
 
 def brute_flags(cfg, u, ah, dt, vlim):
-    """The SSP-RK3 stages from the oracle's rhs and limiter; a cell is marked when
-    a stage output has rho < floor at a volume or face point (before the
-    limiter) or, after it, a volume point with sum_d(|v_d| + cs) > vlim."""
+    """The SSP-RK3 stages from the oracle's rhs and limiter; a cell is marked
+    MARK_NEGATIVE when a stage output has rho < 0 at a volume or face point
+    (before the limiter) and MARK_FAST when, after it, a volume point has
+    sum_d(|v_d| + cs) > vlim."""
     Pv, Pf = point_tables(cfg.k)
     P = np.vstack([Pv, Pf])
     un = u.copy()
     us = u.copy()
-    flag = np.zeros(u.shape[0], dtype=bool)
+    flag = np.zeros(u.shape[0], dtype=np.uint8)
     smax = np.zeros(u.shape[0])
     for a, b in RK3:
         L = O.rhs(cfg, us, ah, dt)
         us = a * un + b * (us + dt * L)
-        flag |= (us[:, 0] @ P.T).min(1) < cfg.rho_floor
+        flag[(us[:, 0] @ P.T).min(1) < 0.0] |= O.MARK_NEGATIVE
         O.limit(cfg, us)
         rv = us[:, 0] @ Pv.T
         sp = sum(np.abs(us[:, 1 + d] @ Pv.T / rv) + cfg.cs for d in range(3)).max(1)
         smax = np.maximum(smax, sp)
-        flag |= sp > vlim
+        flag[sp > vlim] |= O.MARK_FAST
     return us, flag, smax
 
 
@@ -87,16 +89,16 @@ def test_flagged_step_marks_the_cells_its_stages_trouble():
     ref, fref, smax = brute_flags(cfg, u, ah, dt, 1e300)
     w = u.copy()
     st, flag = O.step_flags(cfg, w, ah, dt, 1e300)
-    assert fref.any() and (st & 1)
-    np.testing.assert_array_equal(flag.astype(bool), fref)
+    assert (fref == O.MARK_NEGATIVE).any() and (st & O.ST_LIMITED)
+    np.testing.assert_array_equal(flag, fref)
     np.testing.assert_allclose(w, ref, rtol=0, atol=1e-12)
     # wave-speed marks: a bound between two cells' stage maxima marks the faster half
     s = np.sort(smax)
     vlim = 0.5 * (s[len(s) // 2] + s[len(s) // 2 + 1])
     _, fref2, _ = brute_flags(cfg, u, ah, dt, vlim)
     _, flag2 = O.step_flags(cfg, u.copy(), ah, dt, vlim)
-    assert fref2.sum() > fref.sum()
-    np.testing.assert_array_equal(flag2.astype(bool), fref2)
+    assert ((fref2 & O.MARK_FAST) != 0).sum() == len(s) - len(s) // 2 - 1
+    np.testing.assert_array_equal(flag2, fref2)
 
 
 def test_repetition_is_the_plain_step_when_no_cell_is_troubled():
@@ -127,58 +129,73 @@ def test_repetition_is_the_plain_step_from_the_flattened_input():
     h = math.log2(O.dt(cfg, uf) / dtu)
     assert h == round(h) and 0 <= h <= 6
     ref = uf.copy()
-    st_ref = O.step(cfg, ref, ah, dtu)
+    st_ref = O.step(cfgr, ref, ah, dtu)
     np.testing.assert_array_equal(w, ref)
-    assert not (st_ref & 2)
-    # the accepted step troubles no cell, and every point is at or above the floor
+    assert not (st_ref & O.ST_FAIL)
+    # the accepted step troubles no cell but flat ones for their speed, and every
+    # point is at or above the floor
     _, flag = O.step_flags(cfg, uf.copy(), ah, dtu, O.REPEAT_SPEED * O.speed_bound(cfg, uf))
-    assert not flag.any()
+    flat = ~np.any(uf[:, :, 1:] != 0.0, axis=(1, 2))
+    assert not (flag & O.MARK_NEGATIVE).any() and not (flag.astype(bool) & ~flat).any()
     Pv, Pf = point_tables(2)
     assert (w[:, 0] @ np.vstack([Pv, Pf]).T).min() >= cfg.rho_floor * (1 - 1e-12)
     # scaling higher modes keeps the cell means: the mass is that of u^n
     assert abs(w[:, 0, 0].sum() - u[:, 0, 0].sum()) < 1e-12 * u[:, 0, 0].sum()
 
 
-def test_a_troubled_flat_cell_halves_dt():
-    # flat cells of one density rho0; cell c moves along +x and its left
-    # neighbour along -x, so c drains through its +x face.  The step is linear
-    # in rho0 (fluxes and Pi are, dt is not affected), so the drained fractions
-    # f1 (dt0) and f2 (dt0/2) measured at rho0 = 1 fix a rho0 whose full step
-    # ends below the floor and whose half step does not
+def _diverging_pair(N, k, rho0, V=3.0):
+    """Flat cells of density rho0 at rest but cell c, moving along +x, and its
+    left neighbour, moving along -x: c drains through its +x face."""
+    c = (2 * N + 2) * N + 2                     # cell (2, 2, 2)
+    u = I.uniform_state(N, k, rho=rho0)
+    u[c - 1, 1, 0] = -V * rho0
+    u[c, 1, 0] = V * rho0
+    return u, c
+
+
+def test_a_flat_cell_with_negative_density_halves_dt():
+    # with a prescribed dt of four CFL steps the two flat moving cells end with
+    # negative density; flat cells cannot be scaled, so dt is halved, and the
+    # step at half of it troubles no cell
+    N, k = 6, 1
+    cfgr = O.make_cfg(N, k, positivity="repeat")
+    u, c = _diverging_pair(N, k, 1.0)
+    dt4 = 4.0 * O.dt(cfgr, u)
+    _, flag = O.step_flags(cfgr, u.copy(), None, dt4, 1e300)
+    np.testing.assert_array_equal(np.nonzero(flag)[0], [c - 1, c])
+    assert (flag[[c - 1, c]] == O.MARK_NEGATIVE).all()
+    w = u.copy()
+    st, dtu, att, lev = O.step_repeat(cfgr, w, None, fixed_dt=dt4)
+    assert st >= 0 and (st & O.ST_REPEATED) and att == 2 and not lev.any()
+    assert dtu == 0.5 * dt4
+    ref = u.copy()
+    O.step(cfgr, ref, None, dtu)
+    np.testing.assert_array_equal(w, ref)
+
+
+def test_only_a_non_positive_mean_fails_the_repetition():
+    # the step is linear in rho0 (fluxes and Pi are; dt is not affected), so the
+    # fraction f that c loses in a CFL step, measured at rho0 = 1, fixes a rho0
+    # whose step ends with c's mean in (0, floor): a failure for the rescaling
+    # (dt halved, at most 3 times), a state that stands for the repetition
     N, k = 6, 1
     cfg = O.make_cfg(N, k)
-    c = (2 * N + 2) * N + 2                     # cell (2, 2, 2)
-    V = 3.0
-
-    def state(rho0):
-        u = I.uniform_state(N, k, rho=rho0)
-        u[c - 1, 1, 0] = -V * rho0
-        u[c, 1, 0] = V * rho0
-        return u
-
-    u1 = state(1.0)
+    cfgr = O.make_cfg(N, k, positivity="repeat")
+    u1, c = _diverging_pair(N, k, 1.0)
     dt0 = O.dt(cfg, u1)
-    a, b = u1.copy(), u1.copy()
+    a = u1.copy()
     O.step(cfg, a, None, dt0)
-    O.step(cfg, b, None, dt0 / 2)
-    f1, f2 = 1.0 - a[c, 0, 0], 1.0 - b[c, 0, 0]
-    assert 0 < f2 < f1 < 0.5
-    u = state(cfg.rho_floor / math.sqrt((1.0 - f1) * (1.0 - f2)))
-    assert O.dt(cfg, u) == dt0
-    # the step at dt0 troubles the flat cell (its mean reaches the floor)
-    st0, flag = O.step_flags(cfg, u.copy(), None, dt0, 1e300)
-    assert flag[c] and (st0 & O.ST_FAIL)
+    f = 1.0 - a[c, 0, 0]
+    assert 0.0 < f < 0.5
+    u, _ = _diverging_pair(N, k, cfg.rho_floor / (1.0 - 0.5 * f))
+    assert O.step(cfg, u.copy(), None, dt0) & O.ST_FAIL
     w = u.copy()
-    st, dtu, att, lev = O.step_repeat(O.make_cfg(N, k, positivity="repeat"), w, None)
-    assert st >= 0 and (st & O.ST_REPEATED) and att >= 2
-    assert not lev.any()                        # flat cells: dt halved, nothing scaled
-    h = math.log2(dt0 / dtu)
-    assert h == round(h) and 1 <= h <= 6
+    st, dtu, att, lev = O.step_repeat(cfgr, w, None)
+    assert st >= 0 and not (st & O.ST_FAIL) and att == 1 and dtu == dt0
+    assert 0.0 < w[c, 0, 0] < cfg.rho_floor
     ref = u.copy()
-    O.step(cfg, ref, None, dtu)
+    O.step(cfgr, ref, None, dt0)
     np.testing.assert_array_equal(w, ref)
-    Pv, Pf = point_tables(k)
-    assert (w[:, 0] @ np.vstack([Pv, Pf]).T).min() >= cfg.rho_floor
 
 
 @pytest.mark.timeout(300)
