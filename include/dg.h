@@ -237,14 +237,16 @@ int dg_project_velocity(dg_ctx* ctx, const void* u_in, void* vhat_out);
  *
  * DG_POS_REPEAT (Sec. 3.1, last paragraph, read as the troubled-cell
  * procedure the paper gives for its finite-volume scheme): a cell is troubled
- * when a stage output has rho below the floor at one of its volume or face
- * Gauss points, or a volume point with sum_d(|v_d| + cs) above 1.5 times the
- * bound S that set dt (the stage breaks its step's Courant condition; this
- * test is an addition to the paper's text).  If any cell is troubled, the
- * modes l > 0 of every troubled cell of u^n are multiplied by 1/2 (the first
- * two times in the step) or 0 (the third) and the step is computed again from
- * the modified u^n, with dt from its own S; a troubled cell that is already
- * flat, or a cell mean at the floor, halves dt for the following attempts.
+ * when a stage output has negative rho at one of its volume or face Gauss
+ * points (before the rescaling), or a volume point with sum_d(|v_d| + cs)
+ * above 1.5 times the bound S that set dt (the stage breaks its step's Courant
+ * condition; this test is an addition to the paper's text).  The modes l > 0
+ * of every troubled cell of u^n that is not flat are multiplied by 1/2 (the
+ * first two times in the step) or 0 (the third) and the step is computed
+ * again from the modified u^n, with dt from its own S; a flat cell with
+ * negative density, or a cell mean at the floor, halves dt for the following
+ * attempts.  An attempt whose only troubled cells are flat ones marked for
+ * their speed stands (with the rescaled stage outputs).
  * At most 32 attempts and 6 halvings, then DG_EPOSITIVITY with the state left
  * at u^n with its troubled cells flattened.  One more stream synchronisation
  * per repeated attempt; DG_ST_REPEATED reports that a step was repeated. */

@@ -1315,10 +1315,11 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
         const bool fused = learned && ctx->nu.fused_infer;
         const int pb = ctx->pb;
         // positivity by repetition (Sec. 3.1, last paragraph): the stages mark the
-        // cells they trouble; the marked cells of u^n (register A) are scaled towards
-        // their flat expansion and the step is attempted again; a marked cell that
-        // is already flat, or a failed cell mean, halves dt.  Otherwise the
-        // rescaled stage outputs stand and a failed mean retries with dt/2, dt/4, dt/8
+        // cells they trouble; the marked cells of u^n (register A) that are not flat
+        // are scaled towards their flat expansion and the step is attempted again; a
+        // flat cell with negative density, or a failed cell mean, halves dt.
+        // Otherwise the rescaled stage outputs stand and a failed mean retries with
+        // dt/2, dt/4, dt/8
         const bool repeat = ctx->repeat;
         unsigned char* marks = repeat ? ctx->trouble : nullptr;
         if (repeat && ctx->marks_dirty) {
@@ -1409,7 +1410,13 @@ int dg_step(dg_ctx* ctx, int nsteps, double fixed_dt, double* t_out, double* dt_
             unsigned int fst = 0u;
             CK(cudaMemcpyAsync(&fst, &ctx->ctl->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->st));
             CK(cudaStreamSynchronize(ctx->st));
-            if ((fst & DG_ST_FLAT_) || (status & DG_ST_FAIL)) ++halvings;
+            if ((fst & DG_ST_FLAT_) || (status & DG_ST_FAIL)) {
+                ++halvings;
+            } else if (!(fst & DG_ST_SCALED_)) {
+                // only flat cells marked for their speed: the attempt stands
+                ok = true;
+                break;
+            }
         }
         status &= 0xffu;
         if (repeat && attempts > 1) status |= DG_ST_REPEATED;

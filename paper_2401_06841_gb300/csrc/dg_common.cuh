@@ -141,9 +141,15 @@ enum { F_DT = 1, F_FORCE = 2 };
 #define DG_ST_FAIL_ 2u
 #define DG_ST_NONFINITE_ 4u
 // positivity by repetition (internal, never reported): a stage marked a
-// troubled cell; the flattening found a troubled cell that was already flat
+// troubled cell; the flattening found a flat cell with negative density, and
+// scaled some cell
 #define DG_ST_TROUBLED_ 0x100u
 #define DG_ST_FLAT_ 0x200u
+#define DG_ST_SCALED_ 0x400u
+// per-cell marks: negative density at a Gauss point of a stage output (before
+// its rescaling); a volume point of a stage output faster than the bound
+#define DG_MARK_NEGATIVE 1u
+#define DG_MARK_FAST 2u
 // a stage output whose volume-point sum_d(|v_d| + cs) exceeds this factor times
 // the bound that set dt troubles its cell
 #define DG_REPEAT_SPEED 1.5

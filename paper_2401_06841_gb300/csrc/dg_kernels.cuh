@@ -381,7 +381,9 @@ __global__ void __launch_bounds__(256) k_l1(const T* tab, const T* uA, const T* 
 // ---------------------------------------------------------------------------
 // K_flatten: positivity by repetition (Sec. 3.1, last paragraph): the high-order
 // weights of every cell a stage marked are scaled towards the flat expansion
-// before the step is computed again.  One thread per cell; cells are rare.
+// before the step is computed again (DG_ST_SCALED_); a flat marked cell with
+// negative density reports DG_ST_FLAT_ (dt is halved), a flat cell marked for
+// its speed alone is left as it is.  One thread per cell; marks are rare.
 // ---------------------------------------------------------------------------
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_flatten(T* u, unsigned char* trouble, unsigned char* level, long ncell,
@@ -389,14 +391,15 @@ __global__ void __launch_bounds__(256) k_flatten(T* u, unsigned char* trouble, u
 {
     constexpr int b = Dims<K>::b;
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (long)gridDim.x * blockDim.x) {
-        if (!trouble[c]) continue;
+        const unsigned char m = trouble[c];
+        if (!m) continue;
         trouble[c] = 0;
         T* uc = u + c * 4 * b;
         bool nonzero = false;
         for (int var = 0; var < 4; ++var)
             for (int l = 1; l < b; ++l) nonzero |= uc[var * b + l] != T(0);
         if (!nonzero) {
-            atomicOr(&ctl->status, DG_ST_FLAT_);
+            if (m & DG_MARK_NEGATIVE) atomicOr(&ctl->status, DG_ST_FLAT_);
             continue;
         }
         const unsigned char lv = level[c];
@@ -404,6 +407,7 @@ __global__ void __launch_bounds__(256) k_flatten(T* u, unsigned char* trouble, u
         for (int var = 0; var < 4; ++var)
             for (int l = 1; l < b; ++l) uc[var * b + l] *= f;
         level[c] = (unsigned char)(lv + 1);
+        atomicOr(&ctl->status, DG_ST_SCALED_);
     }
 }
 

@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256, 2) k5_volume(const __grid_constant__ T5Ar
                 const float vx = v[1] * ir, vy = v[2] * ir, vz = v[3] * ir;
                 const float divv = (v[7] * two_h - (vx * v[4] + vy * v[5] + vz * v[6]) * two_h) * ir;
                 if (chk && c < nvalid && fabsf(vx) + fabsf(vy) + fabsf(vz) > vlim) {
-                    a.trouble[c0 + c] = 1;
+                    a.trouble[c0 + c] |= DG_MARK_FAST;
                     atomicOr(&a.ctl->status, DG_ST_TROUBLED_);
                 }
                 float Pi = 0.f;
@@ -960,16 +960,17 @@ __global__ void __launch_bounds__(256, 2) k5_faces(const __grid_constant__ T5Arg
                         mn = other < mn ? other : mn;
                     }
                     const float rbar = rr[0];
+                    if (a.trouble && mn < 0.f) {
+                        const long cc = c0 + 2 * w + cl;
+                        if (lane == 0 && cc < a.ncell) a.trouble[cc] |= DG_MARK_NEGATIVE;
+                        st |= DG_ST_TROUBLED_;
+                    }
                     if (mn < eps) {
-                        if (a.trouble) {
-                            const long cc = c0 + 2 * w + cl;
-                            if (lane == 0 && cc < a.ncell) a.trouble[cc] = 1;
-                            st |= DG_ST_TROUBLED_;
-                        }
                         if (rbar > eps) {
                             thr[cl] = (rbar - eps) / (rbar - mn);
                             st |= DG_ST_LIMITED_;
-                        } else {
+                        } else if (!a.trouble || !(rbar > 0.f)) {
+                            // positivity by repetition: a mean in (0, eps] stands
                             st |= DG_ST_FAIL_;
                         }
                     }
@@ -1125,7 +1126,7 @@ __global__ void __launch_bounds__(256, 3) k5_project(const __grid_constant__ T5A
                     smax = sp > smax ? sp : smax;
                 }
                 if (CHK && c < nvalid && fabsf(vx) + fabsf(vy) + fabsf(vz) > vlim) {
-                    a.trouble[c0 + c] = 1;
+                    a.trouble[c0 + c] |= DG_MARK_FAST;
                     atomicOr(&a.ctl->status, DG_ST_TROUBLED_);
                 }
                 x[pp][0] = vx * wq8;

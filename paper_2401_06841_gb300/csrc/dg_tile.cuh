@@ -579,7 +579,7 @@ __device__ __forceinline__ void tile_project(T* sm, const T* sU, const T* tabs, 
                 // positivity by repetition: a stage output faster than the
                 // Courant condition of its step allows marks its cell
                 if (a.trouble && c0 + c < a.ncell && fabs(vv[it][0]) + fabs(vv[it][1]) + fabs(vv[it][2]) > vlim) {
-                    a.trouble[c0 + c] = 1;
+                    a.trouble[c0 + c] |= DG_MARK_FAST;
                     atomicOr(&a.ctl->status, DG_ST_TROUBLED_);
                 }
             }
@@ -1285,13 +1285,16 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                             mn = other < mn ? other : mn;
                         }
                         const T rbar = r[0];
+                        if (a.trouble && mn < T(0)) {
+                            if (lane == 0 && c0 + c < a.ncell) a.trouble[c0 + c] |= DG_MARK_NEGATIVE;
+                            st |= DG_ST_TROUBLED_;
+                        }
                         if (mn < eps) {
-                            if (a.trouble && lane == 0 && c0 + c < a.ncell) a.trouble[c0 + c] = 1;
-                            if (a.trouble) st |= DG_ST_TROUBLED_;
                             if (rbar > eps) {
                                 thr[cl] = (rbar - eps) / (rbar - mn);
                                 st |= DG_ST_LIMITED_;
-                            } else {
+                            } else if (!a.trouble || !(rbar > T(0))) {
+                                // positivity by repetition: a mean in (0, eps] stands
                                 st |= DG_ST_FAIL_;
                             }
                         }
