@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -23,6 +24,7 @@
 #include <dlfcn.h>
 #include "dg_launch.cuh"
 #include "dg_mlp.cuh"
+#include "dg_tables.cuh"
 #include "dg_tile.cuh"
 
 using namespace dg;
@@ -32,64 +34,10 @@ using namespace dg;
 // ---------------------------------------------------------------------------
 namespace {
 
-// Golub-Welsch: nodes = eigenvalues of the symmetric tridiagonal Jacobi matrix
-// with off-diagonal j/sqrt(4j^2-1); weights = 2 * (first eigenvector entry)^2.
-void gauss_rule(int n, long double* x, long double* w)
-{
-    std::vector<long double> A(n * n, 0.0L), V(n * n, 0.0L);
-    for (int j = 1; j < n; ++j) {
-        long double bj = j / sqrtl(4.0L * j * j - 1.0L);
-        A[(j - 1) * n + j] = A[j * n + j - 1] = bj;
-    }
-    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0L;
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        long double off = 0.0L;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
-        if (off < 1e-40L) break;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                long double apq = A[p * n + q];
-                if (fabsl(apq) < 1e-300L) continue;
-                long double theta = (A[q * n + q] - A[p * n + p]) / (2.0L * apq);
-                long double t = (theta >= 0 ? 1.0L : -1.0L) / (fabsl(theta) + sqrtl(theta * theta + 1.0L));
-                long double c = 1.0L / sqrtl(t * t + 1.0L), s = t * c;
-                for (int k = 0; k < n; ++k) {  // A <- A J
-                    long double akp = A[k * n + p], akq = A[k * n + q];
-                    A[k * n + p] = c * akp - s * akq;
-                    A[k * n + q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < n; ++k) {  // A <- J^T A
-                    long double apk = A[p * n + k], aqk = A[q * n + k];
-                    A[p * n + k] = c * apk - s * aqk;
-                    A[q * n + k] = s * apk + c * aqk;
-                }
-                for (int k = 0; k < n; ++k) {  // V <- V J
-                    long double vkp = V[k * n + p], vkq = V[k * n + q];
-                    V[k * n + p] = c * vkp - s * vkq;
-                    V[k * n + q] = s * vkp + c * vkq;
-                }
-            }
-    }
-    std::vector<int> idx(n);
-    for (int i = 0; i < n; ++i) idx[i] = i;
-    for (int i = 0; i < n; ++i)  // sort ascending
-        for (int j = i + 1; j < n; ++j)
-            if (A[idx[j] * n + idx[j]] < A[idx[i] * n + idx[i]]) std::swap(idx[i], idx[j]);
-    for (int i = 0; i < n; ++i) {
-        long double xi = A[idx[i] * n + idx[i]];
-        x[i] = fabsl(xi) < 1e-30L ? 0.0L : xi;
-        w[i] = 2.0L * V[0 * n + idx[i]] * V[0 * n + idx[i]];
-    }
-    for (int i = 0; i < n / 2; ++i) {  // enforce the exact symmetry of the rule
-        long double xs = 0.5L * (x[n - 1 - i] - x[i]), ws = 0.5L * (w[i] + w[n - 1 - i]);
-        x[i] = -xs;
-        x[n - 1 - i] = xs;
-        w[i] = w[n - 1 - i] = ws;
-    }
-}
+using tables::bf16_rne;
+using tables::gauss_rule;
+using tables::pnorm;
 
-// normalised Legendre sqrt(2m+1) P_m(x), three-term recurrence
 // Recovery weights of the face gradient: on the union of two cells, s in
 // half-cell units (left cell s = xi - 1, right cell s = xi + 1), the polynomial
 // r(s) = sum_{j <= 2K+1} d_j P_j(s/2) whose normalised-Legendre moments on each
@@ -154,18 +102,6 @@ void recovery_weights(int K, double* wL, double* wR)
     }
 }
 
-long double pnorm(int m, long double x)
-{
-    long double p0 = 1.0L, p1 = x;
-    if (m == 0) return 1.0L;
-    for (int j = 2; j <= m; ++j) {
-        long double p2 = ((2.0L * j - 1.0L) * x * p1 - (j - 1.0L) * p0) / j;
-        p0 = p1;
-        p1 = p2;
-    }
-    return sqrtl(2.0L * m + 1.0L) * p1;
-}
-
 template <int K>
 std::vector<double> build_tables()
 {
@@ -227,149 +163,14 @@ std::vector<double> tables_for(int K)
     return build_tables<3>();
 }
 
-// split of x into bfloat16 hi + lo, each rounded to nearest even
-uint16_t bf16_rne(float x)
-{
-    uint32_t u;
-    std::memcpy(&u, &x, 4);
-    const uint32_t lsb = (u >> 16) & 1u;
-    u += 0x7fffu + lsb;
-    return (uint16_t)(u >> 16);
-}
-float bf16_to_float(uint16_t h)
-{
-    const uint32_t u = (uint32_t)h << 16;
-    float x;
-    std::memcpy(&x, &u, 4);
-    return x;
-}
-
-// dense B[K][N] (row-major, zero padded) -> mma.sync m16n8k16 B fragments:
-// words [K/16][N/8][lane][hi(k=2t,2t+1) hi(k=2t+8,2t+9) lo(...) lo(...)], n = g
-void to_fragments(const std::vector<double>& B, int Kd, int Nd, uint32_t* out)
-{
-    for (int kt = 0; kt < Kd / 16; ++kt)
-        for (int nt = 0; nt < Nd / 8; ++nt)
-            for (int lane = 0; lane < 32; ++lane) {
-                const int g = lane >> 2, t = lane & 3, n = nt * 8 + g;
-                uint32_t w[4];
-                for (int half = 0; half < 2; ++half) {
-                    const int k0 = kt * 16 + 2 * t + 8 * half;
-                    uint16_t hi[2], lo[2];
-                    for (int j = 0; j < 2; ++j) {
-                        const float x = (float)B[(size_t)(k0 + j) * Nd + n];
-                        hi[j] = bf16_rne(x);
-                        lo[j] = bf16_rne(x - bf16_to_float(hi[j]));
-                    }
-                    w[half] = (uint32_t)hi[0] | ((uint32_t)hi[1] << 16);
-                    w[2 + half] = (uint32_t)lo[0] | ((uint32_t)lo[1] << 16);
-                }
-                for (int j = 0; j < 4; ++j) out[(((size_t)kt * (Nd / 8) + nt) * 32 + lane) * 4 + j] = w[j];
-            }
-}
-
-// tables of the tile kernels (TileTab<K, BK>): the basis at the volume points
-// (zero padded), its weighted transpose, the 2D face basis and its weighted
-// transpose -- dense for the CUDA-core products, fragment-ordered split-BF16
-// for the tensor-core products -- then the dense basis at the volume and
-// face points for the exact positivity check.  Returned as raw 32/64-bit
-// words of the element type (float bits for BK_X3 fragments).
-template <int K, int BK>
-std::vector<double> build_tile_tables_dense(std::vector<double>& phi_d, std::vector<double>& wphi_d,
-                                            std::vector<double>& psi_d, std::vector<double>& psil_d)
-{
-    using Cf = TileCfg<K, BK>;
-    using TT = TileTab<K, BK>;
-    constexpr int b = Cf::b, n = Cf::n, nq = Cf::nq, ns = Cf::ns, nf = Cf::nf;
-    constexpr int KP = Cf::KP, NQP = Cf::NQP, NP = Cf::NP, B2 = Cf::B2, B2K = Cf::B2K, NSP = Cf::NSP, B2N = Cf::B2N;
-    constexpr Modes<K> M{};
-    constexpr Modes2<K> M2{};
-    std::vector<double> t(TT::total, 0.0);
-    phi_d.assign((size_t)KP * NQP, 0.0);
-    wphi_d.assign((size_t)NQP * NP, 0.0);
-    psi_d.assign((size_t)B2K * NSP, 0.0);
-    psil_d.assign((size_t)NSP * B2N, 0.0);
-    long double xg[16], wg[16];
-    gauss_rule(n, xg, wg);
-    auto phi = [&](int l, long double a, long double bb, long double c) {
-        return pnorm(M.i[l], a) * pnorm(M.j[l], bb) * pnorm(M.l[l], c);
-    };
-    for (int q = 0; q < nq; ++q) {
-        const int ia = q % n, ib = (q / n) % n, ic = q / (n * n);
-        const long double wq = wg[ia] * wg[ib] * wg[ic] / 8.0L;
-        for (int l = 0; l < b; ++l) {
-            const long double p = phi(l, xg[ia], xg[ib], xg[ic]);
-            phi_d[(size_t)l * NQP + q] = (double)p;
-            wphi_d[(size_t)q * NP + l] = (double)(wq * p);
-            t[TT::phiv + l * nq + q] = (double)p;
-        }
-    }
-    for (int s = 0; s < ns; ++s) {
-        const int a = s % n, c = s / n;
-        const long double ws = wg[a] * wg[c];
-        for (int p2 = 0; p2 < B2; ++p2) {
-            const long double ps = pnorm(M2.p[p2], xg[a]) * pnorm(M2.q[p2], xg[c]);
-            psi_d[(size_t)p2 * NSP + s] = (double)ps;
-            psil_d[(size_t)s * B2N + p2] = (double)(ws * ps);
-        }
-    }
-    for (int f = 0; f < 6; ++f) {
-        const int d = f >> 1;
-        const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
-        for (int s = 0; s < ns; ++s) {
-            long double xi[3];
-            xi[d] = (f & 1) ? 1.0L : -1.0L;
-            xi[t1] = xg[s % n];
-            xi[t2] = xg[s / n];
-            for (int l = 0; l < b; ++l) t[TT::phif + l * nf + f * ns + s] = (double)phi(l, xi[0], xi[1], xi[2]);
-        }
-    }
-    if (BK == BK_FMA) {
-        std::copy(phi_d.begin(), phi_d.end(), t.begin() + Cf::oPhi);
-        std::copy(wphi_d.begin(), wphi_d.end(), t.begin() + Cf::oWPhi);
-        std::copy(psi_d.begin(), psi_d.end(), t.begin() + Cf::oPsi);
-        std::copy(psil_d.begin(), psil_d.end(), t.begin() + Cf::oPsiL);
-    }
-    return t;
-}
-
-// tile tables in the element type: FP64, FP32, or FP32 with X3 fragments
-template <int K>
-std::vector<char> tile_tables_bytes(int prec)
-{
-    std::vector<double> ph, wp, ps, pl;
-    if (prec == DG_PREC_F64) {
-        std::vector<double> t = build_tile_tables_dense<K, BK_FMA>(ph, wp, ps, pl);
-        std::vector<char> out(t.size() * sizeof(double));
-        std::memcpy(out.data(), t.data(), out.size());
-        return out;
-    }
-    if (prec == DG_PREC_F32) {
-        std::vector<double> t = build_tile_tables_dense<K, BK_FMA>(ph, wp, ps, pl);
-        std::vector<float> f(t.begin(), t.end());
-        std::vector<char> out(f.size() * sizeof(float));
-        std::memcpy(out.data(), f.data(), out.size());
-        return out;
-    }
-    using Cf = TileCfg<K, BK_X3>;
-    std::vector<double> t = build_tile_tables_dense<K, BK_X3>(ph, wp, ps, pl);
-    std::vector<float> f(t.begin(), t.end());
-    std::vector<uint32_t> w(f.size());
-    std::memcpy(w.data(), f.data(), f.size() * sizeof(float));
-    to_fragments(ph, Cf::KP, Cf::NQP, w.data() + Cf::oPhi);
-    to_fragments(wp, Cf::NQP, Cf::NP, w.data() + Cf::oWPhi);
-    to_fragments(ps, Cf::B2K, Cf::NSP, w.data() + Cf::oPsi);
-    to_fragments(pl, Cf::NSP, Cf::B2N, w.data() + Cf::oPsiL);
-    std::vector<char> out(w.size() * sizeof(uint32_t));
-    std::memcpy(out.data(), w.data(), out.size());
-    return out;
-}
-
+// tables of the tile kernels in the element type of prec (dg_tables.cuh)
 std::vector<char> tile_tables_for(int K, int prec)
 {
-    if (K == 1) return tile_tables_bytes<1>(prec);
-    if (K == 2) return tile_tables_bytes<2>(prec);
-    return tile_tables_bytes<3>(prec);
+    std::unique_ptr<tables::Work> w(new tables::Work);
+    std::vector<char> out(sizeof(double) * tables::kTableWordsMax);
+    const size_t n = tables::fill_tile_tables_for(K, prec, *w, reinterpret_cast<unsigned char*>(out.data()), out.size());
+    out.resize(n);
+    return out;
 }
 
 // Weights (a, b) of an SSP-RK stage out = a u^n + b (u + dt L) as the kernels
