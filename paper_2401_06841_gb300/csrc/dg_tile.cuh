@@ -537,7 +537,7 @@ __device__ __forceinline__ void forcing_sums(const T* sm, const T* sU, const TAr
 
 template <typename T, int K, int BK, bool VABS = false>
 __device__ __forceinline__ void tile_project(T* sm, const T* sU, const T* tabs, const TArgs<T>& a, long c0, bool dt_flag,
-                                             T& smax, double* sums, bool with_sums, T vlim = T(0))
+                                             T& smax, double* sums, bool with_sums)
 {
     constexpr int NPR = VABS ? 4 : 3;  // projected rows per cell: v (and |v|)
     using C = TileCfg<K, BK>;
@@ -578,7 +578,8 @@ __device__ __forceinline__ void tile_project(T* sm, const T* sU, const T* tabs, 
                 }
                 // positivity by repetition: a stage output faster than the
                 // Courant condition of its step allows marks its cell
-                if (a.trouble && c0 + c < a.ncell && fabs(vv[it][0]) + fabs(vv[it][1]) + fabs(vv[it][2]) > vlim) {
+                if (a.trouble && c0 + c < a.ncell &&
+                    fabs(vv[it][0]) + fabs(vv[it][1]) + fabs(vv[it][2]) > T(DG_REPEAT_SPEED * a.ctl->sn - 3.0 * a.ph.cs)) {
                     a.trouble[c0 + c] |= DG_MARK_FAST;
                     atomicOr(&a.ctl->status, DG_ST_TROUBLED_);
                 }
@@ -797,7 +798,6 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
     constexpr bool STAGE = (MODE == TM_STAGE || MODE == TM_STAGE_VABS);
     const bool do_proj = (MODE == TM_PROJECT) || (STAGE && (a.flags & F_NEXTPROJ));
     T dt = T(0), ab0 = T(0), ab1 = T(0), ab2 = T(0);
-    T vlim = T(0);  // positivity by repetition: bound of sum_d |v_d| at the stage output's points
     AvCoef<T> avc{};
     const T diff_vol = T(-4.0 * a.ph.eps / (a.ph.h * a.ph.h));
     if constexpr (MODE != TM_PROJECT) {
@@ -811,7 +811,6 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
             dt = T(dtd);
             avc = av_coef<T>(a.ph, dtd);
             if (blockIdx.x == 0 && tid == 0) a.ctl->dt = dtd;
-            vlim = T(DG_REPEAT_SPEED * sn - 3.0 * a.ph.cs);
         } else {
             dt = T(a.dt_pimax);
             avc = av_coef<T>(a.ph, a.dt_pimax);
@@ -1339,7 +1338,7 @@ __global__ void __launch_bounds__(256) k_tile(TArgs<T> a)
                 if (tile + gridDim.x < ntile) issue(tile + gridDim.x, sR);
                 if (do_proj) {
                     tile_project<T, K, BK, MODE == TM_STAGE_VABS>(sm, sU, tabs, a, c0, (a.flags & F_DT) != 0, smax,
-                                                                 sums, false, vlim);
+                                                                 sums, false);
                     if constexpr (MODE == TM_STAGE_VABS) {
                         if (a.nu_next) tile_nu<T, K, BK>(sm, sU, a, c0);
                     }
