@@ -571,6 +571,52 @@ def config3_arm(args, dev):
             "state_after": {k_: d[k_] for k_ in ("mach", "rho_min", "rho_max", "av_frac")}}
 
 
+def driven_start_arm(args, dev):
+    """Mach-3 OU driving from rest (rho = 1, v = 0; zeta 0.5, seed 11), --start-N^3
+    cells, k=2, SSP-RK3, FP32, in both positivity modes (Sec. 3.1): the rescaling
+    of the stage outputs, run until it fails or reaches the end time, and the
+    repetition of troubled steps, run to --start-t.  Reports how far each got,
+    the repeated attempts (flatten launches) and the state at the end."""
+    import math
+    import torch
+    from paper_2401_06841_gb300 import Solver
+    from paper_2401_06841_gb300 import _lib as B
+    N, k, t_end = args.start_N, 2, args.start_t
+    b = (k + 1) * (k + 2) * (k + 3) // 6
+    out = {"workload": "Mach-3 OU driving (zeta 0.5, seed 11) from rho = 1, v = 0, %d^3 cells, DG k=2 (P2), "
+                       "SSP-RK3, FP32, to t = %g" % (N, t_end)}
+    u0 = torch.zeros(N ** 3, 4, b, dtype=torch.float32, device=dev)
+    u0[:, 0, 0] = 1.0
+    for pos in ("scale", "repeat"):
+        s = Solver(N, k, precision="f32", rk_stages=3, av="vnr", device=dev, positivity=pos)
+        s.set_state(u0)
+        s.set_forcing(mach=3.0, zeta=0.5, seed=11)
+        s.profile(True)
+        t, steps, err = 0.0, 0, None
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(s.stream)
+        try:
+            while t < t_end and steps < 200000:
+                t, _ = s.step(10)
+                steps += 10
+                if pos == "scale" and steps % 100 == 0 and not (s.diagnostics()["max_speed"] < 1e3):
+                    err = "wave speed above 1e3 cs"
+                    break
+        except B.DGError as e:
+            err = str(e)
+        b_ev.record(s.stream)
+        torch.cuda.synchronize()
+        ms = a_ev.elapsed_time(b_ev)
+        prof = s.profile_read()
+        d = s.diagnostics()
+        s.close()
+        out[pos] = {"t_reached": t, "steps": steps, "failed": err, "wall_s": ms * 1e-3,
+                    "flatten_launches": int(prof["n_other"]) if pos == "repeat" else 0,
+                    "state_at_end": {k_: (d[k_] if math.isfinite(d[k_]) else None)
+                                     for k_ in ("mach", "rho_min", "rho_max", "max_speed")}}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -603,6 +649,10 @@ def main():
     ap.add_argument("--c3-N", dest="c3_N", type=int, default=128, help="mesh of the strong-shock configuration")
     ap.add_argument("--c3-steps", dest="c3_steps", type=int, default=100)
     ap.add_argument("--no-c3", dest="no_c3", action="store_true")
+    ap.add_argument("--start-N", dest="start_N", type=int, default=64,
+                    help="mesh of the driven start from rest in both positivity modes")
+    ap.add_argument("--start-t", dest="start_t", type=float, default=0.2)
+    ap.add_argument("--no-start", dest="no_start", action="store_true")
     ap.add_argument("--nu-gate", dest="nu_gate", type=float, default=1.0,
                     help="learned variants: cells with nu/(cs h/p) below this get no viscous pressure, and "
                          "tiles of 16 such cells skip div v")
@@ -748,6 +798,8 @@ def main():
     torch.cuda.empty_cache()
     if not args.no_c3:
         line["config3"] = config3_arm(args, dev)
+    if not args.no_start:
+        line["driven_start"] = driven_start_arm(args, dev)
     if not args.no_adiabatic:
         line["adiabatic"] = adiabatic_arm(args, dev, state_seed, flush, world)
         line["adiabatic_near_isothermal"] = adiabatic_arm(args, dev, state_seed, flush, world, near_isothermal=True)
