@@ -1528,6 +1528,37 @@ static void adi_face_flux(int solver, double gamma, int d, const double WL[5], c
         orc_adi_rusanov(gamma, d, WL, WR, F);
 }
 
+/* the boundary faces along d of the last cell cU (its face xi_d = +1, at
+ * coordinate 1) and of the first cell cD (its face xi_d = -1, at coordinate 0):
+ * ghost states by cfg->bc[d]; each flux goes to its own cell only */
+static void adi_boundary_faces(const orc_cfg* cfg, double gamma, const tabs* T, int d, const double* u,
+                               const double* prim, int cU, int cD, double h, double* dudt)
+{
+    const int b = T->b, ns = T->ns, bc = cfg->bc[d];
+    for (int upper = 0; upper < 2; ++upper) {
+        const int c = upper ? cU : cD;
+        const double* ph = T->phif + ((size_t)(d * 2 + upper) * ns) * b;
+        for (int s = 0; s < ns; ++s) {
+            double W[5], G[5], F[5];
+            W[0] = eval(T, u + (size_t)c * 5 * b, ph + s * b);
+            for (int i = 0; i < 4; ++i) W[1 + i] = eval(T, prim + ((size_t)c * 4 + i) * b, ph + s * b);
+            for (int i = 0; i < 5; ++i) G[i] = W[i];
+            if (bc == ORC_BC_REFLECT) G[1 + d] = -W[1 + d];
+            if (bc == ORC_BC_INFLOW && !upper)
+                for (int i = 0; i < 5; ++i) G[i] = cfg->inflow[i];
+            /* along +e_d: the ghost is the upper neighbour of cU, the lower one of cD */
+            if (upper)
+                adi_face_flux(cfg->riemann, gamma, d, W, G, F);
+            else
+                adi_face_flux(cfg->riemann, gamma, d, G, W, F);
+            const double sgn = upper ? -1.0 : 1.0;
+            for (int var = 0; var < 5; ++var)
+                for (int l = 0; l < b; ++l)
+                    dudt[((size_t)c * 5 + var) * b + l] += sgn * T->ws[s] * ph[s * b + l] * F[var] / (4.0 * h);
+        }
+    }
+}
+
 /* vNR viscous pressure with the local sound speed in the bulk term */
 double orc_adi_vnr(const orc_cfg* cfg, double rho, double c, double divv, double dt)
 {
@@ -1658,7 +1689,9 @@ static int adi_rhs_impl(const orc_cfg* cfg, double gamma, const double* u, const
         *work = w * h * h * h;
     }
 
-    /* surface integral: one pass over interfaces, each flux added to both cells */
+    /* surface integral: one pass over interfaces, each flux added to both cells;
+     * along an axis with boundaries the interface between the last and the first
+     * cell is replaced by the two boundary faces, each with its ghost state */
     for (int iz = 0; iz < N; ++iz)
         for (int iy = 0; iy < N; ++iy)
             for (int ix = 0; ix < N; ++ix) {
@@ -1667,6 +1700,11 @@ static int adi_rhs_impl(const orc_cfg* cfg, double gamma, const double* u, const
                     int cR = cell_index(N, ix + (d == 0), iy + (d == 1), iz + (d == 2));
                     const double* phL = T.phif + ((size_t)(d * 2 + 1) * ns) * b; /* xi_d = +1 in L */
                     const double* phR = T.phif + ((size_t)(d * 2 + 0) * ns) * b; /* xi_d = -1 in R */
+                    const int i_d = d == 0 ? ix : (d == 1 ? iy : iz);
+                    if (cfg->bc[d] != ORC_BC_PERIODIC && i_d == N - 1) {
+                        adi_boundary_faces(cfg, gamma, &T, d, u, prim, cL, cR, h, dudt);
+                        continue;
+                    }
                     for (int s = 0; s < ns; ++s) {
                         double WL[5], WR[5], Fs[5];
                         WL[0] = eval(&T, u + (size_t)cL * 5 * b, phL + s * b);

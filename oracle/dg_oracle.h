@@ -39,7 +39,19 @@ typedef struct {
     int32_t pos_mode;   /* positivity: 0 rescale the stage outputs, 1 also
                            repeat the step with troubled cells flattened
                            (orc_step_repeat)                                  */
+    int32_t bc[3];      /* adiabatic system, per axis: ORC_BC_*              */
+    double inflow[5];   /* ORC_BC_INFLOW: rho, v_x, v_y, v_z, p at the lower
+                           face                                              */
 } orc_cfg;
+
+/* boundaries of the adiabatic system along an axis (the faces at coordinate 0
+ * and 1): periodic; outflow (the ghost state is the cell's own trace);
+ * reflective (the same with the normal velocity negated); inflow (the lower
+ * face sees the prescribed state cfg->inflow, the upper face is an outflow) */
+#define ORC_BC_PERIODIC 0
+#define ORC_BC_OUTFLOW 1
+#define ORC_BC_REFLECT 2
+#define ORC_BC_INFLOW 3
 
 #define ORC_RUSANOV 0
 #define ORC_HLL 1

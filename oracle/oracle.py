@@ -41,11 +41,12 @@ class Cfg(C.Structure):
     _fields_ = [("N", C.c_int32), ("k", C.c_int32), ("cs", C.c_double), ("av_mode", C.c_int32),
                 ("alpha", C.c_double), ("beta", C.c_double), ("rho_floor", C.c_double), ("cfl", C.c_double),
                 ("rk_stages", C.c_int32), ("riemann", C.c_int32), ("eps_diff", C.c_double),
-                ("pos_mode", C.c_int32)]
+                ("pos_mode", C.c_int32), ("bc", C.c_int32 * 3), ("inflow", C.c_double * 5)]
 
 
 RIEMANN = {"rusanov": 0, "hll": 1, "hllc": 2}
 POSITIVITY = {"scale": 0, "repeat": 1}
+BC = {"periodic": 0, "outflow": 1, "reflect": 2, "inflow": 3}
 REPEAT_SPEED = 1.5
 ST_LIMITED, ST_FAIL, ST_REPEATED = 1, 2, 4
 MARK_NEGATIVE, MARK_FAST = 1, 2
@@ -165,11 +166,15 @@ def legendre_deriv(m: int, x: float) -> float:
 
 
 def make_cfg(N, k, cs=1.0, av_mode=1, alpha=2.0, beta=0.2, rho_floor=1e-3, cfl=0.3, rk_stages=None,
-             riemann="rusanov", eps_diff=0.0, positivity="scale") -> Cfg:
+             riemann="rusanov", eps_diff=0.0, positivity="scale", bc=("periodic",) * 3,
+             inflow=(1.0, 0.0, 0.0, 0.0, 1.0)) -> Cfg:
+    """bc, inflow: boundaries of the adiabatic system per axis ('periodic',
+    'outflow', 'reflect', 'inflow' with the state inflow = (rho, v, p) at the
+    lower face); the isothermal system is periodic."""
     if rk_stages is None:
         rk_stages = 2 if k == 1 else 3
     return Cfg(N, k, cs, av_mode, alpha, beta, rho_floor, cfl, rk_stages, RIEMANN[riemann], eps_diff,
-               POSITIVITY[positivity])
+               POSITIVITY[positivity], (C.c_int32 * 3)(*[BC[x] for x in bc]), (C.c_double * 5)(*inflow))
 
 
 def _shape(cfg, nvar=4):
