@@ -465,7 +465,22 @@ typedef struct {
     int32_t riemann;       /* DG_RIEMANN_RUSANOV (0, default) or DG_RIEMANN_HLLC:
                               HLLC of the Euler equations (Davis bounds, contact
                               speed and star states); DG_RIEMANN_HLL: DG_EINVAL */
+    int32_t bc[3];         /* per axis DG_BC_*; DG_BC_PERIODIC (0) when
+                              zero-initialised                                    */
+    double inflow[5];      /* DG_BC_INFLOW: rho, v_x, v_y, v_z, p at the face at
+                              coordinate 0 (rho > 0, p > 0)                      */
 } dg_adi_opts;
+
+/* Boundaries of the adiabatic system along an axis (its faces at coordinates 0
+ * and 1; the paper's Shu-Osher and implosion problems, Sec. 3.1, run between
+ * them): the Riemann flux of such a face takes the cell's own trace and a
+ * ghost state -- the same trace (outflow, zero gradient), the same trace with
+ * the normal velocity negated (reflective wall: no mass or energy crosses), or
+ * the prescribed state inflow at the face at 0 with an outflow at 1. */
+#define DG_BC_PERIODIC 0
+#define DG_BC_OUTFLOW 1
+#define DG_BC_REFLECT 2
+#define DG_BC_INFLOW 3
 /* Sizes in bytes of one state register, the projection buffer and the scratch
  * (null outputs skipped).  DG_EINVAL for a mesh that is not n x n x n with
  * 1 <= n <= 1024, an order outside 1..3 or a precision other than F32/F64. */

@@ -40,7 +40,8 @@ class Opts(C.Structure):
 class AdiOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rk_stages", C.c_int32), ("cfl", C.c_double), ("gamma", C.c_double),
                 ("stream", C.c_void_p), ("u", C.c_void_p * 3), ("prim", C.c_void_p), ("scratch", C.c_void_p),
-                ("scratch_bytes", C.c_size_t), ("riemann", C.c_int32)]
+                ("scratch_bytes", C.c_size_t), ("riemann", C.c_int32), ("bc", C.c_int32 * 3),
+                ("inflow", C.c_double * 5)]
 
 
 class Forcing(C.Structure):

@@ -20,7 +20,8 @@ class AdiabaticSolver:
 
     def __init__(self, N: int, k: int, gamma: float = 1.4, precision: str = "f32", rk_stages: int | None = None,
                  cfl: float = 0.3, av: str = "vnr", alpha: float = 2.0, beta: float = 0.2, floor: float = 1e-3,
-                 device: str | int = "cuda", riemann: str = "rusanov"):
+                 device: str | int = "cuda", riemann: str = "rusanov", bc=("periodic",) * 3,
+                 inflow=(1.0, 0.0, 0.0, 0.0, 1.0)):
         self.L = B.lib()
         self.h = None
         self.N, self.k, self.gamma = N, k, gamma
@@ -45,7 +46,9 @@ class AdiabaticSolver:
             self.scratch = torch.zeros(int(cb.value), dtype=torch.uint8, device=self.device)
         o = B.AdiOpts(self.prec, rk_stages, cfl, gamma, C.c_void_p(self.stream.cuda_stream),
                       (C.c_void_p * 3)(*[r.data_ptr() for r in self.regs]), self.prim.data_ptr(),
-                      self.scratch.data_ptr(), int(cb.value), {"rusanov": 0, "hllc": 2}[riemann])
+                      self.scratch.data_ptr(), int(cb.value), {"rusanov": 0, "hllc": 2}[riemann],
+                      (C.c_int32 * 3)(*[{"periodic": 0, "outflow": 1, "reflect": 2, "inflow": 3}[x] for x in bc]),
+                      (C.c_double * 5)(*inflow))
         torch.cuda.synchronize(self.device)
         h = C.c_void_p()
         self._check(self.L.dg_adi_init(C.byref(h), C.byref(self.mesh), k, C.byref(self.nu), C.byref(o)), None)

@@ -23,6 +23,7 @@
 // source), [2] dissipated energy (reset: the thermal energy taken out).
 #pragma once
 
+#include "../../include/dg.h"
 #include "dg_launch.cuh"
 #include "dg_tile.cuh"
 
@@ -72,6 +73,8 @@ struct AdiArgs {
     int abar_in, abar_out;  // slots of ctl->abar2 read by the right-hand side / written by a projection
     double beta;     // stage mode: weight of this stage's right-hand side in u^(n+1)
     double cs_reset; // reset mode: the isothermal sound speed
+    int bc[3];       // boundaries per axis (DG_BC_*)
+    double inflow[5];  // DG_BC_INFLOW: rho, v_x, v_y, v_z, p at the face at coordinate 0
 };
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
@@ -653,9 +656,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adi(AdiArgs<T> 
                 } else {
                     fside = 1 - side;
                     const long cc = c0 + c;
-                    if (cc < a.ncell) {
-                        int xyz[3];
-                        cell_xyz(cc, a.N, xyz[0], xyz[1], xyz[2]);
+                    int xyz[3] = {0, 0, 0};
+                    if (cc < a.ncell) cell_xyz(cc, a.N, xyz[0], xyz[1], xyz[2]);
+                    const int bcd = a.bc[Dd];
+                    if (cc < a.ncell && bcd != DG_BC_PERIODIC && xyz[Dd] == (side ? a.N - 1 : 0)) {
+                        // a boundary face: the ghost state is the cell's own trace on it
+                        // (outflow; reflective: the normal velocity negated), or the
+                        // prescribed inflow state (flat) at the face at coordinate 0
+                        fside = side;
+                        if (bcd == DG_BC_INFLOW && side == 0) {
+                            const double rin = a.inflow[0];
+                            const double val = field == 0 ? rin
+                                             : field < 4 ? a.inflow[field]
+                                                         : a.inflow[4] - (double)a.gas.c0 * rin;
+#pragma unroll
+                            for (int l = 0; l < b; ++l) cf[l] = l == 0 ? T(val) : T(0);
+                        } else {
+                            const T* src = field == 0 ? sU + c * 5 * b : sPr + (c * 4 + field - 1) * b;
+                            const T sg = (bcd == DG_BC_REFLECT && field == 1 + Dd) ? T(-1) : T(1);
+#pragma unroll
+                            for (int l = 0; l < b; ++l) cf[l] = sg * src[l];
+                        }
+                    } else if (cc < a.ncell) {
                         const long nc = neighbour_along<Dd>(cc, xyz[Dd], side, a.N);
                         const T* src = field == 0 ? a.u_in + nc * 5 * b : a.pr_in + (nc * 4 + field - 1) * b;
                         if constexpr (b % 4 == 0) {

@@ -70,6 +70,8 @@ cudaError_t adi_k(const Launch& L, double gamma, const AdiLaunch& t)
     a.abar_out = t.abar_out;
     a.beta = t.beta;
     a.cs_reset = t.cs_reset;
+    for (int i = 0; i < 3; ++i) a.bc[i] = t.bc[i];
+    for (int i = 0; i < 5; ++i) a.inflow[i] = t.inflow[i];
     if ((t.flags & F_FORCE) && !t.ahat) return cudaErrorInvalidValue;
     const bool driven = (t.flags & F_FORCE) != 0;
     if (t.mode == ADI_PROJECT) return adi_launch<T, K, ADI_PROJECT>(L, a);

@@ -1680,6 +1680,8 @@ struct dg_adi_ctx {
     double cs_ref = 0.0;    // sound speed the driving is scaled with
     double cs_reset = 0.0;  // > 0: uniform temperature restored after every step
     double kap = 0.0;       // energy offset of the stored state (e_s = e - kap rho): cs_reset^2/(gamma - 1)
+    int bc[3] = {DG_BC_PERIODIC, DG_BC_PERIODIC, DG_BC_PERIODIC};  // boundaries per axis
+    double inflow[5] = {1.0, 0.0, 0.0, 0.0, 1.0};                   // DG_BC_INFLOW state (rho, v, p)
     double injected = 0.0, dissipated = 0.0;
     char* scratch = nullptr;
     Ctl* ctl = nullptr;
@@ -1772,6 +1774,8 @@ cudaError_t adi_go(const dg_adi_ctx* c, const AdiLaunch& t)
     const Launch L = adi_make_launch(c);
     AdiLaunch u = t;
     u.kap = c->kap;
+    for (int i = 0; i < 3; ++i) u.bc[i] = c->bc[i];
+    for (int i = 0; i < 5; ++i) u.inflow[i] = c->inflow[i];
     return c->prec == DG_PREC_F64 ? launch_adi<double>(L, c->gamma, u) : launch_adi<float>(L, c->gamma, u);
 }
 
@@ -1807,6 +1811,16 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     if (opts->rk_stages != 2 && opts->rk_stages != 3) return DG_EINVAL;
     if (opts->riemann != DG_RIEMANN_RUSANOV && opts->riemann != DG_RIEMANN_HLLC) return DG_EINVAL;
     if (!(opts->cfl > 0.0) || !(opts->gamma > 1.0) || !opts->stream || !opts->prim || !opts->scratch) return DG_EINVAL;
+    bool inflow_used = false;
+    for (int d = 0; d < 3; ++d) {
+        if (opts->bc[d] < DG_BC_PERIODIC || opts->bc[d] > DG_BC_INFLOW) return DG_EINVAL;
+        inflow_used |= opts->bc[d] == DG_BC_INFLOW;
+    }
+    if (inflow_used) {
+        for (int i = 0; i < 5; ++i)
+            if (!std::isfinite(opts->inflow[i])) return DG_EINVAL;
+        if (!(opts->inflow[0] > 0.0) || !(opts->inflow[4] > 0.0)) return DG_EINVAL;
+    }
     for (int i = 0; i < 3; ++i)
         if (!opts->u[i]) return DG_EINVAL;
     const AdiScratch sl =
@@ -1821,6 +1835,8 @@ int dg_adi_init(dg_adi_ctx** out, const dg_mesh* mesh, int order, const dg_nu_pa
     ctx->prec = opts->precision;
     ctx->rk = opts->rk_stages;
     ctx->riemann = opts->riemann;
+    for (int d = 0; d < 3; ++d) ctx->bc[d] = opts->bc[d];
+    for (int q = 0; q < 5; ++q) ctx->inflow[q] = opts->inflow[q];
     ctx->ncell = (long)ctx->N * ctx->N * ctx->N;
     ctx->h = 1.0 / ctx->N;
     ctx->gamma = opts->gamma;

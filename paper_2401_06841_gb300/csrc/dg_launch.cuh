@@ -132,6 +132,8 @@ struct AdiLaunch {
     double beta;            // stage weight of the injected energy
     double cs_reset;        // reset mode
     double kap;             // energy offset of the stored states: e_s = e - kap rho
+    int bc[3];              // boundaries per axis (DG_BC_*)
+    double inflow[5];       // DG_BC_INFLOW: rho, v, p at the face at coordinate 0
 };
 template <typename T>
 cudaError_t launch_adi(const Launch& L, double gamma, const AdiLaunch& t);
