@@ -116,9 +116,10 @@ def test_repetition_is_the_plain_step_when_no_cell_is_troubled():
     np.testing.assert_array_equal(w, ref)
 
 
-def test_repetition_is_the_plain_step_from_the_flattened_input():
-    cfg, u, ah, _, _ = driven_start(8, 2, 40)
-    cfgr = O.make_cfg(8, 2, positivity="repeat")
+@pytest.mark.parametrize("k,nsteps", [(2, 40), (1, 60)])  # SSP-RK3 and SSP-RK2
+def test_repetition_is_the_plain_step_from_the_flattened_input(k, nsteps):
+    cfg, u, ah, _, _ = driven_start(8, k, nsteps)
+    cfgr = O.make_cfg(8, k, positivity="repeat")
     w = u.copy()
     st, dtu, att, lev = O.step_repeat(cfgr, w, ah)
     assert st >= 0 and (st & O.ST_REPEATED) and att >= 2 and lev.any()
@@ -132,13 +133,16 @@ def test_repetition_is_the_plain_step_from_the_flattened_input():
     st_ref = O.step(cfgr, ref, ah, dtu)
     np.testing.assert_array_equal(w, ref)
     assert not (st_ref & O.ST_FAIL)
-    # the accepted step troubles no cell but flat ones for their speed, and every
-    # point is at or above the floor
+    # the accepted step troubles no cell but flat ones for their speed; no point is
+    # negative, and the cells whose mean is above the floor have every point at it
+    # or above (the rescaling)
     _, flag = O.step_flags(cfg, uf.copy(), ah, dtu, O.REPEAT_SPEED * O.speed_bound(cfg, uf))
     flat = ~np.any(uf[:, :, 1:] != 0.0, axis=(1, 2))
     assert not (flag & O.MARK_NEGATIVE).any() and not (flag.astype(bool) & ~flat).any()
-    Pv, Pf = point_tables(2)
-    assert (w[:, 0] @ np.vstack([Pv, Pf]).T).min() >= cfg.rho_floor * (1 - 1e-12)
+    Pv, Pf = point_tables(k)
+    pts = (w[:, 0] @ np.vstack([Pv, Pf]).T).min(1)
+    assert pts.min() >= 0.0
+    assert (pts[w[:, 0, 0] > cfg.rho_floor] >= cfg.rho_floor * (1 - 1e-12)).all()
     # scaling higher modes keeps the cell means: the mass is that of u^n
     assert abs(w[:, 0, 0].sum() - u[:, 0, 0].sum()) < 1e-12 * u[:, 0, 0].sum()
 
