@@ -80,9 +80,9 @@ extern "C" {
                               dg_step                                           */
 
 typedef struct {
-    int32_t n[3];          /* cells per axis; this build requires n[0]=n[1]=n[2],
+    int32_t n[3];          /* cells per axis; the library requires n[0]=n[1]=n[2],
                               at most 1024 (cell indices fit in 32 bits)         */
-    double L[3];           /* box size; this build requires L = 1                */
+    double L[3];           /* box size; the library requires L = 1              */
 } dg_mesh;
 
 /* Viscous pressure Pi = alpha rho (h/p)^2 |div v|^2 + beta rho cs (h/p) |div v|
